@@ -1,0 +1,287 @@
+"""Pins of the CPU oracle's SVO stages against facts that do not come from
+the oracle: closed forms, brute force on tiny grids, special cases and
+library routines (Sec. 3.2 of the paper)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2405_06997_gb300 import inputs
+
+
+def _decode(key, D):
+    """Morton decode by plain bit extraction (x -> bit 3i, y -> 3i+1, z -> 3i+2)."""
+    x = y = z = 0
+    for i in range(D):
+        x |= ((key >> (3 * i)) & 1) << i
+        y |= ((key >> (3 * i + 1)) & 1) << i
+        z |= ((key >> (3 * i + 2)) & 1) << i
+    return x, y, z
+
+
+# ---------------------------------------------------------------- Morton keys
+def test_morton_is_bijective_and_nested():
+    D = 4
+    keys = {}
+    for x in range(16):
+        for y in range(16):
+            for z in range(16):
+                k = oracle.morton(x, y, z)
+                assert k < 1 << (3 * D)
+                keys[k] = (x, y, z)
+                # nesting: the key's prefix is the key of the parent cell
+                for m in range(1, D + 1):
+                    assert k >> (3 * m) == oracle.morton(x >> m, y >> m, z >> m)
+    assert len(keys) == 1 << (3 * D)
+    assert all(_decode(k, D) == v for k, v in keys.items())
+
+
+def test_morton_axis_order():
+    assert oracle.morton(1, 0, 0) == 1
+    assert oracle.morton(0, 1, 0) == 2
+    assert oracle.morton(0, 0, 1) == 4
+    assert oracle.morton(2047, 2047, 2047) == (1 << 33) - 1
+
+
+# ---------------------------------------------------------------- voxelisation
+@pytest.mark.parametrize("D", [3, 4, 5, 6])
+def test_closed_box_shell_count(D):
+    sc = inputs.closed_box(1, D)
+    sc.quads = sc.quads[:6]  # walls only
+    s = oracle.SVO(sc, D)
+    leaves = int(s.level_off[D + 1] - s.level_off[D])
+    assert leaves == (1 << 3 * D) - ((1 << D) - 2) ** 3
+
+
+def test_single_quad_leaf_count():
+    D = 5
+    q = np.array([[2, 0.4, 0.1, 0.55, 0.2, 0.9, 1.0, 0.0]], np.float32)
+    sc = inputs.Scene(quads=q, spheres=np.zeros((0, 4), np.float32), albedo=np.ones(1, np.float32),
+                      emission=np.zeros(1, np.float32), lo=np.zeros(3, np.float32), size=1.0)
+    s = oracle.SVO(sc, D)
+    # the closed extents [0.1, 0.55] x [0.2, 0.9] cover cells floor(32 * .) inclusive
+    n1 = int(np.floor(0.55 * 32)) - int(np.floor(0.1 * 32)) + 1
+    n2 = int(np.floor(0.9 * 32)) - int(np.floor(0.2 * 32)) + 1
+    assert int(s.level_off[D + 1] - s.level_off[D]) == n1 * n2
+
+
+def test_sphere_voxels_brute_force():
+    """Sample each closed voxel box densely: if sampled distances to the centre
+    straddle r the surface crosses the box (must be occupied); if all sampled
+    distances are clear of r by more than the sampling gap it cannot (must be
+    empty).  Voxels in between are not decided by sampling and are skipped."""
+    D = 4
+    c = np.array([0.47, 0.52, 0.55])
+    r = 0.31
+    sc = inputs.single_sphere(c, r)
+    s = oracle.SVO(sc, D)
+    ex = s.export()
+    occ = set(int(k) for k in ex["key"][s.level_off[D]:s.level_off[D + 1]])
+    h = 1.0 / 16
+    g = np.linspace(0, 1, 9)
+    pts = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3) * h
+    gap = h * np.sqrt(3) / 8
+    decided = 0
+    for x in range(16):
+        for y in range(16):
+            for z in range(16):
+                p = pts + np.array([x, y, z]) * h
+                dist = np.linalg.norm(p - c, axis=1)
+                k = oracle.morton(x, y, z)
+                if dist.min() <= r <= dist.max():
+                    assert k in occ
+                    decided += 1
+                elif dist.min() > r + gap or dist.max() < r - gap:
+                    assert k not in occ
+                    decided += 1
+    assert decided > 3800  # of 4096
+
+
+# ---------------------------------------------------------------- node layout
+def test_node_layout_matches_coordinate_sets():
+    w = inputs.tiny_box(3)
+    D = w.depth
+    s = oracle.SVO(w.scene, D)
+    ex = s.export()
+    lo = s.level_off
+    leaves = [_decode(int(k), D) for k in ex["key"][lo[D]:lo[D + 1]]]
+    for l in range(D + 1):
+        sh = D - l
+        ref = sorted(set((x >> sh, y >> sh, z >> sh) for x, y, z in leaves),
+                     key=lambda c: oracle.morton(*c))
+        got = [_decode(int(k), l) for k in ex["key"][lo[l]:lo[l + 1]]]
+        assert got == ref
+    for l in range(D):
+        m = ex["child_mask"][lo[l]:lo[l + 1]]
+        assert int(np.unpackbits(m).sum()) == int(lo[l + 2] - lo[l + 1])
+    # parent / first_child consistency by coordinates
+    for node in range(lo[1], lo[D + 1]):
+        p = int(ex["parent"][node])
+        assert ex["key"][node] >> np.uint64(3) == ex["key"][p]
+        fc = int(ex["first_child"][p])
+        k = int(ex["key"][node]) & 7
+        below = bin(int(ex["child_mask"][p]) & ((1 << k) - 1)).count("1")
+        assert fc + below == node
+    assert ex["leaf_count"][0] == lo[D + 1] - lo[D]
+
+
+# ---------------------------------------------------------------- normals
+def test_wall_normals_exact():
+    D = 5
+    sc = inputs.closed_box(1, D)
+    sc.quads = sc.quads[:6]
+    s = oracle.SVO(sc, D)
+    ex = s.export()
+    lo = s.level_off
+    res = 1 << D
+    for node in range(lo[D], lo[D + 1]):
+        x, y, z = _decode(int(ex["key"][node]), D)
+        inner = [0 < c < res - 1 for c in (x, y, z)]
+        if sum(inner) != 2:
+            continue  # edges and corners mix walls
+        expect = np.zeros(3, np.float32)
+        for a, c in enumerate((x, y, z)):
+            if not inner[a]:
+                expect[a] = 1.0 if c == 0 else -1.0
+        np.testing.assert_array_equal(ex["normal"][node], expect)
+
+
+def test_sphere_normals_radial():
+    D = 5
+    c = np.array([0.5, 0.5, 0.5])
+    s = oracle.SVO(inputs.single_sphere(c, 0.3), D)
+    ex = s.export()
+    lo = s.level_off
+    h = 1.0 / (1 << D)
+    for node in range(lo[D], lo[D + 1]):
+        v = (np.array(_decode(int(ex["key"][node]), D)) + 0.5) * h - c
+        v /= np.linalg.norm(v)
+        assert float(ex["normal"][node] @ v) > 1 - 1e-6
+
+
+def test_kmeans_opposite_normals_do_not_cancel():
+    n = np.array([[0, 0, 1], [0, 0, -1]] * 3, np.float32)
+    out = oracle.kmeans2(n, np.ones(6, np.float32))
+    assert abs(abs(float(out[2])) - 1.0) < 1e-7
+
+
+def test_kmeans_matches_sklearn_lloyd():
+    KMeans = pytest.importorskip("sklearn.cluster").KMeans
+    rng = np.random.default_rng(5)
+    for trial in range(20):
+        m = int(rng.integers(2, 12))
+        # two groups around +a and -a (the first point in +a): both clusters stay
+        # populated, so the library's empty-cluster relocation never triggers
+        a = rng.normal(size=3)
+        sign = np.where(rng.uniform(size=(m, 1)) < 0.6, 1.0, -1.0)
+        sign[0] = 1.0
+        sign[1] = -1.0
+        pts = sign * a + 0.4 * np.linalg.norm(a) * rng.normal(size=(m, 3))
+        pts /= np.linalg.norm(pts, axis=1, keepdims=True)
+        pts = pts.astype(np.float32)
+        w = rng.integers(1, 5, m).astype(np.float32)
+        init = np.stack([pts[0], -pts[0]]).astype(np.float64)
+        km = KMeans(n_clusters=2, init=init, n_init=1, max_iter=4, tol=0.0,
+                    algorithm="lloyd").fit(pts.astype(np.float64), sample_weight=w)
+        c0 = km.cluster_centers_[0]
+        if np.linalg.norm(c0) == 0:
+            continue
+        got = oracle.kmeans2(pts, w)
+        np.testing.assert_allclose(got, c0 / np.linalg.norm(c0), atol=2e-6)
+
+
+# ---------------------------------------------------------------- UpdateExitance
+def _q(L):
+    Lc = np.where(L > 0, np.minimum(L, np.float32(2 ** 24)), 0).astype(np.float32)
+    return np.rint(Lc.astype(np.float64) * 2.0 ** 20).astype(np.uint64)
+
+
+def test_accumulate_conserves_sums_and_counts():
+    w = inputs.tiny_box(2)
+    s = oracle.SVO(w.scene, w.depth)
+    s.accumulate(w.rec_pos, w.rec_wout, w.rec_L)
+    e = s.exitance()
+    q = _q(w.rec_L)
+    total = int(q.astype(object).sum())
+    assert int(e["acc_sum"].astype(object).sum()) == total
+    assert int(e["acc_cnt"].sum()) == len(q)
+    assert int(e["tot_sum"][0].astype(object).sum()) == total  # root holds everything
+    assert int(e["tot_cnt"][0].sum()) == len(q)
+
+
+def test_accumulate_brute_force_counts_and_sides():
+    """Records away from voxel boundaries land in the voxel holding them; walls'
+    records leave toward the inside, so all of them are on side 0."""
+    w = inputs.tiny_box(4)
+    D = w.depth
+    s = oracle.SVO(w.scene, D)
+    s.accumulate(w.rec_pos, w.rec_wout, w.rec_L)
+    e = s.exitance()
+    ex = s.export()
+    g = w.rec_pos.astype(np.float64) * (1 << D)
+    inplane = np.abs(g - np.rint(g))
+    # keep records whose in-plane coordinates are clear of voxel boundaries
+    on_plane = inplane < 1e-9
+    clear = (np.where(on_plane, 1.0, inplane) > 1e-4).all(axis=1)
+    cells = np.minimum(np.floor(g), (1 << D) - 1).astype(np.int64)
+    lo = s.level_off
+    key_to_node = {int(k): i for i, k in enumerate(ex["key"][lo[D]:lo[D + 1]], start=int(lo[D]))}
+    want = {}
+    for c, ok in zip(cells, clear):
+        if ok:
+            n = key_to_node[oracle.morton(*c)]
+            want[n] = want.get(n, 0) + 1
+    # nodes that only hold clear records must match exactly
+    all_nodes = {}
+    for c in cells:
+        n = key_to_node.get(oracle.morton(*c))
+        all_nodes[n] = all_nodes.get(n, 0) + 1
+    checked = 0
+    for n, k in want.items():
+        if all_nodes[n] == k:
+            assert int(e["acc_cnt"][n].sum()) == k
+            checked += 1
+    assert checked > 1000
+    # leaves inside a wall (axis-aligned normal) only see side 0
+    axis_aligned = np.abs(ex["normal"]).max(axis=1) == 1.0
+    assert int(e["acc_cnt"][axis_aligned, 1].sum()) == 0
+    assert int(e["acc_cnt"][axis_aligned, 0].sum()) > 0.9 * len(w.rec_L)
+
+
+def test_bottom_up_average_single_wall():
+    """All normals equal: every side-0 sum flows to the root's side 0, whose
+    value is the mean of the quantised records."""
+    D = 5
+    q = np.array([[1, 0.0, 0.0, 1.0, 0.0, 1.0, 1.0, 0.0]], np.float32)
+    sc = inputs.Scene(quads=q, spheres=np.zeros((0, 4), np.float32), albedo=np.ones(1, np.float32),
+                      emission=np.zeros(1, np.float32), lo=np.zeros(3, np.float32), size=1.0)
+    s = oracle.SVO(sc, D)
+    rng = np.random.default_rng(0)
+    n = 5000
+    pos = np.stack([rng.uniform(0, 1, n), np.zeros(n), rng.uniform(0, 1, n)], 1).astype(np.float32)
+    wout = np.tile(np.array([0, 1, 0], np.float32), (n, 1))
+    L = rng.uniform(0, 5, n).astype(np.float32)
+    s.accumulate(pos, wout, L)
+    e = s.exitance()
+    qq = _q(L)
+    assert int(e["tot_sum"][0, 0]) == int(qq.astype(object).sum())
+    assert int(e["tot_cnt"][0, 0]) == n
+    mean = float(np.float32(np.float32(int(qq.astype(object).sum())) * np.float32(2 ** -20)) /
+                 np.float32(n))
+    assert e["value"][0, 0] == np.float32(mean)
+    assert e["value"][0, 1] == e["value"][0, 0]   # empty side takes the other side
+
+
+def test_furnace_values_are_one():
+    D = 5
+    sc = inputs.closed_box(1, D)
+    sc.quads = sc.quads[:6]
+    s = oracle.SVO(sc, D)
+    ex = s.export()
+    lo = s.level_off
+    keys = ex["key"][lo[D]:lo[D + 1]]
+    cells = np.array([_decode(int(k), D) for k in keys], np.float64)
+    pos = ((cells + 0.5) / (1 << D)).astype(np.float32)
+    nrm = ex["normal"][lo[D]:lo[D + 1]]
+    s.accumulate(pos, nrm, np.ones(len(pos), np.float32))
+    v = s.exitance()["value"]
+    assert np.all(v == 1.0)
