@@ -1,0 +1,428 @@
+#!/usr/bin/env python
+"""Guided samples/s of the wavefront path-guiding hot path on GB300.
+
+Workload (default): the 1080p frame -- Cornell-style box with the front open
+plus 200 seeded spheres, SVO depth 9 (512^3), 1920x1080 pinhole primary hits
+(about 1.6M alive rays), one radiance record per hit from one Lambertian
+bounce, 2048 bins cut as Zipf(1.2) runs of spatially sorted rays, 32 x 32
+fields with jitter and blur.  Inputs are synthetic and seeded
+(paper_2405_06997_gb300.inputs).
+
+One step = one frame of the per-frame hot path, all through libwfpg.so:
+  svo_accumulate (scatter the frame's records + bottom-up average),
+  bin_rays, guide_build_pdf, guide_sample (one guided sample per ray),
+  guide_eval_pdf (MIS density of one BSDF direction per ray).
+The SVO itself is built once per scene (reported as svo_build_ms).
+
+value = alive rays (= guided samples) per second, device time of the step
+measured with CUDA events on the launching stream, L2 flushed between steps.
+e2e = the same step through the C ABI with host buffers: pinned-host -> device
+copies of the frame's inputs and device -> host copies of its results inside
+the timed region.
+
+--impl reference times the CPU oracle (the plain C++ restatement of the
+method) on the host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "guided samples/s at 1080p on 1 GB300"
+UNIT = "guided samples/s"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="wfpg", choices=["wfpg", "reference"])
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-bins", type=int, default=64, help="bins in the oracle's timed sample")
+    return ap.parse_args()
+
+
+def dist_init(n_gpus):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl"
+        try:
+            import torch
+            if not torch.cuda.is_available():
+                backend = "gloo"
+        except Exception:
+            backend = "gloo"
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        rows = [r.split(",") for r in out.strip().splitlines() if r.strip()]
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for k, name in enumerate(names):
+                if r[5 + k].lower() in ("active", "1"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def make_workload(seed):
+    from paper_2405_06997_gb300 import inputs
+    w = inputs.frame_spheres(seed)
+    rng = np.random.default_rng(seed * 1000 + 7)
+    mis = inputs.cosine_dirs(w.ray_nrm, rng).astype(np.float32)   # one BSDF direction per ray
+    return w, mis
+
+
+# ------------------------------------------------------------------ oracle timing
+def oracle_frame_time(w, mis, bins_sample, frame=0, svo=None):
+    """Time the CPU oracle on one frame with the field/sampling stages run for a
+    bounded sample of bins; returns (extrapolated frame seconds, detail).  The
+    SVO is built once per scene (not part of the frame)."""
+    import oracle
+    t0 = time.perf_counter()
+    s = svo if svo is not None else oracle.SVO(w.scene, w.depth)
+    t_build = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    s.accumulate(w.rec_pos, w.rec_wout, w.rec_L)
+    t_acc = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    b = s.bin_rays(w.ray_pos, w.ray_nrm, mode=1, sizes=w.bin_sizes, seed=w.seed, frame=frame)
+    t_bin = time.perf_counter() - t0
+    nb = b["n_bins"]
+    sel = np.linspace(0, nb - 1, min(bins_sample, nb)).astype(np.int64)
+    t0 = time.perf_counter()
+    g = s.guide_build(w.ray_pos[b["origin_ray"][sel]], sel, w.grid_n, jitter=True, blur=True,
+                      seed=w.seed, frame=frame)
+    t_guide = time.perf_counter() - t0
+    rays = np.flatnonzero(np.isin(b["bin_of_ray"], sel))
+    remap = np.zeros(nb, np.uint32)
+    remap[sel] = np.arange(len(sel), dtype=np.uint32)
+    local = remap[b["bin_of_ray"][rays]]
+    t0 = time.perf_counter()
+    d, p, c = oracle.guide_sample(g["pdf"], g["cdf_row"], g["cdf_marg"], w.grid_n, local, w.u[rays])
+    oracle.guide_eval_pdf(g["pdf"], w.grid_n, local, mis[rays])
+    t_samp = time.perf_counter() - t0
+    frac_bins = len(sel) / nb
+    frac_rays = max(len(rays), 1) / len(w.ray_pos)
+    t_frame = t_acc + t_bin + t_guide / frac_bins + t_samp / frac_rays
+    detail = dict(svo_build_s=t_build, accumulate_s=t_acc, bin_s=t_bin, guide_s=t_guide,
+                  sample_s=t_samp, bins=len(sel), rays=int(len(rays)))
+    return t_frame, detail
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    import oracle
+    w, mis = make_workload(args.seed)
+    R = len(w.ray_pos)
+    svo = oracle.SVO(w.scene, w.depth)
+    times = []
+    detail = None
+    for k in range(args.warmup + args.steps):
+        t, detail = oracle_frame_time(w, mis, args.cpu_bins, frame=k, svo=svo)
+        if k >= args.warmup:
+            times.append(t)
+    t = statistics.mean(times)
+    value = R / t
+    sample = (f"per step: full-frame accumulate ({len(w.rec_L)} records) and binning ({R} rays); "
+              f"fields/CDFs for {detail['bins']} of {len(w.bin_sizes)} bins and sampling + PDF "
+              f"evaluation for their {detail['rays']} rays, scaled to all bins and rays")
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": w.desc, "rays": R, "bins": len(w.bin_sizes), "grid": w.grid_n,
+                       "svo_depth": w.depth},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_gpu(args, world, rank, local):
+    import torch
+    from paper_2405_06997_gb300 import wfpg as W
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w, mis = make_workload(args.seed)
+    R = len(w.ray_pos)
+    n_rec = len(w.rec_L)
+    B = len(w.bin_sizes)
+    N = w.grid_n
+    stream = torch.cuda.current_stream()
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+
+    # SVO generation, once per scene
+    q = T(w.scene.quads)
+    sp = T(w.scene.spheres)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    svo = W.svo_build(q, sp, w.scene.lo, w.scene.size, w.depth)
+    e1.record()
+    torch.cuda.synchronize()
+    svo_build_ms = e0.elapsed_time(e1)
+
+    inp = dict(rec_pos=T(w.rec_pos), rec_wout=T(w.rec_wout), rec_L=T(w.rec_L), ray_pos=T(w.ray_pos),
+               ray_nrm=T(w.ray_nrm), u=T(w.u), mis=T(mis), sizes=T(w.bin_sizes.view(np.int32)))
+    binout = dict(bin_of_ray=torch.empty(R, dtype=torch.int32, device=dev),
+                  ray_order=torch.empty(R, dtype=torch.int32, device=dev),
+                  bin_offset=torch.empty(B + 1, dtype=torch.int32, device=dev),
+                  origin_ray=torch.empty(B, dtype=torch.int32, device=dev),
+                  n_bins=torch.zeros(1, dtype=torch.int32, device=dev))
+    ws = torch.empty(W.bin_rays_workspace_size(svo, R, W.BIN_RUNS, B), dtype=torch.uint8, device=dev)
+    guide = (torch.empty((B, N * N), dtype=torch.float32, device=dev),
+             torch.empty((B, N * N), dtype=torch.float32, device=dev),
+             torch.empty((B, N), dtype=torch.float32, device=dev))
+    samp = (torch.empty((R, 3), dtype=torch.float32, device=dev),
+            torch.empty(R, dtype=torch.float32, device=dev),
+            torch.empty(R, dtype=torch.int32, device=dev))
+    evalout = torch.empty(R, dtype=torch.float32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    ge0, ge1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def step(frame, x, time_guide=False):
+        W.svo_accumulate(svo, x["rec_pos"], x["rec_wout"], x["rec_L"])
+        W.bin_rays(svo, x["ray_pos"], x["ray_nrm"], mode=W.BIN_RUNS, sizes=x["sizes"], seed=w.seed,
+                   frame=frame, bin_cap=B, out=binout, workspace=ws)
+        if time_guide:
+            ge0.record()
+        W.guide_build_pdf(svo, x["ray_pos"], binout["origin_ray"], binout["n_bins"], B, N=N,
+                          jitter=True, blur=True, seed=w.seed, frame=frame, out=guide)
+        if time_guide:
+            ge1.record()
+        W.guide_sample(*guide, N, binout["bin_of_ray"], x["u"], out=samp)
+        W.guide_eval_pdf(guide[0], N, binout["bin_of_ray"], x["mis"], out=evalout)
+
+    for k in range(args.warmup):
+        step(k, inp)
+    torch.cuda.synchronize()
+    status = svo.status()
+
+    clocks = ClockSampler(local) if rank == 0 else None
+    if clocks:
+        clocks.start()
+    launches0 = W.kernel_launches()
+    barrier(world)
+    torch.cuda.synchronize()
+    step_ms, guide_ms = [], []
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.zero_()            # evict L2 between timed steps (outside the timed events)
+        ev[k][0].record()
+        step(args.warmup + k, inp, time_guide=True)
+        ev[k][1].record()
+        ge1.synchronize()
+        guide_ms.append(ge0.elapsed_time(ge1))
+    torch.cuda.synchronize()
+    barrier(world)
+    launches = W.kernel_launches() - launches0
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    ms = statistics.mean(step_ms)
+    ms_max = max_over_ranks(ms, world)
+    rays_all = sum_over_ranks(float(R), world)
+    value = rays_all / (ms_max / 1e3)
+
+    # end to end through the C ABI with host buffers
+    pinned = {k: v.cpu().pin_memory() for k, v in inp.items()}
+    dev_in = {k: torch.empty_like(v) for k, v in inp.items()}
+    host_out = [torch.empty(t.shape, dtype=t.dtype, pin_memory=True) for t in (*samp, evalout)]
+    h2d = sum(v.numel() * v.element_size() for v in pinned.values())
+    d2h = sum(t.numel() * t.element_size() for t in host_out)
+
+    def e2e_step(frame):
+        for k, v in pinned.items():
+            dev_in[k].copy_(v, non_blocking=True)
+        step(frame, dev_in)
+        for h, d in zip(host_out, (*samp, evalout)):
+            h.copy_(d, non_blocking=True)
+
+    for k in range(2):
+        e2e_step(1000 + k)
+    torch.cuda.synchronize()
+    e2e_ms = []
+    for k in range(max(3, args.steps // 2)):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        e2e_step(2000 + k)
+        b.record()
+        b.synchronize()
+        e2e_ms.append(a.elapsed_time(b))
+    e2e_v = rays_all / (max_over_ranks(statistics.mean(e2e_ms), world) / 1e3)
+    clk = clocks.stop() if clocks else None
+
+    if rank != 0:
+        return
+    # roofline of the dominant kernel (guide_build_pdf's field kernel)
+    peak, peak_kind = measured_peaks()
+    gms = statistics.mean(guide_ms)
+    alg = trace_algorithmic_bytes(w, B, N)
+    achieved = alg["bytes"] / (gms / 1e3) / 1e9
+    traffic = read_profile_traffic()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": w.desc, "rays": R, "records": n_rec, "bins": B, "grid": N,
+                   "svo_depth": w.depth, "svo_nodes": svo.n_nodes, "l2": "flushed (256 MiB write) between steps",
+                   "parallelism": f"replicas x{world}"},
+        "svo_build_ms": svo_build_ms,
+        "guide_build_ms": gms,
+        "status": status,
+        "gpu_launches": launches,
+        "e2e": {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "roofline": {"kernel": "k_guide_build", "bound": "hbm", "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                     "peak_kind": peak_kind, "algorithmic_bytes": alg["bytes"],
+                     "algorithmic_model": alg["model"]},
+        "clocks": clk,
+    }
+    if not args.no_cpu_baseline:
+        t_frame, detail = oracle_frame_time(w, mis, args.cpu_bins)
+        line["cpu_baseline"] = {
+            "value": R / t_frame, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"one frame: full accumulate + binning, fields for {detail['bins']} of {B} "
+                      f"bins and sampling/eval of their {detail['rays']} rays, scaled to the frame"}
+    print(json.dumps(line))
+
+
+def trace_algorithmic_bytes(w, B, N, sample_bins=8):
+    """Bytes the field kernel must move for one launch: its outputs (pdf,
+    cdf_row, cdf_marg: B (2 N^2 + N) 4 B) plus, per cone ray, one 8-byte node
+    record per block the walk passes (the oracle counts the maximal empty
+    blocks and leaves on a sample of bins) and the hit node's normal and values
+    (16 + 8 B)."""
+    import oracle
+    s = oracle.SVO(w.scene, w.depth)
+    b = s.bin_rays(w.ray_pos, w.ray_nrm, mode=1, sizes=w.bin_sizes, seed=w.seed, frame=0)
+    sel = np.linspace(0, b["n_bins"] - 1, sample_bins).astype(np.int64)
+    g = s.guide_build(w.ray_pos[b["origin_ray"][sel]], sel, N, jitter=True, blur=True, seed=w.seed,
+                      count_blocks=True)
+    blocks_per_ray = g["blocks"] / (len(sel) * N * N)
+    per_ray = 8.0 * blocks_per_ray + 24.0
+    total = B * (2 * N * N + N) * 4 + B * N * N * per_ray
+    return {"bytes": total, "model": f"outputs B(2N^2+N)*4 + cone rays x (8 B x {blocks_per_ray:.2f} "
+                                     f"blocks + 24 B); blocks counted by the oracle on {len(sel)} bins"}
+
+
+def read_profile_traffic():
+    """DRAM bytes per launch of k_guide_build from the committed ncu summary, if any."""
+    path = os.path.join(ROOT, "profiles", "k_guide_build_frame1080p.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f).get("dram_bytes_per_launch")
+    return None
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_init(args.gpus)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_gpu(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

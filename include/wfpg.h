@@ -1,0 +1,258 @@
+/*
+ * wfpg.h -- C ABI of the GB300 (sm_103a) wavefront path-guiding hot path.
+ *
+ * Method: Yalciner & Akyuz, "Path Guiding for Wavefront Path Tracing: A
+ * Memory Efficient Approach for GPU Path Tracers".  Radiant exitance from
+ * path vertices is cached in one sparse voxel octree (SVO, Sec. 3.2); rays
+ * are binned by position with the SVO (Sec. 3.4, Alg. 2); for each bin a
+ * directional radiance field is cone-traced through the SVO from one origin
+ * (Sec. 3.3, Eq. 6, Alg. 3) and turned into a piecewise-constant PDF/CDF on
+ * the concentric octahedral map (Sec. 3.5, Sec. 3 "Implementation"), which
+ * every ray of the bin samples and which MIS evaluates.
+ *
+ * Conventions shared by every entry point:
+ *  - Return value: WFPG_OK (0) or a negative WFPG_ERR_* code; the message of
+ *    the last failure on the calling thread is wfpg_last_error().  Nothing is
+ *    thrown across the ABI and the library never exits the process.
+ *  - Array arguments are DEVICE pointers owned by the caller (for instance
+ *    torch tensors' data_ptr()), unless a comment says "host".  Layouts are
+ *    stated per argument; "xyz" arrays are n x 3 float32, row-major.
+ *  - `stream` is a cudaStream_t passed as void*.  Work is enqueued on it and
+ *    the call returns without synchronising, except where a comment says the
+ *    call synchronises (svo_build, the export calls, wfpg_svo_status).
+ *  - The SVO handle is owned by the library: svo_build creates it,
+ *    svo_destroy frees it.  Device-side problems (an iteration cap reached, a
+ *    bin count above the caller's capacity, run sizes that do not add up) set
+ *    bits of the handle's status word; wfpg_svo_status reads them.
+ *  - Levels are numbered from the root = 0 to the leaves = depth (the paper
+ *    counts the root as level 1: its l_min = k is l_min = k - 1 here).
+ */
+#ifndef WFPG_H
+#define WFPG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define WFPG_API __attribute__((visibility("default")))
+#else
+#define WFPG_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    WFPG_OK = 0,
+    WFPG_ERR_INVALID_ARG = -1,
+    WFPG_ERR_OOM = -2,
+    WFPG_ERR_CUDA = -3,
+    WFPG_ERR_TIMEOUT = -4,
+    WFPG_ERR_CAPACITY = -5
+};
+
+/* bits of the device status word */
+enum {
+    WFPG_STATUS_TRACE_CAP = 1u << 0,    /* a cone ray hit the walk's step cap (treated as a miss) */
+    WFPG_STATUS_BIN_CAPACITY = 1u << 1, /* bin_rays found more bins than bin_cap */
+    WFPG_STATUS_RUN_SIZES = 1u << 2     /* run sizes do not add up to the ray count */
+};
+
+#define WFPG_MAX_DEPTH 11
+
+/* Procedural scene, device arrays owned by the caller.
+ *  quads   n_quads x 8 float32: axis, plane, lo1, hi1, lo2, hi2, nsign, 0 --
+ *          the quad lies in x[axis] = plane, spans [lo1, hi1] on axis
+ *          (axis+1)%3 and [lo2, hi2] on axis (axis+2)%3, normal nsign*e_axis.
+ *  spheres n_spheres x 4 float32: cx, cy, cz, r.
+ *  lo, size: host values, the cubic AABB [lo, lo + size]^3 voxelised. */
+typedef struct wfpg_scene {
+    const float* quads;
+    uint32_t n_quads;
+    const float* spheres;
+    uint32_t n_spheres;
+    float lo[3];
+    float size;
+} wfpg_scene;
+
+typedef struct wfpg_svo wfpg_svo;
+
+/* Read-only description of a built SVO; the device pointers stay valid until
+ * svo_destroy.  Node arrays are indexed by global node id = level_off[l] +
+ * index within level l (levels hold Morton-sorted unique prefixes). */
+typedef struct wfpg_svo_info {
+    int depth;
+    uint32_t n_nodes;
+    uint32_t n_frags;
+    uint32_t level_off[WFPG_MAX_DEPTH + 2];
+    const void* node;          /* n_nodes x {uint32 first_child, uint32 child_mask} */
+    const uint32_t* parent;    /* n_nodes, 0xFFFFFFFF for the root */
+    const float* normal;       /* n_nodes x 4 (nx, ny, nz, 0): side 0 is N, side 1 is -N */
+    const float* value;        /* n_nodes x 2 averaged exitance per side */
+} wfpg_svo_info;
+
+/*
+ * svo_build -- SVO generation (Sec. 3.2; Table 1 "SVO generation").
+ * Conservative voxelisation of the scene at 2^depth leaves per axis (a voxel
+ * is occupied when a primitive's surface meets the closed voxel box; the
+ * paper rasterises triangles after Crassin & Green), Morton-key radix sort,
+ * level-by-level node allocation, and two normals per node from k-means with
+ * k = 2 (Fig. 2).  depth in [1, WFPG_MAX_DEPTH].  Synchronises `stream`.
+ * Errors: INVALID_ARG (depth, counts, empty scene), OOM, CUDA.
+ */
+WFPG_API int svo_build(const wfpg_scene* scene, int depth, void* stream, wfpg_svo** out);
+WFPG_API int svo_destroy(wfpg_svo* svo);
+WFPG_API int svo_get_info(const wfpg_svo* svo, wfpg_svo_info* out /* host */);
+
+/*
+ * svo_reset_exitance -- zero the accumulated records (all sums and counts).
+ */
+WFPG_API int svo_reset_exitance(wfpg_svo* svo, void* stream);
+
+/*
+ * svo_accumulate -- UpdateExitance (Alg. 1; Eq. 5) followed by the
+ * bottom-up average (Sec. 3.2).  n records: pos (xyz), wout (xyz, the
+ * direction the radiance leaves toward, unit) and L (float32, the local
+ * radiance estimate of Eq. 5).  Each record adds round(clamp(L, 0, 2^24) *
+ * 2^20) to the unsigned 64-bit sum, and 1 to the count, of the deepest
+ * existing node holding pos, on side 0 if dot(N, wout) >= 0 else side 1.
+ * Sums persist across calls (a running mean).  Then every inner node's sums
+ * are recomputed from its own records and its children's sums (each child
+ * side routed to the parent side its normal agrees with) and every node's
+ * value[s] = sum * 2^-20 / count (an empty side takes the other side's value,
+ * else 0).  n may be 0 (only the average is recomputed).
+ */
+WFPG_API int svo_accumulate(wfpg_svo* svo, const float* pos, const float* wout, const float* L,
+                   uint32_t n, void* stream);
+
+/* Binning modes */
+enum {
+    WFPG_BIN_PARTITION_S = 0, /* Alg. 2 */
+    WFPG_BIN_RUNS = 1         /* stand-in for bins of a given length mix, see bin_rays */
+};
+
+typedef struct wfpg_bin_params {
+    int mode;          /* WFPG_BIN_PARTITION_S or WFPG_BIN_RUNS */
+    int l_min;         /* PARTITION_S: lowest level a bin may be (root = 0), clamped to [0, depth] */
+    uint32_t c_ray;    /* PARTITION_S: ray-count threshold (0xFFFFFFFF: bins at l_min) */
+    uint32_t n_sizes;  /* RUNS: number of runs (= bins) */
+    uint64_t seed;     /* SelectOrigin random stream */
+    uint32_t frame;    /* SelectOrigin random stream */
+} wfpg_bin_params;
+
+/*
+ * bin_rays_workspace_size -- bytes of device scratch bin_rays needs for n rays
+ * (host call, no device work).
+ */
+WFPG_API int bin_rays_workspace_size(const wfpg_svo* svo, uint32_t n, const wfpg_bin_params* p,
+                            size_t* bytes /* host */);
+
+/*
+ * bin_rays -- Partition-S (Alg. 2; Sec. 3.4) and SelectOrigin (Sec. 3
+ * "Implementation").
+ * PARTITION_S: every ray descends to the deepest existing node holding pos
+ * and counts there; for levels depth .. l_min a node's total is its own
+ * count plus its children's totals and it is marked when total >= c_ray or
+ * at l_min; each ray ascends to its first marked node (itself included; a
+ * ray whose node lies above l_min keeps its node); bins are numbered by
+ * ascending node id.
+ * RUNS: rays are keyed by their cell at level min(6, depth) (Morton order)
+ * and the octant of nrm, stably sorted by key, and the sorted sequence is cut
+ * into runs of the given `sizes` (device, n_sizes uint32, all > 0, summing to
+ * n); run j is bin j.
+ * Outputs (device, caller-owned): bin_of_ray[n]; ray_order[n] = rays stably
+ * sorted by bin; bin_offset[bin_cap + 1] = exclusive prefix of bin sizes;
+ * origin_ray[bin_cap] = for bin b the ray at position floor(u * size_b) of
+ * its run, u the 24-bit uniform of (seed, frame, b); *n_bins_dev = bin count.
+ * If the bin count exceeds bin_cap, bins >= bin_cap are not written and
+ * WFPG_STATUS_BIN_CAPACITY is set.  `workspace` holds at least
+ * bin_rays_workspace_size() bytes (256-byte aligned); its contents on entry
+ * do not matter.  nrm (xyz) is only read in RUNS mode (may be NULL
+ * otherwise), sizes only in RUNS mode.
+ */
+WFPG_API int bin_rays(const wfpg_svo* svo, const float* pos, const float* nrm, uint32_t n,
+             const wfpg_bin_params* p, const uint32_t* sizes, uint32_t* bin_of_ray,
+             uint32_t* ray_order, uint32_t* bin_offset, uint32_t* origin_ray, uint32_t bin_cap,
+             uint32_t* n_bins_dev, void* workspace, size_t workspace_bytes, void* stream);
+
+typedef struct wfpg_guide_params {
+    int N;             /* field side: 8, 16, 32, 64 or 128 (N x N cells) */
+    float eps;         /* initial field value (the paper's epsilon = 1e-2) */
+    int jitter;        /* 1: jittered direction per cell, 0: cell centre */
+    int blur;          /* 1: separable [1 2 1]/4 blur with the octahedral mirror */
+    float t_skip;      /* a hit leaf must be entered at t >= t_skip (world units) */
+    int cos_weight;    /* 1: multiply the node value by |dot(N, d)| */
+    uint64_t seed;     /* jitter random stream */
+    uint32_t frame;    /* jitter random stream */
+} wfpg_guide_params;
+
+/*
+ * guide_build_pdf -- GuideRays up to GeneratePDF-CDF (Alg. 3; Sec. 3.3 and
+ * 3.5).  For each bin b < min(*n_bins_dev, bin_cap) (all bin_cap bins when
+ * n_bins_dev is NULL): the origin is pos[origin_ray[b]] (pos[b] when
+ * origin_ray is NULL); cell (i, j) (column i along u, row j along v) looks
+ * along the octahedral image of its centre (or a jittered point, stream
+ * (seed, frame, b)); the ray marches the SVO to the first occupied leaf
+ * entered at t >= t_skip, takes the ancestor whose squared side is closest
+ * to t^2 * 4 pi / N^2 (Eq. 6) and reads that node's value on the side facing
+ * back along the ray; field = eps + value (0 on a miss), optionally blurred;
+ * row CDFs and the marginal CDF are inclusive scans in warp order; pdf =
+ * field / total * N^2 / (4 pi).
+ * Outputs (device, caller-owned, float32): pdf[bin_cap][N*N],
+ * cdf_row[bin_cap][N*N], cdf_marg[bin_cap][N].  Bins past the count are not
+ * written.
+ */
+WFPG_API int guide_build_pdf(const wfpg_svo* svo, const float* pos, const uint32_t* origin_ray,
+                    const uint32_t* n_bins_dev, uint32_t bin_cap, const wfpg_guide_params* p,
+                    float* pdf, float* cdf_row, float* cdf_marg, void* stream);
+
+/*
+ * guide_sample -- the guided branch of Alg. 3's sampling step: inverse-CDF
+ * sampling of the piecewise-constant density.  Per ray: t0 = u0 * T; the row
+ * is the first marginal entry > t0 (N-1 if none); t1 = u1 * T_row; the
+ * column the first row-CDF entry > t1; the point inside the cell inverts the
+ * CDF linearly; the direction is its octahedral image.
+ * In: pdf/cdf_row/cdf_marg as written by guide_build_pdf for bin_cap bins of
+ * side N; bin_of_ray[n]; u[n][2] in [0, 1).  Out: dir (xyz), pdf_out[n] (the
+ * cell's density), cell[n] = row * N + column.  A ray whose bin is >= bin_cap
+ * gets dir = 0, pdf 0, cell 0xFFFFFFFF.
+ */
+WFPG_API int guide_sample(const float* pdf, const float* cdf_row, const float* cdf_marg, int N,
+                 uint32_t bin_cap, const uint32_t* bin_of_ray, const float* u, uint32_t n,
+                 float* dir, float* pdf_out, uint32_t* cell, void* stream);
+
+/*
+ * guide_eval_pdf -- density of arbitrary directions (needed by MIS; Sec. 3
+ * "Implementation"): the cell of dir under the octahedral map, i =
+ * floor((u + 1) N / 2) clamped to [0, N-1] (same for the row), and that
+ * cell's pdf.  bin[n], dir (xyz, unit) -> out[n]; bins >= bin_cap give 0.
+ */
+WFPG_API int guide_eval_pdf(const float* pdf, int N, uint32_t bin_cap, const uint32_t* bin,
+                   const float* dir, uint32_t n, float* out, void* stream);
+
+/* -------------------------------------------------------------------------
+ * Inspection (used by tests; each synchronises `stream`).  Host buffers are
+ * sized from svo_get_info: n_nodes entries (x2 for per-side arrays, x3 for
+ * normals), n_frags fragment primitive ids, leaves + 1 fragment offsets.
+ */
+WFPG_API int svo_export(const wfpg_svo* svo, uint64_t* key, uint32_t* first_child, uint8_t* child_mask,
+               uint32_t* parent, float* normal3, uint32_t* leaf_count, uint32_t* frag_off,
+               uint32_t* frag_prim, void* stream);
+WFPG_API int svo_export_exitance(const wfpg_svo* svo, uint64_t* acc_sum, uint32_t* acc_cnt,
+                        uint64_t* tot_sum, uint32_t* tot_cnt, float* value, void* stream);
+
+/* status word: host *flags receives the bits; clear != 0 zeroes it.
+ * Synchronises `stream`. */
+WFPG_API int wfpg_svo_status(wfpg_svo* svo, uint32_t* flags, int clear, void* stream);
+
+WFPG_API const char* wfpg_last_error(void);
+
+/* Number of CUDA kernels this library has launched in this process so far
+ * (host-side counter, all threads and streams). */
+WFPG_API unsigned long long wfpg_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WFPG_H */

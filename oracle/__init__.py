@@ -73,7 +73,7 @@ def _declare(L):
         "orc_bin_rays": (C.c_int64, [P, P, P, SZ, I32, I32, U32, P, U32, U64, U32, P, P, P, P,
                                      U32]),
         "orc_guide_build": (None, [P, P, P, U32, I32, F, I32, I32, F, I32, U64, U32, P, P, P, P,
-                                   P]),
+                                   P, P]),
         "orc_guide_sample": (None, [P, P, P, I32, P, P, SZ, P, P, P]),
         "orc_guide_eval_pdf": (None, [P, I32, P, P, SZ, P]),
         "orc_morton": (U64, [U32, U32, U32]),
@@ -192,7 +192,7 @@ class SVO:
                     origin_ray=org[:nb])
 
     def guide_build(self, origins, bin_ids, N, eps=1e-2, jitter=False, blur=False, t_skip=None,
-                    cos_weight=False, seed=1, frame=0, count_steps=False):
+                    cos_weight=False, seed=1, frame=0, count_steps=False, count_blocks=False):
         origins = _c(origins, np.float32).reshape(-1, 3)
         bin_ids = _c(bin_ids, np.uint32)
         nb = len(origins)
@@ -204,12 +204,16 @@ class SVO:
         cr = np.zeros((nb, NN), np.float32)
         cm = np.zeros((nb, N), np.float32)
         steps = np.zeros(1, np.uint64)
+        blocks = np.zeros(1, np.uint64)
         lib().orc_guide_build(self._h, _p(origins), _p(bin_ids), nb, N, float(eps), int(jitter),
                               int(blur), float(t_skip), int(cos_weight), seed, frame, _p(field),
-                              _p(pdf), _p(cr), _p(cm), _p(steps))
+                              _p(pdf), _p(cr), _p(cm), _p(steps),
+                              _p(blocks) if count_blocks else None)
         out = dict(field=field, pdf=pdf, cdf_row=cr, cdf_marg=cm)
         if count_steps:
             out["steps"] = int(steps[0])
+        if count_blocks:
+            out["blocks"] = int(blocks[0])
         return out
 
     def trace(self, o, d, N=None, omega=None, t_skip=None, cos_weight=False):

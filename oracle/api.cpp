@@ -18,7 +18,7 @@ void select_origins(const uint32_t* ray_order, const std::vector<uint32_t>& bin_
                     uint32_t nb, uint64_t seed, uint32_t frame, uint32_t* origin_ray);
 void build_field(const Svo& s, const float o[3], uint32_t bin, int N, float eps, int jitter,
                  float t_skip, int cos_weight, uint64_t seed, uint32_t frame, float* f,
-                 uint64_t* steps);
+                 uint64_t* steps, uint64_t* blocks);
 void blur_field(float* f, int N);
 void warp_order_scan(float* x, int n);
 void pdf_cdf(const float* f, int N, float* pdf, float* cdf_row, float* cdf_marg);
@@ -105,13 +105,13 @@ int64_t orc_bin_rays(const void* sv, const float* pos, const float* nrm, size_t 
 void orc_guide_build(const void* sv, const float* origins, const uint32_t* bin_ids, uint32_t nb,
                      int N, float eps, int jitter, int blur, float t_skip, int cos_weight,
                      uint64_t seed, uint32_t frame, float* field, float* pdf, float* cdf_row,
-                     float* cdf_marg, uint64_t* steps) {
+                     float* cdf_marg, uint64_t* steps, uint64_t* blocks) {
     const Svo* s = static_cast<const Svo*>(sv);
     const size_t NN = (size_t)N * N;
     for (uint32_t k = 0; k < nb; ++k) {
         float* f = field + k * NN;
         build_field(*s, origins + 3 * k, bin_ids[k], N, eps, jitter, t_skip, cos_weight, seed,
-                    frame, f, steps);
+                    frame, f, steps, blocks);
         if (blur) blur_field(f, N);
         pdf_cdf(f, N, pdf + k * NN, cdf_row + k * NN, cdf_marg + (size_t)k * N);
     }

@@ -22,7 +22,7 @@ static constexpr float ONE_MINUS = 0x1.fffffep-1f;
 // epsilon = 1e-2) and the cone-traced radiance is added.
 void build_field(const Svo& s, const float o[3], uint32_t bin, int N, float eps, int jitter,
                  float t_skip, int cos_weight, uint64_t seed, uint32_t frame, float* f,
-                 uint64_t* steps) {
+                 uint64_t* steps, uint64_t* blocks) {
     const float omega = FOUR_PI / (float)(N * N);
     const float tn = 2.0f / (float)N;
     for (int j = 0; j < N; ++j)
@@ -37,8 +37,9 @@ void build_field(const Svo& s, const float o[3], uint32_t bin, int N, float eps,
             float v = ((float)j + x1) * tn - 1.0f;
             float d[3];
             octa_decode(u, v, d);
-            TraceResult r = trace_cell(s, o, d, t_skip, omega, cos_weight);
+            TraceResult r = trace_cell(s, o, d, t_skip, omega, cos_weight, blocks != nullptr);
             if (steps) *steps += r.steps;
+            if (blocks) *blocks += r.blocks;
             f[c] = eps + r.value;
         }
 }
@@ -86,6 +87,16 @@ void warp_order_scan(float* x, int n) {
     }
 }
 
+// A CDF is the warp-order scan followed by a running maximum.  The running
+// maximum is exact and changes nothing unless rounding in the tree-shaped scan
+// made an entry smaller than the one before it; it keeps every CDF
+// non-decreasing, as a CDF is by definition, so "the first entry greater than
+// t" can be found by bisection.
+static void cdf_scan(float* x, int n) {
+    warp_order_scan(x, n);
+    for (int i = 1; i < n; ++i) x[i] = std::max(x[i], x[i - 1]);
+}
+
 // GeneratePDF-CDF (Alg. 3): the field as a piecewise-constant density on the
 // sphere.  Row CDFs (inclusive), then the marginal CDF over row totals; the
 // density of cell c is f_c / T * N^2 / (4 pi) (each cell spans 4 pi / N^2 sr).
@@ -93,11 +104,11 @@ void pdf_cdf(const float* f, int N, float* pdf, float* cdf_row, float* cdf_marg)
     std::vector<float> rt(N);
     for (int j = 0; j < N; ++j) {
         for (int i = 0; i < N; ++i) cdf_row[j * N + i] = f[j * N + i];
-        warp_order_scan(cdf_row + j * N, N);
+        cdf_scan(cdf_row + j * N, N);
         rt[j] = cdf_row[j * N + N - 1];
     }
     for (int j = 0; j < N; ++j) cdf_marg[j] = rt[j];
-    warp_order_scan(cdf_marg, N);
+    cdf_scan(cdf_marg, N);
     float T = cdf_marg[N - 1];
     float nn = (float)(N * N);
     float den = T * FOUR_PI;

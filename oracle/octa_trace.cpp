@@ -133,7 +133,7 @@ void octa_encode(const float d[3], float* u, float* v) {
 // occupied leaf entered at t >= t_skip (reading: t_skip stands in for the
 // paper's ray offset at the origin's own surface).
 TraceResult trace_cell(const Svo& s, const float o[3], const float d[3], float t_skip,
-                       float omega, int cos_weight) {
+                       float omega, int cos_weight, bool count_blocks) {
     TraceResult R{};
     R.hit = 0;
     R.value = 0.0f;
@@ -185,10 +185,24 @@ TraceResult trace_cell(const Svo& s, const float o[3], const float d[3], float t
             }
         }
     }
-    uint32_t steps = 0;
+    uint32_t steps = 0, blocks = 0;
+    int prev_level = -1;
+    uint64_t prev_block = 0;
     for (;;) {
         ++steps;
         uint64_t key = morton((uint32_t)cell[0], (uint32_t)cell[1], (uint32_t)cell[2]);
+        if (count_blocks) {
+            // instrumentation: the largest block holding this cell that is
+            // either one occupied leaf or empty (the child of the deepest
+            // existing ancestor); count each new block the ray enters
+            int L = D;
+            while (L > 0 && s.find(L, key >> (3 * (D - L))) == NONE) --L;
+            int bl = (L == D) ? D : L + 1;
+            uint64_t b = key >> (3 * (D - bl));
+            if (bl != prev_level || b != prev_block) ++blocks;
+            prev_level = bl;
+            prev_block = b;
+        }
         if (t_cur >= t_skip && s.find(D, key) != NONE) {
             R.hit = 1;
             R.leaf_key = key;
@@ -208,6 +222,7 @@ TraceResult trace_cell(const Svo& s, const float o[3], const float d[3], float t
         if (cell[a] < 0 || cell[a] >= res) break;
     }
     R.steps = steps;
+    R.blocks = blocks;
     if (!R.hit) return R;
     // Eq. 6: footprint A = r^2 * omega with r the entry distance; choose the
     // level whose squared node side is closest to A (ties to the finer level)

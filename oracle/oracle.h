@@ -49,11 +49,13 @@ int64_t orc_bin_rays(const void* svo, const float* pos, const float* nrm, size_t
                      uint32_t* bin_offset, uint32_t* origin_ray, uint32_t bin_cap);
 
 /* GuideRays field + PDF/CDF (Alg. 3) for nb bins with the given origins; bin
- * ids select the jitter streams.  field receives the blurred field. */
+ * ids select the jitter streams.  field receives the blurred field.  steps
+ * (if not NULL) accumulates the leaf cells the cone rays entered; blocks (if
+ * not NULL) the maximal empty blocks and leaves they passed (slow). */
 void orc_guide_build(const void* svo, const float* origins, const uint32_t* bin_ids, uint32_t nb,
                      int N, float eps, int jitter, int blur, float t_skip, int cos_weight,
                      uint64_t seed, uint32_t frame, float* field, float* pdf, float* cdf_row,
-                     float* cdf_marg, uint64_t* steps);
+                     float* cdf_marg, uint64_t* steps, uint64_t* blocks);
 void orc_guide_sample(const float* pdf, const float* cdf_row, const float* cdf_marg, int N,
                       const uint32_t* bin, const float* u, size_t n, float* dir, float* p,
                       uint32_t* cell);

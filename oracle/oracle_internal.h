@@ -141,9 +141,10 @@ struct TraceResult {
     uint32_t node;
     int side;
     float value;
-    uint32_t steps;
+    uint32_t steps;   // leaf cells the DDA entered
+    uint32_t blocks;  // maximal empty blocks and leaves passed (when counted)
 };
 TraceResult trace_cell(const Svo& s, const float o[3], const float d[3], float t_skip,
-                       float omega, int cos_weight);
+                       float omega, int cos_weight, bool count_blocks = false);
 
 }  // namespace orc

@@ -1,0 +1,254 @@
+// extern "C" entry points declared in include/wfpg.h: argument checks,
+// handle lifetime, error reporting, and dispatch to the kernels.
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "sort.cuh"
+#include "svo.cuh"
+
+namespace wfpg {
+int build_svo(const wfpg_scene* scene, int D, cudaStream_t st, wfpg_svo* s, std::string& err);
+int accumulate(wfpg_svo* s, const float* pos, const float* wout, const float* L, uint32_t n, cudaStream_t st);
+size_t bin_workspace_bytes(const wfpg_svo* s, uint32_t n, int mode, uint32_t n_sizes);
+int bin_rays_impl(const wfpg_svo* s, const float* pos, const float* nrm, uint32_t n, const wfpg_bin_params* p,
+                  const uint32_t* sizes, uint32_t* bin_of_ray, uint32_t* ray_order, uint32_t* bin_offset,
+                  uint32_t* origin_ray, uint32_t bin_cap, uint32_t* n_bins_dev, void* workspace, size_t ws_bytes,
+                  cudaStream_t st);
+int guide_build_impl(const wfpg_svo* s, const float* pos, const uint32_t* origin_ray, const uint32_t* n_bins_dev,
+                     uint32_t bin_cap, const wfpg_guide_params* p, float* pdf, float* cdf_row, float* cdf_marg,
+                     cudaStream_t st);
+int guide_sample_impl(const float* pdf, const float* cdf_row, const float* cdf_marg, int N, uint32_t bin_cap,
+                      const uint32_t* bin_of_ray, const float* u, uint32_t n, float* dir, float* pdf_out,
+                      uint32_t* cell, cudaStream_t st);
+int guide_eval_impl(const float* pdf, int N, uint32_t bin_cap, const uint32_t* bin, const float* dir, uint32_t n,
+                    float* out, cudaStream_t st);
+}  // namespace wfpg
+
+using namespace wfpg;
+
+namespace wfpg {
+static std::atomic<unsigned long long> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+}  // namespace wfpg
+
+namespace {
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string& msg) {
+    g_last_error = msg;
+    return code;
+}
+int cuda_fail(const char* where) {
+    cudaError_t e = cudaGetLastError();
+    return fail(WFPG_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+bool valid_n(int N) { return N == 8 || N == 16 || N == 32 || N == 64 || N == 128; }
+inline cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
+}  // namespace
+
+extern "C" {
+
+const char* wfpg_last_error(void) { return g_last_error.c_str(); }
+
+unsigned long long wfpg_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+int svo_build(const wfpg_scene* scene, int depth, void* stream, wfpg_svo** out) {
+    if (!scene || !out) return fail(WFPG_ERR_INVALID_ARG, "svo_build: null scene or out");
+    *out = nullptr;
+    if (depth < 1 || depth > WFPG_MAX_DEPTH)
+        return fail(WFPG_ERR_INVALID_ARG, "svo_build: depth must be in [1, " + std::to_string(WFPG_MAX_DEPTH) + "]");
+    if ((uint64_t)scene->n_quads + scene->n_spheres == 0)
+        return fail(WFPG_ERR_INVALID_ARG, "svo_build: the scene has no primitive");
+    if ((uint64_t)scene->n_quads + scene->n_spheres >= (1u << 20))
+        return fail(WFPG_ERR_INVALID_ARG, "svo_build: at most 2^20 - 1 primitives");
+    if ((scene->n_quads && !scene->quads) || (scene->n_spheres && !scene->spheres))
+        return fail(WFPG_ERR_INVALID_ARG, "svo_build: null primitive array");
+    if (!(scene->size > 0.0f) || !std::isfinite(scene->size))
+        return fail(WFPG_ERR_INVALID_ARG, "svo_build: size must be finite and > 0");
+    wfpg_svo* s = new wfpg_svo();
+    cudaGetDevice(&s->device);
+    std::string err;
+    const int rc = build_svo(scene, depth, as_stream(stream), s, err);
+    if (rc != WFPG_OK) {
+        svo_free_arrays(s);
+        delete s;
+        return fail(rc, "svo_build: " + err);
+    }
+    *out = s;
+    return WFPG_OK;
+}
+
+int svo_destroy(wfpg_svo* svo) {
+    if (!svo) return WFPG_OK;
+    svo_free_arrays(svo);
+    delete svo;
+    return WFPG_OK;
+}
+
+int svo_get_info(const wfpg_svo* s, wfpg_svo_info* out) {
+    if (!s || !out) return fail(WFPG_ERR_INVALID_ARG, "svo_get_info: null argument");
+    out->depth = s->D;
+    out->n_nodes = s->n_nodes;
+    out->n_frags = s->n_frags;
+    std::memcpy(out->level_off, s->level_off, sizeof(out->level_off));
+    out->node = s->node;
+    out->parent = s->parent;
+    out->normal = reinterpret_cast<const float*>(s->normal);
+    out->value = reinterpret_cast<const float*>(s->value);
+    return WFPG_OK;
+}
+
+int svo_reset_exitance(wfpg_svo* s, void* stream) {
+    if (!s) return fail(WFPG_ERR_INVALID_ARG, "svo_reset_exitance: null svo");
+    cudaStream_t st = as_stream(stream);
+    const size_t n = s->n_nodes;
+    if (cudaMemsetAsync(s->acc_sum, 0, 16 * n, st) != cudaSuccess ||
+        cudaMemsetAsync(s->acc_cnt, 0, 8 * n, st) != cudaSuccess ||
+        cudaMemsetAsync(s->tot_sum, 0, 16 * n, st) != cudaSuccess ||
+        cudaMemsetAsync(s->tot_cnt, 0, 8 * n, st) != cudaSuccess ||
+        cudaMemsetAsync(s->value, 0, 8 * n, st) != cudaSuccess)
+        return cuda_fail("svo_reset_exitance");
+    return WFPG_OK;
+}
+
+int svo_accumulate(wfpg_svo* s, const float* pos, const float* wout, const float* L, uint32_t n, void* stream) {
+    if (!s) return fail(WFPG_ERR_INVALID_ARG, "svo_accumulate: null svo");
+    if (n && (!pos || !wout || !L)) return fail(WFPG_ERR_INVALID_ARG, "svo_accumulate: null record array");
+    if (accumulate(s, pos, wout, L, n, as_stream(stream)) != WFPG_OK) return cuda_fail("svo_accumulate");
+    return WFPG_OK;
+}
+
+int bin_rays_workspace_size(const wfpg_svo* s, uint32_t n, const wfpg_bin_params* p, size_t* bytes) {
+    if (!s || !p || !bytes) return fail(WFPG_ERR_INVALID_ARG, "bin_rays_workspace_size: null argument");
+    if (p->mode != WFPG_BIN_PARTITION_S && p->mode != WFPG_BIN_RUNS)
+        return fail(WFPG_ERR_INVALID_ARG, "bin_rays_workspace_size: unknown mode");
+    *bytes = bin_workspace_bytes(s, n, p->mode, p->n_sizes);
+    return WFPG_OK;
+}
+
+int bin_rays(const wfpg_svo* s, const float* pos, const float* nrm, uint32_t n, const wfpg_bin_params* p,
+             const uint32_t* sizes, uint32_t* bin_of_ray, uint32_t* ray_order, uint32_t* bin_offset,
+             uint32_t* origin_ray, uint32_t bin_cap, uint32_t* n_bins_dev, void* workspace, size_t ws_bytes,
+             void* stream) {
+    if (!s || !p) return fail(WFPG_ERR_INVALID_ARG, "bin_rays: null svo or params");
+    if (p->mode != WFPG_BIN_PARTITION_S && p->mode != WFPG_BIN_RUNS)
+        return fail(WFPG_ERR_INVALID_ARG, "bin_rays: unknown mode");
+    if (n >= 0x80000000u) return fail(WFPG_ERR_INVALID_ARG, "bin_rays: at most 2^31 - 1 rays");
+    if (n && (!pos || !bin_of_ray || !ray_order)) return fail(WFPG_ERR_INVALID_ARG, "bin_rays: null ray array");
+    if (!bin_offset || !n_bins_dev || (bin_cap && !origin_ray))
+        return fail(WFPG_ERR_INVALID_ARG, "bin_rays: null bin array");
+    if (p->mode == WFPG_BIN_RUNS) {
+        if (n && !nrm) return fail(WFPG_ERR_INVALID_ARG, "bin_rays: RUNS mode needs nrm");
+        if (p->n_sizes == 0 || !sizes) return fail(WFPG_ERR_INVALID_ARG, "bin_rays: RUNS mode needs sizes");
+        if (p->n_sizes > bin_cap)
+            return fail(WFPG_ERR_CAPACITY, "bin_rays: n_sizes exceeds bin_cap");
+    }
+    const size_t need = bin_workspace_bytes(s, n, p->mode, p->n_sizes);
+    if (!workspace || ws_bytes < need)
+        return fail(WFPG_ERR_INVALID_ARG, "bin_rays: workspace smaller than bin_rays_workspace_size() = " +
+                                              std::to_string(need) + " bytes");
+    if (reinterpret_cast<uintptr_t>(workspace) & 255u)
+        return fail(WFPG_ERR_INVALID_ARG, "bin_rays: workspace must be 256-byte aligned");
+    const int rc = bin_rays_impl(s, pos, nrm, n, p, sizes, bin_of_ray, ray_order, bin_offset, origin_ray, bin_cap,
+                                 n_bins_dev, workspace, ws_bytes, as_stream(stream));
+    if (rc == WFPG_ERR_CUDA) return cuda_fail("bin_rays");
+    if (rc != WFPG_OK) return fail(rc, "bin_rays: failed");
+    return WFPG_OK;
+}
+
+int guide_build_pdf(const wfpg_svo* s, const float* pos, const uint32_t* origin_ray, const uint32_t* n_bins_dev,
+                    uint32_t bin_cap, const wfpg_guide_params* p, float* pdf, float* cdf_row, float* cdf_marg,
+                    void* stream) {
+    if (!s || !p) return fail(WFPG_ERR_INVALID_ARG, "guide_build_pdf: null svo or params");
+    if (!valid_n(p->N)) return fail(WFPG_ERR_INVALID_ARG, "guide_build_pdf: N must be 8, 16, 32, 64 or 128");
+    if (!(p->eps >= 0.0f)) return fail(WFPG_ERR_INVALID_ARG, "guide_build_pdf: eps must be >= 0");
+    if (bin_cap && (!pos || !pdf || !cdf_row || !cdf_marg))
+        return fail(WFPG_ERR_INVALID_ARG, "guide_build_pdf: null array");
+    if (guide_build_impl(s, pos, origin_ray, n_bins_dev, bin_cap, p, pdf, cdf_row, cdf_marg, as_stream(stream)) !=
+        WFPG_OK)
+        return cuda_fail("guide_build_pdf");
+    return WFPG_OK;
+}
+
+int guide_sample(const float* pdf, const float* cdf_row, const float* cdf_marg, int N, uint32_t bin_cap,
+                 const uint32_t* bin_of_ray, const float* u, uint32_t n, float* dir, float* pdf_out, uint32_t* cell,
+                 void* stream) {
+    if (!valid_n(N)) return fail(WFPG_ERR_INVALID_ARG, "guide_sample: N must be 8, 16, 32, 64 or 128");
+    if (n && (!pdf || !cdf_row || !cdf_marg || !bin_of_ray || !u || !dir || !pdf_out || !cell))
+        return fail(WFPG_ERR_INVALID_ARG, "guide_sample: null array");
+    if (reinterpret_cast<uintptr_t>(u) & 7u) return fail(WFPG_ERR_INVALID_ARG, "guide_sample: u must be 8-byte aligned");
+    if (guide_sample_impl(pdf, cdf_row, cdf_marg, N, bin_cap, bin_of_ray, u, n, dir, pdf_out, cell,
+                          as_stream(stream)) != WFPG_OK)
+        return cuda_fail("guide_sample");
+    return WFPG_OK;
+}
+
+int guide_eval_pdf(const float* pdf, int N, uint32_t bin_cap, const uint32_t* bin, const float* dir, uint32_t n,
+                   float* out, void* stream) {
+    if (!valid_n(N)) return fail(WFPG_ERR_INVALID_ARG, "guide_eval_pdf: N must be 8, 16, 32, 64 or 128");
+    if (n && (!pdf || !bin || !dir || !out)) return fail(WFPG_ERR_INVALID_ARG, "guide_eval_pdf: null array");
+    if (guide_eval_impl(pdf, N, bin_cap, bin, dir, n, out, as_stream(stream)) != WFPG_OK)
+        return cuda_fail("guide_eval_pdf");
+    return WFPG_OK;
+}
+
+int svo_export(const wfpg_svo* s, uint64_t* key, uint32_t* first_child, uint8_t* child_mask, uint32_t* parent,
+               float* normal3, uint32_t* leaf_count, uint32_t* frag_off, uint32_t* frag_prim, void* stream) {
+    if (!s) return fail(WFPG_ERR_INVALID_ARG, "svo_export: null svo");
+    cudaStream_t st = as_stream(stream);
+    if (cudaStreamSynchronize(st) != cudaSuccess) return cuda_fail("svo_export");
+    const size_t n = s->n_nodes;
+    std::vector<Node> nodes(n);
+    std::vector<float4> nrm(n);
+    bool ok = cudaMemcpy(nodes.data(), s->node, n * sizeof(Node), cudaMemcpyDeviceToHost) == cudaSuccess &&
+              cudaMemcpy(nrm.data(), s->normal, n * sizeof(float4), cudaMemcpyDeviceToHost) == cudaSuccess;
+    if (ok && key) ok = cudaMemcpy(key, s->key, n * 8, cudaMemcpyDeviceToHost) == cudaSuccess;
+    if (ok && parent) ok = cudaMemcpy(parent, s->parent, n * 4, cudaMemcpyDeviceToHost) == cudaSuccess;
+    if (ok && leaf_count) ok = cudaMemcpy(leaf_count, s->leaf_count, n * 4, cudaMemcpyDeviceToHost) == cudaSuccess;
+    const size_t nl = s->level_off[s->D + 1] - s->level_off[s->D];
+    if (ok && frag_off) ok = cudaMemcpy(frag_off, s->frag_off, (nl + 1) * 4, cudaMemcpyDeviceToHost) == cudaSuccess;
+    if (ok && frag_prim) ok = cudaMemcpy(frag_prim, s->frag_prim, (size_t)s->n_frags * 4, cudaMemcpyDeviceToHost) == cudaSuccess;
+    if (!ok) return cuda_fail("svo_export");
+    for (size_t i = 0; i < n; ++i) {
+        if (first_child) first_child[i] = nodes[i].first_child;
+        if (child_mask) child_mask[i] = (uint8_t)nodes[i].mask;
+        if (normal3) {
+            normal3[3 * i + 0] = nrm[i].x;
+            normal3[3 * i + 1] = nrm[i].y;
+            normal3[3 * i + 2] = nrm[i].z;
+        }
+    }
+    return WFPG_OK;
+}
+
+int svo_export_exitance(const wfpg_svo* s, uint64_t* acc_sum, uint32_t* acc_cnt, uint64_t* tot_sum, uint32_t* tot_cnt,
+                        float* value, void* stream) {
+    if (!s) return fail(WFPG_ERR_INVALID_ARG, "svo_export_exitance: null svo");
+    if (cudaStreamSynchronize(as_stream(stream)) != cudaSuccess) return cuda_fail("svo_export_exitance");
+    const size_t n = 2 * (size_t)s->n_nodes;
+    bool ok = true;
+    if (acc_sum) ok = ok && cudaMemcpy(acc_sum, s->acc_sum, n * 8, cudaMemcpyDeviceToHost) == cudaSuccess;
+    if (acc_cnt) ok = ok && cudaMemcpy(acc_cnt, s->acc_cnt, n * 4, cudaMemcpyDeviceToHost) == cudaSuccess;
+    if (tot_sum) ok = ok && cudaMemcpy(tot_sum, s->tot_sum, n * 8, cudaMemcpyDeviceToHost) == cudaSuccess;
+    if (tot_cnt) ok = ok && cudaMemcpy(tot_cnt, s->tot_cnt, n * 4, cudaMemcpyDeviceToHost) == cudaSuccess;
+    if (value) ok = ok && cudaMemcpy(value, s->value, n * 4, cudaMemcpyDeviceToHost) == cudaSuccess;
+    if (!ok) return cuda_fail("svo_export_exitance");
+    return WFPG_OK;
+}
+
+int wfpg_svo_status(wfpg_svo* s, uint32_t* flags, int clear, void* stream) {
+    if (!s || !flags) return fail(WFPG_ERR_INVALID_ARG, "wfpg_svo_status: null argument");
+    cudaStream_t st = as_stream(stream);
+    if (cudaMemcpyAsync(flags, s->status, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return cuda_fail("wfpg_svo_status");
+    if (clear && (cudaMemsetAsync(s->status, 0, 4, st) != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess))
+        return cuda_fail("wfpg_svo_status");
+    return WFPG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,326 @@
+"""Python binding of the wfpg C ABI (include/wfpg.h).
+
+Argument marshalling only: every step of the path runs in libwfpg.so's CUDA
+kernels.  Tensors are torch CUDA tensors (float32 data; uint32 data carried
+in int32 tensors, bit for bit); work is enqueued on the current torch stream.
+There is no CPU fallback: if the library is not built, importing the binding
+raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+_lib = None
+
+P = C.c_void_p
+U32 = C.c_uint32
+U64 = C.c_uint64
+I32 = C.c_int
+F = C.c_float
+SZ = C.c_size_t
+
+WFPG_OK = 0
+ERRORS = {-1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "TIMEOUT", -5: "CAPACITY"}
+STATUS_TRACE_CAP = 1
+STATUS_BIN_CAPACITY = 2
+STATUS_RUN_SIZES = 4
+BIN_PARTITION_S = 0
+BIN_RUNS = 1
+MAX_DEPTH = 11
+NONE = 0xFFFFFFFF
+
+
+class WfpgError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Scene(C.Structure):
+    _fields_ = [("quads", P), ("n_quads", U32), ("spheres", P), ("n_spheres", U32),
+                ("lo", F * 3), ("size", F)]
+
+
+class SvoInfo(C.Structure):
+    _fields_ = [("depth", I32), ("n_nodes", U32), ("n_frags", U32),
+                ("level_off", U32 * (MAX_DEPTH + 2)), ("node", P), ("parent", P), ("normal", P),
+                ("value", P)]
+
+
+class BinParams(C.Structure):
+    _fields_ = [("mode", I32), ("l_min", I32), ("c_ray", U32), ("n_sizes", U32), ("seed", U64),
+                ("frame", U32)]
+
+
+class GuideParams(C.Structure):
+    _fields_ = [("N", I32), ("eps", F), ("jitter", I32), ("blur", I32), ("t_skip", F),
+                ("cos_weight", I32), ("seed", U64), ("frame", U32)]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libwfpg.so (built by __graft_entry__.build() / build.py)."""
+    global _lib
+    if _lib is None:
+        path = library_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"libwfpg.so is not built ({path}); run __graft_entry__.build()")
+        L = C.CDLL(path)
+        sig = {
+            "svo_build": [P, I32, P, P],
+            "svo_destroy": [P],
+            "svo_get_info": [P, P],
+            "svo_reset_exitance": [P, P],
+            "svo_accumulate": [P, P, P, P, U32, P],
+            "bin_rays_workspace_size": [P, U32, P, P],
+            "bin_rays": [P, P, P, U32, P, P, P, P, P, P, U32, P, P, SZ, P],
+            "guide_build_pdf": [P, P, P, P, U32, P, P, P, P, P],
+            "guide_sample": [P, P, P, I32, U32, P, P, U32, P, P, P, P],
+            "guide_eval_pdf": [P, I32, U32, P, P, U32, P, P],
+            "svo_export": [P, P, P, P, P, P, P, P, P, P],
+            "svo_export_exitance": [P, P, P, P, P, P, P],
+            "wfpg_svo_status": [P, P, I32, P],
+        }
+        for name, args in sig.items():
+            fn = getattr(L, name)
+            fn.restype = I32
+            fn.argtypes = args
+        L.wfpg_last_error.restype = C.c_char_p
+        L.wfpg_last_error.argtypes = []
+        L.wfpg_kernel_launches.restype = C.c_ulonglong
+        L.wfpg_kernel_launches.argtypes = []
+        _lib = L
+    return _lib
+
+
+def kernel_launches() -> int:
+    """Kernels launched by libwfpg.so in this process so far."""
+    return int(lib().wfpg_kernel_launches())
+
+
+def _check(rc):
+    if rc != WFPG_OK:
+        raise WfpgError(rc, lib().wfpg_last_error().decode())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return P(s.cuda_stream)
+
+
+def _ptr(t, dtype=None, n=None, what="tensor"):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{what} must be a CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{what} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{what} must be contiguous")
+    if n is not None and t.numel() < n:
+        raise ValueError(f"{what} holds {t.numel()} elements, needs {n}")
+    return P(t.data_ptr())
+
+
+def _np_ptr(a):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+class SVO:
+    """Library-owned sparse voxel octree (wfpg_svo handle)."""
+
+    def __init__(self, handle):
+        self._h = P(handle)
+        info = SvoInfo()
+        _check(lib().svo_get_info(self._h, C.byref(info)))
+        self.depth = int(info.depth)
+        self.n_nodes = int(info.n_nodes)
+        self.n_frags = int(info.n_frags)
+        self.level_off = np.array(info.level_off[: self.depth + 2], np.uint32)
+        self.size = 1.0
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            lib().svo_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def export(self, stream=None):
+        n = self.n_nodes
+        nl = int(self.level_off[self.depth + 1] - self.level_off[self.depth])
+        out = dict(key=np.zeros(n, np.uint64), first_child=np.zeros(n, np.uint32),
+                   child_mask=np.zeros(n, np.uint8), parent=np.zeros(n, np.uint32),
+                   normal=np.zeros((n, 3), np.float32), leaf_count=np.zeros(n, np.uint32),
+                   frag_off=np.zeros(nl + 1, np.uint32), frag_prim=np.zeros(self.n_frags, np.uint32))
+        _check(lib().svo_export(self._h, *[_np_ptr(out[k]) for k in (
+            "key", "first_child", "child_mask", "parent", "normal", "leaf_count", "frag_off",
+            "frag_prim")], _stream(stream)))
+        out["level_off"] = self.level_off.copy()
+        return out
+
+    def exitance(self, stream=None):
+        n = 2 * self.n_nodes
+        out = dict(acc_sum=np.zeros(n, np.uint64), acc_cnt=np.zeros(n, np.uint32),
+                   tot_sum=np.zeros(n, np.uint64), tot_cnt=np.zeros(n, np.uint32),
+                   value=np.zeros(n, np.float32))
+        _check(lib().svo_export_exitance(self._h, *[_np_ptr(out[k]) for k in (
+            "acc_sum", "acc_cnt", "tot_sum", "tot_cnt", "value")], _stream(stream)))
+        return {k: v.reshape(-1, 2) for k, v in out.items()}
+
+    def status(self, clear=True, stream=None) -> int:
+        f = np.zeros(1, np.uint32)
+        _check(lib().wfpg_svo_status(self._h, _np_ptr(f), int(clear), _stream(stream)))
+        return int(f[0])
+
+    def reset_exitance(self, stream=None):
+        _check(lib().svo_reset_exitance(self._h, _stream(stream)))
+
+
+def svo_build(quads: torch.Tensor, spheres: torch.Tensor, lo, size: float, depth: int,
+              stream=None) -> SVO:
+    """SVO generation (Sec. 3.2).  quads [nq, 8], spheres [ns, 4] float32 CUDA."""
+    sc = Scene()
+    sc.quads = _ptr(quads, torch.float32, what="quads") if quads.numel() else None
+    sc.n_quads = quads.shape[0] if quads.numel() else 0
+    sc.spheres = _ptr(spheres, torch.float32, what="spheres") if spheres.numel() else None
+    sc.n_spheres = spheres.shape[0] if spheres.numel() else 0
+    for a in range(3):
+        sc.lo[a] = float(lo[a])
+    sc.size = float(size)
+    h = P()
+    _check(lib().svo_build(C.byref(sc), int(depth), _stream(stream), C.byref(h)))
+    svo = SVO(h.value)
+    svo.size = float(size)
+    return svo
+
+
+def svo_accumulate(svo: SVO, pos, wout, L, stream=None):
+    """UpdateExitance (Eq. 5, Alg. 1) + bottom-up average."""
+    n = L.numel()
+    _check(lib().svo_accumulate(svo.handle, _ptr(pos, torch.float32, 3 * n, "pos"),
+                                _ptr(wout, torch.float32, 3 * n, "wout"),
+                                _ptr(L, torch.float32, n, "L"), n, _stream(stream)))
+
+
+def bin_rays_workspace_size(svo: SVO, n: int, mode=BIN_PARTITION_S, n_sizes=0) -> int:
+    p = BinParams(mode=mode, n_sizes=n_sizes)
+    b = SZ()
+    _check(lib().bin_rays_workspace_size(svo.handle, n, C.byref(p), C.byref(b)))
+    return int(b.value)
+
+
+def bin_rays(svo: SVO, pos, nrm=None, *, mode=BIN_PARTITION_S, l_min=2, c_ray=0xFFFFFFFF,
+             sizes=None, seed=1, frame=0, bin_cap=None, out=None, workspace=None, stream=None):
+    """Partition-S (Alg. 2) or run-length bins, plus SelectOrigin.  Returns a
+    dict of int32 CUDA tensors (uint32 bit patterns) and the bin-count tensor."""
+    n = pos.shape[0]
+    dev = pos.device
+    n_sizes = 0 if sizes is None else sizes.numel()
+    if bin_cap is None:
+        bin_cap = n_sizes if mode == BIN_RUNS else max(1, min(n, svo.n_nodes))
+    if out is None:
+        out = dict(bin_of_ray=torch.empty(n, dtype=torch.int32, device=dev),
+                   ray_order=torch.empty(n, dtype=torch.int32, device=dev),
+                   bin_offset=torch.empty(bin_cap + 1, dtype=torch.int32, device=dev),
+                   origin_ray=torch.empty(bin_cap, dtype=torch.int32, device=dev),
+                   n_bins=torch.zeros(1, dtype=torch.int32, device=dev))
+    need = bin_rays_workspace_size(svo, n, mode, n_sizes)
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(need, dtype=torch.uint8, device=dev)
+    p = BinParams(mode=mode, l_min=l_min, c_ray=c_ray, n_sizes=n_sizes, seed=seed, frame=frame)
+    _check(lib().bin_rays(svo.handle, _ptr(pos, torch.float32, 3 * n, "pos"),
+                          _ptr(nrm, torch.float32, 3 * n, "nrm") if nrm is not None else None,
+                          n, C.byref(p), _ptr(sizes, torch.int32, what="sizes"),
+                          _ptr(out["bin_of_ray"], torch.int32, n), _ptr(out["ray_order"], torch.int32, n),
+                          _ptr(out["bin_offset"], torch.int32, bin_cap + 1),
+                          _ptr(out["origin_ray"], torch.int32, bin_cap), bin_cap,
+                          _ptr(out["n_bins"], torch.int32, 1), _ptr(workspace, torch.uint8),
+                          workspace.numel(), _stream(stream)))
+    out["bin_cap"] = bin_cap
+    return out
+
+
+def default_t_skip(size: float, depth: int) -> float:
+    """2 * sqrt(3) * leaf side: skips the origin's own surface voxels."""
+    h = np.float32(size) / np.float32(1 << depth)
+    return float(np.float32(np.float32(2.0 * np.sqrt(3.0)) * h))
+
+
+def guide_build_pdf(svo: SVO, pos, origin_ray=None, n_bins=None, bin_cap=None, *, N=16, eps=1e-2,
+                    jitter=False, blur=False, t_skip=None, cos_weight=False, seed=1, frame=0,
+                    out=None, stream=None):
+    """GuideRays field + PDF/CDF (Alg. 3).  Returns (pdf, cdf_row, cdf_marg)."""
+    if bin_cap is None:
+        bin_cap = origin_ray.numel() if origin_ray is not None else pos.shape[0]
+    if t_skip is None:
+        t_skip = default_t_skip(svo.size, svo.depth)
+    dev = pos.device
+    if out is None:
+        out = (torch.empty((bin_cap, N * N), dtype=torch.float32, device=dev),
+               torch.empty((bin_cap, N * N), dtype=torch.float32, device=dev),
+               torch.empty((bin_cap, N), dtype=torch.float32, device=dev))
+    pdf, cr, cm = out
+    p = GuideParams(N=N, eps=eps, jitter=int(jitter), blur=int(blur), t_skip=t_skip,
+                    cos_weight=int(cos_weight), seed=seed, frame=frame)
+    _check(lib().guide_build_pdf(svo.handle, _ptr(pos, torch.float32, what="pos"),
+                                 _ptr(origin_ray, torch.int32, what="origin_ray"),
+                                 _ptr(n_bins, torch.int32, 1, "n_bins"), bin_cap, C.byref(p),
+                                 _ptr(pdf, torch.float32, bin_cap * N * N),
+                                 _ptr(cr, torch.float32, bin_cap * N * N),
+                                 _ptr(cm, torch.float32, bin_cap * N), _stream(stream)))
+    return pdf, cr, cm
+
+
+def guide_sample(pdf, cdf_row, cdf_marg, N, bin_of_ray, u, out=None, stream=None):
+    """Inverse-CDF sampling (Alg. 3).  Returns (dir [n,3], pdf [n], cell [n] int32)."""
+    n = bin_of_ray.numel()
+    bin_cap = cdf_marg.numel() // N
+    dev = u.device
+    if out is None:
+        out = (torch.empty((n, 3), dtype=torch.float32, device=dev),
+               torch.empty(n, dtype=torch.float32, device=dev),
+               torch.empty(n, dtype=torch.int32, device=dev))
+    d, p, c = out
+    _check(lib().guide_sample(_ptr(pdf, torch.float32), _ptr(cdf_row, torch.float32),
+                              _ptr(cdf_marg, torch.float32), N, bin_cap,
+                              _ptr(bin_of_ray, torch.int32, n), _ptr(u, torch.float32, 2 * n, "u"), n,
+                              _ptr(d, torch.float32, 3 * n), _ptr(p, torch.float32, n),
+                              _ptr(c, torch.int32, n), _stream(stream)))
+    return d, p, c
+
+
+def guide_eval_pdf(pdf, N, bins, dirs, out=None, stream=None):
+    """PDF of given directions (MIS)."""
+    n = bins.numel()
+    bin_cap = pdf.numel() // (N * N)
+    if out is None:
+        out = torch.empty(n, dtype=torch.float32, device=dirs.device)
+    _check(lib().guide_eval_pdf(_ptr(pdf, torch.float32), N, bin_cap, _ptr(bins, torch.int32, n),
+                                _ptr(dirs, torch.float32, 3 * n), n, _ptr(out, torch.float32, n),
+                                _stream(stream)))
+    return out
+
+
+def svo_from_scene(scene, depth: int, device="cuda", stream=None) -> SVO:
+    """Upload a procedural scene (paper_2405_06997_gb300.inputs.Scene) and build its SVO."""
+    q = torch.as_tensor(np.ascontiguousarray(scene.quads, np.float32).reshape(-1, 8), device=device)
+    s = torch.as_tensor(np.ascontiguousarray(scene.spheres, np.float32).reshape(-1, 4), device=device)
+    return svo_build(q, s, scene.lo, scene.size, depth, stream=stream)
