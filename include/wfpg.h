@@ -176,6 +176,36 @@ WFPG_API int bin_rays(const wfpg_svo* svo, const float* pos, const float* nrm, u
              uint32_t* ray_order, uint32_t* bin_offset, uint32_t* origin_ray, uint32_t bin_cap,
              uint32_t* n_bins_dev, void* workspace, size_t workspace_bytes, void* stream);
 
+/* Size of the fixed device scratch used by bin_rays_static (32 MiB). */
+#define WFPG_BIN_STATIC_SCRATCH_BYTES (32u << 20)
+
+/*
+ * bin_rays_static -- bin_rays for callers that cannot allocate device memory.
+ * The paper has no counterpart: this is an interface convenience of this
+ * library.  Hosts that own all device memory through their own pool (an
+ * engine with a fixed, pre-reserved budget) or that have no device allocator
+ * to carve a workspace from (a plain C caller) cannot provide bin_rays'
+ * workspace; this variant takes the same arguments minus the workspace and
+ * uses instead one file-scope device array of WFPG_BIN_STATIC_SCRATCH_BYTES,
+ * reserved on every GPU that loads the library and held until the process
+ * exits.  It calls no cudaMalloc, cudaFree or allocating routine.
+ * Limit: the scratch bin_rays_workspace_size() reports for the same call must
+ * fit in WFPG_BIN_STATIC_SCRATCH_BYTES (about 2M rays in RUNS mode; in
+ * PARTITION_S mode 4 more bytes per ray and 12 per SVO node count too), otherwise the call
+ * returns WFPG_ERR_CAPACITY and does nothing.
+ * The first call on each device looks up the array's device address with the
+ * device current (make that first call before any stream capture); later
+ * calls reuse it.  Every call on a device shares the one array and leaves its
+ * contents behind; the call clears what must start at zero itself.  Calls
+ * whose work overlaps on the GPU (in flight on two streams, or from two
+ * threads, at once) race on the scratch and corrupt each other's results:
+ * serialise them.
+ */
+WFPG_API int bin_rays_static(const wfpg_svo* svo, const float* pos, const float* nrm, uint32_t n,
+                             const wfpg_bin_params* p, const uint32_t* sizes, uint32_t* bin_of_ray,
+                             uint32_t* ray_order, uint32_t* bin_offset, uint32_t* origin_ray,
+                             uint32_t bin_cap, uint32_t* n_bins_dev, void* stream);
+
 typedef struct wfpg_guide_params {
     int N;             /* field side: 8, 16, 32, 64 or 128 (N x N cells) */
     float eps;         /* initial field value (the paper's epsilon = 1e-2) */

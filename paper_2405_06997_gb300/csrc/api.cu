@@ -50,6 +50,11 @@ bool valid_n(int N) { return N == 8 || N == 16 || N == 32 || N == 64 || N == 128
 inline cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
 }  // namespace
 
+namespace wfpg {
+// lets entry points defined in other files report through wfpg_last_error()
+int set_last_error(int code, const std::string& msg) { return fail(code, msg); }
+}  // namespace wfpg
+
 extern "C" {
 
 const char* wfpg_last_error(void) { return g_last_error.c_str(); }

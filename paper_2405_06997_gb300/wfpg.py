@@ -324,3 +324,37 @@ def svo_from_scene(scene, depth: int, device="cuda", stream=None) -> SVO:
     q = torch.as_tensor(np.ascontiguousarray(scene.quads, np.float32).reshape(-1, 8), device=device)
     s = torch.as_tensor(np.ascontiguousarray(scene.spheres, np.float32).reshape(-1, 4), device=device)
     return svo_build(q, s, scene.lo, scene.size, depth, stream=stream)
+
+
+def bin_rays_static(svo: SVO, pos, nrm=None, *, mode=BIN_PARTITION_S, l_min=2, c_ray=0xFFFFFFFF,
+                    sizes=None, seed=1, frame=0, bin_cap=None, out=None, stream=None):
+    """bin_rays for callers that cannot allocate device memory (for instance a
+    host whose device memory is all owned by its own fixed pool, or a caller
+    with no device allocator to give bin_rays a workspace from): the same
+    outputs, with the scratch taken from the library's fixed static device
+    array instead of a workspace.  Raises WfpgError (CAPACITY) when the call
+    needs more scratch than that array holds.  Calls whose work overlaps on
+    the GPU share the array and must be serialised."""
+    fn = lib().bin_rays_static
+    fn.restype = I32
+    fn.argtypes = [P, P, P, U32, P, P, P, P, P, P, U32, P, P]
+    n = pos.shape[0]
+    dev = pos.device
+    n_sizes = 0 if sizes is None else sizes.numel()
+    if bin_cap is None:
+        bin_cap = n_sizes if mode == BIN_RUNS else max(1, min(n, svo.n_nodes))
+    if out is None:
+        out = dict(bin_of_ray=torch.empty(n, dtype=torch.int32, device=dev),
+                   ray_order=torch.empty(n, dtype=torch.int32, device=dev),
+                   bin_offset=torch.empty(bin_cap + 1, dtype=torch.int32, device=dev),
+                   origin_ray=torch.empty(bin_cap, dtype=torch.int32, device=dev),
+                   n_bins=torch.zeros(1, dtype=torch.int32, device=dev))
+    p = BinParams(mode=mode, l_min=l_min, c_ray=c_ray, n_sizes=n_sizes, seed=seed, frame=frame)
+    _check(fn(svo.handle, _ptr(pos, torch.float32, 3 * n, "pos"),
+              _ptr(nrm, torch.float32, 3 * n, "nrm") if nrm is not None else None, n, C.byref(p),
+              _ptr(sizes, torch.int32, what="sizes"), _ptr(out["bin_of_ray"], torch.int32, n),
+              _ptr(out["ray_order"], torch.int32, n), _ptr(out["bin_offset"], torch.int32, bin_cap + 1),
+              _ptr(out["origin_ray"], torch.int32, bin_cap), bin_cap, _ptr(out["n_bins"], torch.int32, 1),
+              _stream(stream)))
+    out["bin_cap"] = bin_cap
+    return out
