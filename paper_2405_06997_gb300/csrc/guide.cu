@@ -55,160 +55,48 @@ __device__ __forceinline__ Node load_node(const TraceArgs& T, const Node* s_node
     return n;
 }
 
-// crossing into cell j along axis b (moving in direction st) happens at the
-// boundary j (st > 0) or j + 1 (st < 0); "before (tx, a)" in (time, axis) order
-__device__ __forceinline__ bool crossed(int b, int j, int st, float g, float inv, float tx, int a) {
-    const int kb = st > 0 ? j : j + 1;
-    const float tc = __fmul_rn(__fsub_rn((float)kb, g), inv);
-    return tc < tx || (tc == tx && b < a);
+// time of the crossing into cell j along one axis: boundary j when moving up,
+// j + 1 when moving down; evaluated afresh from the integer boundary
+__device__ __forceinline__ float cross_time(int j, bool up, float g, float inv) {
+    return __fmul_rn(__fsub_rn((float)(up ? j : j + 1), g), inv);
 }
 
-// Cone-traced radiance of one direction from origin o; 0 on a miss.
-__device__ float trace_cell(const TraceArgs& T, const Node* s_nodes, const float o[3], const float3 dv,
-                            uint32_t* status) {
-    const int D = T.D;
-    const int res = 1 << D;
-    const float fres = (float)res;
-    const float d[3] = {dv.x, dv.y, dv.z};
-    float g[3], dsc[3], inv[3];
-    int st[3];
-    bool mv[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        g[a] = __fmul_rn(__fsub_rn(o[a], T.lo[a]), T.scale);
-        dsc[a] = __fmul_rn(d[a], T.scale);
-        mv[a] = d[a] != 0.0f;
-        inv[a] = mv[a] ? __fdiv_rn(1.0f, dsc[a]) : 0.0f;
-        st[a] = d[a] > 0.0f ? 1 : -1;
-    }
-    int cell[3];
-    float t = 0.0f;
-    const bool inside = (g[0] >= 0.0f) && (g[0] <= fres) && (g[1] >= 0.0f) && (g[1] <= fres) &&
-                        (g[2] >= 0.0f) && (g[2] <= fres);
-    if (inside) {
-#pragma unroll
-        for (int a = 0; a < 3; ++a) cell[a] = min((int)g[a], res - 1);
+// Index along one axis that the leaf-by-leaf walk reaches at the crossing
+// (tx, a): the last cell of the block [lo, lo + size) on this axis whose
+// entry crossing comes before (tx, a) in (time, axis) order, starting from
+// the current index c.  `before` says whether this axis precedes axis a.
+__device__ __forceinline__ int advance_axis(int c, int lo, int size, float g, float inv, float ds, float tx,
+                                            bool before) {
+    if (inv == 0.0f || size == 1) return c;
+    const int hi = lo + size - 1;
+    int j = (int)floorf(g + tx * ds);  // estimate only; the checks below decide
+    j = max(lo, min(hi, j));
+    if (inv > 0.0f) {
+        j = max(j, c);
+        while (j < hi) {
+            const float tc = cross_time(j + 1, true, g, inv);
+            if (tc < tx || (tc == tx && before)) ++j;
+            else break;
+        }
+        while (j > c) {
+            const float tc = cross_time(j, true, g, inv);
+            if (tc < tx || (tc == tx && before)) break;
+            --j;
+        }
     } else {
-        float tn = 0.0f, tf = __int_as_float(0x7f800000);
-        int enter = -1;
-        for (int a = 0; a < 3; ++a) {
-            if (!mv[a]) {
-                if (!(g[a] >= 0.0f && g[a] <= fres)) return 0.0f;
-                continue;
-            }
-            const float t0 = __fmul_rn(__fsub_rn(0.0f, g[a]), inv[a]);
-            const float t1 = __fmul_rn(__fsub_rn(fres, g[a]), inv[a]);
-            const float lo_t = (t1 < t0) ? t1 : t0;
-            const float hi_t = (t0 < t1) ? t1 : t0;
-            if (lo_t > tn) {
-                tn = lo_t;
-                enter = a;
-            }
-            tf = (hi_t < tf) ? hi_t : tf;
+        j = min(j, c);
+        while (j > lo) {
+            const float tc = cross_time(j - 1, false, g, inv);
+            if (tc < tx || (tc == tx && before)) --j;
+            else break;
         }
-        if (!(tn <= tf)) return 0.0f;
-        t = tn;
-        for (int a = 0; a < 3; ++a) {
-            if (a == enter) {
-                cell[a] = st[a] > 0 ? 0 : res - 1;
-            } else {
-                const float p = __fadd_rn(g[a], __fmul_rn(tn, dsc[a]));
-                const int c = (p >= 0.0f) ? (int)p : 0;
-                cell[a] = min(c, res - 1);
-            }
+        while (j < c) {
+            const float tc = cross_time(j, false, g, inv);
+            if (tc < tx || (tc == tx && before)) break;
+            ++j;
         }
     }
-    const float INF = __int_as_float(0x7f800000);
-    const int cap = 3 * res + 16;
-    bool hit = false;
-    for (int it = 0; it < cap; ++it) {
-        // deepest existing node holding the current cell
-        uint32_t node = 0;
-        int l = 0;
-        while (l < D) {
-            const Node nd = load_node(T, s_nodes, node);
-            const int k = child_slot(cell, l, D);
-            if (!((nd.mask >> k) & 1u)) break;
-            node = child_id(nd, k);
-            ++l;
-        }
-        int sl;
-        if (l == D) {
-            if (t >= T.t_skip) {
-                hit = true;
-                break;
-            }
-            sl = 0;
-        } else {
-            sl = D - l - 1;  // the empty child block at level l + 1
-        }
-        const int size = 1 << sl;
-        int base[3];
-        float te[3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            base[a] = (cell[a] >> sl) << sl;
-            const int kb = st[a] > 0 ? base[a] + size : base[a];
-            te[a] = mv[a] ? __fmul_rn(__fsub_rn((float)kb, g[a]), inv[a]) : INF;
-        }
-        const int a = (te[0] <= te[1] && te[0] <= te[2]) ? 0 : (te[1] <= te[2] ? 1 : 2);
-        const float tx = te[a];
-        if (tx == INF) return 0.0f;
-        int nc[3];
-#pragma unroll
-        for (int b = 0; b < 3; ++b) {
-            if (b == a) {
-                nc[b] = st[b] > 0 ? base[b] + size : base[b] - 1;
-            } else if (!mv[b] || size == 1) {
-                nc[b] = cell[b];
-            } else {
-                const int lo_b = base[b], hi_b = base[b] + size - 1;
-                const float est = g[b] + tx * dsc[b];
-                int j = (int)floorf(est);
-                j = max(lo_b, min(hi_b, j));
-                if (st[b] > 0) {
-                    j = max(j, cell[b]);
-                    while (j < hi_b && crossed(b, j + 1, 1, g[b], inv[b], tx, a)) ++j;
-                    while (j > cell[b] && !crossed(b, j, 1, g[b], inv[b], tx, a)) --j;
-                } else {
-                    j = min(j, cell[b]);
-                    while (j > lo_b && crossed(b, j - 1, -1, g[b], inv[b], tx, a)) --j;
-                    while (j < cell[b] && !crossed(b, j, -1, g[b], inv[b], tx, a)) ++j;
-                }
-                nc[b] = j;
-            }
-        }
-        t = tx;
-        cell[0] = nc[0];
-        cell[1] = nc[1];
-        cell[2] = nc[2];
-        if (nc[a] < 0 || nc[a] >= res) return 0.0f;
-    }
-    if (!hit) {
-        atomicOr(status, (uint32_t)WFPG_STATUS_TRACE_CAP);
-        return 0.0f;
-    }
-    // Eq. 6: footprint A = t^2 * omega; level whose squared side is closest
-    const float A = __fmul_rn(__fmul_rn(t, t), T.omega);
-    float side = T.S;
-    int best = 0;
-    float bd = INF;
-    for (int l = 0; l <= D; ++l) {
-        const float diff = fabsf(__fsub_rn(__fmul_rn(side, side), A));
-        if (diff <= bd) {
-            bd = diff;
-            best = l;
-        }
-        side = __fmul_rn(side, 0.5f);
-    }
-    uint32_t node = 0;
-    for (int l = 0; l < best; ++l) node = child_id(load_node(T, s_nodes, node), child_slot(cell, l, D));
-    const float4 N = T.normal[node];
-    const float2 V = T.value[node];
-    const float dd = __fadd_rn(__fadd_rn(__fmul_rn(N.x, d[0]), __fmul_rn(N.y, d[1])), __fmul_rn(N.z, d[2]));
-    float L = (dd <= 0.0f) ? V.x : V.y;  // the side facing back along the ray
-    if (T.cos_weight) L = __fmul_rn(L, fabsf(dd));
-    return L;
+    return j;
 }
 
 // inclusive scan of a row of N floats in warp order (chunks of 32: rounds
@@ -247,14 +135,19 @@ __global__ void __launch_bounds__(kGuideThreads) k_guide_build(TraceArgs T, Guid
                                                                float* __restrict__ cdf_row,
                                                                float* __restrict__ cdf_marg, uint32_t* status) {
     extern __shared__ __align__(16) unsigned char smem[];
-    Node* s_nodes = reinterpret_cast<Node*>(smem);
     const int N = G.N, NN = N * N;
-    float* field = reinterpret_cast<float*>(smem + sizeof(Node) * T.smem_nodes);
+    const int D = T.D;
+    Node* s_nodes = reinterpret_cast<Node*>(smem);
+    uint32_t* s_stack = reinterpret_cast<uint32_t*>(smem + sizeof(Node) * T.smem_nodes);
+    float* field = reinterpret_cast<float*>(s_stack + (D + 1) * kGuideThreads);
     float* tmp = field + NN;
     float* rowtot = tmp + NN;
     float* marg = rowtot + N;
+    __shared__ int s_next;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t lt = (1u << lane) - 1u;
     constexpr int kWarps = kGuideThreads / 32;
+    uint32_t* stk = s_stack + tid;  // this thread's node path, one entry per level (stride = block size)
     for (uint32_t i = tid; i < T.smem_nodes; i += kGuideThreads) {
         const uint2 v = __ldg(reinterpret_cast<const uint2*>(T.node) + i);
         s_nodes[i].first_child = v.x;
@@ -263,30 +156,201 @@ __global__ void __launch_bounds__(kGuideThreads) k_guide_build(TraceArgs T, Guid
     __syncthreads();
     const uint32_t nb = n_bins_dev ? min(*n_bins_dev, bin_cap) : bin_cap;
     const float tn = __fdiv_rn(2.0f, (float)N);
+    const int res = 1 << D;
+    const float fres = (float)res;
+    const float INF = __int_as_float(0x7f800000);
+    const int cap = 3 * res + 16;
     for (uint32_t b = blockIdx.x; b < nb; b += gridDim.x) {
         const uint32_t r = origin_ray ? origin_ray[b] : b;
-        float o[3];
-        if (r == kNone) {
-            o[0] = o[1] = o[2] = __int_as_float(0x7fc00000);  // no origin: every cell misses
-        } else {
-            o[0] = pos[3 * (size_t)r + 0];
-            o[1] = pos[3 * (size_t)r + 1];
-            o[2] = pos[3 * (size_t)r + 2];
+        float ox = 0.0f, oy = 0.0f, oz = 0.0f;
+        if (r != kNone) {
+            ox = pos[3 * (size_t)r + 0];
+            oy = pos[3 * (size_t)r + 1];
+            oz = pos[3 * (size_t)r + 2];
         }
+        const float gx = __fmul_rn(__fsub_rn(ox, T.lo[0]), T.scale);
+        const float gy = __fmul_rn(__fsub_rn(oy, T.lo[1]), T.scale);
+        const float gz = __fmul_rn(__fsub_rn(oz, T.lo[2]), T.scale);
         const uint64_t jseed = purpose(G.seed, kJitterPurpose);
         const uint64_t jstream = bin_stream(G.frame, b);
-        for (int c = tid; c < NN; c += kGuideThreads) {
-            const int i = c % N, j = c / N;
-            float x0 = 0.5f, x1 = 0.5f;
-            if (G.jitter) {
-                x0 = uniform01(jseed, jstream, 2ull * c);
-                x1 = uniform01(jseed, jstream, 2ull * c + 1);
+        if (tid == 0) s_next = 0;
+        __syncthreads();
+        // ---- cone rays: each lane marches one cell's ray; finished lanes take the next cell
+        int cid = -1;  // current cell (-1: none, >= NN: no work left)
+        float dx = 0.f, dy = 0.f, dz = 0.f, ivx = 0.f, ivy = 0.f, ivz = 0.f, t = 0.f;
+        int cx = 0, cy = 0, cz = 0, level = 0, steps = 0;
+        uint32_t node = 0;
+        for (;;) {
+            const bool idle = cid < 0;
+            const uint32_t need = __ballot_sync(0xffffffffu, idle);
+            if (need) {
+                const int leader = __ffs(need) - 1;
+                int base = 0;
+                if (lane == leader) base = atomicAdd(&s_next, __popc(need));
+                base = __shfl_sync(0xffffffffu, base, leader);
+                if (idle) {
+                    cid = base + __popc(need & lt);
+                    if (cid < NN) {
+                        // start the cone ray of cell (i, j)
+                        const int i = cid % N, j = cid / N;
+                        float x0 = 0.5f, x1 = 0.5f;
+                        if (G.jitter) {
+                            x0 = uniform01(jseed, jstream, 2ull * cid);
+                            x1 = uniform01(jseed, jstream, 2ull * cid + 1);
+                        }
+                        const float u = __fsub_rn(__fmul_rn(__fadd_rn((float)i, x0), tn), 1.0f);
+                        const float v = __fsub_rn(__fmul_rn(__fadd_rn((float)j, x1), tn), 1.0f);
+                        const float3 d = octa_to_dir(u, v);
+                        dx = d.x;
+                        dy = d.y;
+                        dz = d.z;
+                        const float dsx = __fmul_rn(dx, T.scale), dsy = __fmul_rn(dy, T.scale),
+                                    dsz = __fmul_rn(dz, T.scale);
+                        ivx = dx != 0.0f ? __fdiv_rn(1.0f, dsx) : 0.0f;
+                        ivy = dy != 0.0f ? __fdiv_rn(1.0f, dsy) : 0.0f;
+                        ivz = dz != 0.0f ? __fdiv_rn(1.0f, dsz) : 0.0f;
+                        bool alive = r != kNone;
+                        const bool inside = gx >= 0.0f && gx <= fres && gy >= 0.0f && gy <= fres && gz >= 0.0f &&
+                                            gz <= fres;
+                        t = 0.0f;
+                        if (alive && inside) {
+                            cx = min((int)gx, res - 1);
+                            cy = min((int)gy, res - 1);
+                            cz = min((int)gz, res - 1);
+                        } else if (alive) {
+                            // slab entry into the grid box
+                            float tnr = 0.0f, tfr = INF;
+                            int enter = -1;
+                            const float gg[3] = {gx, gy, gz}, iv[3] = {ivx, ivy, ivz};
+#pragma unroll
+                            for (int a = 0; a < 3; ++a) {
+                                if (iv[a] == 0.0f) {
+                                    if (!(gg[a] >= 0.0f && gg[a] <= fres)) alive = false;
+                                    continue;
+                                }
+                                const float t0 = __fmul_rn(__fsub_rn(0.0f, gg[a]), iv[a]);
+                                const float t1 = __fmul_rn(__fsub_rn(fres, gg[a]), iv[a]);
+                                const float lo_t = (t1 < t0) ? t1 : t0;
+                                const float hi_t = (t0 < t1) ? t1 : t0;
+                                if (lo_t > tnr) {
+                                    tnr = lo_t;
+                                    enter = a;
+                                }
+                                tfr = (hi_t < tfr) ? hi_t : tfr;
+                            }
+                            if (!(tnr <= tfr)) alive = false;
+                            if (alive) {
+                                t = tnr;
+                                const float ds[3] = {dsx, dsy, dsz};
+                                int cc[3];
+#pragma unroll
+                                for (int a = 0; a < 3; ++a) {
+                                    if (a == enter) {
+                                        cc[a] = iv[a] > 0.0f ? 0 : res - 1;
+                                    } else {
+                                        const float p = __fadd_rn(gg[a], __fmul_rn(tnr, ds[a]));
+                                        const int c = (p >= 0.0f) ? (int)p : 0;
+                                        cc[a] = min(c, res - 1);
+                                    }
+                                }
+                                cx = cc[0];
+                                cy = cc[1];
+                                cz = cc[2];
+                            }
+                        }
+                        if (!alive) {
+                            field[cid] = __fadd_rn(G.eps, 0.0f);
+                            cid = -1;
+                        } else {
+                            node = 0;
+                            level = 0;
+                            steps = 0;
+                            stk[0] = 0;
+                        }
+                    }
+                }
             }
-            const float u = __fsub_rn(__fmul_rn(__fadd_rn((float)i, x0), tn), 1.0f);
-            const float v = __fsub_rn(__fmul_rn(__fadd_rn((float)j, x1), tn), 1.0f);
-            const float3 d = octa_to_dir(u, v);
-            const float L = (r == kNone) ? 0.0f : trace_cell(T, s_nodes, o, d, status);
-            field[c] = __fadd_rn(G.eps, L);
+            const bool active = cid >= 0 && cid < NN;
+            if (!__any_sync(0xffffffffu, active)) break;
+            if (!active) continue;
+            // ---- one step: deepest existing node holding the cell, then hit or skip its empty block
+            while (level < D) {
+                const Node nd = load_node(T, s_nodes, node);
+                const int sh = D - 1 - level;
+                const int k = ((cx >> sh) & 1) | (((cy >> sh) & 1) << 1) | (((cz >> sh) & 1) << 2);
+                if (!((nd.mask >> k) & 1u)) break;
+                node = child_id(nd, k);
+                ++level;
+                stk[level * kGuideThreads] = node;
+            }
+            float L = 0.0f;
+            bool done = false;
+            if (level == D && t >= T.t_skip) {
+                // Eq. 6: footprint A = t^2 omega; the level whose squared side is closest
+                const float A = __fmul_rn(__fmul_rn(t, t), T.omega);
+                float side = T.S, bd = INF;
+                int best = 0;
+                for (int l = 0; l <= D; ++l) {
+                    const float diff = fabsf(__fsub_rn(__fmul_rn(side, side), A));
+                    if (diff <= bd) {
+                        bd = diff;
+                        best = l;
+                    }
+                    side = __fmul_rn(side, 0.5f);
+                }
+                const uint32_t an = stk[best * kGuideThreads];
+                const float4 Nn = T.normal[an];
+                const float2 V = T.value[an];
+                const float dd = __fadd_rn(__fadd_rn(__fmul_rn(Nn.x, dx), __fmul_rn(Nn.y, dy)), __fmul_rn(Nn.z, dz));
+                L = (dd <= 0.0f) ? V.x : V.y;  // the side facing back along the ray
+                if (T.cos_weight) L = __fmul_rn(L, fabsf(dd));
+                done = true;
+            } else {
+                // leave the empty block (or the leaf before t_skip) through its first exit crossing
+                const int sl = (level == D) ? 0 : D - level - 1;
+                const int size = 1 << sl;
+                const int bx = (cx >> sl) << sl, by = (cy >> sl) << sl, bz = (cz >> sl) << sl;
+                const float tex = ivx != 0.0f ? cross_time(ivx > 0.0f ? bx + size : bx - 1, ivx > 0.0f, gx, ivx) : INF;
+                const float tey = ivy != 0.0f ? cross_time(ivy > 0.0f ? by + size : by - 1, ivy > 0.0f, gy, ivy) : INF;
+                const float tez = ivz != 0.0f ? cross_time(ivz > 0.0f ? bz + size : bz - 1, ivz > 0.0f, gz, ivz) : INF;
+                const int a = (tex <= tey && tex <= tez) ? 0 : (tey <= tez ? 1 : 2);
+                const float tx = a == 0 ? tex : (a == 1 ? tey : tez);
+                const float dsx = __fmul_rn(dx, T.scale), dsy = __fmul_rn(dy, T.scale), dsz = __fmul_rn(dz, T.scale);
+                int nx, ny, nz;
+                if (a == 0) {
+                    nx = ivx > 0.0f ? bx + size : bx - 1;
+                    ny = advance_axis(cy, by, size, gy, ivy, dsy, tx, false);
+                    nz = advance_axis(cz, bz, size, gz, ivz, dsz, tx, false);
+                } else if (a == 1) {
+                    ny = ivy > 0.0f ? by + size : by - 1;
+                    nx = advance_axis(cx, bx, size, gx, ivx, dsx, tx, true);
+                    nz = advance_axis(cz, bz, size, gz, ivz, dsz, tx, false);
+                } else {
+                    nz = ivz > 0.0f ? bz + size : bz - 1;
+                    nx = advance_axis(cx, bx, size, gx, ivx, dsx, tx, true);
+                    ny = advance_axis(cy, by, size, gy, ivy, dsy, tx, true);
+                }
+                const int na = a == 0 ? nx : (a == 1 ? ny : nz);
+                if (tx == INF || na < 0 || na >= res) {
+                    done = true;  // left the grid: miss
+                } else if (++steps > cap) {
+                    atomicOr(status, (uint32_t)WFPG_STATUS_TRACE_CAP);
+                    done = true;
+                } else {
+                    // restart the descent from the deepest ancestor shared with the new cell
+                    const uint32_t diff = (uint32_t)((cx ^ nx) | (cy ^ ny) | (cz ^ nz));
+                    level = D - 1 - (31 - __clz(diff));
+                    node = stk[level * kGuideThreads];
+                    cx = nx;
+                    cy = ny;
+                    cz = nz;
+                    t = tx;
+                }
+            }
+            if (done) {
+                field[cid] = __fadd_rn(G.eps, L);
+                cid = -1;
+            }
         }
         __syncthreads();
         if (G.blur) {
@@ -401,8 +465,9 @@ __global__ void __launch_bounds__(256) k_guide_eval(const float* __restrict__ pd
 }
 
 // ---------------------------------------------------------------------------
-static size_t guide_smem_bytes(uint32_t smem_nodes, int N) {
-    return sizeof(Node) * smem_nodes + sizeof(float) * (2 * (size_t)N * N + 2 * (size_t)N);
+static size_t guide_smem_bytes(uint32_t smem_nodes, int N, int D) {
+    return sizeof(Node) * smem_nodes + sizeof(uint32_t) * (size_t)(D + 1) * kGuideThreads +
+           sizeof(float) * (2 * (size_t)N * N + 2 * (size_t)N);
 }
 
 int guide_build_impl(const wfpg_svo* s, const float* pos, const uint32_t* origin_ray, const uint32_t* n_bins_dev,
@@ -429,7 +494,7 @@ int guide_build_impl(const wfpg_svo* s, const float* pos, const uint32_t* origin
     G.blur = p->blur;
     G.seed = p->seed;
     G.frame = p->frame;
-    const size_t smem = guide_smem_bytes(T.smem_nodes, p->N);
+    const size_t smem = guide_smem_bytes(T.smem_nodes, p->N, s->D);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k_guide_build, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return WFPG_ERR_CUDA;
