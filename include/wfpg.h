@@ -215,6 +215,8 @@ typedef struct wfpg_guide_params {
     int cos_weight;    /* 1: multiply the node value by |dot(N, d)| */
     uint64_t seed;     /* jitter random stream */
     uint32_t frame;    /* jitter random stream */
+    int block;         /* tuning: threads that work on one bin (64, 128, 256; 0 = default) */
+    int stage;         /* tuning: 1 stage cone directions in shared memory, -1 do not, 0 = default */
 } wfpg_guide_params;
 
 /*

@@ -171,11 +171,16 @@ int guide_build_pdf(const wfpg_svo* s, const float* pos, const uint32_t* origin_
     if (!s || !p) return fail(WFPG_ERR_INVALID_ARG, "guide_build_pdf: null svo or params");
     if (!valid_n(p->N)) return fail(WFPG_ERR_INVALID_ARG, "guide_build_pdf: N must be 8, 16, 32, 64 or 128");
     if (!(p->eps >= 0.0f)) return fail(WFPG_ERR_INVALID_ARG, "guide_build_pdf: eps must be >= 0");
+    if (p->block != 0 && p->block != 64 && p->block != 128 && p->block != 256)
+        return fail(WFPG_ERR_INVALID_ARG, "guide_build_pdf: block must be 0, 64, 128 or 256");
     if (bin_cap && (!pos || !pdf || !cdf_row || !cdf_marg))
         return fail(WFPG_ERR_INVALID_ARG, "guide_build_pdf: null array");
-    if (guide_build_impl(s, pos, origin_ray, n_bins_dev, bin_cap, p, pdf, cdf_row, cdf_marg, as_stream(stream)) !=
-        WFPG_OK)
-        return cuda_fail("guide_build_pdf");
+    const int rc = guide_build_impl(s, pos, origin_ray, n_bins_dev, bin_cap, p, pdf, cdf_row, cdf_marg,
+                                    as_stream(stream));
+    if (rc == WFPG_ERR_INVALID_ARG)
+        return fail(rc, "guide_build_pdf: the field of side " + std::to_string(p->N) +
+                            " does not fit in shared memory with this block size");
+    if (rc != WFPG_OK) return cuda_fail("guide_build_pdf");
     return WFPG_OK;
 }
 

@@ -14,13 +14,18 @@
 // block's exit crossing (the smallest face time, ties x < y < z) and sets the
 // other coordinates to the cells a leaf-by-leaf walk would have reached by
 // that crossing (crossings earlier in (time, axis) order).
+#include <algorithm>
+
 #include "common.cuh"
 #include "svo.cuh"
 
 namespace wfpg {
 
 constexpr float kOneMinus = 0x1.fffffep-1f;
-constexpr int kGuideThreads = 256;
+constexpr int kGuideChunk = 512;   // cells whose directions are staged in shared memory at once
+// defaults measured on the 1080p frame workload (GB300): 256 threads per bin
+// without staging for N >= 32, 64 threads (with staging) for N <= 16
+constexpr int kGuideDefaultThreadsLarge = 256, kGuideDefaultThreadsSmall = 64;
 constexpr int kSmemTopLevels = 3;  // levels 0..3 of the SVO (<= 585 nodes) live in shared memory
 
 struct TraceArgs {
@@ -59,6 +64,21 @@ __device__ __forceinline__ Node load_node(const TraceArgs& T, const Node* s_node
 // j + 1 when moving down; evaluated afresh from the integer boundary
 __device__ __forceinline__ float cross_time(int j, bool up, float g, float inv) {
     return __fmul_rn(__fsub_rn((float)(up ? j : j + 1), g), inv);
+}
+
+// Index along one axis after every crossing strictly before time ts: the
+// leaf-by-leaf walk's coordinate once it has passed all crossings < ts.
+// May step one cell outside [0, res) (the ray left the grid before ts).
+__device__ __forceinline__ int skip_before(int c, float g, float inv, float ts, int res) {
+    if (inv == 0.0f) return c;
+    const bool up = inv > 0.0f;
+    for (int k = 0; k <= res; ++k) {
+        const int nxt = up ? c + 1 : c - 1;
+        if (!(cross_time(nxt, up, g, inv) < ts)) break;
+        c = nxt;
+        if (c < 0 || c >= res) break;
+    }
+    return c;
 }
 
 // Index along one axis that the leaf-by-leaf walk reaches at the crossing
@@ -128,6 +148,10 @@ __device__ __forceinline__ float warp_scan_row(const float* src, float* dst, int
     return mx;
 }
 
+// kGuideThreads threads work on one bin at a time; kStage: the chunk's cone
+// directions are computed by all threads together into shared memory before
+// the march (otherwise each lane computes its ray's direction when it takes it)
+template <int kGuideThreads, bool kStage>
 __global__ void __launch_bounds__(kGuideThreads) k_guide_build(TraceArgs T, GuideArgs G, const float* __restrict__ pos,
                                                                const uint32_t* __restrict__ origin_ray,
                                                                const uint32_t* __restrict__ n_bins_dev,
@@ -137,9 +161,11 @@ __global__ void __launch_bounds__(kGuideThreads) k_guide_build(TraceArgs T, Guid
     extern __shared__ __align__(16) unsigned char smem[];
     const int N = G.N, NN = N * N;
     const int D = T.D;
+    const int chunk = kStage ? (NN < kGuideChunk ? NN : kGuideChunk) : NN;
     Node* s_nodes = reinterpret_cast<Node*>(smem);
     uint32_t* s_stack = reinterpret_cast<uint32_t*>(smem + sizeof(Node) * T.smem_nodes);
-    float* field = reinterpret_cast<float*>(s_stack + (D + 1) * kGuideThreads);
+    float* s_ray = reinterpret_cast<float*>(s_stack + (D + 1) * kGuideThreads);  // 6 x chunk: d, 1/(d 2^D/S)
+    float* field = s_ray + (kStage ? 6 * chunk : 0);
     float* tmp = field + NN;
     float* rowtot = tmp + NN;
     float* marg = rowtot + N;
@@ -171,188 +197,217 @@ __global__ void __launch_bounds__(kGuideThreads) k_guide_build(TraceArgs T, Guid
         const float gx = __fmul_rn(__fsub_rn(ox, T.lo[0]), T.scale);
         const float gy = __fmul_rn(__fsub_rn(oy, T.lo[1]), T.scale);
         const float gz = __fmul_rn(__fsub_rn(oz, T.lo[2]), T.scale);
+        const bool inside = gx >= 0.0f && gx <= fres && gy >= 0.0f && gy <= fres && gz >= 0.0f && gz <= fres;
         const uint64_t jseed = purpose(G.seed, kJitterPurpose);
         const uint64_t jstream = bin_stream(G.frame, b);
-        if (tid == 0) s_next = 0;
-        __syncthreads();
-        // ---- cone rays: each lane marches one cell's ray; finished lanes take the next cell
-        int cid = -1;  // current cell (-1: none, >= NN: no work left)
-        float dx = 0.f, dy = 0.f, dz = 0.f, ivx = 0.f, ivy = 0.f, ivz = 0.f, t = 0.f;
-        int cx = 0, cy = 0, cz = 0, level = 0, steps = 0;
-        uint32_t node = 0;
-        for (;;) {
-            const bool idle = cid < 0;
-            const uint32_t need = __ballot_sync(0xffffffffu, idle);
-            if (need) {
-                const int leader = __ffs(need) - 1;
-                int base = 0;
-                if (lane == leader) base = atomicAdd(&s_next, __popc(need));
-                base = __shfl_sync(0xffffffffu, base, leader);
-                if (idle) {
-                    cid = base + __popc(need & lt);
-                    if (cid < NN) {
-                        // start the cone ray of cell (i, j)
-                        const int i = cid % N, j = cid / N;
-                        float x0 = 0.5f, x1 = 0.5f;
-                        if (G.jitter) {
-                            x0 = uniform01(jseed, jstream, 2ull * cid);
-                            x1 = uniform01(jseed, jstream, 2ull * cid + 1);
-                        }
-                        const float u = __fsub_rn(__fmul_rn(__fadd_rn((float)i, x0), tn), 1.0f);
-                        const float v = __fsub_rn(__fmul_rn(__fadd_rn((float)j, x1), tn), 1.0f);
-                        const float3 d = octa_to_dir(u, v);
-                        dx = d.x;
-                        dy = d.y;
-                        dz = d.z;
-                        const float dsx = __fmul_rn(dx, T.scale), dsy = __fmul_rn(dy, T.scale),
-                                    dsz = __fmul_rn(dz, T.scale);
-                        ivx = dx != 0.0f ? __fdiv_rn(1.0f, dsx) : 0.0f;
-                        ivy = dy != 0.0f ? __fdiv_rn(1.0f, dsy) : 0.0f;
-                        ivz = dz != 0.0f ? __fdiv_rn(1.0f, dsz) : 0.0f;
-                        bool alive = r != kNone;
-                        const bool inside = gx >= 0.0f && gx <= fres && gy >= 0.0f && gy <= fres && gz >= 0.0f &&
-                                            gz <= fres;
-                        t = 0.0f;
-                        if (alive && inside) {
-                            cx = min((int)gx, res - 1);
-                            cy = min((int)gy, res - 1);
-                            cz = min((int)gz, res - 1);
-                        } else if (alive) {
-                            // slab entry into the grid box
-                            float tnr = 0.0f, tfr = INF;
-                            int enter = -1;
-                            const float gg[3] = {gx, gy, gz}, iv[3] = {ivx, ivy, ivz};
-#pragma unroll
-                            for (int a = 0; a < 3; ++a) {
-                                if (iv[a] == 0.0f) {
-                                    if (!(gg[a] >= 0.0f && gg[a] <= fres)) alive = false;
-                                    continue;
+        for (int c0 = 0; c0 < NN; c0 += chunk) {
+            // ---- directions of this chunk's cells, computed by all threads together
+            for (int q = tid; kStage && q < chunk; q += kGuideThreads) {
+                const int c = c0 + q;
+                const int i = c % N, j = c / N;
+                float x0 = 0.5f, x1 = 0.5f;
+                if (G.jitter) {
+                    x0 = uniform01(jseed, jstream, 2ull * c);
+                    x1 = uniform01(jseed, jstream, 2ull * c + 1);
+                }
+                const float u = __fsub_rn(__fmul_rn(__fadd_rn((float)i, x0), tn), 1.0f);
+                const float v = __fsub_rn(__fmul_rn(__fadd_rn((float)j, x1), tn), 1.0f);
+                const float3 d = octa_to_dir(u, v);
+                s_ray[0 * chunk + q] = d.x;
+                s_ray[1 * chunk + q] = d.y;
+                s_ray[2 * chunk + q] = d.z;
+                s_ray[3 * chunk + q] = d.x != 0.0f ? __fdiv_rn(1.0f, __fmul_rn(d.x, T.scale)) : 0.0f;
+                s_ray[4 * chunk + q] = d.y != 0.0f ? __fdiv_rn(1.0f, __fmul_rn(d.y, T.scale)) : 0.0f;
+                s_ray[5 * chunk + q] = d.z != 0.0f ? __fdiv_rn(1.0f, __fmul_rn(d.z, T.scale)) : 0.0f;
+            }
+            if (tid == 0) s_next = 0;
+            __syncthreads();
+            // ---- cone rays: each lane marches one cell's ray; finished lanes take the next cell
+            int q = -1;  // current cell of the chunk (-1: none, >= chunk: no work left)
+            float dx = 0.f, dy = 0.f, dz = 0.f, ivx = 0.f, ivy = 0.f, ivz = 0.f, t = 0.f;
+            int cx = 0, cy = 0, cz = 0, level = 0, steps = 0;
+            uint32_t node = 0;
+            for (;;) {
+                const bool idle = q < 0;
+                const uint32_t need = __ballot_sync(0xffffffffu, idle);
+                if (need) {
+                    const int leader = __ffs(need) - 1;
+                    int base = 0;
+                    if (lane == leader) base = atomicAdd(&s_next, __popc(need));
+                    base = __shfl_sync(0xffffffffu, base, leader);
+                    if (idle) {
+                        q = base + __popc(need & lt);
+                        if (q < chunk) {
+                            if (kStage) {
+                                dx = s_ray[0 * chunk + q];
+                                dy = s_ray[1 * chunk + q];
+                                dz = s_ray[2 * chunk + q];
+                                ivx = s_ray[3 * chunk + q];
+                                ivy = s_ray[4 * chunk + q];
+                                ivz = s_ray[5 * chunk + q];
+                            } else {
+                                const int c = c0 + q;
+                                const int i = c % N, j = c / N;
+                                float x0 = 0.5f, x1 = 0.5f;
+                                if (G.jitter) {
+                                    x0 = uniform01(jseed, jstream, 2ull * c);
+                                    x1 = uniform01(jseed, jstream, 2ull * c + 1);
                                 }
-                                const float t0 = __fmul_rn(__fsub_rn(0.0f, gg[a]), iv[a]);
-                                const float t1 = __fmul_rn(__fsub_rn(fres, gg[a]), iv[a]);
-                                const float lo_t = (t1 < t0) ? t1 : t0;
-                                const float hi_t = (t0 < t1) ? t1 : t0;
-                                if (lo_t > tnr) {
-                                    tnr = lo_t;
-                                    enter = a;
-                                }
-                                tfr = (hi_t < tfr) ? hi_t : tfr;
+                                const float u = __fsub_rn(__fmul_rn(__fadd_rn((float)i, x0), tn), 1.0f);
+                                const float v = __fsub_rn(__fmul_rn(__fadd_rn((float)j, x1), tn), 1.0f);
+                                const float3 d = octa_to_dir(u, v);
+                                dx = d.x;
+                                dy = d.y;
+                                dz = d.z;
+                                ivx = dx != 0.0f ? __fdiv_rn(1.0f, __fmul_rn(dx, T.scale)) : 0.0f;
+                                ivy = dy != 0.0f ? __fdiv_rn(1.0f, __fmul_rn(dy, T.scale)) : 0.0f;
+                                ivz = dz != 0.0f ? __fdiv_rn(1.0f, __fmul_rn(dz, T.scale)) : 0.0f;
                             }
-                            if (!(tnr <= tfr)) alive = false;
-                            if (alive) {
-                                t = tnr;
-                                const float ds[3] = {dsx, dsy, dsz};
-                                int cc[3];
+                            bool alive = r != kNone;
+                            t = 0.0f;
+                            if (alive && inside) {
+                                cx = min((int)gx, res - 1);
+                                cy = min((int)gy, res - 1);
+                                cz = min((int)gz, res - 1);
+                            } else if (alive) {
+                                // slab entry into the grid box
+                                float tnr = 0.0f, tfr = INF;
+                                int enter = -1;
+                                const float gg[3] = {gx, gy, gz}, iv[3] = {ivx, ivy, ivz};
 #pragma unroll
                                 for (int a = 0; a < 3; ++a) {
-                                    if (a == enter) {
-                                        cc[a] = iv[a] > 0.0f ? 0 : res - 1;
-                                    } else {
-                                        const float p = __fadd_rn(gg[a], __fmul_rn(tnr, ds[a]));
-                                        const int c = (p >= 0.0f) ? (int)p : 0;
-                                        cc[a] = min(c, res - 1);
+                                    if (iv[a] == 0.0f) {
+                                        if (!(gg[a] >= 0.0f && gg[a] <= fres)) alive = false;
+                                        continue;
                                     }
+                                    const float t0 = __fmul_rn(__fsub_rn(0.0f, gg[a]), iv[a]);
+                                    const float t1 = __fmul_rn(__fsub_rn(fres, gg[a]), iv[a]);
+                                    const float lo_t = (t1 < t0) ? t1 : t0;
+                                    const float hi_t = (t0 < t1) ? t1 : t0;
+                                    if (lo_t > tnr) {
+                                        tnr = lo_t;
+                                        enter = a;
+                                    }
+                                    tfr = (hi_t < tfr) ? hi_t : tfr;
                                 }
-                                cx = cc[0];
-                                cy = cc[1];
-                                cz = cc[2];
+                                if (!(tnr <= tfr)) alive = false;
+                                if (alive) {
+                                    t = tnr;
+                                    const float dd[3] = {dx, dy, dz};
+                                    int cc[3];
+#pragma unroll
+                                    for (int a = 0; a < 3; ++a) {
+                                        if (a == enter) {
+                                            cc[a] = iv[a] > 0.0f ? 0 : res - 1;
+                                        } else {
+                                            const float p = __fadd_rn(gg[a], __fmul_rn(tnr, __fmul_rn(dd[a], T.scale)));
+                                            const int c = (p >= 0.0f) ? (int)p : 0;
+                                            cc[a] = min(c, res - 1);
+                                        }
+                                    }
+                                    cx = cc[0];
+                                    cy = cc[1];
+                                    cz = cc[2];
+                                }
+                            }
+                            if (alive && t < T.t_skip) {
+                                // no cell entered before t_skip can be the hit: take every
+                                // crossing strictly before t_skip at once (axis by axis)
+                                cx = skip_before(cx, gx, ivx, T.t_skip, res);
+                                cy = skip_before(cy, gy, ivy, T.t_skip, res);
+                                cz = skip_before(cz, gz, ivz, T.t_skip, res);
+                                if (cx < 0 || cx >= res || cy < 0 || cy >= res || cz < 0 || cz >= res) alive = false;
+                            }
+                            if (!alive) {
+                                field[c0 + q] = __fadd_rn(G.eps, 0.0f);
+                                q = -1;
+                            } else {
+                                node = 0;
+                                level = 0;
+                                steps = 0;
+                                stk[0] = 0;
                             }
                         }
-                        if (!alive) {
-                            field[cid] = __fadd_rn(G.eps, 0.0f);
-                            cid = -1;
-                        } else {
-                            node = 0;
-                            level = 0;
-                            steps = 0;
-                            stk[0] = 0;
+                    }
+                }
+                // leave only when every lane has run out of cells (a lane whose new ray
+                // died at its start is idle again and fetches once more)
+                if (__all_sync(0xffffffffu, q >= chunk)) break;
+                if (q < 0 || q >= chunk) continue;  // idle, or out of cells: no ray to step
+                // ---- one step: deepest existing node holding the cell, then hit or skip its empty block
+                while (level < D) {
+                    const Node nd = load_node(T, s_nodes, node);
+                    const int sh = D - 1 - level;
+                    const int k = ((cx >> sh) & 1) | (((cy >> sh) & 1) << 1) | (((cz >> sh) & 1) << 2);
+                    if (!((nd.mask >> k) & 1u)) break;
+                    node = child_id(nd, k);
+                    ++level;
+                    stk[level * kGuideThreads] = node;
+                }
+                float L = 0.0f;
+                bool done = false;
+                if (level == D && t >= T.t_skip) {
+                    // Eq. 6: footprint A = t^2 omega; the level whose squared side is closest
+                    const float A = __fmul_rn(__fmul_rn(t, t), T.omega);
+                    float side = T.S, bd = INF;
+                    int best = 0;
+                    for (int l = 0; l <= D; ++l) {
+                        const float diff = fabsf(__fsub_rn(__fmul_rn(side, side), A));
+                        if (diff <= bd) {
+                            bd = diff;
+                            best = l;
                         }
+                        side = __fmul_rn(side, 0.5f);
                     }
-                }
-            }
-            const bool active = cid >= 0 && cid < NN;
-            if (!__any_sync(0xffffffffu, active)) break;
-            if (!active) continue;
-            // ---- one step: deepest existing node holding the cell, then hit or skip its empty block
-            while (level < D) {
-                const Node nd = load_node(T, s_nodes, node);
-                const int sh = D - 1 - level;
-                const int k = ((cx >> sh) & 1) | (((cy >> sh) & 1) << 1) | (((cz >> sh) & 1) << 2);
-                if (!((nd.mask >> k) & 1u)) break;
-                node = child_id(nd, k);
-                ++level;
-                stk[level * kGuideThreads] = node;
-            }
-            float L = 0.0f;
-            bool done = false;
-            if (level == D && t >= T.t_skip) {
-                // Eq. 6: footprint A = t^2 omega; the level whose squared side is closest
-                const float A = __fmul_rn(__fmul_rn(t, t), T.omega);
-                float side = T.S, bd = INF;
-                int best = 0;
-                for (int l = 0; l <= D; ++l) {
-                    const float diff = fabsf(__fsub_rn(__fmul_rn(side, side), A));
-                    if (diff <= bd) {
-                        bd = diff;
-                        best = l;
-                    }
-                    side = __fmul_rn(side, 0.5f);
-                }
-                const uint32_t an = stk[best * kGuideThreads];
-                const float4 Nn = T.normal[an];
-                const float2 V = T.value[an];
-                const float dd = __fadd_rn(__fadd_rn(__fmul_rn(Nn.x, dx), __fmul_rn(Nn.y, dy)), __fmul_rn(Nn.z, dz));
-                L = (dd <= 0.0f) ? V.x : V.y;  // the side facing back along the ray
-                if (T.cos_weight) L = __fmul_rn(L, fabsf(dd));
-                done = true;
-            } else {
-                // leave the empty block (or the leaf before t_skip) through its first exit crossing
-                const int sl = (level == D) ? 0 : D - level - 1;
-                const int size = 1 << sl;
-                const int bx = (cx >> sl) << sl, by = (cy >> sl) << sl, bz = (cz >> sl) << sl;
-                const float tex = ivx != 0.0f ? cross_time(ivx > 0.0f ? bx + size : bx - 1, ivx > 0.0f, gx, ivx) : INF;
-                const float tey = ivy != 0.0f ? cross_time(ivy > 0.0f ? by + size : by - 1, ivy > 0.0f, gy, ivy) : INF;
-                const float tez = ivz != 0.0f ? cross_time(ivz > 0.0f ? bz + size : bz - 1, ivz > 0.0f, gz, ivz) : INF;
-                const int a = (tex <= tey && tex <= tez) ? 0 : (tey <= tez ? 1 : 2);
-                const float tx = a == 0 ? tex : (a == 1 ? tey : tez);
-                const float dsx = __fmul_rn(dx, T.scale), dsy = __fmul_rn(dy, T.scale), dsz = __fmul_rn(dz, T.scale);
-                int nx, ny, nz;
-                if (a == 0) {
-                    nx = ivx > 0.0f ? bx + size : bx - 1;
-                    ny = advance_axis(cy, by, size, gy, ivy, dsy, tx, false);
-                    nz = advance_axis(cz, bz, size, gz, ivz, dsz, tx, false);
-                } else if (a == 1) {
-                    ny = ivy > 0.0f ? by + size : by - 1;
-                    nx = advance_axis(cx, bx, size, gx, ivx, dsx, tx, true);
-                    nz = advance_axis(cz, bz, size, gz, ivz, dsz, tx, false);
-                } else {
-                    nz = ivz > 0.0f ? bz + size : bz - 1;
-                    nx = advance_axis(cx, bx, size, gx, ivx, dsx, tx, true);
-                    ny = advance_axis(cy, by, size, gy, ivy, dsy, tx, true);
-                }
-                const int na = a == 0 ? nx : (a == 1 ? ny : nz);
-                if (tx == INF || na < 0 || na >= res) {
-                    done = true;  // left the grid: miss
-                } else if (++steps > cap) {
-                    atomicOr(status, (uint32_t)WFPG_STATUS_TRACE_CAP);
+                    const uint32_t an = stk[best * kGuideThreads];
+                    const float4 Nn = T.normal[an];
+                    const float2 V = T.value[an];
+                    const float dd = __fadd_rn(__fadd_rn(__fmul_rn(Nn.x, dx), __fmul_rn(Nn.y, dy)), __fmul_rn(Nn.z, dz));
+                    L = (dd <= 0.0f) ? V.x : V.y;  // the side facing back along the ray
+                    if (T.cos_weight) L = __fmul_rn(L, fabsf(dd));
                     done = true;
                 } else {
-                    // restart the descent from the deepest ancestor shared with the new cell
-                    const uint32_t diff = (uint32_t)((cx ^ nx) | (cy ^ ny) | (cz ^ nz));
-                    level = D - 1 - (31 - __clz(diff));
-                    node = stk[level * kGuideThreads];
-                    cx = nx;
-                    cy = ny;
-                    cz = nz;
-                    t = tx;
+                    // leave the empty block (or a leaf entered before t_skip) through its first exit crossing
+                    const int sl = (level == D) ? 0 : D - level - 1;
+                    const int size = 1 << sl;
+                    const int bx = (cx >> sl) << sl, by = (cy >> sl) << sl, bz = (cz >> sl) << sl;
+                    const int ex = ivx > 0.0f ? bx + size : bx - 1;
+                    const int ey = ivy > 0.0f ? by + size : by - 1;
+                    const int ez = ivz > 0.0f ? bz + size : bz - 1;
+                    const float tex = ivx != 0.0f ? cross_time(ex, ivx > 0.0f, gx, ivx) : INF;
+                    const float tey = ivy != 0.0f ? cross_time(ey, ivy > 0.0f, gy, ivy) : INF;
+                    const float tez = ivz != 0.0f ? cross_time(ez, ivz > 0.0f, gz, ivz) : INF;
+                    const int a = (tex <= tey && tex <= tez) ? 0 : (tey <= tez ? 1 : 2);
+                    const float tx = a == 0 ? tex : (a == 1 ? tey : tez);
+                    const int nx = a == 0 ? ex : advance_axis(cx, bx, size, gx, ivx, __fmul_rn(dx, T.scale), tx, true);
+                    const int ny = a == 1 ? ey : advance_axis(cy, by, size, gy, ivy, __fmul_rn(dy, T.scale), tx, a > 1);
+                    const int nz = a == 2 ? ez : advance_axis(cz, bz, size, gz, ivz, __fmul_rn(dz, T.scale), tx, false);
+                    // (axis order for ties: x precedes an exit along y or z, y precedes
+                    // an exit along z, z precedes nothing)
+                    const int na = a == 0 ? nx : (a == 1 ? ny : nz);
+                    if (tx == INF || na < 0 || na >= res) {
+                        done = true;  // left the grid: miss
+                    } else if (++steps > cap) {
+                        atomicOr(status, (uint32_t)WFPG_STATUS_TRACE_CAP);
+                        done = true;
+                    } else {
+                        // restart the descent from the deepest ancestor shared with the new cell
+                        const uint32_t diff = (uint32_t)((cx ^ nx) | (cy ^ ny) | (cz ^ nz));
+                        level = D - 1 - (31 - __clz(diff));
+                        node = stk[level * kGuideThreads];
+                        cx = nx;
+                        cy = ny;
+                        cz = nz;
+                        t = tx;
+                    }
+                }
+                if (done) {
+                    field[c0 + q] = __fadd_rn(G.eps, L);
+                    q = -1;
                 }
             }
-            if (done) {
-                field[cid] = __fadd_rn(G.eps, L);
-                cid = -1;
-            }
+            __syncthreads();
         }
-        __syncthreads();
         if (G.blur) {
             for (int c = tid; c < NN; c += kGuideThreads) {
                 const int i = c % N, j = c / N;
@@ -465,9 +520,31 @@ __global__ void __launch_bounds__(256) k_guide_eval(const float* __restrict__ pd
 }
 
 // ---------------------------------------------------------------------------
-static size_t guide_smem_bytes(uint32_t smem_nodes, int N, int D) {
-    return sizeof(Node) * smem_nodes + sizeof(uint32_t) * (size_t)(D + 1) * kGuideThreads +
-           sizeof(float) * (2 * (size_t)N * N + 2 * (size_t)N);
+static size_t guide_smem_bytes(uint32_t smem_nodes, int N, int D, int threads, bool stage) {
+    const size_t NN = (size_t)N * N;
+    const size_t chunk = NN < (size_t)kGuideChunk ? NN : (size_t)kGuideChunk;
+    return sizeof(Node) * smem_nodes + sizeof(uint32_t) * (size_t)(D + 1) * threads +
+           sizeof(float) * ((stage ? 6 * chunk : 0) + 2 * NN + 2 * (size_t)N);
+}
+
+template <int kThreads, bool kStage>
+static int launch_guide(const TraceArgs& T, const GuideArgs& G, const float* pos, const uint32_t* origin_ray,
+                        const uint32_t* n_bins_dev, uint32_t bin_cap, float* pdf, float* cdf_row, float* cdf_marg,
+                        uint32_t* status, int D, cudaStream_t st) {
+    auto kernel = k_guide_build<kThreads, kStage>;
+    const size_t smem = guide_smem_bytes(T.smem_nodes, G.N, D, kThreads, kStage);
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return WFPG_ERR_CUDA;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, smem);
+    if (per_sm < 1) return WFPG_ERR_INVALID_ARG;  // the field does not fit in shared memory
+    const uint32_t grid = (uint32_t)std::min<uint64_t>(bin_cap, (uint64_t)sms * per_sm);
+    WFPG_LAUNCH(kernel, grid, kThreads, smem, st, T, G, pos, origin_ray, n_bins_dev, bin_cap, pdf, cdf_row, cdf_marg,
+                status);
+    return cudaGetLastError() == cudaSuccess ? WFPG_OK : WFPG_ERR_CUDA;
 }
 
 int guide_build_impl(const wfpg_svo* s, const float* pos, const uint32_t* origin_ray, const uint32_t* n_bins_dev,
@@ -494,20 +571,21 @@ int guide_build_impl(const wfpg_svo* s, const float* pos, const uint32_t* origin
     G.blur = p->blur;
     G.seed = p->seed;
     G.frame = p->frame;
-    const size_t smem = guide_smem_bytes(T.smem_nodes, p->N, s->D);
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_guide_build, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return WFPG_ERR_CUDA;
-    }
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_guide_build, kGuideThreads, smem);
-    if (per_sm < 1) per_sm = 1;
-    const uint32_t grid = min((uint64_t)bin_cap, (uint64_t)sms * per_sm);
-    WFPG_LAUNCH(k_guide_build, grid, kGuideThreads, smem, st, T, G, pos, origin_ray, n_bins_dev, bin_cap, pdf, cdf_row,
-                                                     cdf_marg, s->status);
-    return cudaGetLastError() == cudaSuccess ? WFPG_OK : WFPG_ERR_CUDA;
+    const bool small = p->N <= 16;
+    const int threads = p->block ? p->block : (small ? kGuideDefaultThreadsSmall : kGuideDefaultThreadsLarge);
+    const bool stage = p->stage == 0 ? small : p->stage > 0;
+    const int D = s->D;
+#define WFPG_GUIDE_CASE(TH)                                                                                       \
+    if (threads == TH)                                                                                            \
+        return stage ? launch_guide<TH, true>(T, G, pos, origin_ray, n_bins_dev, bin_cap, pdf, cdf_row, cdf_marg, \
+                                              s->status, D, st)                                                   \
+                     : launch_guide<TH, false>(T, G, pos, origin_ray, n_bins_dev, bin_cap, pdf, cdf_row,          \
+                                               cdf_marg, s->status, D, st);
+    WFPG_GUIDE_CASE(64)
+    WFPG_GUIDE_CASE(128)
+    WFPG_GUIDE_CASE(256)
+#undef WFPG_GUIDE_CASE
+    return WFPG_ERR_INVALID_ARG;
 }
 
 int guide_sample_impl(const float* pdf, const float* cdf_row, const float* cdf_marg, int N, uint32_t bin_cap,

@@ -287,3 +287,24 @@ def test_frame_scale_sampled_parity(frame_workload):
     np.testing.assert_allclose(p.cpu().numpy()[rays], op, rtol=RTOL, atol=0)
     np.testing.assert_allclose(d.cpu().numpy()[rays], od, rtol=0, atol=1e-6)
     assert g.status() == 0
+
+
+@pytest.mark.parametrize("block", [64, 128, 256])
+@pytest.mark.parametrize("stage", [1, -1])
+def test_guide_build_tile_variants(block, stage):
+    """Every block size / staging choice of the field kernel gives the oracle's field."""
+    w = inputs.tiny_box(6, n_rays=4099)
+    g, o = build_both(w.scene, w.depth)
+    W.svo_accumulate(g, dev(w.rec_pos), dev(w.rec_wout), dev(w.rec_L))
+    o.accumulate(w.rec_pos, w.rec_wout, w.rec_L)
+    pos = dev(w.ray_pos)
+    r = W.bin_rays(g, pos, l_min=2, seed=11, frame=2)
+    ro = o.bin_rays(w.ray_pos, w.ray_nrm, l_min=2, seed=11, frame=2)
+    nb = ro["n_bins"]
+    for N in (32, 64):
+        pdf, cr, cm = W.guide_build_pdf(g, pos, r["origin_ray"], r["n_bins"], r["bin_cap"], N=N, jitter=True,
+                                        blur=True, seed=11, frame=2, block=block, stage=stage)
+        og = o.guide_build(w.ray_pos[ro["origin_ray"]], np.arange(nb), N, jitter=True, blur=True, seed=11, frame=2)
+        assert np.array_equal(pdf[:nb].cpu().numpy(), og["pdf"])
+        assert np.array_equal(cm[:nb].cpu().numpy(), og["cdf_marg"])
+    assert g.status() == 0
