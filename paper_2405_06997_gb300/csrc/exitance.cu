@@ -9,7 +9,7 @@
 
 namespace wfpg {
 
-struct AccArgs {
+struct AccArgs {  // the tree and the grid mapping the scatter needs
     const Node* node;
     const float4* normal;
     int D;
@@ -51,7 +51,7 @@ __device__ __forceinline__ float2 node_values(unsigned long long s0, uint32_t c0
     return make_float2(v0, v1);
 }
 
-// leaves: value straight from their own sums
+// leaves: value straight from their own sums (used when the tree is a single leaf)
 __global__ void k_leaf_values(uint32_t off, uint32_t n, const ulonglong2* __restrict__ acc_sum,
                               const uint2* __restrict__ acc_cnt, float2* __restrict__ value) {
     const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -61,16 +61,17 @@ __global__ void k_leaf_values(uint32_t off, uint32_t n, const ulonglong2* __rest
     value[off + j] = node_values(s.x, c.x, s.y, c.y);
 }
 
-// one inner level: own records + children's totals routed by normal agreement
+// one inner level: own records + children's sums routed to the parent side
+// their normal agrees with; when the children are leaves their values are
+// written here too (a leaf's value comes from its own sums)
 __global__ void k_reduce_level(uint32_t off, uint32_t n, int children_are_leaves, const Node* __restrict__ node,
-                               const float4* __restrict__ normal, const ulonglong2* __restrict__ acc_sum,
+                               const uint8_t* __restrict__ route, const ulonglong2* __restrict__ acc_sum,
                                const uint2* __restrict__ acc_cnt, ulonglong2* __restrict__ tot_sum,
                                uint2* __restrict__ tot_cnt, float2* __restrict__ value) {
     const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
     const uint32_t id = off + j;
     const Node nd = node[id];
-    const float4 P = normal[id];
     const ulonglong2 own = acc_sum[id];
     const uint2 ownc = acc_cnt[id];
     unsigned long long s0 = own.x, s1 = own.y;
@@ -80,13 +81,12 @@ __global__ void k_reduce_level(uint32_t off, uint32_t n, int children_are_leaves
     const int m = __popc(nd.mask);
     for (int k = 0; k < m; ++k) {
         const uint32_t ch = nd.first_child + k;
-        const float4 C = normal[ch];
-        const float dpos = __fadd_rn(__fadd_rn(__fmul_rn(C.x, P.x), __fmul_rn(C.y, P.y)), __fmul_rn(C.z, P.z));
-        const float dneg = __fadd_rn(__fadd_rn(__fmul_rn(-C.x, P.x), __fmul_rn(-C.y, P.y)), __fmul_rn(-C.z, P.z));
+        const uint32_t r = route[ch];
         const ulonglong2 cs = csum[ch];
         const uint2 cc = ccnt[ch];
-        if (dpos >= 0.0f) { s0 += cs.x; c0 += cc.x; } else { s1 += cs.x; c1 += cc.x; }
-        if (dneg >= 0.0f) { s0 += cs.y; c0 += cc.y; } else { s1 += cs.y; c1 += cc.y; }
+        if (children_are_leaves) value[ch] = node_values(cs.x, cc.x, cs.y, cc.y);
+        if (!(r & 1u)) { s0 += cs.x; c0 += cc.x; } else { s1 += cs.x; c1 += cc.x; }
+        if (!(r & 2u)) { s0 += cs.y; c0 += cc.y; } else { s1 += cs.y; c1 += cc.y; }
     }
     tot_sum[id] = make_ulonglong2(s0, s1);
     tot_cnt[id] = make_uint2(c0, c1);
@@ -109,12 +109,14 @@ int accumulate(wfpg_svo* s, const float* pos, const float* wout, const float* L,
     const auto* ac = reinterpret_cast<const uint2*>(s->acc_cnt);
     auto* ts = reinterpret_cast<ulonglong2*>(s->tot_sum);
     auto* tc = reinterpret_cast<uint2*>(s->tot_cnt);
-    const uint32_t nl = s->level_off[D + 1] - s->level_off[D];
-    WFPG_LAUNCH(k_leaf_values, div_up(nl, T), T, 0, st, s->level_off[D], nl, as, ac, s->value);
+    if (D == 0) {
+        const uint32_t nl = s->level_off[D + 1] - s->level_off[D];
+        WFPG_LAUNCH(k_leaf_values, div_up(nl, T), T, 0, st, s->level_off[D], nl, as, ac, s->value);
+    }
     for (int l = D - 1; l >= 0; --l) {
         const uint32_t cnt = s->level_off[l + 1] - s->level_off[l];
-        WFPG_LAUNCH(k_reduce_level, div_up(cnt, T), T, 0, st, s->level_off[l], cnt, l + 1 == D, s->node, s->normal, as, ac, ts,
-                                                     tc, s->value);
+        WFPG_LAUNCH(k_reduce_level, div_up(cnt, T), T, 0, st, s->level_off[l], cnt, l + 1 == D, s->node, s->route,
+                    as, ac, ts, tc, s->value);
     }
     return cudaGetLastError() == cudaSuccess ? WFPG_OK : WFPG_ERR_CUDA;
 }

@@ -20,6 +20,7 @@ struct wfpg_svo {
     uint64_t* key = nullptr;                  // Morton prefix of each node at its level
     uint32_t* leaf_count = nullptr;
     float4* normal = nullptr;                 // (nx, ny, nz, 0)
+    uint8_t* route = nullptr;                 // bit0/bit1: parent side taking this node's side 0/1
     uint32_t* frag_off = nullptr;             // leaves + 1
     uint32_t* frag_prim = nullptr;            // n_frags
     // radiant exitance, two sides per node

@@ -387,8 +387,26 @@ struct DevBuf {
     } while (0)
 }  // namespace
 
+// Which parent side each side of a node feeds in the bottom-up average: side s
+// of child C (normal (1 - 2s) N_C) goes to the parent's side 0 when
+// dot((1 - 2s) N_C, N_P) >= 0, else to side 1.  Fixed once the normals are.
+__global__ void k_route(uint32_t n, const uint32_t* __restrict__ parent, const float4* __restrict__ normal,
+                        uint8_t* __restrict__ route) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t p = parent[i];
+    if (p == kNone) {
+        route[i] = 0;
+        return;
+    }
+    const float4 C = normal[i], P = normal[p];
+    const float dpos = __fadd_rn(__fadd_rn(__fmul_rn(C.x, P.x), __fmul_rn(C.y, P.y)), __fmul_rn(C.z, P.z));
+    const float dneg = __fadd_rn(__fadd_rn(__fmul_rn(-C.x, P.x), __fmul_rn(-C.y, P.y)), __fmul_rn(-C.z, P.z));
+    route[i] = (uint8_t)((dpos >= 0.0f ? 0u : 1u) | (dneg >= 0.0f ? 0u : 2u));
+}
+
 void svo_free_arrays(wfpg_svo* s) {
-    void* ptrs[] = {s->node, s->parent, s->key, s->leaf_count, s->normal, s->frag_off, s->frag_prim,
+    void* ptrs[] = {s->node, s->parent, s->key, s->leaf_count, s->normal, s->route, s->frag_off, s->frag_prim,
                     s->acc_sum, s->acc_cnt, s->tot_sum, s->tot_cnt, s->value, s->status};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -535,6 +553,8 @@ int build_svo(const wfpg_scene* scene, int D, cudaStream_t st, wfpg_svo* s, std:
     for (int l = D - 1; l >= 0; --l)
         WFPG_LAUNCH(k_inner_normals, div_up(lsize[l], T), T, 0, st, s->level_off[l], lsize[l], s->node, s->normal,
                                                            s->leaf_count);
+    WFPG_ALLOC(s->route, (size_t)nn);
+    WFPG_LAUNCH(k_route, div_up(nn, T), T, 0, st, nn, s->parent, s->normal, s->route);
     // 8. exitance arrays, zeroed
     WFPG_ALLOC(s->acc_sum, 16 * (size_t)nn);
     WFPG_ALLOC(s->tot_sum, 16 * (size_t)nn);
