@@ -16,7 +16,7 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRCS = ["svo.cpp", "octa_trace.cpp", "bins.cpp", "guide.cpp", "api.cpp"]
+_SRCS = ["svo.cpp", "octa_trace.cpp", "bins.cpp", "guide.cpp", "api.cpp", "learned.cpp"]
 _HDRS = ["oracle.h", "oracle_internal.h"]
 _OUT = os.path.join(_HERE, "_build", "liboracle.so")
 _lock = threading.Lock()
@@ -88,6 +88,11 @@ def _declare(L):
         "orc_blur": (None, [P, I32]),
         "orc_pdf_cdf": (None, [P, I32, P, P, P]),
         "orc_trace": (None, [P, P, P, SZ, F, F, I32, P, P, P, P, P, P, P, P]),
+        "orc_mlp_num_params": (SZ, []),
+        "orc_mlp_features": (None, [P, P, SZ, P, F, P]),
+        "orc_mlp_forward": (None, [P, P, P, SZ, P, F, I32, P, P]),
+        "orc_mlp_grad": (C.c_double, [P, P, P, SZ, P, F, P, I32, P]),
+        "orc_adam": (None, [P, P, P, P, SZ, I32, C.c_double, C.c_double, C.c_double, C.c_double]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -319,3 +324,47 @@ def pdf_cdf(f, N):
     cm = np.zeros(N, np.float32)
     lib().orc_pdf_cdf(_p(f), N, _p(pdf), _p(cr), _p(cm))
     return pdf, cr, cm
+
+
+# ----------------------------------------------------------------------------- learned proposal
+MLP_IN, MLP_HID, MLP_OUT = 80, 64, 1024
+
+
+def mlp_num_params() -> int:
+    return int(lib().orc_mlp_num_params())
+
+
+def mlp_features(pos, nrm, lo, S):
+    pos, nrm, lo = _c(pos, np.float32), _c(nrm, np.float32), _c(lo, np.float32)
+    out = np.zeros((len(pos), MLP_IN), np.float64)
+    lib().orc_mlp_features(_p(pos), _p(nrm), len(pos), _p(lo), float(S), _p(out))
+    return out
+
+
+def mlp_forward(params, pos, nrm, lo, S, bf16=False):
+    params, pos, nrm, lo = (_c(params, np.float32), _c(pos, np.float32), _c(nrm, np.float32),
+                            _c(lo, np.float32))
+    n = len(pos)
+    z = np.zeros((n, MLP_OUT), np.float64)
+    p = np.zeros((n, MLP_OUT), np.float64)
+    lib().orc_mlp_forward(_p(params), _p(pos), _p(nrm), n, _p(lo), float(S), int(bf16), _p(z), _p(p))
+    return z, p
+
+
+def mlp_grad(params, pos, nrm, lo, S, target, bf16=False):
+    params, pos, nrm, lo = (_c(params, np.float32), _c(pos, np.float32), _c(nrm, np.float32),
+                            _c(lo, np.float32))
+    target = _c(target, np.float32)
+    g = np.zeros(mlp_num_params(), np.float64)
+    loss = lib().orc_mlp_grad(_p(params), _p(pos), _p(nrm), len(pos), _p(lo), float(S), _p(target),
+                              int(bf16), _p(g))
+    return float(loss), g
+
+
+def adam(params, m, v, grad, t, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+    params = _c(params, np.float32).copy()
+    m = _c(m, np.float64).copy()
+    v = _c(v, np.float64).copy()
+    grad = _c(grad, np.float64)
+    lib().orc_adam(_p(params), _p(m), _p(v), _p(grad), len(params), int(t), lr, b1, b2, eps)
+    return params, m, v

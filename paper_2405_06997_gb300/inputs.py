@@ -486,3 +486,32 @@ def frame_spheres(seed: int = 1, width=1920, height=1080, n_bins=2048, depth=9,
                     n_bins_max=n_bins, blur=True, jitter=True, seed=seed,
                     desc=f"cornell+200 spheres D={depth}, {width}x{height} primary hits, "
                          f"{n_bins} Zipf(1.2) bins, {grid_n}x{grid_n}")
+
+
+# --------------------------------------------------------------------------------------
+# learned proposal: initial weights and synthetic target distributions
+
+MLP_IN, MLP_FEAT, MLP_HID, MLP_OUT = 80, 78, 64, 1024
+
+
+def mlp_init(seed: int) -> np.ndarray:
+    """Seeded initial parameters (He-uniform weights, zero biases), flat float32
+    in the order W1[64][80], b1, W2[64][64], b2, W3[64][64], b3, W4[1024][64],
+    b4; the two padding input columns of W1 are zero."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for nout, nin, fan in ((MLP_HID, MLP_IN, MLP_FEAT), (MLP_HID, MLP_HID, MLP_HID),
+                           (MLP_HID, MLP_HID, MLP_HID), (MLP_OUT, MLP_HID, MLP_HID)):
+        lim = math.sqrt(6.0 / fan)
+        W = rng.uniform(-lim, lim, (nout, nin))
+        if nin == MLP_IN:
+            W[:, MLP_FEAT:] = 0.0
+        parts += [W.ravel(), np.zeros(nout)]
+    return np.concatenate(parts).astype(np.float32)
+
+
+def random_distributions(seed: int, n: int, k: int = MLP_OUT, conc: float = 0.3) -> np.ndarray:
+    """n seeded probability vectors over k cells (Dirichlet(conc)), float32."""
+    rng = np.random.default_rng(seed)
+    g = rng.gamma(conc, 1.0, (n, k)) + 1e-6
+    return (g / g.sum(axis=1, keepdims=True)).astype(np.float32)
