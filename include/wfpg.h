@@ -56,7 +56,8 @@ enum {
 enum {
     WFPG_STATUS_TRACE_CAP = 1u << 0,    /* a cone ray hit the walk's step cap (treated as a miss) */
     WFPG_STATUS_BIN_CAPACITY = 1u << 1, /* bin_rays found more bins than bin_cap */
-    WFPG_STATUS_RUN_SIZES = 1u << 2     /* run sizes do not add up to the ray count */
+    WFPG_STATUS_RUN_SIZES = 1u << 2,    /* run sizes do not add up to the ray count */
+    WFPG_STATUS_MMA_TIMEOUT = 1u << 3   /* a tensor-core wait hit its limit (results invalid) */
 };
 
 #define WFPG_MAX_DEPTH 11
@@ -262,6 +263,71 @@ WFPG_API int guide_sample(const float* pdf, const float* cdf_row, const float* c
  */
 WFPG_API int guide_eval_pdf(const float* pdf, int N, uint32_t bin_cap, const uint32_t* bin,
                    const float* dir, uint32_t n, float* out, void* stream);
+
+/* -------------------------------------------------------------------------
+ * Learned proposal -- a project addition; the paper has no counterpart.
+ * An MLP maps a bin origin's position and normal to a distribution over the
+ * 32 x 32 cells of the same octahedral grid: features (78) = p^ = (p - lo) /
+ * size, sin(2^k pi p^) and cos(2^k pi p^) for k = 0..11, and the normal;
+ * layers 78 -> 64 -> 64 -> 64 -> 1024 with ReLU; softmax over the logits.
+ * bfloat16 weights and activations, float32 accumulation on the tensor cores
+ * (tcgen05), float32 master weights and Adam.  It is trained online on the
+ * SVO-traced fields of guide_build_pdf with the loss KL(q || softmax(z)), q
+ * the traced field normalised per bin; the traced PDF stays the fallback and
+ * the judge of the learned one.
+ *
+ * Parameters (WFPG_MLP_PARAMS float32, in this order): W1[64][80] (inputs
+ * padded with two zero columns), b1[64], W2[64][64], b2[64], W3[64][64],
+ * b3[64], W4[1024][64], b4[1024].
+ */
+#define WFPG_MLP_PARAMS 80064
+typedef struct wfpg_mlp wfpg_mlp;
+
+typedef struct wfpg_learned_params {
+    float lo[3];   /* scene AABB lower corner (host) */
+    float size;    /* scene AABB side */
+    float eps;     /* floor added to every cell's probability before the CDF (keeps the PDF > 0) */
+} wfpg_learned_params;
+
+typedef struct wfpg_adam_params {
+    float lr, beta1, beta2, eps;
+    int update;    /* 0: compute the loss (and gradient) only, leave the weights */
+} wfpg_adam_params;
+
+/* mlp_create: device state for batches of up to max_batch samples; params is
+ * a host array of WFPG_MLP_PARAMS floats (NULL: all zero).  Synchronises. */
+WFPG_API int mlp_create(const float* params, uint32_t max_batch, void* stream, wfpg_mlp** out);
+WFPG_API int mlp_destroy(wfpg_mlp* mlp);
+/* copy the float32 master weights to a host array (synchronises) */
+WFPG_API int mlp_get_params(const wfpg_mlp* mlp, float* params, void* stream);
+/* status word (WFPG_STATUS_MMA_TIMEOUT), synchronises */
+WFPG_API int mlp_status(wfpg_mlp* mlp, uint32_t* flags, int clear, void* stream);
+
+/*
+ * guide_learned_build_pdf -- the learned counterpart of guide_build_pdf (N =
+ * 32): for each bin b < min(*n_bins_dev, bin_cap) (all bin_cap when NULL) the
+ * MLP's distribution at the origin pos/nrm[origin_ray[b]] (row b when
+ * origin_ray is NULL), plus eps per cell, becomes pdf / cdf_row / cdf_marg in
+ * exactly the layout guide_sample and guide_eval_pdf read.  bin_cap <=
+ * max_batch.
+ */
+WFPG_API int guide_learned_build_pdf(wfpg_mlp* mlp, const float* pos, const float* nrm,
+                                     const uint32_t* origin_ray, const uint32_t* n_bins_dev,
+                                     uint32_t bin_cap, const wfpg_learned_params* p, float* pdf,
+                                     float* cdf_row, float* cdf_marg, void* stream);
+
+/*
+ * guide_learned_train_step -- one step on n samples (n <= max_batch): pos/nrm
+ * (xyz) of the sample points and target[n][1024], any non-negative field per
+ * sample (normalised here; e.g. the pdf of guide_build_pdf at N = 32).
+ * Writes the mean KL to *loss_out and the gradient (WFPG_MLP_PARAMS floats)
+ * to grad_out when they are not NULL (device pointers); with opt->update the
+ * weights take one Adam step.
+ */
+WFPG_API int guide_learned_train_step(wfpg_mlp* mlp, const float* pos, const float* nrm, uint32_t n,
+                                      const float* target, const wfpg_learned_params* p,
+                                      const wfpg_adam_params* opt, float* loss_out, float* grad_out,
+                                      void* stream);
 
 /* -------------------------------------------------------------------------
  * Inspection (used by tests; each synchronises `stream`).  Host buffers are

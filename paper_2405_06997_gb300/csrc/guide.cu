@@ -447,6 +447,40 @@ __global__ void __launch_bounds__(kGuideThreads) k_guide_build(TraceArgs T, Guid
     }
 }
 
+// PDF and CDFs of given fields (one CTA per bin): row CDFs and the marginal in
+// warp order with a running maximum, pdf = f N^2 / (T 4 pi), as in the traced path
+__global__ void __launch_bounds__(256) k_field_pdf(const float* __restrict__ field, int N,
+                                                   const uint32_t* __restrict__ n_bins_dev, uint32_t bin_cap,
+                                                   float* __restrict__ pdf, float* __restrict__ cdf_row,
+                                                   float* __restrict__ cdf_marg) {
+    extern __shared__ __align__(16) float fsm[];
+    const int NN = N * N;
+    float* f = fsm;
+    float* rows = f + NN;
+    float* rowtot = rows + NN;
+    float* marg = rowtot + N;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t nb = n_bins_dev ? min(*n_bins_dev, bin_cap) : bin_cap;
+    const uint32_t b = blockIdx.x;
+    if (b >= nb) return;
+    for (int c = tid; c < NN; c += 256) f[c] = field[(size_t)b * NN + c];
+    __syncthreads();
+    for (int j = warp; j < N; j += 8) {
+        const float tot = warp_scan_row(f + j * N, rows + j * N, N, lane);
+        if (lane == 0) rowtot[j] = tot;
+    }
+    __syncthreads();
+    if (warp == 0) warp_scan_row(rowtot, marg, N, lane);
+    __syncthreads();
+    const float den = __fmul_rn(marg[N - 1], kFourPi);
+    const float nn = (float)NN;
+    for (int c = tid; c < NN; c += 256) {
+        pdf[(size_t)b * NN + c] = __fdiv_rn(__fmul_rn(f[c], nn), den);
+        cdf_row[(size_t)b * NN + c] = rows[c];
+    }
+    for (int j = tid; j < N; j += 256) cdf_marg[(size_t)b * N + j] = marg[j];
+}
+
 // first index with x[i] > t (N if none); x is non-decreasing
 __device__ __forceinline__ int upper_bound_f(const float* __restrict__ x, int N, float t) {
     int lo = 0, hi = N;
@@ -586,6 +620,17 @@ int guide_build_impl(const wfpg_svo* s, const float* pos, const uint32_t* origin
     WFPG_GUIDE_CASE(256)
 #undef WFPG_GUIDE_CASE
     return WFPG_ERR_INVALID_ARG;
+}
+
+int field_pdf_impl(const float* field, int N, const uint32_t* n_bins_dev, uint32_t bin_cap, float* pdf,
+                   float* cdf_row, float* cdf_marg, cudaStream_t st) {
+    if (bin_cap == 0) return WFPG_OK;
+    const size_t smem = sizeof(float) * (2 * (size_t)N * N + 2 * (size_t)N);
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(k_field_pdf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return WFPG_ERR_CUDA;
+    WFPG_LAUNCH(k_field_pdf, bin_cap, 256, smem, st, field, N, n_bins_dev, bin_cap, pdf, cdf_row, cdf_marg);
+    return cudaGetLastError() == cudaSuccess ? WFPG_OK : WFPG_ERR_CUDA;
 }
 
 int guide_sample_impl(const float* pdf, const float* cdf_row, const float* cdf_marg, int N, uint32_t bin_cap,

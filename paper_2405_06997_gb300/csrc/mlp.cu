@@ -1,0 +1,591 @@
+// The learned proposal (a project addition; the paper has no counterpart):
+// an MLP 78 -> 64 -> 64 -> 64 -> 1024 (ReLU) whose softmax over the 32 x 32
+// octahedral cells proposes a bin's directional distribution, trained online
+// against the SVO-traced fields of Alg. 3 with KL(q || softmax(z)).
+//
+// Every layer, forward and backward, is one tcgen05 GEMM on bfloat16 operands
+// with float32 accumulation in tensor memory:
+//   forward   H1 = relu(X W1^T + b1), H2, H3 likewise, Z = H3 W4^T + b4
+//   backward  G4 = (softmax(Z) - q) / n; dW4 = G4^T H3, dA3 = (G4 W4) o [H3 > 0],
+//             dW3 = dA3^T H2, dA2 = (dA3 W3) o [H2 > 0], ... , dW1 = dA1^T X
+// All GEMMs are "TN": D[M x N] = A[M x K] B[N x K]^T with both operands
+// K-contiguous, so the backward uses transposed copies (written by the
+// forward epilogues and the weight-conversion kernel).  Weight gradients
+// reduce over the batch with split-K and float32 atomics.  Adam updates
+// float32 master weights, then bfloat16 copies are refreshed.
+#include <cuda_bf16.h>
+
+#include <cstring>
+#include <string>
+
+#include "common.cuh"
+#include "svo.cuh"
+#include "tc.cuh"
+
+typedef __nv_bfloat16 bf16;
+
+namespace wfpg {
+int field_pdf_impl(const float* field, int N, const uint32_t* n_bins_dev, uint32_t bin_cap, float* pdf,
+                   float* cdf_row, float* cdf_marg, cudaStream_t st);
+int set_last_error(int code, const std::string& msg);
+}  // namespace wfpg
+
+using namespace wfpg;
+
+namespace {
+
+constexpr int kIn = 80, kHid = 64, kOut = 1024;
+constexpr size_t kOffW1 = 0, kOffB1 = kOffW1 + kHid * kIn, kOffW2 = kOffB1 + kHid, kOffB2 = kOffW2 + kHid * kHid,
+                 kOffW3 = kOffB2 + kHid, kOffB3 = kOffW3 + kHid * kHid, kOffW4 = kOffB3 + kHid,
+                 kOffB4 = kOffW4 + (size_t)kOut * kHid, kParams = kOffB4 + kOut;
+
+enum Epi { kEpiF32 = 0, kEpiBf16Relu = 1, kEpiAtomic = 2, kEpiReluGrad = 3 };
+
+struct GemmArgs {
+    const bf16* A;   // [M][lda], K contiguous
+    const bf16* B;   // [N][ldb], K contiguous
+    int lda, ldb;
+    int M, N, K;
+    int chunks_per_split;  // K chunks of 64 per blockIdx.z
+    float* C;              // f32 output [M][ldc] (kEpiF32, kEpiAtomic)
+    int ldc;
+    bf16* O;               // bf16 output [M][ldo]
+    int ldo;
+    bf16* OT;              // optional transposed bf16 output [N][ldot]
+    int ldot;
+    const float* bias;     // [N] (kEpiF32, kEpiBf16Relu)
+    const bf16* act;       // forward activation [M][ldact] (kEpiReluGrad)
+    int ldact;
+    uint32_t* status;
+};
+
+constexpr int kGemmThreads = 128;
+constexpr int kKChunk = 64;
+
+template <int BN>
+struct TmemCols {
+    static constexpr uint32_t value = BN <= 32 ? 32 : (BN <= 64 ? 64 : (BN <= 128 ? 128 : 256));
+};
+
+// copy rows [r0, r0 + rows) x k [k0, k0 + 64) of a K-contiguous bf16 matrix into
+// the no-swizzle K-major core-matrix layout: 16-byte chunk c of row r goes to
+// (r / 8) * 1024 + c * 128 + (r % 8) * 16; rows or k past the end read zero
+__device__ __forceinline__ void load_tile(uint8_t* smem, const bf16* g, int ld, int r0, int rows, int nrows_total,
+                                          int k0, int K) {
+    for (int idx = threadIdx.x; idx < rows * 8; idx += kGemmThreads) {
+        const int r = idx >> 3, c = idx & 7;
+        const int gr = r0 + r, gk = k0 + c * 8;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (gr < nrows_total && gk < K) v = *reinterpret_cast<const uint4*>(g + (size_t)gr * ld + gk);
+        *reinterpret_cast<uint4*>(smem + (r >> 3) * 1024 + c * 128 + (r & 7) * 16) = v;
+    }
+}
+
+template <int BN, int EPI>
+__global__ void __launch_bounds__(kGemmThreads) k_gemm_tn(GemmArgs g) {
+    __shared__ __align__(1024) uint8_t sA[128 * kKChunk * 2];
+    __shared__ __align__(1024) uint8_t sB[BN * kKChunk * 2];
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tmem_base;
+    constexpr uint32_t kCols = TmemCols<BN>::value;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.x * 128, n0 = blockIdx.y * BN;
+    const int total_chunks = (g.K + kKChunk - 1) / kKChunk;
+    const int kc0 = blockIdx.z * g.chunks_per_split;
+    const int kc1 = min(total_chunks, kc0 + g.chunks_per_split);
+    if (warp == 0) tc::tmem_alloc(&tmem_base, kCols);
+    if (tid == 0) {
+        tc::mbar_init(&mbar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = tmem_base;
+    constexpr uint32_t idesc = tc::idesc_bf16_f32(128, BN);
+    uint32_t phase = 0;
+    bool ok = true;
+    for (int kc = kc0; kc < kc1 && ok; ++kc) {
+        load_tile(sA, g.A, g.lda, m0, 128, g.M, kc * kKChunk, g.K);
+        load_tile(sB, g.B, g.ldb, n0, BN, g.N, kc * kKChunk, g.K);
+        tc::fence_proxy_async();
+        __syncthreads();
+        if (tid == 0) {
+            tc::fence_after_sync();
+            const uint32_t a0 = tc::smem_addr(sA), b0 = tc::smem_addr(sB);
+#pragma unroll
+            for (int s = 0; s < kKChunk / 16; ++s) {
+                // K step of 16 = two core matrices along K (128 B apart); 8-row groups 1024 B apart
+                const uint64_t ad = tc::smem_desc(a0 + s * 256, 128, 1024);
+                const uint64_t bd = tc::smem_desc(b0 + s * 256, 128, 1024);
+                tc::mma_bf16(tmem, ad, bd, idesc, (kc > kc0 || s > 0) ? 1u : 0u);
+            }
+            tc::mma_commit(&mbar);
+        }
+        // the next chunk overwrites the tiles: wait until the MMAs have read them
+        // (bounded; the verdict is made uniform over the CTA)
+        ok = __syncthreads_and(tc::mbar_wait(&mbar, phase)) != 0;
+        phase ^= 1u;
+    }
+    if (!ok && lane == 0) atomicOr(g.status, (uint32_t)WFPG_STATUS_MMA_TIMEOUT);
+    tc::fence_after_sync();
+    if (ok && kc1 > kc0) {
+        const int row = m0 + warp * 32 + lane;
+        for (int c0 = 0; c0 < BN; c0 += 16) {
+            float v[16];
+            tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+            if (row >= g.M) continue;
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int n = n0 + c0 + i;
+                if (n >= g.N) continue;
+                if (EPI == kEpiF32) {
+                    g.C[(size_t)row * g.ldc + n] = v[i] + (g.bias ? g.bias[n] : 0.0f);
+                } else if (EPI == kEpiAtomic) {
+                    atomicAdd(&g.C[(size_t)row * g.ldc + n], v[i]);
+                } else if (EPI == kEpiBf16Relu) {
+                    const bf16 h = __float2bfloat16_rn(fmaxf(v[i] + g.bias[n], 0.0f));
+                    g.O[(size_t)row * g.ldo + n] = h;
+                    if (g.OT) g.OT[(size_t)n * g.ldot + row] = h;
+                } else {  // kEpiReluGrad
+                    const float a = __bfloat162float(g.act[(size_t)row * g.ldact + n]);
+                    const bf16 d = __float2bfloat16_rn(a > 0.0f ? v[i] : 0.0f);
+                    g.O[(size_t)row * g.ldo + n] = d;
+                    if (g.OT) g.OT[(size_t)n * g.ldot + row] = d;
+                }
+            }
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, kCols);
+}
+
+// input features of sample i (origin ray r of bin i when origin_ray is given)
+__global__ void k_mlp_features(const float* __restrict__ pos, const float* __restrict__ nrm,
+                               const uint32_t* __restrict__ origin_ray, const uint32_t* __restrict__ n_dev,
+                               uint32_t n_cap, float lox, float loy, float loz, float inv_s, bf16* __restrict__ X,
+                               bf16* __restrict__ XT, int ldxt) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_cap) return;
+    const uint32_t n = n_dev ? min(*n_dev, n_cap) : n_cap;
+    float f[kIn];
+#pragma unroll
+    for (int k = 0; k < kIn; ++k) f[k] = 0.0f;
+    const uint32_t r = origin_ray ? (i < n ? origin_ray[i] : kNone) : i;
+    if (i < n && r != kNone) {
+        const float ph[3] = {(pos[3 * (size_t)r + 0] - lox) * inv_s, (pos[3 * (size_t)r + 1] - loy) * inv_s,
+                             (pos[3 * (size_t)r + 2] - loz) * inv_s};
+        f[0] = ph[0];
+        f[1] = ph[1];
+        f[2] = ph[2];
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            const float sc = (float)(1 << k);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                f[3 + 6 * k + a] = sinpif(sc * ph[a]);
+                f[6 + 6 * k + a] = cospif(sc * ph[a]);
+            }
+        }
+        f[75] = nrm[3 * (size_t)r + 0];
+        f[76] = nrm[3 * (size_t)r + 1];
+        f[77] = nrm[3 * (size_t)r + 2];
+    }
+#pragma unroll
+    for (int k = 0; k < kIn; ++k) {
+        const bf16 b = __float2bfloat16_rn(f[k]);
+        X[(size_t)i * kIn + k] = b;
+        if (XT) XT[(size_t)k * ldxt + i] = b;
+    }
+}
+
+// one warp per row of 1024 logits: softmax; inference writes the field
+// softmax + eps, training writes G = (softmax - q) / n (bf16) and the KL
+__global__ void k_softmax_rows(const float* __restrict__ Z, uint32_t rows, const uint32_t* __restrict__ n_dev,
+                               float eps, float* __restrict__ field, const float* __restrict__ target,
+                               float inv_n, bf16* __restrict__ G, float* __restrict__ loss) {
+    const uint32_t row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (row >= rows) return;
+    const uint32_t nvalid = n_dev ? min(*n_dev, rows) : rows;
+    const float* z = Z + (size_t)row * kOut;
+    float v[32];
+    float m = -3.4e38f;
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+        v[k] = z[k * 32 + lane];
+        m = fmaxf(m, v[k]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    float s = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+        v[k] = v[k] - m;
+        s += expf(v[k]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    const float inv_s = 1.0f / s, log_s = logf(s);
+    if (!target) {
+#pragma unroll
+        for (int k = 0; k < 32; ++k) field[(size_t)row * kOut + k * 32 + lane] = expf(v[k]) * inv_s + eps;
+        (void)nvalid;
+        return;
+    }
+    const float* t = target + (size_t)row * kOut;
+    float tv[32], ts = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+        tv[k] = t[k * 32 + lane];
+        ts += tv[k];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ts += __shfl_xor_sync(0xffffffffu, ts, o);
+    const float inv_t = ts > 0.0f ? 1.0f / ts : 0.0f;
+    float kl = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+        const float q = tv[k] * inv_t;
+        const float logp = v[k] - log_s;
+        if (q > 0.0f) kl += q * (logf(q) - logp);
+        G[(size_t)row * kOut + k * 32 + lane] = __float2bfloat16_rn((expf(logp) - q) * inv_n);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) kl += __shfl_xor_sync(0xffffffffu, kl, o);
+    if (lane == 0) atomicAdd(loss, kl * inv_n);
+}
+
+// out[c] += sum over rows of G[r][c] (bf16 values as stored)
+__global__ void k_colsum(const bf16* __restrict__ G, int rows, int cols, int ld, int rows_per_block,
+                         float* __restrict__ out) {
+    const int r0 = blockIdx.x * rows_per_block, r1 = min(rows, r0 + rows_per_block);
+    for (int c = threadIdx.x; c < cols; c += blockDim.x) {
+        float s = 0.0f;
+        for (int r = r0; r < r1; ++r) s += __bfloat162float(G[(size_t)r * ld + c]);
+        atomicAdd(&out[c], s);
+    }
+}
+
+// out[c][r] = in[r][c] through a 32 x 32 shared tile
+__global__ void k_transpose(const bf16* __restrict__ in, int rows, int cols, int ldi, bf16* __restrict__ out,
+                            int ldo) {
+    __shared__ bf16 t[32][33];
+    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+        const int r = r0 + k, c = c0 + threadIdx.x;
+        if (r < rows && c < cols) t[k][threadIdx.x] = in[(size_t)r * ldi + c];
+    }
+    __syncthreads();
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+        const int c = c0 + k, r = r0 + threadIdx.x;
+        if (r < rows && c < cols) out[(size_t)c * ldo + r] = t[threadIdx.x][k];
+    }
+}
+
+// Adam (Kingma & Ba 2015) on the float32 master weights
+__global__ void k_adam(float* __restrict__ w, float* __restrict__ m, float* __restrict__ v,
+                       const float* __restrict__ grad, uint32_t n, float lr, float b1, float b2, float eps, float c1,
+                       float c2) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = grad[i];
+    const float mi = b1 * m[i] + (1.0f - b1) * gi;
+    const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+// bf16 copies of the weights: W[out][in] and its transpose
+__global__ void k_convert(const float* __restrict__ W, int nout, int nin, bf16* __restrict__ Wb,
+                          bf16* __restrict__ WbT) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nout * nin) return;
+    const int o = i / nin, k = i % nin;
+    const bf16 b = __float2bfloat16_rn(W[i]);
+    Wb[i] = b;
+    if (WbT) WbT[(size_t)k * nout + o] = b;
+}
+
+}  // namespace
+
+struct wfpg_mlp {
+    int device = 0;
+    uint32_t max_batch = 0, mpad = 0;
+    int step = 0;
+    float *params = nullptr, *m = nullptr, *v = nullptr, *grad = nullptr;
+    bf16 *w1 = nullptr, *w2 = nullptr, *w3 = nullptr, *w4 = nullptr, *w2t = nullptr, *w3t = nullptr,
+         *w4t = nullptr;
+    bf16 *x = nullptr, *xt = nullptr, *h1 = nullptr, *h1t = nullptr, *h2 = nullptr, *h2t = nullptr, *h3 = nullptr,
+         *h3t = nullptr, *g4 = nullptr, *g4t = nullptr, *d3 = nullptr, *d3t = nullptr, *d2 = nullptr,
+         *d2t = nullptr, *d1 = nullptr, *d1t = nullptr;
+    float* z = nullptr;
+    float* field = nullptr;
+    float* loss = nullptr;
+    uint32_t* status = nullptr;
+};
+
+namespace {
+
+template <int BN, int EPI>
+void gemm(const GemmArgs& a, int splits, cudaStream_t st) {
+    GemmArgs g = a;
+    const int chunks = (g.K + kKChunk - 1) / kKChunk;
+    if (splits < 1) splits = 1;
+    if (splits > chunks) splits = chunks;
+    g.chunks_per_split = (chunks + splits - 1) / splits;
+    splits = (chunks + g.chunks_per_split - 1) / g.chunks_per_split;
+    const dim3 grid(div_up(g.M, 128), div_up(g.N, BN), splits);
+    auto kernel = k_gemm_tn<BN, EPI>;
+    WFPG_LAUNCH(kernel, grid, kGemmThreads, 0, st, g);
+}
+
+GemmArgs gargs(const bf16* A, int lda, const bf16* B, int ldb, int M, int N, int K, uint32_t* status) {
+    GemmArgs g;
+    std::memset(&g, 0, sizeof(g));
+    g.A = A;
+    g.lda = lda;
+    g.B = B;
+    g.ldb = ldb;
+    g.M = M;
+    g.N = N;
+    g.K = K;
+    g.status = status;
+    return g;
+}
+
+void convert_weights(wfpg_mlp* s, cudaStream_t st) {
+    const int T = 256;
+    WFPG_LAUNCH(k_convert, div_up(kHid * kIn, T), T, 0, st, s->params + kOffW1, kHid, kIn, s->w1, (bf16*)nullptr);
+    WFPG_LAUNCH(k_convert, div_up(kHid * kHid, T), T, 0, st, s->params + kOffW2, kHid, kHid, s->w2, s->w2t);
+    WFPG_LAUNCH(k_convert, div_up(kHid * kHid, T), T, 0, st, s->params + kOffW3, kHid, kHid, s->w3, s->w3t);
+    WFPG_LAUNCH(k_convert, div_up(kOut * kHid, T), T, 0, st, s->params + kOffW4, kOut, kHid, s->w4, s->w4t);
+}
+
+// forward through the hidden layers and the logits for n rows (X already set)
+void forward(wfpg_mlp* s, int n, bool keep_transposes, cudaStream_t st) {
+    const int mp = (int)s->mpad;
+    GemmArgs g = gargs(s->x, kIn, s->w1, kIn, n, kHid, kIn, s->status);
+    g.O = s->h1;
+    g.ldo = kHid;
+    g.OT = keep_transposes ? s->h1t : nullptr;
+    g.ldot = mp;
+    g.bias = s->params + kOffB1;
+    gemm<64, kEpiBf16Relu>(g, 1, st);
+    g = gargs(s->h1, kHid, s->w2, kHid, n, kHid, kHid, s->status);
+    g.O = s->h2;
+    g.ldo = kHid;
+    g.OT = keep_transposes ? s->h2t : nullptr;
+    g.ldot = mp;
+    g.bias = s->params + kOffB2;
+    gemm<64, kEpiBf16Relu>(g, 1, st);
+    g = gargs(s->h2, kHid, s->w3, kHid, n, kHid, kHid, s->status);
+    g.O = s->h3;
+    g.ldo = kHid;
+    g.OT = keep_transposes ? s->h3t : nullptr;
+    g.ldot = mp;
+    g.bias = s->params + kOffB3;
+    gemm<64, kEpiBf16Relu>(g, 1, st);
+    g = gargs(s->h3, kHid, s->w4, kHid, n, kOut, kHid, s->status);
+    g.C = s->z;
+    g.ldc = kOut;
+    g.bias = s->params + kOffB4;
+    gemm<256, kEpiF32>(g, 1, st);
+}
+
+int mlp_fail(int code, const std::string& msg) { return wfpg::set_last_error(code, msg); }
+
+}  // namespace
+
+extern "C" {
+
+int mlp_create(const float* params, uint32_t max_batch, void* stream, wfpg_mlp** out) {
+    if (!out) return mlp_fail(WFPG_ERR_INVALID_ARG, "mlp_create: null out");
+    *out = nullptr;
+    if (max_batch == 0 || max_batch > (1u << 24))
+        return mlp_fail(WFPG_ERR_INVALID_ARG, "mlp_create: max_batch must be in [1, 2^24]");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    wfpg_mlp* s = new wfpg_mlp();
+    cudaGetDevice(&s->device);
+    s->max_batch = max_batch;
+    s->mpad = (max_batch + 127) / 128 * 128;
+    const size_t mp = s->mpad;
+    bool ok = true;
+    auto alloc = [&](auto** p, size_t bytes) {
+        if (ok && cudaMalloc(reinterpret_cast<void**>(p), bytes ? bytes : 16) != cudaSuccess) ok = false;
+    };
+    alloc(&s->params, 4 * kParams);
+    alloc(&s->m, 4 * kParams);
+    alloc(&s->v, 4 * kParams);
+    alloc(&s->grad, 4 * kParams);
+    alloc(&s->w1, 2 * kHid * kIn);
+    alloc(&s->w2, 2 * kHid * kHid);
+    alloc(&s->w3, 2 * kHid * kHid);
+    alloc(&s->w4, 2 * (size_t)kOut * kHid);
+    alloc(&s->w2t, 2 * kHid * kHid);
+    alloc(&s->w3t, 2 * kHid * kHid);
+    alloc(&s->w4t, 2 * (size_t)kOut * kHid);
+    alloc(&s->x, 2 * mp * kIn);
+    alloc(&s->xt, 2 * mp * kIn);
+    bf16** acts[] = {&s->h1, &s->h1t, &s->h2, &s->h2t, &s->h3, &s->h3t, &s->d3, &s->d3t, &s->d2, &s->d2t,
+                     &s->d1, &s->d1t};
+    for (bf16** a : acts) alloc(a, 2 * mp * kHid);
+    alloc(&s->g4, 2 * mp * kOut);
+    alloc(&s->g4t, 2 * mp * kOut);
+    alloc(&s->z, 4 * mp * kOut);
+    alloc(&s->field, 4 * mp * kOut);
+    alloc(&s->loss, 16);
+    alloc(&s->status, 16);
+    if (!ok) {
+        mlp_destroy(s);
+        return mlp_fail(WFPG_ERR_OOM, "mlp_create: device allocation failed");
+    }
+    if (params)
+        ok = cudaMemcpyAsync(s->params, params, 4 * kParams, cudaMemcpyHostToDevice, st) == cudaSuccess;
+    else
+        ok = cudaMemsetAsync(s->params, 0, 4 * kParams, st) == cudaSuccess;
+    ok = ok && cudaMemsetAsync(s->m, 0, 4 * kParams, st) == cudaSuccess &&
+         cudaMemsetAsync(s->v, 0, 4 * kParams, st) == cudaSuccess &&
+         cudaMemsetAsync(s->status, 0, 16, st) == cudaSuccess;
+    convert_weights(s, st);
+    ok = ok && cudaStreamSynchronize(st) == cudaSuccess;
+    if (!ok) {
+        mlp_destroy(s);
+        return mlp_fail(WFPG_ERR_CUDA, "mlp_create: initialisation failed");
+    }
+    *out = s;
+    return WFPG_OK;
+}
+
+int mlp_destroy(wfpg_mlp* s) {
+    if (!s) return WFPG_OK;
+    void* ptrs[] = {s->params, s->m, s->v, s->grad, s->w1, s->w2, s->w3, s->w4, s->w2t, s->w3t, s->w4t,
+                    s->x, s->xt, s->h1, s->h1t, s->h2, s->h2t, s->h3, s->h3t, s->g4, s->g4t, s->d3,
+                    s->d3t, s->d2, s->d2t, s->d1, s->d1t, s->z, s->field, s->loss, s->status};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    delete s;
+    return WFPG_OK;
+}
+
+int mlp_get_params(const wfpg_mlp* s, float* params, void* stream) {
+    if (!s || !params) return mlp_fail(WFPG_ERR_INVALID_ARG, "mlp_get_params: null argument");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (cudaMemcpyAsync(params, s->params, 4 * kParams, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return mlp_fail(WFPG_ERR_CUDA, "mlp_get_params: copy failed");
+    return WFPG_OK;
+}
+
+int mlp_status(wfpg_mlp* s, uint32_t* flags, int clear, void* stream) {
+    if (!s || !flags) return mlp_fail(WFPG_ERR_INVALID_ARG, "mlp_status: null argument");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (cudaMemcpyAsync(flags, s->status, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return mlp_fail(WFPG_ERR_CUDA, "mlp_status: copy failed");
+    if (clear && cudaMemsetAsync(s->status, 0, 4, st) != cudaSuccess)
+        return mlp_fail(WFPG_ERR_CUDA, "mlp_status: clear failed");
+    return WFPG_OK;
+}
+
+int guide_learned_build_pdf(wfpg_mlp* s, const float* pos, const float* nrm, const uint32_t* origin_ray,
+                            const uint32_t* n_bins_dev, uint32_t bin_cap, const wfpg_learned_params* p, float* pdf,
+                            float* cdf_row, float* cdf_marg, void* stream) {
+    if (!s || !p || !pos || !nrm) return mlp_fail(WFPG_ERR_INVALID_ARG, "guide_learned_build_pdf: null argument");
+    if (bin_cap > s->max_batch)
+        return mlp_fail(WFPG_ERR_CAPACITY, "guide_learned_build_pdf: bin_cap exceeds the MLP's max_batch");
+    if (!(p->size > 0.0f) || !(p->eps >= 0.0f))
+        return mlp_fail(WFPG_ERR_INVALID_ARG, "guide_learned_build_pdf: size must be > 0 and eps >= 0");
+    if (bin_cap == 0) return WFPG_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    WFPG_LAUNCH(k_mlp_features, div_up(bin_cap, 128), 128, 0, st, pos, nrm, origin_ray, n_bins_dev, bin_cap,
+                p->lo[0], p->lo[1], p->lo[2], 1.0f / p->size, s->x, (bf16*)nullptr, 0);
+    forward(s, (int)bin_cap, false, st);
+    WFPG_LAUNCH(k_softmax_rows, div_up((uint64_t)bin_cap * 32, 256), 256, 0, st, s->z, bin_cap, n_bins_dev, p->eps,
+                s->field, (const float*)nullptr, 0.0f, (bf16*)nullptr, (float*)nullptr);
+    if (wfpg::field_pdf_impl(s->field, 32, n_bins_dev, bin_cap, pdf, cdf_row, cdf_marg, st) != WFPG_OK ||
+        cudaGetLastError() != cudaSuccess)
+        return mlp_fail(WFPG_ERR_CUDA, "guide_learned_build_pdf: launch failed");
+    return WFPG_OK;
+}
+
+int guide_learned_train_step(wfpg_mlp* s, const float* pos, const float* nrm, uint32_t n, const float* target,
+                             const wfpg_learned_params* p, const wfpg_adam_params* opt, float* loss_out,
+                             float* grad_out, void* stream) {
+    if (!s || !p || !opt) return mlp_fail(WFPG_ERR_INVALID_ARG, "guide_learned_train_step: null argument");
+    if (n == 0 || n > s->max_batch)
+        return mlp_fail(WFPG_ERR_CAPACITY, "guide_learned_train_step: n must be in [1, max_batch]");
+    if (!pos || !nrm || !target) return mlp_fail(WFPG_ERR_INVALID_ARG, "guide_learned_train_step: null array");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int mp = (int)s->mpad, N = (int)n;
+    const int T = 256;
+    bool ok = cudaMemsetAsync(s->grad, 0, 4 * kParams, st) == cudaSuccess &&
+              cudaMemsetAsync(s->loss, 0, 4, st) == cudaSuccess;
+    WFPG_LAUNCH(k_mlp_features, div_up(n, 128), 128, 0, st, pos, nrm, (const uint32_t*)nullptr,
+                (const uint32_t*)nullptr, n, p->lo[0], p->lo[1], p->lo[2], 1.0f / p->size, s->x, s->xt, mp);
+    forward(s, N, true, st);
+    WFPG_LAUNCH(k_softmax_rows, div_up((uint64_t)n * 32, 256), 256, 0, st, s->z, n, (const uint32_t*)nullptr, 0.0f,
+                (float*)nullptr, target, 1.0f / (float)n, s->g4, s->loss);
+    // output layer: dW4 = G4^T H3 (split-K over the batch), db4, dA3 = (G4 W4) o [H3 > 0]
+    WFPG_LAUNCH(k_transpose, dim3(div_up(kOut, 32), div_up(n, 32)), dim3(32, 8), 0, st, s->g4, N, kOut, kOut, s->g4t,
+                mp);
+    const int rows_per_block = 256;
+    const int splits = max(1, min(256, div_up(n, 256)));
+    GemmArgs g = gargs(s->g4t, mp, s->h3t, mp, kOut, kHid, N, s->status);
+    g.C = s->grad + kOffW4;
+    g.ldc = kHid;
+    gemm<64, kEpiAtomic>(g, splits / 4 > 0 ? splits / 4 : 1, st);
+    WFPG_LAUNCH(k_colsum, div_up(n, rows_per_block), 256, 0, st, s->g4, N, kOut, kOut, rows_per_block,
+                s->grad + kOffB4);
+    g = gargs(s->g4, kOut, s->w4t, kOut, N, kHid, kOut, s->status);
+    g.O = s->d3;
+    g.ldo = kHid;
+    g.OT = s->d3t;
+    g.ldot = mp;
+    g.act = s->h3;
+    g.ldact = kHid;
+    gemm<64, kEpiReluGrad>(g, 1, st);
+    // hidden layers
+    struct Layer {
+        bf16 *dA, *dAt, *Hprev_t, *Hprev, *Wt, *dAprev, *dAprev_t;
+        size_t offW, offB;
+        int nin;
+    } L[3] = {{s->d3, s->d3t, s->h2t, s->h2, s->w3t, s->d2, s->d2t, kOffW3, kOffB3, kHid},
+              {s->d2, s->d2t, s->h1t, s->h1, s->w2t, s->d1, s->d1t, kOffW2, kOffB2, kHid},
+              {s->d1, s->d1t, s->xt, s->x, nullptr, nullptr, nullptr, kOffW1, kOffB1, kIn}};
+    for (int l = 0; l < 3; ++l) {
+        g = gargs(L[l].dAt, mp, L[l].Hprev_t, mp, kHid, L[l].nin, N, s->status);
+        g.C = s->grad + L[l].offW;
+        g.ldc = L[l].nin;
+        if (L[l].nin == kIn) gemm<80, kEpiAtomic>(g, splits, st);
+        else gemm<64, kEpiAtomic>(g, splits, st);
+        WFPG_LAUNCH(k_colsum, div_up(n, rows_per_block), 64, 0, st, L[l].dA, N, kHid, kHid, rows_per_block,
+                    s->grad + L[l].offB);
+        if (L[l].Wt) {
+            g = gargs(L[l].dA, kHid, L[l].Wt, kHid, N, kHid, kHid, s->status);
+            g.O = L[l].dAprev;
+            g.ldo = kHid;
+            g.OT = L[l].dAprev_t;
+            g.ldot = mp;
+            g.act = L[l].Hprev;
+            g.ldact = kHid;
+            gemm<64, kEpiReluGrad>(g, 1, st);
+        }
+    }
+    if (grad_out) ok = ok && cudaMemcpyAsync(grad_out, s->grad, 4 * kParams, cudaMemcpyDeviceToDevice, st) == cudaSuccess;
+    if (loss_out) ok = ok && cudaMemcpyAsync(loss_out, s->loss, 4, cudaMemcpyDeviceToDevice, st) == cudaSuccess;
+    if (opt->update) {
+        s->step += 1;
+        const float c1 = 1.0f - powf(opt->beta1, (float)s->step), c2 = 1.0f - powf(opt->beta2, (float)s->step);
+        WFPG_LAUNCH(k_adam, div_up(kParams, T), T, 0, st, s->params, s->m, s->v, s->grad, (uint32_t)kParams, opt->lr,
+                    opt->beta1, opt->beta2, opt->eps, c1, c2);
+        convert_weights(s, st);
+    }
+    if (!ok || cudaGetLastError() != cudaSuccess)
+        return mlp_fail(WFPG_ERR_CUDA, "guide_learned_train_step: launch failed");
+    return WFPG_OK;
+}
+
+}  // extern "C"

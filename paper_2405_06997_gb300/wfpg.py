@@ -358,3 +358,126 @@ def bin_rays_static(svo: SVO, pos, nrm=None, *, mode=BIN_PARTITION_S, l_min=2, c
               _stream(stream)))
     out["bin_cap"] = bin_cap
     return out
+
+
+# ------------------------------------------------------------------ learned proposal
+MLP_PARAMS = 80064
+STATUS_MMA_TIMEOUT = 8
+
+
+class LearnedParams(C.Structure):
+    _fields_ = [("lo", F * 3), ("size", F), ("eps", F)]
+
+
+class AdamParams(C.Structure):
+    _fields_ = [("lr", F), ("beta1", F), ("beta2", F), ("eps", F), ("update", I32)]
+
+
+def _declare_mlp():
+    L = lib()
+    if getattr(L, "_mlp_declared", False):
+        return L
+    sig = {
+        "mlp_create": [P, U32, P, P],
+        "mlp_destroy": [P],
+        "mlp_get_params": [P, P, P],
+        "mlp_status": [P, P, I32, P],
+        "guide_learned_build_pdf": [P, P, P, P, P, U32, P, P, P, P, P],
+        "guide_learned_train_step": [P, P, P, U32, P, P, P, P, P, P],
+    }
+    for name, args in sig.items():
+        fn = getattr(L, name)
+        fn.restype = I32
+        fn.argtypes = args
+    L._mlp_declared = True
+    return L
+
+
+class MLP:
+    """The learned proposal's network and optimiser state (wfpg_mlp handle)."""
+
+    def __init__(self, params: np.ndarray | None, max_batch: int, stream=None):
+        L = _declare_mlp()
+        h = P()
+        arr = None if params is None else np.ascontiguousarray(params, np.float32)
+        if arr is not None and arr.size != MLP_PARAMS:
+            raise ValueError(f"params must hold {MLP_PARAMS} floats")
+        _check(L.mlp_create(_np_ptr(arr) if arr is not None else None, max_batch, _stream(stream),
+                            C.byref(h)))
+        self._h = h
+        self.max_batch = max_batch
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            _declare_mlp().mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def params(self, stream=None) -> np.ndarray:
+        out = np.zeros(MLP_PARAMS, np.float32)
+        _check(_declare_mlp().mlp_get_params(self._h, _np_ptr(out), _stream(stream)))
+        return out
+
+    def status(self, clear=True, stream=None) -> int:
+        f = np.zeros(1, np.uint32)
+        _check(_declare_mlp().mlp_status(self._h, _np_ptr(f), int(clear), _stream(stream)))
+        return int(f[0])
+
+
+def _learned(lo, size, eps):
+    p = LearnedParams()
+    for a in range(3):
+        p.lo[a] = float(lo[a])
+    p.size = float(size)
+    p.eps = float(eps)
+    return p
+
+
+def guide_learned_build_pdf(mlp: MLP, pos, nrm, origin_ray=None, n_bins=None, bin_cap=None, *, lo=(0, 0, 0),
+                            size=1.0, eps=1e-4, out=None, stream=None):
+    """The learned counterpart of guide_build_pdf (N = 32)."""
+    if bin_cap is None:
+        bin_cap = origin_ray.numel() if origin_ray is not None else pos.shape[0]
+    dev = pos.device
+    N = 32
+    if out is None:
+        out = (torch.empty((bin_cap, N * N), dtype=torch.float32, device=dev),
+               torch.empty((bin_cap, N * N), dtype=torch.float32, device=dev),
+               torch.empty((bin_cap, N), dtype=torch.float32, device=dev))
+    pdf, cr, cm = out
+    p = _learned(lo, size, eps)
+    _check(_declare_mlp().guide_learned_build_pdf(
+        mlp.handle, _ptr(pos, torch.float32, what="pos"), _ptr(nrm, torch.float32, what="nrm"),
+        _ptr(origin_ray, torch.int32, what="origin_ray"), _ptr(n_bins, torch.int32, 1, "n_bins"), bin_cap,
+        C.byref(p), _ptr(pdf, torch.float32, bin_cap * N * N), _ptr(cr, torch.float32, bin_cap * N * N),
+        _ptr(cm, torch.float32, bin_cap * N), _stream(stream)))
+    return pdf, cr, cm
+
+
+def guide_learned_train_step(mlp: MLP, pos, nrm, target, *, lo=(0, 0, 0), size=1.0, lr=1e-3, beta1=0.9,
+                             beta2=0.999, eps=1e-8, update=True, want_grad=False, loss=None, grad=None,
+                             stream=None):
+    """One online training step; returns (loss tensor [1], grad tensor or None)."""
+    n = pos.shape[0]
+    dev = pos.device
+    if loss is None:
+        loss = torch.zeros(1, dtype=torch.float32, device=dev)
+    if want_grad and grad is None:
+        grad = torch.zeros(MLP_PARAMS, dtype=torch.float32, device=dev)
+    p = _learned(lo, size, 0.0)
+    o = AdamParams(lr=lr, beta1=beta1, beta2=beta2, eps=eps, update=int(update))
+    _check(_declare_mlp().guide_learned_train_step(
+        mlp.handle, _ptr(pos, torch.float32, 3 * n, "pos"), _ptr(nrm, torch.float32, 3 * n, "nrm"), n,
+        _ptr(target, torch.float32, n * 1024, "target"), C.byref(p), C.byref(o),
+        _ptr(loss, torch.float32, 1), _ptr(grad, torch.float32, MLP_PARAMS) if want_grad else None,
+        _stream(stream)))
+    return loss, (grad if want_grad else None)
