@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-bins", type=int, default=64, help="bins in the oracle's timed sample")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-proposal section")
+    ap.add_argument("--learned-steps", type=int, default=150, help="online training steps (65,536 bins each)")
+    ap.add_argument("--learned-frames", type=int, default=16, help="frames of the equal-spp comparison")
     return ap.parse_args()
 
 
@@ -375,6 +378,8 @@ def run_gpu(args, world, rank, local):
                      "algorithmic_model": alg["model"]},
         "clocks": clk,
     }
+    if not args.no_learned:
+        line["learned"] = learned_section(args, w, svo)
     if not args.no_cpu_baseline:
         t_frame, detail = oracle_frame_time(w, mis, args.cpu_bins)
         line["cpu_baseline"] = {
@@ -382,6 +387,28 @@ def run_gpu(args, world, rank, local):
             "sample": f"one frame: full accumulate + binning, fields for {detail['bins']} of {B} "
                       f"bins and sampling/eval of their {detail['rays']} rays, scaled to the frame"}
     print(json.dumps(line))
+
+
+def learned_section(args, w, svo):
+    """Learned proposal vs the SVO-traced field on the same frame: online
+    training (65,536 traced bins per step), held-out KL, and per-pixel variance
+    of guided two-bounce estimates at equal samples per pixel."""
+    import torch
+    from paper_2405_06997_gb300 import learned as LG
+    tr = LG.OnlineTrainer(svo, w.scene, batch=65536, pool=1 << 20, lr=1e-3, seed=w.seed)
+    kl0 = tr.heldout_kl()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    tr.train(args.learned_steps)
+    train_s = time.perf_counter() - t0
+    kl1 = tr.heldout_kl()
+    floor = LG.traced_frame_kl(tr)
+    tau = 1.5 * floor
+    cmp = LG.compare_proposals(w, svo, tr.mlp, frames=args.learned_frames, alpha=0.5, seed=w.seed)
+    return {"train_steps": args.learned_steps, "train_batch_bins": 65536, "train_seconds": train_s,
+            "heldout_kl_untrained": kl0, "heldout_kl_trained": kl1, "traced_frame_to_frame_kl": floor,
+            "fallback_threshold": tau, "uses_learned": LG.use_learned(kl1, tau),
+            "equal_spp": cmp, "mlp_status": tr.mlp.status()}
 
 
 def trace_algorithmic_bytes(w, B, N, sample_bins=8):

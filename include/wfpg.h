@@ -330,6 +330,16 @@ WFPG_API int guide_learned_train_step(wfpg_mlp* mlp, const float* pos, const flo
                                       void* stream);
 
 /* -------------------------------------------------------------------------
+ * Measurement helper (renderer side; not part of the paper's method): the
+ * closest hit of n rays (o + t d, t > tmin) against the scene's quads and
+ * spheres.  t_out[i] = hit distance (-1 on a miss), prim_out[i] = primitive
+ * (quads first, then spheres; 0xFFFFFFFF on a miss), nrm_out (xyz, may be
+ * NULL) = geometric normal facing the ray.
+ */
+WFPG_API int wfpg_cast_rays(const wfpg_scene* scene, const float* o, const float* d, uint32_t n,
+                            float tmin, float* t_out, uint32_t* prim_out, float* nrm_out, void* stream);
+
+/* -------------------------------------------------------------------------
  * Inspection (used by tests; each synchronises `stream`).  Host buffers are
  * sized from svo_get_info: n_nodes entries (x2 for per-side arrays, x3 for
  * normals), n_frags fragment primitive ids, leaves + 1 fragment offsets.

@@ -374,12 +374,14 @@ def camera_hits(scene: Scene, eye=(0.5, 0.5, -1.0), width=1920, height=1080, vfo
 
 
 def one_bounce_records(scene: Scene, pos, nrm, prim, view_dir, seed: int):
-    """One radiance record per primary hit from one bounce of a Lambertian path
-    tracer: a cosine-sampled bounce that reaches an emitter carries
-    L = albedo(p1) * Le(p2) back to p1 (the local estimate of the radiance
-    leaving p1 toward the camera); an emissive p1 adds its own Le.  Only the
-    emissive primitives are tested first; rays that reach one are then checked
-    for occluders."""
+    """Radiance records from one bounce of a Lambertian path tracer (Eq. 5 of
+    the paper back-propagates an emitter's radiance to every vertex of the
+    path): one record per primary hit p1, L = albedo(p1) * Le(p2) + Le(p1)
+    when the cosine-sampled bounce reaches an emitter p2 (else Le(p1)),
+    leaving toward the camera; plus one record at every emitter vertex p2
+    that a bounce reached, L = Le(p2), leaving toward p1.  Only the emissive
+    primitives are tested first; rays that reach one are then checked for
+    occluders."""
     rng = np.random.default_rng(seed)
     d2 = cosine_dirs(nrm, rng)
     o2 = pos.astype(np.float64) + 1e-4 * nrm.astype(np.float64)
@@ -403,7 +405,12 @@ def one_bounce_records(scene: Scene, pos, nrm, prim, view_dir, seed: int):
     le2 = np.where(P >= 0, scene.emission[np.maximum(P, 0)], 0.0)
     L = scene.albedo[prim] * le2 + scene.emission[prim]
     wout = -view_dir.astype(np.float64)
-    return pos.astype(np.float32), wout.astype(np.float32), L.astype(np.float32)
+    hit_e = np.flatnonzero(le2 > 0)
+    p2 = o2[hit_e] + T[hit_e, None] * d2[hit_e]
+    rec_pos = np.concatenate([pos.astype(np.float64), p2]).astype(np.float32)
+    rec_w = np.concatenate([wout, -d2[hit_e]]).astype(np.float32)
+    rec_L = np.concatenate([L, le2[hit_e]]).astype(np.float32)
+    return rec_pos, rec_w, rec_L
 
 
 def zipf_bin_sizes(n_rays: int, n_bins: int, s: float, seed: int) -> np.ndarray:
@@ -453,6 +460,7 @@ class Workload:
     jitter: bool = False
     seed: int = 1
     desc: str = ""
+    extra: dict = field(default_factory=dict)
 
 
 def tiny_box(seed: int = 1, n_records: int = 100_000, n_rays: int = 4096) -> Workload:
@@ -483,7 +491,7 @@ def frame_spheres(seed: int = 1, width=1920, height=1080, n_bins=2048, depth=9,
     sizes = zipf_bin_sizes(len(pos), n_bins, 1.2, seed * 1000 + 4)
     return Workload(scene=sc, depth=depth, rec_pos=rp, rec_wout=rw, rec_L=rl, ray_pos=pos,
                     ray_nrm=nrm, u=u, grid_n=grid_n, bin_mode=1, bin_sizes=sizes,
-                    n_bins_max=n_bins, blur=True, jitter=True, seed=seed,
+                    n_bins_max=n_bins, blur=True, jitter=True, seed=seed, extra={"ray_prim": prim},
                     desc=f"cornell+200 spheres D={depth}, {width}x{height} primary hits, "
                          f"{n_bins} Zipf(1.2) bins, {grid_n}x{grid_n}")
 

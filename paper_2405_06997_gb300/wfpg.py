@@ -481,3 +481,25 @@ def guide_learned_train_step(mlp: MLP, pos, nrm, target, *, lo=(0, 0, 0), size=1
         _ptr(loss, torch.float32, 1), _ptr(grad, torch.float32, MLP_PARAMS) if want_grad else None,
         _stream(stream)))
     return loss, (grad if want_grad else None)
+
+
+def cast_rays(quads, spheres, o, d, tmin=1e-5, with_normal=True, stream=None):
+    """Closest hits of rays (o + t d) against a scene's quads / spheres (CUDA
+    tensors); returns (t [-1 on miss], prim [int32, -1 on miss], nrm or None)."""
+    L = lib()
+    fn = L.wfpg_cast_rays
+    fn.restype = I32
+    fn.argtypes = [P, P, P, U32, F, P, P, P, P]
+    n = o.shape[0]
+    sc = Scene()
+    sc.quads = _ptr(quads, torch.float32) if quads.numel() else None
+    sc.n_quads = quads.shape[0] if quads.numel() else 0
+    sc.spheres = _ptr(spheres, torch.float32) if spheres.numel() else None
+    sc.n_spheres = spheres.shape[0] if spheres.numel() else 0
+    t = torch.empty(n, dtype=torch.float32, device=o.device)
+    prim = torch.empty(n, dtype=torch.int32, device=o.device)
+    nrm = torch.empty((n, 3), dtype=torch.float32, device=o.device) if with_normal else None
+    _check(fn(C.byref(sc), _ptr(o, torch.float32, 3 * n), _ptr(d, torch.float32, 3 * n), n, float(tmin),
+              _ptr(t, torch.float32), _ptr(prim, torch.int32), _ptr(nrm, torch.float32) if with_normal else None,
+              _stream(stream)))
+    return t, prim, nrm
