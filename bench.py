@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-bins", type=int, default=64, help="bins in the oracle's timed sample")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-proposal section")
-    ap.add_argument("--learned-steps", type=int, default=150, help="online training steps (65,536 bins each)")
+    ap.add_argument("--learned-steps", type=int, default=500, help="online training steps (65,536 bins each)")
     ap.add_argument("--learned-frames", type=int, default=16, help="frames of the equal-spp comparison")
     return ap.parse_args()
 

@@ -125,7 +125,8 @@ def _cosine_dirs(nrm, u):
     return t * (r * torch.cos(phi)).unsqueeze(1) + b * (r * torch.sin(phi)).unsqueeze(1) + n * z.unsqueeze(1)
 
 
-def guided_estimates(w, svo, proposal, *, frames=16, alpha=0.5, mlp=None, seed=1, device="cuda"):
+def guided_estimates(w, svo, proposal, *, frames=16, alpha=0.5, mlp=None, seed=1, device="cuda", l_min=4,
+                     c_ray=512):
     """Per-pixel estimates of the light leaving each primary hit toward the
     camera, one path per pixel per frame, two bounces deep: the first bounce
     direction w1 is drawn from alpha * guided + (1 - alpha) * cosine and
@@ -133,8 +134,10 @@ def guided_estimates(w, svo, proposal, *, frames=16, alpha=0.5, mlp=None, seed=1
     second bounce is cosine-sampled.
         L = (albedo1 / pi) cos1 / p(w1) * (Le(x2) + albedo2 * Le(x3))
     proposal: 'svo' (traced field), 'learned' (MLP) or 'bsdf' (cosine only).
-    Returns the per-pixel mean and variance over frames and the guiding time
-    per frame (binning + field/PDF + sampling + MIS density), in seconds."""
+    Rays are binned with Partition-S (l_min, c_ray; the paper's Table 1 uses
+    c_ray = 512 and its l_min 5, i.e. 4 here).  Returns the per-pixel mean and
+    variance over frames and the guiding time per frame (binning + field/PDF +
+    sampling + MIS density), in seconds."""
     q = _dev(w.scene.quads, device)
     sp = _dev(w.scene.spheres, device)
     emission = _dev(w.scene.emission, device)
@@ -142,9 +145,8 @@ def guided_estimates(w, svo, proposal, *, frames=16, alpha=0.5, mlp=None, seed=1
     albedo = _dev(w.scene.albedo[w.extra["ray_prim"]], device)
     pos = _dev(w.ray_pos, device)
     nrm = _dev(w.ray_nrm, device)
-    sizes = _dev(w.bin_sizes.view(np.int32), device)
     R = pos.shape[0]
-    B = len(w.bin_sizes)
+    B = 16384  # bin capacity; Partition-S at c_ray = 512 gives a few thousand bins at 1080p
     s1 = torch.zeros(R, dtype=torch.float64, device=device)
     s2 = torch.zeros(R, dtype=torch.float64, device=device)
     guide = None
@@ -157,7 +159,7 @@ def guided_estimates(w, svo, proposal, *, frames=16, alpha=0.5, mlp=None, seed=1
         if a > 0:
             e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
             e[0].record()
-            r = W.bin_rays(svo, pos, nrm, mode=W.BIN_RUNS, sizes=sizes, seed=seed, frame=f, bin_cap=B)
+            r = W.bin_rays(svo, pos, l_min=l_min, c_ray=c_ray, seed=seed, frame=f, bin_cap=B)
             if proposal == "svo":
                 guide = W.guide_build_pdf(svo, pos, r["origin_ray"], r["n_bins"], B, N=32, jitter=True, blur=True,
                                           seed=seed, frame=f, out=guide)
