@@ -140,6 +140,7 @@ typedef struct wfpg_bin_params {
     uint32_t n_sizes;  /* RUNS: number of runs (= bins) */
     uint64_t seed;     /* SelectOrigin random stream */
     uint32_t frame;    /* SelectOrigin random stream */
+    const uint32_t* n_dev; /* optional DEVICE count of valid rays (the first *n_dev of the n); NULL: all n */
 } wfpg_bin_params;
 
 /*
@@ -241,6 +242,29 @@ WFPG_API int guide_build_pdf(const wfpg_svo* svo, const float* pos, const uint32
                     float* pdf, float* cdf_row, float* cdf_marg, void* stream);
 
 /*
+ * guide_build_sample -- GuideRays as Alg. 3 states it: the field, its PDF
+ * and CDFs live in shared memory only, and the bin's own rays sample from them
+ * (guided density or BSDF, MIS) before the CTA moves on; nothing per bin is
+ * written to global memory.  One persistent launch over all bins.
+ * After bin b's CDF is built, every ray r of the bin (ray_order[bin_offset[b]
+ * .. bin_offset[b+1]), as bin_rays writes them) takes u[r] = (u0, u1, u2):
+ * if u2 < alpha it samples the field exactly as guide_sample does with
+ * (u0, u1), else a cosine-distributed direction about the unit normal nrm[r]
+ * (Malley's method on the orthonormal frame of Duff et al. 2017).  dir[r]
+ * (xyz) gets the direction, pdf_out[r] the one-sample mixture density
+ * alpha * field density + (1 - alpha) * max(0, cos) / pi there (the field
+ * density of a cosine sample is its cell's, as guide_eval_pdf gives).
+ * pos, nrm, u: device, [n][3]; bins as bin_rays writes them; alpha in [0, 1].
+ * Rays of bins >= min(*n_bins_dev, bin_cap) are not written.  Errors: invalid
+ * N / eps / alpha / block, or a null array, give WFPG_ERR_INVALID_ARG.
+ */
+WFPG_API int guide_build_sample(const wfpg_svo* svo, const float* pos, const float* nrm,
+                                const uint32_t* origin_ray, const uint32_t* n_bins_dev, uint32_t bin_cap,
+                                const uint32_t* ray_order, const uint32_t* bin_offset, const float* u,
+                                float alpha, const wfpg_guide_params* p, float* dir, float* pdf_out,
+                                void* stream);
+
+/*
  * guide_sample -- the guided branch of Alg. 3's sampling step: inverse-CDF
  * sampling of the piecewise-constant density.  Per ray: t0 = u0 * T; the row
  * is the first marginal entry > t0 (N-1 if none); t1 = u1 * T_row; the
@@ -328,6 +352,112 @@ WFPG_API int guide_learned_train_step(wfpg_mlp* mlp, const float* pos, const flo
                                       const float* target, const wfpg_learned_params* p,
                                       const wfpg_adam_params* opt, float* loss_out, float* grad_out,
                                       void* stream);
+
+/* -------------------------------------------------------------------------
+ * Batched wavefront frame (a project addition; the paper launches every stage
+ * of every depth from the host).  One frame is Alg. 1 for every pixel of a
+ * pinhole camera, run entirely on the device:
+ *   camera rays -> closest hits -> for each depth i = 1 .. max_depth:
+ *     Partition-S (Alg. 2) of the live paths -> GuideRays (Alg. 3, fused:
+ *     field + PDF/CDF in shared memory, then the bin's rays draw their next
+ *     direction from alpha * guided + (1 - alpha) * cosine, exact density) ->
+ *     Lambertian BSDF weight, closest hit, emission, Russian roulette from
+ *     vertex rr_depth on (survival min(0.95, albedo)), order-preserving
+ *     compaction of the survivors;
+ *   then UpdateExitance: every vertex of every path gives one radiance
+ *   record by Eq. 5 (zero when no emitter follows it), and svo_accumulate
+ *   adds them and re-averages the tree.
+ * Ray counts live in device memory between the stages, so the frame has no
+ * host round trip and is replayed as one captured CUDA graph.  A frame index
+ * in device memory advances after each frame and keys every random stream
+ * (bins' origins, cell jitter, per-path uniforms: SplitMix64 counters).
+ * The emitted radiance and albedo of a hit come from per-primitive device
+ * arrays (quads first, then spheres); a primitive with albedo 0 ends a path.
+ * Per-pixel sums of the path estimate and of its square accumulate over
+ * frames (frame_image gives mean and variance of the mean).
+ */
+#define WFPG_FRAME_MAX_DEPTH 8
+
+typedef struct wfpg_camera {
+    float eye[3];
+    float forward[3];   /* unit view direction */
+    float up[3];        /* unit, orthogonal to forward */
+    float vfov_deg;     /* vertical field of view */
+    uint32_t width, height;
+} wfpg_camera;
+
+typedef struct wfpg_frame_params {
+    int max_depth;            /* guided bounces per path, 1 .. WFPG_FRAME_MAX_DEPTH */
+    int rr_depth;             /* Russian roulette at vertices >= rr_depth (1 = first hit) */
+    float alpha;              /* guided share of the one-sample mixture, [0, 1] */
+    int l_min;                /* Partition-S */
+    uint32_t c_ray;
+    wfpg_guide_params guide;  /* N, eps, jitter, blur, t_skip, cos_weight, block, stage (seed/frame unused) */
+    uint64_t seed;
+    int update;               /* 1: UpdateExitance after each frame */
+} wfpg_frame_params;
+
+typedef struct wfpg_frame wfpg_frame;
+
+typedef struct wfpg_frame_stats {
+    uint64_t frames;                                /* frames run since create / reset_image */
+    uint32_t paths[WFPG_FRAME_MAX_DEPTH + 1];       /* live paths guided at depth i (last frame) */
+    uint32_t bins[WFPG_FRAME_MAX_DEPTH + 1];        /* Partition-S bins at depth i (last frame) */
+    uint32_t records;                               /* Eq. 5 records of the last frame */
+    uint64_t guided_samples;                        /* sum of paths[] over all frames run */
+    uint32_t status;                                /* the SVO's status bits */
+    unsigned long long kernels_per_frame;           /* kernels in one captured frame */
+} wfpg_frame_stats;
+
+/* Creates a frame over an existing SVO (not owned; it must outlive the frame)
+ * and scene (device pointers, not owned).  emission, albedo: device float
+ * arrays, one per primitive.  Allocates the path state (about
+ * 4 * W * H * (12 * (max_depth + 1) + 48) bytes).  Synchronises `stream`. */
+WFPG_API int frame_create(wfpg_svo* svo, const wfpg_scene* scene, const float* emission, const float* albedo,
+                          const wfpg_camera* cam, const wfpg_frame_params* p, wfpg_frame** out, void* stream);
+WFPG_API int frame_destroy(wfpg_frame* f);
+/* Runs n_frames frames on `stream` (asynchronous).  use_graph != 0 replays a
+ * captured CUDA graph (captured on first use after create / set_params). */
+WFPG_API int frame_run(wfpg_frame* f, uint32_t n_frames, int use_graph, void* stream);
+/* Replaces the parameters (same max_depth or smaller; drops the graph). */
+WFPG_API int frame_set_params(wfpg_frame* f, const wfpg_frame_params* p);
+WFPG_API int frame_get_params(const wfpg_frame* f, wfpg_frame_params* p);
+/* Zeroes the per-pixel sums and the frame count. */
+WFPG_API int frame_reset_image(wfpg_frame* f, void* stream);
+/* mean[W*H] and var[W*H] (device, may be NULL): per-pixel mean of the path
+ * estimates over the frames run and the variance of one estimate (unbiased,
+ * 0 when fewer than 2 frames). */
+WFPG_API int frame_image(wfpg_frame* f, float* mean, float* var, void* stream);
+/* Synchronises `stream` and reads the last frame's counts. */
+WFPG_API int frame_stats(wfpg_frame* f, wfpg_frame_stats* out, void* stream);
+/* Picks the grid side N among n_N candidates and the field kernel's tile
+ * (block 64/128/256, staged or not): per N the fastest tile by frame time,
+ * then the N with the least (mean per-pixel variance x frame time) over
+ * `frames` frames.  The trial frames update the SVO as ordinary frames do.
+ * Writes the choice into *chosen and applies it; resets the image. */
+WFPG_API int frame_autotune(wfpg_frame* f, const int* N_candidates, int n_N, uint32_t frames,
+                            wfpg_frame_params* chosen, float* ms_per_frame, void* stream);
+
+/* Copies of internal buffers for inspection (tests): `what` selects one of
+ * the WFPG_FRAME_BUF_* arrays; `bytes` must equal its size. */
+enum {
+    WFPG_FRAME_BUF_VT = 0,      /* float [max_depth+1][W*H]: throughput T(p_k) of vertex k */
+    WFPG_FRAME_BUF_VLE = 1,     /* float [max_depth+1][W*H]: emitted radiance at vertex k */
+    WFPG_FRAME_BUF_VPOS = 2,    /* float [max_depth+1][W*H][3] */
+    WFPG_FRAME_BUF_VWO = 3,     /* float [max_depth+1][W*H][3]: unit direction toward the previous vertex */
+    WFPG_FRAME_BUF_NV = 4,      /* u32 [W*H]: vertices of each path */
+    WFPG_FRAME_BUF_REC_POS = 5, /* float [(max_depth+1)*W*H][3]; first `records` entries valid */
+    WFPG_FRAME_BUF_REC_WOUT = 6,
+    WFPG_FRAME_BUF_REC_L = 7,   /* float [(max_depth+1)*W*H] */
+    WFPG_FRAME_BUF_REC_SRC = 8, /* u32 [(max_depth+1)*W*H]: k * W*H + path of each record */
+    WFPG_FRAME_BUF_Q_POS = 9,   /* float [W*H][3]: positions of the last guided depth's queue */
+    WFPG_FRAME_BUF_Q_NRM = 10,
+    WFPG_FRAME_BUF_Q_U = 11,    /* float [W*H][3]: its uniforms */
+    WFPG_FRAME_BUF_Q_DIR = 12,  /* float [W*H][3]: its sampled directions */
+    WFPG_FRAME_BUF_Q_PDF = 13,  /* float [W*H]: their mixture densities */
+    WFPG_FRAME_BUF_Q_PATH = 14, /* u32 [W*H]: path (pixel) of each queue slot */
+};
+WFPG_API int frame_export(const wfpg_frame* f, int what, void* dst, size_t bytes, void* stream);
 
 /* -------------------------------------------------------------------------
  * Measurement helper (renderer side; not part of the paper's method): the

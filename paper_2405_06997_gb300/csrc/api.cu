@@ -12,15 +12,20 @@
 
 namespace wfpg {
 int build_svo(const wfpg_scene* scene, int D, cudaStream_t st, wfpg_svo* s, std::string& err);
-int accumulate(wfpg_svo* s, const float* pos, const float* wout, const float* L, uint32_t n, cudaStream_t st);
+int accumulate(wfpg_svo* s, const float* pos, const float* wout, const float* L, uint32_t n, cudaStream_t st,
+               const uint32_t* n_dev = nullptr);
 size_t bin_workspace_bytes(const wfpg_svo* s, uint32_t n, int mode, uint32_t n_sizes);
 int bin_rays_impl(const wfpg_svo* s, const float* pos, const float* nrm, uint32_t n, const wfpg_bin_params* p,
                   const uint32_t* sizes, uint32_t* bin_of_ray, uint32_t* ray_order, uint32_t* bin_offset,
                   uint32_t* origin_ray, uint32_t bin_cap, uint32_t* n_bins_dev, void* workspace, size_t ws_bytes,
-                  cudaStream_t st);
+                  cudaStream_t st, const uint32_t* frame_dev = nullptr);
 int guide_build_impl(const wfpg_svo* s, const float* pos, const uint32_t* origin_ray, const uint32_t* n_bins_dev,
                      uint32_t bin_cap, const wfpg_guide_params* p, float* pdf, float* cdf_row, float* cdf_marg,
-                     cudaStream_t st);
+                     cudaStream_t st, const uint32_t* frame_dev = nullptr);
+int guide_fused_impl(const wfpg_svo* s, const float* pos, const float* nrm, const uint32_t* origin_ray,
+                     const uint32_t* n_bins_dev, uint32_t bin_cap, const uint32_t* ray_order,
+                     const uint32_t* bin_offset, const float* u, float alpha, const wfpg_guide_params* p, float* dir,
+                     float* pdf_out, cudaStream_t st, const uint32_t* frame_dev = nullptr);
 int guide_sample_impl(const float* pdf, const float* cdf_row, const float* cdf_marg, int N, uint32_t bin_cap,
                       const uint32_t* bin_of_ray, const float* u, uint32_t n, float* dir, float* pdf_out,
                       uint32_t* cell, cudaStream_t st);
@@ -33,6 +38,7 @@ using namespace wfpg;
 namespace wfpg {
 static std::atomic<unsigned long long> g_launches{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void note_launches(long long n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
 }  // namespace wfpg
 
 namespace {
@@ -181,6 +187,26 @@ int guide_build_pdf(const wfpg_svo* s, const float* pos, const uint32_t* origin_
         return fail(rc, "guide_build_pdf: the field of side " + std::to_string(p->N) +
                             " does not fit in shared memory with this block size");
     if (rc != WFPG_OK) return cuda_fail("guide_build_pdf");
+    return WFPG_OK;
+}
+
+int guide_build_sample(const wfpg_svo* s, const float* pos, const float* nrm, const uint32_t* origin_ray,
+                       const uint32_t* n_bins_dev, uint32_t bin_cap, const uint32_t* ray_order,
+                       const uint32_t* bin_offset, const float* u, float alpha, const wfpg_guide_params* p, float* dir,
+                       float* pdf_out, void* stream) {
+    if (!s || !p) return fail(WFPG_ERR_INVALID_ARG, "guide_build_sample: null svo or params");
+    if (!valid_n(p->N)) return fail(WFPG_ERR_INVALID_ARG, "guide_build_sample: N must be 8, 16, 32, 64 or 128");
+    if (!(p->eps >= 0.0f)) return fail(WFPG_ERR_INVALID_ARG, "guide_build_sample: eps must be >= 0");
+    if (!(alpha >= 0.0f && alpha <= 1.0f)) return fail(WFPG_ERR_INVALID_ARG, "guide_build_sample: alpha in [0, 1]");
+    if (p->block != 0 && p->block != 64 && p->block != 128 && p->block != 256)
+        return fail(WFPG_ERR_INVALID_ARG, "guide_build_sample: block must be 0, 64, 128 or 256");
+    if (bin_cap && (!pos || !nrm || !ray_order || !bin_offset || !u || !dir || !pdf_out))
+        return fail(WFPG_ERR_INVALID_ARG, "guide_build_sample: null array");
+    const int rc = guide_fused_impl(s, pos, nrm, origin_ray, n_bins_dev, bin_cap, ray_order, bin_offset, u, alpha, p,
+                                    dir, pdf_out, as_stream(stream));
+    if (rc == WFPG_ERR_INVALID_ARG)
+        return fail(rc, "guide_build_sample: the field does not fit in shared memory with this block size");
+    if (rc != WFPG_OK) return cuda_fail("guide_build_sample");
     return WFPG_OK;
 }
 

@@ -16,12 +16,18 @@ __device__ __forceinline__ int level_of(const LevelOffsets& L, int D, uint32_t n
     return l;
 }
 
+// number of valid rays: the device count when given (at most the capacity n)
+__device__ __forceinline__ uint32_t ray_count(uint32_t n, const uint32_t* n_dev) {
+    return n_dev ? min(*n_dev, n) : n;
+}
+
 // DescendLeaf + AtomicAdd: each ray counts at the deepest node holding it
 __global__ void __launch_bounds__(256) k_bin_descend(const Node* __restrict__ nodes, int D, float lox, float loy,
                                                      float loz, float scale, const float* __restrict__ pos, uint32_t n,
-                                                     uint32_t* __restrict__ ray_node, uint32_t* __restrict__ count) {
+                                                     const uint32_t* __restrict__ n_dev, uint32_t* __restrict__ ray_node,
+                                                     uint32_t* __restrict__ count) {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    if (i >= ray_count(n, n_dev)) return;
     int c[3];
     c[0] = grid_index(pos[3 * (size_t)i + 0], lox, scale, D);
     c[1] = grid_index(pos[3 * (size_t)i + 1], loy, scale, D);
@@ -50,11 +56,12 @@ __global__ void k_bin_level(uint32_t off, uint32_t n, int is_leaf_level, int is_
 }
 
 // AscendAndFindMarked
-__global__ void __launch_bounds__(256) k_bin_ascend(uint32_t* __restrict__ ray_node, uint32_t n, LevelOffsets L, int D,
+__global__ void __launch_bounds__(256) k_bin_ascend(uint32_t* __restrict__ ray_node, uint32_t n,
+                                                    const uint32_t* __restrict__ n_dev, LevelOffsets L, int D,
                                                     int l_min, const uint32_t* __restrict__ parent,
                                                     const uint32_t* __restrict__ total, uint32_t* __restrict__ used) {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    if (i >= ray_count(n, n_dev)) return;
     uint32_t nd = ray_node[i];
     if (level_of(L, D, nd) >= l_min) {
         while (!(total[nd] >> 31)) nd = parent[nd];
@@ -63,23 +70,32 @@ __global__ void __launch_bounds__(256) k_bin_ascend(uint32_t* __restrict__ ray_n
     used[nd] = 1u;
 }
 
+// rays past the device count get the largest key, so a stable sort leaves
+// them after every valid ray
 __global__ void __launch_bounds__(256) k_bin_ids(const uint32_t* __restrict__ bin_node, uint32_t n,
+                                                 const uint32_t* __restrict__ n_dev,
                                                  const uint32_t* __restrict__ rank, uint32_t* __restrict__ bin_of_ray,
                                                  uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    vals[i] = i;
+    if (i >= ray_count(n, n_dev)) {
+        keys[i] = 0xffffffffu;
+        return;
+    }
     const uint32_t b = rank[bin_node[i]];
     bin_of_ray[i] = b;
     keys[i] = b;
-    vals[i] = i;
 }
 
 // bin_offset[b] = first sorted position of bin b; bin_offset[n_bins] = n
-__global__ void __launch_bounds__(256) k_bin_offsets(const uint32_t* __restrict__ sorted_bins, uint32_t n,
+__global__ void __launch_bounds__(256) k_bin_offsets(const uint32_t* __restrict__ sorted_bins, uint32_t n_cap,
+                                                     const uint32_t* __restrict__ n_dev,
                                                      uint32_t* __restrict__ bin_offset, uint32_t bin_cap,
                                                      const uint32_t* __restrict__ n_bins_dev,
                                                      uint32_t* __restrict__ status) {
     const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t n = ray_count(n_cap, n_dev);
     if (p == 0) {
         const uint32_t nb = *n_bins_dev;
         if (nb <= bin_cap) bin_offset[nb] = n;
@@ -92,9 +108,13 @@ __global__ void __launch_bounds__(256) k_bin_offsets(const uint32_t* __restrict_
 
 // SelectOrigin: bin b takes position floor(u24 * size / 2^24) of its run
 __global__ void k_bin_origins(const uint32_t* __restrict__ bin_offset, const uint32_t* __restrict__ ray_order,
-                              uint32_t n, const uint32_t* __restrict__ n_bins_dev, uint32_t bin_cap, uint64_t seed,
-                              uint32_t frame, uint32_t* __restrict__ origin_ray) {
+                              uint32_t n_cap, const uint32_t* __restrict__ n_dev,
+                              const uint32_t* __restrict__ n_bins_dev, uint32_t bin_cap, uint64_t seed,
+                              uint32_t frame_arg, const uint32_t* __restrict__ frame_dev,
+                              uint32_t* __restrict__ origin_ray) {
     const uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t n = ray_count(n_cap, n_dev);
+    const uint32_t frame = frame_dev ? *frame_dev : frame_arg;
     const uint32_t nb = min(*n_bins_dev, bin_cap);
     if (b >= nb) return;
     const uint32_t lo = bin_offset[b], hi = bin_offset[b + 1];
@@ -110,10 +130,16 @@ __global__ void k_bin_origins(const uint32_t* __restrict__ bin_offset, const uin
 
 // ---------------------------------------------------------------- runs mode
 __global__ void __launch_bounds__(256) k_runs_keys(const float* __restrict__ pos, const float* __restrict__ nrm,
-                                                   uint32_t n, float lox, float loy, float loz, float scale, int D,
-                                                   uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+                                                   uint32_t n, const uint32_t* __restrict__ n_dev, float lox, float loy,
+                                                   float loz, float scale, int D, uint32_t* __restrict__ keys,
+                                                   uint32_t* __restrict__ vals) {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    vals[i] = i;
+    if (i >= ray_count(n, n_dev)) {
+        keys[i] = 0xffffffffu;
+        return;
+    }
     const int q = D < 6 ? D : 6;
     const uint32_t cx = (uint32_t)grid_index(pos[3 * (size_t)i + 0], lox, scale, D) >> (D - q);
     const uint32_t cy = (uint32_t)grid_index(pos[3 * (size_t)i + 1], loy, scale, D) >> (D - q);
@@ -121,13 +147,13 @@ __global__ void __launch_bounds__(256) k_runs_keys(const float* __restrict__ pos
     const uint32_t oct = (nrm[3 * (size_t)i + 0] < 0.0f ? 1u : 0u) | (nrm[3 * (size_t)i + 1] < 0.0f ? 2u : 0u) |
                          (nrm[3 * (size_t)i + 2] < 0.0f ? 4u : 0u);
     keys[i] = (uint32_t)(morton3(cx, cy, cz) << 3) | oct;
-    vals[i] = i;
 }
 
 __global__ void k_runs_check(const uint32_t* __restrict__ sizes, uint32_t nb, const uint32_t* __restrict__ total,
-                             uint32_t n, uint32_t* __restrict__ bin_offset, uint32_t* __restrict__ n_bins_dev,
-                             uint32_t* __restrict__ status) {
+                             uint32_t n_cap, const uint32_t* __restrict__ n_dev, uint32_t* __restrict__ bin_offset,
+                             uint32_t* __restrict__ n_bins_dev, uint32_t* __restrict__ status) {
     const uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t n = ray_count(n_cap, n_dev);
     if (b == 0) {
         bin_offset[nb] = *total;
         *n_bins_dev = nb;
@@ -137,9 +163,11 @@ __global__ void k_runs_check(const uint32_t* __restrict__ sizes, uint32_t nb, co
 }
 
 __global__ void __launch_bounds__(256) k_runs_bins(const uint32_t* __restrict__ bin_offset, uint32_t nb,
-                                                   const uint32_t* __restrict__ ray_order, uint32_t n,
+                                                   const uint32_t* __restrict__ ray_order, uint32_t n_cap,
+                                                   const uint32_t* __restrict__ n_dev,
                                                    uint32_t* __restrict__ bin_of_ray) {
     const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t n = ray_count(n_cap, n_dev);
     if (p >= n) return;
     uint32_t lo = 0, hi = nb;  // last b with bin_offset[b] <= p
     while (hi - lo > 1) {
@@ -175,7 +203,8 @@ size_t bin_workspace_bytes(const wfpg_svo* s, uint32_t n, int mode, uint32_t n_s
 int bin_rays_impl(const wfpg_svo* s, const float* pos, const float* nrm, uint32_t n, const wfpg_bin_params* p,
                   const uint32_t* sizes, uint32_t* bin_of_ray, uint32_t* ray_order, uint32_t* bin_offset,
                   uint32_t* origin_ray, uint32_t bin_cap, uint32_t* n_bins_dev, void* workspace, size_t ws_bytes,
-                  cudaStream_t st) {
+                  cudaStream_t st, const uint32_t* frame_dev) {
+    const uint32_t* nd = p->n_dev;  // optional device count of valid rays (<= n)
     const int T = 256;
     const int D = s->D;
     Arena ws{static_cast<char*>(workspace), ws_bytes, 0, false};
@@ -197,7 +226,7 @@ int bin_rays_impl(const wfpg_svo* s, const float* pos, const float* nrm, uint32_
         cudaMemsetAsync(used, 0, 4 * (size_t)s->n_nodes, st);
         if (n > 0)
             WFPG_LAUNCH(k_bin_descend, div_up(n, T), T, 0, st, s->node, D, s->lo[0], s->lo[1], s->lo[2], s->scale, pos, n,
-                                                      ray_node, count);
+                        nd, ray_node, count);
         for (int l = D; l >= l_min; --l) {
             const uint32_t cnt = s->level_off[l + 1] - s->level_off[l];
             WFPG_LAUNCH(k_bin_level, div_up(cnt, T), T, 0, st, s->level_off[l], cnt, l == D, l == l_min, p->c_ray, s->node,
@@ -206,35 +235,35 @@ int bin_rays_impl(const wfpg_svo* s, const float* pos, const float* nrm, uint32_
         LevelOffsets L;
         for (int l = 0; l < WFPG_MAX_DEPTH + 2; ++l) L.off[l] = s->level_off[l];
         if (n > 0)
-            WFPG_LAUNCH(k_bin_ascend, div_up(n, T), T, 0, st, ray_node, n, L, D, l_min, s->parent, total, used);
+            WFPG_LAUNCH(k_bin_ascend, div_up(n, T), T, 0, st, ray_node, n, nd, L, D, l_min, s->parent, total, used);
         scan_exclusive(used, used, s->n_nodes, n_bins_dev, ws, st);
         if (n > 0)
-            WFPG_LAUNCH(k_bin_ids, div_up(n, T), T, 0, st, ray_node, n, used, bin_of_ray, keys, vals);
+            WFPG_LAUNCH(k_bin_ids, div_up(n, T), T, 0, st, ray_node, n, nd, used, bin_of_ray, keys, vals);
         const uint64_t max_bins = n < s->n_nodes ? n : s->n_nodes;
         radix_sort_pairs_u32(keys, keys_alt, vals, vals_alt, n, bits_for(max_bins), ws, st, &skeys, &svals);
         if (n > 0 && svals != ray_order)
             cudaMemcpyAsync(ray_order, svals, 4 * (size_t)n, cudaMemcpyDeviceToDevice, st);
-        WFPG_LAUNCH(k_bin_offsets, div_up(n + 1, T), T, 0, st, skeys, n, bin_offset, bin_cap, n_bins_dev, s->status);
+        WFPG_LAUNCH(k_bin_offsets, div_up(n + 1, T), T, 0, st, skeys, n, nd, bin_offset, bin_cap, n_bins_dev, s->status);
     } else {
         if (p->n_sizes > bin_cap) return WFPG_ERR_CAPACITY;
         const int q = D < 6 ? D : 6;
         uint32_t* tot = ws.take<uint32_t>(1);
         if (ws.overflow) return WFPG_ERR_INVALID_ARG;
         if (n > 0)
-            WFPG_LAUNCH(k_runs_keys, div_up(n, T), T, 0, st, pos, nrm, n, s->lo[0], s->lo[1], s->lo[2], s->scale, D, keys,
-                                                    vals);
+            WFPG_LAUNCH(k_runs_keys, div_up(n, T), T, 0, st, pos, nrm, n, nd, s->lo[0], s->lo[1], s->lo[2], s->scale, D,
+                        keys, vals);
         radix_sort_pairs_u32(keys, keys_alt, vals, vals_alt, n, 3 * q + 3, ws, st, &skeys, &svals);
         if (n > 0 && svals != ray_order)
             cudaMemcpyAsync(ray_order, svals, 4 * (size_t)n, cudaMemcpyDeviceToDevice, st);
         scan_exclusive(sizes, bin_offset, p->n_sizes, tot, ws, st);
-        WFPG_LAUNCH(k_runs_check, div_up(p->n_sizes + 1, T), T, 0, st, sizes, p->n_sizes, tot, n, bin_offset, n_bins_dev,
-                                                             s->status);
+        WFPG_LAUNCH(k_runs_check, div_up(p->n_sizes + 1, T), T, 0, st, sizes, p->n_sizes, tot, n, nd, bin_offset,
+                    n_bins_dev, s->status);
         if (n > 0 && p->n_sizes > 0)
-            WFPG_LAUNCH(k_runs_bins, div_up(n, T), T, 0, st, bin_offset, p->n_sizes, ray_order, n, bin_of_ray);
+            WFPG_LAUNCH(k_runs_bins, div_up(n, T), T, 0, st, bin_offset, p->n_sizes, ray_order, n, nd, bin_of_ray);
     }
     if (bin_cap > 0)
-        WFPG_LAUNCH(k_bin_origins, div_up(bin_cap, T), T, 0, st, bin_offset, ray_order, n, n_bins_dev, bin_cap, p->seed,
-                                                        p->frame, origin_ray);
+        WFPG_LAUNCH(k_bin_origins, div_up(bin_cap, T), T, 0, st, bin_offset, ray_order, n, nd, n_bins_dev, bin_cap,
+                    p->seed, p->frame, frame_dev, origin_ray);
     return cudaGetLastError() == cudaSuccess ? WFPG_OK : WFPG_ERR_CUDA;
 }
 

@@ -20,7 +20,7 @@ size_t bin_workspace_bytes(const wfpg_svo* s, uint32_t n, int mode, uint32_t n_s
 int bin_rays_impl(const wfpg_svo* s, const float* pos, const float* nrm, uint32_t n, const wfpg_bin_params* p,
                   const uint32_t* sizes, uint32_t* bin_of_ray, uint32_t* ray_order, uint32_t* bin_offset,
                   uint32_t* origin_ray, uint32_t bin_cap, uint32_t* n_bins_dev, void* workspace, size_t ws_bytes,
-                  cudaStream_t st);
+                  cudaStream_t st, const uint32_t* frame_dev = nullptr);
 int set_last_error(int code, const std::string& msg);
 }  // namespace wfpg
 

@@ -19,10 +19,11 @@ struct AccArgs {  // the tree and the grid mapping the scatter needs
 
 __global__ void __launch_bounds__(256) k_accumulate(AccArgs A, const float* __restrict__ pos,
                                                     const float* __restrict__ wout, const float* __restrict__ L,
-                                                    uint32_t n, unsigned long long* __restrict__ acc_sum,
+                                                    uint32_t n, const uint32_t* __restrict__ n_dev,
+                                                    unsigned long long* __restrict__ acc_sum,
                                                     uint32_t* __restrict__ acc_cnt) {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    if (i >= (n_dev ? min(*n_dev, n) : n)) return;
     int c[3];
     c[0] = grid_index(pos[3 * (size_t)i + 0], A.lo[0], A.scale, A.D);
     c[1] = grid_index(pos[3 * (size_t)i + 1], A.lo[1], A.scale, A.D);
@@ -93,7 +94,9 @@ __global__ void k_reduce_level(uint32_t off, uint32_t n, int children_are_leaves
     value[id] = node_values(s0, c0, s1, c1);
 }
 
-int accumulate(wfpg_svo* s, const float* pos, const float* wout, const float* L, uint32_t n, cudaStream_t st) {
+// n_dev: optional device count of valid records (the first min(*n_dev, n))
+int accumulate(wfpg_svo* s, const float* pos, const float* wout, const float* L, uint32_t n, cudaStream_t st,
+               const uint32_t* n_dev) {
     const int T = 256;
     if (n > 0) {
         AccArgs A;
@@ -102,7 +105,7 @@ int accumulate(wfpg_svo* s, const float* pos, const float* wout, const float* L,
         A.D = s->D;
         for (int a = 0; a < 3; ++a) A.lo[a] = s->lo[a];
         A.scale = s->scale;
-        WFPG_LAUNCH(k_accumulate, div_up(n, T), T, 0, st, A, pos, wout, L, n, s->acc_sum, s->acc_cnt);
+        WFPG_LAUNCH(k_accumulate, div_up(n, T), T, 0, st, A, pos, wout, L, n, n_dev, s->acc_sum, s->acc_cnt);
     }
     const int D = s->D;
     const auto* as = reinterpret_cast<const ulonglong2*>(s->acc_sum);

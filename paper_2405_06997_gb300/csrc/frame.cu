@@ -1,0 +1,732 @@
+// Batched wavefront frame: Alg. 1 for every pixel of a pinhole camera with
+// no host round trip, captured once as a CUDA graph and replayed per frame.
+//
+// Per depth the live paths sit in a compact queue (structure of arrays, in
+// pixel order: compaction is an exclusive scan, so every run is
+// deterministic); Partition-S and the fused GuideRays launch read the queue
+// length from device memory, so the same launches serve every depth and
+// every frame.  The path history (throughput, emission, position and
+// direction toward the previous vertex, per vertex) is kept for Eq. 5, which
+// runs once per frame after the last depth (UpdateExitance in Alg. 1).
+#include <algorithm>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "cast.cuh"
+#include "common.cuh"
+#include "sort.cuh"
+#include "svo.cuh"
+
+namespace wfpg {
+
+int set_last_error(int code, const std::string& msg);
+void note_launches(long long n);
+int bin_rays_impl(const wfpg_svo* s, const float* pos, const float* nrm, uint32_t n, const wfpg_bin_params* p,
+                  const uint32_t* sizes, uint32_t* bin_of_ray, uint32_t* ray_order, uint32_t* bin_offset,
+                  uint32_t* origin_ray, uint32_t bin_cap, uint32_t* n_bins_dev, void* workspace, size_t ws_bytes,
+                  cudaStream_t st, const uint32_t* frame_dev);
+size_t bin_workspace_bytes(const wfpg_svo* s, uint32_t n, int mode, uint32_t n_sizes);
+int guide_fused_impl(const wfpg_svo* s, const float* pos, const float* nrm, const uint32_t* origin_ray,
+                     const uint32_t* n_bins_dev, uint32_t bin_cap, const uint32_t* ray_order,
+                     const uint32_t* bin_offset, const float* u, float alpha, const wfpg_guide_params* p, float* dir,
+                     float* pdf_out, cudaStream_t st, const uint32_t* frame_dev);
+int accumulate(wfpg_svo* s, const float* pos, const float* wout, const float* L, uint32_t n, cudaStream_t st,
+               const uint32_t* n_dev);
+
+constexpr uint64_t kPathPurpose = 2;  // per-path uniforms (0: origins, 1: jitter)
+constexpr uint32_t kDepthStride = 16; // random-stream frame index = frame * 16 + depth
+constexpr float kInvPi = 0.31830988618379067f;
+
+// one queue of live paths (or the staging copy the shading writes)
+struct Queue {
+    uint32_t* path;
+    float* pos;  // xyz
+    float* nrm;  // xyz, facing the incoming ray
+    float* T;    // throughput of the continuation (Russian roulette included)
+    float* alb;  // albedo at the vertex
+    float* u;    // xyz uniforms of the next direction (queues only)
+};
+
+struct FrameView {
+    const float* quads;
+    uint32_t nq;
+    const float* spheres;
+    uint32_t ns;
+    const float* emission;
+    const float* albedo;
+    uint32_t P, W, H;
+    float eye[3], fwd[3], right[3], up[3];  // right and up scaled by the image-plane half extents
+    int max_depth, rr_depth;
+    uint64_t pseed;
+    float offset;  // origin offset along the normal for continuation rays
+    float* vT;
+    float* vLe;
+    float* vpos;
+    float* vwo;
+    uint32_t* nv;
+    double* img_sum;
+    double* img_sq;
+    uint32_t* counters;  // [0 .. max_depth - 1]: paths per depth; [WFPG_FRAME_MAX_DEPTH + 1]: records
+    uint32_t* fidx;      // [0 .. max_depth]: random-stream frame index per depth
+    uint32_t* frame_counter;
+    unsigned long long* frames_run;
+    unsigned long long* guided;
+};
+
+__device__ __forceinline__ float path_uniform(const FrameView& F, uint32_t path, uint32_t counter) {
+    return uniform01(F.pseed, ((uint64_t)F.fidx[0] << 32) | path, counter);
+}
+
+__global__ void k_frame_begin(FrameView F) {
+    const uint32_t fc = *F.frame_counter;
+    for (int k = threadIdx.x; k <= F.max_depth; k += blockDim.x) F.fidx[k] = fc * kDepthStride + k;
+    for (int k = threadIdx.x; k <= WFPG_FRAME_MAX_DEPTH + 1; k += blockDim.x) F.counters[k] = 0;
+}
+
+// survival test at 1-based vertex v (>= rr_depth): min(0.95, albedo)
+__device__ __forceinline__ bool roulette(const FrameView& F, uint32_t path, int v, float alb, float* T) {
+    if (v < F.rr_depth) return true;
+    const float q = fminf(0.95f, alb);
+    if (path_uniform(F, path, 4u * (uint32_t)(v - 1) + 3u) >= q) return false;
+    *T = *T / q;
+    return true;
+}
+
+__device__ __forceinline__ void store3(float* a, size_t i, float x, float y, float z) {
+    a[3 * i] = x;
+    a[3 * i + 1] = y;
+    a[3 * i + 2] = z;
+}
+
+// primary rays through pixel centres, their closest hits = vertex 1
+__global__ void __launch_bounds__(256) k_camera(FrameView F, Queue S, uint32_t* __restrict__ flags) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= F.P) return;
+    const uint32_t x = i % F.W, y = i / F.W;
+    const float px = ((float)x + 0.5f) / (float)F.W * 2.0f - 1.0f;
+    const float py = 1.0f - ((float)y + 0.5f) / (float)F.H * 2.0f;
+    float dx = F.fwd[0] + px * F.right[0] + py * F.up[0];
+    float dy = F.fwd[1] + px * F.right[1] + py * F.up[1];
+    float dz = F.fwd[2] + px * F.right[2] + py * F.up[2];
+    const float inv = 1.0f / sqrtf(dx * dx + dy * dy + dz * dz);
+    dx *= inv;
+    dy *= inv;
+    dz *= inv;
+    const Hit h = cast_closest(F.quads, F.nq, F.spheres, F.ns, F.eye[0], F.eye[1], F.eye[2], dx, dy, dz, 0.0f);
+    uint32_t flag = 0;
+    F.nv[i] = 0;
+    if (h.prim != kNone) {
+        const float hx = F.eye[0] + h.t * dx, hy = F.eye[1] + h.t * dy, hz = F.eye[2] + h.t * dz;
+        const float3 n = hit_normal(F.quads, F.nq, F.spheres, h, F.eye[0], F.eye[1], F.eye[2], dx, dy, dz);
+        const float a = F.albedo[h.prim];
+        F.vT[i] = 1.0f;
+        F.vLe[i] = F.emission[h.prim];
+        store3(F.vpos, i, hx, hy, hz);
+        store3(F.vwo, i, -dx, -dy, -dz);
+        F.nv[i] = 1;
+        float T = 1.0f;
+        if (a > 0.0f && F.max_depth >= 1 && roulette(F, i, 1, a, &T)) {
+            S.path[i] = i;
+            store3(S.pos, i, hx, hy, hz);
+            store3(S.nrm, i, n.x, n.y, n.z);
+            S.T[i] = T;
+            S.alb[i] = a;
+            flag = 1;
+        }
+    }
+    flags[i] = flag;
+}
+
+// staging slot i -> queue slot offs[i] for the survivors; draws the uniforms of depth k
+__global__ void __launch_bounds__(256) k_compact(FrameView F, Queue S, Queue Q, const uint32_t* __restrict__ flags,
+                                                 const uint32_t* __restrict__ offs, int k) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= F.P || !flags[i]) return;
+    const uint32_t j = offs[i];
+    const uint32_t path = S.path[i];
+    Q.path[j] = path;
+    store3(Q.pos, j, S.pos[3 * (size_t)i], S.pos[3 * (size_t)i + 1], S.pos[3 * (size_t)i + 2]);
+    store3(Q.nrm, j, S.nrm[3 * (size_t)i], S.nrm[3 * (size_t)i + 1], S.nrm[3 * (size_t)i + 2]);
+    Q.T[j] = S.T[i];
+    Q.alb[j] = S.alb[i];
+    const uint32_t c = 4u * (uint32_t)k;
+    store3(Q.u, j, path_uniform(F, path, c), path_uniform(F, path, c + 1), path_uniform(F, path, c + 2));
+}
+
+// Lambertian BSDF weight, closest hit (vertex k + 2), emission, roulette
+__global__ void __launch_bounds__(256) k_shade(FrameView F, Queue Q, const float* __restrict__ dir,
+                                               const float* __restrict__ pdf, Queue S, uint32_t* __restrict__ flags,
+                                               int k) {
+    const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= F.P) return;
+    uint32_t flag = 0;
+    if (s < F.counters[k]) {
+        const uint32_t path = Q.path[s];
+        const float nx = Q.nrm[3 * (size_t)s], ny = Q.nrm[3 * (size_t)s + 1], nz = Q.nrm[3 * (size_t)s + 2];
+        const float dx = dir[3 * (size_t)s], dy = dir[3 * (size_t)s + 1], dz = dir[3 * (size_t)s + 2];
+        const float p = pdf[s];
+        const float cs = nx * dx + ny * dy + nz * dz;
+        if (p > 0.0f && cs > 0.0f) {
+            float T = Q.T[s] * (Q.alb[s] * kInvPi) * cs / p;
+            const float ox = Q.pos[3 * (size_t)s] + F.offset * nx;
+            const float oy = Q.pos[3 * (size_t)s + 1] + F.offset * ny;
+            const float oz = Q.pos[3 * (size_t)s + 2] + F.offset * nz;
+            const Hit h = cast_closest(F.quads, F.nq, F.spheres, F.ns, ox, oy, oz, dx, dy, dz, 0.0f);
+            if (h.prim != kNone) {
+                const size_t v = (size_t)(k + 1) * F.P + path;
+                const float hx = ox + h.t * dx, hy = oy + h.t * dy, hz = oz + h.t * dz;
+                const float a = F.albedo[h.prim];
+                F.vT[v] = T;
+                F.vLe[v] = F.emission[h.prim];
+                store3(F.vpos, v, hx, hy, hz);
+                store3(F.vwo, v, -dx, -dy, -dz);
+                F.nv[path] = (uint32_t)(k + 2);
+                if (a > 0.0f && k + 1 < F.max_depth && roulette(F, path, k + 2, a, &T)) {
+                    const float3 n = hit_normal(F.quads, F.nq, F.spheres, h, ox, oy, oz, dx, dy, dz);
+                    S.path[s] = path;
+                    store3(S.pos, s, hx, hy, hz);
+                    store3(S.nrm, s, n.x, n.y, n.z);
+                    S.T[s] = T;
+                    S.alb[s] = a;
+                    flag = 1;
+                }
+            }
+        }
+    }
+    flags[s] = flag;
+}
+
+// Eq. 5 for every vertex of every path, back to front: the suffix sum
+// S_k = sum_{n >= k} T_n Le_n gives L_k = S_k / T_k; S_1 is the path estimate.
+__global__ void __launch_bounds__(256) k_records(FrameView F, float* __restrict__ rec_pos,
+                                                 float* __restrict__ rec_wout, float* __restrict__ rec_L,
+                                                 uint32_t* __restrict__ rec_src) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t n = i < F.P ? F.nv[i] : 0u;
+    // one atomic per warp reserves the warp's records
+    uint32_t incl = n;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= (uint32_t)o) incl += t;
+    }
+    uint32_t base = 0;
+    if (lane == 31) base = atomicAdd(&F.counters[WFPG_FRAME_MAX_DEPTH + 1], incl);
+    base = __shfl_sync(0xffffffffu, base, 31) + incl - n;
+    if (i >= F.P) return;
+    float S = 0.0f;
+    for (int v = (int)n - 1; v >= 0; --v) {
+        const size_t e = (size_t)v * F.P + i;
+        const float T = F.vT[e];
+        S = S + T * F.vLe[e];
+        const uint32_t r = base + (uint32_t)v;
+        rec_pos[3 * (size_t)r] = F.vpos[3 * e];
+        rec_pos[3 * (size_t)r + 1] = F.vpos[3 * e + 1];
+        rec_pos[3 * (size_t)r + 2] = F.vpos[3 * e + 2];
+        rec_wout[3 * (size_t)r] = F.vwo[3 * e];
+        rec_wout[3 * (size_t)r + 1] = F.vwo[3 * e + 1];
+        rec_wout[3 * (size_t)r + 2] = F.vwo[3 * e + 2];
+        rec_L[r] = S / T;
+        rec_src[r] = (uint32_t)e;
+    }
+    const double L = (double)S;
+    F.img_sum[i] += L;
+    F.img_sq[i] += L * L;
+}
+
+__global__ void k_frame_end(FrameView F) {
+    unsigned long long g = 0;
+    for (int k = 0; k < F.max_depth; ++k) g += F.counters[k];
+    *F.guided += g;
+    *F.frames_run += 1ull;
+    *F.frame_counter += 1u;
+}
+
+__global__ void __launch_bounds__(256) k_image(const double* __restrict__ sum, const double* __restrict__ sq,
+                                               const unsigned long long* __restrict__ frames, uint32_t P,
+                                               float* __restrict__ mean, float* __restrict__ var) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P) return;
+    const double f = (double)*frames;
+    const double m = f > 0 ? sum[i] / f : 0.0;
+    if (mean) mean[i] = (float)m;
+    if (var) var[i] = f > 1 ? (float)fmax(0.0, (sq[i] - f * m * m) / (f - 1.0)) : 0.0f;
+}
+
+// mean over pixels of the per-pixel variance (one block; for the autotuner)
+__global__ void k_mean_var(const double* __restrict__ sum, const double* __restrict__ sq,
+                           const unsigned long long* __restrict__ frames, uint32_t P, double* __restrict__ out) {
+    __shared__ double red[256];
+    const double f = (double)*frames;
+    double acc = 0.0;
+    for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) {
+        const double m = sum[i] / f;
+        acc += fmax(0.0, (sq[i] - f * m * m) / (f - 1.0));
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = red[0] / (double)P;
+}
+
+}  // namespace wfpg
+
+using namespace wfpg;
+
+struct wfpg_frame {
+    wfpg_svo* svo = nullptr;
+    wfpg_scene scene{};
+    const float* emission = nullptr;
+    const float* albedo = nullptr;
+    wfpg_camera cam{};
+    wfpg_frame_params p{};
+    int depth_cap = 0;  // max_depth the buffers were sized for
+    uint32_t P = 0;
+    uint32_t bin_cap = 0;
+    std::vector<void*> allocs;
+    Queue q[2]{}, stage{};
+    uint32_t* flags = nullptr;
+    uint32_t* offs = nullptr;
+    float* dir = nullptr;
+    float* pdf = nullptr;
+    uint32_t* bin_of_ray = nullptr;
+    uint32_t* ray_order = nullptr;
+    uint32_t* bin_offset = nullptr;
+    uint32_t* origin_ray = nullptr;
+    uint32_t* n_bins = nullptr;  // [WFPG_FRAME_MAX_DEPTH + 1]
+    void* bin_ws = nullptr;
+    size_t bin_ws_bytes = 0;
+    void* scan_ws = nullptr;
+    size_t scan_ws_bytes = 0;
+    float* vT = nullptr;
+    float* vLe = nullptr;
+    float* vpos = nullptr;
+    float* vwo = nullptr;
+    uint32_t* nv = nullptr;
+    float* rec_pos = nullptr;
+    float* rec_wout = nullptr;
+    float* rec_L = nullptr;
+    uint32_t* rec_src = nullptr;
+    double* img_sum = nullptr;
+    double* img_sq = nullptr;
+    uint32_t* counters = nullptr;  // [WFPG_FRAME_MAX_DEPTH + 2]
+    uint32_t* fidx = nullptr;      // [WFPG_FRAME_MAX_DEPTH + 1]
+    uint32_t* frame_counter = nullptr;
+    unsigned long long* frames_run = nullptr;
+    unsigned long long* guided = nullptr;
+    double* scalar = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    unsigned long long graph_kernels = 0;
+    ~wfpg_frame() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        for (void* a : allocs) cudaFree(a);
+    }
+    template <typename T>
+    bool alloc(T** out, size_t count) {
+        void* ptr = nullptr;
+        if (cudaMalloc(&ptr, std::max<size_t>(count * sizeof(T), 16)) != cudaSuccess) return false;
+        allocs.push_back(ptr);
+        *out = static_cast<T*>(ptr);
+        return true;
+    }
+    void drop_graph() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        exec = nullptr;
+        graph = nullptr;
+    }
+    FrameView view() const {
+        FrameView F;
+        F.quads = scene.quads;
+        F.nq = scene.n_quads;
+        F.spheres = scene.spheres;
+        F.ns = scene.n_spheres;
+        F.emission = emission;
+        F.albedo = albedo;
+        F.P = P;
+        F.W = cam.width;
+        F.H = cam.height;
+        const float th = tanf(cam.vfov_deg * 0.5f * 3.14159265358979f / 180.0f);
+        const float aspect = (float)cam.width / (float)cam.height;
+        const float* f = cam.forward;
+        const float* u = cam.up;
+        // image x grows along up x forward (+x for a camera looking along +z with +y up)
+        const float r[3] = {u[1] * f[2] - u[2] * f[1], u[2] * f[0] - u[0] * f[2], u[0] * f[1] - u[1] * f[0]};
+        for (int a = 0; a < 3; ++a) {
+            F.eye[a] = cam.eye[a];
+            F.fwd[a] = f[a];
+            F.right[a] = r[a] * th * aspect;
+            F.up[a] = u[a] * th;
+        }
+        F.max_depth = p.max_depth;
+        F.rr_depth = p.rr_depth;
+        F.pseed = purpose(p.seed, kPathPurpose);
+        F.offset = 1e-4f * scene.size;
+        F.vT = vT;
+        F.vLe = vLe;
+        F.vpos = vpos;
+        F.vwo = vwo;
+        F.nv = nv;
+        F.img_sum = img_sum;
+        F.img_sq = img_sq;
+        F.counters = counters;
+        F.fidx = fidx;
+        F.frame_counter = frame_counter;
+        F.frames_run = frames_run;
+        F.guided = guided;
+        return F;
+    }
+    // one frame's launches on st
+    int enqueue(cudaStream_t st) {
+        const FrameView F = view();
+        const int T = 256;
+        const uint32_t g = div_up(P, T);
+        WFPG_LAUNCH(k_frame_begin, 1, 32, 0, st, F);
+        WFPG_LAUNCH(k_camera, g, T, 0, st, F, stage, flags);
+        for (int k = 0; k < p.max_depth; ++k) {
+            Queue& Q = q[k & 1];
+            {
+                Arena ws{static_cast<char*>(scan_ws), scan_ws_bytes, 0, false};
+                scan_exclusive(flags, offs, P, counters + k, ws, st);
+            }
+            WFPG_LAUNCH(k_compact, g, T, 0, st, F, stage, Q, flags, offs, k);
+            wfpg_bin_params bp{};
+            bp.mode = WFPG_BIN_PARTITION_S;
+            bp.l_min = p.l_min;
+            bp.c_ray = p.c_ray;
+            bp.seed = p.seed;
+            bp.n_dev = counters + k;
+            int rc = bin_rays_impl(svo, Q.pos, Q.nrm, P, &bp, nullptr, bin_of_ray, ray_order, bin_offset, origin_ray,
+                                   bin_cap, n_bins + k, bin_ws, bin_ws_bytes, st, fidx + k);
+            if (rc != WFPG_OK) return rc;
+            wfpg_guide_params gp = p.guide;
+            gp.seed = p.seed;
+            rc = guide_fused_impl(svo, Q.pos, Q.nrm, origin_ray, n_bins + k, bin_cap, ray_order, bin_offset, Q.u,
+                                  p.alpha, &gp, dir, pdf, st, fidx + k);
+            if (rc != WFPG_OK) return rc;
+            WFPG_LAUNCH(k_shade, g, T, 0, st, F, Q, dir, pdf, stage, flags, k);
+        }
+        WFPG_LAUNCH(k_records, g, T, 0, st, F, rec_pos, rec_wout, rec_L, rec_src);
+        if (p.update) {
+            const int rc = accumulate(svo, rec_pos, rec_wout, rec_L, (uint32_t)((size_t)(p.max_depth + 1) * P), st,
+                                      counters + WFPG_FRAME_MAX_DEPTH + 1);
+            if (rc != WFPG_OK) return rc;
+        }
+        WFPG_LAUNCH(k_frame_end, 1, 1, 0, st, F);
+        return cudaGetLastError() == cudaSuccess ? WFPG_OK : WFPG_ERR_CUDA;
+    }
+    int capture(cudaStream_t st) {
+        drop_graph();
+        cudaStream_t cs;
+        if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return WFPG_ERR_CUDA;
+        const unsigned long long before = wfpg_kernel_launches();
+        int rc = WFPG_OK;
+        if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) rc = WFPG_ERR_CUDA;
+        if (rc == WFPG_OK) {
+            rc = enqueue(cs);
+            const cudaError_t e = cudaStreamEndCapture(cs, &graph);
+            if (rc == WFPG_OK && e != cudaSuccess) rc = WFPG_ERR_CUDA;
+        }
+        graph_kernels = wfpg_kernel_launches() - before;
+        note_launches(-(long long)graph_kernels);  // captured launches run only when replayed
+        if (rc == WFPG_OK && cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) rc = WFPG_ERR_CUDA;
+        cudaStreamDestroy(cs);
+        if (rc != WFPG_OK) drop_graph();
+        (void)st;
+        return rc;
+    }
+};
+
+static int ffail(int code, const char* msg) { return set_last_error(code, msg); }
+
+static bool valid_grid_n(int N) { return N == 8 || N == 16 || N == 32 || N == 64 || N == 128; }
+
+static int check_params(const wfpg_frame_params* p, int depth_cap) {
+    if (!p) return ffail(WFPG_ERR_INVALID_ARG, "frame: null params");
+    if (p->max_depth < 1 || p->max_depth > WFPG_FRAME_MAX_DEPTH || (depth_cap && p->max_depth > depth_cap))
+        return ffail(WFPG_ERR_INVALID_ARG, "frame: max_depth out of range");
+    if (!(p->alpha >= 0.0f && p->alpha <= 1.0f)) return ffail(WFPG_ERR_INVALID_ARG, "frame: alpha must be in [0, 1]");
+    if (!valid_grid_n(p->guide.N)) return ffail(WFPG_ERR_INVALID_ARG, "frame: N must be 8, 16, 32, 64 or 128");
+    if (!(p->guide.eps >= 0.0f)) return ffail(WFPG_ERR_INVALID_ARG, "frame: eps must be >= 0");
+    if (p->guide.block != 0 && p->guide.block != 64 && p->guide.block != 128 && p->guide.block != 256)
+        return ffail(WFPG_ERR_INVALID_ARG, "frame: block must be 0, 64, 128 or 256");
+    if (p->c_ray == 0) return ffail(WFPG_ERR_INVALID_ARG, "frame: c_ray must be >= 1");
+    return WFPG_OK;
+}
+
+extern "C" {
+
+int frame_create(wfpg_svo* svo, const wfpg_scene* scene, const float* emission, const float* albedo,
+                 const wfpg_camera* cam, const wfpg_frame_params* p, wfpg_frame** out, void* stream) {
+    if (!svo || !scene || !emission || !albedo || !cam || !out)
+        return ffail(WFPG_ERR_INVALID_ARG, "frame_create: null argument");
+    *out = nullptr;
+    if (cam->width == 0 || cam->height == 0 || (uint64_t)cam->width * cam->height > (1u << 30))
+        return ffail(WFPG_ERR_INVALID_ARG, "frame_create: image size out of range");
+    if (!(cam->vfov_deg > 0.0f && cam->vfov_deg < 180.0f))
+        return ffail(WFPG_ERR_INVALID_ARG, "frame_create: vfov_deg must be in (0, 180)");
+    if (const int rc = check_params(p, 0)) return rc;
+    auto* f = new wfpg_frame();
+    f->svo = svo;
+    f->scene = *scene;
+    f->emission = emission;
+    f->albedo = albedo;
+    f->cam = *cam;
+    f->p = *p;
+    f->depth_cap = p->max_depth;
+    const uint32_t P = cam->width * cam->height;
+    f->P = P;
+    f->bin_cap = std::max<uint32_t>(1, std::min<uint32_t>(P, svo->n_nodes));
+    const size_t V = (size_t)(p->max_depth + 1) * P;
+    bool ok = true;
+    for (int j = 0; j < 3; ++j) {
+        Queue& Q = j < 2 ? f->q[j] : f->stage;
+        ok = ok && f->alloc(&Q.path, P) && f->alloc(&Q.pos, 3 * (size_t)P) && f->alloc(&Q.nrm, 3 * (size_t)P) &&
+             f->alloc(&Q.T, P) && f->alloc(&Q.alb, P);
+        if (j < 2) ok = ok && f->alloc(&Q.u, 3 * (size_t)P);
+    }
+    f->bin_ws_bytes = bin_workspace_bytes(svo, P, WFPG_BIN_PARTITION_S, 0);
+    f->scan_ws_bytes = scan_workspace_bytes(P) + 1024;
+    ok = ok && f->alloc(&f->flags, P) && f->alloc(&f->offs, P) && f->alloc(&f->dir, 3 * (size_t)P) &&
+         f->alloc(&f->pdf, P) && f->alloc(&f->bin_of_ray, P) && f->alloc(&f->ray_order, P) &&
+         f->alloc(&f->bin_offset, (size_t)f->bin_cap + 1) && f->alloc(&f->origin_ray, f->bin_cap) &&
+         f->alloc(&f->n_bins, WFPG_FRAME_MAX_DEPTH + 1) &&
+         f->alloc(reinterpret_cast<char**>(&f->bin_ws), f->bin_ws_bytes) &&
+         f->alloc(reinterpret_cast<char**>(&f->scan_ws), f->scan_ws_bytes) && f->alloc(&f->vT, V) &&
+         f->alloc(&f->vLe, V) && f->alloc(&f->vpos, 3 * V) && f->alloc(&f->vwo, 3 * V) && f->alloc(&f->nv, P) &&
+         f->alloc(&f->rec_pos, 3 * V) && f->alloc(&f->rec_wout, 3 * V) && f->alloc(&f->rec_L, V) &&
+         f->alloc(&f->rec_src, V) && f->alloc(&f->img_sum, P) && f->alloc(&f->img_sq, P) &&
+         f->alloc(&f->counters, WFPG_FRAME_MAX_DEPTH + 2) && f->alloc(&f->fidx, WFPG_FRAME_MAX_DEPTH + 1) &&
+         f->alloc(&f->frame_counter, 1) && f->alloc(&f->frames_run, 1) && f->alloc(&f->guided, 1) &&
+         f->alloc(&f->scalar, 1);
+    if (!ok) {
+        delete f;
+        cudaGetLastError();
+        return ffail(WFPG_ERR_OOM, "frame_create: device allocation failed");
+    }
+    auto st = static_cast<cudaStream_t>(stream);
+    cudaMemsetAsync(f->counters, 0, 4 * (WFPG_FRAME_MAX_DEPTH + 2), st);
+    cudaMemsetAsync(f->n_bins, 0, 4 * (WFPG_FRAME_MAX_DEPTH + 1), st);
+    cudaMemsetAsync(f->nv, 0, 4 * (size_t)P, st);
+    cudaMemsetAsync(f->img_sum, 0, 8 * (size_t)P, st);
+    cudaMemsetAsync(f->img_sq, 0, 8 * (size_t)P, st);
+    cudaMemsetAsync(f->frame_counter, 0, 4, st);
+    cudaMemsetAsync(f->frames_run, 0, 8, st);
+    cudaMemsetAsync(f->guided, 0, 8, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess) {
+        delete f;
+        return ffail(WFPG_ERR_CUDA, "frame_create: initialisation failed");
+    }
+    *out = f;
+    return WFPG_OK;
+}
+
+int frame_destroy(wfpg_frame* f) {
+    if (f) {
+        cudaDeviceSynchronize();
+        delete f;
+    }
+    return WFPG_OK;
+}
+
+int frame_run(wfpg_frame* f, uint32_t n_frames, int use_graph, void* stream) {
+    if (!f) return ffail(WFPG_ERR_INVALID_ARG, "frame_run: null frame");
+    auto st = static_cast<cudaStream_t>(stream);
+    if (use_graph && !f->exec) {
+        const int rc = f->capture(st);
+        if (rc != WFPG_OK) return ffail(rc, "frame_run: graph capture failed");
+    }
+    for (uint32_t i = 0; i < n_frames; ++i) {
+        if (use_graph) {
+            if (cudaGraphLaunch(f->exec, st) != cudaSuccess) return ffail(WFPG_ERR_CUDA, "frame_run: graph launch");
+            note_launches((long long)f->graph_kernels);
+        } else {
+            const int rc = f->enqueue(st);
+            if (rc != WFPG_OK) return ffail(rc, "frame_run: launch failed");
+        }
+    }
+    return WFPG_OK;
+}
+
+int frame_set_params(wfpg_frame* f, const wfpg_frame_params* p) {
+    if (!f) return ffail(WFPG_ERR_INVALID_ARG, "frame_set_params: null frame");
+    if (const int rc = check_params(p, f->depth_cap)) return rc;
+    f->drop_graph();
+    f->p = *p;
+    return WFPG_OK;
+}
+
+int frame_get_params(const wfpg_frame* f, wfpg_frame_params* p) {
+    if (!f || !p) return ffail(WFPG_ERR_INVALID_ARG, "frame_get_params: null argument");
+    *p = f->p;
+    return WFPG_OK;
+}
+
+int frame_reset_image(wfpg_frame* f, void* stream) {
+    if (!f) return ffail(WFPG_ERR_INVALID_ARG, "frame_reset_image: null frame");
+    auto st = static_cast<cudaStream_t>(stream);
+    cudaMemsetAsync(f->img_sum, 0, 8 * (size_t)f->P, st);
+    cudaMemsetAsync(f->img_sq, 0, 8 * (size_t)f->P, st);
+    cudaMemsetAsync(f->frames_run, 0, 8, st);
+    cudaMemsetAsync(f->guided, 0, 8, st);
+    return cudaGetLastError() == cudaSuccess ? WFPG_OK : ffail(WFPG_ERR_CUDA, "frame_reset_image");
+}
+
+int frame_image(wfpg_frame* f, float* mean, float* var, void* stream) {
+    if (!f) return ffail(WFPG_ERR_INVALID_ARG, "frame_image: null frame");
+    WFPG_LAUNCH(k_image, div_up(f->P, 256), 256, 0, static_cast<cudaStream_t>(stream), f->img_sum, f->img_sq,
+                f->frames_run, f->P, mean, var);
+    return cudaGetLastError() == cudaSuccess ? WFPG_OK : ffail(WFPG_ERR_CUDA, "frame_image");
+}
+
+int frame_stats(wfpg_frame* f, wfpg_frame_stats* out, void* stream) {
+    if (!f || !out) return ffail(WFPG_ERR_INVALID_ARG, "frame_stats: null argument");
+    auto st = static_cast<cudaStream_t>(stream);
+    uint32_t c[WFPG_FRAME_MAX_DEPTH + 2], nb[WFPG_FRAME_MAX_DEPTH + 1];
+    unsigned long long fr = 0, g = 0;
+    uint32_t status = 0;
+    cudaMemcpyAsync(c, f->counters, sizeof c, cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(nb, f->n_bins, sizeof nb, cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(&fr, f->frames_run, 8, cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(&g, f->guided, 8, cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(&status, f->svo->status, 4, cudaMemcpyDeviceToHost, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess) return ffail(WFPG_ERR_CUDA, "frame_stats: copy failed");
+    std::memset(out, 0, sizeof *out);
+    out->frames = fr;
+    for (int k = 0; k < f->p.max_depth; ++k) {
+        out->paths[k] = c[k];
+        out->bins[k] = nb[k];
+    }
+    out->records = c[WFPG_FRAME_MAX_DEPTH + 1];
+    out->guided_samples = g;
+    out->status = status;
+    out->kernels_per_frame = f->graph_kernels;
+    return WFPG_OK;
+}
+
+int frame_autotune(wfpg_frame* f, const int* N_candidates, int n_N, uint32_t frames, wfpg_frame_params* chosen,
+                   float* ms_per_frame, void* stream) {
+    if (!f || !N_candidates || n_N < 1 || frames < 2)
+        return ffail(WFPG_ERR_INVALID_ARG, "frame_autotune: need candidates and frames >= 2");
+    for (int i = 0; i < n_N; ++i)
+        if (!valid_grid_n(N_candidates[i])) return ffail(WFPG_ERR_INVALID_ARG, "frame_autotune: bad N candidate");
+    auto st = static_cast<cudaStream_t>(stream);
+    const wfpg_frame_params base = f->p;
+    static const int kTiles[6][2] = {{64, 1}, {64, -1}, {128, 1}, {128, -1}, {256, 1}, {256, -1}};
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    double best_fom = -1.0;
+    wfpg_frame_params best = base;
+    float best_ms = 0.0f;
+    int rc = WFPG_OK;
+    for (int i = 0; i < n_N && rc == WFPG_OK; ++i) {
+        wfpg_frame_params t = base;
+        t.guide.N = N_candidates[i];
+        float tile_ms = -1.0f;
+        wfpg_frame_params tile_best = t;
+        for (const auto& tile : kTiles) {
+            t.guide.block = tile[0];
+            t.guide.stage = tile[1];
+            f->p = t;
+            f->drop_graph();
+            if (f->capture(st) != WFPG_OK) {  // this tile does not fit (shared memory): skip it
+                cudaGetLastError();
+                continue;
+            }
+            cudaGraphLaunch(f->exec, st);  // warm
+            cudaEventRecord(e0, st);
+            cudaGraphLaunch(f->exec, st);
+            cudaGraphLaunch(f->exec, st);
+            cudaEventRecord(e1, st);
+            note_launches(3ll * (long long)f->graph_kernels);
+            if (cudaEventSynchronize(e1) != cudaSuccess) {
+                rc = WFPG_ERR_CUDA;
+                break;
+            }
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            ms *= 0.5f;
+            if (tile_ms < 0.0f || ms < tile_ms) {
+                tile_ms = ms;
+                tile_best = t;
+            }
+        }
+        if (rc != WFPG_OK || tile_ms < 0.0f) continue;
+        f->p = tile_best;
+        f->drop_graph();
+        if (f->capture(st) != WFPG_OK) continue;
+        frame_reset_image(f, st);
+        for (uint32_t k = 0; k < frames; ++k) cudaGraphLaunch(f->exec, st);
+        note_launches((long long)frames * (long long)f->graph_kernels);
+        WFPG_LAUNCH(k_mean_var, 1, 256, 0, st, f->img_sum, f->img_sq, f->frames_run, f->P, f->scalar);
+        double mv = 0.0;
+        cudaMemcpyAsync(&mv, f->scalar, 8, cudaMemcpyDeviceToHost, st);
+        if (cudaStreamSynchronize(st) != cudaSuccess) {
+            rc = WFPG_ERR_CUDA;
+            break;
+        }
+        const double fom = mv * (double)tile_ms;
+        if (best_fom < 0.0 || fom < best_fom) {
+            best_fom = fom;
+            best = tile_best;
+            best_ms = tile_ms;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != WFPG_OK) {
+        f->p = base;
+        f->drop_graph();
+        return ffail(rc, "frame_autotune: CUDA error");
+    }
+    if (best_fom < 0.0) {
+        f->p = base;
+        f->drop_graph();
+        return ffail(WFPG_ERR_INVALID_ARG, "frame_autotune: no candidate fits");
+    }
+    f->p = best;
+    f->drop_graph();
+    frame_reset_image(f, st);
+    if (chosen) *chosen = best;
+    if (ms_per_frame) *ms_per_frame = best_ms;
+    return cudaStreamSynchronize(st) == cudaSuccess ? WFPG_OK : ffail(WFPG_ERR_CUDA, "frame_autotune");
+}
+
+int frame_export(const wfpg_frame* f, int what, void* dst, size_t bytes, void* stream) {
+    if (!f || !dst) return ffail(WFPG_ERR_INVALID_ARG, "frame_export: null argument");
+    const size_t P = f->P, V = (size_t)(f->depth_cap + 1) * P;
+    const int last = (f->p.max_depth - 1) & 1;
+    const void* src = nullptr;
+    size_t n = 0;
+    switch (what) {
+        case WFPG_FRAME_BUF_VT: src = f->vT; n = 4 * V; break;
+        case WFPG_FRAME_BUF_VLE: src = f->vLe; n = 4 * V; break;
+        case WFPG_FRAME_BUF_VPOS: src = f->vpos; n = 12 * V; break;
+        case WFPG_FRAME_BUF_VWO: src = f->vwo; n = 12 * V; break;
+        case WFPG_FRAME_BUF_NV: src = f->nv; n = 4 * P; break;
+        case WFPG_FRAME_BUF_REC_POS: src = f->rec_pos; n = 12 * V; break;
+        case WFPG_FRAME_BUF_REC_WOUT: src = f->rec_wout; n = 12 * V; break;
+        case WFPG_FRAME_BUF_REC_L: src = f->rec_L; n = 4 * V; break;
+        case WFPG_FRAME_BUF_REC_SRC: src = f->rec_src; n = 4 * V; break;
+        case WFPG_FRAME_BUF_Q_POS: src = f->q[last].pos; n = 12 * P; break;
+        case WFPG_FRAME_BUF_Q_NRM: src = f->q[last].nrm; n = 12 * P; break;
+        case WFPG_FRAME_BUF_Q_U: src = f->q[last].u; n = 12 * P; break;
+        case WFPG_FRAME_BUF_Q_DIR: src = f->dir; n = 12 * P; break;
+        case WFPG_FRAME_BUF_Q_PDF: src = f->pdf; n = 4 * P; break;
+        case WFPG_FRAME_BUF_Q_PATH: src = f->q[last].path; n = 4 * P; break;
+        default: return ffail(WFPG_ERR_INVALID_ARG, "frame_export: unknown buffer");
+    }
+    if (bytes != n) return ffail(WFPG_ERR_INVALID_ARG, "frame_export: size mismatch");
+    if (cudaMemcpyAsync(dst, src, n, cudaMemcpyDeviceToDevice, static_cast<cudaStream_t>(stream)) != cudaSuccess)
+        return ffail(WFPG_ERR_CUDA, "frame_export: copy failed");
+    return WFPG_OK;
+}
+
+}  // extern "C"

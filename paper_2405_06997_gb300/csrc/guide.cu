@@ -6,7 +6,8 @@
 // the N x N cell rays through the SVO -- the top levels staged in shared
 // memory, deeper nodes read as 8-byte records through the read-only path --
 // the field, its blur and its scans stay in shared memory, and only the
-// finished pdf / cdf_row / cdf_marg rows go to global memory.
+// finished pdf / cdf_row / cdf_marg rows go to global memory (or, in the fused
+// variant, only the directions and densities of the bin's own rays).
 //
 // The SVO march returns exactly the leaf that a leaf-by-leaf 3D DDA returns:
 // every boundary time is evaluated afresh as (k - g) / (d * 2^D / S) for an
@@ -49,6 +50,19 @@ struct GuideArgs {
     int blur;
     uint64_t seed;
     uint32_t frame;
+    const uint32_t* frame_dev;  // when set, the frame index is read from device memory
+};
+
+// fused sampling: after a bin's CDF is built in shared memory, every ray of the
+// bin draws its next direction from alpha * field + (1 - alpha) * cosine
+struct FusedArgs {
+    const uint32_t* ray_order;
+    const uint32_t* bin_offset;
+    const float* nrm;   // xyz per ray
+    const float* u;     // 3 uniforms per ray: two for the direction, one for the mixture choice
+    float alpha;
+    float* dir;         // xyz per ray
+    float* pdf;         // mixture density per ray
 };
 
 __device__ __forceinline__ Node load_node(const TraceArgs& T, const Node* s_nodes, uint32_t id) {
@@ -119,6 +133,68 @@ __device__ __forceinline__ int advance_axis(int c, int lo, int size, float g, fl
     return j;
 }
 
+// first index with x[i] > t (N if none) in a non-decreasing shared-memory row
+__device__ __forceinline__ int upper_bound_s(const float* x, int N, float t) {
+    int lo = 0, hi = N;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (x[mid] > t) hi = mid;
+        else lo = mid + 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ float clamp_unit(float x) {
+    if (!(x >= 0.0f)) return 0.0f;
+    return x >= 1.0f ? kOneMinus : x;
+}
+
+// inverse-CDF sample of the piecewise-constant field (row CDFs C, marginal M,
+// all in shared memory); returns the direction and the chosen cell's field
+// value (same arithmetic as guide_sample)
+__device__ __forceinline__ float3 sample_cdf(const float* f, const float* C, const float* M, int N, float u0,
+                                             float u1, float tn, float* fcell) {
+    const float t0 = __fmul_rn(u0, M[N - 1]);
+    const int r = min(upper_bound_s(M, N, t0), N - 1);
+    const float* Cr = C + r * N;
+    const float t1 = __fmul_rn(u1, Cr[N - 1]);
+    const int c = min(upper_bound_s(Cr, N, t1), N - 1);
+    const float mlo = r > 0 ? M[r - 1] : 0.0f, mhi = M[r];
+    const float clo = c > 0 ? Cr[c - 1] : 0.0f, chi = Cr[c];
+    const float beta = clamp_unit(__fdiv_rn(__fsub_rn(t0, mlo), __fsub_rn(mhi, mlo)));
+    const float alpha = clamp_unit(__fdiv_rn(__fsub_rn(t1, clo), __fsub_rn(chi, clo)));
+    const float su = __fsub_rn(__fmul_rn(__fadd_rn((float)c, alpha), tn), 1.0f);
+    const float sv = __fsub_rn(__fmul_rn(__fadd_rn((float)r, beta), tn), 1.0f);
+    *fcell = f[r * N + c];
+    return octa_to_dir(su, sv);
+}
+
+// cell of a direction under the octahedral map (same arithmetic as guide_eval_pdf)
+__device__ __forceinline__ int octa_cell(float3 d, int N) {
+    const float2 uv = dir_to_octa(d.x, d.y, d.z);
+    const float hn = __fmul_rn((float)N, 0.5f);
+    const float a = __fmul_rn(__fadd_rn(uv.x, 1.0f), hn), c = __fmul_rn(__fadd_rn(uv.y, 1.0f), hn);
+    const int i = min((a >= 0.0f) ? (int)a : 0, N - 1);
+    const int j = min((c >= 0.0f) ? (int)c : 0, N - 1);
+    return j * N + i;
+}
+
+// cosine-distributed direction about the unit normal n (orthonormal basis of
+// Duff et al. 2017, "Building an orthonormal basis, revisited")
+__device__ __forceinline__ float3 cosine_dir(float nx, float ny, float nz, float u0, float u1) {
+    const float sg = nz >= 0.0f ? 1.0f : -1.0f;
+    const float a = -1.0f / (sg + nz);
+    const float bb = nx * ny * a;
+    const float tx = 1.0f + sg * nx * nx * a, ty = sg * bb, tz = -sg * nx;
+    const float bx = bb, by = sg + ny * ny * a, bz = -ny;
+    const float r = sqrtf(u0);
+    float sp, cp;
+    sincospif(2.0f * u1, &sp, &cp);
+    const float z = sqrtf(fmaxf(0.0f, 1.0f - u0));
+    return make_float3(r * cp * tx + r * sp * bx + z * nx, r * cp * ty + r * sp * by + z * ny,
+                       r * cp * tz + r * sp * bz + z * nz);
+}
+
 // inclusive scan of a row of N floats in warp order (chunks of 32: rounds
 // k = 1, 2, 4, 8, 16 of x[i] += x[i-k], later chunks add the running total),
 // then a running maximum (exact; keeps the CDF non-decreasing under rounding)
@@ -151,8 +227,9 @@ __device__ __forceinline__ float warp_scan_row(const float* src, float* dst, int
 // kGuideThreads threads work on one bin at a time; kStage: the chunk's cone
 // directions are computed by all threads together into shared memory before
 // the march (otherwise each lane computes its ray's direction when it takes it)
-template <int kGuideThreads, bool kStage>
-__global__ void __launch_bounds__(kGuideThreads) k_guide_build(TraceArgs T, GuideArgs G, const float* __restrict__ pos,
+template <int kGuideThreads, bool kStage, bool kFused>
+__global__ void __launch_bounds__(kGuideThreads) k_guide_build(TraceArgs T, GuideArgs G, FusedArgs F,
+                                                               const float* __restrict__ pos,
                                                                const uint32_t* __restrict__ origin_ray,
                                                                const uint32_t* __restrict__ n_bins_dev,
                                                                uint32_t bin_cap, float* __restrict__ pdf,
@@ -199,7 +276,7 @@ __global__ void __launch_bounds__(kGuideThreads) k_guide_build(TraceArgs T, Guid
         const float gz = __fmul_rn(__fsub_rn(oz, T.lo[2]), T.scale);
         const bool inside = gx >= 0.0f && gx <= fres && gy >= 0.0f && gy <= fres && gz >= 0.0f && gz <= fres;
         const uint64_t jseed = purpose(G.seed, kJitterPurpose);
-        const uint64_t jstream = bin_stream(G.frame, b);
+        const uint64_t jstream = bin_stream(G.frame_dev ? *G.frame_dev : G.frame, b);
         for (int c0 = 0; c0 < NN; c0 += chunk) {
             // ---- directions of this chunk's cells, computed by all threads together
             for (int q = tid; kStage && q < chunk; q += kGuideThreads) {
@@ -436,13 +513,37 @@ __global__ void __launch_bounds__(kGuideThreads) k_guide_build(TraceArgs T, Guid
         __syncthreads();
         const float den = __fmul_rn(marg[N - 1], kFourPi);
         const float nn = (float)NN;
-        float* gp = pdf + (size_t)b * NN;
-        float* gc = cdf_row + (size_t)b * NN;
-        for (int c = tid; c < NN; c += kGuideThreads) {
-            gp[c] = __fdiv_rn(__fmul_rn(field[c], nn), den);
-            gc[c] = tmp[c];
+        if (!kFused) {
+            float* gp = pdf + (size_t)b * NN;
+            float* gc = cdf_row + (size_t)b * NN;
+            for (int c = tid; c < NN; c += kGuideThreads) {
+                gp[c] = __fdiv_rn(__fmul_rn(field[c], nn), den);
+                gc[c] = tmp[c];
+            }
+            for (int j = tid; j < N; j += kGuideThreads) cdf_marg[(size_t)b * N + j] = marg[j];
+        } else {
+            // the bin's rays sample straight from the shared-memory CDF
+            const uint32_t r_lo = F.bin_offset[b], r_hi = F.bin_offset[b + 1];
+            for (uint32_t k = r_lo + tid; k < r_hi; k += kGuideThreads) {
+                const uint32_t ray = F.ray_order[k];
+                const float u0 = F.u[3 * (size_t)ray], u1 = F.u[3 * (size_t)ray + 1], u2 = F.u[3 * (size_t)ray + 2];
+                const float nx = F.nrm[3 * (size_t)ray], ny = F.nrm[3 * (size_t)ray + 1], nz = F.nrm[3 * (size_t)ray + 2];
+                float3 d;
+                float pg;
+                if (u2 < F.alpha) {
+                    d = sample_cdf(field, tmp, marg, N, u0, u1, tn, &pg);
+                    pg = __fdiv_rn(__fmul_rn(pg, nn), den);
+                } else {
+                    d = cosine_dir(nx, ny, nz, u0, u1);
+                    pg = __fdiv_rn(__fmul_rn(field[octa_cell(d, N)], nn), den);
+                }
+                const float cs = fmaxf(0.0f, nx * d.x + ny * d.y + nz * d.z);
+                F.dir[3 * (size_t)ray] = d.x;
+                F.dir[3 * (size_t)ray + 1] = d.y;
+                F.dir[3 * (size_t)ray + 2] = d.z;
+                F.pdf[ray] = F.alpha * pg + (1.0f - F.alpha) * cs * 0.31830988618379067f;
+            }
         }
-        for (int j = tid; j < N; j += kGuideThreads) cdf_marg[(size_t)b * N + j] = marg[j];
         __syncthreads();
     }
 }
@@ -561,11 +662,11 @@ static size_t guide_smem_bytes(uint32_t smem_nodes, int N, int D, int threads, b
            sizeof(float) * ((stage ? 6 * chunk : 0) + 2 * NN + 2 * (size_t)N);
 }
 
-template <int kThreads, bool kStage>
-static int launch_guide(const TraceArgs& T, const GuideArgs& G, const float* pos, const uint32_t* origin_ray,
-                        const uint32_t* n_bins_dev, uint32_t bin_cap, float* pdf, float* cdf_row, float* cdf_marg,
-                        uint32_t* status, int D, cudaStream_t st) {
-    auto kernel = k_guide_build<kThreads, kStage>;
+template <int kThreads, bool kStage, bool kFused>
+static int launch_guide(const TraceArgs& T, const GuideArgs& G, const FusedArgs& F, const float* pos,
+                        const uint32_t* origin_ray, const uint32_t* n_bins_dev, uint32_t bin_cap, float* pdf,
+                        float* cdf_row, float* cdf_marg, uint32_t* status, int D, cudaStream_t st) {
+    auto kernel = k_guide_build<kThreads, kStage, kFused>;
     const size_t smem = guide_smem_bytes(T.smem_nodes, G.N, D, kThreads, kStage);
     if (smem > 48 * 1024 &&
         cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
@@ -576,50 +677,77 @@ static int launch_guide(const TraceArgs& T, const GuideArgs& G, const float* pos
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, smem);
     if (per_sm < 1) return WFPG_ERR_INVALID_ARG;  // the field does not fit in shared memory
     const uint32_t grid = (uint32_t)std::min<uint64_t>(bin_cap, (uint64_t)sms * per_sm);
-    WFPG_LAUNCH(kernel, grid, kThreads, smem, st, T, G, pos, origin_ray, n_bins_dev, bin_cap, pdf, cdf_row, cdf_marg,
-                status);
+    WFPG_LAUNCH(kernel, grid, kThreads, smem, st, T, G, F, pos, origin_ray, n_bins_dev, bin_cap, pdf, cdf_row,
+                cdf_marg, status);
     return cudaGetLastError() == cudaSuccess ? WFPG_OK : WFPG_ERR_CUDA;
 }
 
-int guide_build_impl(const wfpg_svo* s, const float* pos, const uint32_t* origin_ray, const uint32_t* n_bins_dev,
-                     uint32_t bin_cap, const wfpg_guide_params* p, float* pdf, float* cdf_row, float* cdf_marg,
-                     cudaStream_t st) {
-    if (bin_cap == 0) return WFPG_OK;
-    TraceArgs T;
-    T.node = s->node;
-    T.normal = s->normal;
-    T.value = s->value;
-    T.D = s->D;
-    for (int a = 0; a < 3; ++a) T.lo[a] = s->lo[a];
-    T.scale = s->scale;
-    T.S = s->S;
-    T.t_skip = p->t_skip;
-    T.omega = kFourPi / (float)(p->N * p->N);
-    T.cos_weight = p->cos_weight;
+static void trace_setup(const wfpg_svo* s, const wfpg_guide_params* p, TraceArgs* T, GuideArgs* G,
+                        const uint32_t* frame_dev) {
+    T->node = s->node;
+    T->normal = s->normal;
+    T->value = s->value;
+    T->D = s->D;
+    for (int a = 0; a < 3; ++a) T->lo[a] = s->lo[a];
+    T->scale = s->scale;
+    T->S = s->S;
+    T->t_skip = p->t_skip;
+    T->omega = kFourPi / (float)(p->N * p->N);
+    T->cos_weight = p->cos_weight;
     const int top = s->D < kSmemTopLevels ? s->D : kSmemTopLevels;
-    T.smem_nodes = s->level_off[top + 1];
-    GuideArgs G;
-    G.N = p->N;
-    G.eps = p->eps;
-    G.jitter = p->jitter;
-    G.blur = p->blur;
-    G.seed = p->seed;
-    G.frame = p->frame;
+    T->smem_nodes = s->level_off[top + 1];
+    G->N = p->N;
+    G->eps = p->eps;
+    G->jitter = p->jitter;
+    G->blur = p->blur;
+    G->seed = p->seed;
+    G->frame = p->frame;
+    G->frame_dev = frame_dev;
+}
+
+template <bool kFused>
+static int dispatch_guide(const wfpg_svo* s, const wfpg_guide_params* p, const TraceArgs& T, const GuideArgs& G,
+                          const FusedArgs& F, const float* pos, const uint32_t* origin_ray,
+                          const uint32_t* n_bins_dev, uint32_t bin_cap, float* pdf, float* cdf_row, float* cdf_marg,
+                          cudaStream_t st) {
     const bool small = p->N <= 16;
     const int threads = p->block ? p->block : (small ? kGuideDefaultThreadsSmall : kGuideDefaultThreadsLarge);
     const bool stage = p->stage == 0 ? small : p->stage > 0;
     const int D = s->D;
-#define WFPG_GUIDE_CASE(TH)                                                                                       \
-    if (threads == TH)                                                                                            \
-        return stage ? launch_guide<TH, true>(T, G, pos, origin_ray, n_bins_dev, bin_cap, pdf, cdf_row, cdf_marg, \
-                                              s->status, D, st)                                                   \
-                     : launch_guide<TH, false>(T, G, pos, origin_ray, n_bins_dev, bin_cap, pdf, cdf_row,          \
-                                               cdf_marg, s->status, D, st);
+#define WFPG_GUIDE_CASE(TH)                                                                                        \
+    if (threads == TH)                                                                                             \
+        return stage ? launch_guide<TH, true, kFused>(T, G, F, pos, origin_ray, n_bins_dev, bin_cap, pdf, cdf_row, \
+                                                      cdf_marg, s->status, D, st)                                  \
+                     : launch_guide<TH, false, kFused>(T, G, F, pos, origin_ray, n_bins_dev, bin_cap, pdf,         \
+                                                       cdf_row, cdf_marg, s->status, D, st);
     WFPG_GUIDE_CASE(64)
     WFPG_GUIDE_CASE(128)
     WFPG_GUIDE_CASE(256)
 #undef WFPG_GUIDE_CASE
     return WFPG_ERR_INVALID_ARG;
+}
+
+int guide_build_impl(const wfpg_svo* s, const float* pos, const uint32_t* origin_ray, const uint32_t* n_bins_dev,
+                     uint32_t bin_cap, const wfpg_guide_params* p, float* pdf, float* cdf_row, float* cdf_marg,
+                     cudaStream_t st, const uint32_t* frame_dev) {
+    if (bin_cap == 0) return WFPG_OK;
+    TraceArgs T;
+    GuideArgs G;
+    trace_setup(s, p, &T, &G, frame_dev);
+    FusedArgs F{};
+    return dispatch_guide<false>(s, p, T, G, F, pos, origin_ray, n_bins_dev, bin_cap, pdf, cdf_row, cdf_marg, st);
+}
+
+int guide_fused_impl(const wfpg_svo* s, const float* pos, const float* nrm, const uint32_t* origin_ray,
+                     const uint32_t* n_bins_dev, uint32_t bin_cap, const uint32_t* ray_order,
+                     const uint32_t* bin_offset, const float* u, float alpha, const wfpg_guide_params* p, float* dir,
+                     float* pdf_out, cudaStream_t st, const uint32_t* frame_dev) {
+    if (bin_cap == 0) return WFPG_OK;
+    TraceArgs T;
+    GuideArgs G;
+    trace_setup(s, p, &T, &G, frame_dev);
+    FusedArgs F{ray_order, bin_offset, nrm, u, alpha, dir, pdf_out};
+    return dispatch_guide<true>(s, p, T, G, F, pos, origin_ray, n_bins_dev, bin_cap, nullptr, nullptr, nullptr, st);
 }
 
 int field_pdf_impl(const float* field, int N, const uint32_t* n_bins_dev, uint32_t bin_cap, float* pdf,

@@ -4,7 +4,7 @@
 // scene's true incident radiance.
 #include <string>
 
-#include "common.cuh"
+#include "cast.cuh"
 
 namespace wfpg {
 
@@ -17,58 +17,14 @@ __global__ void __launch_bounds__(256) k_cast(const float* __restrict__ quads, u
     if (i >= n) return;
     const float ox = o[3 * (size_t)i], oy = o[3 * (size_t)i + 1], oz = o[3 * (size_t)i + 2];
     const float dx = d[3 * (size_t)i], dy = d[3 * (size_t)i + 1], dz = d[3 * (size_t)i + 2];
-    const float oo[3] = {ox, oy, oz}, dd[3] = {dx, dy, dz};
-    float best = __int_as_float(0x7f800000);
-    uint32_t bp = kNone;
-    for (uint32_t q = 0; q < nq; ++q) {
-        const float* Q = quads + 8 * (size_t)q;
-        const int a = (int)Q[0], b = (a + 1) % 3, c = (a + 2) % 3;
-        if (dd[a] == 0.0f) continue;
-        const float t = (Q[1] - oo[a]) / dd[a];
-        if (!(t > tmin) || t >= best) continue;
-        const float pb = oo[b] + t * dd[b], pc = oo[c] + t * dd[c];
-        if (pb >= Q[2] && pb <= Q[3] && pc >= Q[4] && pc <= Q[5]) {
-            best = t;
-            bp = q;
-        }
-    }
-    for (uint32_t s = 0; s < ns; ++s) {
-        const float* S = spheres + 4 * (size_t)s;
-        const float cx = ox - S[0], cy = oy - S[1], cz = oz - S[2];
-        const float bq = dx * cx + dy * cy + dz * cz;
-        const float cq = cx * cx + cy * cy + cz * cz - S[3] * S[3];
-        const float disc = bq * bq - cq;
-        if (disc < 0.0f) continue;
-        const float sq = sqrtf(disc);
-        float t = -bq - sq;
-        if (!(t > tmin)) t = -bq + sq;
-        if (t > tmin && t < best) {
-            best = t;
-            bp = nq + s;
-        }
-    }
-    t_out[i] = bp == kNone ? -1.0f : best;
-    prim_out[i] = bp;
+    const Hit h = cast_closest(quads, nq, spheres, ns, ox, oy, oz, dx, dy, dz, tmin);
+    t_out[i] = h.t;
+    prim_out[i] = h.prim;
     if (nrm_out) {
-        float nx = 0.f, ny = 0.f, nz = 0.f;
-        if (bp != kNone && bp < nq) {
-            const float* Q = quads + 8 * (size_t)bp;
-            const int a = (int)Q[0];
-            (a == 0 ? nx : (a == 1 ? ny : nz)) = Q[6];
-        } else if (bp != kNone) {
-            const float* S = spheres + 4 * (size_t)(bp - nq);
-            nx = (ox + best * dx - S[0]) / S[3];
-            ny = (oy + best * dy - S[1]) / S[3];
-            nz = (oz + best * dz - S[2]) / S[3];
-        }
-        if (nx * dx + ny * dy + nz * dz > 0.0f) {  // face the incoming ray
-            nx = -nx;
-            ny = -ny;
-            nz = -nz;
-        }
-        nrm_out[3 * (size_t)i] = nx;
-        nrm_out[3 * (size_t)i + 1] = ny;
-        nrm_out[3 * (size_t)i + 2] = nz;
+        const float3 nn = hit_normal(quads, nq, spheres, h, ox, oy, oz, dx, dy, dz);
+        nrm_out[3 * (size_t)i] = nn.x;
+        nrm_out[3 * (size_t)i + 1] = nn.y;
+        nrm_out[3 * (size_t)i + 2] = nn.z;
     }
 }
 

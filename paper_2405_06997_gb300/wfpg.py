@@ -55,12 +55,34 @@ class SvoInfo(C.Structure):
 
 class BinParams(C.Structure):
     _fields_ = [("mode", I32), ("l_min", I32), ("c_ray", U32), ("n_sizes", U32), ("seed", U64),
-                ("frame", U32)]
+                ("frame", U32), ("n_dev", P)]
 
 
 class GuideParams(C.Structure):
     _fields_ = [("N", I32), ("eps", F), ("jitter", I32), ("blur", I32), ("t_skip", F),
                 ("cos_weight", I32), ("seed", U64), ("frame", U32), ("block", I32), ("stage", I32)]
+
+
+FRAME_MAX_DEPTH = 8
+
+
+class Camera(C.Structure):
+    _fields_ = [("eye", F * 3), ("forward", F * 3), ("up", F * 3), ("vfov_deg", F), ("width", U32),
+                ("height", U32)]
+
+
+class FrameParams(C.Structure):
+    _fields_ = [("max_depth", I32), ("rr_depth", I32), ("alpha", F), ("l_min", I32), ("c_ray", U32),
+                ("guide", GuideParams), ("seed", U64), ("update", I32)]
+
+
+class FrameStats(C.Structure):
+    _fields_ = [("frames", U64), ("paths", U32 * (FRAME_MAX_DEPTH + 1)), ("bins", U32 * (FRAME_MAX_DEPTH + 1)),
+                ("records", U32), ("guided_samples", U64), ("status", U32), ("kernels_per_frame", C.c_ulonglong)]
+
+
+FRAME_BUF = {"vT": 0, "vLe": 1, "vpos": 2, "vwo": 3, "nv": 4, "rec_pos": 5, "rec_wout": 6, "rec_L": 7,
+             "rec_src": 8, "q_pos": 9, "q_nrm": 10, "q_u": 11, "q_dir": 12, "q_pdf": 13, "q_path": 14}
 
 
 def library_path() -> str:
@@ -85,10 +107,21 @@ def lib():
             "bin_rays": [P, P, P, U32, P, P, P, P, P, P, U32, P, P, SZ, P],
             "guide_build_pdf": [P, P, P, P, U32, P, P, P, P, P],
             "guide_sample": [P, P, P, I32, U32, P, P, U32, P, P, P, P],
+            "guide_build_sample": [P, P, P, P, P, U32, P, P, P, F, P, P, P, P],
             "guide_eval_pdf": [P, I32, U32, P, P, U32, P, P],
             "svo_export": [P, P, P, P, P, P, P, P, P, P],
             "svo_export_exitance": [P, P, P, P, P, P, P],
             "wfpg_svo_status": [P, P, I32, P],
+            "frame_create": [P, P, P, P, P, P, P, P],
+            "frame_destroy": [P],
+            "frame_run": [P, U32, I32, P],
+            "frame_set_params": [P, P],
+            "frame_get_params": [P, P],
+            "frame_reset_image": [P, P],
+            "frame_image": [P, P, P, P],
+            "frame_stats": [P, P, P],
+            "frame_autotune": [P, P, I32, U32, P, P, P],
+            "frame_export": [P, I32, P, SZ, P],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -287,6 +320,33 @@ def guide_build_pdf(svo: SVO, pos, origin_ray=None, n_bins=None, bin_cap=None, *
                                  _ptr(cr, torch.float32, bin_cap * N * N),
                                  _ptr(cm, torch.float32, bin_cap * N), _stream(stream)))
     return pdf, cr, cm
+
+
+def guide_build_sample(svo: SVO, pos, nrm, bins, u, *, alpha=0.5, N=16, eps=1e-2, jitter=False, blur=False,
+                       t_skip=None, cos_weight=False, seed=1, frame=0, block=0, stage=0, out=None,
+                       stream=None):
+    """guide_build_pdf + one-sample mixture sampling in one launch.  bins is the
+    dict bin_rays returns; u holds 3 uniforms per ray.  Returns (dir [n,3],
+    mixture pdf [n])."""
+    n = pos.shape[0]
+    bin_cap = bins["origin_ray"].numel()
+    if t_skip is None:
+        t_skip = default_t_skip(svo.size, svo.depth)
+    if out is None:
+        out = (torch.empty((n, 3), dtype=torch.float32, device=pos.device),
+               torch.empty(n, dtype=torch.float32, device=pos.device))
+    d, pm = out
+    p = GuideParams(N=N, eps=eps, jitter=int(jitter), blur=int(blur), t_skip=t_skip,
+                    cos_weight=int(cos_weight), seed=seed, frame=frame, block=block, stage=stage)
+    _check(lib().guide_build_sample(svo.handle, _ptr(pos, torch.float32, 3 * n, "pos"),
+                                    _ptr(nrm, torch.float32, 3 * n, "nrm"),
+                                    _ptr(bins["origin_ray"], torch.int32, bin_cap),
+                                    _ptr(bins["n_bins"], torch.int32, 1), bin_cap,
+                                    _ptr(bins["ray_order"], torch.int32, n),
+                                    _ptr(bins["bin_offset"], torch.int32, bin_cap + 1),
+                                    _ptr(u, torch.float32, 3 * n, "u"), alpha, C.byref(p),
+                                    _ptr(d, torch.float32, 3 * n), _ptr(pm, torch.float32, n), _stream(stream)))
+    return d, pm
 
 
 def guide_sample(pdf, cdf_row, cdf_marg, N, bin_of_ray, u, out=None, stream=None):
@@ -503,3 +563,110 @@ def cast_rays(quads, spheres, o, d, tmin=1e-5, with_normal=True, stream=None):
               _ptr(t, torch.float32), _ptr(prim, torch.int32), _ptr(nrm, torch.float32) if with_normal else None,
               _stream(stream)))
     return t, prim, nrm
+
+
+class Frame:
+    """Batched wavefront frame over an SVO (frame_create .. frame_destroy).
+
+    scene: paper_2405_06997_gb300.inputs.Scene (uploaded here); the SVO must
+    outlive the frame.  Camera: eye, unit forward and up, vertical fov,
+    width x height.  All work runs in libwfpg.so; run(use_graph=True)
+    replays one captured CUDA graph per frame."""
+
+    def __init__(self, svo: SVO, scene, *, eye, forward=(0.0, 0.0, 1.0), up=(0.0, 1.0, 0.0), vfov=60.0,
+                 width=1920, height=1080, max_depth=4, rr_depth=2, alpha=0.5, l_min=2, c_ray=512, N=32,
+                 eps=1e-2, jitter=True, blur=True, cos_weight=False, block=0, stage=0, seed=1, update=True,
+                 device="cuda", stream=None):
+        self.svo = svo
+        self._q = torch.as_tensor(np.ascontiguousarray(scene.quads, np.float32).reshape(-1, 8), device=device)
+        self._s = torch.as_tensor(np.ascontiguousarray(scene.spheres, np.float32).reshape(-1, 4), device=device)
+        self._e = torch.as_tensor(np.ascontiguousarray(scene.emission, np.float32), device=device)
+        self._a = torch.as_tensor(np.ascontiguousarray(scene.albedo, np.float32), device=device)
+        self._scene = Scene(quads=_ptr(self._q), n_quads=self._q.shape[0], spheres=_ptr(self._s),
+                            n_spheres=self._s.shape[0], lo=(F * 3)(*[float(v) for v in scene.lo]),
+                            size=float(scene.size))
+        self.width, self.height = int(width), int(height)
+        self.cam = Camera(eye=(F * 3)(*eye), forward=(F * 3)(*forward), up=(F * 3)(*up), vfov_deg=vfov,
+                          width=self.width, height=self.height)
+        gp = GuideParams(N=N, eps=eps, jitter=int(jitter), blur=int(blur),
+                         t_skip=default_t_skip(svo.size, svo.depth), cos_weight=int(cos_weight), seed=seed,
+                         frame=0, block=block, stage=stage)
+        self.params = FrameParams(max_depth=max_depth, rr_depth=rr_depth, alpha=alpha, l_min=l_min, c_ray=c_ray,
+                                  guide=gp, seed=seed, update=int(update))
+        self.device = device
+        h = P()
+        _check(lib().frame_create(svo.handle, C.byref(self._scene), _ptr(self._e), _ptr(self._a),
+                                  C.byref(self.cam), C.byref(self.params), C.byref(h), _stream(stream)))
+        self.handle = h
+        self.max_depth_cap = max_depth
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and _lib is not None:
+            _lib.frame_destroy(h)
+            self.handle = None
+
+    @property
+    def pixels(self):
+        return self.width * self.height
+
+    def run(self, n_frames=1, use_graph=True, stream=None):
+        _check(lib().frame_run(self.handle, n_frames, int(use_graph), _stream(stream)))
+
+    def set_params(self, **kw):
+        p = FrameParams()
+        _check(lib().frame_get_params(self.handle, C.byref(p)))
+        for k, v in kw.items():
+            if hasattr(p.guide, k) and k not in ("seed",):
+                setattr(p.guide, k, v)
+            else:
+                setattr(p, k, v)
+        _check(lib().frame_set_params(self.handle, C.byref(p)))
+        self.params = p
+
+    def get_params(self):
+        p = FrameParams()
+        _check(lib().frame_get_params(self.handle, C.byref(p)))
+        return p
+
+    def reset_image(self, stream=None):
+        _check(lib().frame_reset_image(self.handle, _stream(stream)))
+
+    def image(self, stream=None):
+        """(mean, variance of one estimate) per pixel, [H, W] float32 tensors."""
+        m = torch.empty(self.pixels, dtype=torch.float32, device=self.device)
+        v = torch.empty(self.pixels, dtype=torch.float32, device=self.device)
+        _check(lib().frame_image(self.handle, _ptr(m), _ptr(v), _stream(stream)))
+        return m.view(self.height, self.width), v.view(self.height, self.width)
+
+    def stats(self, stream=None):
+        st = FrameStats()
+        _check(lib().frame_stats(self.handle, C.byref(st), _stream(stream)))
+        d = self.get_params().max_depth
+        return {"frames": int(st.frames), "paths": [int(x) for x in st.paths[:d]],
+                "bins": [int(x) for x in st.bins[:d]], "records": int(st.records),
+                "guided_samples": int(st.guided_samples), "status": int(st.status),
+                "kernels_per_frame": int(st.kernels_per_frame)}
+
+    def autotune(self, N_candidates=(16, 32, 64), frames=4, stream=None):
+        """Native autotuner: fastest tile per N, then the N with the least
+        variance x time.  Returns (chosen params dict, ms per frame)."""
+        arr = (I32 * len(N_candidates))(*N_candidates)
+        p = FrameParams()
+        ms = F()
+        _check(lib().frame_autotune(self.handle, arr, len(N_candidates), frames, C.byref(p), C.byref(ms),
+                                    _stream(stream)))
+        self.params = p
+        return {"N": p.guide.N, "block": p.guide.block, "stage": p.guide.stage}, float(ms.value)
+
+    def export(self, what, stream=None):
+        """Copy of an internal buffer (see WFPG_FRAME_BUF_* in include/wfpg.h)."""
+        P_ = self.pixels
+        V = (self.max_depth_cap + 1) * P_
+        shapes = {"vT": (V,), "vLe": (V,), "vpos": (V, 3), "vwo": (V, 3), "nv": (P_,), "rec_pos": (V, 3),
+                  "rec_wout": (V, 3), "rec_L": (V,), "rec_src": (V,), "q_pos": (P_, 3), "q_nrm": (P_, 3),
+                  "q_u": (P_, 3), "q_dir": (P_, 3), "q_pdf": (P_,), "q_path": (P_,)}
+        ints = ("nv", "rec_src", "q_path")
+        t = torch.empty(shapes[what], dtype=torch.int32 if what in ints else torch.float32, device=self.device)
+        _check(lib().frame_export(self.handle, FRAME_BUF[what], _ptr(t), t.numel() * 4, _stream(stream)))
+        return t

@@ -36,3 +36,30 @@ def test_last_error_is_empty_string_initially():
     lib = ctypes.CDLL(build.build())
     lib.wfpg_last_error.restype = ctypes.c_char_p
     assert lib.wfpg_last_error() == b""
+
+
+def test_ctypes_structs_match_the_header(tmp_path):
+    """The binding's ctypes structures have the C layout (size and offset of
+    every field) that include/wfpg.h gives."""
+    import subprocess
+
+    from paper_2405_06997_gb300 import wfpg as W
+
+    structs = {"wfpg_scene": W.Scene, "wfpg_bin_params": W.BinParams, "wfpg_guide_params": W.GuideParams,
+               "wfpg_camera": W.Camera, "wfpg_frame_params": W.FrameParams, "wfpg_frame_stats": W.FrameStats}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "wfpg.h"', "int main(void) {"]
+    for cname, cls in structs.items():
+        lines.append(f'printf("{cname} %zu\\n", sizeof({cname}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'printf("{cname}.{fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = dict(line.rsplit(" ", 1) for line in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                              check=True).stdout.split("\n") if line)
+    for cname, cls in structs.items():
+        assert int(out[cname]) == ctypes.sizeof(cls), cname
+        for fname, _ in cls._fields_:
+            assert int(out[f"{cname}.{fname}"]) == getattr(cls, fname).offset, (cname, fname)
