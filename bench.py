@@ -55,6 +55,10 @@ def parse():
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-proposal section")
     ap.add_argument("--learned-steps", type=int, default=500, help="online training steps (65,536 bins each)")
     ap.add_argument("--learned-frames", type=int, default=16, help="frames of the equal-spp comparison")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-frame section")
+    ap.add_argument("--batched-frames", type=int, default=20, help="timed frames of the batched section")
+    ap.add_argument("--batched-only", action="store_true",
+                    help="run only the batched section with a fixed N = 32 tile (for profiling) and print it")
     return ap.parse_args()
 
 
@@ -350,6 +354,32 @@ def run_gpu(args, world, rank, local):
         b.synchronize()
         e2e_ms.append(a.elapsed_time(b))
     e2e_v = rays_all / (max_over_ranks(statistics.mean(e2e_ms), world) / 1e3)
+
+    # the same frame with GuideRays fused as Alg. 3 states it (field, PDF and
+    # CDFs in shared memory; each ray draws from alpha * guided + (1 - alpha) *
+    # cosine with its exact density): accumulate + bin_rays + guide_build_sample
+    u3 = torch.cat([inp["u"], T(inputs_uniforms(w.seed + 5, (R, 1)))], dim=1).contiguous()
+    fused_out = (torch.empty((R, 3), dtype=torch.float32, device=dev), torch.empty(R, dtype=torch.float32, device=dev))
+
+    def fused_step(frame):
+        W.svo_accumulate(svo, inp["rec_pos"], inp["rec_wout"], inp["rec_L"])
+        W.bin_rays(svo, inp["ray_pos"], inp["ray_nrm"], mode=W.BIN_RUNS, sizes=inp["sizes"], seed=w.seed,
+                   frame=frame, bin_cap=B, out=binout, workspace=ws)
+        W.guide_build_sample(svo, inp["ray_pos"], inp["ray_nrm"], binout, u3, alpha=0.5, N=N, jitter=True,
+                             blur=True, seed=w.seed, frame=frame, out=fused_out)
+
+    for k in range(3):
+        fused_step(3000 + k)
+    fused_ms = []
+    for k in range(args.steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fused_step(4000 + k)
+        b.record()
+        b.synchronize()
+        fused_ms.append(a.elapsed_time(b))
+    fused_v = rays_all / (max_over_ranks(statistics.mean(fused_ms), world) / 1e3)
     clk = clocks.stop() if clocks else None
 
     if rank != 0:
@@ -359,7 +389,7 @@ def run_gpu(args, world, rank, local):
     gms = statistics.mean(guide_ms)
     alg = trace_algorithmic_bytes(w, B, N)
     achieved = alg["bytes"] / (gms / 1e3) / 1e9
-    traffic = read_profile_traffic()
+    traffic, issue = read_profile_traffic()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
@@ -372,14 +402,18 @@ def run_gpu(args, world, rank, local):
         "status": status,
         "gpu_launches": launches,
         "e2e": {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "fused_step": {"value": fused_v, "unit": UNIT, "ms_per_step": statistics.mean(fused_ms),
+                       "calls": "svo_accumulate + bin_rays + guide_build_sample (alpha 0.5)"},
         "roofline": {"kernel": "k_guide_build", "bound": "hbm", "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                      "peak_kind": peak_kind, "algorithmic_bytes": alg["bytes"],
-                     "algorithmic_model": alg["model"]},
+                     "algorithmic_model": alg["model"], "ncu": issue},
         "clocks": clk,
     }
     if not args.no_learned:
         line["learned"] = learned_section(args, w, svo)
+    if not args.no_batched:
+        line["batched"] = batched_section(args)
     if not args.no_cpu_baseline:
         t_frame, detail = oracle_frame_time(w, mis, args.cpu_bins)
         line["cpu_baseline"] = {
@@ -411,6 +445,57 @@ def learned_section(args, w, svo):
             "equal_spp": cmp, "mlp_status": tr.mlp.status()}
 
 
+def inputs_uniforms(seed, shape):
+    from paper_2405_06997_gb300 import inputs
+    return inputs.uniforms24(seed, shape)
+
+
+def batched_section(args, autotune=True):
+    """The batched wavefront frame: the closed box of the small workload
+    (SVO depth 6, seeded with its 100k records) seen from inside at 1920x1080,
+    4 guided bounces with Russian roulette from the second hit, Eq. 5 records
+    of every vertex accumulated after each frame, Partition-S bins (l_min 2,
+    c_ray 512), everything in one CUDA graph per frame; N and the field
+    kernel's tile picked by the native autotuner."""
+    import torch
+    from paper_2405_06997_gb300 import inputs, wfpg as W
+    w = inputs.tiny_box(args.seed)
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    svo = W.svo_from_scene(w.scene, w.depth)
+    W.svo_accumulate(svo, T(w.rec_pos), T(w.rec_wout), T(w.rec_L))
+    f = W.Frame(svo, w.scene, eye=(0.5, 0.5, 0.05), forward=(0.0, 0.0, 1.0), up=(0.0, 1.0, 0.0), vfov=70.0,
+                width=1920, height=1080, max_depth=4, rr_depth=2, alpha=0.5, l_min=2, c_ray=512, N=32,
+                seed=args.seed)
+    t0 = time.perf_counter()
+    choice, tune_ms = f.autotune((16, 32, 64), frames=4) if autotune else ({"N": 32, "block": 0, "stage": 0}, None)
+    tune_s = time.perf_counter() - t0
+    f.run(3)
+    f.reset_image()
+    torch.cuda.synchronize()
+    launches0 = W.kernel_launches()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    f.run(args.batched_frames)
+    b.record()
+    b.synchronize()
+    ms = a.elapsed_time(b) / args.batched_frames
+    st = f.stats()
+    m, v = f.image()
+    return {"workload": "closed box (D 6, 100k seed records), camera inside at (0.5, 0.5, 0.05) looking +z, "
+                        "vfov 70, 1920x1080, 4 guided bounces, RR from vertex 2 (survival min(0.95, albedo)), "
+                        "alpha 0.5 guided / 0.5 cosine, Partition-S l_min 2 c_ray 512, jitter + blur",
+            "autotune": {"choice": choice, "ms_per_frame": tune_ms, "seconds": tune_s,
+                         "candidates": {"N": [16, 32, 64], "block": [64, 128, 256], "staged": [True, False]}},
+            "frames": args.batched_frames, "ms_per_frame": ms,
+            "guided_samples_per_s": st["guided_samples"] / (ms * args.batched_frames / 1e3),
+            "paths_per_s": f.pixels / (ms / 1e3),
+            "paths_per_depth": st["paths"], "bins_per_depth": st["bins"], "records_per_frame": st["records"],
+            "graph_kernels_per_frame": st["kernels_per_frame"],
+            "gpu_launches": W.kernel_launches() - launches0,
+            "mean_pixel_variance": float(v.double().mean()), "mean_radiance": float(m.double().mean()),
+            "status": st["status"], "l2": "working set (path state ~0.6 GB) larger than L2"}
+
+
 def trace_algorithmic_bytes(w, B, N, sample_bins=8):
     """Bytes the field kernel must move for one launch: its outputs (pdf,
     cdf_row, cdf_marg: B (2 N^2 + N) 4 B) plus, per cone ray, one 8-byte node
@@ -431,18 +516,30 @@ def trace_algorithmic_bytes(w, B, N, sample_bins=8):
 
 
 def read_profile_traffic():
-    """DRAM bytes per launch of k_guide_build from the committed ncu summary, if any."""
+    """DRAM bytes per launch of k_guide_build (and its issue counters) from the
+    committed ncu summary -- only while the kernel source is the one captured."""
+    import hashlib
     path = os.path.join(ROOT, "profiles", "k_guide_build_frame1080p.json")
-    if os.path.exists(path):
-        with open(path) as f:
-            return json.load(f).get("dram_bytes_per_launch")
-    return None
+    if not os.path.exists(path):
+        return None, None
+    with open(path) as f:
+        d = json.load(f)
+    with open(os.path.join(ROOT, d["source"]), "rb") as f:
+        if hashlib.sha256(f.read()).hexdigest() != d["source_sha256"]:
+            return None, None
+    return d["dram_bytes_per_launch"], {"issue_active_pct": d["issue_active_pct"],
+                                        "active_lanes_per_warp_instruction": d["active_lanes_per_warp_instruction"],
+                                        "limiter": "instruction issue with divergence (DRAM well below peak)"}
 
 
 def main():
     args = parse()
     world, rank, local = dist_init(args.gpus)
-    if args.impl == "reference":
+    if args.batched_only:
+        import torch
+        torch.cuda.set_device(local)
+        print(json.dumps(batched_section(args, autotune=False)))
+    elif args.impl == "reference":
         run_reference(args, world, rank)
     else:
         run_gpu(args, world, rank, local)

@@ -219,6 +219,8 @@ typedef struct wfpg_guide_params {
     uint32_t frame;    /* jitter random stream */
     int block;         /* tuning: threads that work on one bin (64, 128, 256; 0 = default) */
     int stage;         /* tuning: 1 stage cone directions in shared memory, -1 do not, 0 = default */
+    uint32_t split;    /* guide_build_sample: bins with more rays than this are sampled by a second,
+                          GPU-wide launch (0 = default 2048, 0xFFFFFFFF = never); results do not change */
 } wfpg_guide_params;
 
 /*
@@ -255,14 +257,22 @@ WFPG_API int guide_build_pdf(const wfpg_svo* svo, const float* pos, const uint32
  * alpha * field density + (1 - alpha) * max(0, cos) / pi there (the field
  * density of a cosine sample is its cell's, as guide_eval_pdf gives).
  * pos, nrm, u: device, [n][3]; bins as bin_rays writes them; alpha in [0, 1].
+ * A bin with more than p->split rays (a Zipf head bin can hold a large share
+ * of the frame) copies its field and CDFs to a workspace slot and its rays are
+ * drawn by a second launch over the whole GPU with the same arithmetic.
  * Rays of bins >= min(*n_bins_dev, bin_cap) are not written.  Errors: invalid
- * N / eps / alpha / block, or a null array, give WFPG_ERR_INVALID_ARG.
+ * N / eps / alpha / block, or a null array, give WFPG_ERR_INVALID_ARG; a
+ * workspace smaller than guide_build_sample_workspace_size gives
+ * WFPG_ERR_CAPACITY.
  */
 WFPG_API int guide_build_sample(const wfpg_svo* svo, const float* pos, const float* nrm,
                                 const uint32_t* origin_ray, const uint32_t* n_bins_dev, uint32_t bin_cap,
                                 const uint32_t* ray_order, const uint32_t* bin_offset, const float* u,
-                                float alpha, const wfpg_guide_params* p, float* dir, float* pdf_out,
-                                void* stream);
+                                uint32_t n, float alpha, const wfpg_guide_params* p, float* dir, float* pdf_out,
+                                void* workspace, size_t ws_bytes, void* stream);
+/* Device workspace guide_build_sample needs for n rays (spill slots of the
+ * bins larger than p->split: their fields and CDFs). */
+WFPG_API int guide_build_sample_workspace_size(int N, uint32_t n, uint32_t split, size_t* bytes);
 
 /*
  * guide_sample -- the guided branch of Alg. 3's sampling step: inverse-CDF

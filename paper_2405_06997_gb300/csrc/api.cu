@@ -25,7 +25,9 @@ int guide_build_impl(const wfpg_svo* s, const float* pos, const uint32_t* origin
 int guide_fused_impl(const wfpg_svo* s, const float* pos, const float* nrm, const uint32_t* origin_ray,
                      const uint32_t* n_bins_dev, uint32_t bin_cap, const uint32_t* ray_order,
                      const uint32_t* bin_offset, const float* u, float alpha, const wfpg_guide_params* p, float* dir,
-                     float* pdf_out, cudaStream_t st, const uint32_t* frame_dev = nullptr);
+                     float* pdf_out, uint32_t n, void* workspace, size_t ws_bytes, cudaStream_t st,
+                     const uint32_t* frame_dev = nullptr);
+size_t guide_fused_workspace_bytes(int N, uint32_t n, uint32_t split);
 int guide_sample_impl(const float* pdf, const float* cdf_row, const float* cdf_marg, int N, uint32_t bin_cap,
                       const uint32_t* bin_of_ray, const float* u, uint32_t n, float* dir, float* pdf_out,
                       uint32_t* cell, cudaStream_t st);
@@ -190,10 +192,18 @@ int guide_build_pdf(const wfpg_svo* s, const float* pos, const uint32_t* origin_
     return WFPG_OK;
 }
 
+int guide_build_sample_workspace_size(int N, uint32_t n, uint32_t split, size_t* bytes) {
+    if (!bytes) return fail(WFPG_ERR_INVALID_ARG, "guide_build_sample_workspace_size: null bytes");
+    if (!valid_n(N)) return fail(WFPG_ERR_INVALID_ARG, "guide_build_sample_workspace_size: bad N");
+    *bytes = guide_fused_workspace_bytes(N, n, split);
+    return WFPG_OK;
+}
+
 int guide_build_sample(const wfpg_svo* s, const float* pos, const float* nrm, const uint32_t* origin_ray,
                        const uint32_t* n_bins_dev, uint32_t bin_cap, const uint32_t* ray_order,
-                       const uint32_t* bin_offset, const float* u, float alpha, const wfpg_guide_params* p, float* dir,
-                       float* pdf_out, void* stream) {
+                       const uint32_t* bin_offset, const float* u, uint32_t n, float alpha,
+                       const wfpg_guide_params* p, float* dir, float* pdf_out, void* workspace, size_t ws_bytes,
+                       void* stream) {
     if (!s || !p) return fail(WFPG_ERR_INVALID_ARG, "guide_build_sample: null svo or params");
     if (!valid_n(p->N)) return fail(WFPG_ERR_INVALID_ARG, "guide_build_sample: N must be 8, 16, 32, 64 or 128");
     if (!(p->eps >= 0.0f)) return fail(WFPG_ERR_INVALID_ARG, "guide_build_sample: eps must be >= 0");
@@ -202,8 +212,10 @@ int guide_build_sample(const wfpg_svo* s, const float* pos, const float* nrm, co
         return fail(WFPG_ERR_INVALID_ARG, "guide_build_sample: block must be 0, 64, 128 or 256");
     if (bin_cap && (!pos || !nrm || !ray_order || !bin_offset || !u || !dir || !pdf_out))
         return fail(WFPG_ERR_INVALID_ARG, "guide_build_sample: null array");
+    if (ws_bytes < guide_fused_workspace_bytes(p->N, n, p->split) || (ws_bytes && !workspace))
+        return fail(WFPG_ERR_CAPACITY, "guide_build_sample: workspace too small");
     const int rc = guide_fused_impl(s, pos, nrm, origin_ray, n_bins_dev, bin_cap, ray_order, bin_offset, u, alpha, p,
-                                    dir, pdf_out, as_stream(stream));
+                                    dir, pdf_out, n, workspace, ws_bytes, as_stream(stream));
     if (rc == WFPG_ERR_INVALID_ARG)
         return fail(rc, "guide_build_sample: the field does not fit in shared memory with this block size");
     if (rc != WFPG_OK) return cuda_fail("guide_build_sample");

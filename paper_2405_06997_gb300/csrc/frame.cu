@@ -30,7 +30,9 @@ size_t bin_workspace_bytes(const wfpg_svo* s, uint32_t n, int mode, uint32_t n_s
 int guide_fused_impl(const wfpg_svo* s, const float* pos, const float* nrm, const uint32_t* origin_ray,
                      const uint32_t* n_bins_dev, uint32_t bin_cap, const uint32_t* ray_order,
                      const uint32_t* bin_offset, const float* u, float alpha, const wfpg_guide_params* p, float* dir,
-                     float* pdf_out, cudaStream_t st, const uint32_t* frame_dev);
+                     float* pdf_out, uint32_t n, void* workspace, size_t ws_bytes, cudaStream_t st,
+                     const uint32_t* frame_dev);
+size_t guide_fused_workspace_bytes(int N, uint32_t n, uint32_t split);
 int accumulate(wfpg_svo* s, const float* pos, const float* wout, const float* L, uint32_t n, cudaStream_t st,
                const uint32_t* n_dev);
 
@@ -302,6 +304,8 @@ struct wfpg_frame {
     size_t bin_ws_bytes = 0;
     void* scan_ws = nullptr;
     size_t scan_ws_bytes = 0;
+    void* guide_ws = nullptr;  // spill slots of the fused GuideRays launch (sized for N = 128)
+    size_t guide_ws_bytes = 0;
     float* vT = nullptr;
     float* vLe = nullptr;
     float* vpos = nullptr;
@@ -408,7 +412,7 @@ struct wfpg_frame {
             wfpg_guide_params gp = p.guide;
             gp.seed = p.seed;
             rc = guide_fused_impl(svo, Q.pos, Q.nrm, origin_ray, n_bins + k, bin_cap, ray_order, bin_offset, Q.u,
-                                  p.alpha, &gp, dir, pdf, st, fidx + k);
+                                  p.alpha, &gp, dir, pdf, P, guide_ws, guide_ws_bytes, st, fidx + k);
             if (rc != WFPG_OK) return rc;
             WFPG_LAUNCH(k_shade, g, T, 0, st, F, Q, dir, pdf, stage, flags, k);
         }
@@ -457,6 +461,8 @@ static int check_params(const wfpg_frame_params* p, int depth_cap) {
     if (p->guide.block != 0 && p->guide.block != 64 && p->guide.block != 128 && p->guide.block != 256)
         return ffail(WFPG_ERR_INVALID_ARG, "frame: block must be 0, 64, 128 or 256");
     if (p->c_ray == 0) return ffail(WFPG_ERR_INVALID_ARG, "frame: c_ray must be >= 1");
+    if (p->guide.split != 0 && p->guide.split != 0xFFFFFFFFu && p->guide.split < 2048)
+        return ffail(WFPG_ERR_INVALID_ARG, "frame: guide.split must be 0, >= 2048 or 0xFFFFFFFF");
     return WFPG_OK;
 }
 
@@ -493,12 +499,14 @@ int frame_create(wfpg_svo* svo, const wfpg_scene* scene, const float* emission, 
     }
     f->bin_ws_bytes = bin_workspace_bytes(svo, P, WFPG_BIN_PARTITION_S, 0);
     f->scan_ws_bytes = scan_workspace_bytes(P) + 1024;
+    f->guide_ws_bytes = guide_fused_workspace_bytes(128, P, 0);
     ok = ok && f->alloc(&f->flags, P) && f->alloc(&f->offs, P) && f->alloc(&f->dir, 3 * (size_t)P) &&
          f->alloc(&f->pdf, P) && f->alloc(&f->bin_of_ray, P) && f->alloc(&f->ray_order, P) &&
          f->alloc(&f->bin_offset, (size_t)f->bin_cap + 1) && f->alloc(&f->origin_ray, f->bin_cap) &&
          f->alloc(&f->n_bins, WFPG_FRAME_MAX_DEPTH + 1) &&
          f->alloc(reinterpret_cast<char**>(&f->bin_ws), f->bin_ws_bytes) &&
-         f->alloc(reinterpret_cast<char**>(&f->scan_ws), f->scan_ws_bytes) && f->alloc(&f->vT, V) &&
+         f->alloc(reinterpret_cast<char**>(&f->scan_ws), f->scan_ws_bytes) &&
+         f->alloc(reinterpret_cast<char**>(&f->guide_ws), f->guide_ws_bytes) && f->alloc(&f->vT, V) &&
          f->alloc(&f->vLe, V) && f->alloc(&f->vpos, 3 * V) && f->alloc(&f->vwo, 3 * V) && f->alloc(&f->nv, P) &&
          f->alloc(&f->rec_pos, 3 * V) && f->alloc(&f->rec_wout, 3 * V) && f->alloc(&f->rec_L, V) &&
          f->alloc(&f->rec_src, V) && f->alloc(&f->img_sum, P) && f->alloc(&f->img_sq, P) &&

@@ -18,6 +18,7 @@
 #include <algorithm>
 
 #include "common.cuh"
+#include "sort.cuh"
 #include "svo.cuh"
 
 namespace wfpg {
@@ -54,7 +55,9 @@ struct GuideArgs {
 };
 
 // fused sampling: after a bin's CDF is built in shared memory, every ray of the
-// bin draws its next direction from alpha * field + (1 - alpha) * cosine
+// bin draws its next direction from alpha * field + (1 - alpha) * cosine.  A bin
+// with more than `split` rays copies its field and CDFs to a spill slot instead,
+// and k_spill_sample draws its rays with the whole GPU (same arithmetic).
 struct FusedArgs {
     const uint32_t* ray_order;
     const uint32_t* bin_offset;
@@ -63,7 +66,15 @@ struct FusedArgs {
     float alpha;
     float* dir;         // xyz per ray
     float* pdf;         // mixture density per ray
+    uint32_t split;     // 0: never spill
+    uint32_t spill_cap;
+    unsigned long long* spill_ctr;  // (slots << 40) | chunks, appended together
+    uint32_t* spill_bin;            // bin of each slot
+    uint32_t* spill_base;           // first chunk of each slot
+    float* spill_tab;               // per slot: field (N^2), row CDFs (N^2), marginal (N)
 };
+constexpr int kSpillChunk = 256;  // rays per block-iteration of k_spill_sample
+constexpr unsigned long long kSpillChunkMask = (1ull << 40) - 1;
 
 __device__ __forceinline__ Node load_node(const TraceArgs& T, const Node* s_nodes, uint32_t id) {
     if (id < T.smem_nodes) return s_nodes[id];
@@ -195,6 +206,53 @@ __device__ __forceinline__ float3 cosine_dir(float nx, float ny, float nz, float
                        r * cp * tz + r * sp * bz + z * nz);
 }
 
+// one ray of the one-sample mixture: guided (inverse CDF) if u2 < alpha, else
+// cosine about the normal; writes the direction and the mixture density
+__device__ __forceinline__ void sample_ray(const FusedArgs& F, uint32_t ray, const float* f, const float* C,
+                                           const float* M, int N, float nn, float den, float tn) {
+    const float u0 = F.u[3 * (size_t)ray], u1 = F.u[3 * (size_t)ray + 1], u2 = F.u[3 * (size_t)ray + 2];
+    const float nx = F.nrm[3 * (size_t)ray], ny = F.nrm[3 * (size_t)ray + 1], nz = F.nrm[3 * (size_t)ray + 2];
+    float3 d;
+    float pg;
+    if (u2 < F.alpha) {
+        d = sample_cdf(f, C, M, N, u0, u1, tn, &pg);
+        pg = __fdiv_rn(__fmul_rn(pg, nn), den);
+    } else {
+        d = cosine_dir(nx, ny, nz, u0, u1);
+        pg = __fdiv_rn(__fmul_rn(f[octa_cell(d, N)], nn), den);
+    }
+    const float cs = fmaxf(0.0f, nx * d.x + ny * d.y + nz * d.z);
+    F.dir[3 * (size_t)ray] = d.x;
+    F.dir[3 * (size_t)ray + 1] = d.y;
+    F.dir[3 * (size_t)ray + 2] = d.z;
+    F.pdf[ray] = F.alpha * pg + (1.0f - F.alpha) * cs * 0.31830988618379067f;
+}
+
+// rays of the spilled bins, kSpillChunk per block-iteration, tables read from
+// global memory (L2); chunk c belongs to the last slot whose first chunk <= c
+__global__ void __launch_bounds__(kSpillChunk) k_spill_sample(FusedArgs F, int N) {
+    const unsigned long long ctr = *F.spill_ctr;
+    const uint32_t nslots = min((uint32_t)(ctr >> 40), F.spill_cap);
+    const uint32_t nch = (uint32_t)(ctr & kSpillChunkMask);
+    if (nslots == 0) return;
+    const int NN = N * N;
+    const float nn = (float)NN, tn = __fdiv_rn(2.0f, (float)N);
+    for (uint32_t c = blockIdx.x; c < nch; c += gridDim.x) {
+        uint32_t lo = 0, hi = nslots;
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (F.spill_base[mid] <= c) lo = mid;
+            else hi = mid;
+        }
+        const uint32_t b = F.spill_bin[lo];
+        const uint32_t k = F.bin_offset[b] + (c - F.spill_base[lo]) * kSpillChunk + threadIdx.x;
+        if (k >= F.bin_offset[b + 1]) continue;
+        const float* tab = F.spill_tab + (size_t)lo * (2 * NN + N);
+        const float den = __fmul_rn(tab[2 * NN + N - 1], kFourPi);
+        sample_ray(F, F.ray_order[k], tab, tab + NN, tab + 2 * NN, N, nn, den, tn);
+    }
+}
+
 // inclusive scan of a row of N floats in warp order (chunks of 32: rounds
 // k = 1, 2, 4, 8, 16 of x[i] += x[i-k], later chunks add the running total),
 // then a running maximum (exact; keeps the CDF non-decreasing under rounding)
@@ -227,8 +285,10 @@ __device__ __forceinline__ float warp_scan_row(const float* src, float* dst, int
 // kGuideThreads threads work on one bin at a time; kStage: the chunk's cone
 // directions are computed by all threads together into shared memory before
 // the march (otherwise each lane computes its ray's direction when it takes it)
+// 1280 resident threads per SM (40 warps): at most 51 registers a thread, the
+// budget the unfused kernel fits in, so the fused variant keeps its occupancy
 template <int kGuideThreads, bool kStage, bool kFused>
-__global__ void __launch_bounds__(kGuideThreads) k_guide_build(TraceArgs T, GuideArgs G, FusedArgs F,
+__global__ void __launch_bounds__(kGuideThreads, 1280 / kGuideThreads) k_guide_build(TraceArgs T, GuideArgs G, FusedArgs F,
                                                                const float* __restrict__ pos,
                                                                const uint32_t* __restrict__ origin_ray,
                                                                const uint32_t* __restrict__ n_bins_dev,
@@ -247,6 +307,7 @@ __global__ void __launch_bounds__(kGuideThreads) k_guide_build(TraceArgs T, Guid
     float* rowtot = tmp + NN;
     float* marg = rowtot + N;
     __shared__ int s_next;
+    __shared__ uint32_t s_slot;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t lt = (1u << lane) - 1u;
     constexpr int kWarps = kGuideThreads / 32;
@@ -522,27 +583,34 @@ __global__ void __launch_bounds__(kGuideThreads) k_guide_build(TraceArgs T, Guid
             }
             for (int j = tid; j < N; j += kGuideThreads) cdf_marg[(size_t)b * N + j] = marg[j];
         } else {
-            // the bin's rays sample straight from the shared-memory CDF
             const uint32_t r_lo = F.bin_offset[b], r_hi = F.bin_offset[b + 1];
-            for (uint32_t k = r_lo + tid; k < r_hi; k += kGuideThreads) {
-                const uint32_t ray = F.ray_order[k];
-                const float u0 = F.u[3 * (size_t)ray], u1 = F.u[3 * (size_t)ray + 1], u2 = F.u[3 * (size_t)ray + 2];
-                const float nx = F.nrm[3 * (size_t)ray], ny = F.nrm[3 * (size_t)ray + 1], nz = F.nrm[3 * (size_t)ray + 2];
-                float3 d;
-                float pg;
-                if (u2 < F.alpha) {
-                    d = sample_cdf(field, tmp, marg, N, u0, u1, tn, &pg);
-                    pg = __fdiv_rn(__fmul_rn(pg, nn), den);
-                } else {
-                    d = cosine_dir(nx, ny, nz, u0, u1);
-                    pg = __fdiv_rn(__fmul_rn(field[octa_cell(d, N)], nn), den);
+            bool spilled = false;
+            if (F.split && r_hi - r_lo > F.split) {  // uniform over the block
+                if (tid == 0) {
+                    const uint32_t nch = (r_hi - r_lo + kSpillChunk - 1) / kSpillChunk;
+                    const unsigned long long old = atomicAdd(F.spill_ctr, (1ull << 40) | nch);
+                    const uint32_t slot = (uint32_t)(old >> 40);
+                    if (slot < F.spill_cap) {
+                        F.spill_bin[slot] = b;
+                        F.spill_base[slot] = (uint32_t)(old & kSpillChunkMask);
+                    }
+                    s_slot = slot;
                 }
-                const float cs = fmaxf(0.0f, nx * d.x + ny * d.y + nz * d.z);
-                F.dir[3 * (size_t)ray] = d.x;
-                F.dir[3 * (size_t)ray + 1] = d.y;
-                F.dir[3 * (size_t)ray + 2] = d.z;
-                F.pdf[ray] = F.alpha * pg + (1.0f - F.alpha) * cs * 0.31830988618379067f;
+                __syncthreads();
+                const uint32_t slot = s_slot;
+                if (slot < F.spill_cap) {
+                    float* tab = F.spill_tab + (size_t)slot * (2 * NN + N);
+                    for (int c = tid; c < NN; c += kGuideThreads) {
+                        tab[c] = field[c];
+                        tab[NN + c] = tmp[c];
+                    }
+                    for (int j = tid; j < N; j += kGuideThreads) tab[2 * NN + j] = marg[j];
+                    spilled = true;
+                }
             }
+            // otherwise the bin's rays sample straight from the shared-memory CDF
+            for (uint32_t k = r_lo + tid; !spilled && k < r_hi; k += kGuideThreads)
+                sample_ray(F, F.ray_order[k], field, tmp, marg, N, nn, den, tn);
         }
         __syncthreads();
     }
@@ -738,16 +806,58 @@ int guide_build_impl(const wfpg_svo* s, const float* pos, const uint32_t* origin
     return dispatch_guide<false>(s, p, T, G, F, pos, origin_ray, n_bins_dev, bin_cap, pdf, cdf_row, cdf_marg, st);
 }
 
+constexpr uint32_t kGuideSplitDefault = 2048;
+
+static uint32_t split_of(const wfpg_guide_params* p) {
+    return p->split == 0 ? kGuideSplitDefault : (p->split == 0xFFFFFFFFu ? 0u : p->split);
+}
+
+size_t guide_fused_workspace_bytes(int N, uint32_t n, uint32_t split_param) {
+    wfpg_guide_params p{};
+    p.split = split_param;
+    const uint32_t split = split_of(&p);
+    const size_t cap = split ? (size_t)n / split + 1 : 0;
+    return arena_bytes<unsigned long long>(1) + 2 * arena_bytes<uint32_t>(cap) +
+           arena_bytes<float>(cap * (2 * (size_t)N * N + N)) + 256;
+}
+
 int guide_fused_impl(const wfpg_svo* s, const float* pos, const float* nrm, const uint32_t* origin_ray,
                      const uint32_t* n_bins_dev, uint32_t bin_cap, const uint32_t* ray_order,
                      const uint32_t* bin_offset, const float* u, float alpha, const wfpg_guide_params* p, float* dir,
-                     float* pdf_out, cudaStream_t st, const uint32_t* frame_dev) {
+                     float* pdf_out, uint32_t n, void* workspace, size_t ws_bytes, cudaStream_t st,
+                     const uint32_t* frame_dev) {
     if (bin_cap == 0) return WFPG_OK;
     TraceArgs T;
     GuideArgs G;
     trace_setup(s, p, &T, &G, frame_dev);
-    FusedArgs F{ray_order, bin_offset, nrm, u, alpha, dir, pdf_out};
-    return dispatch_guide<true>(s, p, T, G, F, pos, origin_ray, n_bins_dev, bin_cap, nullptr, nullptr, nullptr, st);
+    FusedArgs F{};
+    F.ray_order = ray_order;
+    F.bin_offset = bin_offset;
+    F.nrm = nrm;
+    F.u = u;
+    F.alpha = alpha;
+    F.dir = dir;
+    F.pdf = pdf_out;
+    F.split = split_of(p);
+    if (F.split) {
+        const size_t cap = (size_t)n / F.split + 1;
+        Arena ws{static_cast<char*>(workspace), ws_bytes, 0, false};
+        F.spill_ctr = ws.take<unsigned long long>(1);
+        F.spill_bin = ws.take<uint32_t>(cap);
+        F.spill_base = ws.take<uint32_t>(cap);
+        F.spill_tab = ws.take<float>(cap * (2 * (size_t)p->N * p->N + p->N));
+        if (ws.overflow) return WFPG_ERR_CAPACITY;
+        F.spill_cap = (uint32_t)cap;
+        if (cudaMemsetAsync(F.spill_ctr, 0, sizeof(unsigned long long), st) != cudaSuccess) return WFPG_ERR_CUDA;
+    }
+    const int rc =
+        dispatch_guide<true>(s, p, T, G, F, pos, origin_ray, n_bins_dev, bin_cap, nullptr, nullptr, nullptr, st);
+    if (rc != WFPG_OK || !F.split) return rc;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    WFPG_LAUNCH(k_spill_sample, (uint32_t)sms * 8, kSpillChunk, 0, st, F, p->N);
+    return cudaGetLastError() == cudaSuccess ? WFPG_OK : WFPG_ERR_CUDA;
 }
 
 int field_pdf_impl(const float* field, int N, const uint32_t* n_bins_dev, uint32_t bin_cap, float* pdf,

@@ -60,7 +60,8 @@ class BinParams(C.Structure):
 
 class GuideParams(C.Structure):
     _fields_ = [("N", I32), ("eps", F), ("jitter", I32), ("blur", I32), ("t_skip", F),
-                ("cos_weight", I32), ("seed", U64), ("frame", U32), ("block", I32), ("stage", I32)]
+                ("cos_weight", I32), ("seed", U64), ("frame", U32), ("block", I32), ("stage", I32),
+                ("split", U32)]
 
 
 FRAME_MAX_DEPTH = 8
@@ -107,7 +108,8 @@ def lib():
             "bin_rays": [P, P, P, U32, P, P, P, P, P, P, U32, P, P, SZ, P],
             "guide_build_pdf": [P, P, P, P, U32, P, P, P, P, P],
             "guide_sample": [P, P, P, I32, U32, P, P, U32, P, P, P, P],
-            "guide_build_sample": [P, P, P, P, P, U32, P, P, P, F, P, P, P, P],
+            "guide_build_sample": [P, P, P, P, P, U32, P, P, P, U32, F, P, P, P, P, SZ, P],
+            "guide_build_sample_workspace_size": [I32, U32, U32, P],
             "guide_eval_pdf": [P, I32, U32, P, P, U32, P, P],
             "svo_export": [P, P, P, P, P, P, P, P, P, P],
             "svo_export_exitance": [P, P, P, P, P, P, P],
@@ -322,12 +324,18 @@ def guide_build_pdf(svo: SVO, pos, origin_ray=None, n_bins=None, bin_cap=None, *
     return pdf, cr, cm
 
 
+def guide_build_sample_workspace_size(N: int, n: int, split: int = 0) -> int:
+    b = SZ()
+    _check(lib().guide_build_sample_workspace_size(N, n, split, C.byref(b)))
+    return int(b.value)
+
+
 def guide_build_sample(svo: SVO, pos, nrm, bins, u, *, alpha=0.5, N=16, eps=1e-2, jitter=False, blur=False,
-                       t_skip=None, cos_weight=False, seed=1, frame=0, block=0, stage=0, out=None,
-                       stream=None):
-    """guide_build_pdf + one-sample mixture sampling in one launch.  bins is the
-    dict bin_rays returns; u holds 3 uniforms per ray.  Returns (dir [n,3],
-    mixture pdf [n])."""
+                       t_skip=None, cos_weight=False, seed=1, frame=0, block=0, stage=0, split=0, out=None,
+                       workspace=None, stream=None):
+    """guide_build_pdf + one-sample mixture sampling in one launch (plus a
+    GPU-wide launch for bins above `split` rays).  bins is the dict bin_rays
+    returns; u holds 3 uniforms per ray.  Returns (dir [n,3], mixture pdf [n])."""
     n = pos.shape[0]
     bin_cap = bins["origin_ray"].numel()
     if t_skip is None:
@@ -335,17 +343,21 @@ def guide_build_sample(svo: SVO, pos, nrm, bins, u, *, alpha=0.5, N=16, eps=1e-2
     if out is None:
         out = (torch.empty((n, 3), dtype=torch.float32, device=pos.device),
                torch.empty(n, dtype=torch.float32, device=pos.device))
+    need = guide_build_sample_workspace_size(N, n, split)
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(need, dtype=torch.uint8, device=pos.device)
     d, pm = out
     p = GuideParams(N=N, eps=eps, jitter=int(jitter), blur=int(blur), t_skip=t_skip,
-                    cos_weight=int(cos_weight), seed=seed, frame=frame, block=block, stage=stage)
+                    cos_weight=int(cos_weight), seed=seed, frame=frame, block=block, stage=stage, split=split)
     _check(lib().guide_build_sample(svo.handle, _ptr(pos, torch.float32, 3 * n, "pos"),
                                     _ptr(nrm, torch.float32, 3 * n, "nrm"),
                                     _ptr(bins["origin_ray"], torch.int32, bin_cap),
                                     _ptr(bins["n_bins"], torch.int32, 1), bin_cap,
                                     _ptr(bins["ray_order"], torch.int32, n),
                                     _ptr(bins["bin_offset"], torch.int32, bin_cap + 1),
-                                    _ptr(u, torch.float32, 3 * n, "u"), alpha, C.byref(p),
-                                    _ptr(d, torch.float32, 3 * n), _ptr(pm, torch.float32, n), _stream(stream)))
+                                    _ptr(u, torch.float32, 3 * n, "u"), n, alpha, C.byref(p),
+                                    _ptr(d, torch.float32, 3 * n), _ptr(pm, torch.float32, n),
+                                    _ptr(workspace, torch.uint8), workspace.numel(), _stream(stream)))
     return d, pm
 
 

@@ -85,6 +85,24 @@ def test_fused_equals_unfused_and_oracle(N, alpha):
     assert g.status() == 0
 
 
+@pytest.mark.parametrize("split", [1, 64, 700])
+def test_fused_split_bins_give_identical_samples(split):
+    """Bins above `split` rays are sampled by the GPU-wide second launch from
+    spilled tables: the directions and densities do not change."""
+    w, g, _ = box_svo(8)
+    n = w.ray_pos.shape[0]
+    pos, nrm = dev(w.ray_pos), dev(w.ray_nrm)
+    sizes = inputs.zipf_bin_sizes(n, 24, 1.2, 5)
+    r = W.bin_rays(g, pos, nrm, mode=W.BIN_RUNS, sizes=dev(sizes.astype(np.uint32).view(np.int32)), seed=2)
+    assert sizes.max() > 700
+    u = dev(inputs.uniforms24(23, (n, 3)))
+    kw = dict(alpha=0.5, N=32, jitter=True, blur=True, seed=2, frame=1)
+    d0, p0 = W.guide_build_sample(g, pos, nrm, r, u, split=0xFFFFFFFF, **kw)
+    d1, p1 = W.guide_build_sample(g, pos, nrm, r, u, split=split, **kw)
+    assert torch.equal(d0, d1) and torch.equal(p0, p1)
+    assert g.status() == 0
+
+
 def test_fused_rejects_bad_alpha():
     w, g, _ = box_svo(4, records=False)
     pos, nrm = dev(w.ray_pos[:64]), dev(w.ray_nrm[:64])
