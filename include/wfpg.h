@@ -275,6 +275,22 @@ WFPG_API int guide_build_sample(const wfpg_svo* svo, const float* pos, const flo
 WFPG_API int guide_build_sample_workspace_size(int N, uint32_t n, uint32_t split, size_t* bytes);
 
 /*
+ * guide_sample_mix -- the sampling step of guide_build_sample from stored
+ * tables (as guide_build_pdf or guide_learned_build_pdf write them): ray i of
+ * bin b = bin_of_ray[i] takes u[i] = (u0, u1, u2); if u2 < alpha the guided
+ * inverse-CDF sample (as guide_sample), else the cosine direction about
+ * nrm[i]; pdf_out[i] = alpha * pdf[b][cell(dir)] + (1 - alpha) * max(0, cos)
+ * / pi.  A ray whose bin is >= min(*n_bins_dev, bin_cap) (NULL: bin_cap) has
+ * no table and takes the cosine branch with density cos / pi.  Rays
+ * i >= min(*n_dev, n) (NULL: n) are not written.  With the same field, the
+ * results equal guide_build_sample's bit for bit.
+ */
+WFPG_API int guide_sample_mix(const float* pdf, const float* cdf_row, const float* cdf_marg, int N,
+                              uint32_t bin_cap, const uint32_t* n_bins_dev, const uint32_t* bin_of_ray,
+                              const float* nrm, const float* u, uint32_t n, const uint32_t* n_dev, float alpha,
+                              float* dir, float* pdf_out, void* stream);
+
+/*
  * guide_sample -- the guided branch of Alg. 3's sampling step: inverse-CDF
  * sampling of the piecewise-constant density.  Per ray: t0 = u0 * T; the row
  * is the first marginal entry > t0 (N-1 if none); t1 = u1 * T_row; the
@@ -405,6 +421,9 @@ typedef struct wfpg_frame_params {
     wfpg_guide_params guide;  /* N, eps, jitter, blur, t_skip, cos_weight, block, stage (seed/frame unused) */
     uint64_t seed;
     int update;               /* 1: UpdateExitance after each frame */
+    int caster;               /* closest hits: 0 auto (SVO walk above 64 primitives), 1 every primitive, 2 SVO walk */
+    int proposal;             /* guided part: 0 SVO-traced field (fused GuideRays), 1 learned MLP (N must be 32;
+                                 frame_set_mlp first) */
 } wfpg_frame_params;
 
 typedef struct wfpg_frame wfpg_frame;
@@ -431,6 +450,11 @@ WFPG_API int frame_destroy(wfpg_frame* f);
 WFPG_API int frame_run(wfpg_frame* f, uint32_t n_frames, int use_graph, void* stream);
 /* Replaces the parameters (same max_depth or smaller; drops the graph). */
 WFPG_API int frame_set_params(wfpg_frame* f, const wfpg_frame_params* p);
+/* The MLP the learned proposal uses (not owned; NULL detaches).  Its bins per
+ * depth are capped at min(its max_batch, the frame's bin capacity); rays of
+ * bins past the cap take the cosine branch alone.  lp (copied): the scene box
+ * and eps for guide_learned_build_pdf.  Drops the graph. */
+WFPG_API int frame_set_mlp(wfpg_frame* f, wfpg_mlp* mlp, const wfpg_learned_params* lp);
 WFPG_API int frame_get_params(const wfpg_frame* f, wfpg_frame_params* p);
 /* Zeroes the per-pixel sums and the frame count. */
 WFPG_API int frame_reset_image(wfpg_frame* f, void* stream);
@@ -478,6 +502,15 @@ WFPG_API int frame_export(const wfpg_frame* f, int what, void* dst, size_t bytes
  */
 WFPG_API int wfpg_cast_rays(const wfpg_scene* scene, const float* o, const float* d, uint32_t n,
                             float tmin, float* t_out, uint32_t* prim_out, float* nrm_out, void* stream);
+/* The same closest hit, with the scene's SVO (built from the same scene) as
+ * the acceleration structure: the leaf-resolution walk of the cone march
+ * visits the occupied leaves front to back and tests each leaf's fragment
+ * list; empty blocks are skipped whole.  Hits agree with wfpg_cast_rays up
+ * to a relative 1e-5 in t where two primitives are hit at nearly the same
+ * distance. */
+WFPG_API int wfpg_cast_rays_svo(const wfpg_svo* svo, const wfpg_scene* scene, const float* o, const float* d,
+                                uint32_t n, float tmin, float* t_out, uint32_t* prim_out, float* nrm_out,
+                                void* stream);
 
 /* -------------------------------------------------------------------------
  * Inspection (used by tests; each synchronises `stream`).  Host buffers are

@@ -28,6 +28,9 @@ int guide_fused_impl(const wfpg_svo* s, const float* pos, const float* nrm, cons
                      float* pdf_out, uint32_t n, void* workspace, size_t ws_bytes, cudaStream_t st,
                      const uint32_t* frame_dev = nullptr);
 size_t guide_fused_workspace_bytes(int N, uint32_t n, uint32_t split);
+int sample_mix_impl(const float* pdf, const float* cdf_row, const float* cdf_marg, int N, uint32_t bin_cap,
+                    const uint32_t* n_bins_dev, const uint32_t* bin_of_ray, const float* nrm, const float* u,
+                    uint32_t n, const uint32_t* n_dev, float alpha, float* dir, float* pdf_out, cudaStream_t st);
 int guide_sample_impl(const float* pdf, const float* cdf_row, const float* cdf_marg, int N, uint32_t bin_cap,
                       const uint32_t* bin_of_ray, const float* u, uint32_t n, float* dir, float* pdf_out,
                       uint32_t* cell, cudaStream_t st);
@@ -219,6 +222,19 @@ int guide_build_sample(const wfpg_svo* s, const float* pos, const float* nrm, co
     if (rc == WFPG_ERR_INVALID_ARG)
         return fail(rc, "guide_build_sample: the field does not fit in shared memory with this block size");
     if (rc != WFPG_OK) return cuda_fail("guide_build_sample");
+    return WFPG_OK;
+}
+
+int guide_sample_mix(const float* pdf, const float* cdf_row, const float* cdf_marg, int N, uint32_t bin_cap,
+                     const uint32_t* n_bins_dev, const uint32_t* bin_of_ray, const float* nrm, const float* u,
+                     uint32_t n, const uint32_t* n_dev, float alpha, float* dir, float* pdf_out, void* stream) {
+    if (!valid_n(N)) return fail(WFPG_ERR_INVALID_ARG, "guide_sample_mix: N must be 8, 16, 32, 64 or 128");
+    if (!(alpha >= 0.0f && alpha <= 1.0f)) return fail(WFPG_ERR_INVALID_ARG, "guide_sample_mix: alpha in [0, 1]");
+    if (n && (!bin_of_ray || !nrm || !u || !dir || !pdf_out || (bin_cap && (!pdf || !cdf_row || !cdf_marg))))
+        return fail(WFPG_ERR_INVALID_ARG, "guide_sample_mix: null array");
+    if (sample_mix_impl(pdf, cdf_row, cdf_marg, N, bin_cap, n_bins_dev, bin_of_ray, nrm, u, n, n_dev, alpha, dir,
+                        pdf_out, as_stream(stream)) != WFPG_OK)
+        return cuda_fail("guide_sample_mix");
     return WFPG_OK;
 }
 

@@ -4,6 +4,7 @@
 // wavefront from one path vertex to the next.
 #pragma once
 #include "common.cuh"
+#include "march.cuh"
 
 namespace wfpg {
 
@@ -12,40 +13,168 @@ struct Hit {
     uint32_t prim;  // kNone if nothing is hit
 };
 
+// distance to primitive `prim` along the ray (t > tmin), +inf if it is missed
+__device__ __forceinline__ float hit_prim(const float* __restrict__ quads, uint32_t nq,
+                                          const float* __restrict__ spheres, uint32_t prim, const float oo[3],
+                                          const float dd[3], float tmin) {
+    const float INF = __int_as_float(0x7f800000);
+    if (prim < nq) {
+        const float* Q = quads + 8 * (size_t)prim;
+        const int a = (int)Q[0], b = (a + 1) % 3, c = (a + 2) % 3;
+        if (dd[a] == 0.0f) return INF;
+        const float t = (Q[1] - oo[a]) / dd[a];
+        if (!(t > tmin)) return INF;
+        const float pb = oo[b] + t * dd[b], pc = oo[c] + t * dd[c];
+        return (pb >= Q[2] && pb <= Q[3] && pc >= Q[4] && pc <= Q[5]) ? t : INF;
+    }
+    const float* S = spheres + 4 * (size_t)(prim - nq);
+    const float cx = oo[0] - S[0], cy = oo[1] - S[1], cz = oo[2] - S[2];
+    const float bq = dd[0] * cx + dd[1] * cy + dd[2] * cz;
+    const float cq = cx * cx + cy * cy + cz * cz - S[3] * S[3];
+    const float disc = bq * bq - cq;
+    if (disc < 0.0f) return INF;
+    const float sq = sqrtf(disc);
+    float t = -bq - sq;
+    if (!(t > tmin)) t = -bq + sq;
+    return t > tmin ? t : INF;
+}
+
+// every primitive, nearest first hit (small scenes)
 __device__ __forceinline__ Hit cast_closest(const float* __restrict__ quads, uint32_t nq,
                                             const float* __restrict__ spheres, uint32_t ns, float ox, float oy,
                                             float oz, float dx, float dy, float dz, float tmin) {
     const float oo[3] = {ox, oy, oz}, dd[3] = {dx, dy, dz};
     float best = __int_as_float(0x7f800000);
     uint32_t bp = kNone;
-    for (uint32_t q = 0; q < nq; ++q) {
-        const float* Q = quads + 8 * (size_t)q;
-        const int a = (int)Q[0], b = (a + 1) % 3, c = (a + 2) % 3;
-        if (dd[a] == 0.0f) continue;
-        const float t = (Q[1] - oo[a]) / dd[a];
-        if (!(t > tmin) || t >= best) continue;
-        const float pb = oo[b] + t * dd[b], pc = oo[c] + t * dd[c];
-        if (pb >= Q[2] && pb <= Q[3] && pc >= Q[4] && pc <= Q[5]) {
+    for (uint32_t p = 0; p < nq + ns; ++p) {
+        const float t = hit_prim(quads, nq, spheres, p, oo, dd, tmin);
+        if (t < best) {
             best = t;
-            bp = q;
-        }
-    }
-    for (uint32_t s = 0; s < ns; ++s) {
-        const float* S = spheres + 4 * (size_t)s;
-        const float cx = ox - S[0], cy = oy - S[1], cz = oz - S[2];
-        const float bq = dx * cx + dy * cy + dz * cz;
-        const float cq = cx * cx + cy * cy + cz * cz - S[3] * S[3];
-        const float disc = bq * bq - cq;
-        if (disc < 0.0f) continue;
-        const float sq = sqrtf(disc);
-        float t = -bq - sq;
-        if (!(t > tmin)) t = -bq + sq;
-        if (t > tmin && t < best) {
-            best = t;
-            bp = nq + s;
+            bp = p;
         }
     }
     return Hit{bp == kNone ? -1.0f : best, bp};
+}
+
+// The SVO as a ray-casting acceleration structure: node records plus each
+// leaf's fragment list (the primitives the conservative voxelisation found in it).
+struct SvoCast {
+    const Node* node;
+    const uint32_t* frag_off;   // per leaf, + 1
+    const uint32_t* frag_prim;
+    uint32_t leaf_off;          // global id of the first leaf
+    int D;
+    float lo[3];
+    float scale;                // 2^D / S
+};
+
+// Closest hit by walking the SVO front to back with the leaf-resolution walk
+// of the cone march: every occupied leaf the ray passes is visited in order;
+// its primitives are tested and the nearest hit that lies within the leaf's
+// stretch of the ray (plus a relative tolerance) ends the walk.  A primitive
+// overlaps every leaf its surface passes (conservative voxelisation), so the
+// first accepted hit is the closest.  Empty blocks are skipped whole.
+__device__ __forceinline__ Hit cast_svo(const SvoCast& V, const float* __restrict__ quads, uint32_t nq,
+                                        const float* __restrict__ spheres, float ox, float oy, float oz, float dx,
+                                        float dy, float dz, float tmin) {
+    const float INF = __int_as_float(0x7f800000);
+    const int D = V.D, res = 1 << D;
+    const float fres = (float)res;
+    const float oo[3] = {ox, oy, oz}, dd[3] = {dx, dy, dz};
+    const float gx = (ox - V.lo[0]) * V.scale, gy = (oy - V.lo[1]) * V.scale, gz = (oz - V.lo[2]) * V.scale;
+    const float ivx = dx != 0.0f ? 1.0f / (dx * V.scale) : 0.0f;
+    const float ivy = dy != 0.0f ? 1.0f / (dy * V.scale) : 0.0f;
+    const float ivz = dz != 0.0f ? 1.0f / (dz * V.scale) : 0.0f;
+    int cx, cy, cz;
+    if (gx >= 0.0f && gx <= fres && gy >= 0.0f && gy <= fres && gz >= 0.0f && gz <= fres) {
+        cx = min((int)gx, res - 1);
+        cy = min((int)gy, res - 1);
+        cz = min((int)gz, res - 1);
+    } else {  // slab entry into the grid box
+        const float gg[3] = {gx, gy, gz}, iv[3] = {ivx, ivy, ivz};
+        float tnr = 0.0f, tfr = INF;
+        int enter = -1;
+        for (int a = 0; a < 3; ++a) {
+            if (iv[a] == 0.0f) {
+                if (!(gg[a] >= 0.0f && gg[a] <= fres)) return Hit{-1.0f, kNone};
+                continue;
+            }
+            const float t0 = (0.0f - gg[a]) * iv[a], t1 = (fres - gg[a]) * iv[a];
+            const float lo_t = fminf(t0, t1), hi_t = fmaxf(t0, t1);
+            if (lo_t > tnr) {
+                tnr = lo_t;
+                enter = a;
+            }
+            tfr = fminf(hi_t, tfr);
+        }
+        if (!(tnr <= tfr)) return Hit{-1.0f, kNone};
+        int cc[3];
+        for (int a = 0; a < 3; ++a) {
+            if (a == enter) {
+                cc[a] = iv[a] > 0.0f ? 0 : res - 1;
+            } else {
+                const float p = gg[a] + tnr * dd[a] * V.scale;
+                cc[a] = min((p >= 0.0f) ? (int)p : 0, res - 1);
+            }
+        }
+        cx = cc[0];
+        cy = cc[1];
+        cz = cc[2];
+    }
+    uint32_t stk[WFPG_MAX_DEPTH + 1];
+    stk[0] = 0;
+    int level = 0;
+    uint32_t node = 0;
+    const int cap = 3 * res + 16;
+    for (int steps = 0; steps <= cap; ++steps) {
+        while (level < D) {  // deepest existing node holding the cell
+            const Node nd = V.node[node];
+            const int sh = D - 1 - level;
+            const int k = ((cx >> sh) & 1) | (((cy >> sh) & 1) << 1) | (((cz >> sh) & 1) << 2);
+            if (!((nd.mask >> k) & 1u)) break;
+            node = child_id(nd, k);
+            ++level;
+            stk[level] = node;
+        }
+        // exit crossing of the current block (a leaf when level == D)
+        const int sl = (level == D) ? 0 : D - level - 1;
+        const int size = 1 << sl;
+        const int bx = (cx >> sl) << sl, by = (cy >> sl) << sl, bz = (cz >> sl) << sl;
+        const int ex = ivx > 0.0f ? bx + size : bx - 1;
+        const int ey = ivy > 0.0f ? by + size : by - 1;
+        const int ez = ivz > 0.0f ? bz + size : bz - 1;
+        const float tex = ivx != 0.0f ? cross_time(ex, ivx > 0.0f, gx, ivx) : INF;
+        const float tey = ivy != 0.0f ? cross_time(ey, ivy > 0.0f, gy, ivy) : INF;
+        const float tez = ivz != 0.0f ? cross_time(ez, ivz > 0.0f, gz, ivz) : INF;
+        const int a = (tex <= tey && tex <= tez) ? 0 : (tey <= tez ? 1 : 2);
+        const float tx = a == 0 ? tex : (a == 1 ? tey : tez);
+        if (level == D) {
+            const uint32_t leaf = node - V.leaf_off;
+            float best = INF;
+            uint32_t bp = kNone;
+            for (uint32_t f = V.frag_off[leaf]; f < V.frag_off[leaf + 1]; ++f) {
+                const uint32_t p = V.frag_prim[f];
+                const float th = hit_prim(quads, nq, spheres, p, oo, dd, tmin);
+                if (th < best) {
+                    best = th;
+                    bp = p;
+                }
+            }
+            if (bp != kNone && best <= tx + 1e-5f * fmaxf(1.0f, tx)) return Hit{best, bp};
+        }
+        const int nx = a == 0 ? ex : advance_axis(cx, bx, size, gx, ivx, dx * V.scale, tx, true);
+        const int ny = a == 1 ? ey : advance_axis(cy, by, size, gy, ivy, dy * V.scale, tx, a > 1);
+        const int nz = a == 2 ? ez : advance_axis(cz, bz, size, gz, ivz, dz * V.scale, tx, false);
+        const int na = a == 0 ? nx : (a == 1 ? ny : nz);
+        if (tx == INF || na < 0 || na >= res) return Hit{-1.0f, kNone};
+        const uint32_t diff = (uint32_t)((cx ^ nx) | (cy ^ ny) | (cz ^ nz));
+        level = D - 1 - (31 - __clz(diff));
+        node = stk[level];
+        cx = nx;
+        cy = ny;
+        cz = nz;
+    }
+    return Hit{-1.0f, kNone};
 }
 
 // geometric normal at a hit, turned to face the incoming direction d

@@ -35,6 +35,11 @@ int guide_fused_impl(const wfpg_svo* s, const float* pos, const float* nrm, cons
 size_t guide_fused_workspace_bytes(int N, uint32_t n, uint32_t split);
 int accumulate(wfpg_svo* s, const float* pos, const float* wout, const float* L, uint32_t n, cudaStream_t st,
                const uint32_t* n_dev);
+int sample_mix_impl(const float* pdf, const float* cdf_row, const float* cdf_marg, int N, uint32_t bin_cap,
+                    const uint32_t* n_bins_dev, const uint32_t* bin_of_ray, const float* nrm, const float* u,
+                    uint32_t n, const uint32_t* n_dev, float alpha, float* dir, float* pdf_out, cudaStream_t st);
+SvoCast svo_cast_view(const wfpg_svo* s);
+uint32_t mlp_max_batch(const wfpg_mlp* m);
 
 constexpr uint64_t kPathPurpose = 2;  // per-path uniforms (0: origins, 1: jitter)
 constexpr uint32_t kDepthStride = 16; // random-stream frame index = frame * 16 + depth
@@ -62,6 +67,8 @@ struct FrameView {
     int max_depth, rr_depth;
     uint64_t pseed;
     float offset;  // origin offset along the normal for continuation rays
+    SvoCast sv;
+    int svo_cast;  // 1: closest hits by the SVO walk, 0: every primitive
     float* vT;
     float* vLe;
     float* vpos;
@@ -84,6 +91,12 @@ __global__ void k_frame_begin(FrameView F) {
     const uint32_t fc = *F.frame_counter;
     for (int k = threadIdx.x; k <= F.max_depth; k += blockDim.x) F.fidx[k] = fc * kDepthStride + k;
     for (int k = threadIdx.x; k <= WFPG_FRAME_MAX_DEPTH + 1; k += blockDim.x) F.counters[k] = 0;
+}
+
+__device__ __forceinline__ Hit frame_cast(const FrameView& F, float ox, float oy, float oz, float dx, float dy,
+                                          float dz) {
+    return F.svo_cast ? cast_svo(F.sv, F.quads, F.nq, F.spheres, ox, oy, oz, dx, dy, dz, 0.0f)
+                      : cast_closest(F.quads, F.nq, F.spheres, F.ns, ox, oy, oz, dx, dy, dz, 0.0f);
 }
 
 // survival test at 1-based vertex v (>= rr_depth): min(0.95, albedo)
@@ -115,7 +128,7 @@ __global__ void __launch_bounds__(256) k_camera(FrameView F, Queue S, uint32_t* 
     dx *= inv;
     dy *= inv;
     dz *= inv;
-    const Hit h = cast_closest(F.quads, F.nq, F.spheres, F.ns, F.eye[0], F.eye[1], F.eye[2], dx, dy, dz, 0.0f);
+    const Hit h = frame_cast(F, F.eye[0], F.eye[1], F.eye[2], dx, dy, dz);
     uint32_t flag = 0;
     F.nv[i] = 0;
     if (h.prim != kNone) {
@@ -174,7 +187,7 @@ __global__ void __launch_bounds__(256) k_shade(FrameView F, Queue Q, const float
             const float ox = Q.pos[3 * (size_t)s] + F.offset * nx;
             const float oy = Q.pos[3 * (size_t)s + 1] + F.offset * ny;
             const float oz = Q.pos[3 * (size_t)s + 2] + F.offset * nz;
-            const Hit h = cast_closest(F.quads, F.nq, F.spheres, F.ns, ox, oy, oz, dx, dy, dz, 0.0f);
+            const Hit h = frame_cast(F, ox, oy, oz, dx, dy, dz);
             if (h.prim != kNone) {
                 const size_t v = (size_t)(k + 1) * F.P + path;
                 const float hx = ox + h.t * dx, hy = oy + h.t * dy, hz = oz + h.t * dz;
@@ -323,6 +336,12 @@ struct wfpg_frame {
     unsigned long long* frames_run = nullptr;
     unsigned long long* guided = nullptr;
     double* scalar = nullptr;
+    wfpg_mlp* mlp = nullptr;
+    wfpg_learned_params lp{};
+    uint32_t learned_cap = 0;        // bins per depth the learned tables hold
+    float* tab_pdf = nullptr;        // [learned_cap][32 * 32]
+    float* tab_cr = nullptr;
+    float* tab_cm = nullptr;         // [learned_cap][32]
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     unsigned long long graph_kernels = 0;
@@ -372,6 +391,8 @@ struct wfpg_frame {
         F.rr_depth = p.rr_depth;
         F.pseed = purpose(p.seed, kPathPurpose);
         F.offset = 1e-4f * scene.size;
+        F.sv = svo_cast_view(svo);
+        F.svo_cast = p.caster == 2 || (p.caster == 0 && scene.n_quads + scene.n_spheres > 64);
         F.vT = vT;
         F.vLe = vLe;
         F.vpos = vpos;
@@ -409,10 +430,19 @@ struct wfpg_frame {
             int rc = bin_rays_impl(svo, Q.pos, Q.nrm, P, &bp, nullptr, bin_of_ray, ray_order, bin_offset, origin_ray,
                                    bin_cap, n_bins + k, bin_ws, bin_ws_bytes, st, fidx + k);
             if (rc != WFPG_OK) return rc;
-            wfpg_guide_params gp = p.guide;
-            gp.seed = p.seed;
-            rc = guide_fused_impl(svo, Q.pos, Q.nrm, origin_ray, n_bins + k, bin_cap, ray_order, bin_offset, Q.u,
-                                  p.alpha, &gp, dir, pdf, P, guide_ws, guide_ws_bytes, st, fidx + k);
+            if (p.proposal == 1) {  // learned: MLP tables for the bins' origins, then the mixture
+                if (!mlp) return WFPG_ERR_INVALID_ARG;
+                rc = guide_learned_build_pdf(mlp, Q.pos, Q.nrm, origin_ray, n_bins + k, learned_cap, &lp, tab_pdf,
+                                             tab_cr, tab_cm, st);
+                if (rc != WFPG_OK) return rc;
+                rc = sample_mix_impl(tab_pdf, tab_cr, tab_cm, 32, learned_cap, n_bins + k, bin_of_ray, Q.nrm, Q.u, P,
+                                     counters + k, p.alpha, dir, pdf, st);
+            } else {
+                wfpg_guide_params gp = p.guide;
+                gp.seed = p.seed;
+                rc = guide_fused_impl(svo, Q.pos, Q.nrm, origin_ray, n_bins + k, bin_cap, ray_order, bin_offset,
+                                      Q.u, p.alpha, &gp, dir, pdf, P, guide_ws, guide_ws_bytes, st, fidx + k);
+            }
             if (rc != WFPG_OK) return rc;
             WFPG_LAUNCH(k_shade, g, T, 0, st, F, Q, dir, pdf, stage, flags, k);
         }
@@ -463,6 +493,10 @@ static int check_params(const wfpg_frame_params* p, int depth_cap) {
     if (p->c_ray == 0) return ffail(WFPG_ERR_INVALID_ARG, "frame: c_ray must be >= 1");
     if (p->guide.split != 0 && p->guide.split != 0xFFFFFFFFu && p->guide.split < 2048)
         return ffail(WFPG_ERR_INVALID_ARG, "frame: guide.split must be 0, >= 2048 or 0xFFFFFFFF");
+    if (p->caster < 0 || p->caster > 2) return ffail(WFPG_ERR_INVALID_ARG, "frame: caster must be 0, 1 or 2");
+    if (p->proposal < 0 || p->proposal > 1) return ffail(WFPG_ERR_INVALID_ARG, "frame: proposal must be 0 or 1");
+    if (p->proposal == 1 && p->guide.N != 32)
+        return ffail(WFPG_ERR_INVALID_ARG, "frame: the learned proposal has N = 32");
     return WFPG_OK;
 }
 
@@ -545,6 +579,7 @@ int frame_destroy(wfpg_frame* f) {
 
 int frame_run(wfpg_frame* f, uint32_t n_frames, int use_graph, void* stream) {
     if (!f) return ffail(WFPG_ERR_INVALID_ARG, "frame_run: null frame");
+    if (f->p.proposal == 1 && !f->mlp) return ffail(WFPG_ERR_INVALID_ARG, "frame_run: learned proposal without MLP");
     auto st = static_cast<cudaStream_t>(stream);
     if (use_graph && !f->exec) {
         const int rc = f->capture(st);
@@ -567,6 +602,25 @@ int frame_set_params(wfpg_frame* f, const wfpg_frame_params* p) {
     if (const int rc = check_params(p, f->depth_cap)) return rc;
     f->drop_graph();
     f->p = *p;
+    return WFPG_OK;
+}
+
+int frame_set_mlp(wfpg_frame* f, wfpg_mlp* mlp, const wfpg_learned_params* lp) {
+    if (!f || (mlp && !lp)) return ffail(WFPG_ERR_INVALID_ARG, "frame_set_mlp: null argument");
+    f->drop_graph();
+    f->mlp = mlp;
+    if (!mlp) return WFPG_OK;
+    f->lp = *lp;
+    const uint32_t cap = std::min(f->bin_cap, mlp_max_batch(mlp));
+    if (cap > f->learned_cap) {  // grow the tables (kept for the frame's lifetime)
+        if (!f->alloc(&f->tab_pdf, (size_t)cap * 1024) || !f->alloc(&f->tab_cr, (size_t)cap * 1024) ||
+            !f->alloc(&f->tab_cm, (size_t)cap * 32)) {
+            cudaGetLastError();
+            f->mlp = nullptr;
+            return ffail(WFPG_ERR_OOM, "frame_set_mlp: device allocation failed");
+        }
+    }
+    f->learned_cap = cap;
     return WFPG_OK;
 }
 

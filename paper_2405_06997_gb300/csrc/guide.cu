@@ -18,6 +18,7 @@
 #include <algorithm>
 
 #include "common.cuh"
+#include "march.cuh"
 #include "sort.cuh"
 #include "svo.cuh"
 
@@ -83,65 +84,6 @@ __device__ __forceinline__ Node load_node(const TraceArgs& T, const Node* s_node
     n.first_child = v.x;
     n.mask = v.y;
     return n;
-}
-
-// time of the crossing into cell j along one axis: boundary j when moving up,
-// j + 1 when moving down; evaluated afresh from the integer boundary
-__device__ __forceinline__ float cross_time(int j, bool up, float g, float inv) {
-    return __fmul_rn(__fsub_rn((float)(up ? j : j + 1), g), inv);
-}
-
-// Index along one axis after every crossing strictly before time ts: the
-// leaf-by-leaf walk's coordinate once it has passed all crossings < ts.
-// May step one cell outside [0, res) (the ray left the grid before ts).
-__device__ __forceinline__ int skip_before(int c, float g, float inv, float ts, int res) {
-    if (inv == 0.0f) return c;
-    const bool up = inv > 0.0f;
-    for (int k = 0; k <= res; ++k) {
-        const int nxt = up ? c + 1 : c - 1;
-        if (!(cross_time(nxt, up, g, inv) < ts)) break;
-        c = nxt;
-        if (c < 0 || c >= res) break;
-    }
-    return c;
-}
-
-// Index along one axis that the leaf-by-leaf walk reaches at the crossing
-// (tx, a): the last cell of the block [lo, lo + size) on this axis whose
-// entry crossing comes before (tx, a) in (time, axis) order, starting from
-// the current index c.  `before` says whether this axis precedes axis a.
-__device__ __forceinline__ int advance_axis(int c, int lo, int size, float g, float inv, float ds, float tx,
-                                            bool before) {
-    if (inv == 0.0f || size == 1) return c;
-    const int hi = lo + size - 1;
-    int j = (int)floorf(g + tx * ds);  // estimate only; the checks below decide
-    j = max(lo, min(hi, j));
-    if (inv > 0.0f) {
-        j = max(j, c);
-        while (j < hi) {
-            const float tc = cross_time(j + 1, true, g, inv);
-            if (tc < tx || (tc == tx && before)) ++j;
-            else break;
-        }
-        while (j > c) {
-            const float tc = cross_time(j, true, g, inv);
-            if (tc < tx || (tc == tx && before)) break;
-            --j;
-        }
-    } else {
-        j = min(j, c);
-        while (j > lo) {
-            const float tc = cross_time(j - 1, false, g, inv);
-            if (tc < tx || (tc == tx && before)) --j;
-            else break;
-        }
-        while (j < c) {
-            const float tc = cross_time(j, false, g, inv);
-            if (tc < tx || (tc == tx && before)) break;
-            ++j;
-        }
-    }
-    return j;
 }
 
 // first index with x[i] > t (N if none) in a non-decreasing shared-memory row
@@ -702,6 +644,55 @@ __global__ void __launch_bounds__(256) k_guide_sample(const float* __restrict__ 
     cell[i] = (uint32_t)(r * N + c);
 }
 
+// one-sample mixture from stored tables (what the fused launch does from shared
+// memory): guided with probability alpha, else cosine; a ray whose bin has no
+// table (>= the built count) takes the cosine branch with alpha = 0
+__global__ void __launch_bounds__(256) k_sample_mix(const float* __restrict__ pdf, const float* __restrict__ cdf_row,
+                                                    const float* __restrict__ cdf_marg, int N, uint32_t bin_cap,
+                                                    const uint32_t* __restrict__ n_bins_dev,
+                                                    const uint32_t* __restrict__ bin_of_ray,
+                                                    const float* __restrict__ nrm, const float* __restrict__ u,
+                                                    uint32_t n_cap, const uint32_t* __restrict__ n_dev, float alpha,
+                                                    float* __restrict__ dir, float* __restrict__ pdf_out) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t n = n_dev ? min(*n_dev, n_cap) : n_cap;
+    if (i >= n) return;
+    const uint32_t nb = n_bins_dev ? min(*n_bins_dev, bin_cap) : bin_cap;
+    const uint32_t b = bin_of_ray[i];
+    const float u0 = u[3 * (size_t)i], u1 = u[3 * (size_t)i + 1], u2 = u[3 * (size_t)i + 2];
+    const float nx = nrm[3 * (size_t)i], ny = nrm[3 * (size_t)i + 1], nz = nrm[3 * (size_t)i + 2];
+    const int NN = N * N;
+    float3 d;
+    float pg = 0.0f, a = alpha;
+    if (b >= nb) {
+        a = 0.0f;
+        d = cosine_dir(nx, ny, nz, u0, u1);
+    } else if (u2 < alpha) {
+        const float* M = cdf_marg + (size_t)b * N;
+        const float t0 = __fmul_rn(u0, M[N - 1]);
+        const int r = min(upper_bound_f(M, N, t0), N - 1);
+        const float* C = cdf_row + ((size_t)b * N + r) * N;
+        const float t1 = __fmul_rn(u1, C[N - 1]);
+        const int c = min(upper_bound_f(C, N, t1), N - 1);
+        const float mlo = r > 0 ? M[r - 1] : 0.0f, mhi = M[r];
+        const float clo = c > 0 ? C[c - 1] : 0.0f, chi = C[c];
+        const float beta = clamp01(__fdiv_rn(__fsub_rn(t0, mlo), __fsub_rn(mhi, mlo)));
+        const float al = clamp01(__fdiv_rn(__fsub_rn(t1, clo), __fsub_rn(chi, clo)));
+        const float tn = __fdiv_rn(2.0f, (float)N);
+        d = octa_to_dir(__fsub_rn(__fmul_rn(__fadd_rn((float)c, al), tn), 1.0f),
+                        __fsub_rn(__fmul_rn(__fadd_rn((float)r, beta), tn), 1.0f));
+        pg = pdf[(size_t)b * NN + r * N + c];
+    } else {
+        d = cosine_dir(nx, ny, nz, u0, u1);
+        pg = pdf[(size_t)b * NN + octa_cell(d, N)];
+    }
+    const float cs = fmaxf(0.0f, nx * d.x + ny * d.y + nz * d.z);
+    dir[3 * (size_t)i] = d.x;
+    dir[3 * (size_t)i + 1] = d.y;
+    dir[3 * (size_t)i + 2] = d.z;
+    pdf_out[i] = a * pg + (1.0f - a) * cs * 0.31830988618379067f;
+}
+
 __global__ void __launch_bounds__(256) k_guide_eval(const float* __restrict__ pdf, int N, uint32_t bin_cap,
                                                     const uint32_t* __restrict__ bin, const float* __restrict__ dir,
                                                     uint32_t n, float* __restrict__ out) {
@@ -877,6 +868,15 @@ int guide_sample_impl(const float* pdf, const float* cdf_row, const float* cdf_m
     if (n == 0) return WFPG_OK;
     WFPG_LAUNCH(k_guide_sample, div_up(n, 256), 256, 0, st, pdf, cdf_row, cdf_marg, N, bin_cap, bin_of_ray,
                                                    reinterpret_cast<const float2*>(u), n, dir, pdf_out, cell);
+    return cudaGetLastError() == cudaSuccess ? WFPG_OK : WFPG_ERR_CUDA;
+}
+
+int sample_mix_impl(const float* pdf, const float* cdf_row, const float* cdf_marg, int N, uint32_t bin_cap,
+                    const uint32_t* n_bins_dev, const uint32_t* bin_of_ray, const float* nrm, const float* u,
+                    uint32_t n, const uint32_t* n_dev, float alpha, float* dir, float* pdf_out, cudaStream_t st) {
+    if (n == 0) return WFPG_OK;
+    WFPG_LAUNCH(k_sample_mix, div_up(n, 256), 256, 0, st, pdf, cdf_row, cdf_marg, N, bin_cap, n_bins_dev, bin_of_ray,
+                nrm, u, n, n_dev, alpha, dir, pdf_out);
     return cudaGetLastError() == cudaSuccess ? WFPG_OK : WFPG_ERR_CUDA;
 }
 

@@ -399,6 +399,10 @@ int mlp_fail(int code, const std::string& msg) { return wfpg::set_last_error(cod
 
 }  // namespace
 
+namespace wfpg {
+uint32_t mlp_max_batch(const wfpg_mlp* m) { return m->max_batch; }
+}  // namespace wfpg
+
 extern "C" {
 
 int mlp_create(const float* params, uint32_t max_batch, void* stream, wfpg_mlp** out) {

@@ -74,7 +74,7 @@ class Camera(C.Structure):
 
 class FrameParams(C.Structure):
     _fields_ = [("max_depth", I32), ("rr_depth", I32), ("alpha", F), ("l_min", I32), ("c_ray", U32),
-                ("guide", GuideParams), ("seed", U64), ("update", I32)]
+                ("guide", GuideParams), ("seed", U64), ("update", I32), ("caster", I32), ("proposal", I32)]
 
 
 class FrameStats(C.Structure):
@@ -124,6 +124,9 @@ def lib():
             "frame_stats": [P, P, P],
             "frame_autotune": [P, P, I32, U32, P, P, P],
             "frame_export": [P, I32, P, SZ, P],
+            "frame_set_mlp": [P, P, P],
+            "guide_sample_mix": [P, P, P, I32, U32, P, P, P, P, U32, P, F, P, P, P],
+            "wfpg_cast_rays_svo": [P, P, P, P, U32, F, P, P, P, P],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -577,6 +580,44 @@ def cast_rays(quads, spheres, o, d, tmin=1e-5, with_normal=True, stream=None):
     return t, prim, nrm
 
 
+def cast_rays_svo(svo: SVO, quads, spheres, o, d, tmin=1e-5, with_normal=True, stream=None):
+    """cast_rays with the scene's SVO as the acceleration structure (the SVO
+    must have been built from these quads and spheres)."""
+    n = o.shape[0]
+    sc = Scene()
+    sc.quads = _ptr(quads, torch.float32) if quads.numel() else None
+    sc.n_quads = quads.shape[0] if quads.numel() else 0
+    sc.spheres = _ptr(spheres, torch.float32) if spheres.numel() else None
+    sc.n_spheres = spheres.shape[0] if spheres.numel() else 0
+    t = torch.empty(n, dtype=torch.float32, device=o.device)
+    prim = torch.empty(n, dtype=torch.int32, device=o.device)
+    nrm = torch.empty((n, 3), dtype=torch.float32, device=o.device) if with_normal else None
+    _check(lib().wfpg_cast_rays_svo(svo.handle, C.byref(sc), _ptr(o, torch.float32, 3 * n),
+                                    _ptr(d, torch.float32, 3 * n), n, float(tmin), _ptr(t, torch.float32),
+                                    _ptr(prim, torch.int32), _ptr(nrm, torch.float32) if with_normal else None,
+                                    _stream(stream)))
+    return t, prim, nrm
+
+
+def guide_sample_mix(pdf, cdf_row, cdf_marg, N, bins, nrm, u, *, alpha=0.5, n_bins=None, n_dev=None, out=None,
+                     stream=None):
+    """One-sample mixture (guided with probability alpha, else cosine) from
+    stored tables.  bins: bin_of_ray (int32); u: [n, 3].  Returns (dir, pdf)."""
+    n = bins.numel()
+    bin_cap = cdf_marg.numel() // N
+    if out is None:
+        out = (torch.empty((n, 3), dtype=torch.float32, device=u.device),
+               torch.empty(n, dtype=torch.float32, device=u.device))
+    d, pm = out
+    _check(lib().guide_sample_mix(_ptr(pdf, torch.float32), _ptr(cdf_row, torch.float32),
+                                  _ptr(cdf_marg, torch.float32), N, bin_cap, _ptr(n_bins, torch.int32, 1, "n_bins"),
+                                  _ptr(bins, torch.int32, n), _ptr(nrm, torch.float32, 3 * n, "nrm"),
+                                  _ptr(u, torch.float32, 3 * n, "u"), n, _ptr(n_dev, torch.int32, 1, "n_dev"),
+                                  alpha, _ptr(d, torch.float32, 3 * n), _ptr(pm, torch.float32, n),
+                                  _stream(stream)))
+    return d, pm
+
+
 class Frame:
     """Batched wavefront frame over an SVO (frame_create .. frame_destroy).
 
@@ -588,7 +629,7 @@ class Frame:
     def __init__(self, svo: SVO, scene, *, eye, forward=(0.0, 0.0, 1.0), up=(0.0, 1.0, 0.0), vfov=60.0,
                  width=1920, height=1080, max_depth=4, rr_depth=2, alpha=0.5, l_min=2, c_ray=512, N=32,
                  eps=1e-2, jitter=True, blur=True, cos_weight=False, block=0, stage=0, seed=1, update=True,
-                 device="cuda", stream=None):
+                 caster=0, proposal=0, device="cuda", stream=None):
         self.svo = svo
         self._q = torch.as_tensor(np.ascontiguousarray(scene.quads, np.float32).reshape(-1, 8), device=device)
         self._s = torch.as_tensor(np.ascontiguousarray(scene.spheres, np.float32).reshape(-1, 4), device=device)
@@ -604,7 +645,7 @@ class Frame:
                          t_skip=default_t_skip(svo.size, svo.depth), cos_weight=int(cos_weight), seed=seed,
                          frame=0, block=block, stage=stage)
         self.params = FrameParams(max_depth=max_depth, rr_depth=rr_depth, alpha=alpha, l_min=l_min, c_ray=c_ray,
-                                  guide=gp, seed=seed, update=int(update))
+                                  guide=gp, seed=seed, update=int(update), caster=caster, proposal=proposal)
         self.device = device
         h = P()
         _check(lib().frame_create(svo.handle, C.byref(self._scene), _ptr(self._e), _ptr(self._a),
@@ -635,6 +676,13 @@ class Frame:
                 setattr(p, k, v)
         _check(lib().frame_set_params(self.handle, C.byref(p)))
         self.params = p
+
+    def set_mlp(self, mlp, lo, size, eps=1e-4):
+        """Attach the learned proposal's MLP (the frame keeps a reference)."""
+        self._mlp = mlp
+        lp = LearnedParams(lo=(F * 3)(*[float(v) for v in lo]), size=float(size), eps=float(eps))
+        _check(lib().frame_set_mlp(self.handle, mlp.handle if mlp is not None else None,
+                                   C.byref(lp) if mlp is not None else None))
 
     def get_params(self):
         p = FrameParams()

@@ -46,7 +46,9 @@ def test_ctypes_structs_match_the_header(tmp_path):
     from paper_2405_06997_gb300 import wfpg as W
 
     structs = {"wfpg_scene": W.Scene, "wfpg_bin_params": W.BinParams, "wfpg_guide_params": W.GuideParams,
-               "wfpg_camera": W.Camera, "wfpg_frame_params": W.FrameParams, "wfpg_frame_stats": W.FrameStats}
+               "wfpg_camera": W.Camera, "wfpg_frame_params": W.FrameParams, "wfpg_frame_stats": W.FrameStats,
+               "wfpg_learned_params": W.LearnedParams, "wfpg_adam_params": W.AdamParams,
+               "wfpg_svo_info": W.SvoInfo}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "wfpg.h"', "int main(void) {"]
     for cname, cls in structs.items():
         lines.append(f'printf("{cname} %zu\\n", sizeof({cname}));')

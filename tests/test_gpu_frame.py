@@ -246,3 +246,121 @@ def test_frame_rejects_bad_params():
         f.set_params(max_depth=3)
     with pytest.raises(W.WfpgError):
         f.set_params(N=12)
+
+
+# ------------------------------------------------- table-based mixture sampling
+def test_sample_mix_from_tables_equals_fused():
+    """guide_build_pdf + guide_sample_mix give guide_build_sample's directions
+    and densities bit for bit (same field, same per-ray arithmetic)."""
+    w, g, _ = box_svo(9)
+    n = w.ray_pos.shape[0]
+    pos, nrm = dev(w.ray_pos), dev(w.ray_nrm)
+    u = dev(inputs.uniforms24(31, (n, 3)))
+    r = W.bin_rays(g, pos, nrm, l_min=2, c_ray=64, seed=4, frame=2)
+    kw = dict(N=32, jitter=True, blur=True, seed=4, frame=2)
+    d0, p0 = W.guide_build_sample(g, pos, nrm, r, u, alpha=0.4, **kw)
+    tabs = W.guide_build_pdf(g, pos, r["origin_ray"], r["n_bins"], r["bin_cap"], **kw)
+    d1, p1 = W.guide_sample_mix(*tabs, 32, r["bin_of_ray"], nrm, u, alpha=0.4, n_bins=r["n_bins"])
+    assert torch.equal(d0, d1) and torch.equal(p0, p1)
+    # a bin without a table takes the cosine branch with density cos / pi
+    nb0 = torch.zeros(1, dtype=torch.int32, device="cuda")
+    d2, p2 = W.guide_sample_mix(*tabs, 32, r["bin_of_ray"], nrm, u, alpha=0.4, n_bins=nb0)
+    oc = OF.cosine_dirs(w.ray_nrm.astype(np.float64), inputs.uniforms24(31, (n, 3))[:, :2].astype(np.float64))
+    np.testing.assert_allclose(d2.cpu().numpy(), oc, rtol=0, atol=4e-6)
+    cs = np.maximum(0, np.einsum("ij,ij->i", w.ray_nrm.astype(np.float64), d2.cpu().numpy().astype(np.float64)))
+    np.testing.assert_allclose(p2.cpu().numpy(), cs / np.pi, rtol=1e-5, atol=1e-7)
+
+
+# ------------------------------------------------------------- SVO ray caster
+def _random_rays(scene, n, seed, inside=True):
+    rng = np.random.default_rng(seed)
+    lo, S = np.asarray(scene.lo, np.float64), float(scene.size)
+    o = lo + S * rng.uniform(0.02, 0.98, (n, 3))
+    if not inside:
+        o[: n // 2] = lo + S * rng.uniform(-0.5, 1.5, (n // 2, 3))
+    d = rng.normal(size=(n, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    return o.astype(np.float32), d.astype(np.float32)
+
+
+@pytest.mark.parametrize("name", ["spheres", "city"])
+def test_svo_caster_matches_brute_force(name):
+    if name == "spheres":
+        sc, D = inputs.cornell_spheres(3), 8
+    else:
+        sc, D = inputs.city(2, n_boxes=300, n_lights=10), 9
+    g = W.svo_from_scene(sc, D)
+    q, sp = dev(sc.quads), dev(sc.spheres)
+    o, d = _random_rays(sc, 20000, 5, inside=(name == "spheres"))
+    t0, p0, n0 = W.cast_rays(q, sp, dev(o), dev(d), tmin=1e-4)
+    t1, p1, n1 = W.cast_rays_svo(g, q, sp, dev(o), dev(d), tmin=1e-4)
+    t0, p0, t1, p1 = t0.cpu().numpy(), p0.cpu().numpy(), t1.cpu().numpy(), p1.cpu().numpy()
+    same = p0 == p1
+    # where both name the same primitive the distance is the same arithmetic
+    np.testing.assert_array_equal(t0[same], t1[same])
+    # a different primitive only where two surfaces are hit at nearly the same distance
+    diff = ~same
+    assert diff.sum() <= 0.001 * len(p0), diff.sum()
+    hit = diff & (p0 >= 0) & (p1 >= 0)
+    np.testing.assert_allclose(t1[hit], t0[hit], rtol=2e-5)
+    assert np.all(p0[diff & (p1 < 0)] < 0) or diff.sum() == 0
+    assert (p0 >= 0).mean() > 0.05
+
+
+# ------------------------------------------------------------- frame options
+def test_frame_svo_caster_gives_the_same_image():
+    w, g1, _ = box_svo(10)
+    _, g2, _ = box_svo(10)
+    f1 = make_frame(g1, w.scene, caster=1, width=128, height=72)
+    f2 = make_frame(g2, w.scene, caster=2, width=128, height=72)
+    f1.run(4)
+    f2.run(4)
+    m1, _ = f1.image()
+    m2, _ = f2.image()
+    differ = (m1 != m2).float().mean().item()
+    assert differ < 0.01, differ
+    assert abs(m1.mean().item() - m2.mean().item()) < 0.01 * m1.mean().item()
+
+
+def test_frame_learned_proposal():
+    """Learned mode: the frame's guiding equals guide_learned_build_pdf +
+    guide_sample_mix on its own queue, and its frames stay unbiased."""
+    w, g, _ = box_svo(11)
+    mlp = W.MLP(inputs.mlp_init(5), max_batch=4096)
+    f = make_frame(g, w.scene, max_depth=1, update=False, N=32, c_ray=128, proposal=1)
+    with pytest.raises(W.WfpgError):
+        f.run(1)  # no MLP attached yet
+    f.set_mlp(mlp, w.scene.lo, w.scene.size)
+    f.run(1, use_graph=False)
+    n = f.stats()["paths"][0]
+    qp, qn, qu = (f.export(k)[:n].contiguous() for k in ("q_pos", "q_nrm", "q_u"))
+    r = W.bin_rays(g, qp, qn, l_min=2, c_ray=128, seed=3, frame=0, bin_cap=min(f.pixels, g.n_nodes))
+    cap = min(r["bin_cap"], 4096)
+    tabs = W.guide_learned_build_pdf(mlp, qp, qn, r["origin_ray"], r["n_bins"], cap, lo=w.scene.lo,
+                                     size=w.scene.size)
+    d, pm = W.guide_sample_mix(*tabs, 32, r["bin_of_ray"], qn, qu, alpha=0.5, n_bins=r["n_bins"])
+    assert torch.equal(f.export("q_dir")[:n], d)
+    assert torch.equal(f.export("q_pdf")[:n], pm)
+    # unbiased: learned-guided frames agree with cosine-only frames
+    frames, res = 40, {}
+    for alpha in (0.0, 0.5):
+        fr = make_frame(g, w.scene, width=96, height=54, alpha=alpha, max_depth=3, N=32, proposal=1,
+                        seed=21 + int(alpha * 10))
+        fr.set_mlp(mlp, w.scene.lo, w.scene.size)
+        fr.run(frames)
+        m, v = fr.image()
+        res[alpha] = (float(m.double().mean()), float(np.sqrt(v.double().sum().item() / frames) / fr.pixels))
+    (mu0, s0), (mu1, s1) = res[0.0], res[0.5]
+    assert abs(mu1 - mu0) < 5 * np.hypot(s0, s1), res
+
+
+def test_city_frame_runs_with_the_svo_caster():
+    sc = inputs.city(3, n_boxes=400, n_lights=12)
+    g = W.svo_from_scene(sc, 9)
+    f = W.Frame(g, sc, eye=(250.0, 120.0, -60.0), forward=(0.0, -0.3939193, 0.9191450),
+                up=(0.0, 0.9191450, 0.3939193), vfov=60.0, width=192, height=108, max_depth=3, N=32, seed=2)
+    f.run(3)
+    st = f.stats()
+    m, _ = f.image()
+    assert st["status"] == 0 and st["paths"][0] > 0.3 * f.pixels
+    assert torch.isfinite(m).all() and m.mean().item() > 0
