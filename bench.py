@@ -57,6 +57,10 @@ def parse():
     ap.add_argument("--learned-frames", type=int, default=16, help="frames of the equal-spp comparison")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-frame section")
     ap.add_argument("--batched-frames", type=int, default=20, help="timed frames of the batched section")
+    ap.add_argument("--no-city", action="store_true", help="skip the large city section")
+    ap.add_argument("--city-only", action="store_true", help="run only the city section and print it")
+    ap.add_argument("--city-frames", type=int, default=8, help="frames per proposal in the city section")
+    ap.add_argument("--city-train-steps", type=int, default=200, help="online training steps on the city")
     ap.add_argument("--batched-only", action="store_true",
                     help="run only the batched section with a fixed N = 32 tile (for profiling) and print it")
     return ap.parse_args()
@@ -414,6 +418,8 @@ def run_gpu(args, world, rank, local):
         line["learned"] = learned_section(args, w, svo)
     if not args.no_batched:
         line["batched"] = batched_section(args)
+    if not args.no_city:
+        line["city"] = city_section(args)
     if not args.no_cpu_baseline:
         t_frame, detail = oracle_frame_time(w, mis, args.cpu_bins)
         line["cpu_baseline"] = {
@@ -496,6 +502,71 @@ def batched_section(args, autotune=True):
             "status": st["status"], "l2": "working set (path state ~0.6 GB) larger than L2"}
 
 
+def city_section(args):
+    """The large configuration: procedural city (5000 boxes, 50 area lights,
+    S = 500), SVO depth 11 (2048^3), 3840x2160, 4 guided bounces, closest hits
+    by the SVO walk, 64 x 64 traced fields; the learned proposal trained online
+    on the city's traced fields, used or replaced by the traced field by the
+    fallback rule; both proposals mixed 50/50 with cosine (BSDF) sampling."""
+    import torch
+    from paper_2405_06997_gb300 import inputs, learned as LG, wfpg as W
+    sc = inputs.city(args.seed)
+    q = torch.from_numpy(np.ascontiguousarray(sc.quads)).cuda()
+    sp = torch.from_numpy(np.ascontiguousarray(sc.spheres)).cuda()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    svo = W.svo_build(q, sp, sc.lo, sc.size, 11)
+    b.record()
+    b.synchronize()
+    build_ms = a.elapsed_time(b)
+    cam = dict(eye=(250.0, 100.0, -50.0), forward=(0.0, -0.31622777, 0.9486833), up=(0.0, 0.9486833, 0.31622777),
+               vfov=60.0, width=3840, height=2160, max_depth=4, rr_depth=2, alpha=0.5, l_min=2, c_ray=512,
+               seed=args.seed, caster=2)
+    out = {"workload": "city (5000 boxes log-U[0.5, 20], 50 area lights, S 500), SVO depth 11, camera at "
+                       "(250, 100, -50) looking down 18.4 deg, vfov 60, 3840x2160, 4 guided bounces, RR from "
+                       "vertex 2, alpha 0.5, Partition-S l_min 2 c_ray 512, closest hits by the SVO walk",
+           "svo_build_ms": build_ms, "svo_nodes": svo.n_nodes, "svo_leaves": int(svo.level_off[12] - svo.level_off[11])}
+    # the traced proposal (64 x 64) warms the cache, then is timed
+    f = W.Frame(svo, sc, N=64, **cam)
+    f.run(4)
+    f.reset_image()
+    torch.cuda.synchronize()
+
+    def timed(frame, n):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        frame.reset_image()
+        e0.record()
+        frame.run(n)
+        e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / n
+        st = frame.stats()
+        m, v = frame.image()
+        return {"ms_per_frame": ms, "guided_samples_per_s": st["guided_samples"] / (ms * n / 1e3),
+                "paths_per_depth": st["paths"], "bins_per_depth": st["bins"], "records_per_frame": st["records"],
+                "mean_pixel_variance": float(v.double().mean()), "mean_radiance": float(m.double().mean()),
+                "status": st["status"], "graph_kernels_per_frame": st["kernels_per_frame"]}
+
+    out["svo_traced_64"] = timed(f, args.city_frames)
+    # the learned proposal: trained online against traced 32 x 32 fields of the city
+    tr = LG.OnlineTrainer(svo, sc, batch=65536, pool=1 << 20, lr=1e-3, seed=args.seed)
+    t0 = time.perf_counter()
+    tr.train(args.city_train_steps)
+    train_s = time.perf_counter() - t0
+    kl = tr.heldout_kl()
+    tau = 1.5 * LG.traced_frame_kl(tr)
+    fl = W.Frame(svo, sc, N=32, proposal=1, **cam)
+    fl.set_mlp(tr.mlp, sc.lo, sc.size)
+    fl.run(2)
+    out["learned_32"] = timed(fl, args.city_frames)
+    use = LG.use_learned(kl, tau)
+    out["learned_training"] = {"steps": args.city_train_steps, "batch_bins": 65536, "seconds": train_s,
+                               "heldout_kl": kl, "fallback_threshold": tau, "uses_learned": use}
+    out["chosen"] = "learned" if use else "svo_traced (fallback)"
+    return out
+
+
 def trace_algorithmic_bytes(w, B, N, sample_bins=8):
     """Bytes the field kernel must move for one launch: its outputs (pdf,
     cdf_row, cdf_marg: B (2 N^2 + N) 4 B) plus, per cone ray, one 8-byte node
@@ -535,7 +606,11 @@ def read_profile_traffic():
 def main():
     args = parse()
     world, rank, local = dist_init(args.gpus)
-    if args.batched_only:
+    if args.city_only:
+        import torch
+        torch.cuda.set_device(local)
+        print(json.dumps(city_section(args)))
+    elif args.batched_only:
         import torch
         torch.cuda.set_device(local)
         print(json.dumps(batched_section(args, autotune=False)))
