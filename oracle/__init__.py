@@ -87,7 +87,7 @@ def _declare(L):
         "orc_warp_scan": (None, [P, I32]),
         "orc_blur": (None, [P, I32]),
         "orc_pdf_cdf": (None, [P, I32, P, P, P]),
-        "orc_trace": (None, [P, P, P, SZ, F, F, I32, P, P, P, P, P, P, P, P]),
+        "orc_trace": (None, [P, P, P, SZ, F, F, I32, P, P, P, P, P, P, P, P, P]),
         "orc_mlp_num_params": (SZ, []),
         "orc_mlp_features": (None, [P, P, SZ, P, F, P]),
         "orc_mlp_forward": (None, [P, P, P, SZ, P, F, I32, P, P]),
@@ -232,10 +232,11 @@ class SVO:
         out = dict(hit=np.zeros(n, np.int32), leaf_key=np.zeros(n, np.uint64),
                    t_entry=np.zeros(n, np.float32), level=np.zeros(n, np.int32),
                    node=np.zeros(n, np.uint32), side=np.zeros(n, np.int32),
-                   value=np.zeros(n, np.float32), steps=np.zeros(n, np.uint32))
+                   value=np.zeros(n, np.float32), steps=np.zeros(n, np.uint32),
+                   blocks=np.zeros(n, np.uint32))
         lib().orc_trace(self._h, _p(o), _p(d), n, float(t_skip), float(omega), int(cos_weight),
                         *[_p(out[k]) for k in ("hit", "leaf_key", "t_entry", "level", "node",
-                                               "side", "value", "steps")])
+                                               "side", "value", "steps", "blocks")])
         return out
 
 

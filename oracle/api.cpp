@@ -155,10 +155,12 @@ void orc_pdf_cdf(const float* f, int N, float* pdf, float* cdf_row, float* cdf_m
 }
 void orc_trace(const void* sv, const float* o, const float* d, size_t n, float t_skip,
                float omega, int cos_weight, int32_t* hit, uint64_t* leaf_key, float* t_entry,
-               int32_t* level, uint32_t* node, int32_t* side, float* value, uint32_t* steps) {
+               int32_t* level, uint32_t* node, int32_t* side, float* value, uint32_t* steps,
+               uint32_t* blocks) {
     const Svo* s = static_cast<const Svo*>(sv);
     for (size_t i = 0; i < n; ++i) {
-        TraceResult r = trace_cell(*s, o + 3 * i, d + 3 * i, t_skip, omega, cos_weight);
+        TraceResult r = trace_cell(*s, o + 3 * i, d + 3 * i, t_skip, omega, cos_weight, blocks != nullptr);
+        if (blocks) blocks[i] = r.blocks;
         hit[i] = r.hit;
         leaf_key[i] = r.hit ? r.leaf_key : 0;
         t_entry[i] = r.hit ? r.t_entry : 0.0f;

@@ -76,7 +76,8 @@ void orc_blur(float* f, int N);
 void orc_pdf_cdf(const float* f, int N, float* pdf, float* cdf_row, float* cdf_marg);
 void orc_trace(const void* svo, const float* o, const float* d, size_t n, float t_skip,
                float omega, int cos_weight, int32_t* hit, uint64_t* leaf_key, float* t_entry,
-               int32_t* level, uint32_t* node, int32_t* side, float* value, uint32_t* steps);
+               int32_t* level, uint32_t* node, int32_t* side, float* value, uint32_t* steps,
+               uint32_t* blocks);
 
 #ifdef __cplusplus
 }

@@ -227,6 +227,91 @@ __device__ __forceinline__ float warp_scan_row(const float* src, float* dst, int
 // kGuideThreads threads work on one bin at a time; kStage: the chunk's cone
 // directions are computed by all threads together into shared memory before
 // the march (otherwise each lane computes its ray's direction when it takes it)
+constexpr int kWbWords = 11;  // per buffered ray: cell, d (3), 1/(d 2^D/S) (3), t, start cell (3)
+
+// direction of cell c (jittered point or centre) and its per-axis reciprocal
+// 1 / (d 2^D / S) (0 on an axis the ray does not move along)
+__device__ __forceinline__ void cell_ray(const TraceArgs& T, const GuideArgs& G, int c, uint64_t jseed,
+                                         uint64_t jstream, float tn, float3* d, float3* iv) {
+    const int N = G.N;
+    const int i = c % N, j = c / N;
+    float x0 = 0.5f, x1 = 0.5f;
+    if (G.jitter) {
+        x0 = uniform01(jseed, jstream, 2ull * c);
+        x1 = uniform01(jseed, jstream, 2ull * c + 1);
+    }
+    const float u = __fsub_rn(__fmul_rn(__fadd_rn((float)i, x0), tn), 1.0f);
+    const float v = __fsub_rn(__fmul_rn(__fadd_rn((float)j, x1), tn), 1.0f);
+    *d = octa_to_dir(u, v);
+    iv->x = d->x != 0.0f ? __fdiv_rn(1.0f, __fmul_rn(d->x, T.scale)) : 0.0f;
+    iv->y = d->y != 0.0f ? __fdiv_rn(1.0f, __fmul_rn(d->y, T.scale)) : 0.0f;
+    iv->z = d->z != 0.0f ? __fdiv_rn(1.0f, __fmul_rn(d->z, T.scale)) : 0.0f;
+}
+
+// start of a cone ray: the cell holding the origin (or the slab entry into the
+// grid box, with its entry time), then every crossing strictly before t_skip
+// taken at once (no cell entered before t_skip can be the hit).  False if the
+// ray never reaches a cell at t_skip inside the grid.
+__device__ __forceinline__ bool ray_start(const TraceArgs& T, bool has_origin, bool inside, float gx, float gy,
+                                          float gz, float dx, float dy, float dz, float ivx, float ivy, float ivz,
+                                          int res, float fres, float* t, int* cx, int* cy, int* cz) {
+    const float INF = __int_as_float(0x7f800000);
+    bool alive = has_origin;
+    *t = 0.0f;
+    if (alive && inside) {
+        *cx = min((int)gx, res - 1);
+        *cy = min((int)gy, res - 1);
+        *cz = min((int)gz, res - 1);
+    } else if (alive) {
+        // slab entry into the grid box
+        float tnr = 0.0f, tfr = INF;
+        int enter = -1;
+        const float gg[3] = {gx, gy, gz}, iv[3] = {ivx, ivy, ivz};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            if (iv[a] == 0.0f) {
+                if (!(gg[a] >= 0.0f && gg[a] <= fres)) alive = false;
+                continue;
+            }
+            const float t0 = __fmul_rn(__fsub_rn(0.0f, gg[a]), iv[a]);
+            const float t1 = __fmul_rn(__fsub_rn(fres, gg[a]), iv[a]);
+            const float lo_t = (t1 < t0) ? t1 : t0;
+            const float hi_t = (t0 < t1) ? t1 : t0;
+            if (lo_t > tnr) {
+                tnr = lo_t;
+                enter = a;
+            }
+            tfr = (hi_t < tfr) ? hi_t : tfr;
+        }
+        if (!(tnr <= tfr)) alive = false;
+        if (alive) {
+            *t = tnr;
+            const float dd[3] = {dx, dy, dz};
+            int cc[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                if (a == enter) {
+                    cc[a] = iv[a] > 0.0f ? 0 : res - 1;
+                } else {
+                    const float p = __fadd_rn(gg[a], __fmul_rn(tnr, __fmul_rn(dd[a], T.scale)));
+                    const int c = (p >= 0.0f) ? (int)p : 0;
+                    cc[a] = min(c, res - 1);
+                }
+            }
+            *cx = cc[0];
+            *cy = cc[1];
+            *cz = cc[2];
+        }
+    }
+    if (alive && *t < T.t_skip) {
+        *cx = skip_before(*cx, gx, ivx, T.t_skip, res);
+        *cy = skip_before(*cy, gy, ivy, T.t_skip, res);
+        *cz = skip_before(*cz, gz, ivz, T.t_skip, res);
+        if (*cx < 0 || *cx >= res || *cy < 0 || *cy >= res || *cz < 0 || *cz >= res) alive = false;
+    }
+    return alive;
+}
+
 // 1280 resident threads per SM (40 warps): at most 51 registers a thread, the
 // budget the unfused kernel fits in, so the fused variant keeps its occupancy
 template <int kGuideThreads, bool kStage, bool kFused>
@@ -244,7 +329,8 @@ __global__ void __launch_bounds__(kGuideThreads, 1280 / kGuideThreads) k_guide_b
     Node* s_nodes = reinterpret_cast<Node*>(smem);
     uint32_t* s_stack = reinterpret_cast<uint32_t*>(smem + sizeof(Node) * T.smem_nodes);
     float* s_ray = reinterpret_cast<float*>(s_stack + (D + 1) * kGuideThreads);  // 6 x chunk: d, 1/(d 2^D/S)
-    float* field = s_ray + (kStage ? 6 * chunk : 0);
+    float* wbuf = s_ray;  // unstaged: per warp, kWbWords x 32 entries of ready rays
+    float* field = s_ray + (kStage ? 6 * chunk : (kGuideThreads / 32) * kWbWords * 32);
     float* tmp = field + NN;
     float* rowtot = tmp + NN;
     float* marg = rowtot + N;
@@ -283,22 +369,14 @@ __global__ void __launch_bounds__(kGuideThreads, 1280 / kGuideThreads) k_guide_b
         for (int c0 = 0; c0 < NN; c0 += chunk) {
             // ---- directions of this chunk's cells, computed by all threads together
             for (int q = tid; kStage && q < chunk; q += kGuideThreads) {
-                const int c = c0 + q;
-                const int i = c % N, j = c / N;
-                float x0 = 0.5f, x1 = 0.5f;
-                if (G.jitter) {
-                    x0 = uniform01(jseed, jstream, 2ull * c);
-                    x1 = uniform01(jseed, jstream, 2ull * c + 1);
-                }
-                const float u = __fsub_rn(__fmul_rn(__fadd_rn((float)i, x0), tn), 1.0f);
-                const float v = __fsub_rn(__fmul_rn(__fadd_rn((float)j, x1), tn), 1.0f);
-                const float3 d = octa_to_dir(u, v);
+                float3 d, iv;
+                cell_ray(T, G, c0 + q, jseed, jstream, tn, &d, &iv);
                 s_ray[0 * chunk + q] = d.x;
                 s_ray[1 * chunk + q] = d.y;
                 s_ray[2 * chunk + q] = d.z;
-                s_ray[3 * chunk + q] = d.x != 0.0f ? __fdiv_rn(1.0f, __fmul_rn(d.x, T.scale)) : 0.0f;
-                s_ray[4 * chunk + q] = d.y != 0.0f ? __fdiv_rn(1.0f, __fmul_rn(d.y, T.scale)) : 0.0f;
-                s_ray[5 * chunk + q] = d.z != 0.0f ? __fdiv_rn(1.0f, __fmul_rn(d.z, T.scale)) : 0.0f;
+                s_ray[3 * chunk + q] = iv.x;
+                s_ray[4 * chunk + q] = iv.y;
+                s_ray[5 * chunk + q] = iv.z;
             }
             if (tid == 0) s_next = 0;
             __syncthreads();
@@ -307,113 +385,104 @@ __global__ void __launch_bounds__(kGuideThreads, 1280 / kGuideThreads) k_guide_b
             float dx = 0.f, dy = 0.f, dz = 0.f, ivx = 0.f, ivy = 0.f, ivz = 0.f, t = 0.f;
             int cx = 0, cy = 0, cz = 0, level = 0, steps = 0;
             uint32_t node = 0;
+            int wb_n = 0, wb_head = 0;  // unstaged: entries in this warp's ray buffer, next one to hand out
+            bool wb_dry = false;        // unstaged: no cells of the chunk left for this warp
+            float* wb = wbuf + warp * (kWbWords * 32);
             for (;;) {
                 const bool idle = q < 0;
                 const uint32_t need = __ballot_sync(0xffffffffu, idle);
-                if (need) {
-                    const int leader = __ffs(need) - 1;
-                    int base = 0;
-                    if (lane == leader) base = atomicAdd(&s_next, __popc(need));
-                    base = __shfl_sync(0xffffffffu, base, leader);
-                    if (idle) {
-                        q = base + __popc(need & lt);
-                        if (q < chunk) {
-                            if (kStage) {
+                if (kStage) {
+                    if (need) {
+                        const int leader = __ffs(need) - 1;
+                        int base = 0;
+                        if (lane == leader) base = atomicAdd(&s_next, __popc(need));
+                        base = __shfl_sync(0xffffffffu, base, leader);
+                        if (idle) {
+                            q = base + __popc(need & lt);
+                            if (q < chunk) {
                                 dx = s_ray[0 * chunk + q];
                                 dy = s_ray[1 * chunk + q];
                                 dz = s_ray[2 * chunk + q];
                                 ivx = s_ray[3 * chunk + q];
                                 ivy = s_ray[4 * chunk + q];
                                 ivz = s_ray[5 * chunk + q];
-                            } else {
-                                const int c = c0 + q;
-                                const int i = c % N, j = c / N;
-                                float x0 = 0.5f, x1 = 0.5f;
-                                if (G.jitter) {
-                                    x0 = uniform01(jseed, jstream, 2ull * c);
-                                    x1 = uniform01(jseed, jstream, 2ull * c + 1);
+                                const bool alive = ray_start(T, r != kNone, inside, gx, gy, gz, dx, dy, dz, ivx, ivy,
+                                                             ivz, res, fres, &t, &cx, &cy, &cz);
+                                if (!alive) {
+                                    field[c0 + q] = __fadd_rn(G.eps, 0.0f);
+                                    q = -1;
+                                } else {
+                                    node = 0;
+                                    level = 0;
+                                    steps = 0;
+                                    stk[0] = 0;
                                 }
-                                const float u = __fsub_rn(__fmul_rn(__fadd_rn((float)i, x0), tn), 1.0f);
-                                const float v = __fsub_rn(__fmul_rn(__fadd_rn((float)j, x1), tn), 1.0f);
-                                const float3 d = octa_to_dir(u, v);
-                                dx = d.x;
-                                dy = d.y;
-                                dz = d.z;
-                                ivx = dx != 0.0f ? __fdiv_rn(1.0f, __fmul_rn(dx, T.scale)) : 0.0f;
-                                ivy = dy != 0.0f ? __fdiv_rn(1.0f, __fmul_rn(dy, T.scale)) : 0.0f;
-                                ivz = dz != 0.0f ? __fdiv_rn(1.0f, __fmul_rn(dz, T.scale)) : 0.0f;
-                            }
-                            bool alive = r != kNone;
-                            t = 0.0f;
-                            if (alive && inside) {
-                                cx = min((int)gx, res - 1);
-                                cy = min((int)gy, res - 1);
-                                cz = min((int)gz, res - 1);
-                            } else if (alive) {
-                                // slab entry into the grid box
-                                float tnr = 0.0f, tfr = INF;
-                                int enter = -1;
-                                const float gg[3] = {gx, gy, gz}, iv[3] = {ivx, ivy, ivz};
-#pragma unroll
-                                for (int a = 0; a < 3; ++a) {
-                                    if (iv[a] == 0.0f) {
-                                        if (!(gg[a] >= 0.0f && gg[a] <= fres)) alive = false;
-                                        continue;
-                                    }
-                                    const float t0 = __fmul_rn(__fsub_rn(0.0f, gg[a]), iv[a]);
-                                    const float t1 = __fmul_rn(__fsub_rn(fres, gg[a]), iv[a]);
-                                    const float lo_t = (t1 < t0) ? t1 : t0;
-                                    const float hi_t = (t0 < t1) ? t1 : t0;
-                                    if (lo_t > tnr) {
-                                        tnr = lo_t;
-                                        enter = a;
-                                    }
-                                    tfr = (hi_t < tfr) ? hi_t : tfr;
-                                }
-                                if (!(tnr <= tfr)) alive = false;
-                                if (alive) {
-                                    t = tnr;
-                                    const float dd[3] = {dx, dy, dz};
-                                    int cc[3];
-#pragma unroll
-                                    for (int a = 0; a < 3; ++a) {
-                                        if (a == enter) {
-                                            cc[a] = iv[a] > 0.0f ? 0 : res - 1;
-                                        } else {
-                                            const float p = __fadd_rn(gg[a], __fmul_rn(tnr, __fmul_rn(dd[a], T.scale)));
-                                            const int c = (p >= 0.0f) ? (int)p : 0;
-                                            cc[a] = min(c, res - 1);
-                                        }
-                                    }
-                                    cx = cc[0];
-                                    cy = cc[1];
-                                    cz = cc[2];
-                                }
-                            }
-                            if (alive && t < T.t_skip) {
-                                // no cell entered before t_skip can be the hit: take every
-                                // crossing strictly before t_skip at once (axis by axis)
-                                cx = skip_before(cx, gx, ivx, T.t_skip, res);
-                                cy = skip_before(cy, gy, ivy, T.t_skip, res);
-                                cz = skip_before(cz, gz, ivz, T.t_skip, res);
-                                if (cx < 0 || cx >= res || cy < 0 || cy >= res || cz < 0 || cz >= res) alive = false;
-                            }
-                            if (!alive) {
-                                field[c0 + q] = __fadd_rn(G.eps, 0.0f);
-                                q = -1;
-                            } else {
-                                node = 0;
-                                level = 0;
-                                steps = 0;
-                                stk[0] = 0;
                             }
                         }
                     }
+                    // leave only when every lane has run out of cells (a lane whose new ray
+                    // died at its start is idle again and fetches once more)
+                    if (__all_sync(0xffffffffu, q >= chunk)) break;
+                    if (q < 0 || q >= chunk) continue;  // idle, or out of cells: no ray to step
+                } else {
+                    // the whole warp sets up the next 32 cells' rays at once (converged), so a
+                    // lane that finishes a ray takes a ready one instead of stalling its warp
+                    // on a setup of its own
+                    if (need && wb_head == wb_n && !wb_dry) {
+                        int base = 0;
+                        if (lane == 0) base = atomicAdd(&s_next, 32);
+                        base = __shfl_sync(0xffffffffu, base, 0);
+                        wb_n = max(0, min(32, chunk - base));
+                        wb_head = 0;
+                        wb_dry = wb_n == 0;
+                        if (lane < wb_n) {
+                            const int c = c0 + base + lane;
+                            float3 d, iv;
+                            cell_ray(T, G, c, jseed, jstream, tn, &d, &iv);
+                            float t0;
+                            int x0, y0, z0;
+                            const bool alive = ray_start(T, r != kNone, inside, gx, gy, gz, d.x, d.y, d.z, iv.x,
+                                                         iv.y, iv.z, res, fres, &t0, &x0, &y0, &z0);
+                            if (!alive) field[c] = __fadd_rn(G.eps, 0.0f);
+                            wb[0 * 32 + lane] = __int_as_float(alive ? base + lane : -1);
+                            wb[1 * 32 + lane] = d.x;
+                            wb[2 * 32 + lane] = d.y;
+                            wb[3 * 32 + lane] = d.z;
+                            wb[4 * 32 + lane] = iv.x;
+                            wb[5 * 32 + lane] = iv.y;
+                            wb[6 * 32 + lane] = iv.z;
+                            wb[7 * 32 + lane] = t0;
+                            wb[8 * 32 + lane] = __int_as_float(x0);
+                            wb[9 * 32 + lane] = __int_as_float(y0);
+                            wb[10 * 32 + lane] = __int_as_float(z0);
+                        }
+                        __syncwarp();
+                    }
+                    if (need && wb_head < wb_n) {
+                        const int k = wb_head + __popc(need & lt);
+                        if (idle && k < wb_n) {
+                            q = __float_as_int(wb[0 * 32 + k]);  // -1: the ray died at its start
+                            dx = wb[1 * 32 + k];
+                            dy = wb[2 * 32 + k];
+                            dz = wb[3 * 32 + k];
+                            ivx = wb[4 * 32 + k];
+                            ivy = wb[5 * 32 + k];
+                            ivz = wb[6 * 32 + k];
+                            t = wb[7 * 32 + k];
+                            cx = __float_as_int(wb[8 * 32 + k]);
+                            cy = __float_as_int(wb[9 * 32 + k]);
+                            cz = __float_as_int(wb[10 * 32 + k]);
+                            node = 0;
+                            level = 0;
+                            steps = 0;
+                            stk[0] = 0;
+                        }
+                        wb_head = min(wb_n, wb_head + __popc(need));
+                        __syncwarp();  // entries are read before a refill overwrites them
+                    }
+                    if (wb_dry && __all_sync(0xffffffffu, q < 0)) break;
+                    if (q < 0) continue;  // idle: no ray to step
                 }
-                // leave only when every lane has run out of cells (a lane whose new ray
-                // died at its start is idle again and fetches once more)
-                if (__all_sync(0xffffffffu, q >= chunk)) break;
-                if (q < 0 || q >= chunk) continue;  // idle, or out of cells: no ray to step
                 // ---- one step: deepest existing node holding the cell, then hit or skip its empty block
                 while (level < D) {
                     const Node nd = load_node(T, s_nodes, node);
@@ -717,8 +786,9 @@ __global__ void __launch_bounds__(256) k_guide_eval(const float* __restrict__ pd
 static size_t guide_smem_bytes(uint32_t smem_nodes, int N, int D, int threads, bool stage) {
     const size_t NN = (size_t)N * N;
     const size_t chunk = NN < (size_t)kGuideChunk ? NN : (size_t)kGuideChunk;
+    const size_t rays = stage ? 6 * chunk : (size_t)(threads / 32) * kWbWords * 32;
     return sizeof(Node) * smem_nodes + sizeof(uint32_t) * (size_t)(D + 1) * threads +
-           sizeof(float) * ((stage ? 6 * chunk : 0) + 2 * NN + 2 * (size_t)N);
+           sizeof(float) * (rays + 2 * NN + 2 * (size_t)N);
 }
 
 template <int kThreads, bool kStage, bool kFused>

@@ -36,8 +36,18 @@ __device__ __forceinline__ int advance_axis(int c, int lo, int size, float g, fl
                                             bool before) {
     if (inv == 0.0f || size == 1) return c;
     const int hi = lo + size - 1;
-    int j = (int)floorf(g + tx * ds);  // estimate only; the checks below decide
-    j = max(lo, min(hi, j));
+    const float p = g + tx * ds;
+    const float fp = floorf(p);
+    int j = (int)fp;
+    // Fast path: the crossing tests below are monotone in the cell index and
+    // agree with the real-number position up to relative roundings; their sum
+    // stays under 1e-6 (|g| + |p| + 1) cells (four roundings of 2^-24 on the
+    // crossing times, three on p).  When p lies at least that far inside a
+    // cell, the tests would return floor(p) itself.
+    const float m = 1e-6f * (fabsf(g) + fabsf(p) + 1.0f);
+    const float f = p - fp;
+    if (f >= m && f <= 1.0f - m && j >= lo && j <= hi && (inv > 0.0f ? j >= c : j <= c)) return j;
+    j = max(lo, min(hi, j));  // otherwise the estimate is only a start; the checks decide
     if (inv > 0.0f) {
         j = max(j, c);
         while (j < hi) {
