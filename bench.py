@@ -111,6 +111,12 @@ def sum_over_ranks(x, world):
     return float(t.item())
 
 
+def job_rate(units, seconds, world):
+    """Whole-job throughput of replicas: units summed over ranks / the slowest
+    rank's time (weak scaling: every rank runs its own frame)."""
+    return sum_over_ranks(float(units), world) / max_over_ranks(float(seconds), world)
+
+
 class ClockSampler:
     """nvidia-smi clock/throttle samples during the timed region."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -329,7 +335,7 @@ def run_gpu(args, world, rank, local):
     ms = statistics.mean(step_ms)
     ms_max = max_over_ranks(ms, world)
     rays_all = sum_over_ranks(float(R), world)
-    value = rays_all / (ms_max / 1e3)
+    value = job_rate(R, ms / 1e3, world)
 
     # end to end through the C ABI with host buffers
     pinned = {k: v.cpu().pin_memory() for k, v in inp.items()}
@@ -435,7 +441,8 @@ def learned_section(args, w, svo):
     of guided two-bounce estimates at equal samples per pixel."""
     import torch
     from paper_2405_06997_gb300 import learned as LG
-    tr = LG.OnlineTrainer(svo, w.scene, batch=65536, pool=1 << 20, lr=1e-3, seed=w.seed)
+    # online training on the frame's own guided points (the primary hits), targets traced on the fly
+    tr = LG.OnlineTrainer(svo, w.scene, batch=65536, lr=1e-3, seed=w.seed, points=(w.ray_pos, w.ray_nrm))
     kl0 = tr.heldout_kl()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -446,6 +453,7 @@ def learned_section(args, w, svo):
     tau = 1.5 * floor
     cmp = LG.compare_proposals(w, svo, tr.mlp, frames=args.learned_frames, alpha=0.5, seed=w.seed)
     return {"train_steps": args.learned_steps, "train_batch_bins": 65536, "train_seconds": train_s,
+            "train_points": "the frame's primary hits (4096 held out)",
             "heldout_kl_untrained": kl0, "heldout_kl_trained": kl1, "traced_frame_to_frame_kl": floor,
             "fallback_threshold": tau, "uses_learned": LG.use_learned(kl1, tau),
             "equal_spp": cmp, "mlp_status": tr.mlp.status()}
@@ -549,8 +557,14 @@ def city_section(args):
                 "status": st["status"], "graph_kernels_per_frame": st["kernels_per_frame"]}
 
     out["svo_traced_64"] = timed(f, args.city_frames)
-    # the learned proposal: trained online against traced 32 x 32 fields of the city
-    tr = LG.OnlineTrainer(svo, sc, batch=65536, pool=1 << 20, lr=1e-3, seed=args.seed)
+    # the learned proposal: trained online against traced 32 x 32 fields at the frame's own
+    # guided points (its first-depth queue: the camera hits that continue)
+    f1 = W.Frame(svo, sc, N=64, max_depth=1, update=False, **{k: v for k, v in cam.items() if k != "max_depth"})
+    f1.run(1, use_graph=False)
+    n1 = f1.stats()["paths"][0]
+    pts = (f1.export("q_pos")[:n1].clone(), f1.export("q_nrm")[:n1].clone())
+    del f1
+    tr = LG.OnlineTrainer(svo, sc, batch=65536, lr=1e-3, seed=args.seed, points=pts)
     t0 = time.perf_counter()
     tr.train(args.city_train_steps)
     train_s = time.perf_counter() - t0
@@ -560,6 +574,13 @@ def city_section(args):
     fl.set_mlp(tr.mlp, sc.lo, sc.size)
     fl.run(2)
     out["learned_32"] = timed(fl, args.city_frames)
+    del fl
+    # the MLP costs a few hundred kFLOP per bin: finer bins (c_ray 128) at little cost
+    ff = W.Frame(svo, sc, N=32, proposal=1, **dict(cam, c_ray=128))
+    ff.set_mlp(tr.mlp, sc.lo, sc.size)
+    ff.run(2)
+    out["learned_32_fine"] = dict(timed(ff, args.city_frames), c_ray=128)
+    del ff
     use = LG.use_learned(kl, tau)
     out["learned_training"] = {"steps": args.city_train_steps, "batch_bins": 65536, "seconds": train_s,
                                "heldout_kl": kl, "fallback_threshold": tau, "uses_learned": use}

@@ -26,24 +26,40 @@ def _dev(a, device):
 
 class OnlineTrainer:
     """Trains the MLP on batches of surface points whose targets are traced
-    through the SVO on the fly (guide_build_pdf, N = 32, jitter + blur)."""
+    through the SVO on the fly (guide_build_pdf, N = 32, jitter + blur).
+
+    The points come from `points` = (pos, nrm) when given -- e.g. the frame's
+    own guided path vertices, the places whose traced grids the method
+    generates -- else area-uniformly from the scene's surfaces.  `heldout`
+    points are kept out of training: the last ones of `points`, or a separate
+    area-uniform draw."""
 
     def __init__(self, svo, scene, *, batch=65536, pool=1 << 20, lr=1e-3, seed=1, device="cuda",
-                 params=None, heldout=4096):
+                 params=None, heldout=4096, points=None):
         self.svo = svo
         self.scene = scene
         self.batch = batch
         self.lr = lr
         self.seed = seed
-        rng = np.random.default_rng(seed)
-        pos, nrm, _ = inputs.surface_points(scene, rng, pool)
-        self.pos = _dev(pos, device)
-        self.nrm = _dev(nrm, device)
-        hrng = np.random.default_rng(seed + 7919)
-        hp, hn, _ = inputs.surface_points(scene, hrng, heldout)
-        self.hpos = _dev(hp, device)
-        self.hnrm = _dev(hn, device)
-        self.mlp = W.MLP(params if params is not None else inputs.mlp_init(seed), max_batch=max(batch, heldout))
+        if points is not None:
+            pos, nrm = (torch.as_tensor(np.asarray(x) if not isinstance(x, torch.Tensor) else x) for x in points)
+            pos, nrm = pos.to(device).float(), nrm.to(device).float()
+            perm = torch.from_numpy(np.random.default_rng(seed).permutation(pos.shape[0])).to(device)
+            pos, nrm = pos[perm], nrm[perm]
+            self.hpos, self.hnrm = pos[-heldout:].contiguous(), nrm[-heldout:].contiguous()
+            self.pos, self.nrm = pos[:-heldout].contiguous(), nrm[:-heldout].contiguous()
+        else:
+            rng = np.random.default_rng(seed)
+            ppos, pnrm, _ = inputs.surface_points(scene, rng, pool)
+            self.pos = _dev(ppos, device)
+            self.nrm = _dev(pnrm, device)
+            hrng = np.random.default_rng(seed + 7919)
+            hp, hn, _ = inputs.surface_points(scene, hrng, heldout)
+            self.hpos = _dev(hp, device)
+            self.hnrm = _dev(hn, device)
+        heldout = self.hpos.shape[0]
+        self.batch = batch = min(batch, self.pos.shape[0])
+        self.mlp = W.MLP(params if params is not None else inputs.mlp_init(seed), max_batch=max(batch, heldout, 65536))
         self.tgt = (torch.empty((batch, 1024), dtype=torch.float32, device=device),
                     torch.empty((batch, 1024), dtype=torch.float32, device=device),
                     torch.empty((batch, 32), dtype=torch.float32, device=device))
@@ -126,7 +142,7 @@ def _cosine_dirs(nrm, u):
 
 
 def guided_estimates(w, svo, proposal, *, frames=16, alpha=0.5, mlp=None, seed=1, device="cuda", l_min=4,
-                     c_ray=512):
+                     c_ray=512, bin_cap=16384):
     """Per-pixel estimates of the light leaving each primary hit toward the
     camera, one path per pixel per frame, two bounces deep: the first bounce
     direction w1 is drawn from alpha * guided + (1 - alpha) * cosine and
@@ -137,7 +153,8 @@ def guided_estimates(w, svo, proposal, *, frames=16, alpha=0.5, mlp=None, seed=1
     Rays are binned with Partition-S (l_min, c_ray; the paper's Table 1 uses
     c_ray = 512 and its l_min 5, i.e. 4 here).  Returns the per-pixel mean and
     variance over frames and the guiding time per frame (binning + field/PDF +
-    sampling + MIS density), in seconds."""
+    sampling + MIS density), in seconds.  A cheap proposal can afford finer
+    bins (smaller c_ray, more bins: bin_cap) than tracing."""
     q = _dev(w.scene.quads, device)
     sp = _dev(w.scene.spheres, device)
     emission = _dev(w.scene.emission, device)
@@ -146,7 +163,7 @@ def guided_estimates(w, svo, proposal, *, frames=16, alpha=0.5, mlp=None, seed=1
     pos = _dev(w.ray_pos, device)
     nrm = _dev(w.ray_nrm, device)
     R = pos.shape[0]
-    B = 16384  # bin capacity; Partition-S at c_ray = 512 gives a few thousand bins at 1080p
+    B = bin_cap  # Partition-S at c_ray = 512 gives a few thousand bins at 1080p
     s1 = torch.zeros(R, dtype=torch.float64, device=device)
     s2 = torch.zeros(R, dtype=torch.float64, device=device)
     guide = None
@@ -198,18 +215,24 @@ def guided_estimates(w, svo, proposal, *, frames=16, alpha=0.5, mlp=None, seed=1
     return mean, var, float(np.mean(times[1:] if len(times) > 1 else times))
 
 
-def compare_proposals(w, svo, mlp, *, frames=16, alpha=0.5, seed=1):
+def compare_proposals(w, svo, mlp, *, frames=16, alpha=0.5, seed=1, fine_c_ray=32, fine_bin_cap=65536):
     """Equal-samples comparison of the traced and learned proposals (and the
     cosine-only baseline): mean per-pixel variance, mean estimate, proposal
-    time per frame and guided samples/s."""
+    time per frame and guided samples/s.  'learned_fine' evaluates the MLP on
+    Partition-S bins of fine_c_ray rays (the MLP's cost per bin is a few
+    hundred kFLOP, a traced field's is N^2 cone rays)."""
     out = {}
-    for name in ("bsdf", "svo", "learned"):
-        m, v, t = guided_estimates(w, svo, name, frames=frames, alpha=alpha, mlp=mlp, seed=seed)
+    runs = (("bsdf", "bsdf", {}), ("svo", "svo", {}), ("learned", "learned", {}),
+            ("learned_fine", "learned", {"c_ray": fine_c_ray, "bin_cap": fine_bin_cap}))
+    for name, proposal, kw in runs:
+        m, v, t = guided_estimates(w, svo, proposal, frames=frames, alpha=alpha, mlp=mlp, seed=seed, **kw)
         out[name] = {"mean": float(m.mean().item()), "variance": float(v.mean().item()),
                      "guiding_seconds_per_frame": t, "guided_samples_per_s": len(w.ray_pos) / t if t > 0 else None}
-    out["variance_ratio_learned_over_svo"] = out["learned"]["variance"] / out["svo"]["variance"]
-    # work-normalised: (variance x guiding time) of the traced over the learned proposal
-    out["efficiency_ratio_learned_over_svo"] = (
-        (out["svo"]["variance"] * out["svo"]["guiding_seconds_per_frame"]) /
-        (out["learned"]["variance"] * out["learned"]["guiding_seconds_per_frame"]))
+    out["learned_fine"]["c_ray"] = fine_c_ray
+    for name in ("learned", "learned_fine"):
+        out[f"variance_ratio_{name}_over_svo"] = out[name]["variance"] / out["svo"]["variance"]
+        # work-normalised: (variance x guiding time) of the traced over the learned proposal
+        out[f"efficiency_ratio_{name}_over_svo"] = (
+            (out["svo"]["variance"] * out["svo"]["guiding_seconds_per_frame"]) /
+            (out[name]["variance"] * out[name]["guiding_seconds_per_frame"]))
     return out

@@ -182,7 +182,7 @@ def _pipeline(w, N, jitter, blur, l_min=2, c_ray=0xFFFFFFFF, seed=11, frame=2):
 
 
 @pytest.mark.parametrize("N,jitter,blur", [(16, False, False), (16, True, True), (8, True, False),
-                                           (32, False, True), (64, True, True)])
+                                           (32, False, True), (64, True, True), (128, True, True)])
 def test_guide_build_matches_oracle(N, jitter, blur):
     w = inputs.tiny_box(6, n_rays=4099)
     g, o, r, ro, (pdf, cr, cm), og, nb = _pipeline(w, N, jitter, blur)
