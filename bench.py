@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-bins", type=int, default=64, help="bins in the oracle's timed sample")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-proposal section")
-    ap.add_argument("--learned-steps", type=int, default=500, help="online training steps (65,536 bins each)")
+    ap.add_argument("--learned-steps", type=int, default=2000, help="online training steps (65,536 bins each)")
     ap.add_argument("--learned-frames", type=int, default=16, help="frames of the equal-spp comparison")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-frame section")
     ap.add_argument("--batched-frames", type=int, default=20, help="timed frames of the batched section")
@@ -166,13 +166,17 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def measured_peaks():
+def measured_peaks(key="hbm_gbs"):
+    """The machine's measured peak (HBM copy GB/s, or cuBLAS bf16 TFLOP/s burst /
+    sustained), else the earlier GB300 measurement."""
+    fallback = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
         with open(path) as f:
             p = json.load(f)
-        return float(p["hbm_gbs"]), "measured"
-    return 6800.0, "fallback"
+        if key in p:
+            return float(p[key]), "measured"
+    return fallback[key], "fallback"
 
 
 def make_workload(seed):
@@ -440,7 +444,7 @@ def learned_section(args, w, svo):
     training (65,536 traced bins per step), held-out KL, and per-pixel variance
     of guided two-bounce estimates at equal samples per pixel."""
     import torch
-    from paper_2405_06997_gb300 import learned as LG
+    from paper_2405_06997_gb300 import learned as LG, wfpg as W
     # online training on the frame's own guided points (the primary hits), targets traced on the fly
     tr = LG.OnlineTrainer(svo, w.scene, batch=65536, lr=1e-3, seed=w.seed, points=(w.ray_pos, w.ray_nrm))
     kl0 = tr.heldout_kl()
@@ -450,10 +454,29 @@ def learned_section(args, w, svo):
     train_s = time.perf_counter() - t0
     kl1 = tr.heldout_kl()
     floor = LG.traced_frame_kl(tr)
+    # the MLP's own training step (forward + backward + Adam, tcgen05 GEMMs) on one traced batch
+    tr._targets(tr.pos[:65536], tr.tgt, 0)
+    for _ in range(3):
+        W.guide_learned_train_step(tr.mlp, tr.pos[:65536], tr.nrm[:65536], tr.tgt[0], lo=tr.lo, size=tr.size,
+                                   lr=0.0, loss=tr.loss)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(20):
+        W.guide_learned_train_step(tr.mlp, tr.pos[:65536], tr.nrm[:65536], tr.tgt[0], lo=tr.lo, size=tr.size,
+                                   lr=0.0, loss=tr.loss)
+    e1.record()
+    e1.synchronize()
+    step_ms = e0.elapsed_time(e1) / 20
+    flop = 3 * 157440 * 65536  # forward + both backward GEMMs per layer
+    peak, _ = measured_peaks("bf16_tflops_sustained")
     tau = 1.5 * floor
     cmp = LG.compare_proposals(w, svo, tr.mlp, frames=args.learned_frames, alpha=0.5, seed=w.seed)
     return {"train_steps": args.learned_steps, "train_batch_bins": 65536, "train_seconds": train_s,
             "train_points": "the frame's primary hits (4096 held out)",
+            "train_step_mlp_ms": step_ms,
+            "tensor": {"bound": "tensor", "achieved": flop / (step_ms / 1e3) / 1e12, "peak": peak,
+                       "unit": "TFLOP/s", "frac": flop / (step_ms / 1e3) / 1e12 / peak,
+                       "flop_per_step": flop, "note": "65,536 bins; 3 x 157,440 FLOP per bin"},
             "heldout_kl_untrained": kl0, "heldout_kl_trained": kl1, "traced_frame_to_frame_kl": floor,
             "fallback_threshold": tau, "uses_learned": LG.use_learned(kl1, tau),
             "equal_spp": cmp, "mlp_status": tr.mlp.status()}
