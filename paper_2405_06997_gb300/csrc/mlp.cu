@@ -11,10 +11,11 @@
 // All GEMMs are "TN": D[M x N] = A[M x K] B[N x K]^T with both operands
 // K-contiguous, so the backward uses transposed copies (written by the
 // forward epilogues and the weight-conversion kernel).  Weight gradients
-// reduce over the batch with split-K and float32 atomics.  Adam updates
+// reduce over the batch with split-K: per-split partial tiles, then one summing pass.  Adam updates
 // float32 master weights, then bfloat16 copies are refreshed.
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cstring>
 #include <string>
 
@@ -39,16 +40,17 @@ constexpr size_t kOffW1 = 0, kOffB1 = kOffW1 + kHid * kIn, kOffW2 = kOffB1 + kHi
                  kOffW3 = kOffB2 + kHid, kOffB3 = kOffW3 + kHid * kHid, kOffW4 = kOffB3 + kHid,
                  kOffB4 = kOffW4 + (size_t)kOut * kHid, kParams = kOffB4 + kOut;
 
-enum Epi { kEpiF32 = 0, kEpiBf16Relu = 1, kEpiAtomic = 2, kEpiReluGrad = 3 };
+enum Epi { kEpiF32 = 0, kEpiBf16Relu = 1, kEpiPartial = 2, kEpiReluGrad = 3 };
 
 struct GemmArgs {
     const bf16* A;   // [M][lda], K contiguous
     const bf16* B;   // [N][ldb], K contiguous
     int lda, ldb;
     int M, N, K;
-    int chunks_per_split;  // K chunks of 64 per blockIdx.z
-    float* C;              // f32 output [M][ldc] (kEpiF32, kEpiAtomic)
+    int chunks_per_split;  // K chunks (KChunk<BN>) per blockIdx.z
+    float* C;              // f32 output [M][ldc] (kEpiF32); per split z: C + z * split_stride (kEpiPartial)
     int ldc;
+    size_t split_stride;
     bf16* O;               // bf16 output [M][ldo]
     int ldo;
     bf16* OT;              // optional transposed bf16 output [N][ldot]
@@ -60,31 +62,42 @@ struct GemmArgs {
 };
 
 constexpr int kGemmThreads = 128;
-constexpr int kKChunk = 64;
+constexpr int kSplitsW4 = 64;       // K splits of the output layer's weight gradient (8 row tiles each)
+constexpr int kSplitsHidden = 256;  // K splits of the hidden layers' weight gradients
+// K elements per pipeline step: 128 for narrow tiles (more bytes in flight per
+// CTA on the long-K weight-gradient GEMMs), 64 for the 256-wide logits tile
+template <int BN>
+struct KChunk {
+    static constexpr int value = BN <= 80 ? 128 : 64;
+};
 
 template <int BN>
 struct TmemCols {
     static constexpr uint32_t value = BN <= 32 ? 32 : (BN <= 64 ? 64 : (BN <= 128 ? 128 : 256));
 };
 
-// copy rows [r0, r0 + rows) x k [k0, k0 + 64) of a K-contiguous bf16 matrix into
+// copy rows [r0, r0 + rows) x k [k0, k0 + KC) of a K-contiguous bf16 matrix into
 // the no-swizzle K-major core-matrix layout: 16-byte chunk c of row r goes to
-// (r / 8) * 1024 + c * 128 + (r % 8) * 16; rows or k past the end read zero
+// (r / 8) * (KC * 16) + c * 128 + (r % 8) * 16; rows or k past the end read zero
+template <int KC>
 __device__ __forceinline__ void load_tile(uint8_t* smem, const bf16* g, int ld, int r0, int rows, int nrows_total,
                                           int k0, int K) {
-    for (int idx = threadIdx.x; idx < rows * 8; idx += kGemmThreads) {
-        const int r = idx >> 3, c = idx & 7;
+    constexpr int kCpr = KC / 8;  // 16-byte chunks per row
+    for (int idx = threadIdx.x; idx < rows * kCpr; idx += kGemmThreads) {
+        const int r = idx / kCpr, c = idx % kCpr;
         const int gr = r0 + r, gk = k0 + c * 8;
         uint4 v = make_uint4(0u, 0u, 0u, 0u);
         if (gr < nrows_total && gk < K) v = *reinterpret_cast<const uint4*>(g + (size_t)gr * ld + gk);
-        *reinterpret_cast<uint4*>(smem + (r >> 3) * 1024 + c * 128 + (r & 7) * 16) = v;
+        *reinterpret_cast<uint4*>(smem + (r >> 3) * (KC * 16) + c * 128 + (r & 7) * 16) = v;
     }
 }
 
 template <int BN, int EPI>
 __global__ void __launch_bounds__(kGemmThreads) k_gemm_tn(GemmArgs g) {
-    __shared__ __align__(1024) uint8_t sA[128 * kKChunk * 2];
-    __shared__ __align__(1024) uint8_t sB[BN * kKChunk * 2];
+    constexpr int kKChunk = KChunk<BN>::value;
+    extern __shared__ __align__(1024) uint8_t gemm_smem[];
+    uint8_t* sA = gemm_smem;                      // 128 x kKChunk bf16
+    uint8_t* sB = gemm_smem + 128 * kKChunk * 2;  // BN x kKChunk bf16
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tmem_base;
     constexpr uint32_t kCols = TmemCols<BN>::value;
@@ -106,8 +119,8 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm_tn(GemmArgs g) {
     uint32_t phase = 0;
     bool ok = true;
     for (int kc = kc0; kc < kc1 && ok; ++kc) {
-        load_tile(sA, g.A, g.lda, m0, 128, g.M, kc * kKChunk, g.K);
-        load_tile(sB, g.B, g.ldb, n0, BN, g.N, kc * kKChunk, g.K);
+        load_tile<kKChunk>(sA, g.A, g.lda, m0, 128, g.M, kc * kKChunk, g.K);
+        load_tile<kKChunk>(sB, g.B, g.ldb, n0, BN, g.N, kc * kKChunk, g.K);
         tc::fence_proxy_async();
         __syncthreads();
         if (tid == 0) {
@@ -115,9 +128,9 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm_tn(GemmArgs g) {
             const uint32_t a0 = tc::smem_addr(sA), b0 = tc::smem_addr(sB);
 #pragma unroll
             for (int s = 0; s < kKChunk / 16; ++s) {
-                // K step of 16 = two core matrices along K (128 B apart); 8-row groups 1024 B apart
-                const uint64_t ad = tc::smem_desc(a0 + s * 256, 128, 1024);
-                const uint64_t bd = tc::smem_desc(b0 + s * 256, 128, 1024);
+                // K step of 16 = two core matrices along K (128 B apart); 8-row groups kKChunk * 16 B apart
+                const uint64_t ad = tc::smem_desc(a0 + s * 256, 128, kKChunk * 16);
+                const uint64_t bd = tc::smem_desc(b0 + s * 256, 128, kKChunk * 16);
                 tc::mma_bf16(tmem, ad, bd, idesc, (kc > kc0 || s > 0) ? 1u : 0u);
             }
             tc::mma_commit(&mbar);
@@ -135,14 +148,72 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm_tn(GemmArgs g) {
             float v[16];
             tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
             if (row >= g.M) continue;
+            // full 16-column chunks of the row-major outputs go out as 16-byte stores
+            if (n0 + c0 + 16 <= g.N) {
+                if ((EPI == kEpiF32 || EPI == kEpiPartial) && (g.ldc & 3) == 0 && ((uintptr_t)g.C & 15) == 0 &&
+                    (EPI != kEpiPartial || (g.split_stride & 3) == 0)) {
+                    float* crow = g.C + (EPI == kEpiPartial ? (size_t)blockIdx.z * g.split_stride : 0);
+                    float4* cp = reinterpret_cast<float4*>(crow + (size_t)row * g.ldc + n0 + c0);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        float4 o = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+                        if (EPI == kEpiF32 && g.bias) {
+                            const float* bb = g.bias + n0 + c0 + 4 * q;
+                            o.x += bb[0];
+                            o.y += bb[1];
+                            o.z += bb[2];
+                            o.w += bb[3];
+                        }
+                        cp[q] = o;
+                    }
+                    continue;
+                }
+                if ((EPI == kEpiBf16Relu || EPI == kEpiReluGrad) && (g.ldo & 7) == 0 && ((uintptr_t)g.O & 15) == 0 &&
+                    (EPI != kEpiReluGrad || ((g.ldact & 7) == 0 && ((uintptr_t)g.act & 15) == 0))) {
+                    float ar[16];  // forward activations of the 16 columns (ReLU gradient mask)
+                    if (EPI == kEpiReluGrad) {
+                        const uint4* ap = reinterpret_cast<const uint4*>(g.act + (size_t)row * g.ldact + n0 + c0);
+#pragma unroll
+                        for (int q = 0; q < 2; ++q) {
+                            const uint4 a4 = ap[q];
+                            const uint32_t aw[4] = {a4.x, a4.y, a4.z, a4.w};
+#pragma unroll
+                            for (int h = 0; h < 4; ++h) {
+                                ar[8 * q + 2 * h] = __bfloat162float(__ushort_as_bfloat16((unsigned short)(aw[h] & 0xffffu)));
+                                ar[8 * q + 2 * h + 1] = __bfloat162float(__ushort_as_bfloat16((unsigned short)(aw[h] >> 16)));
+                            }
+                        }
+                    }
+                    uint32_t w[8];
+#pragma unroll
+                    for (int h = 0; h < 8; ++h) {
+                        bf16 e[2];
+#pragma unroll
+                        for (int k = 0; k < 2; ++k) {
+                            const int i = 2 * h + k, n = n0 + c0 + i;
+                            if (EPI == kEpiBf16Relu) {
+                                e[k] = __float2bfloat16_rn(fmaxf(v[i] + g.bias[n], 0.0f));
+                            } else {
+                                e[k] = __float2bfloat16_rn(ar[i] > 0.0f ? v[i] : 0.0f);
+                            }
+                            if (g.OT) g.OT[(size_t)n * g.ldot + row] = e[k];
+                        }
+                        w[h] = (uint32_t)__bfloat16_as_ushort(e[0]) | ((uint32_t)__bfloat16_as_ushort(e[1]) << 16);
+                    }
+                    uint4* op = reinterpret_cast<uint4*>(g.O + (size_t)row * g.ldo + n0 + c0);
+                    op[0] = make_uint4(w[0], w[1], w[2], w[3]);
+                    op[1] = make_uint4(w[4], w[5], w[6], w[7]);
+                    continue;
+                }
+            }
 #pragma unroll
             for (int i = 0; i < 16; ++i) {
                 const int n = n0 + c0 + i;
                 if (n >= g.N) continue;
                 if (EPI == kEpiF32) {
                     g.C[(size_t)row * g.ldc + n] = v[i] + (g.bias ? g.bias[n] : 0.0f);
-                } else if (EPI == kEpiAtomic) {
-                    atomicAdd(&g.C[(size_t)row * g.ldc + n], v[i]);
+                } else if (EPI == kEpiPartial) {
+                    g.C[(size_t)blockIdx.z * g.split_stride + (size_t)row * g.ldc + n] = v[i];
                 } else if (EPI == kEpiBf16Relu) {
                     const bf16 h = __float2bfloat16_rn(fmaxf(v[i] + g.bias[n], 0.0f));
                     g.O[(size_t)row * g.ldo + n] = h;
@@ -192,11 +263,21 @@ __global__ void k_mlp_features(const float* __restrict__ pos, const float* __res
         f[76] = nrm[3 * (size_t)r + 1];
         f[77] = nrm[3 * (size_t)r + 2];
     }
+    // the row: 80 bf16 = 10 x 16-byte stores (rows are 160 B apart, so 16-byte aligned)
+    uint4* xr = reinterpret_cast<uint4*>(X + (size_t)i * kIn);
 #pragma unroll
-    for (int k = 0; k < kIn; ++k) {
-        const bf16 b = __float2bfloat16_rn(f[k]);
-        X[(size_t)i * kIn + k] = b;
-        if (XT) XT[(size_t)k * ldxt + i] = b;
+    for (int q = 0; q < kIn / 8; ++q) {
+        uint32_t w[4];
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            const bf16 lo = __float2bfloat16_rn(f[8 * q + 2 * h]), hi = __float2bfloat16_rn(f[8 * q + 2 * h + 1]);
+            w[h] = (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+        }
+        xr[q] = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+    if (XT) {  // transposed copy: consecutive threads write consecutive rows of XT
+#pragma unroll
+        for (int k = 0; k < kIn; ++k) XT[(size_t)k * ldxt + i] = __float2bfloat16_rn(f[k]);
     }
 }
 
@@ -257,32 +338,115 @@ __global__ void k_softmax_rows(const float* __restrict__ Z, uint32_t rows, const
     if (lane == 0) atomicAdd(loss, kl * inv_n);
 }
 
-// out[c] += sum over rows of G[r][c] (bf16 values as stored)
-__global__ void k_colsum(const bf16* __restrict__ G, int rows, int cols, int ld, int rows_per_block,
-                         float* __restrict__ out) {
-    const int r0 = blockIdx.x * rows_per_block, r1 = min(rows, r0 + rows_per_block);
-    for (int c = threadIdx.x; c < cols; c += blockDim.x) {
-        float s = 0.0f;
-        for (int r = r0; r < r1; ++r) s += __bfloat162float(G[(size_t)r * ld + c]);
-        atomicAdd(&out[c], s);
+
+// out[i] = sum over the splits of part[z][i] (split-K weight gradients): a
+// block covers 32 outputs, its 8 warps take every 8th split, then the 8
+// partial sums are added in warp order (deterministic)
+__global__ void __launch_bounds__(256) k_sum_splits(const float* __restrict__ part, int splits, uint32_t mn,
+                                                    float* __restrict__ out) {
+    __shared__ float red[8][32];
+    const uint32_t i = blockIdx.x * 32 + threadIdx.x;
+    float acc = 0.0f;
+    if (i < mn)
+        for (int z = threadIdx.y; z < splits; z += 8) acc += part[(size_t)z * mn + i];
+    red[threadIdx.y][threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.y == 0 && i < mn) {
+        float sum = 0.0f;
+#pragma unroll
+        for (int y = 0; y < 8; ++y) sum += red[y][threadIdx.x];
+        out[i] = sum;
     }
 }
 
-// out[c][r] = in[r][c] through a 32 x 32 shared tile
-__global__ void k_transpose(const bf16* __restrict__ in, int rows, int cols, int ldi, bf16* __restrict__ out,
-                            int ldo) {
-    __shared__ bf16 t[32][33];
-    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
-    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
-        const int r = r0 + k, c = c0 + threadIdx.x;
-        if (r < rows && c < cols) t[k][threadIdx.x] = in[(size_t)r * ldi + c];
+// out[r] += sum over k < n of AT[r][k] for a bf16 matrix stored transposed
+// (rows = features, k = batch): blockIdx.y = row, blockIdx.x = a stretch of
+// 8192 k, coalesced 4-byte reads, one atomic per block (out zeroed before)
+__global__ void __launch_bounds__(256) k_rowsum(const bf16* __restrict__ AT, int n, int ld, float* __restrict__ out) {
+    __shared__ float red[256];
+    const bf16* a = AT + (size_t)blockIdx.y * ld;
+    const int k0 = blockIdx.x * 8192, k1 = min(n, k0 + 8192);
+    float acc = 0.0f;
+    for (int k = k0 + 2 * (int)threadIdx.x; k < k1; k += 512) {
+        if (k + 1 < k1 && (ld & 1) == 0) {
+            const __nv_bfloat162 v = *reinterpret_cast<const __nv_bfloat162*>(a + k);
+            acc += __bfloat162float(v.x) + __bfloat162float(v.y);
+        } else {
+            acc += __bfloat162float(a[k]);
+            if (k + 1 < k1) acc += __bfloat162float(a[k + 1]);
+        }
     }
+    red[threadIdx.x] = acc;
     __syncthreads();
-    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
-        const int c = c0 + k, r = r0 + threadIdx.x;
-        if (r < rows && c < cols) out[(size_t)c * ldo + r] = t[threadIdx.x][k];
+    for (int o = 128; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) atomicAdd(&out[blockIdx.y], red[0]);
+}
+
+// out[c][r] = in[r][c] and colsum[c] += sum over r of in[r][c], for a bf16
+// matrix with an even row stride: 64 x 64 tiles through shared memory, two
+// columns (rows of out) per 4-byte access; one block covers 64 columns x 256
+// rows and adds its column sums with one atomic per column
+__global__ void __launch_bounds__(256) k_transpose_colsum(const bf16* __restrict__ in, int rows, int cols, int ldi,
+                                                          bf16* __restrict__ out, int ldo,
+                                                          float* __restrict__ colsum) {
+    __shared__ bf16 t[64][66];
+    __shared__ float part[8][64];
+    const int c0 = blockIdx.x * 64, rb = blockIdx.y * 256;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    float s0 = 0.0f, s1 = 0.0f;
+    const int rend = min(rows, rb + 256);
+    for (int r0 = rb; r0 < rend; r0 += 64) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int r = r0 + ty + 8 * k, c = c0 + 2 * tx;
+            bf16 a = __float2bfloat16_rn(0.0f), b = a;
+            if (r < rows && c + 1 < cols) {
+                const __nv_bfloat162 v = *reinterpret_cast<const __nv_bfloat162*>(in + (size_t)r * ldi + c);
+                a = v.x;
+                b = v.y;
+            } else if (r < rows && c < cols) {
+                a = in[(size_t)r * ldi + c];
+            }
+            t[ty + 8 * k][2 * tx] = a;
+            t[ty + 8 * k][2 * tx + 1] = b;
+            s0 += __bfloat162float(a);
+            s1 += __bfloat162float(b);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int c = c0 + ty + 8 * k, r = r0 + 2 * tx;
+            if (c >= cols) continue;
+            if (r + 1 < rows && ((ldo & 1) == 0)) {
+                __nv_bfloat162 v;
+                v.x = t[2 * tx][ty + 8 * k];
+                v.y = t[2 * tx + 1][ty + 8 * k];
+                *reinterpret_cast<__nv_bfloat162*>(out + (size_t)c * ldo + r) = v;
+            } else {
+                if (r < rows) out[(size_t)c * ldo + r] = t[2 * tx][ty + 8 * k];
+                if (r + 1 < rows) out[(size_t)c * ldo + r + 1] = t[2 * tx + 1][ty + 8 * k];
+            }
+        }
+        __syncthreads();
+    }
+    part[ty][2 * tx] = s0;
+    part[ty][2 * tx + 1] = s1;
+    __syncthreads();
+    if (ty == 0) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int c = 2 * tx + h;
+            float sum = 0.0f;
+#pragma unroll
+            for (int y = 0; y < 8; ++y) sum += part[y][c];
+            if (c0 + c < cols) atomicAdd(&colsum[c0 + c], sum);
+        }
     }
 }
+
 
 // Adam (Kingma & Ba 2015) on the float32 master weights
 __global__ void k_adam(float* __restrict__ w, float* __restrict__ m, float* __restrict__ v,
@@ -322,6 +486,7 @@ struct wfpg_mlp {
          *h3t = nullptr, *g4 = nullptr, *g4t = nullptr, *d3 = nullptr, *d3t = nullptr, *d2 = nullptr,
          *d2t = nullptr, *d1 = nullptr, *d1t = nullptr;
     float* z = nullptr;
+    float* part = nullptr;  // split-K partial weight gradients
     float* field = nullptr;
     float* loss = nullptr;
     uint32_t* status = nullptr;
@@ -329,8 +494,10 @@ struct wfpg_mlp {
 
 namespace {
 
+// launches the GEMM; returns the number of K splits it used
 template <int BN, int EPI>
-void gemm(const GemmArgs& a, int splits, cudaStream_t st) {
+int gemm(const GemmArgs& a, int splits, cudaStream_t st) {
+    constexpr int kKChunk = KChunk<BN>::value;
     GemmArgs g = a;
     const int chunks = (g.K + kKChunk - 1) / kKChunk;
     if (splits < 1) splits = 1;
@@ -339,7 +506,27 @@ void gemm(const GemmArgs& a, int splits, cudaStream_t st) {
     splits = (chunks + g.chunks_per_split - 1) / g.chunks_per_split;
     const dim3 grid(div_up(g.M, 128), div_up(g.N, BN), splits);
     auto kernel = k_gemm_tn<BN, EPI>;
-    WFPG_LAUNCH(kernel, grid, kGemmThreads, 0, st, g);
+    const int smem = (128 + BN) * kKChunk * 2;
+    // the tiles plus the kernel's static shared memory exceed the default 48 KB
+    // window for the wide instantiations: raise the dynamic limit once
+    static bool raised = false;
+    if (!raised && smem > 32 * 1024) {
+        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        raised = true;
+    }
+    WFPG_LAUNCH(kernel, grid, kGemmThreads, smem, st, g);
+    return splits;
+}
+
+// split-K weight gradient: partial tiles into s->part, then their sum into out
+template <int BN>
+void weight_grad(wfpg_mlp* s, GemmArgs g, int splits, float* out, cudaStream_t st) {
+    g.C = s->part;
+    g.ldc = g.N;
+    g.split_stride = (size_t)g.M * g.N;
+    const int used = gemm<BN, kEpiPartial>(g, splits, st);
+    const uint32_t mn = (uint32_t)(g.M * g.N);
+    WFPG_LAUNCH(k_sum_splits, div_up(mn, 32), dim3(32, 8), 0, st, s->part, used, mn, out);
 }
 
 GemmArgs gargs(const bf16* A, int lda, const bf16* B, int ldb, int M, int N, int K, uint32_t* status) {
@@ -424,6 +611,7 @@ int mlp_create(const float* params, uint32_t max_batch, void* stream, wfpg_mlp**
     alloc(&s->m, 4 * kParams);
     alloc(&s->v, 4 * kParams);
     alloc(&s->grad, 4 * kParams);
+    alloc(&s->part, 4 * (size_t)std::max(kSplitsW4 * kOut * kHid, kSplitsHidden * kHid * kIn));
     alloc(&s->w1, 2 * kHid * kIn);
     alloc(&s->w2, 2 * kHid * kHid);
     alloc(&s->w3, 2 * kHid * kHid);
@@ -465,7 +653,7 @@ int mlp_create(const float* params, uint32_t max_batch, void* stream, wfpg_mlp**
 
 int mlp_destroy(wfpg_mlp* s) {
     if (!s) return WFPG_OK;
-    void* ptrs[] = {s->params, s->m, s->v, s->grad, s->w1, s->w2, s->w3, s->w4, s->w2t, s->w3t, s->w4t,
+    void* ptrs[] = {s->params, s->m, s->v, s->grad, s->part, s->w1, s->w2, s->w3, s->w4, s->w2t, s->w3t, s->w4t,
                     s->x, s->xt, s->h1, s->h1t, s->h2, s->h2t, s->h3, s->h3t, s->g4, s->g4t, s->d3,
                     s->d3t, s->d2, s->d2t, s->d1, s->d1t, s->z, s->field, s->loss, s->status};
     for (void* p : ptrs)
@@ -533,16 +721,11 @@ int guide_learned_train_step(wfpg_mlp* s, const float* pos, const float* nrm, ui
     WFPG_LAUNCH(k_softmax_rows, div_up((uint64_t)n * 32, 256), 256, 0, st, s->z, n, (const uint32_t*)nullptr, 0.0f,
                 (float*)nullptr, target, 1.0f / (float)n, s->g4, s->loss);
     // output layer: dW4 = G4^T H3 (split-K over the batch), db4, dA3 = (G4 W4) o [H3 > 0]
-    WFPG_LAUNCH(k_transpose, dim3(div_up(kOut, 32), div_up(n, 32)), dim3(32, 8), 0, st, s->g4, N, kOut, kOut, s->g4t,
-                mp);
-    const int rows_per_block = 256;
-    const int splits = max(1, min(256, div_up(n, 256)));
+    // G4^T for the weight gradient, and db4 = column sums of G4, in one pass over G4
+    WFPG_LAUNCH(k_transpose_colsum, dim3(div_up(kOut, 64), div_up(n, 256)), dim3(32, 8), 0, st, s->g4, N, kOut, kOut,
+                s->g4t, mp, s->grad + kOffB4);
     GemmArgs g = gargs(s->g4t, mp, s->h3t, mp, kOut, kHid, N, s->status);
-    g.C = s->grad + kOffW4;
-    g.ldc = kHid;
-    gemm<64, kEpiAtomic>(g, splits / 4 > 0 ? splits / 4 : 1, st);
-    WFPG_LAUNCH(k_colsum, div_up(n, rows_per_block), 256, 0, st, s->g4, N, kOut, kOut, rows_per_block,
-                s->grad + kOffB4);
+    weight_grad<64>(s, g, kSplitsW4, s->grad + kOffW4, st);
     g = gargs(s->g4, kOut, s->w4t, kOut, N, kHid, kOut, s->status);
     g.O = s->d3;
     g.ldo = kHid;
@@ -561,12 +744,9 @@ int guide_learned_train_step(wfpg_mlp* s, const float* pos, const float* nrm, ui
               {s->d1, s->d1t, s->xt, s->x, nullptr, nullptr, nullptr, kOffW1, kOffB1, kIn}};
     for (int l = 0; l < 3; ++l) {
         g = gargs(L[l].dAt, mp, L[l].Hprev_t, mp, kHid, L[l].nin, N, s->status);
-        g.C = s->grad + L[l].offW;
-        g.ldc = L[l].nin;
-        if (L[l].nin == kIn) gemm<80, kEpiAtomic>(g, splits, st);
-        else gemm<64, kEpiAtomic>(g, splits, st);
-        WFPG_LAUNCH(k_colsum, div_up(n, rows_per_block), 64, 0, st, L[l].dA, N, kHid, kHid, rows_per_block,
-                    s->grad + L[l].offB);
+        if (L[l].nin == kIn) weight_grad<80>(s, g, kSplitsHidden, s->grad + L[l].offW, st);
+        else weight_grad<64>(s, g, kSplitsHidden, s->grad + L[l].offW, st);
+        WFPG_LAUNCH(k_rowsum, dim3(div_up(n, 8192), kHid), 256, 0, st, L[l].dAt, N, mp, s->grad + L[l].offB);
         if (L[l].Wt) {
             g = gargs(L[l].dA, kHid, L[l].Wt, kHid, N, kHid, kHid, s->status);
             g.O = L[l].dAprev;
