@@ -26,9 +26,9 @@ namespace wfpg {
 
 constexpr float kOneMinus = 0x1.fffffep-1f;
 constexpr int kGuideChunk = 512;   // cells whose directions are staged in shared memory at once
-// defaults measured on the 1080p frame workload (GB300): 256 threads per bin
-// without staging for N >= 32, 64 threads (with staging) for N <= 16
-constexpr int kGuideDefaultThreadsLarge = 256, kGuideDefaultThreadsSmall = 64;
+// default threads per bin (measured on the 1080p frame workload, GB300): 64
+// with staged directions for N <= 16, 128 for N = 32, 256 above, unstaged
+constexpr int kGuideDefaultThreadsSmall = 64, kGuideDefaultThreadsMid = 128, kGuideDefaultThreadsLarge = 256;
 constexpr int kSmemTopLevels = 3;  // levels 0..3 of the SVO (<= 585 nodes) live in shared memory
 
 struct TraceArgs {
@@ -312,10 +312,11 @@ __device__ __forceinline__ bool ray_start(const TraceArgs& T, bool has_origin, b
     return alive;
 }
 
-// 1280 resident threads per SM (40 warps): at most 51 registers a thread, the
-// budget the unfused kernel fits in, so the fused variant keeps its occupancy
+// 1024 resident threads per SM (32 warps): up to 64 registers a thread.  The
+// walk is issue-bound, and 64 registers (fewer recomputed values) beat 48
+// registers with 40 warps on the GB300; the fused variant gets the same budget
 template <int kGuideThreads, bool kStage, bool kFused>
-__global__ void __launch_bounds__(kGuideThreads, 1280 / kGuideThreads) k_guide_build(TraceArgs T, GuideArgs G, FusedArgs F,
+__global__ void __launch_bounds__(kGuideThreads, 1024 / kGuideThreads) k_guide_build(TraceArgs T, GuideArgs G, FusedArgs F,
                                                                const float* __restrict__ pos,
                                                                const uint32_t* __restrict__ origin_ray,
                                                                const uint32_t* __restrict__ n_bins_dev,
@@ -840,7 +841,9 @@ static int dispatch_guide(const wfpg_svo* s, const wfpg_guide_params* p, const T
                           const uint32_t* n_bins_dev, uint32_t bin_cap, float* pdf, float* cdf_row, float* cdf_marg,
                           cudaStream_t st) {
     const bool small = p->N <= 16;
-    const int threads = p->block ? p->block : (small ? kGuideDefaultThreadsSmall : kGuideDefaultThreadsLarge);
+    const int threads = p->block ? p->block
+                                 : (small ? kGuideDefaultThreadsSmall
+                                          : (p->N <= 32 ? kGuideDefaultThreadsMid : kGuideDefaultThreadsLarge));
     const bool stage = p->stage == 0 ? small : p->stage > 0;
     const int D = s->D;
 #define WFPG_GUIDE_CASE(TH)                                                                                        \
