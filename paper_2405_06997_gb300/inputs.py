@@ -115,6 +115,26 @@ def single_sphere(center, radius) -> Scene:
                  lo=np.zeros(3, np.float32), size=1.0, name="single_sphere")
 
 
+def small_deep(seed: int) -> Scene:
+    """Maximum-depth test scene: six small quads facing one another (one of
+    them emissive, radiance 10) around a tiny sphere, all inside [0.45, 0.55]^3
+    of the unit cube -- about 2e4 occupied leaves at depth 11 (2048^3)."""
+    rng = np.random.default_rng(seed)
+    c, h = 0.5, 0.03
+    quads = [
+        _quad(0, c - h, c - h, c + h, c - h, c + h, +1), _quad(0, c + h, c - h, c + h, c - h, c + h, -1),
+        _quad(1, c - h, c - h, c + h, c - h, c + h, +1), _quad(1, c + h, c - h, c + h, c - h, c + h, -1),
+        _quad(2, c - h, c - h, c + h, c - h, c + h, +1), _quad(2, c + h, c - h, c + h, c - h, c + h, -1),
+    ]
+    albedo = np.concatenate([rng.uniform(0.3, 0.8, 6), [0.5]]).astype(np.float32)
+    albedo[3] = 0.0
+    emission = np.zeros(7, np.float32)
+    emission[3] = 10.0
+    spheres = np.array([[c + 0.004, c - 0.003, c + 0.002, 0.008]], np.float32)
+    return Scene(quads=np.array(quads, np.float32), spheres=spheres, albedo=albedo, emission=emission,
+                 lo=np.zeros(3, np.float32), size=1.0, name=f"small_deep(seed={seed})")
+
+
 def city(seed: int, n_boxes: int = 5000, n_lights: int = 50, size: float = 500.0) -> Scene:
     """Procedural city: ground quad, n seeded boxes (side log-uniform in
     [0.5, 20], uniform on the ground) and n emissive quads hovering above."""

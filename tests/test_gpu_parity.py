@@ -308,3 +308,35 @@ def test_guide_build_tile_variants(block, stage):
         assert np.array_equal(pdf[:nb].cpu().numpy(), og["pdf"])
         assert np.array_equal(cm[:nb].cpu().numpy(), og["cdf_marg"])
     assert g.status() == 0
+
+
+# ------------------------------------------------------------------ maximum depth
+def test_depth_11_end_to_end_exact():
+    """Depth 11 (2048^3, 33-bit Morton keys): SVO layout, exitance sums, bins,
+    origins and the traced fields equal the oracle's bit for bit."""
+    sc = inputs.small_deep(1)
+    D = 11
+    g, o = build_both(sc, D)
+    assert_svo_equal(g, o)
+    rng = np.random.default_rng(5)
+    pos, nrm, prim = inputs.surface_points(sc, rng, 20000)
+    wout = inputs.cosine_dirs(nrm, rng).astype(np.float32)
+    L = np.where(prim == 3, 10.0, sc.albedo[prim] * 10.0 * rng.uniform(0, 1, len(prim))).astype(np.float32)
+    W.svo_accumulate(g, dev(pos), dev(wout), dev(L))
+    o.accumulate(pos, wout, L)
+    ge, oe = g.exitance(), o.exitance()
+    np.testing.assert_array_equal(ge["acc_sum"], oe["acc_sum"])
+    np.testing.assert_array_equal(ge["value"], oe["value"])
+    rp, rn, _ = inputs.surface_points(sc, np.random.default_rng(6), 3001)
+    for l_min, c_ray in ((3, 0xFFFFFFFF), (8, 64)):
+        r = W.bin_rays(g, dev(rp), dev(rn), l_min=l_min, c_ray=c_ray, seed=4, frame=1)
+        ro = o.bin_rays(rp, rn, l_min=l_min, c_ray=c_ray, seed=4, frame=1)
+        nb = ro["n_bins"]
+        np.testing.assert_array_equal(u32(r["bin_of_ray"]), ro["bin_of_ray"])
+        np.testing.assert_array_equal(u32(r["origin_ray"])[:nb], ro["origin_ray"][:nb])
+    pdf, cr, cm = W.guide_build_pdf(g, dev(rp), r["origin_ray"], r["n_bins"], r["bin_cap"], N=16, jitter=True,
+                                    blur=True, seed=4, frame=1)
+    sel = np.arange(0, nb, max(1, nb // 12))
+    og = o.guide_build(rp[ro["origin_ray"][sel]], sel, 16, jitter=True, blur=True, seed=4, frame=1)
+    assert np.array_equal(pdf.cpu().numpy()[sel], og["pdf"])
+    assert g.status() == 0
