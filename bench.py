@@ -645,7 +645,7 @@ def read_profile_traffic():
             return None, None
     return d["dram_bytes_per_launch"], {"issue_active_pct": d["issue_active_pct"],
                                         "active_lanes_per_warp_instruction": d["active_lanes_per_warp_instruction"],
-                                        "limiter": "instruction issue with divergence (DRAM well below peak)"}
+                                        "limiter": "instruction issue and latency with divergence (DRAM well below peak)"}
 
 
 def main():
