@@ -364,3 +364,19 @@ def test_city_frame_runs_with_the_svo_caster():
     m, _ = f.image()
     assert st["status"] == 0 and st["paths"][0] > 0.3 * f.pixels
     assert torch.isfinite(m).all() and m.mean().item() > 0
+
+
+def test_frame_that_sees_nothing():
+    """A camera outside the scene looking away: no hits, so every depth's queue
+    is empty, Partition-S and GuideRays get zero rays, no records are
+    accumulated, and the image is black -- without errors or status bits."""
+    w, g, _ = box_svo(12)
+    before = g.exitance()
+    f = make_frame(g, w.scene, eye=(0.5, 0.5, -2.0), forward=(0.0, 0.0, -1.0), width=64, height=36)
+    f.run(2, use_graph=False)
+    f.run(2, use_graph=True)
+    st = f.stats()
+    m, v = f.image()
+    assert st["paths"] == [0, 0, 0, 0] and st["records"] == 0 and st["status"] == 0
+    assert float(m.abs().max()) == 0.0 and float(v.abs().max()) == 0.0
+    np.testing.assert_array_equal(g.exitance()["acc_sum"], before["acc_sum"])
