@@ -344,21 +344,27 @@ def run_gpu(args, world, rank, local):
             torch.empty(R, dtype=torch.int32, device=dev))
     evalout = torch.empty(R, dtype=torch.float32, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
-    ge0, ge1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    stage_names = ("accumulate", "bin_rays", "guide_build_pdf", "guide_sample", "guide_eval_pdf")
+    sev = [torch.cuda.Event(enable_timing=True) for _ in range(len(stage_names) + 1)]
+    stage_ms = {k: [] for k in stage_names}
 
     def step(frame, x, time_guide=False, outs=None):
         so, eo = outs if outs is not None else (samp, evalout)
+        mark = (lambda i: sev[i].record()) if time_guide else (lambda i: None)
+        mark(0)
         W.svo_accumulate(svo, x["rec_pos"], x["rec_wout"], x["rec_L"])
+        mark(1)
         W.bin_rays(svo, x["ray_pos"], x["ray_nrm"], mode=W.BIN_RUNS, sizes=x["sizes"], seed=w.seed,
                    frame=frame, bin_cap=B, out=binout, workspace=ws)
-        if time_guide:
-            ge0.record()
+        mark(2)
         W.guide_build_pdf(svo, x["ray_pos"], binout["origin_ray"], binout["n_bins"], B, N=N,
                           jitter=True, blur=True, seed=w.seed, frame=frame, out=guide)
-        if time_guide:
-            ge1.record()
+        mark(3)
         W.guide_sample(*guide, N, binout["bin_of_ray"], x["u"], out=so)
+        mark(4)
         W.guide_eval_pdf(guide[0], N, binout["bin_of_ray"], x["mis"], out=eo)
+        mark(5)
 
     for k in range(args.warmup):
         step(k, inp)
@@ -380,8 +386,10 @@ def run_gpu(args, world, rank, local):
         ev[k][0].record()
         step(args.warmup + k, inp, time_guide=True)
         ev[k][1].record()
-        ge1.synchronize()
-        guide_ms.append(ge0.elapsed_time(ge1))
+        sev[-1].synchronize()
+        for j, name in enumerate(stage_names):
+            stage_ms[name].append(sev[j].elapsed_time(sev[j + 1]))
+        guide_ms.append(stage_ms["guide_build_pdf"][-1])
     torch.cuda.synchronize()
     barrier(world)
     launches = W.kernel_launches() - launches0
@@ -491,6 +499,7 @@ def run_gpu(args, world, rank, local):
                 "l2": "flushed (256 MiB write) before every step"},
         "fused_step": {"value": fused_v, "unit": UNIT, "ms_per_step": statistics.mean(fused_ms),
                        "calls": "svo_accumulate + bin_rays + guide_build_sample (alpha 0.5)"},
+        "stages": stage_rooflines(stage_ms, alg["bytes"], R, n_rec, svo.n_nodes, peak),
         "roofline": {"kernel": "k_guide_build", "bound": "hbm", "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                      "peak_kind": peak_kind, "algorithmic_bytes": alg["bytes"],
@@ -681,6 +690,23 @@ def city_section(args):
     out["learned_training"] = {"steps": args.city_train_steps, "batch_bins": 65536, "seconds": train_s,
                                "heldout_kl": kl, "fallback_threshold": tau, "uses_learned": use}
     out["chosen"] = "learned" if use else "svo_traced (fallback)"
+    return out
+
+
+def stage_rooflines(stage_ms, trace_bytes, R, n_rec, n_nodes, peak):
+    """Mean CUDA-event time of each call of the step, its algorithmic bytes and
+    the achieved fraction of the measured HBM bandwidth (bytes per unit:
+    accumulate 40 B per record (28 B read + 12 B atomics) + 48 B per node for the
+    bottom-up average; run-mode binning 92 B per ray (pos + normal 24, keys 8,
+    3 radix passes x 16, order + bin id 12); the field kernel as modelled in the
+    roofline object; sampling 32 B and evaluation 20 B per ray)."""
+    model = {"accumulate": 40.0 * n_rec + 48.0 * n_nodes, "bin_rays": 92.0 * R, "guide_build_pdf": trace_bytes,
+             "guide_sample": 32.0 * R, "guide_eval_pdf": 20.0 * R}
+    out = {}
+    for name, ts in stage_ms.items():
+        ms = statistics.mean(ts)
+        gbs = model[name] / (ms / 1e3) / 1e9
+        out[name] = {"ms": ms, "algorithmic_bytes": model[name], "GB_s": gbs, "frac": gbs / peak}
     return out
 
 
