@@ -439,7 +439,8 @@ typedef struct wfpg_frame_stats {
 } wfpg_frame_stats;
 
 /* Creates a frame over an existing SVO (not owned; it must outlive the frame)
- * and scene (device pointers, not owned).  emission, albedo: device float
+ * and scene (device pointers, not owned).  W x H x (WFPG_FRAME_MAX_DEPTH + 1)
+ * must stay below 2^32 (32-bit record indices; about 477M pixels).  emission, albedo: device float
  * arrays, one per primitive.  Allocates the path state (about
  * 4 * W * H * (12 * (max_depth + 1) + 48) bytes).  Synchronises `stream`. */
 WFPG_API int frame_create(wfpg_svo* svo, const wfpg_scene* scene, const float* emission, const float* albedo,

@@ -507,7 +507,9 @@ int frame_create(wfpg_svo* svo, const wfpg_scene* scene, const float* emission, 
     if (!svo || !scene || !emission || !albedo || !cam || !out)
         return ffail(WFPG_ERR_INVALID_ARG, "frame_create: null argument");
     *out = nullptr;
-    if (cam->width == 0 || cam->height == 0 || (uint64_t)cam->width * cam->height > (1u << 30))
+    // record slots (max_depth + 1) x W x H are addressed with 32-bit indices
+    if (cam->width == 0 || cam->height == 0 ||
+        (uint64_t)cam->width * cam->height * (uint64_t)(WFPG_FRAME_MAX_DEPTH + 1) > 0xFFFFFFFFull)
         return ffail(WFPG_ERR_INVALID_ARG, "frame_create: image size out of range");
     if (!(cam->vfov_deg > 0.0f && cam->vfov_deg < 180.0f))
         return ffail(WFPG_ERR_INVALID_ARG, "frame_create: vfov_deg must be in (0, 180)");

@@ -16,6 +16,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <string>
 
@@ -508,11 +509,14 @@ int gemm(const GemmArgs& a, int splits, cudaStream_t st) {
     auto kernel = k_gemm_tn<BN, EPI>;
     const int smem = (128 + BN) * kKChunk * 2;
     // the tiles plus the kernel's static shared memory exceed the default 48 KB
-    // window for the wide instantiations: raise the dynamic limit once
-    static bool raised = false;
-    if (!raised && smem > 32 * 1024) {
+    // window for the wide instantiations: raise the dynamic limit once per device
+    static std::atomic<uint64_t> raised{0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const uint64_t bit = 1ull << (dev & 63);
+    if (smem > 32 * 1024 && !(raised.load(std::memory_order_relaxed) & bit)) {
         cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        raised = true;
+        raised.fetch_or(bit, std::memory_order_relaxed);
     }
     WFPG_LAUNCH(kernel, grid, kGemmThreads, smem, st, g);
     return splits;
