@@ -529,12 +529,21 @@ __global__ void __launch_bounds__(kGuideThreads, 1024 / kGuideThreads) k_guide_b
                     const float tez = ivz != 0.0f ? cross_time(ez, ivz > 0.0f, gz, ivz) : INF;
                     const int a = (tex <= tey && tex <= tez) ? 0 : (tey <= tez ? 1 : 2);
                     const float tx = a == 0 ? tex : (a == 1 ? tey : tez);
-                    const int nx = a == 0 ? ex : advance_axis(cx, bx, size, gx, ivx, __fmul_rn(dx, T.scale), tx, true);
-                    const int ny = a == 1 ? ey : advance_axis(cy, by, size, gy, ivy, __fmul_rn(dy, T.scale), tx, a > 1);
-                    const int nz = a == 2 ? ez : advance_axis(cz, bz, size, gz, ivz, __fmul_rn(dz, T.scale), tx, false);
-                    // (axis order for ties: x precedes an exit along y or z, y precedes
-                    // an exit along z, z precedes nothing)
-                    const int na = a == 0 ? nx : (a == 1 ? ny : nz);
+                    // the two other axes p < q, gathered by selects so that every lane runs
+                    // the catch-up exactly twice (ties: an axis precedes the exit axis a
+                    // when its index is smaller)
+                    const int p = a == 0 ? 1 : 0, q = a == 2 ? 1 : 2;
+                    const int cp = p == 0 ? cx : cy, cq = q == 1 ? cy : cz;
+                    const int bp = p == 0 ? bx : by, bq = q == 1 ? by : bz;
+                    const float gp = p == 0 ? gx : gy, gq = q == 1 ? gy : gz;
+                    const float ip = p == 0 ? ivx : ivy, iq = q == 1 ? ivy : ivz;
+                    const float dp = p == 0 ? dx : dy, dq = q == 1 ? dy : dz;
+                    const int np = advance_axis(cp, bp, size, gp, ip, __fmul_rn(dp, T.scale), tx, p < a);
+                    const int nq = advance_axis(cq, bq, size, gq, iq, __fmul_rn(dq, T.scale), tx, q < a);
+                    const int na = a == 0 ? ex : (a == 1 ? ey : ez);
+                    const int nx = a == 0 ? na : np;
+                    const int ny = a == 1 ? na : (p == 1 ? np : nq);
+                    const int nz = a == 2 ? na : nq;
                     if (tx == INF || na < 0 || na >= res) {
                         done = true;  // left the grid: miss
                     } else if (++steps > cap) {
