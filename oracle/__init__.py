@@ -16,7 +16,7 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRCS = ["svo.cpp", "octa_trace.cpp", "bins.cpp", "guide.cpp", "api.cpp", "learned.cpp"]
+_SRCS = ["svo.cpp", "octa_trace.cpp", "bins.cpp", "guide.cpp", "api.cpp", "learned.cpp", "product.cpp"]
 _HDRS = ["oracle.h", "oracle_internal.h"]
 _OUT = os.path.join(_HERE, "_build", "liboracle.so")
 _lock = threading.Lock()
@@ -89,6 +89,10 @@ def _declare(L):
         "orc_pdf_cdf": (None, [P, I32, P, P, P]),
         "orc_trace": (None, [P, P, P, SZ, F, F, I32, P, P, P, P, P, P, P, P, P]),
         "orc_mlp_num_params": (SZ, []),
+        "orc_product_block_sums": (None, [P, I32, SZ, P]),
+        "orc_product_sample": (None, [P, P, I32, P, P, P, SZ, P, P, P]),
+        "orc_product_eval": (None, [P, P, I32, P, P, P, SZ, P]),
+        "orc_product_block_weight": (F, [P, I32]),
         "orc_mlp_features": (None, [P, P, SZ, P, F, P]),
         "orc_mlp_forward": (None, [P, P, P, SZ, P, F, I32, P, P]),
         "orc_mlp_grad": (C.c_double, [P, P, P, SZ, P, F, P, I32, P]),
@@ -369,3 +373,44 @@ def adam(params, m, v, grad, t, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
     grad = _c(grad, np.float64)
     lib().orc_adam(_p(params), _p(m), _p(v), _p(grad), len(params), int(t), lr, b1, b2, eps)
     return params, m, v
+
+
+# ---------------------------------------------------------------- product guiding (Sec. 3.6)
+def product_block_sums(pdf, N):
+    """S[bin][64]: sums of the cell densities over the 8 x 8 blocks (row-major)."""
+    pdf = _c(pdf, np.float32).reshape(-1, N * N)
+    S = np.zeros((pdf.shape[0], 64), np.float32)
+    lib().orc_product_block_sums(_p(pdf), N, pdf.shape[0], _p(S))
+    return S
+
+
+def product_sample(pdf, S, N, bins, nrm, u):
+    """Two-stage product sampling (block from beta_B S_B, then cell and point in
+    the block from the field).  Returns (dir [n,3], pdf [n], cell [n])."""
+    pdf = _c(pdf, np.float32)
+    S = _c(S, np.float32)
+    bins = _c(bins, np.uint32)
+    nrm = _c(nrm, np.float32).reshape(-1, 3)
+    u = _c(u, np.float32).reshape(-1, 2)
+    n = len(bins)
+    d = np.zeros((n, 3), np.float32)
+    p = np.zeros(n, np.float32)
+    c = np.zeros(n, np.uint32)
+    lib().orc_product_sample(_p(pdf), _p(S), N, _p(bins), _p(nrm), _p(u), n, _p(d), _p(p), _p(c))
+    return d, p, c
+
+
+def product_eval(pdf, S, N, bins, nrm, dirs):
+    """Product density of given directions."""
+    pdf = _c(pdf, np.float32)
+    S = _c(S, np.float32)
+    bins = _c(bins, np.uint32)
+    nrm = _c(nrm, np.float32).reshape(-1, 3)
+    dirs = _c(dirs, np.float32).reshape(-1, 3)
+    out = np.zeros(len(bins), np.float32)
+    lib().orc_product_eval(_p(pdf), _p(S), N, _p(bins), _p(nrm), _p(dirs), len(bins), _p(out))
+    return out
+
+
+def product_block_weight(n, B):
+    return float(lib().orc_product_block_weight(_p(_c(n, np.float32)), int(B)))
