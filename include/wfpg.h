@@ -291,6 +291,42 @@ WFPG_API int guide_sample_mix(const float* pdf, const float* cdf_row, const floa
                               float* dir, float* pdf_out, void* stream);
 
 /*
+ * Product path guiding (Sec. 3.6): the bin's field at 8 x 8 blocks of
+ * b x b cells (b = N / 8; N = 8 .. 128) times the ray's Lambertian BSDF at the
+ * same resolution, sampled in two stages -- a block, then a cell and a point in
+ * it from the full-resolution field inside the block.  Definitions:
+ *   S_B    = sum of the cell densities pdf_c of block B (row-major blocks,
+ *            cells summed row by row);
+ *   beta_B = max(0, n . w_B) + 2^-10, w_B the octahedral image of the block's
+ *            centre (the floor keeps the density positive wherever the field is);
+ *   Z      = running sum of beta_B S_B over B = 0 .. 63;
+ *   p(w)   = beta_B pdf_c N^2 / (4 pi Z)   (normalised over the sphere).
+ * Sampling with (u0, u1): block = first B whose running sum exceeds u0 Z; the
+ * remainder picks the row inside the block by the running sum of its row sums,
+ * u1 the cell of that row by the running sum of its cells, and the in-cell
+ * offsets invert those sums linearly (as guide_sample does).  All sums run
+ * sequentially in the stated order, binary32.
+ *
+ * guide_product_sums: S[bin][64] for bins < min(*n_bins_dev, bin_cap), from
+ *   pdf tables as guide_build_pdf or guide_learned_build_pdf write them.
+ * guide_product_sample: per ray i < min(*n_dev, n): u[i] = (u0, u1, u2); if
+ *   u2 < alpha the product sample, else a cosine direction about nrm[i];
+ *   pdf_out[i] = alpha * p(dir) + (1 - alpha) * max(0, cos) / pi; cell[i] (may
+ *   be NULL) = the product-sampled cell, 0xFFFFFFFF for the cosine branch.  A
+ *   ray whose bin has no table takes the cosine branch with alpha = 0.
+ * guide_product_eval: the same mixture density of given directions.
+ */
+WFPG_API int guide_product_sums(const float* pdf, int N, uint32_t bin_cap, const uint32_t* n_bins_dev, float* S,
+                                void* stream);
+WFPG_API int guide_product_sample(const float* pdf, const float* S, int N, uint32_t bin_cap,
+                                  const uint32_t* n_bins_dev, const uint32_t* bin_of_ray, const float* nrm,
+                                  const float* u, uint32_t n, const uint32_t* n_dev, float alpha, float* dir,
+                                  float* pdf_out, uint32_t* cell, void* stream);
+WFPG_API int guide_product_eval(const float* pdf, const float* S, int N, uint32_t bin_cap,
+                                const uint32_t* n_bins_dev, const uint32_t* bin, const float* nrm,
+                                const float* dir, uint32_t n, float alpha, float* out, void* stream);
+
+/*
  * guide_sample -- the guided branch of Alg. 3's sampling step: inverse-CDF
  * sampling of the piecewise-constant density.  Per ray: t0 = u0 * T; the row
  * is the first marginal entry > t0 (N-1 if none); t1 = u1 * T_row; the

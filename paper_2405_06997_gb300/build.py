@@ -19,7 +19,7 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libwfpg.so")
 
 SOURCES = ["sort.cu", "svo_build.cu", "exitance.cu", "bins.cu", "guide.cu", "api.cu",
-           "bins_static.cu", "mlp.cu", "harness.cu", "frame.cu"]
+           "bins_static.cu", "mlp.cu", "harness.cu", "frame.cu", "product.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "--fmad=false", "-Xcompiler", "-fPIC",
               "-Xcompiler", "-fvisibility=hidden", "-I", INCLUDE, "-I", CSRC]

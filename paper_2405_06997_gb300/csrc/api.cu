@@ -28,6 +28,15 @@ int guide_fused_impl(const wfpg_svo* s, const float* pos, const float* nrm, cons
                      float* pdf_out, uint32_t n, void* workspace, size_t ws_bytes, cudaStream_t st,
                      const uint32_t* frame_dev = nullptr);
 size_t guide_fused_workspace_bytes(int N, uint32_t n, uint32_t split);
+int product_sums_impl(const float* pdf, int N, uint32_t bin_cap, const uint32_t* n_bins_dev, float* S,
+                      cudaStream_t st);
+int product_sample_impl(const float* pdf, const float* S, int N, uint32_t bin_cap, const uint32_t* n_bins_dev,
+                        const uint32_t* bin_of_ray, const float* nrm, const float* u, uint32_t n,
+                        const uint32_t* n_dev, float alpha, float* dir, float* pdf_out, uint32_t* cell,
+                        cudaStream_t st);
+int product_eval_impl(const float* pdf, const float* S, int N, uint32_t bin_cap, const uint32_t* n_bins_dev,
+                      const uint32_t* bin, const float* nrm, const float* dir, uint32_t n, float alpha, float* out,
+                      cudaStream_t st);
 int sample_mix_impl(const float* pdf, const float* cdf_row, const float* cdf_marg, int N, uint32_t bin_cap,
                     const uint32_t* n_bins_dev, const uint32_t* bin_of_ray, const float* nrm, const float* u,
                     uint32_t n, const uint32_t* n_dev, float alpha, float* dir, float* pdf_out, cudaStream_t st);
@@ -222,6 +231,41 @@ int guide_build_sample(const wfpg_svo* s, const float* pos, const float* nrm, co
     if (rc == WFPG_ERR_INVALID_ARG)
         return fail(rc, "guide_build_sample: the field does not fit in shared memory with this block size");
     if (rc != WFPG_OK) return cuda_fail("guide_build_sample");
+    return WFPG_OK;
+}
+
+int guide_product_sums(const float* pdf, int N, uint32_t bin_cap, const uint32_t* n_bins_dev, float* S,
+                       void* stream) {
+    if (!valid_n(N)) return fail(WFPG_ERR_INVALID_ARG, "guide_product_sums: N must be 8, 16, 32, 64 or 128");
+    if (bin_cap && (!pdf || !S)) return fail(WFPG_ERR_INVALID_ARG, "guide_product_sums: null array");
+    if (product_sums_impl(pdf, N, bin_cap, n_bins_dev, S, as_stream(stream)) != WFPG_OK)
+        return cuda_fail("guide_product_sums");
+    return WFPG_OK;
+}
+
+int guide_product_sample(const float* pdf, const float* S, int N, uint32_t bin_cap, const uint32_t* n_bins_dev,
+                         const uint32_t* bin_of_ray, const float* nrm, const float* u, uint32_t n,
+                         const uint32_t* n_dev, float alpha, float* dir, float* pdf_out, uint32_t* cell,
+                         void* stream) {
+    if (!valid_n(N)) return fail(WFPG_ERR_INVALID_ARG, "guide_product_sample: N must be 8, 16, 32, 64 or 128");
+    if (!(alpha >= 0.0f && alpha <= 1.0f)) return fail(WFPG_ERR_INVALID_ARG, "guide_product_sample: alpha in [0, 1]");
+    if (n && (!bin_of_ray || !nrm || !u || !dir || !pdf_out || (bin_cap && (!pdf || !S))))
+        return fail(WFPG_ERR_INVALID_ARG, "guide_product_sample: null array");
+    if (product_sample_impl(pdf, S, N, bin_cap, n_bins_dev, bin_of_ray, nrm, u, n, n_dev, alpha, dir, pdf_out, cell,
+                            as_stream(stream)) != WFPG_OK)
+        return cuda_fail("guide_product_sample");
+    return WFPG_OK;
+}
+
+int guide_product_eval(const float* pdf, const float* S, int N, uint32_t bin_cap, const uint32_t* n_bins_dev,
+                       const uint32_t* bin, const float* nrm, const float* dir, uint32_t n, float alpha, float* out,
+                       void* stream) {
+    if (!valid_n(N)) return fail(WFPG_ERR_INVALID_ARG, "guide_product_eval: N must be 8, 16, 32, 64 or 128");
+    if (!(alpha >= 0.0f && alpha <= 1.0f)) return fail(WFPG_ERR_INVALID_ARG, "guide_product_eval: alpha in [0, 1]");
+    if (n && (!bin || !nrm || !dir || !out || (bin_cap && (!pdf || !S))))
+        return fail(WFPG_ERR_INVALID_ARG, "guide_product_eval: null array");
+    if (product_eval_impl(pdf, S, N, bin_cap, n_bins_dev, bin, nrm, dir, n, alpha, out, as_stream(stream)) != WFPG_OK)
+        return cuda_fail("guide_product_eval");
     return WFPG_OK;
 }
 

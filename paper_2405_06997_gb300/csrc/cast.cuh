@@ -162,10 +162,16 @@ __device__ __forceinline__ Hit cast_svo(const SvoCast& V, const float* __restric
             }
             if (bp != kNone && best <= tx + 1e-5f * fmaxf(1.0f, tx)) return Hit{best, bp};
         }
-        const int nx = a == 0 ? ex : advance_axis(cx, bx, size, gx, ivx, dx * V.scale, tx, true);
-        const int ny = a == 1 ? ey : advance_axis(cy, by, size, gy, ivy, dy * V.scale, tx, a > 1);
-        const int nz = a == 2 ? ez : advance_axis(cz, bz, size, gz, ivz, dz * V.scale, tx, false);
-        const int na = a == 0 ? nx : (a == 1 ? ny : nz);
+        // the two other axes p < q by selects: two catch-ups with uniform control flow
+        const int p = a == 0 ? 1 : 0, q = a == 2 ? 1 : 2;
+        const int np = advance_axis(p == 0 ? cx : cy, p == 0 ? bx : by, size, p == 0 ? gx : gy, p == 0 ? ivx : ivy,
+                                    (p == 0 ? dx : dy) * V.scale, tx, p < a);
+        const int nq = advance_axis(q == 1 ? cy : cz, q == 1 ? by : bz, size, q == 1 ? gy : gz, q == 1 ? ivy : ivz,
+                                    (q == 1 ? dy : dz) * V.scale, tx, q < a);
+        const int na = a == 0 ? ex : (a == 1 ? ey : ez);
+        const int nx = a == 0 ? na : np;
+        const int ny = a == 1 ? na : (p == 1 ? np : nq);
+        const int nz = a == 2 ? na : nq;
         if (tx == INF || na < 0 || na >= res) return Hit{-1.0f, kNone};
         const uint32_t diff = (uint32_t)((cx ^ nx) | (cy ^ ny) | (cz ^ nz));
         level = D - 1 - (31 - __clz(diff));

@@ -201,6 +201,32 @@ __device__ __forceinline__ float2 dir_to_octa(float dx, float dy, float dz) {
     return make_float2(dx < 0.0f ? -bu : bu, dy < 0.0f ? -bv : bv);
 }
 
+// cell of a direction under the octahedral map (the cell guide_eval_pdf reads)
+__device__ __forceinline__ int octa_cell(float3 d, int N) {
+    const float2 uv = dir_to_octa(d.x, d.y, d.z);
+    const float hn = __fmul_rn((float)N, 0.5f);
+    const float a = __fmul_rn(__fadd_rn(uv.x, 1.0f), hn), c = __fmul_rn(__fadd_rn(uv.y, 1.0f), hn);
+    const int i = min((a >= 0.0f) ? (int)a : 0, N - 1);
+    const int j = min((c >= 0.0f) ? (int)c : 0, N - 1);
+    return j * N + i;
+}
+
+// cosine-distributed direction about the unit normal n (orthonormal basis of
+// Duff et al. 2017, "Building an orthonormal basis, revisited")
+__device__ __forceinline__ float3 cosine_dir(float nx, float ny, float nz, float u0, float u1) {
+    const float sg = nz >= 0.0f ? 1.0f : -1.0f;
+    const float a = -1.0f / (sg + nz);
+    const float bb = nx * ny * a;
+    const float tx = 1.0f + sg * nx * nx * a, ty = sg * bb, tz = -sg * nx;
+    const float bx = bb, by = sg + ny * ny * a, bz = -ny;
+    const float r = sqrtf(u0);
+    float sp, cp;
+    sincospif(2.0f * u1, &sp, &cp);
+    const float z = sqrtf(fmaxf(0.0f, 1.0f - u0));
+    return make_float3(r * cp * tx + r * sp * bx + z * nx, r * cp * ty + r * sp * by + z * ny,
+                       r * cp * tz + r * sp * bz + z * nz);
+}
+
 // ---------------------------------------------------------------------------
 // host-side count of kernel launches issued by this library
 void note_launch();

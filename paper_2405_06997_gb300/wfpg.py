@@ -126,6 +126,9 @@ def lib():
             "frame_export": [P, I32, P, SZ, P],
             "frame_set_mlp": [P, P, P],
             "guide_sample_mix": [P, P, P, I32, U32, P, P, P, P, U32, P, F, P, P, P],
+            "guide_product_sums": [P, I32, U32, P, P, P],
+            "guide_product_sample": [P, P, I32, U32, P, P, P, P, U32, P, F, P, P, P, P],
+            "guide_product_eval": [P, P, I32, U32, P, P, P, P, U32, F, P, P],
             "wfpg_cast_rays_svo": [P, P, P, P, U32, F, P, P, P, P],
         }
         for name, args in sig.items():
@@ -616,6 +619,47 @@ def guide_sample_mix(pdf, cdf_row, cdf_marg, N, bins, nrm, u, *, alpha=0.5, n_bi
                                   alpha, _ptr(d, torch.float32, 3 * n), _ptr(pm, torch.float32, n),
                                   _stream(stream)))
     return d, pm
+
+
+def guide_product_sums(pdf, N, n_bins=None, out=None, stream=None):
+    """Per-bin sums of the field's cell densities over its 8 x 8 blocks (Sec. 3.6)."""
+    bin_cap = pdf.numel() // (N * N)
+    if out is None:
+        out = torch.empty((bin_cap, 64), dtype=torch.float32, device=pdf.device)
+    _check(lib().guide_product_sums(_ptr(pdf, torch.float32), N, bin_cap, _ptr(n_bins, torch.int32, 1, "n_bins"),
+                                    _ptr(out, torch.float32, bin_cap * 64), _stream(stream)))
+    return out
+
+
+def guide_product_sample(pdf, S, N, bins, nrm, u, *, alpha=1.0, n_bins=None, n_dev=None, out=None, stream=None):
+    """Product-guided sampling (Sec. 3.6) mixed with cosine sampling.  bins:
+    bin_of_ray; u: [n, 3].  Returns (dir, mixture pdf, cell [-1 for cosine])."""
+    n = bins.numel()
+    bin_cap = pdf.numel() // (N * N)
+    if out is None:
+        out = (torch.empty((n, 3), dtype=torch.float32, device=u.device),
+               torch.empty(n, dtype=torch.float32, device=u.device),
+               torch.empty(n, dtype=torch.int32, device=u.device))
+    d, p, c = out
+    _check(lib().guide_product_sample(_ptr(pdf, torch.float32), _ptr(S, torch.float32), N, bin_cap,
+                                      _ptr(n_bins, torch.int32, 1, "n_bins"), _ptr(bins, torch.int32, n),
+                                      _ptr(nrm, torch.float32, 3 * n, "nrm"), _ptr(u, torch.float32, 3 * n, "u"), n,
+                                      _ptr(n_dev, torch.int32, 1, "n_dev"), alpha, _ptr(d, torch.float32, 3 * n),
+                                      _ptr(p, torch.float32, n), _ptr(c, torch.int32, n), _stream(stream)))
+    return d, p, c
+
+
+def guide_product_eval(pdf, S, N, bins, nrm, dirs, *, alpha=1.0, n_bins=None, out=None, stream=None):
+    """Mixture density alpha * product + (1 - alpha) * cosine of given directions."""
+    n = bins.numel()
+    bin_cap = pdf.numel() // (N * N)
+    if out is None:
+        out = torch.empty(n, dtype=torch.float32, device=dirs.device)
+    _check(lib().guide_product_eval(_ptr(pdf, torch.float32), _ptr(S, torch.float32), N, bin_cap,
+                                    _ptr(n_bins, torch.int32, 1, "n_bins"), _ptr(bins, torch.int32, n),
+                                    _ptr(nrm, torch.float32, 3 * n, "nrm"), _ptr(dirs, torch.float32, 3 * n), n, alpha,
+                                    _ptr(out, torch.float32, n), _stream(stream)))
+    return out
 
 
 class Frame:
