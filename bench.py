@@ -473,6 +473,24 @@ def run_gpu(args, world, rank, local):
         b.synchronize()
         fused_ms.append(a.elapsed_time(b))
     fused_v = rays_all / (max_over_ranks(statistics.mean(fused_ms), world) / 1e3)
+
+    # product guiding (Sec. 3.6) on the same frame's fields: block sums + the
+    # two-stage product sample mixed 50/50 with cosine sampling (density included)
+    step(5000, inp)
+    psums = torch.empty((B, 64), dtype=torch.float32, device=dev)
+    pout = (torch.empty((R, 3), dtype=torch.float32, device=dev), torch.empty(R, dtype=torch.float32, device=dev),
+            torch.empty(R, dtype=torch.int32, device=dev))
+    prod_ms = []
+    for k in range(3 + args.steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        W.guide_product_sums(guide[0], N, n_bins=binout["n_bins"], out=psums)
+        W.guide_product_sample(guide[0], psums, N, binout["bin_of_ray"], inp["ray_nrm"], u3, alpha=0.5,
+                               n_bins=binout["n_bins"], out=pout)
+        b.record()
+        b.synchronize()
+        if k >= 3:
+            prod_ms.append(a.elapsed_time(b))
     clk = clocks.stop() if clocks else None
 
     if rank != 0:
@@ -497,6 +515,8 @@ def run_gpu(args, world, rank, local):
         "e2e": {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": e2e_ms[0], "copies": "pinned host <-> device on upload / download streams, double-buffered",
                 "l2": "flushed (256 MiB write) before every step"},
+        "product_sampling": {"ms": statistics.mean(prod_ms), "samples_per_s": R / (statistics.mean(prod_ms) / 1e3),
+                             "calls": "guide_product_sums + guide_product_sample (alpha 0.5) on the step's fields"},
         "fused_step": {"value": fused_v, "unit": UNIT, "ms_per_step": statistics.mean(fused_ms),
                        "calls": "svo_accumulate + bin_rays + guide_build_sample (alpha 0.5)"},
         "stages": stage_rooflines(stage_ms, alg["bytes"], R, n_rec, svo.n_nodes, peak),

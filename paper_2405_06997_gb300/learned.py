@@ -149,7 +149,8 @@ def guided_estimates(w, svo, proposal, *, frames=16, alpha=0.5, mlp=None, seed=1
     weighted by that mixture density (so the estimator stays unbiased); the
     second bounce is cosine-sampled.
         L = (albedo1 / pi) cos1 / p(w1) * (Le(x2) + albedo2 * Le(x3))
-    proposal: 'svo' (traced field), 'learned' (MLP) or 'bsdf' (cosine only).
+    proposal: 'svo' (traced field), 'svo_product' (traced field times the BSDF at
+    8 x 8 blocks, Sec. 3.6), 'learned' (MLP) or 'bsdf' (cosine only).
     Rays are binned with Partition-S (l_min, c_ray; the paper's Table 1 uses
     c_ray = 512 and its l_min 5, i.e. 4 here).  Returns the per-pixel mean and
     variance over frames and the guiding time per frame (binning + field/PDF +
@@ -177,26 +178,42 @@ def guided_estimates(w, svo, proposal, *, frames=16, alpha=0.5, mlp=None, seed=1
             e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
             e[0].record()
             r = W.bin_rays(svo, pos, l_min=l_min, c_ray=c_ray, seed=seed, frame=f, bin_cap=B)
-            if proposal == "svo":
+            if proposal in ("svo", "svo_product"):
                 guide = W.guide_build_pdf(svo, pos, r["origin_ray"], r["n_bins"], B, N=32, jitter=True, blur=True,
                                           seed=seed, frame=f, out=guide)
             else:
                 guide = W.guide_learned_build_pdf(mlp, pos, nrm, r["origin_ray"], r["n_bins"], B, lo=w.scene.lo,
                                                   size=w.scene.size, out=guide)
-            dg, _, _ = W.guide_sample(*guide, 32, r["bin_of_ray"], u[:, 0:2].contiguous())
-            e[1].record()
-            d = torch.where((u[:, 4] < a).unsqueeze(1), dg, dc).contiguous()
-            e[2].record()
-            pg = W.guide_eval_pdf(guide[0], 32, r["bin_of_ray"], d)
-            e[3].record()
-            e[3].synchronize()
-            t_guide = (e[0].elapsed_time(e[1]) + e[2].elapsed_time(e[3])) / 1e3
+            if proposal == "svo_product":
+                # Sec. 3.6: the field times the ray's BSDF at 8 x 8 blocks; the call
+                # returns the mixture (alpha product, 1 - alpha cosine) and its density
+                S = W.guide_product_sums(guide[0], 32, n_bins=r["n_bins"])
+                uu = torch.stack([u[:, 0], u[:, 1], u[:, 4]], dim=1).contiguous()
+                d, pmix, _ = W.guide_product_sample(guide[0], S, 32, r["bin_of_ray"], nrm, uu, alpha=a,
+                                                    n_bins=r["n_bins"])
+                e[1].record()
+                e[2].record()
+                e[3].record()
+                e[3].synchronize()
+                t_guide = e[0].elapsed_time(e[3]) / 1e3
+            else:
+                dg, _, _ = W.guide_sample(*guide, 32, r["bin_of_ray"], u[:, 0:2].contiguous())
+                e[1].record()
+                d = torch.where((u[:, 4] < a).unsqueeze(1), dg, dc).contiguous()
+                e[2].record()
+                pg = W.guide_eval_pdf(guide[0], 32, r["bin_of_ray"], d)
+                e[3].record()
+                e[3].synchronize()
+                t_guide = (e[0].elapsed_time(e[1]) + e[2].elapsed_time(e[3])) / 1e3
         else:
             d = dc.contiguous()
         cos = torch.clamp((d * nrm).sum(dim=1), min=0.0)
-        p = (1 - a) * cos / math.pi
-        if a > 0:
-            p = p + a * pg
+        if proposal == "svo_product":
+            p = pmix
+        else:
+            p = (1 - a) * cos / math.pi
+            if a > 0:
+                p = p + a * pg
         t1, prim1, n2 = W.cast_rays(q, sp, (pos + 1e-4 * nrm).contiguous(), d)
         hit1 = prim1 >= 0
         pi1 = prim1.clamp(min=0).long()
@@ -222,14 +239,14 @@ def compare_proposals(w, svo, mlp, *, frames=16, alpha=0.5, seed=1, fine_c_ray=3
     Partition-S bins of fine_c_ray rays (the MLP's cost per bin is a few
     hundred kFLOP, a traced field's is N^2 cone rays)."""
     out = {}
-    runs = (("bsdf", "bsdf", {}), ("svo", "svo", {}), ("learned", "learned", {}),
+    runs = (("bsdf", "bsdf", {}), ("svo", "svo", {}), ("svo_product", "svo_product", {}), ("learned", "learned", {}),
             ("learned_fine", "learned", {"c_ray": fine_c_ray, "bin_cap": fine_bin_cap}))
     for name, proposal, kw in runs:
         m, v, t = guided_estimates(w, svo, proposal, frames=frames, alpha=alpha, mlp=mlp, seed=seed, **kw)
         out[name] = {"mean": float(m.mean().item()), "variance": float(v.mean().item()),
                      "guiding_seconds_per_frame": t, "guided_samples_per_s": len(w.ray_pos) / t if t > 0 else None}
     out["learned_fine"]["c_ray"] = fine_c_ray
-    for name in ("learned", "learned_fine"):
+    for name in ("svo_product", "learned", "learned_fine"):
         out[f"variance_ratio_{name}_over_svo"] = out[name]["variance"] / out["svo"]["variance"]
         # work-normalised: (variance x guiding time) of the traced over the learned proposal
         out[f"efficiency_ratio_{name}_over_svo"] = (
