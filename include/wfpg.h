@@ -460,6 +460,12 @@ typedef struct wfpg_frame_params {
     int caster;               /* closest hits: 0 auto (SVO walk above 64 primitives), 1 every primitive, 2 SVO walk */
     int proposal;             /* guided part: 0 SVO-traced field (fused GuideRays), 1 learned MLP (N must be 32;
                                  frame_set_mlp first) */
+    int decay;                /* 1: the traced grid halves per depth (N, N/2, N/4, ..., at least 8), as the
+                                 paper runs 128^2 .. 16^2 over four bounces */
+    int combine;              /* image combination over frames (Eq. 7, weights h(i) of frame i = 1, 2, ...):
+                                 0 constant, 1 linear (min(i, 5)), 2 quadratic (min(i, 5)^2), 3 one-two
+                                 (1 then 2), 4 discard first (0 then 1), 5 PT first (frame 1 unguided,
+                                 then constant) */
 } wfpg_frame_params;
 
 typedef struct wfpg_frame wfpg_frame;
@@ -495,8 +501,9 @@ WFPG_API int frame_set_mlp(wfpg_frame* f, wfpg_mlp* mlp, const wfpg_learned_para
 WFPG_API int frame_get_params(const wfpg_frame* f, wfpg_frame_params* p);
 /* Zeroes the per-pixel sums and the frame count. */
 WFPG_API int frame_reset_image(wfpg_frame* f, void* stream);
-/* mean[W*H] and var[W*H] (device, may be NULL): per-pixel mean of the path
- * estimates over the frames run and the variance of one estimate (unbiased,
+/* mean[W*H] and var[W*H] (device, may be NULL): per-pixel combination of the
+ * frames' path estimates, sum h(i) S_i / sum h(i) with the weights of
+ * `combine`, and the (unweighted) variance of one frame's estimate (unbiased,
  * 0 when fewer than 2 frames). */
 WFPG_API int frame_image(wfpg_frame* f, float* mean, float* var, void* stream);
 /* Synchronises `stream` and reads the last frame's counts. */

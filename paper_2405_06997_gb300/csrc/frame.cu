@@ -76,6 +76,9 @@ struct FrameView {
     uint32_t* nv;
     double* img_sum;
     double* img_sq;
+    double* img_wsum;  // sum of h(i) x estimate
+    double* wsum;      // sum of h(i)
+    int combine;
     uint32_t* counters;  // [0 .. max_depth - 1]: paths per depth; [WFPG_FRAME_MAX_DEPTH + 1]: records
     uint32_t* fidx;      // [0 .. max_depth]: random-stream frame index per depth
     uint32_t* frame_counter;
@@ -85,6 +88,18 @@ struct FrameView {
 
 __device__ __forceinline__ float path_uniform(const FrameView& F, uint32_t path, uint32_t counter) {
     return uniform01(F.pseed, ((uint64_t)F.fidx[0] << 32) | path, counter);
+}
+
+// Eq. 7's frame weight h(i), i = 1, 2, ... (PT first weighs every frame 1; its
+// first frame runs unguided)
+__device__ __forceinline__ double combine_weight(int combine, unsigned long long i) {
+    switch (combine) {
+        case 1: return (double)(i < 5 ? i : 5);
+        case 2: return (double)(i < 5 ? i * i : 25);
+        case 3: return i == 1 ? 1.0 : 2.0;
+        case 4: return i == 1 ? 0.0 : 1.0;
+        default: return 1.0;
+    }
 }
 
 __global__ void k_frame_begin(FrameView F) {
@@ -248,24 +263,27 @@ __global__ void __launch_bounds__(256) k_records(FrameView F, float* __restrict_
     const double L = (double)S;
     F.img_sum[i] += L;
     F.img_sq[i] += L * L;
+    F.img_wsum[i] += combine_weight(F.combine, *F.frames_run + 1ull) * L;
 }
 
 __global__ void k_frame_end(FrameView F) {
     unsigned long long g = 0;
     for (int k = 0; k < F.max_depth; ++k) g += F.counters[k];
     *F.guided += g;
+    *F.wsum += combine_weight(F.combine, *F.frames_run + 1ull);
     *F.frames_run += 1ull;
     *F.frame_counter += 1u;
 }
 
 __global__ void __launch_bounds__(256) k_image(const double* __restrict__ sum, const double* __restrict__ sq,
+                                               const double* __restrict__ wsum_px, const double* __restrict__ wsum,
                                                const unsigned long long* __restrict__ frames, uint32_t P,
                                                float* __restrict__ mean, float* __restrict__ var) {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= P) return;
     const double f = (double)*frames;
     const double m = f > 0 ? sum[i] / f : 0.0;
-    if (mean) mean[i] = (float)m;
+    if (mean) mean[i] = *wsum > 0.0 ? (float)(wsum_px[i] / *wsum) : 0.0f;
     if (var) var[i] = f > 1 ? (float)fmax(0.0, (sq[i] - f * m * m) / (f - 1.0)) : 0.0f;
 }
 
@@ -330,6 +348,9 @@ struct wfpg_frame {
     uint32_t* rec_src = nullptr;
     double* img_sum = nullptr;
     double* img_sq = nullptr;
+    double* img_wsum = nullptr;
+    double* wsum = nullptr;
+    unsigned long long frames_since_reset = 0;  // host-side count (PT first runs frame 1 unguided)
     uint32_t* counters = nullptr;  // [WFPG_FRAME_MAX_DEPTH + 2]
     uint32_t* fidx = nullptr;      // [WFPG_FRAME_MAX_DEPTH + 1]
     uint32_t* frame_counter = nullptr;
@@ -400,6 +421,9 @@ struct wfpg_frame {
         F.nv = nv;
         F.img_sum = img_sum;
         F.img_sq = img_sq;
+        F.img_wsum = img_wsum;
+        F.wsum = wsum;
+        F.combine = p.combine;
         F.counters = counters;
         F.fidx = fidx;
         F.frame_counter = frame_counter;
@@ -440,6 +464,7 @@ struct wfpg_frame {
             } else {
                 wfpg_guide_params gp = p.guide;
                 gp.seed = p.seed;
+                if (p.decay) gp.N = std::max(8, p.guide.N >> k);
                 rc = guide_fused_impl(svo, Q.pos, Q.nrm, origin_ray, n_bins + k, bin_cap, ray_order, bin_offset,
                                       Q.u, p.alpha, &gp, dir, pdf, P, guide_ws, guide_ws_bytes, st, fidx + k);
             }
@@ -497,6 +522,7 @@ static int check_params(const wfpg_frame_params* p, int depth_cap) {
     if (p->proposal < 0 || p->proposal > 1) return ffail(WFPG_ERR_INVALID_ARG, "frame: proposal must be 0 or 1");
     if (p->proposal == 1 && p->guide.N != 32)
         return ffail(WFPG_ERR_INVALID_ARG, "frame: the learned proposal has N = 32");
+    if (p->combine < 0 || p->combine > 5) return ffail(WFPG_ERR_INVALID_ARG, "frame: combine must be 0 .. 5");
     return WFPG_OK;
 }
 
@@ -546,6 +572,7 @@ int frame_create(wfpg_svo* svo, const wfpg_scene* scene, const float* emission, 
          f->alloc(&f->vLe, V) && f->alloc(&f->vpos, 3 * V) && f->alloc(&f->vwo, 3 * V) && f->alloc(&f->nv, P) &&
          f->alloc(&f->rec_pos, 3 * V) && f->alloc(&f->rec_wout, 3 * V) && f->alloc(&f->rec_L, V) &&
          f->alloc(&f->rec_src, V) && f->alloc(&f->img_sum, P) && f->alloc(&f->img_sq, P) &&
+         f->alloc(&f->img_wsum, P) && f->alloc(&f->wsum, 1) &&
          f->alloc(&f->counters, WFPG_FRAME_MAX_DEPTH + 2) && f->alloc(&f->fidx, WFPG_FRAME_MAX_DEPTH + 1) &&
          f->alloc(&f->frame_counter, 1) && f->alloc(&f->frames_run, 1) && f->alloc(&f->guided, 1) &&
          f->alloc(&f->scalar, 1);
@@ -560,6 +587,8 @@ int frame_create(wfpg_svo* svo, const wfpg_scene* scene, const float* emission, 
     cudaMemsetAsync(f->nv, 0, 4 * (size_t)P, st);
     cudaMemsetAsync(f->img_sum, 0, 8 * (size_t)P, st);
     cudaMemsetAsync(f->img_sq, 0, 8 * (size_t)P, st);
+    cudaMemsetAsync(f->img_wsum, 0, 8 * (size_t)P, st);
+    cudaMemsetAsync(f->wsum, 0, 8, st);
     cudaMemsetAsync(f->frame_counter, 0, 4, st);
     cudaMemsetAsync(f->frames_run, 0, 8, st);
     cudaMemsetAsync(f->guided, 0, 8, st);
@@ -588,6 +617,16 @@ int frame_run(wfpg_frame* f, uint32_t n_frames, int use_graph, void* stream) {
         if (rc != WFPG_OK) return ffail(rc, "frame_run: graph capture failed");
     }
     for (uint32_t i = 0; i < n_frames; ++i) {
+        if (f->p.combine == 5 && f->frames_since_reset == 0) {  // PT first: the first frame unguided
+            const float alpha = f->p.alpha;
+            f->p.alpha = 0.0f;
+            const int rc = f->enqueue(st);
+            f->p.alpha = alpha;
+            ++f->frames_since_reset;
+            if (rc != WFPG_OK) return ffail(rc, "frame_run: launch failed");
+            continue;
+        }
+        ++f->frames_since_reset;
         if (use_graph) {
             if (cudaGraphLaunch(f->exec, st) != cudaSuccess) return ffail(WFPG_ERR_CUDA, "frame_run: graph launch");
             note_launches((long long)f->graph_kernels);
@@ -637,6 +676,9 @@ int frame_reset_image(wfpg_frame* f, void* stream) {
     auto st = static_cast<cudaStream_t>(stream);
     cudaMemsetAsync(f->img_sum, 0, 8 * (size_t)f->P, st);
     cudaMemsetAsync(f->img_sq, 0, 8 * (size_t)f->P, st);
+    cudaMemsetAsync(f->img_wsum, 0, 8 * (size_t)f->P, st);
+    cudaMemsetAsync(f->wsum, 0, 8, st);
+    f->frames_since_reset = 0;
     cudaMemsetAsync(f->frames_run, 0, 8, st);
     cudaMemsetAsync(f->guided, 0, 8, st);
     return cudaGetLastError() == cudaSuccess ? WFPG_OK : ffail(WFPG_ERR_CUDA, "frame_reset_image");
@@ -645,7 +687,7 @@ int frame_reset_image(wfpg_frame* f, void* stream) {
 int frame_image(wfpg_frame* f, float* mean, float* var, void* stream) {
     if (!f) return ffail(WFPG_ERR_INVALID_ARG, "frame_image: null frame");
     WFPG_LAUNCH(k_image, div_up(f->P, 256), 256, 0, static_cast<cudaStream_t>(stream), f->img_sum, f->img_sq,
-                f->frames_run, f->P, mean, var);
+                f->img_wsum, f->wsum, f->frames_run, f->P, mean, var);
     return cudaGetLastError() == cudaSuccess ? WFPG_OK : ffail(WFPG_ERR_CUDA, "frame_image");
 }
 

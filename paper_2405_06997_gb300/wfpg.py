@@ -74,7 +74,8 @@ class Camera(C.Structure):
 
 class FrameParams(C.Structure):
     _fields_ = [("max_depth", I32), ("rr_depth", I32), ("alpha", F), ("l_min", I32), ("c_ray", U32),
-                ("guide", GuideParams), ("seed", U64), ("update", I32), ("caster", I32), ("proposal", I32)]
+                ("guide", GuideParams), ("seed", U64), ("update", I32), ("caster", I32), ("proposal", I32),
+                ("decay", I32), ("combine", I32)]
 
 
 class FrameStats(C.Structure):
@@ -82,6 +83,7 @@ class FrameStats(C.Structure):
                 ("records", U32), ("guided_samples", U64), ("status", U32), ("kernels_per_frame", C.c_ulonglong)]
 
 
+COMBINE = {"constant": 0, "linear": 1, "quadratic": 2, "one-two": 3, "discard-first": 4, "pt-first": 5}
 FRAME_BUF = {"vT": 0, "vLe": 1, "vpos": 2, "vwo": 3, "nv": 4, "rec_pos": 5, "rec_wout": 6, "rec_L": 7,
              "rec_src": 8, "q_pos": 9, "q_nrm": 10, "q_u": 11, "q_dir": 12, "q_pdf": 13, "q_path": 14}
 
@@ -673,7 +675,7 @@ class Frame:
     def __init__(self, svo: SVO, scene, *, eye, forward=(0.0, 0.0, 1.0), up=(0.0, 1.0, 0.0), vfov=60.0,
                  width=1920, height=1080, max_depth=4, rr_depth=2, alpha=0.5, l_min=2, c_ray=512, N=32,
                  eps=1e-2, jitter=True, blur=True, cos_weight=False, block=0, stage=0, seed=1, update=True,
-                 caster=0, proposal=0, device="cuda", stream=None):
+                 caster=0, proposal=0, decay=False, combine=0, device="cuda", stream=None):
         self.svo = svo
         self._q = torch.as_tensor(np.ascontiguousarray(scene.quads, np.float32).reshape(-1, 8), device=device)
         self._s = torch.as_tensor(np.ascontiguousarray(scene.spheres, np.float32).reshape(-1, 4), device=device)
@@ -689,7 +691,8 @@ class Frame:
                          t_skip=default_t_skip(svo.size, svo.depth), cos_weight=int(cos_weight), seed=seed,
                          frame=0, block=block, stage=stage)
         self.params = FrameParams(max_depth=max_depth, rr_depth=rr_depth, alpha=alpha, l_min=l_min, c_ray=c_ray,
-                                  guide=gp, seed=seed, update=int(update), caster=caster, proposal=proposal)
+                                  guide=gp, seed=seed, update=int(update), caster=caster, proposal=proposal,
+                                  decay=int(decay), combine=combine)
         self.device = device
         h = P()
         _check(lib().frame_create(svo.handle, C.byref(self._scene), _ptr(self._e), _ptr(self._a),

@@ -380,3 +380,46 @@ def test_frame_that_sees_nothing():
     assert st["paths"] == [0, 0, 0, 0] and st["records"] == 0 and st["status"] == 0
     assert float(m.abs().max()) == 0.0 and float(v.abs().max()) == 0.0
     np.testing.assert_array_equal(g.exitance()["acc_sum"], before["acc_sum"])
+
+
+def test_combination_heuristics_weigh_the_frames():
+    """Eq. 7: the linear heuristic's image equals sum h(i) S_i / sum h(i) of the
+    per-frame estimates S_i (from a constant-weight run with the same seeds), and
+    PT first's first frame is the unguided frame."""
+    K = 7
+    w, g1, _ = box_svo(13)
+    _, g2, _ = box_svo(13)
+    fa = make_frame(g1, w.scene, width=64, height=36)
+    fb = make_frame(g2, w.scene, width=64, height=36, combine=W.COMBINE["linear"])
+    means = []
+    for k in range(K):
+        fa.run(1)
+        means.append(fa.image()[0].double().cpu().numpy())
+    S = [means[0]] + [(k + 1) * means[k] - k * means[k - 1] for k in range(1, K)]
+    h = np.array([min(i, 5) for i in range(1, K + 1)], np.float64)
+    ref = sum(hi * Si for hi, Si in zip(h, S)) / h.sum()
+    fb.run(K)
+    np.testing.assert_allclose(fb.image()[0].double().cpu().numpy(), ref, rtol=2e-5, atol=1e-6)
+    # PT first: frame 1 equals a frame with alpha = 0
+    _, g3, _ = box_svo(13)
+    _, g4, _ = box_svo(13)
+    fc = make_frame(g3, w.scene, width=64, height=36, combine=W.COMBINE["pt-first"])
+    fd = make_frame(g4, w.scene, width=64, height=36, alpha=0.0)
+    fc.run(1)
+    fd.run(1)
+    assert torch.equal(fc.image()[0], fd.image()[0])
+
+
+def test_decaying_resolution_per_depth():
+    """decay: depth k traces N >> k; the frame's second depth equals standalone
+    calls at N / 2 on its queue (frame index 0 * 16 + 1)."""
+    w, g, _ = box_svo(14)
+    f = make_frame(g, w.scene, max_depth=2, update=False, N=32, c_ray=128, decay=True)
+    f.run(1, use_graph=False)
+    n = f.stats()["paths"][1]
+    assert n > 0
+    qp, qn, qu = (f.export(k)[:n].contiguous() for k in ("q_pos", "q_nrm", "q_u"))
+    r = W.bin_rays(g, qp, qn, l_min=2, c_ray=128, seed=3, frame=1, bin_cap=min(f.pixels, g.n_nodes))
+    d, pm = W.guide_build_sample(g, qp, qn, r, qu, alpha=0.5, N=16, jitter=True, blur=True, seed=3, frame=1)
+    assert torch.equal(f.export("q_dir")[:n], d)
+    assert torch.equal(f.export("q_pdf")[:n], pm)
