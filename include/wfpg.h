@@ -459,7 +459,9 @@ typedef struct wfpg_frame_params {
     int update;               /* 1: UpdateExitance after each frame */
     int caster;               /* closest hits: 0 auto (SVO walk above 64 primitives), 1 every primitive, 2 SVO walk */
     int proposal;             /* guided part: 0 SVO-traced field (fused GuideRays), 1 learned MLP (N must be 32;
-                                 frame_set_mlp first) */
+                                 frame_set_mlp first), 2 SVO-traced field times the BSDF (product guiding,
+                                 Sec. 3.6; tables for up to 65,536 bins per depth, rays of further bins
+                                 take the cosine branch) */
     int decay;                /* 1: the traced grid halves per depth (N, N/2, N/4, ..., at least 8), as the
                                  paper runs 128^2 .. 16^2 over four bounces */
     int combine;              /* image combination over frames (Eq. 7, weights h(i) of frame i = 1, 2, ...):

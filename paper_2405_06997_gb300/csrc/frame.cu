@@ -39,6 +39,15 @@ int sample_mix_impl(const float* pdf, const float* cdf_row, const float* cdf_mar
                     const uint32_t* n_bins_dev, const uint32_t* bin_of_ray, const float* nrm, const float* u,
                     uint32_t n, const uint32_t* n_dev, float alpha, float* dir, float* pdf_out, cudaStream_t st);
 SvoCast svo_cast_view(const wfpg_svo* s);
+int guide_build_impl(const wfpg_svo* s, const float* pos, const uint32_t* origin_ray, const uint32_t* n_bins_dev,
+                     uint32_t bin_cap, const wfpg_guide_params* p, float* pdf, float* cdf_row, float* cdf_marg,
+                     cudaStream_t st, const uint32_t* frame_dev);
+int product_sums_impl(const float* pdf, int N, uint32_t bin_cap, const uint32_t* n_bins_dev, float* S,
+                      cudaStream_t st);
+int product_sample_impl(const float* pdf, const float* S, int N, uint32_t bin_cap, const uint32_t* n_bins_dev,
+                        const uint32_t* bin_of_ray, const float* nrm, const float* u, uint32_t n,
+                        const uint32_t* n_dev, float alpha, float* dir, float* pdf_out, uint32_t* cell,
+                        cudaStream_t st);
 uint32_t mlp_max_batch(const wfpg_mlp* m);
 
 constexpr uint64_t kPathPurpose = 2;  // per-path uniforms (0: origins, 1: jitter)
@@ -359,6 +368,12 @@ struct wfpg_frame {
     double* scalar = nullptr;
     wfpg_mlp* mlp = nullptr;
     wfpg_learned_params lp{};
+    uint32_t product_cap = 0;        // bins per depth the product tables hold
+    int product_n = 0;               // grid side they are sized for
+    float* prod_pdf = nullptr;       // [product_cap][N^2]
+    float* prod_cr = nullptr;
+    float* prod_cm = nullptr;        // [product_cap][N]
+    float* prod_S = nullptr;         // [product_cap][64]
     uint32_t learned_cap = 0;        // bins per depth the learned tables hold
     float* tab_pdf = nullptr;        // [learned_cap][32 * 32]
     float* tab_cr = nullptr;
@@ -454,7 +469,17 @@ struct wfpg_frame {
             int rc = bin_rays_impl(svo, Q.pos, Q.nrm, P, &bp, nullptr, bin_of_ray, ray_order, bin_offset, origin_ray,
                                    bin_cap, n_bins + k, bin_ws, bin_ws_bytes, st, fidx + k);
             if (rc != WFPG_OK) return rc;
-            if (p.proposal == 1) {  // learned: MLP tables for the bins' origins, then the mixture
+            if (p.proposal == 2) {  // product guiding (Sec. 3.6): field tables, block sums, two-stage sample
+                wfpg_guide_params gp = p.guide;
+                gp.seed = p.seed;
+                if (p.decay) gp.N = std::max(8, p.guide.N >> k);
+                rc = guide_build_impl(svo, Q.pos, origin_ray, n_bins + k, product_cap, &gp, prod_pdf, prod_cr,
+                                      prod_cm, st, fidx + k);
+                if (rc == WFPG_OK) rc = product_sums_impl(prod_pdf, gp.N, product_cap, n_bins + k, prod_S, st);
+                if (rc == WFPG_OK)
+                    rc = product_sample_impl(prod_pdf, prod_S, gp.N, product_cap, n_bins + k, bin_of_ray, Q.nrm,
+                                             Q.u, P, counters + k, p.alpha, dir, pdf, nullptr, st);
+            } else if (p.proposal == 1) {  // learned: MLP tables for the bins' origins, then the mixture
                 if (!mlp) return WFPG_ERR_INVALID_ARG;
                 rc = guide_learned_build_pdf(mlp, Q.pos, Q.nrm, origin_ray, n_bins + k, learned_cap, &lp, tab_pdf,
                                              tab_cr, tab_cm, st);
@@ -479,6 +504,21 @@ struct wfpg_frame {
         }
         WFPG_LAUNCH(k_frame_end, 1, 1, 0, st, F);
         return cudaGetLastError() == cudaSuccess ? WFPG_OK : WFPG_ERR_CUDA;
+    }
+    // tables for the product proposal, allocated outside any capture (kept for the frame's lifetime)
+    bool ensure_product_tables() {
+        if (p.proposal != 2) return true;
+        const uint32_t cap = std::min<uint32_t>(bin_cap, 65536u);
+        if (cap <= product_cap && p.guide.N <= product_n) return true;
+        const size_t NN = (size_t)p.guide.N * p.guide.N;
+        if (!alloc(&prod_pdf, cap * NN) || !alloc(&prod_cr, cap * NN) || !alloc(&prod_cm, (size_t)cap * p.guide.N) ||
+            !alloc(&prod_S, (size_t)cap * 64)) {
+            cudaGetLastError();
+            return false;
+        }
+        product_cap = cap;
+        product_n = p.guide.N;
+        return true;
     }
     int capture(cudaStream_t st) {
         drop_graph();
@@ -519,7 +559,7 @@ static int check_params(const wfpg_frame_params* p, int depth_cap) {
     if (p->guide.split != 0 && p->guide.split != 0xFFFFFFFFu && p->guide.split < 2048)
         return ffail(WFPG_ERR_INVALID_ARG, "frame: guide.split must be 0, >= 2048 or 0xFFFFFFFF");
     if (p->caster < 0 || p->caster > 2) return ffail(WFPG_ERR_INVALID_ARG, "frame: caster must be 0, 1 or 2");
-    if (p->proposal < 0 || p->proposal > 1) return ffail(WFPG_ERR_INVALID_ARG, "frame: proposal must be 0 or 1");
+    if (p->proposal < 0 || p->proposal > 2) return ffail(WFPG_ERR_INVALID_ARG, "frame: proposal must be 0, 1 or 2");
     if (p->proposal == 1 && p->guide.N != 32)
         return ffail(WFPG_ERR_INVALID_ARG, "frame: the learned proposal has N = 32");
     if (p->combine < 0 || p->combine > 5) return ffail(WFPG_ERR_INVALID_ARG, "frame: combine must be 0 .. 5");
@@ -580,6 +620,10 @@ int frame_create(wfpg_svo* svo, const wfpg_scene* scene, const float* emission, 
         delete f;
         cudaGetLastError();
         return ffail(WFPG_ERR_OOM, "frame_create: device allocation failed");
+    }
+    if (!f->ensure_product_tables()) {
+        delete f;
+        return ffail(WFPG_ERR_OOM, "frame_create: device allocation of the product tables failed");
     }
     auto st = static_cast<cudaStream_t>(stream);
     cudaMemsetAsync(f->counters, 0, 4 * (WFPG_FRAME_MAX_DEPTH + 2), st);
@@ -642,7 +686,12 @@ int frame_set_params(wfpg_frame* f, const wfpg_frame_params* p) {
     if (!f) return ffail(WFPG_ERR_INVALID_ARG, "frame_set_params: null frame");
     if (const int rc = check_params(p, f->depth_cap)) return rc;
     f->drop_graph();
+    const wfpg_frame_params old = f->p;
     f->p = *p;
+    if (!f->ensure_product_tables()) {
+        f->p = old;
+        return ffail(WFPG_ERR_OOM, "frame_set_params: device allocation of the product tables failed");
+    }
     return WFPG_OK;
 }
 

@@ -423,3 +423,30 @@ def test_decaying_resolution_per_depth():
     d, pm = W.guide_build_sample(g, qp, qn, r, qu, alpha=0.5, N=16, jitter=True, blur=True, seed=3, frame=1)
     assert torch.equal(f.export("q_dir")[:n], d)
     assert torch.equal(f.export("q_pdf")[:n], pm)
+
+
+def test_frame_product_guiding():
+    """proposal 2 (product guiding, Sec. 3.6): the frame's guiding equals
+    guide_build_pdf + guide_product_sums + guide_product_sample on its queue,
+    and product-guided frames stay unbiased."""
+    w, g, _ = box_svo(15)
+    f = make_frame(g, w.scene, max_depth=1, update=False, N=32, c_ray=128, proposal=2)
+    f.run(1, use_graph=False)
+    n = f.stats()["paths"][0]
+    qp, qn, qu = (f.export(k)[:n].contiguous() for k in ("q_pos", "q_nrm", "q_u"))
+    cap = min(f.pixels, g.n_nodes, 65536)
+    r = W.bin_rays(g, qp, qn, l_min=2, c_ray=128, seed=3, frame=0, bin_cap=cap)
+    tabs = W.guide_build_pdf(g, qp, r["origin_ray"], r["n_bins"], cap, N=32, jitter=True, blur=True, seed=3, frame=0)
+    S = W.guide_product_sums(tabs[0], 32, n_bins=r["n_bins"])
+    d, pm, _ = W.guide_product_sample(tabs[0], S, 32, r["bin_of_ray"], qn, qu, alpha=0.5, n_bins=r["n_bins"])
+    assert torch.equal(f.export("q_dir")[:n], d)
+    assert torch.equal(f.export("q_pdf")[:n], pm)
+    frames, res = 40, {}
+    for alpha in (0.0, 0.5):
+        fr = make_frame(g, w.scene, width=96, height=54, alpha=alpha, max_depth=3, N=32, proposal=2,
+                        seed=31 + int(alpha * 10))
+        fr.run(frames)
+        m, v = fr.image()
+        res[alpha] = (float(m.double().mean()), float(np.sqrt(v.double().sum().item() / frames) / fr.pixels))
+    (mu0, s0), (mu1, s1) = res[0.0], res[0.5]
+    assert abs(mu1 - mu0) < 5 * np.hypot(s0, s1), res
