@@ -468,6 +468,9 @@ typedef struct wfpg_frame_params {
                                  0 constant, 1 linear (min(i, 5)), 2 quadratic (min(i, 5)^2), 3 one-two
                                  (1 then 2), 4 discard first (0 then 1), 5 PT first (frame 1 unguided,
                                  then constant) */
+    int nee;                  /* 1: next-event estimation at every guided vertex (an emissive primitive by
+                                 power, a uniform point on it, a shadow ray), combined with the mixture's
+                                 samples by the power heuristic; Eq. 5 records include it */
 } wfpg_frame_params;
 
 typedef struct wfpg_frame wfpg_frame;
@@ -536,6 +539,11 @@ enum {
     WFPG_FRAME_BUF_Q_DIR = 12,  /* float [W*H][3]: its sampled directions */
     WFPG_FRAME_BUF_Q_PDF = 13,  /* float [W*H]: their mixture densities */
     WFPG_FRAME_BUF_Q_PATH = 14, /* u32 [W*H]: path (pixel) of each queue slot */
+    WFPG_FRAME_BUF_VNEE = 15,   /* float [max_depth+1][W*H]: MIS-weighted light sample per unit T(p_k) (nee) */
+    WFPG_FRAME_BUF_NEE_DIR = 16, /* float [W*H][3]: last depth's light-sample direction per queue slot (nee) */
+    WFPG_FRAME_BUF_NEE_PL = 17,  /* float [W*H]: its light-sampling density (solid angle; 0: none) */
+    WFPG_FRAME_BUF_NEE_PM = 18,  /* float [W*H]: the mixture's density in that direction */
+    WFPG_FRAME_BUF_NEE_L = 19,   /* float [W*H]: f cos Le / p_light of the sample (0: occluded) */
 };
 WFPG_API int frame_export(const wfpg_frame* f, int what, void* dst, size_t bytes, void* stream);
 

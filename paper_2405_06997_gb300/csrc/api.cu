@@ -26,7 +26,8 @@ int guide_fused_impl(const wfpg_svo* s, const float* pos, const float* nrm, cons
                      const uint32_t* n_bins_dev, uint32_t bin_cap, const uint32_t* ray_order,
                      const uint32_t* bin_offset, const float* u, float alpha, const wfpg_guide_params* p, float* dir,
                      float* pdf_out, uint32_t n, void* workspace, size_t ws_bytes, cudaStream_t st,
-                     const uint32_t* frame_dev = nullptr);
+                     const uint32_t* frame_dev = nullptr, const float* eval_dir = nullptr,
+                     float* eval_pdf = nullptr);
 size_t guide_fused_workspace_bytes(int N, uint32_t n, uint32_t split);
 int product_sums_impl(const float* pdf, int N, uint32_t bin_cap, const uint32_t* n_bins_dev, float* S,
                       cudaStream_t st);
@@ -36,7 +37,7 @@ int product_sample_impl(const float* pdf, const float* S, int N, uint32_t bin_ca
                         cudaStream_t st);
 int product_eval_impl(const float* pdf, const float* S, int N, uint32_t bin_cap, const uint32_t* n_bins_dev,
                       const uint32_t* bin, const float* nrm, const float* dir, uint32_t n, float alpha, float* out,
-                      cudaStream_t st);
+                      cudaStream_t st, const uint32_t* n_dev = nullptr);
 int sample_mix_impl(const float* pdf, const float* cdf_row, const float* cdf_marg, int N, uint32_t bin_cap,
                     const uint32_t* n_bins_dev, const uint32_t* bin_of_ray, const float* nrm, const float* u,
                     uint32_t n, const uint32_t* n_dev, float alpha, float* dir, float* pdf_out, cudaStream_t st);

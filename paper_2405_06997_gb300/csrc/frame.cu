@@ -31,7 +31,7 @@ int guide_fused_impl(const wfpg_svo* s, const float* pos, const float* nrm, cons
                      const uint32_t* n_bins_dev, uint32_t bin_cap, const uint32_t* ray_order,
                      const uint32_t* bin_offset, const float* u, float alpha, const wfpg_guide_params* p, float* dir,
                      float* pdf_out, uint32_t n, void* workspace, size_t ws_bytes, cudaStream_t st,
-                     const uint32_t* frame_dev);
+                     const uint32_t* frame_dev, const float* eval_dir, float* eval_pdf);
 size_t guide_fused_workspace_bytes(int N, uint32_t n, uint32_t split);
 int accumulate(wfpg_svo* s, const float* pos, const float* wout, const float* L, uint32_t n, cudaStream_t st,
                const uint32_t* n_dev);
@@ -39,6 +39,12 @@ int sample_mix_impl(const float* pdf, const float* cdf_row, const float* cdf_mar
                     const uint32_t* n_bins_dev, const uint32_t* bin_of_ray, const float* nrm, const float* u,
                     uint32_t n, const uint32_t* n_dev, float alpha, float* dir, float* pdf_out, cudaStream_t st);
 SvoCast svo_cast_view(const wfpg_svo* s);
+int product_eval_impl(const float* pdf, const float* S, int N, uint32_t bin_cap, const uint32_t* n_bins_dev,
+                      const uint32_t* bin, const float* nrm, const float* dir, uint32_t n, float alpha, float* out,
+                      cudaStream_t st, const uint32_t* n_dev);
+int mix_eval_impl(const float* pdf, int N, uint32_t bin_cap, const uint32_t* n_bins_dev, const uint32_t* bin_of_ray,
+                  const float* nrm, const float* dir, uint32_t n, const uint32_t* n_dev, float alpha, float* out,
+                  cudaStream_t st);
 int guide_build_impl(const wfpg_svo* s, const float* pos, const uint32_t* origin_ray, const uint32_t* n_bins_dev,
                      uint32_t bin_cap, const wfpg_guide_params* p, float* pdf, float* cdf_row, float* cdf_marg,
                      cudaStream_t st, const uint32_t* frame_dev);
@@ -51,6 +57,7 @@ int product_sample_impl(const float* pdf, const float* S, int N, uint32_t bin_ca
 uint32_t mlp_max_batch(const wfpg_mlp* m);
 
 constexpr uint64_t kPathPurpose = 2;  // per-path uniforms (0: origins, 1: jitter)
+constexpr uint32_t kPathStride = 8;   // uniforms per depth: direction 0-1, mixture 2, roulette 3, light 4-6
 constexpr uint32_t kDepthStride = 16; // random-stream frame index = frame * 16 + depth
 constexpr float kInvPi = 0.31830988618379067f;
 
@@ -86,6 +93,18 @@ struct FrameView {
     double* img_sum;
     double* img_sq;
     double* img_wsum;  // sum of h(i) x estimate
+    // next-event estimation (0 lights: off)
+    int nee;
+    uint32_t n_lights;
+    const uint32_t* light_prim;   // emissive primitives
+    const float* light_cdf;       // inclusive power CDF over them (last = 1)
+    const float* prim_pmf;        // per primitive: its selection probability (0 if not a light)
+    const float* prim_area;       // per primitive: area
+    float* nee_dir;               // per queue slot: direction to the light sample
+    float* nee_l;                 // per queue slot: f cos Le / p_light (0: no unoccluded sample)
+    float* nee_pl;                // per queue slot: light sample density (solid angle)
+    float* nee_pm;                // per queue slot: the mixture's density at nee_dir
+    float* vNee;                  // per vertex: MIS-weighted light sample per unit T(p_k)
     double* wsum;      // sum of h(i)
     int combine;
     uint32_t* counters;  // [0 .. max_depth - 1]: paths per depth; [WFPG_FRAME_MAX_DEPTH + 1]: records
@@ -127,7 +146,7 @@ __device__ __forceinline__ Hit frame_cast(const FrameView& F, float ox, float oy
 __device__ __forceinline__ bool roulette(const FrameView& F, uint32_t path, int v, float alb, float* T) {
     if (v < F.rr_depth) return true;
     const float q = fminf(0.95f, alb);
-    if (path_uniform(F, path, 4u * (uint32_t)(v - 1) + 3u) >= q) return false;
+    if (path_uniform(F, path, kPathStride * (uint32_t)(v - 1) + 3u) >= q) return false;
     *T = *T / q;
     return true;
 }
@@ -160,7 +179,8 @@ __global__ void __launch_bounds__(256) k_camera(FrameView F, Queue S, uint32_t* 
         const float3 n = hit_normal(F.quads, F.nq, F.spheres, h, F.eye[0], F.eye[1], F.eye[2], dx, dy, dz);
         const float a = F.albedo[h.prim];
         F.vT[i] = 1.0f;
-        F.vLe[i] = F.emission[h.prim];
+        F.vLe[i] = F.emission[h.prim];  // seen by the camera: no other strategy to weigh against
+        if (F.nee) F.vNee[i] = 0.0f;
         store3(F.vpos, i, hx, hy, hz);
         store3(F.vwo, i, -dx, -dy, -dz);
         F.nv[i] = 1;
@@ -189,8 +209,83 @@ __global__ void __launch_bounds__(256) k_compact(FrameView F, Queue S, Queue Q, 
     store3(Q.nrm, j, S.nrm[3 * (size_t)i], S.nrm[3 * (size_t)i + 1], S.nrm[3 * (size_t)i + 2]);
     Q.T[j] = S.T[i];
     Q.alb[j] = S.alb[i];
-    const uint32_t c = 4u * (uint32_t)k;
+    const uint32_t c = kPathStride * (uint32_t)k;
     store3(Q.u, j, path_uniform(F, path, c), path_uniform(F, path, c + 1), path_uniform(F, path, c + 2));
+}
+
+// light-sample density (solid angle) of reaching emissive primitive `prim` at
+// distance t along a direction whose cosine with the light's normal is cl
+__device__ __forceinline__ float light_pdf(const FrameView& F, uint32_t prim, float t, float cl) {
+    const float pmf = F.prim_pmf[prim];
+    if (!(pmf > 0.0f) || !(cl > 0.0f)) return 0.0f;
+    return pmf * t * t / (F.prim_area[prim] * cl);
+}
+
+// geometric normal of a primitive at point (x, y, z) (unnormalised side)
+__device__ __forceinline__ float3 prim_normal(const FrameView& F, uint32_t prim, float x, float y, float z) {
+    if (prim < F.nq) {
+        const float* Q = F.quads + 8 * (size_t)prim;
+        const int a = (int)Q[0];
+        return make_float3(a == 0 ? 1.0f : 0.0f, a == 1 ? 1.0f : 0.0f, a == 2 ? 1.0f : 0.0f);
+    }
+    const float* Sp = F.spheres + 4 * (size_t)(prim - F.nq);
+    return make_float3((x - Sp[0]) / Sp[3], (y - Sp[1]) / Sp[3], (z - Sp[2]) / Sp[3]);
+}
+
+// next-event estimation at the queue's vertices: an emissive primitive by
+// power, a uniform point on it, a shadow ray; Lambertian f cos Le / p_light
+__global__ void __launch_bounds__(256) k_nee(FrameView F, Queue Q, int k) {
+    const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= F.counters[k]) return;
+    const uint32_t path = Q.path[s];
+    const uint32_t c0 = kPathStride * (uint32_t)k + 4u;
+    const float us = path_uniform(F, path, c0), ua = path_uniform(F, path, c0 + 1), ub = path_uniform(F, path, c0 + 2);
+    uint32_t l = F.n_lights - 1;
+    for (uint32_t j = 0; j < F.n_lights; ++j)
+        if (F.light_cdf[j] > us) {
+            l = j;
+            break;
+        }
+    const uint32_t prim = F.light_prim[l];
+    float y[3];
+    if (prim < F.nq) {
+        const float* Qd = F.quads + 8 * (size_t)prim;
+        const int a = (int)Qd[0], b = (a + 1) % 3, c = (a + 2) % 3;
+        y[a] = Qd[1];
+        y[b] = Qd[2] + ua * (Qd[3] - Qd[2]);
+        y[c] = Qd[4] + ub * (Qd[5] - Qd[4]);
+    } else {
+        const float* Sp = F.spheres + 4 * (size_t)(prim - F.nq);
+        const float z = 1.0f - 2.0f * ua, r = sqrtf(fmaxf(0.0f, 1.0f - z * z));
+        float sp, cp;
+        sincospif(2.0f * ub, &sp, &cp);
+        y[0] = Sp[0] + Sp[3] * r * cp;
+        y[1] = Sp[1] + Sp[3] * r * sp;
+        y[2] = Sp[2] + Sp[3] * z;
+    }
+    const float nx = Q.nrm[3 * (size_t)s], ny = Q.nrm[3 * (size_t)s + 1], nz = Q.nrm[3 * (size_t)s + 2];
+    const float ox = Q.pos[3 * (size_t)s] + F.offset * nx;
+    const float oy = Q.pos[3 * (size_t)s + 1] + F.offset * ny;
+    const float oz = Q.pos[3 * (size_t)s + 2] + F.offset * nz;
+    const float ddx = y[0] - ox, ddy = y[1] - oy, ddz = y[2] - oz;
+    const float dist = sqrtf(ddx * ddx + ddy * ddy + ddz * ddz);
+    float L = 0.0f, pl = 0.0f, wx = 0.0f, wy = 0.0f, wz = 1.0f;
+    if (dist > 0.0f) {
+        wx = ddx / dist;
+        wy = ddy / dist;
+        wz = ddz / dist;
+        const float3 nl = prim_normal(F, prim, y[0], y[1], y[2]);
+        pl = light_pdf(F, prim, dist, fabsf(nl.x * wx + nl.y * wy + nl.z * wz));
+        const float cs = nx * wx + ny * wy + nz * wz;
+        if (pl > 0.0f && cs > 0.0f) {
+            const Hit h = frame_cast(F, ox, oy, oz, wx, wy, wz);
+            if (h.prim == prim && fabsf(h.t - dist) <= 1e-3f * dist)
+                L = (Q.alb[s] * kInvPi) * cs * F.emission[prim] / pl;
+        }
+    }
+    store3(F.nee_dir, s, wx, wy, wz);
+    F.nee_l[s] = L;
+    F.nee_pl[s] = pl;
 }
 
 // Lambertian BSDF weight, closest hit (vertex k + 2), emission, roulette
@@ -206,6 +301,13 @@ __global__ void __launch_bounds__(256) k_shade(FrameView F, Queue Q, const float
         const float dx = dir[3 * (size_t)s], dy = dir[3 * (size_t)s + 1], dz = dir[3 * (size_t)s + 2];
         const float p = pdf[s];
         const float cs = nx * dx + ny * dy + nz * dz;
+        if (F.nee) {  // the light sample, weighed against the mixture by the power heuristic
+            const float pl = F.nee_pl[s], pm = F.nee_pm[s];
+            const float w = pl > 0.0f ? pl * pl / (pl * pl + pm * pm) : 0.0f;
+            const size_t vc = (size_t)k * F.P + path;
+            // per unit T(p_k): the continuation's roulette factor Q.T / T(p_k) applies
+            F.vNee[vc] = w * F.nee_l[s] * (Q.T[s] / F.vT[vc]);
+        }
         if (p > 0.0f && cs > 0.0f) {
             float T = Q.T[s] * (Q.alb[s] * kInvPi) * cs / p;
             const float ox = Q.pos[3 * (size_t)s] + F.offset * nx;
@@ -217,7 +319,14 @@ __global__ void __launch_bounds__(256) k_shade(FrameView F, Queue Q, const float
                 const float hx = ox + h.t * dx, hy = oy + h.t * dy, hz = oz + h.t * dz;
                 const float a = F.albedo[h.prim];
                 F.vT[v] = T;
-                F.vLe[v] = F.emission[h.prim];
+                float Le = F.emission[h.prim];
+                if (F.nee && Le > 0.0f) {  // the mixture's sample of a light, weighed against light sampling
+                    const float3 nl = prim_normal(F, h.prim, hx, hy, hz);
+                    const float pl = light_pdf(F, h.prim, h.t, fabsf(nl.x * dx + nl.y * dy + nl.z * dz));
+                    Le = Le * (p * p / (p * p + pl * pl));
+                }
+                F.vLe[v] = Le;
+                if (F.nee) F.vNee[v] = 0.0f;
                 store3(F.vpos, v, hx, hy, hz);
                 store3(F.vwo, v, -dx, -dy, -dz);
                 F.nv[path] = (uint32_t)(k + 2);
@@ -258,7 +367,7 @@ __global__ void __launch_bounds__(256) k_records(FrameView F, float* __restrict_
     for (int v = (int)n - 1; v >= 0; --v) {
         const size_t e = (size_t)v * F.P + i;
         const float T = F.vT[e];
-        S = S + T * F.vLe[e];
+        S = S + T * (F.nee ? F.vLe[e] + F.vNee[e] : F.vLe[e]);
         const uint32_t r = base + (uint32_t)v;
         rec_pos[3 * (size_t)r] = F.vpos[3 * e];
         rec_pos[3 * (size_t)r + 1] = F.vpos[3 * e + 1];
@@ -368,6 +477,16 @@ struct wfpg_frame {
     double* scalar = nullptr;
     wfpg_mlp* mlp = nullptr;
     wfpg_learned_params lp{};
+    uint32_t n_lights = 0;           // emissive primitives (next-event estimation)
+    uint32_t* light_prim = nullptr;
+    float* light_cdf = nullptr;
+    float* prim_pmf = nullptr;
+    float* prim_area = nullptr;
+    float* nee_dir = nullptr;
+    float* nee_l = nullptr;
+    float* nee_pl = nullptr;
+    float* nee_pm = nullptr;
+    float* vNee = nullptr;
     uint32_t product_cap = 0;        // bins per depth the product tables hold
     int product_n = 0;               // grid side they are sized for
     float* prod_pdf = nullptr;       // [product_cap][N^2]
@@ -439,6 +558,17 @@ struct wfpg_frame {
         F.img_wsum = img_wsum;
         F.wsum = wsum;
         F.combine = p.combine;
+        F.nee = p.nee && n_lights > 0;
+        F.n_lights = n_lights;
+        F.light_prim = light_prim;
+        F.light_cdf = light_cdf;
+        F.prim_pmf = prim_pmf;
+        F.prim_area = prim_area;
+        F.nee_dir = nee_dir;
+        F.nee_l = nee_l;
+        F.nee_pl = nee_pl;
+        F.nee_pm = nee_pm;
+        F.vNee = vNee;
         F.counters = counters;
         F.fidx = fidx;
         F.frame_counter = frame_counter;
@@ -460,6 +590,8 @@ struct wfpg_frame {
                 scan_exclusive(flags, offs, P, counters + k, ws, st);
             }
             WFPG_LAUNCH(k_compact, g, T, 0, st, F, stage, Q, flags, offs, k);
+            const bool nee = F.nee != 0;
+            if (nee) WFPG_LAUNCH(k_nee, g, T, 0, st, F, Q, k);
             wfpg_bin_params bp{};
             bp.mode = WFPG_BIN_PARTITION_S;
             bp.l_min = p.l_min;
@@ -479,6 +611,9 @@ struct wfpg_frame {
                 if (rc == WFPG_OK)
                     rc = product_sample_impl(prod_pdf, prod_S, gp.N, product_cap, n_bins + k, bin_of_ray, Q.nrm,
                                              Q.u, P, counters + k, p.alpha, dir, pdf, nullptr, st);
+                if (rc == WFPG_OK && nee)
+                    rc = product_eval_impl(prod_pdf, prod_S, gp.N, product_cap, n_bins + k, bin_of_ray, Q.nrm, nee_dir,
+                                           P, p.alpha, nee_pm, st, counters + k);
             } else if (p.proposal == 1) {  // learned: MLP tables for the bins' origins, then the mixture
                 if (!mlp) return WFPG_ERR_INVALID_ARG;
                 rc = guide_learned_build_pdf(mlp, Q.pos, Q.nrm, origin_ray, n_bins + k, learned_cap, &lp, tab_pdf,
@@ -486,12 +621,16 @@ struct wfpg_frame {
                 if (rc != WFPG_OK) return rc;
                 rc = sample_mix_impl(tab_pdf, tab_cr, tab_cm, 32, learned_cap, n_bins + k, bin_of_ray, Q.nrm, Q.u, P,
                                      counters + k, p.alpha, dir, pdf, st);
+                if (rc == WFPG_OK && nee)
+                    rc = mix_eval_impl(tab_pdf, 32, learned_cap, n_bins + k, bin_of_ray, Q.nrm, nee_dir, P,
+                                       counters + k, p.alpha, nee_pm, st);
             } else {
                 wfpg_guide_params gp = p.guide;
                 gp.seed = p.seed;
                 if (p.decay) gp.N = std::max(8, p.guide.N >> k);
                 rc = guide_fused_impl(svo, Q.pos, Q.nrm, origin_ray, n_bins + k, bin_cap, ray_order, bin_offset,
-                                      Q.u, p.alpha, &gp, dir, pdf, P, guide_ws, guide_ws_bytes, st, fidx + k);
+                                      Q.u, p.alpha, &gp, dir, pdf, P, guide_ws, guide_ws_bytes, st, fidx + k,
+                                      nee ? nee_dir : nullptr, nee ? nee_pm : nullptr);
             }
             if (rc != WFPG_OK) return rc;
             WFPG_LAUNCH(k_shade, g, T, 0, st, F, Q, dir, pdf, stage, flags, k);
@@ -563,6 +702,7 @@ static int check_params(const wfpg_frame_params* p, int depth_cap) {
     if (p->proposal == 1 && p->guide.N != 32)
         return ffail(WFPG_ERR_INVALID_ARG, "frame: the learned proposal has N = 32");
     if (p->combine < 0 || p->combine > 5) return ffail(WFPG_ERR_INVALID_ARG, "frame: combine must be 0 .. 5");
+    if (p->nee != 0 && p->nee != 1) return ffail(WFPG_ERR_INVALID_ARG, "frame: nee must be 0 or 1");
     return WFPG_OK;
 }
 
@@ -624,6 +764,49 @@ int frame_create(wfpg_svo* svo, const wfpg_scene* scene, const float* emission, 
     if (!f->ensure_product_tables()) {
         delete f;
         return ffail(WFPG_ERR_OOM, "frame_create: device allocation of the product tables failed");
+    }
+    // next-event estimation: the emissive primitives, chosen in proportion to emitted power
+    {
+        const uint32_t nq = scene->n_quads, ns = scene->n_spheres, np = nq + ns;
+        std::vector<float> hq(8 * (size_t)nq), hs(4 * (size_t)ns), he(np);
+        bool okc = (nq == 0 || cudaMemcpy(hq.data(), scene->quads, 4 * hq.size(), cudaMemcpyDeviceToHost) == cudaSuccess) &&
+                   (ns == 0 || cudaMemcpy(hs.data(), scene->spheres, 4 * hs.size(), cudaMemcpyDeviceToHost) == cudaSuccess) &&
+                   (np == 0 || cudaMemcpy(he.data(), emission, 4 * he.size(), cudaMemcpyDeviceToHost) == cudaSuccess);
+        std::vector<float> area(np, 0.0f), pmf(np, 0.0f);
+        std::vector<uint32_t> lp;
+        std::vector<double> power;
+        double total = 0.0;
+        for (uint32_t k = 0; okc && k < np; ++k) {
+            area[k] = k < nq ? (hq[8 * k + 3] - hq[8 * k + 2]) * (hq[8 * k + 5] - hq[8 * k + 4])
+                             : 12.566370614359172f * hs[4 * (k - nq) + 3] * hs[4 * (k - nq) + 3];
+            if (he[k] > 0.0f && area[k] > 0.0f) {
+                lp.push_back(k);
+                power.push_back((double)he[k] * area[k]);
+                total += power.back();
+            }
+        }
+        std::vector<float> cdf(lp.size());
+        double acc = 0.0;
+        for (size_t j = 0; j < lp.size(); ++j) {
+            acc += power[j];
+            cdf[j] = j + 1 == lp.size() ? 1.0f : (float)(acc / total);
+            pmf[lp[j]] = (float)(power[j] / total);
+        }
+        f->n_lights = (uint32_t)lp.size();
+        const size_t V2 = (size_t)(p->max_depth + 1) * P;
+        okc = okc && f->alloc(&f->light_prim, std::max<size_t>(1, lp.size())) &&
+              f->alloc(&f->light_cdf, std::max<size_t>(1, lp.size())) && f->alloc(&f->prim_pmf, std::max<uint32_t>(1, np)) &&
+              f->alloc(&f->prim_area, std::max<uint32_t>(1, np)) && f->alloc(&f->nee_dir, 3 * (size_t)P) &&
+              f->alloc(&f->nee_l, P) && f->alloc(&f->nee_pl, P) && f->alloc(&f->nee_pm, P) && f->alloc(&f->vNee, V2);
+        okc = okc && (lp.empty() || (cudaMemcpy(f->light_prim, lp.data(), 4 * lp.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
+                                     cudaMemcpy(f->light_cdf, cdf.data(), 4 * cdf.size(), cudaMemcpyHostToDevice) == cudaSuccess)) &&
+              (np == 0 || (cudaMemcpy(f->prim_pmf, pmf.data(), 4 * (size_t)np, cudaMemcpyHostToDevice) == cudaSuccess &&
+                           cudaMemcpy(f->prim_area, area.data(), 4 * (size_t)np, cudaMemcpyHostToDevice) == cudaSuccess));
+        if (!okc) {
+            delete f;
+            cudaGetLastError();
+            return ffail(WFPG_ERR_OOM, "frame_create: light table setup failed");
+        }
     }
     auto st = static_cast<cudaStream_t>(stream);
     cudaMemsetAsync(f->counters, 0, 4 * (WFPG_FRAME_MAX_DEPTH + 2), st);
@@ -876,6 +1059,11 @@ int frame_export(const wfpg_frame* f, int what, void* dst, size_t bytes, void* s
         case WFPG_FRAME_BUF_Q_DIR: src = f->dir; n = 12 * P; break;
         case WFPG_FRAME_BUF_Q_PDF: src = f->pdf; n = 4 * P; break;
         case WFPG_FRAME_BUF_Q_PATH: src = f->q[last].path; n = 4 * P; break;
+        case WFPG_FRAME_BUF_VNEE: src = f->vNee; n = 4 * V; break;
+        case WFPG_FRAME_BUF_NEE_DIR: src = f->nee_dir; n = 12 * P; break;
+        case WFPG_FRAME_BUF_NEE_PL: src = f->nee_pl; n = 4 * P; break;
+        case WFPG_FRAME_BUF_NEE_PM: src = f->nee_pm; n = 4 * P; break;
+        case WFPG_FRAME_BUF_NEE_L: src = f->nee_l; n = 4 * P; break;
         default: return ffail(WFPG_ERR_INVALID_ARG, "frame_export: unknown buffer");
     }
     if (bytes != n) return ffail(WFPG_ERR_INVALID_ARG, "frame_export: size mismatch");

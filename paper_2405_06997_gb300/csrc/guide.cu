@@ -73,6 +73,8 @@ struct FusedArgs {
     uint32_t* spill_bin;            // bin of each slot
     uint32_t* spill_base;           // first chunk of each slot
     float* spill_tab;               // per slot: field (N^2), row CDFs (N^2), marginal (N)
+    const float* eval_dir;          // optional: a second direction per ray (e.g. a light sample) whose
+    float* eval_pdf;                // mixture density is written here, from the same field
 };
 constexpr int kSpillChunk = 256;  // rays per block-iteration of k_spill_sample
 constexpr unsigned long long kSpillChunkMask = (1ull << 40) - 1;
@@ -144,6 +146,13 @@ __device__ __forceinline__ void sample_ray(const FusedArgs& F, uint32_t ray, con
     F.dir[3 * (size_t)ray + 1] = d.y;
     F.dir[3 * (size_t)ray + 2] = d.z;
     F.pdf[ray] = F.alpha * pg + (1.0f - F.alpha) * cs * 0.31830988618379067f;
+    if (F.eval_dir) {
+        const float3 e = make_float3(F.eval_dir[3 * (size_t)ray], F.eval_dir[3 * (size_t)ray + 1],
+                                     F.eval_dir[3 * (size_t)ray + 2]);
+        const float pe = __fdiv_rn(__fmul_rn(f[octa_cell(e, N)], nn), den);
+        const float ce = fmaxf(0.0f, nx * e.x + ny * e.y + nz * e.z);
+        F.eval_pdf[ray] = F.alpha * pe + (1.0f - F.alpha) * ce * 0.31830988618379067f;
+    }
 }
 
 // rays of the spilled bins, kSpillChunk per block-iteration, tables read from
@@ -874,7 +883,7 @@ int guide_fused_impl(const wfpg_svo* s, const float* pos, const float* nrm, cons
                      const uint32_t* n_bins_dev, uint32_t bin_cap, const uint32_t* ray_order,
                      const uint32_t* bin_offset, const float* u, float alpha, const wfpg_guide_params* p, float* dir,
                      float* pdf_out, uint32_t n, void* workspace, size_t ws_bytes, cudaStream_t st,
-                     const uint32_t* frame_dev) {
+                     const uint32_t* frame_dev, const float* eval_dir, float* eval_pdf) {
     if (bin_cap == 0) return WFPG_OK;
     TraceArgs T;
     GuideArgs G;
@@ -887,6 +896,8 @@ int guide_fused_impl(const wfpg_svo* s, const float* pos, const float* nrm, cons
     F.alpha = alpha;
     F.dir = dir;
     F.pdf = pdf_out;
+    F.eval_dir = eval_dir;
+    F.eval_pdf = eval_pdf;
     F.split = split_of(p);
     if (F.split) {
         const size_t cap = (size_t)n / F.split + 1;
@@ -926,6 +937,36 @@ int guide_sample_impl(const float* pdf, const float* cdf_row, const float* cdf_m
     if (n == 0) return WFPG_OK;
     WFPG_LAUNCH(k_guide_sample, div_up(n, 256), 256, 0, st, pdf, cdf_row, cdf_marg, N, bin_cap, bin_of_ray,
                                                    reinterpret_cast<const float2*>(u), n, dir, pdf_out, cell);
+    return cudaGetLastError() == cudaSuccess ? WFPG_OK : WFPG_ERR_CUDA;
+}
+
+// mixture density alpha * table density + (1 - alpha) * cos+ / pi of given
+// directions (rays < *n_dev; a bin without a table: alpha = 0)
+__global__ void __launch_bounds__(256) k_mix_eval(const float* __restrict__ pdf, int N, uint32_t bin_cap,
+                                                  const uint32_t* __restrict__ n_bins_dev,
+                                                  const uint32_t* __restrict__ bin_of_ray,
+                                                  const float* __restrict__ nrm, const float* __restrict__ dir,
+                                                  uint32_t n_cap, const uint32_t* __restrict__ n_dev, float alpha,
+                                                  float* __restrict__ out) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t n = n_dev ? min(*n_dev, n_cap) : n_cap;
+    if (i >= n) return;
+    const uint32_t nb = n_bins_dev ? min(*n_bins_dev, bin_cap) : bin_cap;
+    const uint32_t b = bin_of_ray[i];
+    const float3 d = make_float3(dir[3 * (size_t)i], dir[3 * (size_t)i + 1], dir[3 * (size_t)i + 2]);
+    const float cs = fmaxf(0.0f, nrm[3 * (size_t)i] * d.x + nrm[3 * (size_t)i + 1] * d.y + nrm[3 * (size_t)i + 2] * d.z);
+    float a = alpha, pg = 0.0f;
+    if (b >= nb) a = 0.0f;
+    else pg = pdf[(size_t)b * N * N + octa_cell(d, N)];
+    out[i] = a * pg + (1.0f - a) * cs * 0.31830988618379067f;
+}
+
+int mix_eval_impl(const float* pdf, int N, uint32_t bin_cap, const uint32_t* n_bins_dev, const uint32_t* bin_of_ray,
+                  const float* nrm, const float* dir, uint32_t n, const uint32_t* n_dev, float alpha, float* out,
+                  cudaStream_t st) {
+    if (n == 0) return WFPG_OK;
+    WFPG_LAUNCH(k_mix_eval, div_up(n, 256), 256, 0, st, pdf, N, bin_cap, n_bins_dev, bin_of_ray, nrm, dir, n, n_dev,
+                alpha, out);
     return cudaGetLastError() == cudaSuccess ? WFPG_OK : WFPG_ERR_CUDA;
 }
 

@@ -177,11 +177,13 @@ __global__ void __launch_bounds__(256) k_product_sample(const float* __restrict_
 __global__ void __launch_bounds__(256) k_product_eval(const float* __restrict__ pdf, const float* __restrict__ S,
                                                       int N, uint32_t bin_cap, const uint32_t* __restrict__ n_bins_dev,
                                                       const uint32_t* __restrict__ bin, const float* __restrict__ nrm,
-                                                      const float* __restrict__ dir, uint32_t n, float alpha,
+                                                      const float* __restrict__ dir, uint32_t n_cap,
+                                                      const uint32_t* __restrict__ n_dev, float alpha,
                                                       float* __restrict__ out) {
     __shared__ float s_dir[192];
     load_block_dirs(s_dir);
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t n = n_dev ? min(*n_dev, n_cap) : n_cap;
     if (i >= n) return;
     const uint32_t nb = n_bins_dev ? min(*n_bins_dev, bin_cap) : bin_cap;
     const float nx = nrm[3 * (size_t)i], ny = nrm[3 * (size_t)i + 1], nz = nrm[3 * (size_t)i + 2];
@@ -220,10 +222,10 @@ int product_sample_impl(const float* pdf, const float* S, int N, uint32_t bin_ca
 
 int product_eval_impl(const float* pdf, const float* S, int N, uint32_t bin_cap, const uint32_t* n_bins_dev,
                       const uint32_t* bin, const float* nrm, const float* dir, uint32_t n, float alpha, float* out,
-                      cudaStream_t st) {
+                      cudaStream_t st, const uint32_t* n_dev) {
     if (n == 0) return WFPG_OK;
-    WFPG_LAUNCH(k_product_eval, div_up(n, 256), 256, 0, st, pdf, S, N, bin_cap, n_bins_dev, bin, nrm, dir, n, alpha,
-                out);
+    WFPG_LAUNCH(k_product_eval, div_up(n, 256), 256, 0, st, pdf, S, N, bin_cap, n_bins_dev, bin, nrm, dir, n, n_dev,
+                alpha, out);
     return cudaGetLastError() == cudaSuccess ? WFPG_OK : WFPG_ERR_CUDA;
 }
 

@@ -75,7 +75,7 @@ class Camera(C.Structure):
 class FrameParams(C.Structure):
     _fields_ = [("max_depth", I32), ("rr_depth", I32), ("alpha", F), ("l_min", I32), ("c_ray", U32),
                 ("guide", GuideParams), ("seed", U64), ("update", I32), ("caster", I32), ("proposal", I32),
-                ("decay", I32), ("combine", I32)]
+                ("decay", I32), ("combine", I32), ("nee", I32)]
 
 
 class FrameStats(C.Structure):
@@ -85,7 +85,8 @@ class FrameStats(C.Structure):
 
 COMBINE = {"constant": 0, "linear": 1, "quadratic": 2, "one-two": 3, "discard-first": 4, "pt-first": 5}
 FRAME_BUF = {"vT": 0, "vLe": 1, "vpos": 2, "vwo": 3, "nv": 4, "rec_pos": 5, "rec_wout": 6, "rec_L": 7,
-             "rec_src": 8, "q_pos": 9, "q_nrm": 10, "q_u": 11, "q_dir": 12, "q_pdf": 13, "q_path": 14}
+             "rec_src": 8, "q_pos": 9, "q_nrm": 10, "q_u": 11, "q_dir": 12, "q_pdf": 13, "q_path": 14, "vNee": 15,
+             "nee_dir": 16, "nee_pl": 17, "nee_pm": 18, "nee_l": 19}
 
 
 def library_path() -> str:
@@ -675,7 +676,7 @@ class Frame:
     def __init__(self, svo: SVO, scene, *, eye, forward=(0.0, 0.0, 1.0), up=(0.0, 1.0, 0.0), vfov=60.0,
                  width=1920, height=1080, max_depth=4, rr_depth=2, alpha=0.5, l_min=2, c_ray=512, N=32,
                  eps=1e-2, jitter=True, blur=True, cos_weight=False, block=0, stage=0, seed=1, update=True,
-                 caster=0, proposal=0, decay=False, combine=0, device="cuda", stream=None):
+                 caster=0, proposal=0, decay=False, combine=0, nee=False, device="cuda", stream=None):
         self.svo = svo
         self._q = torch.as_tensor(np.ascontiguousarray(scene.quads, np.float32).reshape(-1, 8), device=device)
         self._s = torch.as_tensor(np.ascontiguousarray(scene.spheres, np.float32).reshape(-1, 4), device=device)
@@ -692,7 +693,7 @@ class Frame:
                          frame=0, block=block, stage=stage)
         self.params = FrameParams(max_depth=max_depth, rr_depth=rr_depth, alpha=alpha, l_min=l_min, c_ray=c_ray,
                                   guide=gp, seed=seed, update=int(update), caster=caster, proposal=proposal,
-                                  decay=int(decay), combine=combine)
+                                  decay=int(decay), combine=combine, nee=int(nee))
         self.device = device
         h = P()
         _check(lib().frame_create(svo.handle, C.byref(self._scene), _ptr(self._e), _ptr(self._a),
@@ -770,9 +771,10 @@ class Frame:
         """Copy of an internal buffer (see WFPG_FRAME_BUF_* in include/wfpg.h)."""
         P_ = self.pixels
         V = (self.max_depth_cap + 1) * P_
-        shapes = {"vT": (V,), "vLe": (V,), "vpos": (V, 3), "vwo": (V, 3), "nv": (P_,), "rec_pos": (V, 3),
+        shapes = {"vT": (V,), "vLe": (V,), "vNee": (V,), "vpos": (V, 3), "vwo": (V, 3), "nv": (P_,), "rec_pos": (V, 3),
                   "rec_wout": (V, 3), "rec_L": (V,), "rec_src": (V,), "q_pos": (P_, 3), "q_nrm": (P_, 3),
-                  "q_u": (P_, 3), "q_dir": (P_, 3), "q_pdf": (P_,), "q_path": (P_,)}
+                  "q_u": (P_, 3), "q_dir": (P_, 3), "q_pdf": (P_,), "q_path": (P_,), "nee_dir": (P_, 3),
+                  "nee_pl": (P_,), "nee_pm": (P_,), "nee_l": (P_,)}
         ints = ("nv", "rec_src", "q_path")
         t = torch.empty(shapes[what], dtype=torch.int32 if what in ints else torch.float32, device=self.device)
         _check(lib().frame_export(self.handle, FRAME_BUF[what], _ptr(t), t.numel() * 4, _stream(stream)))

@@ -450,3 +450,103 @@ def test_frame_product_guiding():
         res[alpha] = (float(m.double().mean()), float(np.sqrt(v.double().sum().item() / frames) / fr.pixels))
     (mu0, s0), (mu1, s1) = res[0.0], res[0.5]
     assert abs(mu1 - mu0) < 5 * np.hypot(s0, s1), res
+
+
+# ------------------------------------------------- next-event estimation + MIS
+def _frame_mean(g, scene, frames, mlp=None, **kw):
+    f = make_frame(g, scene, width=96, height=54, max_depth=3, **kw)
+    if mlp is not None:
+        f.set_mlp(mlp, scene.lo, scene.size)
+    f.run(frames)
+    m, v = f.image()
+    P = f.pixels
+    return float(m.double().mean()), float(np.sqrt(v.double().sum().item() / frames) / P), float(v.double().mean())
+
+
+def test_nee_records_follow_eq5():
+    """With light sampling the suffix sums of Eq. 5 run over T_k (Le_k + Nee_k):
+    the records equal the oracle's back-propagation of the exported history."""
+    w, g, _ = box_svo(16)
+    f = make_frame(g, w.scene, nee=True)
+    f.run(1, use_graph=False)
+    P, Dm = f.pixels, 4
+    nv = f.export("nv").cpu().numpy()
+    vT = f.export("vT").cpu().numpy().reshape(Dm + 1, P).T
+    vLe = f.export("vLe").cpu().numpy().reshape(Dm + 1, P).T
+    vNee = f.export("vNee").cpu().numpy().reshape(Dm + 1, P).T
+    R = f.stats()["records"]
+    assert R == int(nv.sum()) > 0
+    idx = np.arange(Dm + 1)[None, :] < nv[:, None]
+    assert np.count_nonzero(vNee[idx]) > 0.05 * R      # the light is seen from many vertices
+    assert np.all(vNee[idx] >= 0)
+    # a vertex that ends its path (roulette or the last depth) draws no light sample
+    last = np.take_along_axis(vNee, np.maximum(nv - 1, 0)[:, None], 1)[:, 0]
+    assert np.all(last[(nv == Dm + 1)] == 0)
+    src = u32(f.export("rec_src"))[:R]
+    L = f.export("rec_L").cpu().numpy()[:R]
+    p, k, oL = OF.eq5_records(vT, (vLe.astype(np.float64) + vNee).astype(np.float32), nv)
+    osrc = (k - 1) * P + p
+    order = np.argsort(src)
+    np.testing.assert_array_equal(src[order], np.sort(osrc))
+    np.testing.assert_allclose(L[order], oL[np.argsort(osrc)], rtol=1e-4, atol=1e-6)
+
+
+def test_nee_light_sample_and_mixture_density():
+    """The light sample's direction points at the light, its density is the
+    area-to-solid-angle change of a uniform point on the ceiling quad, and the
+    mixture density there is what guide_build_pdf + guide_eval_pdf give."""
+    w, g, _ = box_svo(17)
+    f = make_frame(g, w.scene, max_depth=1, update=False, N=32, c_ray=128, nee=True)
+    f.run(1, use_graph=False)
+    n = f.stats()["paths"][0]
+    qp, qn = (f.export(k)[:n].contiguous() for k in ("q_pos", "q_nrm"))
+    ed = f.export("nee_dir")[:n].contiguous()
+    pl = f.export("nee_pl")[:n].cpu().numpy()
+    pm = f.export("nee_pm")[:n]
+    nl = f.export("nee_l")[:n].cpu().numpy()
+    torch.testing.assert_close(torch.linalg.norm(ed, dim=1), torch.ones(n, device="cuda"), rtol=0, atol=2e-6)
+    # the mixture density of the light direction from the same field tables
+    r = W.bin_rays(g, qp, qn, l_min=2, c_ray=128, seed=3, frame=0, bin_cap=min(f.pixels, g.n_nodes))
+    pdf, _, _ = W.guide_build_pdf(g, qp, r["origin_ray"], r["n_bins"], min(f.pixels, g.n_nodes), N=32, jitter=True,
+                                  blur=True, seed=3, frame=0)
+    pe = W.guide_eval_pdf(pdf, 32, r["bin_of_ray"], ed)
+    cs = torch.clamp((ed * qn).sum(dim=1), min=0)
+    torch.testing.assert_close(pm, 0.5 * pe + 0.5 * cs / np.pi, rtol=1e-6, atol=1e-7)
+    # light density: the ray from the offset origin meets the light's plane at distance t, cos from its axis
+    quads, em = w.scene.quads, w.scene.emission
+    lights = np.flatnonzero(em[:len(quads)] > 0)
+    assert len(lights) == 1
+    Ql = np.asarray(quads[lights[0]], np.float64)
+    a = int(Ql[0])
+    area = (Ql[3] - Ql[2]) * (Ql[5] - Ql[4])
+    o = qp.cpu().numpy().astype(np.float64) + 1e-4 * w.scene.size * qn.cpu().numpy()
+    e = ed.cpu().numpy().astype(np.float64)
+    t = (Ql[1] - o[:, a]) / e[:, a]
+    ref = t * t / (area * np.abs(e[:, a]))
+    ok = (pl > 0) & (np.abs(e[:, a]) > 1e-2)
+    assert ok.mean() > 0.5
+    np.testing.assert_allclose(pl[ok], ref[ok], rtol=2e-3)
+    # an unoccluded sample above the horizon carries albedo/pi cos Le / p_light
+    vis = nl > 0
+    assert vis.mean() > 0.3
+    alb = w.scene.albedo
+    cosv = (e * qn.cpu().numpy()).sum(1)
+    assert np.all(cosv[vis] > 0)
+    Le = em[lights[0]]
+    kval = nl[vis] * pl[vis] * np.pi / (cosv[vis] * Le)
+    assert np.all((kval > 0) & (kval <= 1 + 1e-4))     # the albedo of the vertex's surface
+    assert np.all(np.min(np.abs(kval[:, None] - alb[None, :]), axis=1) < 1e-3)
+
+
+@pytest.mark.parametrize("proposal", [0, 1, 2])
+def test_nee_frames_are_unbiased_and_less_noisy(proposal):
+    """Light sampling combined with the mixture by the power heuristic leaves the
+    mean image unchanged (against cosine-only frames without it) and lowers its
+    variance in a box lit by a small ceiling light."""
+    w, g, _ = box_svo(18)
+    frames = 40
+    mlp = W.MLP(inputs.mlp_init(5), max_batch=4096) if proposal == 1 else None
+    mu0, s0, v0 = _frame_mean(g, w.scene, frames, alpha=0.0, seed=41)
+    mu1, s1, v1 = _frame_mean(g, w.scene, frames, mlp=mlp, alpha=0.5, seed=43, nee=True, proposal=proposal, N=32)
+    assert abs(mu1 - mu0) < 5 * np.hypot(s0, s1), (mu0, mu1, s0, s1)
+    assert v1 < 0.8 * v0, (v0, v1)
