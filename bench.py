@@ -620,6 +620,22 @@ def batched_section(args, autotune=True):
     ms = a.elapsed_time(b) / args.batched_frames
     st = f.stats()
     m, v = f.image()
+    # the same frames with next-event estimation (power-heuristic MIS against the mixture)
+    f.set_params(nee=1)
+    f.run(3)
+    f.reset_image()
+    torch.cuda.synchronize()
+    a.record()
+    f.run(args.batched_frames)
+    b.record()
+    b.synchronize()
+    ms_nee = a.elapsed_time(b) / args.batched_frames
+    m2, v2 = f.image()
+    var0, var1 = float(v.double().mean()), float(v2.double().mean())
+    nee = {"ms_per_frame": ms_nee, "mean_pixel_variance": var1, "mean_radiance": float(m2.double().mean()),
+           "variance_ratio": var1 / var0, "efficiency_gain": (var0 * ms) / (var1 * ms_nee),
+           "note": "one light sample per guided vertex (light by power, uniform point, shadow ray); "
+                   "efficiency = 1 / (variance x time), against the same frames without it"}
     return {"workload": "closed box (D 6, 100k seed records), camera inside at (0.5, 0.5, 0.05) looking +z, "
                         "vfov 70, 1920x1080, 4 guided bounces, RR from vertex 2 (survival min(0.95, albedo)), "
                         "alpha 0.5 guided / 0.5 cosine, Partition-S l_min 2 c_ray 512, jitter + blur",
@@ -632,7 +648,7 @@ def batched_section(args, autotune=True):
             "graph_kernels_per_frame": st["kernels_per_frame"],
             "gpu_launches": W.kernel_launches() - launches0,
             "mean_pixel_variance": float(v.double().mean()), "mean_radiance": float(m.double().mean()),
-            "status": st["status"], "l2": "working set (path state ~0.6 GB) larger than L2"}
+            "status": st["status"], "l2": "working set (path state ~0.6 GB) larger than L2", "nee": nee}
 
 
 def city_section(args):
