@@ -446,6 +446,14 @@ typedef struct wfpg_camera {
     float up[3];        /* unit, orthogonal to forward */
     float vfov_deg;     /* vertical field of view */
     uint32_t width, height;
+    /* Probe mode (radiance-field validation, Fig. 3): probe_pos != NULL replaces the pinhole.  It
+       points to device float [height][3] probe points (copied at frame_create); pixel (x, y) is
+       cell x of the side-probe_n concentric octahedral grid around point y (width must be
+       probe_n^2) and its primary ray leaves point y in a uniformly random direction inside
+       that cell, redrawn every frame.  The mean image is then the cell-averaged incident
+       radiance at each probe (the cells have equal solid angle).  eye/forward/up/vfov unused. */
+    const float* probe_pos;
+    uint32_t probe_n;   /* 1 .. 1024 in probe mode */
 } wfpg_camera;
 
 typedef struct wfpg_frame_params {
@@ -470,7 +478,9 @@ typedef struct wfpg_frame_params {
                                  then constant) */
     int nee;                  /* 1: next-event estimation at every guided vertex (an emissive primitive by
                                  power, a uniform point on it, a shadow ray), combined with the mixture's
-                                 samples by the power heuristic; Eq. 5 records include it */
+                                 samples by the power heuristic; Eq. 5 records include it, and a
+                                 vertex's own record keeps its full emission while the vertices before
+                                 it receive the MIS-weighted share */
 } wfpg_frame_params;
 
 typedef struct wfpg_frame wfpg_frame;
@@ -544,6 +554,7 @@ enum {
     WFPG_FRAME_BUF_NEE_PL = 17,  /* float [W*H]: its light-sampling density (solid angle; 0: none) */
     WFPG_FRAME_BUF_NEE_PM = 18,  /* float [W*H]: the mixture's density in that direction */
     WFPG_FRAME_BUF_NEE_L = 19,   /* float [W*H]: f cos Le / p_light of the sample (0: occluded) */
+    WFPG_FRAME_BUF_VLW = 20,     /* float [max_depth+1][W*H]: emission as the previous vertex sees it (MIS-weighted) */
 };
 WFPG_API int frame_export(const wfpg_frame* f, int what, void* dst, size_t bytes, void* stream);
 

@@ -56,7 +56,7 @@ def mixture_pdf(p_guided, n, d, alpha):
     return alpha * np.asarray(p_guided, np.float64) + (1.0 - alpha) * cs / np.pi
 
 
-def eq5_records(T, Le, nv):
+def eq5_records(T, Le, nv, Le_seen=None):
     """Radiance records of Eq. 5 for a batch of paths.
 
     T, Le: [paths, depth] throughput T(p_k) and emitted radiance Le(p_k) of
@@ -66,13 +66,20 @@ def eq5_records(T, Le, nv):
     records zero radiance (the exitance is a count-weighted average of the
     records, so zeros keep it an estimate of the mean, not of the mean over
     lit paths only).  Returns (path, k, L) arrays, ordered by path then k
-    (k counted from 1)."""
+    (k counted from 1).
+
+    Le_seen (optional, same shape): the radiance of vertex n as the vertices
+    before it receive it, when it differs from what the vertex itself emits --
+    with light sampling, a light reached by a BSDF/guided sample passes on only
+    its MIS-weighted share, while its own record keeps the full emission:
+    L_k = Le(p_k) + sum over n > k of T(p_n) / T(p_k) * Le_seen(p_n)."""
     T = np.asarray(T, np.float64)
     Le = np.asarray(Le, np.float64)
+    Ls = Le if Le_seen is None else np.asarray(Le_seen, np.float64)
     out_p, out_k, out_L = [], [], []
     for i in range(T.shape[0]):
         for k in range(int(nv[i])):
             out_p.append(i)
             out_k.append(k + 1)
-            out_L.append(sum(T[i, m] / T[i, k] * Le[i, m] for m in range(k, int(nv[i]))))
+            out_L.append(Le[i, k] + sum(T[i, m] / T[i, k] * Ls[i, m] for m in range(k + 1, int(nv[i]))))
     return np.array(out_p, np.int64), np.array(out_k, np.int64), np.array(out_L, np.float64)

@@ -80,6 +80,8 @@ struct FrameView {
     const float* albedo;
     uint32_t P, W, H;
     float eye[3], fwd[3], right[3], up[3];  // right and up scaled by the image-plane half extents
+    const float* probe_pos;                   // probe mode: points [H][3] (null: pinhole)
+    uint32_t probe_n;                         // probe mode: side of the octahedral grid (W = probe_n^2)
     int max_depth, rr_depth;
     uint64_t pseed;
     float offset;  // origin offset along the normal for continuation rays
@@ -105,6 +107,7 @@ struct FrameView {
     float* nee_pl;                // per queue slot: light sample density (solid angle)
     float* nee_pm;                // per queue slot: the mixture's density at nee_dir
     float* vNee;                  // per vertex: MIS-weighted light sample per unit T(p_k)
+    float* vLw;                   // per vertex: its emission as the previous vertex sees it (MIS-weighted)
     double* wsum;      // sum of h(i)
     int combine;
     uint32_t* counters;  // [0 .. max_depth - 1]: paths per depth; [WFPG_FRAME_MAX_DEPTH + 1]: records
@@ -162,25 +165,43 @@ __global__ void __launch_bounds__(256) k_camera(FrameView F, Queue S, uint32_t* 
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= F.P) return;
     const uint32_t x = i % F.W, y = i / F.W;
-    const float px = ((float)x + 0.5f) / (float)F.W * 2.0f - 1.0f;
-    const float py = 1.0f - ((float)y + 0.5f) / (float)F.H * 2.0f;
-    float dx = F.fwd[0] + px * F.right[0] + py * F.up[0];
-    float dy = F.fwd[1] + px * F.right[1] + py * F.up[1];
-    float dz = F.fwd[2] + px * F.right[2] + py * F.up[2];
-    const float inv = 1.0f / sqrtf(dx * dx + dy * dy + dz * dz);
-    dx *= inv;
-    dy *= inv;
-    dz *= inv;
-    const Hit h = frame_cast(F, F.eye[0], F.eye[1], F.eye[2], dx, dy, dz);
+    float ex = F.eye[0], ey = F.eye[1], ez = F.eye[2], dx, dy, dz;
+    if (F.probe_pos) {  // a uniform direction inside octahedral cell x around probe y
+        const uint32_t c0 = kPathStride * WFPG_FRAME_MAX_DEPTH;
+        const float tn = 2.0f / (float)F.probe_n;
+        const float su = ((float)(x % F.probe_n) + path_uniform(F, i, c0)) * tn - 1.0f;
+        const float sv = ((float)(x / F.probe_n) + path_uniform(F, i, c0 + 1)) * tn - 1.0f;
+        const float3 d = octa_to_dir(fminf(su, 1.0f), fminf(sv, 1.0f));
+        dx = d.x;
+        dy = d.y;
+        dz = d.z;
+        ex = F.probe_pos[3 * (size_t)y];
+        ey = F.probe_pos[3 * (size_t)y + 1];
+        ez = F.probe_pos[3 * (size_t)y + 2];
+    } else {
+        const float px = ((float)x + 0.5f) / (float)F.W * 2.0f - 1.0f;
+        const float py = 1.0f - ((float)y + 0.5f) / (float)F.H * 2.0f;
+        dx = F.fwd[0] + px * F.right[0] + py * F.up[0];
+        dy = F.fwd[1] + px * F.right[1] + py * F.up[1];
+        dz = F.fwd[2] + px * F.right[2] + py * F.up[2];
+        const float inv = 1.0f / sqrtf(dx * dx + dy * dy + dz * dz);
+        dx *= inv;
+        dy *= inv;
+        dz *= inv;
+    }
+    const Hit h = frame_cast(F, ex, ey, ez, dx, dy, dz);
     uint32_t flag = 0;
     F.nv[i] = 0;
     if (h.prim != kNone) {
-        const float hx = F.eye[0] + h.t * dx, hy = F.eye[1] + h.t * dy, hz = F.eye[2] + h.t * dz;
-        const float3 n = hit_normal(F.quads, F.nq, F.spheres, h, F.eye[0], F.eye[1], F.eye[2], dx, dy, dz);
+        const float hx = ex + h.t * dx, hy = ey + h.t * dy, hz = ez + h.t * dz;
+        const float3 n = hit_normal(F.quads, F.nq, F.spheres, h, ex, ey, ez, dx, dy, dz);
         const float a = F.albedo[h.prim];
         F.vT[i] = 1.0f;
         F.vLe[i] = F.emission[h.prim];  // seen by the camera: no other strategy to weigh against
-        if (F.nee) F.vNee[i] = 0.0f;
+        if (F.nee) {
+            F.vNee[i] = 0.0f;
+            F.vLw[i] = F.vLe[i];
+        }
         store3(F.vpos, i, hx, hy, hz);
         store3(F.vwo, i, -dx, -dy, -dz);
         F.nv[i] = 1;
@@ -319,14 +340,18 @@ __global__ void __launch_bounds__(256) k_shade(FrameView F, Queue Q, const float
                 const float hx = ox + h.t * dx, hy = oy + h.t * dy, hz = oz + h.t * dz;
                 const float a = F.albedo[h.prim];
                 F.vT[v] = T;
-                float Le = F.emission[h.prim];
-                if (F.nee && Le > 0.0f) {  // the mixture's sample of a light, weighed against light sampling
-                    const float3 nl = prim_normal(F, h.prim, hx, hy, hz);
-                    const float pl = light_pdf(F, h.prim, h.t, fabsf(nl.x * dx + nl.y * dy + nl.z * dz));
-                    Le = Le * (p * p / (p * p + pl * pl));
-                }
+                const float Le = F.emission[h.prim];
                 F.vLe[v] = Le;
-                if (F.nee) F.vNee[v] = 0.0f;
+                if (F.nee) {  // the mixture's sample of a light, weighed against light sampling
+                    float w = 1.0f;
+                    if (Le > 0.0f) {
+                        const float3 nl = prim_normal(F, h.prim, hx, hy, hz);
+                        const float pl = light_pdf(F, h.prim, h.t, fabsf(nl.x * dx + nl.y * dy + nl.z * dz));
+                        w = p * p / (p * p + pl * pl);
+                    }
+                    F.vLw[v] = Le * w;
+                    F.vNee[v] = 0.0f;
+                }
                 store3(F.vpos, v, hx, hy, hz);
                 store3(F.vwo, v, -dx, -dy, -dz);
                 F.nv[path] = (uint32_t)(k + 2);
@@ -363,11 +388,14 @@ __global__ void __launch_bounds__(256) k_records(FrameView F, float* __restrict_
     if (lane == 31) base = atomicAdd(&F.counters[WFPG_FRAME_MAX_DEPTH + 1], incl);
     base = __shfl_sync(0xffffffffu, base, 31) + incl - n;
     if (i >= F.P) return;
-    float S = 0.0f;
+    // S: what the vertices after v contribute, as v sees them; Sv: v's own record (with NEE a
+    // vertex's record holds its full emission, the vertex before it the MIS-weighted share)
+    float S = 0.0f, Sv = 0.0f;
     for (int v = (int)n - 1; v >= 0; --v) {
         const size_t e = (size_t)v * F.P + i;
         const float T = F.vT[e];
-        S = S + T * (F.nee ? F.vLe[e] + F.vNee[e] : F.vLe[e]);
+        Sv = S + T * (F.nee ? F.vLe[e] + F.vNee[e] : F.vLe[e]);
+        S = F.nee ? S + T * (F.vLw[e] + F.vNee[e]) : Sv;
         const uint32_t r = base + (uint32_t)v;
         rec_pos[3 * (size_t)r] = F.vpos[3 * e];
         rec_pos[3 * (size_t)r + 1] = F.vpos[3 * e + 1];
@@ -375,10 +403,10 @@ __global__ void __launch_bounds__(256) k_records(FrameView F, float* __restrict_
         rec_wout[3 * (size_t)r] = F.vwo[3 * e];
         rec_wout[3 * (size_t)r + 1] = F.vwo[3 * e + 1];
         rec_wout[3 * (size_t)r + 2] = F.vwo[3 * e + 2];
-        rec_L[r] = S / T;
+        rec_L[r] = Sv / T;
         rec_src[r] = (uint32_t)e;
     }
-    const double L = (double)S;
+    const double L = (double)Sv;
     F.img_sum[i] += L;
     F.img_sq[i] += L * L;
     F.img_wsum[i] += combine_weight(F.combine, *F.frames_run + 1ull) * L;
@@ -477,6 +505,7 @@ struct wfpg_frame {
     double* scalar = nullptr;
     wfpg_mlp* mlp = nullptr;
     wfpg_learned_params lp{};
+    float* probe_pos = nullptr;      // probe mode: the frame's copy of the probe points
     uint32_t n_lights = 0;           // emissive primitives (next-event estimation)
     uint32_t* light_prim = nullptr;
     float* light_cdf = nullptr;
@@ -487,6 +516,7 @@ struct wfpg_frame {
     float* nee_pl = nullptr;
     float* nee_pm = nullptr;
     float* vNee = nullptr;
+    float* vLw = nullptr;
     uint32_t product_cap = 0;        // bins per depth the product tables hold
     int product_n = 0;               // grid side they are sized for
     float* prod_pdf = nullptr;       // [product_cap][N^2]
@@ -542,6 +572,8 @@ struct wfpg_frame {
             F.right[a] = r[a] * th * aspect;
             F.up[a] = u[a] * th;
         }
+        F.probe_pos = probe_pos;
+        F.probe_n = cam.probe_n;
         F.max_depth = p.max_depth;
         F.rr_depth = p.rr_depth;
         F.pseed = purpose(p.seed, kPathPurpose);
@@ -569,6 +601,7 @@ struct wfpg_frame {
         F.nee_pl = nee_pl;
         F.nee_pm = nee_pm;
         F.vNee = vNee;
+        F.vLw = vLw;
         F.counters = counters;
         F.fidx = fidx;
         F.frame_counter = frame_counter;
@@ -717,8 +750,10 @@ int frame_create(wfpg_svo* svo, const wfpg_scene* scene, const float* emission, 
     if (cam->width == 0 || cam->height == 0 ||
         (uint64_t)cam->width * cam->height * (uint64_t)(WFPG_FRAME_MAX_DEPTH + 1) > 0xFFFFFFFFull)
         return ffail(WFPG_ERR_INVALID_ARG, "frame_create: image size out of range");
-    if (!(cam->vfov_deg > 0.0f && cam->vfov_deg < 180.0f))
+    if (!cam->probe_pos && !(cam->vfov_deg > 0.0f && cam->vfov_deg < 180.0f))
         return ffail(WFPG_ERR_INVALID_ARG, "frame_create: vfov_deg must be in (0, 180)");
+    if (cam->probe_pos && (cam->probe_n == 0 || cam->probe_n > 1024 || cam->width != cam->probe_n * cam->probe_n))
+        return ffail(WFPG_ERR_INVALID_ARG, "frame_create: probe mode needs 1 <= probe_n <= 1024 and width = probe_n^2");
     if (const int rc = check_params(p, 0)) return rc;
     auto* f = new wfpg_frame();
     f->svo = svo;
@@ -765,6 +800,14 @@ int frame_create(wfpg_svo* svo, const wfpg_scene* scene, const float* emission, 
         delete f;
         return ffail(WFPG_ERR_OOM, "frame_create: device allocation of the product tables failed");
     }
+    if (cam->probe_pos) {
+        if (!f->alloc(&f->probe_pos, 3 * (size_t)cam->height) ||
+            cudaMemcpy(f->probe_pos, cam->probe_pos, 12 * (size_t)cam->height, cudaMemcpyDeviceToDevice) != cudaSuccess) {
+            delete f;
+            cudaGetLastError();
+            return ffail(WFPG_ERR_INVALID_ARG, "frame_create: probe points could not be copied");
+        }
+    }
     // next-event estimation: the emissive primitives, chosen in proportion to emitted power
     {
         const uint32_t nq = scene->n_quads, ns = scene->n_spheres, np = nq + ns;
@@ -797,7 +840,8 @@ int frame_create(wfpg_svo* svo, const wfpg_scene* scene, const float* emission, 
         okc = okc && f->alloc(&f->light_prim, std::max<size_t>(1, lp.size())) &&
               f->alloc(&f->light_cdf, std::max<size_t>(1, lp.size())) && f->alloc(&f->prim_pmf, std::max<uint32_t>(1, np)) &&
               f->alloc(&f->prim_area, std::max<uint32_t>(1, np)) && f->alloc(&f->nee_dir, 3 * (size_t)P) &&
-              f->alloc(&f->nee_l, P) && f->alloc(&f->nee_pl, P) && f->alloc(&f->nee_pm, P) && f->alloc(&f->vNee, V2);
+              f->alloc(&f->nee_l, P) && f->alloc(&f->nee_pl, P) && f->alloc(&f->nee_pm, P) && f->alloc(&f->vNee, V2) &&
+              f->alloc(&f->vLw, V2);
         okc = okc && (lp.empty() || (cudaMemcpy(f->light_prim, lp.data(), 4 * lp.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
                                      cudaMemcpy(f->light_cdf, cdf.data(), 4 * cdf.size(), cudaMemcpyHostToDevice) == cudaSuccess)) &&
               (np == 0 || (cudaMemcpy(f->prim_pmf, pmf.data(), 4 * (size_t)np, cudaMemcpyHostToDevice) == cudaSuccess &&
@@ -1064,6 +1108,7 @@ int frame_export(const wfpg_frame* f, int what, void* dst, size_t bytes, void* s
         case WFPG_FRAME_BUF_NEE_PL: src = f->nee_pl; n = 4 * P; break;
         case WFPG_FRAME_BUF_NEE_PM: src = f->nee_pm; n = 4 * P; break;
         case WFPG_FRAME_BUF_NEE_L: src = f->nee_l; n = 4 * P; break;
+        case WFPG_FRAME_BUF_VLW: src = f->vLw; n = 4 * V; break;
         default: return ffail(WFPG_ERR_INVALID_ARG, "frame_export: unknown buffer");
     }
     if (bytes != n) return ffail(WFPG_ERR_INVALID_ARG, "frame_export: size mismatch");

@@ -69,7 +69,7 @@ FRAME_MAX_DEPTH = 8
 
 class Camera(C.Structure):
     _fields_ = [("eye", F * 3), ("forward", F * 3), ("up", F * 3), ("vfov_deg", F), ("width", U32),
-                ("height", U32)]
+                ("height", U32), ("probe_pos", C.c_void_p), ("probe_n", U32)]
 
 
 class FrameParams(C.Structure):
@@ -86,7 +86,7 @@ class FrameStats(C.Structure):
 COMBINE = {"constant": 0, "linear": 1, "quadratic": 2, "one-two": 3, "discard-first": 4, "pt-first": 5}
 FRAME_BUF = {"vT": 0, "vLe": 1, "vpos": 2, "vwo": 3, "nv": 4, "rec_pos": 5, "rec_wout": 6, "rec_L": 7,
              "rec_src": 8, "q_pos": 9, "q_nrm": 10, "q_u": 11, "q_dir": 12, "q_pdf": 13, "q_path": 14, "vNee": 15,
-             "nee_dir": 16, "nee_pl": 17, "nee_pm": 18, "nee_l": 19}
+             "nee_dir": 16, "nee_pl": 17, "nee_pm": 18, "nee_l": 19, "vLw": 20}
 
 
 def library_path() -> str:
@@ -670,13 +670,17 @@ class Frame:
 
     scene: paper_2405_06997_gb300.inputs.Scene (uploaded here); the SVO must
     outlive the frame.  Camera: eye, unit forward and up, vertical fov,
-    width x height.  All work runs in libwfpg.so; run(use_graph=True)
+    width x height; or, with probes (float [n][3] points) and probe_n, one
+    image row per probe point whose pixels are the probe_n^2 octahedral cells
+    around it (a uniform direction in the cell per frame: the mean image is the
+    cell-averaged incident radiance).  All work runs in libwfpg.so; run(use_graph=True)
     replays one captured CUDA graph per frame."""
 
     def __init__(self, svo: SVO, scene, *, eye, forward=(0.0, 0.0, 1.0), up=(0.0, 1.0, 0.0), vfov=60.0,
                  width=1920, height=1080, max_depth=4, rr_depth=2, alpha=0.5, l_min=2, c_ray=512, N=32,
                  eps=1e-2, jitter=True, blur=True, cos_weight=False, block=0, stage=0, seed=1, update=True,
-                 caster=0, proposal=0, decay=False, combine=0, nee=False, device="cuda", stream=None):
+                 caster=0, proposal=0, decay=False, combine=0, nee=False, probes=None, probe_n=0, device="cuda",
+                 stream=None):
         self.svo = svo
         self._q = torch.as_tensor(np.ascontiguousarray(scene.quads, np.float32).reshape(-1, 8), device=device)
         self._s = torch.as_tensor(np.ascontiguousarray(scene.spheres, np.float32).reshape(-1, 4), device=device)
@@ -686,8 +690,14 @@ class Frame:
                             n_spheres=self._s.shape[0], lo=(F * 3)(*[float(v) for v in scene.lo]),
                             size=float(scene.size))
         self.width, self.height = int(width), int(height)
+        self._probes = None
+        if probes is not None:  # probe mode: one row of probe_n^2 octahedral cells per point
+            self._probes = torch.as_tensor(probes, dtype=torch.float32, device=device).reshape(-1, 3).contiguous()
+            self.width, self.height = int(probe_n) ** 2, self._probes.shape[0]
         self.cam = Camera(eye=(F * 3)(*eye), forward=(F * 3)(*forward), up=(F * 3)(*up), vfov_deg=vfov,
-                          width=self.width, height=self.height)
+                          width=self.width, height=self.height,
+                          probe_pos=_ptr(self._probes) if self._probes is not None else None,
+                          probe_n=int(probe_n) if probes is not None else 0)
         gp = GuideParams(N=N, eps=eps, jitter=int(jitter), blur=int(blur),
                          t_skip=default_t_skip(svo.size, svo.depth), cos_weight=int(cos_weight), seed=seed,
                          frame=0, block=block, stage=stage)
@@ -771,7 +781,7 @@ class Frame:
         """Copy of an internal buffer (see WFPG_FRAME_BUF_* in include/wfpg.h)."""
         P_ = self.pixels
         V = (self.max_depth_cap + 1) * P_
-        shapes = {"vT": (V,), "vLe": (V,), "vNee": (V,), "vpos": (V, 3), "vwo": (V, 3), "nv": (P_,), "rec_pos": (V, 3),
+        shapes = {"vT": (V,), "vLe": (V,), "vNee": (V,), "vLw": (V,), "vpos": (V, 3), "vwo": (V, 3), "nv": (P_,), "rec_pos": (V, 3),
                   "rec_wout": (V, 3), "rec_L": (V,), "rec_src": (V,), "q_pos": (P_, 3), "q_nrm": (P_, 3),
                   "q_u": (P_, 3), "q_dir": (P_, 3), "q_pdf": (P_,), "q_path": (P_,), "nee_dir": (P_, 3),
                   "nee_pl": (P_,), "nee_pm": (P_,), "nee_l": (P_,)}

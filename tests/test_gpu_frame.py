@@ -474,6 +474,7 @@ def test_nee_records_follow_eq5():
     vT = f.export("vT").cpu().numpy().reshape(Dm + 1, P).T
     vLe = f.export("vLe").cpu().numpy().reshape(Dm + 1, P).T
     vNee = f.export("vNee").cpu().numpy().reshape(Dm + 1, P).T
+    vLw = f.export("vLw").cpu().numpy().reshape(Dm + 1, P).T
     R = f.stats()["records"]
     assert R == int(nv.sum()) > 0
     idx = np.arange(Dm + 1)[None, :] < nv[:, None]
@@ -484,7 +485,11 @@ def test_nee_records_follow_eq5():
     assert np.all(last[(nv == Dm + 1)] == 0)
     src = u32(f.export("rec_src"))[:R]
     L = f.export("rec_L").cpu().numpy()[:R]
-    p, k, oL = OF.eq5_records(vT, (vLe.astype(np.float64) + vNee).astype(np.float32), nv)
+    # lights reached by the mixture pass on their MIS-weighted emission, and keep the full one
+    hitl = idx & (vLe > 0)
+    hitl[:, 0] = False
+    assert np.all(vLw[hitl] <= vLe[hitl]) and np.any(vLw[hitl] < vLe[hitl])
+    p, k, oL = OF.eq5_records(vT, vLe.astype(np.float64) + vNee, nv, Le_seen=vLw.astype(np.float64) + vNee)
     osrc = (k - 1) * P + p
     order = np.argsort(src)
     np.testing.assert_array_equal(src[order], np.sort(osrc))

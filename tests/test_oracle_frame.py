@@ -104,3 +104,20 @@ def test_eq5_first_record_is_path_estimate():
         if p[j] == p[j + 1] and k[j + 1] == k[j] + 1:
             i, kk = p[j], k[j] - 1
             np.testing.assert_allclose(L[j], Le[i, kk] + T[i, kk + 1] / T[i, kk] * L[j + 1], rtol=1e-12)
+
+
+def test_eq5_with_light_sampling_hand_path():
+    """With light sampling a light reached by the mixture passes on only its
+    MIS-weighted share w Le to the vertices before it, and keeps its full
+    emission in its own record; light samples Nee_k add at their vertex."""
+    T = np.array([[1.0, 0.5, 0.25]])
+    Le = np.array([[0.0, 0.0, 8.0]])
+    w = 0.25
+    nee = np.array([[0.5, 2.0, 0.0]])
+    p, k, L = OF.eq5_records(T, Le + nee, [3], Le_seen=np.array([[0.0, 0.0, w * 8.0]]) + nee)
+    # L_3 = 8; L_2 = 2 + (0.25 / 0.5) * 2 = 3; L_1 = 0.5 + 0.5 * 2 + 0.25 * 2 = 2
+    np.testing.assert_allclose(L, [2.0, 3.0, 8.0])
+    # without a separate seen radiance it is the plain suffix sum
+    p2, k2, L2 = OF.eq5_records(T, Le + nee, [3], Le_seen=Le + nee)
+    np.testing.assert_allclose(L2, OF.eq5_records(T, Le + nee, [3])[2], rtol=1e-15)
+    np.testing.assert_allclose(L2, [0.5 + 1.0 + 2.0, 2.0 + 4.0, 8.0])
