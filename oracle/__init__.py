@@ -60,7 +60,7 @@ SZ = C.c_size_t
 
 def _declare(L):
     sig = {
-        "orc_svo_build": (P, [P, I32, P, I32, P, F, I32]),
+        "orc_svo_build": (P, [P, I32, P, I32, P, I32, P, F, I32]),
         "orc_svo_free": (None, [P]),
         "orc_svo_num_nodes": (U32, [P]),
         "orc_svo_level_off": (None, [P, P]),
@@ -122,9 +122,11 @@ class SVO:
         self.D = int(depth)
         self._q = _c(scene.quads, np.float32).reshape(-1, 8)
         self._s = _c(scene.spheres, np.float32).reshape(-1, 4)
+        tris = getattr(scene, "tris", None)
+        self._t = _c(np.zeros((0, 9), np.float32) if tris is None else tris, np.float32).reshape(-1, 9)
         self.lo = _c(scene.lo, np.float32)
         self.S = float(scene.size)
-        h = lib().orc_svo_build(_p(self._q), len(self._q), _p(self._s), len(self._s),
+        h = lib().orc_svo_build(_p(self._q), len(self._q), _p(self._s), len(self._s), _p(self._t), len(self._t),
                                 _p(self.lo), self.S, self.D)
         if not h:
             raise ValueError("scene occupies no voxel")

@@ -31,9 +31,9 @@ using namespace orc;
 
 extern "C" {
 
-void* orc_svo_build(const float* quads, int nq, const float* spheres, int ns, const float* lo,
-                    float S, int D) {
-    return build_svo(quads, nq, spheres, ns, lo, S, D);
+void* orc_svo_build(const float* quads, int nq, const float* spheres, int ns, const float* tris, int nt,
+                    const float* lo, float S, int D) {
+    return build_svo(quads, nq, spheres, ns, tris, nt, lo, S, D);
 }
 void orc_svo_free(void* s) { delete static_cast<Svo*>(s); }
 uint32_t orc_svo_num_nodes(const void* s) { return static_cast<const Svo*>(s)->num_nodes(); }

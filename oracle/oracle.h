@@ -21,8 +21,8 @@ extern "C" {
 
 /* SVO build (Sec. 3.2): conservative voxelisation, Morton sort, hierarchy,
  * k-means normals.  NULL if the scene occupies no voxel. */
-void* orc_svo_build(const float* quads, int nq, const float* spheres, int ns, const float* lo,
-                    float S, int D);
+void* orc_svo_build(const float* quads, int nq, const float* spheres, int ns, const float* tris, int nt,
+                    const float* lo, float S, int D);
 void orc_svo_free(void* svo);
 uint32_t orc_svo_num_nodes(const void* svo);
 void orc_svo_level_off(const void* svo, uint32_t* out /* D + 2 */);

@@ -120,8 +120,8 @@ struct Svo {
     uint32_t deepest(const float p[3]) const;
 };
 
-Svo* build_svo(const float* quads, int nq, const float* spheres, int ns, const float lo[3],
-               float S, int D);
+Svo* build_svo(const float* quads, int nq, const float* spheres, int ns, const float* tris, int nt,
+               const float lo[3], float S, int D);
 
 // k-means with k = 2 over weighted unit vectors (Sec. 3.2, Fig. 2)
 void kmeans2(const float* n, const float* w, int m, float out[3]);

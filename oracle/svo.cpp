@@ -2,8 +2,8 @@
 //
 // SVO construction and radiant-exitance caching, Sec. 3.2 of the paper:
 //  * conservative voxelisation of the scene (the paper rasterises triangles,
-//    after Crassin & Green 2012; here the primitives are analytic quads and
-//    spheres tested against closed voxel boxes),
+//    after Crassin & Green 2012; here analytic quads and spheres, and
+//    triangles by the separating-axis test, against closed voxel boxes),
 //  * Morton-key sort and a level-by-level unique-prefix hierarchy (the paper
 //    builds it after Karras 2012; the set of octree nodes is the same),
 //  * two normals per node from k-means with k = 2 (Fig. 2),
@@ -96,10 +96,50 @@ struct Frag {
     }
 };
 
+double dot3(const double a[3], const double b[3]) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+
+// Triangle / closed box overlap by the separating axis theorem (Akenine-Moller
+// 2001): the two convex sets are disjoint iff their projections are disjoint on
+// one of 13 axes -- the box's three face normals, the triangle's normal, and
+// the nine cross products of a box axis with a triangle edge.  Box-centred
+// coordinates, binary64, one rounding per written operation; touching counts
+// as overlap.
+bool tri_box_overlap(const float* T, const double c[3], double e) {
+    double v[3][3];
+    for (int i = 0; i < 3; ++i)
+        for (int a = 0; a < 3; ++a) v[i][a] = (double)T[3 * i + a] - c[a];
+    for (int a = 0; a < 3; ++a) {  // face normals: the triangle's bounding interval against [-e, e]
+        double mn = std::min(v[0][a], std::min(v[1][a], v[2][a]));
+        double mx = std::max(v[0][a], std::max(v[1][a], v[2][a]));
+        if (mn > e || mx < -e) return false;
+    }
+    double f[3][3];  // edges v1 - v0, v2 - v1, v0 - v2
+    for (int i = 0; i < 3; ++i)
+        for (int a = 0; a < 3; ++a) f[i][a] = v[(i + 1) % 3][a] - v[i][a];
+    for (int i = 0; i < 3; ++i) {
+        for (int k = 0; k < 3; ++k) {  // axis e_k x f_i
+            double ax[3];
+            ax[k] = 0.0;
+            ax[(k + 1) % 3] = -f[i][(k + 2) % 3];
+            ax[(k + 2) % 3] = f[i][(k + 1) % 3];
+            double p0 = dot3(ax, v[0]), p1 = dot3(ax, v[1]), p2 = dot3(ax, v[2]);
+            double r = e * (std::fabs(ax[0]) + std::fabs(ax[1]) + std::fabs(ax[2]));
+            double mn = std::min(p0, std::min(p1, p2)), mx = std::max(p0, std::max(p1, p2));
+            if (mn > r || mx < -r) return false;
+        }
+    }
+    // the triangle's plane
+    double n[3] = {f[0][1] * f[1][2] - f[0][2] * f[1][1], f[0][2] * f[1][0] - f[0][0] * f[1][2],
+                   f[0][0] * f[1][1] - f[0][1] * f[1][0]};
+    double d = dot3(n, v[0]);
+    double r = e * (std::fabs(n[0]) + std::fabs(n[1]) + std::fabs(n[2]));
+    return !(d > r || d < -r);
+}
+
 // Conservative voxelisation: a voxel is occupied when the primitive's surface
 // meets the closed voxel box.
-void voxelize(const float* quads, int nq, const float* spheres, int ns, const float lo[3],
-              float S, int D, std::vector<Frag>& out) {
+void voxelize(const float* quads, int nq, const float* spheres, int ns, const float* tris, int nt,
+              const float lo[3], float S, int D, std::vector<Frag>& out) {
     const float scale = (float)(1 << D) / S;
     for (int q = 0; q < nq; ++q) {
         const float* Q = quads + 8 * q;
@@ -147,13 +187,56 @@ void voxelize(const float* quads, int nq, const float* spheres, int ns, const fl
                                        (uint32_t)(nq + s)});
                 }
     }
+    // triangles: every voxel of the vertices' bounding box widened by one, by the SAT test
+    for (int t = 0; t < nt; ++t) {
+        const float* T = tris + 9 * t;
+        int lo_i[3], hi_i[3];
+        for (int a = 0; a < 3; ++a) {
+            double mn = std::min((double)T[a], std::min((double)T[3 + a], (double)T[6 + a]));
+            double mx = std::max((double)T[a], std::max((double)T[3 + a], (double)T[6 + a]));
+            lo_i[a] = (int)std::max(0.0, std::floor((mn - (double)lo[a]) / h) - 1.0);
+            hi_i[a] = (int)std::min((double)(res - 1), std::floor((mx - (double)lo[a]) / h) + 1.0);
+        }
+        for (int iz = lo_i[2]; iz <= hi_i[2]; ++iz)
+            for (int iy = lo_i[1]; iy <= hi_i[1]; ++iy)
+                for (int ix = lo_i[0]; ix <= hi_i[0]; ++ix) {
+                    int idx[3] = {ix, iy, iz};
+                    double c[3];
+                    for (int a = 0; a < 3; ++a) c[a] = (double)lo[a] + ((double)idx[a] + 0.5) * h;
+                    if (tri_box_overlap(T, c, h * 0.5))
+                        out.push_back({morton((uint32_t)ix, (uint32_t)iy, (uint32_t)iz),
+                                       (uint32_t)(nq + ns + t)});
+                }
+    }
 }
 
 // analytic normal of primitive `prim` for the fragment in leaf (ix, iy, iz):
 // quads use their stored normal, spheres the direction from the centre to the
-// voxel centre (the normal at the surface point nearest the voxel centre)
-void frag_normal(const float* quads, int nq, const float* spheres, const Svo& s, uint32_t prim,
-                 uint64_t key, float out[3]) {
+// voxel centre (the normal at the surface point nearest the voxel centre),
+// triangles their geometric normal (v1 - v0) x (v2 - v0), normalised
+void frag_normal(const float* quads, int nq, const float* spheres, int ns, const float* tris, const Svo& s,
+                 uint32_t prim, uint64_t key, float out[3]) {
+    if ((int)prim >= nq + ns) {
+        const float* T = tris + 9 * (prim - nq - ns);
+        float e1[3], e2[3];
+        for (int a = 0; a < 3; ++a) {
+            e1[a] = T[3 + a] - T[a];
+            e2[a] = T[6 + a] - T[a];
+        }
+        float n[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+        float len2 = n[0] * n[0] + n[1] * n[1] + n[2] * n[2];
+        if (len2 > 0) {
+            float len = std::sqrt(len2);
+            out[0] = n[0] / len;
+            out[1] = n[1] / len;
+            out[2] = n[2] / len;
+        } else {
+            out[0] = 0.0f;
+            out[1] = 1.0f;
+            out[2] = 0.0f;
+        }
+        return;
+    }
     if ((int)prim < nq) {
         const float* Q = quads + 8 * prim;
         int a = (int)Q[0];
@@ -185,10 +268,10 @@ void frag_normal(const float* quads, int nq, const float* spheres, const Svo& s,
 
 }  // namespace
 
-Svo* build_svo(const float* quads, int nq, const float* spheres, int ns, const float lo[3],
-               float S, int D) {
+Svo* build_svo(const float* quads, int nq, const float* spheres, int ns, const float* tris, int nt,
+               const float lo[3], float S, int D) {
     std::vector<Frag> frags;
-    voxelize(quads, nq, spheres, ns, lo, S, D, frags);
+    voxelize(quads, nq, spheres, ns, tris, nt, lo, S, D, frags);
     if (frags.empty()) return nullptr;
     std::sort(frags.begin(), frags.end());
 
@@ -240,7 +323,7 @@ Svo* build_svo(const float* quads, int nq, const float* spheres, int ns, const f
         fn.assign(3 * (e - b), 0.0f);
         fw.assign(e - b, 1.0f);
         for (uint32_t f = b; f < e; ++f)
-            frag_normal(quads, nq, spheres, *s, s->frag_prim[f], s->keys[D][j], &fn[3 * (f - b)]);
+            frag_normal(quads, nq, spheres, ns, tris, *s, s->frag_prim[f], s->keys[D][j], &fn[3 * (f - b)]);
         kmeans2(fn.data(), fw.data(), (int)(e - b), &s->normal[3 * (size_t)node]);
         s->leaf_count[node] = 1;
     }

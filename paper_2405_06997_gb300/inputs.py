@@ -41,6 +41,8 @@ class Scene:
     size: float                       # side S of the cubic AABB
     name: str = ""
     extra: dict = field(default_factory=dict)
+    # float32 [nt, 9]: v0, v1, v2; primitive ids count quads, then spheres, then triangles
+    tris: np.ndarray = field(default_factory=lambda: np.zeros((0, 9), np.float32))
 
     @property
     def n_quads(self) -> int:
@@ -49,6 +51,10 @@ class Scene:
     @property
     def n_spheres(self) -> int:
         return int(self.spheres.shape[0])
+
+    @property
+    def n_tris(self) -> int:
+        return int(self.tris.shape[0])
 
 
 def _quad(axis, plane, lo1, hi1, lo2, hi2, nsign):
@@ -201,6 +207,132 @@ def cosine_dirs(normals: np.ndarray, rng) -> np.ndarray:
     t, bt = _frame(n)
     d = t * x[:, None] + bt * y[:, None] + n * z[:, None]
     return d / np.linalg.norm(d, axis=1, keepdims=True)
+
+
+# --------------------------------------------------------------------------------------
+# triangle meshes (the paper voxelises triangle scenes; these are procedural stand-ins)
+
+def _box_tris():
+    """The six walls of the unit cube as 12 triangles, (v1 - v0) x (v2 - v0) inward."""
+    out = []
+    for ax in range(3):
+        a1, a2 = (ax + 1) % 3, (ax + 2) % 3
+        for plane, sgn in ((0.0, +1.0), (1.0, -1.0)):
+            c = np.zeros((4, 3))
+            c[:, ax] = plane
+            c[:, a1] = [0, 1, 1, 0]
+            c[:, a2] = [0, 0, 1, 1]
+            for t in ((0, 1, 2), (0, 2, 3)):
+                v = c[list(t)]
+                n = np.cross(v[1] - v[0], v[2] - v[0])
+                if n[ax] * sgn < 0:
+                    v = v[[0, 2, 1]]
+                out.append(v.ravel())
+    return np.array(out)
+
+
+def _icosphere(center, radius, subdiv, rng=None, bump=0.0):
+    """Subdivided icosahedron, outward winding; bump > 0 displaces the vertices
+    radially by a seeded factor U[1 - bump, 1 + bump] (a rock)."""
+    t = (1.0 + 5 ** 0.5) / 2.0
+    V = [[-1, t, 0], [1, t, 0], [-1, -t, 0], [1, -t, 0], [0, -1, t], [0, 1, t], [0, -1, -t], [0, 1, -t],
+         [t, 0, -1], [t, 0, 1], [-t, 0, -1], [-t, 0, 1]]
+    V = [list(np.array(v) / np.linalg.norm(v)) for v in V]
+    F = [(0, 11, 5), (0, 5, 1), (0, 1, 7), (0, 7, 10), (0, 10, 11), (1, 5, 9), (5, 11, 4), (11, 10, 2),
+         (10, 7, 6), (7, 1, 8), (3, 9, 4), (3, 4, 2), (3, 2, 6), (3, 6, 8), (3, 8, 9), (4, 9, 5), (2, 4, 11),
+         (6, 2, 10), (8, 6, 7), (9, 8, 1)]
+    for _ in range(subdiv):
+        mid = {}
+
+        def m(a, b):
+            k = (min(a, b), max(a, b))
+            if k not in mid:
+                v = np.array(V[a]) + np.array(V[b])
+                V.append(list(v / np.linalg.norm(v)))
+                mid[k] = len(V) - 1
+            return mid[k]
+        F = [f for a, b, c in F for f in ((a, m(a, b), m(c, a)), (b, m(b, c), m(a, b)), (c, m(c, a), m(b, c)),
+                                          (m(a, b), m(b, c), m(c, a)))]
+    V = np.array(V)
+    if bump > 0:
+        V = V * rng.uniform(1 - bump, 1 + bump, (len(V), 1))
+    V = np.asarray(center) + radius * V
+    tri = V[np.array(F)]
+    n = np.cross(tri[:, 1] - tri[:, 0], tri[:, 2] - tri[:, 0])
+    flip = np.einsum("ij,ij->i", n, tri.mean(axis=1) - np.asarray(center)) < 0
+    tri[flip] = tri[flip][:, [0, 2, 1]]
+    return tri.reshape(-1, 9)
+
+
+def _torus(center, R, r, nu, nv):
+    """Torus about the y axis (major radius R, minor r), nu x nv quads split in two."""
+    u = np.linspace(0, 2 * np.pi, nu + 1)[:-1]
+    v = np.linspace(0, 2 * np.pi, nv + 1)[:-1]
+    P = np.zeros((nu, nv, 3))
+    for i, a in enumerate(u):
+        for j, b in enumerate(v):
+            P[i, j] = [(R + r * np.cos(b)) * np.cos(a), r * np.sin(b), (R + r * np.cos(b)) * np.sin(a)]
+    P += np.asarray(center)
+    out = []
+    for i in range(nu):
+        for j in range(nv):
+            a, b = P[i, j], P[(i + 1) % nu, j]
+            c, d = P[(i + 1) % nu, (j + 1) % nv], P[i, (j + 1) % nv]
+            for t in ((a, b, c), (a, c, d)):
+                # outward winding: the normal points away from the tube's centre line
+                m = (t[0] + t[1] + t[2]) / 3 - np.asarray(center)
+                ring = R * np.array([m[0], 0.0, m[2]]) / np.hypot(m[0], m[2])
+                n = np.cross(t[1] - t[0], t[2] - t[0])
+                out.append(np.concatenate(t if n @ (m - ring) > 0 else (t[0], t[2], t[1])))
+    return np.array(out)
+
+
+def mesh_room(seed: int = 1, depth: int = 7, subdiv: int = 3) -> Scene:
+    """A closed unit box made of triangles (walls albedo U[0.3, 0.8] each), a
+    ceiling light of two triangles (radiance 10) half a leaf below the
+    ceiling, and three meshes: an icosphere, a seeded rock (bumped
+    icosphere) and a torus -- about 3.3k triangles at subdiv 3.  No quads or
+    spheres: every primitive is a triangle."""
+    rng = np.random.default_rng(seed)
+    h = 1.0 / (1 << depth)
+    walls = _box_tris()
+    y = 1.0 - 0.5 * h
+    light = np.array([[0.35, y, 0.35, 0.65, y, 0.35, 0.65, y, 0.65],   # winding normal -y (down)
+                      [0.35, y, 0.35, 0.65, y, 0.65, 0.35, y, 0.65]])
+    ico = _icosphere((0.3, 0.25, 0.6), 0.18, subdiv)
+    rock = _icosphere((0.72, 0.2, 0.35), 0.15, subdiv, rng=rng, bump=0.15)
+    torus = _torus((0.55, 0.55, 0.7), 0.17, 0.06, 32, 16)
+    parts = [walls, light, ico, rock, torus]
+    tris = np.concatenate(parts).astype(np.float32)
+    alb = np.concatenate([np.repeat(rng.uniform(0.3, 0.8, 6), 2), [0.0, 0.0],
+                          np.full(len(ico), 0.7), np.full(len(rock), 0.45), np.full(len(torus), 0.6)])
+    emi = np.zeros(len(tris))
+    emi[len(walls):len(walls) + 2] = 10.0
+    return Scene(quads=np.zeros((0, 8), np.float32), spheres=np.zeros((0, 4), np.float32),
+                 albedo=alb.astype(np.float32), emission=emi.astype(np.float32), lo=np.zeros(3, np.float32),
+                 size=1.0, name=f"mesh_room(seed={seed},D={depth},subdiv={subdiv})", tris=tris)
+
+
+def tri_area(tris):
+    t = np.asarray(tris, np.float64).reshape(-1, 9)
+    return 0.5 * np.linalg.norm(np.cross(t[:, 3:6] - t[:, 0:3], t[:, 6:9] - t[:, 0:3]), axis=1)
+
+
+def tri_surface_points(scene: Scene, rng, n: int, use=None):
+    """Area-uniform points on the scene's triangles (or the subset `use`).
+    Returns (pos, nrm, prim) with nrm the winding normal (v1 - v0) x (v2 - v0)."""
+    t = scene.tris.astype(np.float64)
+    sel = np.arange(len(t)) if use is None else np.asarray(use)
+    a = tri_area(t[sel])
+    pick = sel[rng.choice(len(sel), size=n, p=a / a.sum())]
+    T = t[pick]
+    s = np.sqrt(rng.uniform(0, 1, n))
+    b = rng.uniform(0, 1, n)
+    w0, w1 = 1 - s, b * s
+    pos = w0[:, None] * T[:, 0:3] + w1[:, None] * T[:, 3:6] + (1 - w0 - w1)[:, None] * T[:, 6:9]
+    nrm = np.cross(T[:, 3:6] - T[:, 0:3], T[:, 6:9] - T[:, 0:3])
+    nrm /= np.linalg.norm(nrm, axis=1, keepdims=True)
+    return pos.astype(np.float32), nrm.astype(np.float32), pick + scene.n_quads + scene.n_spheres
 
 
 def _quad_area(q):
@@ -481,6 +613,26 @@ class Workload:
     seed: int = 1
     desc: str = ""
     extra: dict = field(default_factory=dict)
+
+
+def mesh_box(seed: int = 1, n_records: int = 100_000, n_rays: int = 4096, depth: int = 7) -> Workload:
+    """The triangle-mesh room (mesh_room), SVO depth 7 (128^3), 100k records
+    (area-uniform on every triangle, w_out cosine about the winding normal,
+    L = emission on the light, else albedo * 10 * U[0, 1]), 4096 rays on the
+    non-emissive triangles; otherwise as tiny_box."""
+    sc = mesh_room(seed, depth)
+    rng = np.random.default_rng(seed * 1000 + 1)
+    rp, rn, prim = tri_surface_points(sc, rng, n_records)
+    rw = cosine_dirs(rn, rng).astype(np.float32)
+    emi = sc.emission[prim]
+    rl = np.where(emi > 0, emi, sc.albedo[prim] * 10.0 * rng.uniform(0, 1, n_records)).astype(np.float32)
+    rng2 = np.random.default_rng(seed * 1000 + 2)
+    pp, pn, _ = tri_surface_points(sc, rng2, n_rays, use=np.flatnonzero(sc.emission == 0))
+    u = uniforms24(seed * 1000 + 3, (n_rays, 2))
+    return Workload(scene=sc, depth=depth, rec_pos=rp, rec_wout=rw, rec_L=rl, ray_pos=pp, ray_nrm=pn, u=u,
+                    grid_n=16, bin_mode=0, l_min=2, c_ray=0xFFFFFFFF, n_bins_max=128, blur=False, jitter=False,
+                    seed=seed, desc=f"triangle-mesh room ({sc.n_tris} triangles) D={depth}, 100k records, "
+                                    "4096 rays, 16x16")
 
 
 def tiny_box(seed: int = 1, n_records: int = 100_000, n_rays: int = 4096) -> Workload:
