@@ -62,11 +62,15 @@ enum {
 
 #define WFPG_MAX_DEPTH 11
 
-/* Procedural scene, device arrays owned by the caller.
+/* Scene, device arrays owned by the caller.
  *  quads   n_quads x 8 float32: axis, plane, lo1, hi1, lo2, hi2, nsign, 0 --
  *          the quad lies in x[axis] = plane, spans [lo1, hi1] on axis
  *          (axis+1)%3 and [lo2, hi2] on axis (axis+2)%3, normal nsign*e_axis.
  *  spheres n_spheres x 4 float32: cx, cy, cz, r.
+ *  tris    n_tris x 9 float32: v0, v1, v2 (triangle meshes, Sec. 3.2); the
+ *          fragment normal is the winding normal (v1 - v0) x (v2 - v0).
+ *  Primitive ids count the quads, then the spheres, then the triangles
+ *  (at most 2^20 primitives in all).
  *  lo, size: host values, the cubic AABB [lo, lo + size]^3 voxelised. */
 typedef struct wfpg_scene {
     const float* quads;
@@ -75,6 +79,8 @@ typedef struct wfpg_scene {
     uint32_t n_spheres;
     float lo[3];
     float size;
+    const float* tris;
+    uint32_t n_tris;
 } wfpg_scene;
 
 typedef struct wfpg_svo wfpg_svo;

@@ -87,11 +87,11 @@ int svo_build(const wfpg_scene* scene, int depth, void* stream, wfpg_svo** out) 
     *out = nullptr;
     if (depth < 1 || depth > WFPG_MAX_DEPTH)
         return fail(WFPG_ERR_INVALID_ARG, "svo_build: depth must be in [1, " + std::to_string(WFPG_MAX_DEPTH) + "]");
-    if ((uint64_t)scene->n_quads + scene->n_spheres == 0)
+    if ((uint64_t)scene->n_quads + scene->n_spheres + scene->n_tris == 0)
         return fail(WFPG_ERR_INVALID_ARG, "svo_build: the scene has no primitive");
-    if ((uint64_t)scene->n_quads + scene->n_spheres >= (1u << 20))
+    if ((uint64_t)scene->n_quads + scene->n_spheres + scene->n_tris >= (1u << 20))
         return fail(WFPG_ERR_INVALID_ARG, "svo_build: at most 2^20 - 1 primitives");
-    if ((scene->n_quads && !scene->quads) || (scene->n_spheres && !scene->spheres))
+    if ((scene->n_quads && !scene->quads) || (scene->n_spheres && !scene->spheres) || (scene->n_tris && !scene->tris))
         return fail(WFPG_ERR_INVALID_ARG, "svo_build: null primitive array");
     if (!(scene->size > 0.0f) || !std::isfinite(scene->size))
         return fail(WFPG_ERR_INVALID_ARG, "svo_build: size must be finite and > 0");

@@ -1,7 +1,7 @@
-// Closest-hit ray casting against the procedural scenes' analytic primitives
-// (axis-aligned quads, then spheres; a primitive id counts the quads first).
-// A renderer-side helper, not part of the guiding method: it moves the
-// wavefront from one path vertex to the next.
+// Closest-hit ray casting against the scenes' primitives (axis-aligned quads,
+// spheres, triangles; a primitive id counts the quads, then the spheres, then
+// the triangles).  A renderer-side helper, not part of the guiding method: it
+// moves the wavefront from one path vertex to the next.
 #pragma once
 #include "common.cuh"
 #include "march.cuh"
@@ -13,13 +13,57 @@ struct Hit {
     uint32_t prim;  // kNone if nothing is hit
 };
 
-// distance to primitive `prim` along the ray (t > tmin), +inf if it is missed
-__device__ __forceinline__ float hit_prim(const float* __restrict__ quads, uint32_t nq,
-                                          const float* __restrict__ spheres, uint32_t prim, const float oo[3],
-                                          const float dd[3], float tmin) {
+// the scene's primitive arrays on the device
+struct Prims {
+    const float* quads;
+    uint32_t nq;
+    const float* spheres;
+    uint32_t ns;
+    const float* tris;
+    uint32_t nt;
+};
+
+inline Prims prims_of(const wfpg_scene& s) {
+    return Prims{s.quads, s.n_quads, s.spheres, s.n_spheres, s.tris, s.n_tris};
+}
+
+__device__ __forceinline__ float3 sub3(const float* a, const float* b) {
+    return make_float3(a[0] - b[0], a[1] - b[1], a[2] - b[2]);
+}
+
+__device__ __forceinline__ float3 cross3(float3 a, float3 b) {
+    return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+
+__device__ __forceinline__ float dot3(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+
+// winding normal (v1 - v0) x (v2 - v0) of triangle t, unnormalised
+__device__ __forceinline__ float3 tri_cross(const float* T) { return cross3(sub3(T + 3, T), sub3(T + 6, T)); }
+
+// distance to primitive `prim` along the ray (t > tmin), +inf if it is missed;
+// triangles by Moller-Trumbore (two-sided)
+__device__ __forceinline__ float hit_prim(const Prims& S, uint32_t prim, const float oo[3], const float dd[3],
+                                          float tmin) {
     const float INF = __int_as_float(0x7f800000);
-    if (prim < nq) {
-        const float* Q = quads + 8 * (size_t)prim;
+    if (prim >= S.nq + S.ns) {
+        const float* T = S.tris + 9 * (size_t)(prim - S.nq - S.ns);
+        const float3 e1 = sub3(T + 3, T), e2 = sub3(T + 6, T);
+        const float3 d = make_float3(dd[0], dd[1], dd[2]);
+        const float3 pv = cross3(d, e2);
+        const float det = dot3(e1, pv);
+        if (det == 0.0f) return INF;
+        const float inv = 1.0f / det;
+        const float3 tv = make_float3(oo[0] - T[0], oo[1] - T[1], oo[2] - T[2]);
+        const float u = dot3(tv, pv) * inv;
+        if (!(u >= 0.0f && u <= 1.0f)) return INF;
+        const float3 qv = cross3(tv, e1);
+        const float v = dot3(d, qv) * inv;
+        if (!(v >= 0.0f && u + v <= 1.0f)) return INF;
+        const float t = dot3(e2, qv) * inv;
+        return t > tmin ? t : INF;
+    }
+    if (prim < S.nq) {
+        const float* Q = S.quads + 8 * (size_t)prim;
         const int a = (int)Q[0], b = (a + 1) % 3, c = (a + 2) % 3;
         if (dd[a] == 0.0f) return INF;
         const float t = (Q[1] - oo[a]) / dd[a];
@@ -27,10 +71,10 @@ __device__ __forceinline__ float hit_prim(const float* __restrict__ quads, uint3
         const float pb = oo[b] + t * dd[b], pc = oo[c] + t * dd[c];
         return (pb >= Q[2] && pb <= Q[3] && pc >= Q[4] && pc <= Q[5]) ? t : INF;
     }
-    const float* S = spheres + 4 * (size_t)(prim - nq);
-    const float cx = oo[0] - S[0], cy = oo[1] - S[1], cz = oo[2] - S[2];
+    const float* Sp = S.spheres + 4 * (size_t)(prim - S.nq);
+    const float cx = oo[0] - Sp[0], cy = oo[1] - Sp[1], cz = oo[2] - Sp[2];
     const float bq = dd[0] * cx + dd[1] * cy + dd[2] * cz;
-    const float cq = cx * cx + cy * cy + cz * cz - S[3] * S[3];
+    const float cq = cx * cx + cy * cy + cz * cz - Sp[3] * Sp[3];
     const float disc = bq * bq - cq;
     if (disc < 0.0f) return INF;
     const float sq = sqrtf(disc);
@@ -40,14 +84,13 @@ __device__ __forceinline__ float hit_prim(const float* __restrict__ quads, uint3
 }
 
 // every primitive, nearest first hit (small scenes)
-__device__ __forceinline__ Hit cast_closest(const float* __restrict__ quads, uint32_t nq,
-                                            const float* __restrict__ spheres, uint32_t ns, float ox, float oy,
-                                            float oz, float dx, float dy, float dz, float tmin) {
+__device__ __forceinline__ Hit cast_closest(const Prims& S, float ox, float oy, float oz, float dx, float dy,
+                                            float dz, float tmin) {
     const float oo[3] = {ox, oy, oz}, dd[3] = {dx, dy, dz};
     float best = __int_as_float(0x7f800000);
     uint32_t bp = kNone;
-    for (uint32_t p = 0; p < nq + ns; ++p) {
-        const float t = hit_prim(quads, nq, spheres, p, oo, dd, tmin);
+    for (uint32_t p = 0; p < S.nq + S.ns + S.nt; ++p) {
+        const float t = hit_prim(S, p, oo, dd, tmin);
         if (t < best) {
             best = t;
             bp = p;
@@ -74,8 +117,7 @@ struct SvoCast {
 // stretch of the ray (plus a relative tolerance) ends the walk.  A primitive
 // overlaps every leaf its surface passes (conservative voxelisation), so the
 // first accepted hit is the closest.  Empty blocks are skipped whole.
-__device__ __forceinline__ Hit cast_svo(const SvoCast& V, const float* __restrict__ quads, uint32_t nq,
-                                        const float* __restrict__ spheres, float ox, float oy, float oz, float dx,
+__device__ __forceinline__ Hit cast_svo(const SvoCast& V, const Prims& S, float ox, float oy, float oz, float dx,
                                         float dy, float dz, float tmin) {
     const float INF = __int_as_float(0x7f800000);
     const int D = V.D, res = 1 << D;
@@ -154,7 +196,7 @@ __device__ __forceinline__ Hit cast_svo(const SvoCast& V, const float* __restric
             uint32_t bp = kNone;
             for (uint32_t f = V.frag_off[leaf]; f < V.frag_off[leaf + 1]; ++f) {
                 const uint32_t p = V.frag_prim[f];
-                const float th = hit_prim(quads, nq, spheres, p, oo, dd, tmin);
+                const float th = hit_prim(S, p, oo, dd, tmin);
                 if (th < best) {
                     best = th;
                     bp = p;
@@ -184,19 +226,24 @@ __device__ __forceinline__ Hit cast_svo(const SvoCast& V, const float* __restric
 }
 
 // geometric normal at a hit, turned to face the incoming direction d
-__device__ __forceinline__ float3 hit_normal(const float* __restrict__ quads, uint32_t nq,
-                                             const float* __restrict__ spheres, const Hit& h, float ox, float oy,
-                                             float oz, float dx, float dy, float dz) {
+__device__ __forceinline__ float3 hit_normal(const Prims& S, const Hit& h, float ox, float oy, float oz, float dx,
+                                             float dy, float dz) {
     float nx = 0.f, ny = 0.f, nz = 0.f;
-    if (h.prim != kNone && h.prim < nq) {
-        const float* Q = quads + 8 * (size_t)h.prim;
+    if (h.prim != kNone && h.prim < S.nq) {
+        const float* Q = S.quads + 8 * (size_t)h.prim;
         const int a = (int)Q[0];
         (a == 0 ? nx : (a == 1 ? ny : nz)) = Q[6];
+    } else if (h.prim != kNone && h.prim < S.nq + S.ns) {
+        const float* Sp = S.spheres + 4 * (size_t)(h.prim - S.nq);
+        nx = (ox + h.t * dx - Sp[0]) / Sp[3];
+        ny = (oy + h.t * dy - Sp[1]) / Sp[3];
+        nz = (oz + h.t * dz - Sp[2]) / Sp[3];
     } else if (h.prim != kNone) {
-        const float* S = spheres + 4 * (size_t)(h.prim - nq);
-        nx = (ox + h.t * dx - S[0]) / S[3];
-        ny = (oy + h.t * dy - S[1]) / S[3];
-        nz = (oz + h.t * dz - S[2]) / S[3];
+        const float3 c = tri_cross(S.tris + 9 * (size_t)(h.prim - S.nq - S.ns));
+        const float inv = 1.0f / sqrtf(dot3(c, c));
+        nx = c.x * inv;
+        ny = c.y * inv;
+        nz = c.z * inv;
     }
     if (nx * dx + ny * dy + nz * dz > 0.0f) {
         nx = -nx;

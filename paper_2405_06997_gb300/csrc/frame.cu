@@ -9,6 +9,7 @@
 // direction toward the previous vertex, per vertex) is kept for Eq. 5, which
 // runs once per frame after the last depth (UpdateExitance in Alg. 1).
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -72,10 +73,7 @@ struct Queue {
 };
 
 struct FrameView {
-    const float* quads;
-    uint32_t nq;
-    const float* spheres;
-    uint32_t ns;
+    Prims pr;                     // the scene's quads, spheres and triangles
     const float* emission;
     const float* albedo;
     uint32_t P, W, H;
@@ -141,8 +139,8 @@ __global__ void k_frame_begin(FrameView F) {
 
 __device__ __forceinline__ Hit frame_cast(const FrameView& F, float ox, float oy, float oz, float dx, float dy,
                                           float dz) {
-    return F.svo_cast ? cast_svo(F.sv, F.quads, F.nq, F.spheres, ox, oy, oz, dx, dy, dz, 0.0f)
-                      : cast_closest(F.quads, F.nq, F.spheres, F.ns, ox, oy, oz, dx, dy, dz, 0.0f);
+    return F.svo_cast ? cast_svo(F.sv, F.pr, ox, oy, oz, dx, dy, dz, 0.0f)
+                      : cast_closest(F.pr, ox, oy, oz, dx, dy, dz, 0.0f);
 }
 
 // survival test at 1-based vertex v (>= rr_depth): min(0.95, albedo)
@@ -194,7 +192,7 @@ __global__ void __launch_bounds__(256) k_camera(FrameView F, Queue S, uint32_t* 
     F.nv[i] = 0;
     if (h.prim != kNone) {
         const float hx = ex + h.t * dx, hy = ey + h.t * dy, hz = ez + h.t * dz;
-        const float3 n = hit_normal(F.quads, F.nq, F.spheres, h, ex, ey, ez, dx, dy, dz);
+        const float3 n = hit_normal(F.pr, h, ex, ey, ez, dx, dy, dz);
         const float a = F.albedo[h.prim];
         F.vT[i] = 1.0f;
         F.vLe[i] = F.emission[h.prim];  // seen by the camera: no other strategy to weigh against
@@ -244,12 +242,17 @@ __device__ __forceinline__ float light_pdf(const FrameView& F, uint32_t prim, fl
 
 // geometric normal of a primitive at point (x, y, z) (unnormalised side)
 __device__ __forceinline__ float3 prim_normal(const FrameView& F, uint32_t prim, float x, float y, float z) {
-    if (prim < F.nq) {
-        const float* Q = F.quads + 8 * (size_t)prim;
+    if (prim < F.pr.nq) {
+        const float* Q = F.pr.quads + 8 * (size_t)prim;
         const int a = (int)Q[0];
         return make_float3(a == 0 ? 1.0f : 0.0f, a == 1 ? 1.0f : 0.0f, a == 2 ? 1.0f : 0.0f);
     }
-    const float* Sp = F.spheres + 4 * (size_t)(prim - F.nq);
+    if (prim >= F.pr.nq + F.pr.ns) {
+        const float3 c = tri_cross(F.pr.tris + 9 * (size_t)(prim - F.pr.nq - F.pr.ns));
+        const float inv = 1.0f / sqrtf(dot3(c, c));
+        return make_float3(c.x * inv, c.y * inv, c.z * inv);
+    }
+    const float* Sp = F.pr.spheres + 4 * (size_t)(prim - F.pr.nq);
     return make_float3((x - Sp[0]) / Sp[3], (y - Sp[1]) / Sp[3], (z - Sp[2]) / Sp[3]);
 }
 
@@ -269,14 +272,18 @@ __global__ void __launch_bounds__(256) k_nee(FrameView F, Queue Q, int k) {
         }
     const uint32_t prim = F.light_prim[l];
     float y[3];
-    if (prim < F.nq) {
-        const float* Qd = F.quads + 8 * (size_t)prim;
+    if (prim < F.pr.nq) {
+        const float* Qd = F.pr.quads + 8 * (size_t)prim;
         const int a = (int)Qd[0], b = (a + 1) % 3, c = (a + 2) % 3;
         y[a] = Qd[1];
         y[b] = Qd[2] + ua * (Qd[3] - Qd[2]);
         y[c] = Qd[4] + ub * (Qd[5] - Qd[4]);
+    } else if (prim >= F.pr.nq + F.pr.ns) {  // uniform on the triangle: barycentrics (1 - sqrt(ua), ub sqrt(ua))
+        const float* T = F.pr.tris + 9 * (size_t)(prim - F.pr.nq - F.pr.ns);
+        const float su = sqrtf(ua), b0 = 1.0f - su, b1 = ub * su, b2 = 1.0f - b0 - b1;
+        for (int a = 0; a < 3; ++a) y[a] = b0 * T[a] + b1 * T[3 + a] + b2 * T[6 + a];
     } else {
-        const float* Sp = F.spheres + 4 * (size_t)(prim - F.nq);
+        const float* Sp = F.pr.spheres + 4 * (size_t)(prim - F.pr.nq);
         const float z = 1.0f - 2.0f * ua, r = sqrtf(fmaxf(0.0f, 1.0f - z * z));
         float sp, cp;
         sincospif(2.0f * ub, &sp, &cp);
@@ -356,7 +363,7 @@ __global__ void __launch_bounds__(256) k_shade(FrameView F, Queue Q, const float
                 store3(F.vwo, v, -dx, -dy, -dz);
                 F.nv[path] = (uint32_t)(k + 2);
                 if (a > 0.0f && k + 1 < F.max_depth && roulette(F, path, k + 2, a, &T)) {
-                    const float3 n = hit_normal(F.quads, F.nq, F.spheres, h, ox, oy, oz, dx, dy, dz);
+                    const float3 n = hit_normal(F.pr, h, ox, oy, oz, dx, dy, dz);
                     S.path[s] = path;
                     store3(S.pos, s, hx, hy, hz);
                     store3(S.nrm, s, n.x, n.y, n.z);
@@ -551,10 +558,7 @@ struct wfpg_frame {
     }
     FrameView view() const {
         FrameView F;
-        F.quads = scene.quads;
-        F.nq = scene.n_quads;
-        F.spheres = scene.spheres;
-        F.ns = scene.n_spheres;
+        F.pr = prims_of(scene);
         F.emission = emission;
         F.albedo = albedo;
         F.P = P;
@@ -579,7 +583,7 @@ struct wfpg_frame {
         F.pseed = purpose(p.seed, kPathPurpose);
         F.offset = 1e-4f * scene.size;
         F.sv = svo_cast_view(svo);
-        F.svo_cast = p.caster == 2 || (p.caster == 0 && scene.n_quads + scene.n_spheres > 64);
+        F.svo_cast = p.caster == 2 || (p.caster == 0 && scene.n_quads + scene.n_spheres + scene.n_tris > 64);
         F.vT = vT;
         F.vLe = vLe;
         F.vpos = vpos;
@@ -810,18 +814,29 @@ int frame_create(wfpg_svo* svo, const wfpg_scene* scene, const float* emission, 
     }
     // next-event estimation: the emissive primitives, chosen in proportion to emitted power
     {
-        const uint32_t nq = scene->n_quads, ns = scene->n_spheres, np = nq + ns;
-        std::vector<float> hq(8 * (size_t)nq), hs(4 * (size_t)ns), he(np);
+        const uint32_t nq = scene->n_quads, ns = scene->n_spheres, nt = scene->n_tris, np = nq + ns + nt;
+        std::vector<float> hq(8 * (size_t)nq), hs(4 * (size_t)ns), ht(9 * (size_t)nt), he(np);
         bool okc = (nq == 0 || cudaMemcpy(hq.data(), scene->quads, 4 * hq.size(), cudaMemcpyDeviceToHost) == cudaSuccess) &&
                    (ns == 0 || cudaMemcpy(hs.data(), scene->spheres, 4 * hs.size(), cudaMemcpyDeviceToHost) == cudaSuccess) &&
+                   (nt == 0 || cudaMemcpy(ht.data(), scene->tris, 4 * ht.size(), cudaMemcpyDeviceToHost) == cudaSuccess) &&
                    (np == 0 || cudaMemcpy(he.data(), emission, 4 * he.size(), cudaMemcpyDeviceToHost) == cudaSuccess);
         std::vector<float> area(np, 0.0f), pmf(np, 0.0f);
         std::vector<uint32_t> lp;
         std::vector<double> power;
         double total = 0.0;
         for (uint32_t k = 0; okc && k < np; ++k) {
-            area[k] = k < nq ? (hq[8 * k + 3] - hq[8 * k + 2]) * (hq[8 * k + 5] - hq[8 * k + 4])
-                             : 12.566370614359172f * hs[4 * (k - nq) + 3] * hs[4 * (k - nq) + 3];
+            if (k < nq) {
+                area[k] = (hq[8 * k + 3] - hq[8 * k + 2]) * (hq[8 * k + 5] - hq[8 * k + 4]);
+            } else if (k < nq + ns) {
+                area[k] = 12.566370614359172f * hs[4 * (k - nq) + 3] * hs[4 * (k - nq) + 3];
+            } else {
+                const float* T = ht.data() + 9 * (size_t)(k - nq - ns);
+                const double e1[3] = {(double)T[3] - T[0], (double)T[4] - T[1], (double)T[5] - T[2]};
+                const double e2[3] = {(double)T[6] - T[0], (double)T[7] - T[1], (double)T[8] - T[2]};
+                const double c[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2],
+                                     e1[0] * e2[1] - e1[1] * e2[0]};
+                area[k] = (float)(0.5 * std::sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]));
+            }
             if (he[k] > 0.0f && area[k] > 0.0f) {
                 lp.push_back(k);
                 power.push_back((double)he[k] * area[k]);

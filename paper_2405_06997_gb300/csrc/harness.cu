@@ -1,7 +1,7 @@
 // Renderer-side helper for measuring the guiding (not part of the paper's
-// method): closest-hit ray casting against the procedural scenes' analytic
-// quads and spheres, so that guided estimators can be evaluated against the
-// scene's true incident radiance.
+// method): closest-hit ray casting against the scenes' quads, spheres and
+// triangles, so that guided estimators can be evaluated against the scene's
+// true incident radiance.
 #include <string>
 
 #include "cast.cuh"
@@ -9,28 +9,25 @@
 
 namespace wfpg {
 
-__global__ void __launch_bounds__(256) k_cast(const float* __restrict__ quads, uint32_t nq,
-                                              const float* __restrict__ spheres, uint32_t ns,
-                                              const float* __restrict__ o, const float* __restrict__ d, uint32_t n,
+__global__ void __launch_bounds__(256) k_cast(Prims S, const float* __restrict__ o, const float* __restrict__ d, uint32_t n,
                                               float tmin, float* __restrict__ t_out, uint32_t* __restrict__ prim_out,
                                               float* __restrict__ nrm_out) {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const float ox = o[3 * (size_t)i], oy = o[3 * (size_t)i + 1], oz = o[3 * (size_t)i + 2];
     const float dx = d[3 * (size_t)i], dy = d[3 * (size_t)i + 1], dz = d[3 * (size_t)i + 2];
-    const Hit h = cast_closest(quads, nq, spheres, ns, ox, oy, oz, dx, dy, dz, tmin);
+    const Hit h = cast_closest(S, ox, oy, oz, dx, dy, dz, tmin);
     t_out[i] = h.t;
     prim_out[i] = h.prim;
     if (nrm_out) {
-        const float3 nn = hit_normal(quads, nq, spheres, h, ox, oy, oz, dx, dy, dz);
+        const float3 nn = hit_normal(S, h, ox, oy, oz, dx, dy, dz);
         nrm_out[3 * (size_t)i] = nn.x;
         nrm_out[3 * (size_t)i + 1] = nn.y;
         nrm_out[3 * (size_t)i + 2] = nn.z;
     }
 }
 
-__global__ void __launch_bounds__(256) k_cast_svo(SvoCast V, const float* __restrict__ quads, uint32_t nq,
-                                                  const float* __restrict__ spheres, const float* __restrict__ o,
+__global__ void __launch_bounds__(256) k_cast_svo(SvoCast V, Prims S, const float* __restrict__ o,
                                                   const float* __restrict__ d, uint32_t n, float tmin,
                                                   float* __restrict__ t_out, uint32_t* __restrict__ prim_out,
                                                   float* __restrict__ nrm_out) {
@@ -38,11 +35,11 @@ __global__ void __launch_bounds__(256) k_cast_svo(SvoCast V, const float* __rest
     if (i >= n) return;
     const float ox = o[3 * (size_t)i], oy = o[3 * (size_t)i + 1], oz = o[3 * (size_t)i + 2];
     const float dx = d[3 * (size_t)i], dy = d[3 * (size_t)i + 1], dz = d[3 * (size_t)i + 2];
-    const Hit h = cast_svo(V, quads, nq, spheres, ox, oy, oz, dx, dy, dz, tmin);
+    const Hit h = cast_svo(V, S, ox, oy, oz, dx, dy, dz, tmin);
     t_out[i] = h.t;
     prim_out[i] = h.prim;
     if (nrm_out) {
-        const float3 nn = hit_normal(quads, nq, spheres, h, ox, oy, oz, dx, dy, dz);
+        const float3 nn = hit_normal(S, h, ox, oy, oz, dx, dy, dz);
         nrm_out[3 * (size_t)i] = nn.x;
         nrm_out[3 * (size_t)i + 1] = nn.y;
         nrm_out[3 * (size_t)i + 2] = nn.z;
@@ -70,8 +67,8 @@ extern "C" int wfpg_cast_rays(const wfpg_scene* scene, const float* o, const flo
     if (!scene || (n && (!o || !d || !t_out || !prim_out)))
         return wfpg::set_last_error(WFPG_ERR_INVALID_ARG, "wfpg_cast_rays: null argument");
     if (n == 0) return WFPG_OK;
-    WFPG_LAUNCH(wfpg::k_cast, wfpg::div_up(n, 256), 256, 0, static_cast<cudaStream_t>(stream), scene->quads,
-                scene->n_quads, scene->spheres, scene->n_spheres, o, d, n, tmin, t_out, prim_out, nrm_out);
+    WFPG_LAUNCH(wfpg::k_cast, wfpg::div_up(n, 256), 256, 0, static_cast<cudaStream_t>(stream),
+                wfpg::prims_of(*scene), o, d, n, tmin, t_out, prim_out, nrm_out);
     if (cudaGetLastError() != cudaSuccess) return wfpg::set_last_error(WFPG_ERR_CUDA, "wfpg_cast_rays: launch failed");
     return WFPG_OK;
 }
@@ -83,8 +80,7 @@ extern "C" int wfpg_cast_rays_svo(const wfpg_svo* svo, const wfpg_scene* scene, 
         return wfpg::set_last_error(WFPG_ERR_INVALID_ARG, "wfpg_cast_rays_svo: null argument");
     if (n == 0) return WFPG_OK;
     WFPG_LAUNCH(wfpg::k_cast_svo, wfpg::div_up(n, 256), 256, 0, static_cast<cudaStream_t>(stream),
-                wfpg::svo_cast_view(svo), scene->quads, scene->n_quads, scene->spheres, o, d, n, tmin, t_out,
-                prim_out, nrm_out);
+                wfpg::svo_cast_view(svo), wfpg::prims_of(*scene), o, d, n, tmin, t_out, prim_out, nrm_out);
     if (cudaGetLastError() != cudaSuccess)
         return wfpg::set_last_error(WFPG_ERR_CUDA, "wfpg_cast_rays_svo: launch failed");
     return WFPG_OK;

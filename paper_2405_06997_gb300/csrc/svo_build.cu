@@ -1,5 +1,5 @@
 // SVO generation (Sec. 3.2): conservative voxelisation of analytic quads and
-// spheres, Morton-key radix sort, unique leaves, level-by-level node
+// spheres and of triangle meshes (separating-axis test), Morton-key radix sort, unique leaves, level-by-level node
 // allocation (children contiguous and Morton-ordered under each parent) and
 // two normals per node from k-means with k = 2 (Fig. 2).
 #include <string>
@@ -23,6 +23,8 @@ struct SceneDev {
     uint32_t nq;
     const float* spheres;
     uint32_t ns;
+    const float* tris;
+    uint32_t nt;
     float lo[3];
     float S;
     float scale;
@@ -30,11 +32,12 @@ struct SceneDev {
 };
 
 // candidate voxel box of each primitive; quads: exact cells of the closed
-// quad; spheres: bounding cube widened by one voxel (the exact test decides)
+// quad; spheres and triangles: bounding box widened by one voxel (the exact
+// test decides)
 __global__ void k_prim_ranges(SceneDev sc, PrimRange* __restrict__ ranges, uint32_t* __restrict__ cnt,
                               unsigned long long* __restrict__ total, uint32_t* __restrict__ bad) {
     const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= sc.nq + sc.ns) return;
+    if (p >= sc.nq + sc.ns + sc.nt) return;
     PrimRange r;
     const int res = 1 << sc.D;
     bool ok = true;
@@ -51,6 +54,20 @@ __global__ void k_prim_ranges(SceneDev sc, PrimRange* __restrict__ ranges, uint3
             r.hi[b] = grid_index(Q[3], sc.lo[b], sc.scale, sc.D);
             r.lo[c] = grid_index(Q[4], sc.lo[c], sc.scale, sc.D);
             r.hi[c] = grid_index(Q[5], sc.lo[c], sc.scale, sc.D);
+        }
+    } else if (p >= sc.nq + sc.ns) {
+        const float* T = sc.tris + 9 * (size_t)(p - sc.nq - sc.ns);
+        const double h = (double)sc.S / (double)res;
+        for (int a = 0; a < 3; ++a) {
+            const double mn = fmin((double)T[a], fmin((double)T[3 + a], (double)T[6 + a]));
+            const double mx = fmax((double)T[a], fmax((double)T[3 + a], (double)T[6 + a]));
+            double l0 = floor(__ddiv_rn(__dsub_rn(mn, (double)sc.lo[a]), h)) - 1.0;
+            double l1 = floor(__ddiv_rn(__dsub_rn(mx, (double)sc.lo[a]), h)) + 1.0;
+            l0 = fmax(l0, 0.0);
+            l1 = fmin(l1, (double)(res - 1));
+            r.lo[a] = (int)l0;
+            r.hi[a] = (int)l1;
+            if (!(l0 <= l1)) ok = false;
         }
     } else {
         const float* P = sc.spheres + 4 * (size_t)(p - sc.nq);
@@ -101,6 +118,58 @@ __device__ __forceinline__ bool sphere_hits_voxel(const float* P, const float lo
     return dmin2 <= r2 && r2 <= dmax2;
 }
 
+__device__ __forceinline__ double ddot3(const double a[3], const double b[3]) {
+    return __dadd_rn(__dadd_rn(__dmul_rn(a[0], b[0]), __dmul_rn(a[1], b[1])), __dmul_rn(a[2], b[2]));
+}
+
+// triangle / closed voxel box overlap by the separating axis theorem
+// (Akenine-Moller 2001): disjoint iff the projections separate on one of the
+// box's face normals, the triangle's normal, or a box axis crossed with a
+// triangle edge.  Box-centred, binary64, one rounding per operation (the
+// order fixed, so every caller decides the same voxels); touching overlaps.
+__device__ __forceinline__ bool tri_hits_voxel(const float* T, const float lo[3], double h, int x, int y, int z) {
+    const int idx[3] = {x, y, z};
+    const double e = __dmul_rn(h, 0.5);
+    double v[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const double c = __dadd_rn((double)lo[a], __dmul_rn(__dadd_rn((double)idx[a], 0.5), h));
+#pragma unroll
+        for (int i = 0; i < 3; ++i) v[i][a] = __dsub_rn((double)T[3 * i + a], c);
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const double mn = fmin(v[0][a], fmin(v[1][a], v[2][a]));
+        const double mx = fmax(v[0][a], fmax(v[1][a], v[2][a]));
+        if (mn > e || mx < -e) return false;
+    }
+    double f[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) f[i][a] = __dsub_rn(v[(i + 1) % 3][a], v[i][a]);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            double ax[3];
+            ax[k] = 0.0;
+            ax[(k + 1) % 3] = -f[i][(k + 2) % 3];
+            ax[(k + 2) % 3] = f[i][(k + 1) % 3];
+            const double p0 = ddot3(ax, v[0]), p1 = ddot3(ax, v[1]), p2 = ddot3(ax, v[2]);
+            const double r = __dmul_rn(e, __dadd_rn(__dadd_rn(fabs(ax[0]), fabs(ax[1])), fabs(ax[2])));
+            const double mn = fmin(p0, fmin(p1, p2)), mx = fmax(p0, fmax(p1, p2));
+            if (mn > r || mx < -r) return false;
+        }
+    }
+    const double n[3] = {__dsub_rn(__dmul_rn(f[0][1], f[1][2]), __dmul_rn(f[0][2], f[1][1])),
+                         __dsub_rn(__dmul_rn(f[0][2], f[1][0]), __dmul_rn(f[0][0], f[1][2])),
+                         __dsub_rn(__dmul_rn(f[0][0], f[1][1]), __dmul_rn(f[0][1], f[1][0]))};
+    const double d = ddot3(n, v[0]);
+    const double r = __dmul_rn(e, __dadd_rn(__dadd_rn(fabs(n[0]), fabs(n[1])), fabs(n[2])));
+    return !(d > r || d < -r);
+}
+
 template <bool kEmit>
 __global__ void __launch_bounds__(256) k_voxel_test(SceneDev sc, const PrimRange* __restrict__ ranges,
                                                     const uint32_t* __restrict__ cand_off, uint32_t n_prims,
@@ -129,7 +198,9 @@ __global__ void __launch_bounds__(256) k_voxel_test(SceneDev sc, const PrimRange
             const int x = r.lo[0] + (int)(local % dx);
             const int y = r.lo[1] + (int)((local / dx) % dy);
             const int z = r.lo[2] + (int)(local / (dx * dy));
-            pass = (p < sc.nq) ? true : sphere_hits_voxel(sc.spheres + 4 * (size_t)(p - sc.nq), sc.lo, h, x, y, z);
+            pass = (p < sc.nq)           ? true
+                   : (p < sc.nq + sc.ns) ? sphere_hits_voxel(sc.spheres + 4 * (size_t)(p - sc.nq), sc.lo, h, x, y, z)
+                                         : tri_hits_voxel(sc.tris + 9 * (size_t)(p - sc.nq - sc.ns), sc.lo, h, x, y, z);
             key = (morton3((uint32_t)x, (uint32_t)y, (uint32_t)z) << kPrimBits) | p;
         }
         if (kEmit) {
@@ -270,16 +341,39 @@ __device__ void kmeans2(const Src& src, int m, float out[3]) {
 }
 
 // fragment normals of one leaf: quads give their normal, spheres the unit
-// vector from the centre to the voxel centre
+// vector from the centre to the voxel centre, triangles their normalised
+// winding normal (v1 - v0) x (v2 - v0)
 struct LeafFrags {
     const float* quads;
     uint32_t nq;
     const float* spheres;
+    uint32_t ns;
+    const float* tris;
     const uint32_t* prim;
     float vc[3];
     __device__ void get(int f, float n[3], float* w) const {
         const uint32_t p = prim[f];
         *w = 1.0f;
+        if (p >= nq + ns) {
+            const float* T = tris + 9 * (size_t)(p - nq - ns);
+            const float e1[3] = {__fsub_rn(T[3], T[0]), __fsub_rn(T[4], T[1]), __fsub_rn(T[5], T[2])};
+            const float e2[3] = {__fsub_rn(T[6], T[0]), __fsub_rn(T[7], T[1]), __fsub_rn(T[8], T[2])};
+            const float c0 = __fsub_rn(__fmul_rn(e1[1], e2[2]), __fmul_rn(e1[2], e2[1]));
+            const float c1 = __fsub_rn(__fmul_rn(e1[2], e2[0]), __fmul_rn(e1[0], e2[2]));
+            const float c2 = __fsub_rn(__fmul_rn(e1[0], e2[1]), __fmul_rn(e1[1], e2[0]));
+            const float len2 = __fadd_rn(__fadd_rn(__fmul_rn(c0, c0), __fmul_rn(c1, c1)), __fmul_rn(c2, c2));
+            if (len2 > 0.f) {
+                const float len = __fsqrt_rn(len2);
+                n[0] = __fdiv_rn(c0, len);
+                n[1] = __fdiv_rn(c1, len);
+                n[2] = __fdiv_rn(c2, len);
+            } else {
+                n[0] = 0.f;
+                n[1] = 1.f;
+                n[2] = 0.f;
+            }
+            return;
+        }
         if (p < nq) {
             const float* Q = quads + 8 * (size_t)p;
             const int a = (int)Q[0];
@@ -315,6 +409,8 @@ __global__ void k_leaf_normals(SceneDev sc, const uint64_t* __restrict__ leaf_ke
     src.quads = sc.quads;
     src.nq = sc.nq;
     src.spheres = sc.spheres;
+    src.ns = sc.ns;
+    src.tris = sc.tris;
     src.prim = frag_prim + frag_off[j];
     for (int a = 0; a < 3; ++a)
         src.vc[a] = __fadd_rn(sc.lo[a], __fmul_rn(__fadd_rn((float)c[a], 0.5f), h));
@@ -418,6 +514,8 @@ int build_svo(const wfpg_scene* scene, int D, cudaStream_t st, wfpg_svo* s, std:
     sc.nq = scene->n_quads;
     sc.spheres = scene->spheres;
     sc.ns = scene->n_spheres;
+    sc.tris = scene->tris;
+    sc.nt = scene->n_tris;
     for (int a = 0; a < 3; ++a) sc.lo[a] = scene->lo[a];
     sc.S = scene->size;
     sc.scale = (float)(1 << D) / scene->size;
@@ -426,7 +524,7 @@ int build_svo(const wfpg_scene* scene, int D, cudaStream_t st, wfpg_svo* s, std:
     for (int a = 0; a < 3; ++a) s->lo[a] = sc.lo[a];
     s->S = sc.S;
     s->scale = sc.scale;
-    const uint32_t n_prims = sc.nq + sc.ns;
+    const uint32_t n_prims = sc.nq + sc.ns + sc.nt;
     const int T = 256;
 
     // 1. candidate boxes and counts

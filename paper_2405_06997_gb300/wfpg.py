@@ -44,7 +44,7 @@ class WfpgError(RuntimeError):
 
 class Scene(C.Structure):
     _fields_ = [("quads", P), ("n_quads", U32), ("spheres", P), ("n_spheres", U32),
-                ("lo", F * 3), ("size", F)]
+                ("lo", F * 3), ("size", F), ("tris", P), ("n_tris", U32)]
 
 
 class SvoInfo(C.Structure):
@@ -238,17 +238,26 @@ class SVO:
         _check(lib().svo_reset_exitance(self._h, _stream(stream)))
 
 
-def svo_build(quads: torch.Tensor, spheres: torch.Tensor, lo, size: float, depth: int,
-              stream=None) -> SVO:
-    """SVO generation (Sec. 3.2).  quads [nq, 8], spheres [ns, 4] float32 CUDA."""
+def _scene_struct(quads, spheres, tris=None, lo=(0.0, 0.0, 0.0), size=1.0):
     sc = Scene()
     sc.quads = _ptr(quads, torch.float32, what="quads") if quads.numel() else None
     sc.n_quads = quads.shape[0] if quads.numel() else 0
     sc.spheres = _ptr(spheres, torch.float32, what="spheres") if spheres.numel() else None
     sc.n_spheres = spheres.shape[0] if spheres.numel() else 0
+    if tris is not None and tris.numel():
+        sc.tris = _ptr(tris, torch.float32, what="tris")
+        sc.n_tris = tris.shape[0]
     for a in range(3):
         sc.lo[a] = float(lo[a])
     sc.size = float(size)
+    return sc
+
+
+def svo_build(quads: torch.Tensor, spheres: torch.Tensor, lo, size: float, depth: int,
+              stream=None, tris: torch.Tensor = None) -> SVO:
+    """SVO generation (Sec. 3.2).  quads [nq, 8], spheres [ns, 4], tris [nt, 9]
+    (optional) float32 CUDA."""
+    sc = _scene_struct(quads, spheres, tris, lo, size)
     h = P()
     _check(lib().svo_build(C.byref(sc), int(depth), _stream(stream), C.byref(h)))
     svo = SVO(h.value)
@@ -404,7 +413,9 @@ def svo_from_scene(scene, depth: int, device="cuda", stream=None) -> SVO:
     """Upload a procedural scene (paper_2405_06997_gb300.inputs.Scene) and build its SVO."""
     q = torch.as_tensor(np.ascontiguousarray(scene.quads, np.float32).reshape(-1, 8), device=device)
     s = torch.as_tensor(np.ascontiguousarray(scene.spheres, np.float32).reshape(-1, 4), device=device)
-    return svo_build(q, s, scene.lo, scene.size, depth, stream=stream)
+    t = torch.as_tensor(np.ascontiguousarray(getattr(scene, "tris", np.zeros((0, 9))), np.float32).reshape(-1, 9),
+                        device=device)
+    return svo_build(q, s, scene.lo, scene.size, depth, stream=stream, tris=t)
 
 
 def bin_rays_static(svo: SVO, pos, nrm=None, *, mode=BIN_PARTITION_S, l_min=2, c_ray=0xFFFFFFFF,
@@ -564,19 +575,16 @@ def guide_learned_train_step(mlp: MLP, pos, nrm, target, *, lo=(0, 0, 0), size=1
     return loss, (grad if want_grad else None)
 
 
-def cast_rays(quads, spheres, o, d, tmin=1e-5, with_normal=True, stream=None):
-    """Closest hits of rays (o + t d) against a scene's quads / spheres (CUDA
-    tensors); returns (t [-1 on miss], prim [int32, -1 on miss], nrm or None)."""
+def cast_rays(quads, spheres, o, d, tmin=1e-5, with_normal=True, stream=None, tris=None):
+    """Closest hits of rays (o + t d) against a scene's quads / spheres /
+    triangles (CUDA tensors); returns (t [-1 on miss], prim [int32, -1 on
+    miss], nrm or None)."""
     L = lib()
     fn = L.wfpg_cast_rays
     fn.restype = I32
     fn.argtypes = [P, P, P, U32, F, P, P, P, P]
     n = o.shape[0]
-    sc = Scene()
-    sc.quads = _ptr(quads, torch.float32) if quads.numel() else None
-    sc.n_quads = quads.shape[0] if quads.numel() else 0
-    sc.spheres = _ptr(spheres, torch.float32) if spheres.numel() else None
-    sc.n_spheres = spheres.shape[0] if spheres.numel() else 0
+    sc = _scene_struct(quads, spheres, tris)
     t = torch.empty(n, dtype=torch.float32, device=o.device)
     prim = torch.empty(n, dtype=torch.int32, device=o.device)
     nrm = torch.empty((n, 3), dtype=torch.float32, device=o.device) if with_normal else None
@@ -586,15 +594,11 @@ def cast_rays(quads, spheres, o, d, tmin=1e-5, with_normal=True, stream=None):
     return t, prim, nrm
 
 
-def cast_rays_svo(svo: SVO, quads, spheres, o, d, tmin=1e-5, with_normal=True, stream=None):
+def cast_rays_svo(svo: SVO, quads, spheres, o, d, tmin=1e-5, with_normal=True, stream=None, tris=None):
     """cast_rays with the scene's SVO as the acceleration structure (the SVO
-    must have been built from these quads and spheres)."""
+    must have been built from these quads, spheres and triangles)."""
     n = o.shape[0]
-    sc = Scene()
-    sc.quads = _ptr(quads, torch.float32) if quads.numel() else None
-    sc.n_quads = quads.shape[0] if quads.numel() else 0
-    sc.spheres = _ptr(spheres, torch.float32) if spheres.numel() else None
-    sc.n_spheres = spheres.shape[0] if spheres.numel() else 0
+    sc = _scene_struct(quads, spheres, tris)
     t = torch.empty(n, dtype=torch.float32, device=o.device)
     prim = torch.empty(n, dtype=torch.int32, device=o.device)
     nrm = torch.empty((n, 3), dtype=torch.float32, device=o.device) if with_normal else None
@@ -686,9 +690,9 @@ class Frame:
         self._s = torch.as_tensor(np.ascontiguousarray(scene.spheres, np.float32).reshape(-1, 4), device=device)
         self._e = torch.as_tensor(np.ascontiguousarray(scene.emission, np.float32), device=device)
         self._a = torch.as_tensor(np.ascontiguousarray(scene.albedo, np.float32), device=device)
-        self._scene = Scene(quads=_ptr(self._q), n_quads=self._q.shape[0], spheres=_ptr(self._s),
-                            n_spheres=self._s.shape[0], lo=(F * 3)(*[float(v) for v in scene.lo]),
-                            size=float(scene.size))
+        self._t = torch.as_tensor(np.ascontiguousarray(getattr(scene, "tris", np.zeros((0, 9))), np.float32)
+                                  .reshape(-1, 9), device=device)
+        self._scene = _scene_struct(self._q, self._s, self._t, scene.lo, scene.size)
         self.width, self.height = int(width), int(height)
         self._probes = None
         if probes is not None:  # probe mode: one row of probe_n^2 octahedral cells per point
