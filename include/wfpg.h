@@ -243,7 +243,9 @@ typedef struct wfpg_guide_params {
  * field / total * N^2 / (4 pi).
  * Outputs (device, caller-owned, float32): pdf[bin_cap][N*N],
  * cdf_row[bin_cap][N*N], cdf_marg[bin_cap][N].  Bins past the count are not
- * written.
+ * written.  The SVO holds the field kernel's bin counter (zeroed on the stream
+ * before each launch): field calls on one SVO (this, guide_build_sample,
+ * frames) must be ordered on the GPU, as its status word already requires.
  */
 WFPG_API int guide_build_pdf(const wfpg_svo* svo, const float* pos, const uint32_t* origin_ray,
                     const uint32_t* n_bins_dev, uint32_t bin_cap, const wfpg_guide_params* p,

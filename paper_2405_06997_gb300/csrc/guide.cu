@@ -307,7 +307,8 @@ __global__ void __launch_bounds__(kGuideThreads, 1024 / kGuideThreads) k_guide_b
                                                                const uint32_t* __restrict__ n_bins_dev,
                                                                uint32_t bin_cap, float* __restrict__ pdf,
                                                                float* __restrict__ cdf_row,
-                                                               float* __restrict__ cdf_marg, uint32_t* status) {
+                                                               float* __restrict__ cdf_marg, uint32_t* status,
+                                                               uint32_t* __restrict__ bin_next) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int N = G.N, NN = N * N;
     const int D = T.D;
@@ -338,7 +339,11 @@ __global__ void __launch_bounds__(kGuideThreads, 1024 / kGuideThreads) k_guide_b
     const float fres = (float)res;
     const float INF = __int_as_float(0x7f800000);
     const int cap = 3 * res + 16;
-    for (uint32_t b = blockIdx.x; b < nb; b += gridDim.x) {
+    // bins are taken dynamically: the first one by CTA index, the next from a
+    // counter (zeroed before the launch) as each CTA finishes, so that cheap and
+    // expensive bins even out across the persistent CTAs
+    __shared__ uint32_t s_bin;
+    for (uint32_t b = blockIdx.x; b < nb;) {
         const uint32_t r = origin_ray ? origin_ray[b] : b;
         float ox = 0.0f, oy = 0.0f, oz = 0.0f;
         if (r != kNone) {
@@ -619,6 +624,9 @@ __global__ void __launch_bounds__(kGuideThreads, 1024 / kGuideThreads) k_guide_b
                 sample_ray(F, F.ray_order[k], field, tmp, marg, N, nn, den, tn);
         }
         __syncthreads();
+        if (tid == 0) s_bin = gridDim.x + atomicAdd(bin_next, 1u);
+        __syncthreads();
+        b = s_bin;
     }
 }
 
@@ -789,7 +797,8 @@ static size_t guide_smem_bytes(uint32_t smem_nodes, int N, int D, int threads, b
 template <int kThreads, bool kStage, bool kFused>
 static int launch_guide(const TraceArgs& T, const GuideArgs& G, const FusedArgs& F, const float* pos,
                         const uint32_t* origin_ray, const uint32_t* n_bins_dev, uint32_t bin_cap, float* pdf,
-                        float* cdf_row, float* cdf_marg, uint32_t* status, int D, cudaStream_t st) {
+                        float* cdf_row, float* cdf_marg, uint32_t* status, uint32_t* bin_next, int D,
+                        cudaStream_t st) {
     auto kernel = k_guide_build<kThreads, kStage, kFused>;
     const size_t smem = guide_smem_bytes(T.smem_nodes, G.N, D, kThreads, kStage);
     if (smem > 48 * 1024 &&
@@ -801,8 +810,9 @@ static int launch_guide(const TraceArgs& T, const GuideArgs& G, const FusedArgs&
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, smem);
     if (per_sm < 1) return WFPG_ERR_INVALID_ARG;  // the field does not fit in shared memory
     const uint32_t grid = (uint32_t)std::min<uint64_t>(bin_cap, (uint64_t)sms * per_sm);
+    if (cudaMemsetAsync(bin_next, 0, sizeof(uint32_t), st) != cudaSuccess) return WFPG_ERR_CUDA;
     WFPG_LAUNCH(kernel, grid, kThreads, smem, st, T, G, F, pos, origin_ray, n_bins_dev, bin_cap, pdf, cdf_row,
-                cdf_marg, status);
+                cdf_marg, status, bin_next);
     return cudaGetLastError() == cudaSuccess ? WFPG_OK : WFPG_ERR_CUDA;
 }
 
@@ -843,9 +853,9 @@ static int dispatch_guide(const wfpg_svo* s, const wfpg_guide_params* p, const T
 #define WFPG_GUIDE_CASE(TH)                                                                                        \
     if (threads == TH)                                                                                             \
         return stage ? launch_guide<TH, true, kFused>(T, G, F, pos, origin_ray, n_bins_dev, bin_cap, pdf, cdf_row, \
-                                                      cdf_marg, s->status, D, st)                                  \
+                                                      cdf_marg, s->status, s->bin_next, D, st)                     \
                      : launch_guide<TH, false, kFused>(T, G, F, pos, origin_ray, n_bins_dev, bin_cap, pdf,         \
-                                                       cdf_row, cdf_marg, s->status, D, st);
+                                                       cdf_row, cdf_marg, s->status, s->bin_next, D, st);
     WFPG_GUIDE_CASE(64)
     WFPG_GUIDE_CASE(128)
     WFPG_GUIDE_CASE(256)

@@ -29,7 +29,8 @@ struct wfpg_svo {
     unsigned long long* tot_sum = nullptr;    // own + children (inner nodes)
     uint32_t* tot_cnt = nullptr;
     float2* value = nullptr;
-    uint32_t* status = nullptr;               // WFPG_STATUS_* bits
+    uint32_t* status = nullptr;               // WFPG_STATUS_* bits (word 0); word 1: bin_next
+    uint32_t* bin_next = nullptr;             // next bin for the field kernel's CTAs (reset per launch)
 };
 
 namespace wfpg {

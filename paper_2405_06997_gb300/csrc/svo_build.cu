@@ -660,6 +660,7 @@ int build_svo(const wfpg_scene* scene, int D, cudaStream_t st, wfpg_svo* s, std:
     WFPG_ALLOC(s->tot_cnt, 8 * (size_t)nn);
     WFPG_ALLOC(s->value, sizeof(float2) * (size_t)nn);
     WFPG_ALLOC(s->status, 16);
+    s->bin_next = s->status + 1;
     WFPG_TRY(cudaMemsetAsync(s->acc_sum, 0, 16 * (size_t)nn, st));
     WFPG_TRY(cudaMemsetAsync(s->tot_sum, 0, 16 * (size_t)nn, st));
     WFPG_TRY(cudaMemsetAsync(s->acc_cnt, 0, 8 * (size_t)nn, st));
