@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--city-only", action="store_true", help="run only the city section and print it")
     ap.add_argument("--city-frames", type=int, default=8, help="frames per proposal in the city section")
     ap.add_argument("--city-train-steps", type=int, default=200, help="online training steps on the city")
+    ap.add_argument("--no-mesh", action="store_true", help="skip the triangle-mesh section")
+    ap.add_argument("--mesh-only", action="store_true", help="run only the triangle-mesh section and print it")
     ap.add_argument("--batched-only", action="store_true",
                     help="run only the batched section with a fixed N = 32 tile (for profiling) and print it")
     return ap.parse_args()
@@ -532,6 +534,8 @@ def run_gpu(args, world, rank, local):
         line["batched"] = batched_section(args)
     if not args.no_city:
         line["city"] = city_section(args)
+    if not args.no_mesh:
+        line["mesh"] = mesh_section(args)
     if not args.no_cpu_baseline:
         t_frame, detail = oracle_frame_time(w, mis, args.cpu_bins)
         line["cpu_baseline"] = {
@@ -651,6 +655,52 @@ def batched_section(args, autotune=True):
             "mean_pixel_variance": float(v.double().mean()), "mean_radiance": float(m.double().mean()),
             "status": st["status"], "l2": "working set (path state ~0.6 GB) larger than L2", "nee": nee,
             "field_validation": field}
+
+
+def mesh_section(args, frames=10):
+    """Triangle meshes (the paper voxelises triangle scenes): the mesh room at
+    subdivision 5 (about 42k triangles: a closed box, a ceiling light of two
+    triangles, an icosphere, a rock and a torus), SVO depth 9 (SAT
+    voxelisation + k-means winding normals), then batched 1080p frames from
+    inside the room (4 guided bounces, RR, NEE with the triangle light, closest
+    hits by the SVO walk over the leaves' triangle lists), constant N = 32 and
+    the decaying resolution (64, 32, 16, 8 over the depths)."""
+    import torch
+    from paper_2405_06997_gb300 import inputs, wfpg as W
+    sc = inputs.mesh_room(args.seed, 9, subdiv=5)
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    q, sp, tr = T(sc.quads), T(sc.spheres), T(sc.tris)
+    W.svo_build(q, sp, sc.lo, sc.size, 9, tris=tr)  # first build: module load and allocator warm-up
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    svo = W.svo_build(q, sp, sc.lo, sc.size, 9, tris=tr)
+    b.record()
+    b.synchronize()
+    build_ms = a.elapsed_time(b)
+    out = {"workload": f"mesh room ({sc.n_tris} triangles), SVO depth 9, camera at (0.5, 0.5, 0.05) looking +z, "
+                       "vfov 70, 1920x1080, 4 guided bounces, RR from vertex 2, alpha 0.5, NEE, Partition-S "
+                       "l_min 2 c_ray 512, closest hits by the SVO walk",
+           "triangles": sc.n_tris, "svo_build_ms": build_ms, "svo_nodes": svo.n_nodes}
+    for name, kw in (("constant_32", dict(N=32)), ("decay_64", dict(N=64, decay=True))):
+        f = W.Frame(svo, sc, eye=(0.5, 0.5, 0.05), vfov=70.0, width=1920, height=1080, max_depth=4, rr_depth=2,
+                    alpha=0.5, l_min=2, c_ray=512, seed=args.seed, nee=True, caster=2, **kw)
+        f.run(3)
+        f.reset_image()
+        torch.cuda.synchronize()
+        a.record()
+        f.run(frames)
+        b.record()
+        b.synchronize()
+        ms = a.elapsed_time(b) / frames
+        st = f.stats()
+        m, v = f.image()
+        out[name] = {"ms_per_frame": ms, "guided_samples_per_s": st["guided_samples"] / (ms * frames / 1e3),
+                     "paths_per_depth": st["paths"], "bins_per_depth": st["bins"],
+                     "mean_pixel_variance": float(v.double().mean()), "mean_radiance": float(m.double().mean()),
+                     "status": st["status"]}
+        del f
+    return out
 
 
 def field_validation(f, svo, w, args, n_probes=16, N=32, ref_frames=64):
@@ -821,6 +871,10 @@ def main():
         import torch
         torch.cuda.set_device(local)
         print(json.dumps(city_section(args)))
+    elif args.mesh_only:
+        import torch
+        torch.cuda.set_device(local)
+        print(json.dumps(mesh_section(args)))
     elif args.batched_only:
         import torch
         torch.cuda.set_device(local)

@@ -555,3 +555,20 @@ def test_nee_frames_are_unbiased_and_less_noisy(proposal):
     mu1, s1, v1 = _frame_mean(g, w.scene, frames, mlp=mlp, alpha=0.5, seed=43, nee=True, proposal=proposal, N=32)
     assert abs(mu1 - mu0) < 5 * np.hypot(s0, s1), (mu0, mu1, s0, s1)
     assert v1 < 0.8 * v0, (v0, v1)
+
+
+def test_nee_without_lights_is_the_plain_frame():
+    """A scene with no emissive primitive has nothing to sample: nee = 1 runs
+    the same frames as nee = 0 (and both images are black)."""
+    import copy
+    w, g1, _ = box_svo(19)
+    _, g2, _ = box_svo(19)
+    sc = copy.deepcopy(w.scene)
+    sc.emission = np.zeros_like(sc.emission)
+    f1 = make_frame(g1, sc, width=64, height=36, nee=True)
+    f2 = make_frame(g2, sc, width=64, height=36, nee=False)
+    f1.run(2)
+    f2.run(2)
+    assert torch.equal(f1.image()[0], f2.image()[0])
+    assert float(f1.image()[0].abs().max()) == 0.0
+    np.testing.assert_array_equal(g1.exitance()["acc_sum"], g2.exitance()["acc_sum"])
