@@ -264,12 +264,14 @@ __global__ void __launch_bounds__(256) k_nee(FrameView F, Queue Q, int k) {
     const uint32_t path = Q.path[s];
     const uint32_t c0 = kPathStride * (uint32_t)k + 4u;
     const float us = path_uniform(F, path, c0), ua = path_uniform(F, path, c0 + 1), ub = path_uniform(F, path, c0 + 2);
-    uint32_t l = F.n_lights - 1;
-    for (uint32_t j = 0; j < F.n_lights; ++j)
-        if (F.light_cdf[j] > us) {
-            l = j;
-            break;
-        }
+    // the first light whose inclusive power CDF exceeds us (bisection; the last CDF entry is 1)
+    uint32_t lo = 0, hi = F.n_lights - 1;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (F.light_cdf[mid] > us) hi = mid;
+        else lo = mid + 1;
+    }
+    const uint32_t l = lo;
     const uint32_t prim = F.light_prim[l];
     float y[3];
     if (prim < F.pr.nq) {
