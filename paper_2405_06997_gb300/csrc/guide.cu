@@ -212,6 +212,7 @@ __device__ __forceinline__ float warp_scan_row(const float* src, float* dst, int
 // kGuideThreads threads work on one bin at a time; kStage: the chunk's cone
 // directions are computed by all threads together into shared memory before
 // the march (otherwise each lane computes its ray's direction when it takes it)
+constexpr int kDescentPerPass = 4;  // SVO levels a lane descends per pass of the walk loop
 constexpr int kWbWords = 11;  // per buffered ray: cell, d (3), 1/(d 2^D/S) (3), t, start cell (3)
 
 // direction of cell c (jittered point or centre) and its per-axis reciprocal
@@ -474,8 +475,15 @@ __global__ void __launch_bounds__(kGuideThreads, 1024 / kGuideThreads) k_guide_b
                     if (wb_dry && __all_sync(0xffffffffu, q < 0)) break;
                     if (q < 0) continue;  // idle: no ray to step
                 }
-                // ---- one step: deepest existing node holding the cell, then hit or skip its empty block
-                while (level < D) {
+                // ---- one step: deepest existing node holding the cell, then hit or skip its empty block.
+                // At most kDescentPerPass levels per pass of the loop: a lane with a deeper descent
+                // goes on in the next pass instead of holding its whole warp in this one
+                bool settled = true;
+                for (int dl = 0; level < D; ++dl) {
+                    if (dl == kDescentPerPass) {
+                        settled = false;
+                        break;
+                    }
                     const Node nd = load_node(T, s_nodes, node);
                     const int sh = D - 1 - level;
                     const int k = ((cx >> sh) & 1) | (((cy >> sh) & 1) << 1) | (((cz >> sh) & 1) << 2);
@@ -484,6 +492,7 @@ __global__ void __launch_bounds__(kGuideThreads, 1024 / kGuideThreads) k_guide_b
                     ++level;
                     stk[level * kGuideThreads] = node;
                 }
+                if (!settled) continue;
                 float L = 0.0f;
                 bool done = false;
                 if (level == D && t >= T.t_skip) {
