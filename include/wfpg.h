@@ -227,6 +227,9 @@ typedef struct wfpg_guide_params {
     int stage;         /* tuning: 1 stage cone directions in shared memory, -1 do not, 0 = default */
     uint32_t split;    /* guide_build_sample: bins with more rays than this are sampled by a second,
                           GPU-wide launch (0 = default 2048, 0xFFFFFFFF = never); results do not change */
+    uint32_t parts;    /* guide_build_pdf: the cells of a bin are traced by this many CTAs (1, 2, 4 or 8),
+                          the last one finishing the bin; 0 = auto: split while the parts of all bins
+                          fit in one wave of resident CTAs (few bins); results do not change */
 } wfpg_guide_params;
 
 /*

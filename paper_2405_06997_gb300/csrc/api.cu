@@ -191,6 +191,8 @@ int guide_build_pdf(const wfpg_svo* s, const float* pos, const uint32_t* origin_
                     void* stream) {
     if (!s || !p) return fail(WFPG_ERR_INVALID_ARG, "guide_build_pdf: null svo or params");
     if (!valid_n(p->N)) return fail(WFPG_ERR_INVALID_ARG, "guide_build_pdf: N must be 8, 16, 32, 64 or 128");
+    if (p->parts != 0 && p->parts != 1 && p->parts != 2 && p->parts != 4 && p->parts != 8)
+        return fail(WFPG_ERR_INVALID_ARG, "guide_build_pdf: parts must be 0, 1, 2, 4 or 8");
     if (!(p->eps >= 0.0f)) return fail(WFPG_ERR_INVALID_ARG, "guide_build_pdf: eps must be >= 0");
     if (p->block != 0 && p->block != 64 && p->block != 128 && p->block != 256)
         return fail(WFPG_ERR_INVALID_ARG, "guide_build_pdf: block must be 0, 64, 128 or 256");

@@ -309,7 +309,8 @@ __global__ void __launch_bounds__(kGuideThreads, 1024 / kGuideThreads) k_guide_b
                                                                uint32_t bin_cap, float* __restrict__ pdf,
                                                                float* __restrict__ cdf_row,
                                                                float* __restrict__ cdf_marg, uint32_t* status,
-                                                               uint32_t* __restrict__ bin_next) {
+                                                               uint32_t* __restrict__ bin_next, int parts_arg,
+                                                               uint32_t slots) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int N = G.N, NN = N * N;
     const int D = T.D;
@@ -340,11 +341,26 @@ __global__ void __launch_bounds__(kGuideThreads, 1024 / kGuideThreads) k_guide_b
     const float fres = (float)res;
     const float INF = __int_as_float(0x7f800000);
     const int cap = 3 * res + 16;
-    // bins are taken dynamically: the first one by CTA index, the next from a
-    // counter (zeroed before the launch) as each CTA finishes, so that cheap and
-    // expensive bins even out across the persistent CTAs
-    __shared__ uint32_t s_bin;
-    for (uint32_t b = blockIdx.x; b < nb;) {
+    // Work units are (bin, part): the cells of a bin are split over `parts` CTAs
+    // (1 for the fused call); the CTA that completes a bin's last part gathers its
+    // field and finishes the bin.  Units are taken dynamically: the first by CTA
+    // index, the next from a counter (zeroed before the launch) as each CTA
+    // finishes one, so that cheap and expensive units even out.  By default a bin
+    // is split only while its parts still fit in one wave of resident CTAs: with
+    // few bins the idle SMs take parts of them; with a wave of bins or more,
+    // splitting only adds each part's tail.
+    int parts = kFused ? 1 : parts_arg;
+    if (!kFused && parts == 0) {
+        parts = 1;
+        while (parts < 8 && (uint64_t)nb * (uint64_t)(2 * parts) <= slots) parts *= 2;
+    }
+    const int part_cells = NN / parts;
+    const uint32_t n_units = nb * (uint32_t)parts;
+    __shared__ uint32_t s_unit;
+    __shared__ int s_last;
+    for (uint32_t u = blockIdx.x; u < n_units;) {
+        const uint32_t b = u / (uint32_t)parts;
+        const int cbeg = (int)(u % (uint32_t)parts) * part_cells, cend = cbeg + part_cells;
         const uint32_t r = origin_ray ? origin_ray[b] : b;
         float ox = 0.0f, oy = 0.0f, oz = 0.0f;
         if (r != kNone) {
@@ -358,9 +374,10 @@ __global__ void __launch_bounds__(kGuideThreads, 1024 / kGuideThreads) k_guide_b
         const bool inside = gx >= 0.0f && gx <= fres && gy >= 0.0f && gy <= fres && gz >= 0.0f && gz <= fres;
         const uint64_t jseed = purpose(G.seed, kJitterPurpose);
         const uint64_t jstream = bin_stream(G.frame_dev ? *G.frame_dev : G.frame, b);
-        for (int c0 = 0; c0 < NN; c0 += chunk) {
+        for (int c0 = cbeg; c0 < cend; c0 += chunk) {
+            const int cn = min(chunk, cend - c0);  // cells in this chunk
             // ---- directions of this chunk's cells, computed by all threads together
-            for (int q = tid; kStage && q < chunk; q += kGuideThreads) {
+            for (int q = tid; kStage && q < cn; q += kGuideThreads) {
                 float3 d, iv;
                 cell_ray(T, G, c0 + q, jseed, jstream, tn, &d, &iv);
                 s_ray[0 * chunk + q] = d.x;
@@ -373,7 +390,7 @@ __global__ void __launch_bounds__(kGuideThreads, 1024 / kGuideThreads) k_guide_b
             if (tid == 0) s_next = 0;
             __syncthreads();
             // ---- cone rays: each lane marches one cell's ray; finished lanes take the next cell
-            int q = -1;  // current cell of the chunk (-1: none, >= chunk: no work left)
+            int q = -1;  // current cell of the chunk (-1: none, >= cn: no work left)
             float dx = 0.f, dy = 0.f, dz = 0.f, ivx = 0.f, ivy = 0.f, ivz = 0.f, t = 0.f;
             int cx = 0, cy = 0, cz = 0, level = 0, steps = 0;
             uint32_t node = 0;
@@ -391,7 +408,7 @@ __global__ void __launch_bounds__(kGuideThreads, 1024 / kGuideThreads) k_guide_b
                         base = __shfl_sync(0xffffffffu, base, leader);
                         if (idle) {
                             q = base + __popc(need & lt);
-                            if (q < chunk) {
+                            if (q < cn) {
                                 dx = s_ray[0 * chunk + q];
                                 dy = s_ray[1 * chunk + q];
                                 dz = s_ray[2 * chunk + q];
@@ -414,8 +431,8 @@ __global__ void __launch_bounds__(kGuideThreads, 1024 / kGuideThreads) k_guide_b
                     }
                     // leave only when every lane has run out of cells (a lane whose new ray
                     // died at its start is idle again and fetches once more)
-                    if (__all_sync(0xffffffffu, q >= chunk)) break;
-                    if (q < 0 || q >= chunk) continue;  // idle, or out of cells: no ray to step
+                    if (__all_sync(0xffffffffu, q >= cn)) break;
+                    if (q < 0 || q >= cn) continue;  // idle, or out of cells: no ray to step
                 } else {
                     // the whole warp sets up the next 32 cells' rays at once (converged), so a
                     // lane that finishes a ray takes a ready one instead of stalling its warp
@@ -424,7 +441,7 @@ __global__ void __launch_bounds__(kGuideThreads, 1024 / kGuideThreads) k_guide_b
                         int base = 0;
                         if (lane == 0) base = atomicAdd(&s_next, 32);
                         base = __shfl_sync(0xffffffffu, base, 0);
-                        wb_n = max(0, min(32, chunk - base));
+                        wb_n = max(0, min(32, cn - base));
                         wb_head = 0;
                         wb_dry = wb_n == 0;
                         if (lane < wb_n) {
@@ -566,7 +583,23 @@ __global__ void __launch_bounds__(kGuideThreads, 1024 / kGuideThreads) k_guide_b
             }
             __syncthreads();
         }
-        if (G.blur) {
+        bool finish = true;
+        if (parts > 1) {  // publish this part's cells; the CTA of the bin's last part gathers them all
+            float* gf = pdf + (size_t)b * NN;  // the bin's pdf row holds the field until it is finished
+            for (int c = cbeg + tid; c < cend; c += kGuideThreads) gf[c] = field[c];
+            __threadfence();
+            __syncthreads();
+            if (tid == 0)
+                s_last = atomicAdd(reinterpret_cast<uint32_t*>(cdf_marg + (size_t)b * N), 1u) == (uint32_t)(parts - 1);
+            __syncthreads();
+            finish = s_last != 0;
+            if (finish) {
+                __threadfence();
+                for (int c = tid; c < NN; c += kGuideThreads) field[c] = __ldcg(gf + c);
+                __syncthreads();
+            }
+        }
+        if (finish && G.blur) {
             for (int c = tid; c < NN; c += kGuideThreads) {
                 const int i = c % N, j = c / N;
                 const float up = (j > 0) ? field[(j - 1) * N + i] : field[N - 1 - i];
@@ -585,16 +618,18 @@ __global__ void __launch_bounds__(kGuideThreads, 1024 / kGuideThreads) k_guide_b
             __syncthreads();
         }
         // row CDFs (one warp per row) into tmp, row totals into rowtot
-        for (int j = warp; j < N; j += kWarps) {
+        for (int j = warp; finish && j < N; j += kWarps) {
             const float tot = warp_scan_row(field + j * N, tmp + j * N, N, lane);
             if (lane == 0) rowtot[j] = tot;
         }
         __syncthreads();
-        if (warp == 0) warp_scan_row(rowtot, marg, N, lane);
+        if (finish && warp == 0) warp_scan_row(rowtot, marg, N, lane);
         __syncthreads();
         const float den = __fmul_rn(marg[N - 1], kFourPi);
         const float nn = (float)NN;
-        if (!kFused) {
+        if (!finish) {
+            // another part of this bin finishes it
+        } else if (!kFused) {
             float* gp = pdf + (size_t)b * NN;
             float* gc = cdf_row + (size_t)b * NN;
             for (int c = tid; c < NN; c += kGuideThreads) {
@@ -633,9 +668,9 @@ __global__ void __launch_bounds__(kGuideThreads, 1024 / kGuideThreads) k_guide_b
                 sample_ray(F, F.ray_order[k], field, tmp, marg, N, nn, den, tn);
         }
         __syncthreads();
-        if (tid == 0) s_bin = gridDim.x + atomicAdd(bin_next, 1u);
+        if (tid == 0) s_unit = gridDim.x + atomicAdd(bin_next, 1u);
         __syncthreads();
-        b = s_bin;
+        u = s_unit;
     }
 }
 
@@ -803,11 +838,18 @@ static size_t guide_smem_bytes(uint32_t smem_nodes, int N, int D, int threads, b
            sizeof(float) * (rays + 2 * NN + 2 * (size_t)N);
 }
 
+// zeroes the per-bin part counters (the first word of each bin's cdf_marg row)
+__global__ void k_zero_part_counters(float* cdf_marg, int N, const uint32_t* n_bins_dev, uint32_t bin_cap) {
+    const uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t nb = n_bins_dev ? min(*n_bins_dev, bin_cap) : bin_cap;
+    if (b < nb) reinterpret_cast<uint32_t*>(cdf_marg)[(size_t)b * N] = 0u;
+}
+
 template <int kThreads, bool kStage, bool kFused>
 static int launch_guide(const TraceArgs& T, const GuideArgs& G, const FusedArgs& F, const float* pos,
                         const uint32_t* origin_ray, const uint32_t* n_bins_dev, uint32_t bin_cap, float* pdf,
                         float* cdf_row, float* cdf_marg, uint32_t* status, uint32_t* bin_next, int D,
-                        cudaStream_t st) {
+                        int parts_param, cudaStream_t st) {
     auto kernel = k_guide_build<kThreads, kStage, kFused>;
     const size_t smem = guide_smem_bytes(T.smem_nodes, G.N, D, kThreads, kStage);
     if (smem > 48 * 1024 &&
@@ -818,10 +860,17 @@ static int launch_guide(const TraceArgs& T, const GuideArgs& G, const FusedArgs&
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, smem);
     if (per_sm < 1) return WFPG_ERR_INVALID_ARG;  // the field does not fit in shared memory
-    const uint32_t grid = (uint32_t)std::min<uint64_t>(bin_cap, (uint64_t)sms * per_sm);
+    // parts per bin (unfused only; 0: chosen in the kernel from the device-side bin count)
+    const uint64_t slots = (uint64_t)sms * per_sm;
+    int parts = kFused ? 1 : parts_param;
+    if (parts == 0 && (uint64_t)bin_cap * 2 > slots) parts = 1;  // the kernel could not split either
+    const uint64_t most = parts == 0 ? 8 : (uint64_t)parts;
+    const uint32_t grid = (uint32_t)std::min<uint64_t>((uint64_t)bin_cap * most, slots);
     if (cudaMemsetAsync(bin_next, 0, sizeof(uint32_t), st) != cudaSuccess) return WFPG_ERR_CUDA;
+    if (parts != 1)
+        WFPG_LAUNCH(k_zero_part_counters, div_up(bin_cap, 256), 256, 0, st, cdf_marg, G.N, n_bins_dev, bin_cap);
     WFPG_LAUNCH(kernel, grid, kThreads, smem, st, T, G, F, pos, origin_ray, n_bins_dev, bin_cap, pdf, cdf_row,
-                cdf_marg, status, bin_next);
+                cdf_marg, status, bin_next, parts, (uint32_t)std::min<uint64_t>(slots, 0xFFFFFFFFull));
     return cudaGetLastError() == cudaSuccess ? WFPG_OK : WFPG_ERR_CUDA;
 }
 
@@ -862,9 +911,10 @@ static int dispatch_guide(const wfpg_svo* s, const wfpg_guide_params* p, const T
 #define WFPG_GUIDE_CASE(TH)                                                                                        \
     if (threads == TH)                                                                                             \
         return stage ? launch_guide<TH, true, kFused>(T, G, F, pos, origin_ray, n_bins_dev, bin_cap, pdf, cdf_row, \
-                                                      cdf_marg, s->status, s->bin_next, D, st)                     \
+                                                      cdf_marg, s->status, s->bin_next, D, (int)p->parts, st)      \
                      : launch_guide<TH, false, kFused>(T, G, F, pos, origin_ray, n_bins_dev, bin_cap, pdf,         \
-                                                       cdf_row, cdf_marg, s->status, s->bin_next, D, st);
+                                                       cdf_row, cdf_marg, s->status, s->bin_next, D,              \
+                                                       (int)p->parts, st);
     WFPG_GUIDE_CASE(64)
     WFPG_GUIDE_CASE(128)
     WFPG_GUIDE_CASE(256)

@@ -61,7 +61,7 @@ class BinParams(C.Structure):
 class GuideParams(C.Structure):
     _fields_ = [("N", I32), ("eps", F), ("jitter", I32), ("blur", I32), ("t_skip", F),
                 ("cos_weight", I32), ("seed", U64), ("frame", U32), ("block", I32), ("stage", I32),
-                ("split", U32)]
+                ("split", U32), ("parts", U32)]
 
 
 FRAME_MAX_DEPTH = 8
@@ -319,7 +319,7 @@ def default_t_skip(size: float, depth: int) -> float:
 
 def guide_build_pdf(svo: SVO, pos, origin_ray=None, n_bins=None, bin_cap=None, *, N=16, eps=1e-2,
                     jitter=False, blur=False, t_skip=None, cos_weight=False, seed=1, frame=0,
-                    block=0, stage=0, out=None, stream=None):
+                    block=0, stage=0, parts=0, out=None, stream=None):
     """GuideRays field + PDF/CDF (Alg. 3).  Returns (pdf, cdf_row, cdf_marg)."""
     if bin_cap is None:
         bin_cap = origin_ray.numel() if origin_ray is not None else pos.shape[0]
@@ -332,7 +332,7 @@ def guide_build_pdf(svo: SVO, pos, origin_ray=None, n_bins=None, bin_cap=None, *
                torch.empty((bin_cap, N), dtype=torch.float32, device=dev))
     pdf, cr, cm = out
     p = GuideParams(N=N, eps=eps, jitter=int(jitter), blur=int(blur), t_skip=t_skip,
-                    cos_weight=int(cos_weight), seed=seed, frame=frame, block=block, stage=stage)
+                    cos_weight=int(cos_weight), seed=seed, frame=frame, block=block, stage=stage, parts=parts)
     _check(lib().guide_build_pdf(svo.handle, _ptr(pos, torch.float32, what="pos"),
                                  _ptr(origin_ray, torch.int32, what="origin_ray"),
                                  _ptr(n_bins, torch.int32, 1, "n_bins"), bin_cap, C.byref(p),
