@@ -371,7 +371,7 @@ WFPG_API int guide_eval_pdf(const float* pdf, int N, uint32_t bin_cap, const uin
  * (tcgen05), float32 master weights and Adam.  It is trained online on the
  * SVO-traced fields of guide_build_pdf with the loss KL(q || softmax(z)), q
  * the traced field normalised per bin; the traced PDF stays the fallback and
- * the judge of the learned one.
+ * the reference the learned one is scored against.
  *
  * Parameters (WFPG_MLP_PARAMS float32, in this order): W1[64][80] (inputs
  * padded with two zero columns), b1[64], W2[64][64], b2[64], W3[64][64],
