@@ -246,6 +246,16 @@ def test_frame_rejects_bad_params():
         f.set_params(max_depth=3)
     with pytest.raises(W.WfpgError):
         f.set_params(N=12)
+    with pytest.raises(W.WfpgError):
+        f.set_params(nee=2)
+    with pytest.raises(W.WfpgError):
+        f.set_params(combine=6)
+    # probe mode: width must be probe_n^2, probe_n in [1, 1024]
+    pts = np.full((3, 3), 0.5, np.float32)
+    with pytest.raises(W.WfpgError):
+        make_frame(g, w.scene, probes=pts, probe_n=2000)
+    f2 = make_frame(g, w.scene, probes=pts, probe_n=4, max_depth=1)
+    assert f2.pixels == 3 * 16
 
 
 # ------------------------------------------------- table-based mixture sampling

@@ -157,6 +157,8 @@ def test_invalid_arguments_raise():
         W.guide_build_pdf(g, dev(w.ray_pos), bin_cap=2, N=12)
     assert e.value.code == -1
     with pytest.raises(W.WfpgError):
+        W.guide_build_pdf(g, dev(w.ray_pos), bin_cap=2, N=16, parts=3)
+    with pytest.raises(W.WfpgError):
         W.svo_build(dev(w.scene.quads), dev(w.scene.spheres), w.scene.lo, 1.0, 12)
     empty_q = np.array([[0, 5.0, 5.0, 6.0, 5.0, 6.0, 1.0, 0.0]], np.float32)  # outside the box
     with pytest.raises(W.WfpgError):
@@ -339,4 +341,22 @@ def test_depth_11_end_to_end_exact():
     sel = np.arange(0, nb, max(1, nb // 12))
     og = o.guide_build(rp[ro["origin_ray"][sel]], sel, 16, jitter=True, blur=True, seed=4, frame=1)
     assert np.array_equal(pdf.cpu().numpy()[sel], og["pdf"])
+    assert g.status() == 0
+
+
+@pytest.mark.parametrize("parts", [2, 8])
+def test_split_bins_give_identical_tables(parts):
+    """A bin's cells traced by several CTAs (the last one finishing the bin)
+    give the same tables as one CTA per bin, bit for bit."""
+    w = inputs.tiny_box(8, n_rays=4099)
+    g, o = build_both(w.scene, w.depth)
+    W.svo_accumulate(g, dev(w.rec_pos), dev(w.rec_wout), dev(w.rec_L))
+    pos = dev(w.ray_pos)
+    r = W.bin_rays(g, pos, l_min=2, seed=3, frame=1)
+    kw = dict(N=32, jitter=True, blur=True, seed=3, frame=1)
+    one = W.guide_build_pdf(g, pos, r["origin_ray"], r["n_bins"], r["bin_cap"], parts=1, **kw)
+    split = W.guide_build_pdf(g, pos, r["origin_ray"], r["n_bins"], r["bin_cap"], parts=parts, **kw)
+    nb = int(r["n_bins"].item())
+    for a, b in zip(one, split):
+        assert torch.equal(a[:nb], b[:nb])
     assert g.status() == 0
