@@ -143,7 +143,46 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm_tn(GemmArgs g) {
     }
     if (!ok && lane == 0) atomicOr(g.status, (uint32_t)WFPG_STATUS_MMA_TIMEOUT);
     tc::fence_after_sync();
-    if (ok && kc1 > kc0) {
+    bool staged = false;
+    if (EPI == kEpiF32 && BN == 256 && ok && kc1 > kc0 && m0 + 128 <= g.M && n0 + BN <= g.N && (g.ldc & 3) == 0 &&
+        ((uintptr_t)g.C & 15) == 0) {
+        // The wide f32 tile (the logits) goes out through shared memory, 64 columns at a
+        // time: each thread moves its TMEM row into a padded staging row, then the CTA
+        // writes whole 256-byte row segments (a thread per row would scatter every store
+        // over 32 rows).  The MMAs have finished reading the operand tiles, so their
+        // shared memory holds the staging slice.
+        constexpr int kSlice = 64, kLd = kSlice + 4;
+        float* stage = reinterpret_cast<float*>(gemm_smem);
+        for (int s0 = 0; s0 < BN; s0 += kSlice) {
+#pragma unroll
+            for (int c = 0; c < kSlice; c += 16) {
+                float v[16];
+                tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(s0 + c), v);
+                float* srow = stage + (warp * 32 + lane) * kLd + c;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    float4 o = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+                    if (g.bias) {
+                        const float* bb = g.bias + n0 + s0 + c + 4 * q;
+                        o.x += bb[0];
+                        o.y += bb[1];
+                        o.z += bb[2];
+                        o.w += bb[3];
+                    }
+                    *reinterpret_cast<float4*>(srow + 4 * q) = o;
+                }
+            }
+            __syncthreads();
+            for (int it = tid; it < 128 * (kSlice / 4); it += kGemmThreads) {
+                const int r = it / (kSlice / 4), c4 = it % (kSlice / 4);
+                *reinterpret_cast<float4*>(g.C + (size_t)(m0 + r) * g.ldc + n0 + s0 + 4 * c4) =
+                    *reinterpret_cast<const float4*>(stage + r * kLd + 4 * c4);
+            }
+            __syncthreads();
+        }
+        staged = true;
+    }
+    if (ok && kc1 > kc0 && !staged) {
         const int row = m0 + warp * 32 + lane;
         for (int c0 = 0; c0 < BN; c0 += 16) {
             float v[16];
