@@ -301,7 +301,7 @@ __device__ __forceinline__ bool ray_start(const TraceArgs& T, bool has_origin, b
 // 1024 resident threads per SM (32 warps): up to 64 registers a thread.  The
 // walk is issue-bound, and 64 registers (fewer recomputed values) beat 48
 // registers with 40 warps on the GB300; the fused variant gets the same budget
-template <int kGuideThreads, bool kStage, bool kFused>
+template <int kGuideThreads, bool kStage, bool kFused, bool kSplit>
 __global__ void __launch_bounds__(kGuideThreads, 1024 / kGuideThreads) k_guide_build(TraceArgs T, GuideArgs G, FusedArgs F,
                                                                const float* __restrict__ pos,
                                                                const uint32_t* __restrict__ origin_ray,
@@ -349,8 +349,8 @@ __global__ void __launch_bounds__(kGuideThreads, 1024 / kGuideThreads) k_guide_b
     // is split only while its parts still fit in one wave of resident CTAs: with
     // few bins the idle SMs take parts of them; with a wave of bins or more,
     // splitting only adds each part's tail.
-    int parts = kFused ? 1 : parts_arg;
-    if (!kFused && parts == 0) {
+    int parts = (kFused || !kSplit) ? 1 : parts_arg;
+    if (kSplit && !kFused && parts == 0) {
         parts = 1;
         while (parts < 8 && (uint64_t)nb * (uint64_t)(2 * parts) <= slots) parts *= 2;
     }
@@ -845,25 +845,44 @@ __global__ void k_zero_part_counters(float* cdf_marg, int N, const uint32_t* n_b
     if (b < nb) reinterpret_cast<uint32_t*>(cdf_marg)[(size_t)b * N] = 0u;
 }
 
+// resident CTAs of `kernel` on the whole GPU (0 when the field does not fit), after
+// raising its dynamic shared-memory limit where needed
+template <typename Kernel>
+static uint64_t guide_slots(Kernel kernel, int threads, size_t smem, int* rc) {
+    *rc = WFPG_OK;
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        *rc = WFPG_ERR_CUDA;
+        return 0;
+    }
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
+    if (per_sm < 1) *rc = WFPG_ERR_INVALID_ARG;  // the field does not fit in shared memory
+    return (uint64_t)sms * (uint64_t)(per_sm > 0 ? per_sm : 0);
+}
+
 template <int kThreads, bool kStage, bool kFused>
 static int launch_guide(const TraceArgs& T, const GuideArgs& G, const FusedArgs& F, const float* pos,
                         const uint32_t* origin_ray, const uint32_t* n_bins_dev, uint32_t bin_cap, float* pdf,
                         float* cdf_row, float* cdf_marg, uint32_t* status, uint32_t* bin_next, int D,
                         int parts_param, cudaStream_t st) {
-    auto kernel = k_guide_build<kThreads, kStage, kFused>;
+    // one CTA per bin unless the unfused call may split bins (a separate instantiation:
+    // the split bookkeeping costs the one-CTA kernel registers and residency)
+    auto kernel = k_guide_build<kThreads, kStage, kFused, false>;
     const size_t smem = guide_smem_bytes(T.smem_nodes, G.N, D, kThreads, kStage);
-    if (smem > 48 * 1024 &&
-        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-        return WFPG_ERR_CUDA;
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, smem);
-    if (per_sm < 1) return WFPG_ERR_INVALID_ARG;  // the field does not fit in shared memory
+    int rc = WFPG_OK;
+    uint64_t slots = guide_slots(kernel, kThreads, smem, &rc);
+    if (rc != WFPG_OK) return rc;
     // parts per bin (unfused only; 0: chosen in the kernel from the device-side bin count)
-    const uint64_t slots = (uint64_t)sms * per_sm;
     int parts = kFused ? 1 : parts_param;
     if (parts == 0 && (uint64_t)bin_cap * 2 > slots) parts = 1;  // the kernel could not split either
+    if (!kFused && parts != 1) {
+        kernel = k_guide_build<kThreads, kStage, kFused, !kFused>;
+        slots = guide_slots(kernel, kThreads, smem, &rc);
+        if (rc != WFPG_OK) return rc;
+    }
     const uint64_t most = parts == 0 ? 8 : (uint64_t)parts;
     const uint32_t grid = (uint32_t)std::min<uint64_t>((uint64_t)bin_cap * most, slots);
     if (cudaMemsetAsync(bin_next, 0, sizeof(uint32_t), st) != cudaSuccess) return WFPG_ERR_CUDA;
