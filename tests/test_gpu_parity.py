@@ -87,6 +87,33 @@ def test_accumulate_exact():
         np.testing.assert_array_equal(ge[k][inner], oe[k][inner], err_msg=k)
 
 
+def test_accumulate_over_many_small_batches():
+    """300 small batches, each landing in a different corner of the box, leave
+    exactly the oracle's running sums and bottom-up averages; after a reset one
+    batch gives a fresh tree's values."""
+    w = inputs.tiny_box(3, n_records=30_000)
+    g, o = build_both(w.scene, w.depth)
+    order = np.argsort(w.rec_pos[:, 0] + 2 * w.rec_pos[:, 1] + 4 * w.rec_pos[:, 2])
+    chunks = np.array_split(order, 300)
+    for c in chunks:
+        W.svo_accumulate(g, dev(w.rec_pos[c]), dev(w.rec_wout[c]), dev(w.rec_L[c]))
+        o.accumulate(w.rec_pos[c], w.rec_wout[c], w.rec_L[c])
+    ge, oe = g.exitance(), o.exitance()
+    lo = g.level_off
+    inner = slice(0, int(lo[w.depth]))
+    for k in ("acc_sum", "acc_cnt", "value"):
+        np.testing.assert_array_equal(ge[k], oe[k], err_msg=k)
+    for k in ("tot_sum", "tot_cnt"):
+        np.testing.assert_array_equal(ge[k][inner], oe[k][inner], err_msg=k)
+    # a reset, then one batch
+    g.reset_exitance()
+    o2 = oracle.SVO(w.scene, w.depth)
+    c = chunks[7]
+    W.svo_accumulate(g, dev(w.rec_pos[c]), dev(w.rec_wout[c]), dev(w.rec_L[c]))
+    o2.accumulate(w.rec_pos[c], w.rec_wout[c], w.rec_L[c])
+    np.testing.assert_array_equal(g.exitance()["value"], o2.exitance()["value"])
+
+
 def test_accumulate_empty_batch():
     w = inputs.tiny_box(1)
     g, o = build_both(w.scene, w.depth)
