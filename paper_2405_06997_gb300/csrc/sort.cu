@@ -100,21 +100,29 @@ void scan_exclusive(const uint32_t* in, uint32_t* out, uint32_t n, uint32_t* tot
 }
 
 // ---------------------------------------------------------------------------
+// per-tile digit counts: each warp counts into its own sub-histogram (keys that
+// are already partly sorted by earlier passes would otherwise pile onto a few
+// shared-memory counters), then the sub-histograms are summed per digit
 template <typename K>
 __global__ void __launch_bounds__(kSortBlock) k_radix_hist(const K* __restrict__ keys, uint32_t n,
                                                            int shift, uint32_t* __restrict__ hist,
                                                            uint32_t tiles) {
-    __shared__ uint32_t h[256];
-    h[threadIdx.x] = 0;
+    constexpr int W = kSortBlock / 32;
+    __shared__ uint32_t h[W][256];
+    const int w = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < W * 256; i += kSortBlock) (&h[0][0])[i] = 0u;
     __syncthreads();
     const uint32_t base = blockIdx.x * kSortTile;
 #pragma unroll 4
     for (int r = 0; r < kSortItems; ++r) {
         const uint32_t e = base + r * kSortBlock + threadIdx.x;
-        if (e < n) atomicAdd(&h[(uint32_t)(keys[e] >> shift) & 255u], 1u);
+        if (e < n) atomicAdd(&h[w][(uint32_t)(keys[e] >> shift) & 255u], 1u);
     }
     __syncthreads();
-    hist[threadIdx.x * tiles + blockIdx.x] = h[threadIdx.x];
+    uint32_t sum = 0u;
+#pragma unroll
+    for (int ww = 0; ww < W; ++ww) sum += h[ww][threadIdx.x];
+    hist[threadIdx.x * tiles + blockIdx.x] = sum;
 }
 
 template <typename K, bool kVals>
