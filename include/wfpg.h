@@ -445,7 +445,8 @@ WFPG_API int guide_learned_train_step(wfpg_mlp* mlp, const float* pos, const flo
  * in device memory advances after each frame and keys every random stream
  * (bins' origins, cell jitter, per-path uniforms: SplitMix64 counters).
  * The emitted radiance and albedo of a hit come from per-primitive device
- * arrays (quads first, then spheres); a primitive with albedo 0 ends a path.
+ * arrays (quads first, then spheres, then triangles); a primitive with albedo
+ * 0 ends a path.
  * Per-pixel sums of the path estimate and of its square accumulate over
  * frames (frame_image gives mean and variance of the mean).
  */
@@ -510,7 +511,10 @@ typedef struct wfpg_frame_stats {
  * and scene (device pointers, not owned).  W x H x (WFPG_FRAME_MAX_DEPTH + 1)
  * must stay below 2^32 (32-bit record indices; about 477M pixels).  emission, albedo: device float
  * arrays, one per primitive.  Allocates the path state (about
- * 4 * W * H * (12 * (max_depth + 1) + 48) bytes).  Synchronises `stream`. */
+ * 4 * W * H * (14 * (max_depth + 1) + 52) bytes, with the light-sample buffers) and builds the
+ * light table from the scene (emissive primitives, chosen in proportion to emission x area).
+ * Errors: invalid camera or parameters give WFPG_ERR_INVALID_ARG (probe mode: probe_n outside
+ * 1 .. 1024 or width != probe_n^2); failed allocations WFPG_ERR_OOM.  Synchronises `stream`. */
 WFPG_API int frame_create(wfpg_svo* svo, const wfpg_scene* scene, const float* emission, const float* albedo,
                           const wfpg_camera* cam, const wfpg_frame_params* p, wfpg_frame** out, void* stream);
 WFPG_API int frame_destroy(wfpg_frame* f);
