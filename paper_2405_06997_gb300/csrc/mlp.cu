@@ -64,7 +64,7 @@ struct GemmArgs {
 
 constexpr int kGemmThreads = 128;
 constexpr int kSplitsW4 = 64;       // K splits of the output layer's weight gradient (8 row tiles each)
-constexpr int kSplitsHidden = 256;  // K splits of the hidden layers' weight gradients
+constexpr int kSplitsHidden = 512;  // K splits of the hidden layers' weight gradients (one 128-row chunk each)
 // K elements per pipeline step: 128 for narrow tiles (more bytes in flight per
 // CTA on the long-K weight-gradient GEMMs), 64 for the 256-wide logits tile
 template <int BN>
