@@ -474,7 +474,7 @@ struct DevBuf {
     } while (0)
 #define WFPG_ALLOC(buf, bytes)                                          \
     do {                                                                \
-        cudaError_t e_ = cudaMalloc(&(buf), (bytes) ? (bytes) : 16);    \
+        cudaError_t e_ = cudaMalloc(&(buf), (bytes) != 0 ? (bytes) : 16); \
         if (e_ != cudaSuccess) {                                        \
             err = std::string("device allocation of ") + std::to_string((size_t)(bytes)) + \
                   " bytes failed: " + cudaGetErrorString(e_);           \
