@@ -87,7 +87,7 @@ void product_sample_one(const float* pdf, const float* S, int N, const float n[3
     const float lo = B > 0 ? C[B - 1] : 0.0f;
     const float u0p = clamp_unit((t - lo) / (C[B] - lo));
     const int b = N / 8, i0 = (B % 8) * b, j0 = (B / 8) * b;
-    float CR[16];
+    float CR[16] = {};
     float acc = 0.0f;
     for (int r = 0; r < b; ++r) {
         float s = 0.0f;
@@ -101,7 +101,7 @@ void product_sample_one(const float* pdf, const float* S, int N, const float n[3
         if (CR[k] > t0) { r = k; break; }
     const float rlo = r > 0 ? CR[r - 1] : 0.0f;
     const float beta_r = clamp_unit((t0 - rlo) / (CR[r] - rlo));
-    float CC[16];
+    float CC[16] = {};
     acc = 0.0f;
     for (int c = 0; c < b; ++c) {
         acc = acc + pdf[(j0 + r) * N + i0 + c];
