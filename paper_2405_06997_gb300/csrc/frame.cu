@@ -336,7 +336,8 @@ __global__ void __launch_bounds__(256) k_shade(FrameView F, Queue Q, const float
             const float w = pl > 0.0f ? pl * pl / (pl * pl + pm * pm) : 0.0f;
             const size_t vc = (size_t)k * F.P + path;
             // per unit T(p_k): the continuation's roulette factor Q.T / T(p_k) applies
-            F.vNee[vc] = w * F.nee_l[s] * (Q.T[s] / F.vT[vc]);
+            const float tk = F.vT[vc];
+            F.vNee[vc] = tk > 0.0f ? w * F.nee_l[s] * (Q.T[s] / tk) : 0.0f;
         }
         if (p > 0.0f && cs > 0.0f) {
             float T = Q.T[s] * (Q.alb[s] * kInvPi) * cs / p;
