@@ -169,3 +169,19 @@ def test_mesh_room_voxels_cover_its_surface():
     g = np.clip(np.floor(pos.astype(np.float64) * (1 << D)), 0, (1 << D) - 1).astype(int)
     for x, y, z in g:
         assert oracle.morton(int(x), int(y), int(z)) in leaves
+
+
+def test_mesh_room_windings_and_light():
+    """The generator's windings: the room's walls face inward, the meshes'
+    triangles outward (away from their centres / the torus tube), the light's
+    two triangles face down and cover [0.35, 0.65]^2."""
+    sc = inputs.mesh_room(1, 7, subdiv=2)
+    t = sc.tris.astype(np.float64).reshape(-1, 3, 3)
+    n = np.cross(t[:, 1] - t[:, 0], t[:, 2] - t[:, 0])
+    c = t.mean(axis=1)
+    assert np.all(np.einsum("ij,ij->i", n[:12], 0.5 - c[:12]) > 0)          # walls inward
+    assert np.all(n[12:14, 1] < 0) and np.all(sc.emission[12:14] == 10.0)  # light faces down
+    np.testing.assert_allclose(inputs.tri_area(sc.tris[12:14]).sum(), 0.09, rtol=1e-6)
+    ico = slice(14, 14 + 320)
+    assert np.all(np.einsum("ij,ij->i", n[ico], c[ico] - np.array([0.3, 0.25, 0.6])) > 0)
+    assert np.all(sc.albedo[:12] >= 0.3) and np.all(sc.albedo[12:14] == 0.0)
