@@ -11,7 +11,9 @@ adds around the guiding calls:
 * radiance records by back-propagation along a path (Sec. 3.2, Eq. 5):
   the radiance leaving vertex p_k toward p_{k-1} is T(p_n) / T(p_k) times the
   emission found at p_n, summed over every emitter vertex p_n at or after p_k
-  (zero when the path finds no emitter after p_k).
+  (zero when the path finds no emitter after p_k);
+* the sample-combination heuristics across frames (Sec. 3.7, Eq. 7): the
+  image is the h(i)-weighted average of the per-frame images.
 
 Only the tests import this module.
 """
@@ -83,3 +85,45 @@ def eq5_records(T, Le, nv, Le_seen=None):
             out_k.append(k + 1)
             out_L.append(Le[i, k] + sum(T[i, m] / T[i, k] * Ls[i, m] for m in range(k + 1, int(nv[i]))))
     return np.array(out_p, np.int64), np.array(out_k, np.int64), np.array(out_L, np.float64)
+
+
+HEURISTICS = ("constant", "linear", "quadratic", "one-two", "discard-first", "pt-first")
+
+
+def combine_weight(kind, i):
+    """h(i) of the sample-combination heuristics (Sec. 3.7) for frame i
+    (1-based): constant 1; linear i below 5, else 5; quadratic i^2 below 5,
+    else 25; one-two 1 for the first frame, else 2; discard-first 0 for the
+    first frame, else 1; PT first weighs its frames equally (its first frame
+    is traced without guiding, which the frame itself decides)."""
+    i = int(i)
+    if i < 1:
+        raise ValueError("frames are counted from 1")
+    if kind == "linear":
+        return float(i) if i < 5 else 5.0
+    if kind == "quadratic":
+        return float(i * i) if i < 5 else 25.0
+    if kind == "one-two":
+        return 1.0 if i == 1 else 2.0
+    if kind == "discard-first":
+        return 0.0 if i == 1 else 1.0
+    if kind in ("constant", "pt-first"):
+        return 1.0
+    raise ValueError(f"unknown heuristic {kind!r}")
+
+
+def combine_images(S, kind, W=None):
+    """Eq. 7: I = sum_i W_i S_i h(i) / sum_i W_i h(i) over the frames' images
+    S[i - 1] (any shape after the first axis), summed in frame order in
+    float64.  W_i (default 1: every frame is one sample per pixel) weighs a
+    frame by its sample count.  A zero weight sum gives a zero image."""
+    S = np.asarray(S, np.float64)
+    K = S.shape[0]
+    W = np.ones(K) if W is None else np.asarray(W, np.float64)
+    num = np.zeros(S.shape[1:], np.float64)
+    den = 0.0
+    for i in range(1, K + 1):
+        w = W[i - 1] * combine_weight(kind, i)
+        num = num + w * S[i - 1]
+        den = den + w
+    return num / den if den > 0.0 else np.zeros_like(num)

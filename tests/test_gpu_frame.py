@@ -393,7 +393,7 @@ def test_frame_that_sees_nothing():
 
 
 def test_combination_heuristics_weigh_the_frames():
-    """Eq. 7: the linear heuristic's image equals sum h(i) S_i / sum h(i) of the
+    """Eq. 7: the linear heuristic's image equals the oracle's combination of the
     per-frame estimates S_i (from a constant-weight run with the same seeds), and
     PT first's first frame is the unguided frame."""
     K = 7
@@ -406,8 +406,7 @@ def test_combination_heuristics_weigh_the_frames():
         fa.run(1)
         means.append(fa.image()[0].double().cpu().numpy())
     S = [means[0]] + [(k + 1) * means[k] - k * means[k - 1] for k in range(1, K)]
-    h = np.array([min(i, 5) for i in range(1, K + 1)], np.float64)
-    ref = sum(hi * Si for hi, Si in zip(h, S)) / h.sum()
+    ref = OF.combine_images(np.stack(S), "linear")
     fb.run(K)
     np.testing.assert_allclose(fb.image()[0].double().cpu().numpy(), ref, rtol=2e-5, atol=1e-6)
     # PT first: frame 1 equals a frame with alpha = 0

@@ -121,3 +121,65 @@ def test_eq5_with_light_sampling_hand_path():
     p2, k2, L2 = OF.eq5_records(T, Le + nee, [3], Le_seen=Le + nee)
     np.testing.assert_allclose(L2, OF.eq5_records(T, Le + nee, [3])[2], rtol=1e-15)
     np.testing.assert_allclose(L2, [0.5 + 1.0 + 2.0, 2.0 + 4.0, 8.0])
+
+
+# Sample-combination heuristics (Sec. 3.7, Eq. 7).  The weights below are the
+# cases the paper prints for frames 1..7; the pins compare the combination with
+# library averages of replicated frames, which a wrong weight, index or
+# normalisation would not reproduce.
+PRINTED = {
+    "constant": [1, 1, 1, 1, 1, 1, 1],
+    "linear": [1, 2, 3, 4, 5, 5, 5],
+    "quadratic": [1, 4, 9, 16, 25, 25, 25],
+    "one-two": [1, 2, 2, 2, 2, 2, 2],
+    "discard-first": [0, 1, 1, 1, 1, 1, 1],
+    "pt-first": [1, 1, 1, 1, 1, 1, 1],
+}
+
+
+def test_combination_weights_are_the_printed_cases():
+    assert set(PRINTED) == set(OF.HEURISTICS)
+    for kind, h in PRINTED.items():
+        assert [OF.combine_weight(kind, i) for i in range(1, 8)] == h, kind
+    for kind in OF.HEURISTICS:  # every weight stays at its last printed value
+        assert OF.combine_weight(kind, 1000) == PRINTED[kind][-1]
+
+
+def test_combination_equals_the_mean_of_replicated_frames():
+    """Integer weights: Eq. 7 with W = 1 is the plain mean (numpy) of the
+    sequence in which frame i appears h(i) times."""
+    rng = np.random.default_rng(7)
+    K = 7
+    S = rng.uniform(0.0, 3.0, (K, 5, 4))
+    for kind, h in PRINTED.items():
+        rep = np.concatenate([np.repeat(S[i:i + 1], h[i], axis=0) for i in range(K)])
+        np.testing.assert_allclose(OF.combine_images(S, kind), rep.mean(axis=0), rtol=1e-13, err_msg=kind)
+    # the constant heuristic is numpy's mean; discard-first ignores frame 1
+    np.testing.assert_allclose(OF.combine_images(S, "constant"), S.mean(axis=0), rtol=1e-13)
+    S2 = S.copy()
+    S2[0] = 1e6
+    np.testing.assert_array_equal(OF.combine_images(S2, "discard-first"), OF.combine_images(S, "discard-first"))
+
+
+def test_combination_keeps_constant_images_and_is_unbiased():
+    rng = np.random.default_rng(8)
+    img = rng.uniform(0.5, 2.0, (3, 3))
+    for kind in OF.HEURISTICS:
+        np.testing.assert_allclose(OF.combine_images(np.repeat(img[None], 9, axis=0), kind), img, rtol=1e-14)
+    # independent unbiased frames (mean 1, different variances) stay unbiased
+    trials, K = 20000, 8
+    noise = rng.normal(size=(trials, K)) * np.linspace(2.0, 0.5, K)
+    for kind in OF.HEURISTICS:
+        est = np.array([OF.combine_images(1.0 + noise[t], kind) for t in range(0, trials, 4)])
+        se = est.std(ddof=1) / np.sqrt(len(est))
+        assert abs(est.mean() - 1.0) < 4 * se, (kind, est.mean(), se)
+
+
+def test_combination_with_sample_counts():
+    """W_i = samples of frame i: the constant heuristic is the per-sample mean
+    (numpy's weighted average); a zero weight sum gives a zero image."""
+    rng = np.random.default_rng(9)
+    S = rng.uniform(size=(5, 6))
+    Wn = np.array([1, 4, 2, 8, 3], np.float64)
+    np.testing.assert_allclose(OF.combine_images(S, "constant", Wn), np.average(S, axis=0, weights=Wn), rtol=1e-13)
+    np.testing.assert_array_equal(OF.combine_images(S[:1], "discard-first"), np.zeros(6))
