@@ -272,6 +272,28 @@ def host_cores():
         return os.cpu_count() or 1
 
 
+def host_cpu():
+    """The host CPU's name: /proc/cpuinfo's model name (x86), else its
+    implementer and part codes (Arm), with the machine type."""
+    import platform
+    fields = {}
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                k, sep, v = line.partition(":")
+                if sep and k.strip() not in fields:
+                    fields[k.strip()] = v.strip()
+    except OSError:
+        pass
+    if "model name" in fields:
+        name = fields["model name"]
+    elif "CPU part" in fields:
+        name = f"implementer {fields.get('CPU implementer', '?')} part {fields['CPU part']}"
+    else:
+        name = platform.processor() or "unknown"
+    return f"{platform.machine()} {name}"
+
+
 def oracle_pool(seed, cores):
     import multiprocessing as mp
     pool = mp.get_context("spawn").Pool(cores, initializer=_oracle_worker_init, initargs=(seed,))
@@ -378,7 +400,7 @@ def run_reference(args, world, rank):
             "config": {"workload": w.desc, "rays": R, "bins": len(w.bin_sizes), "grid": w.grid_n,
                        "svo_depth": w.depth},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": sample},
+                             "sample": sample, "cpu": host_cpu()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -699,7 +721,7 @@ def run_gpu(args, world, rank, local):
             "sample": f"one frame: full accumulate + binning on one core, then fields + sampling/eval for "
                       f"{nbins} of {B} bins ({nrays} rays) split over {cores} processes, the parallel "
                       f"region's wall time scaled to the frame",
-            "single_core": single}
+            "single_core": single, "cpu": host_cpu()}
     print(json.dumps(line))
 
 
