@@ -285,3 +285,96 @@ def test_furnace_values_are_one():
     s.accumulate(pos, nrm, np.ones(len(pos), np.float32))
     v = s.exitance()["value"]
     assert np.all(v == 1.0)
+
+
+def _subtree_index(ex, D):
+    """For every level l and every node at a level >= l: the index of its
+    ancestor at level l, from the Morton keys alone (key >> 3 (l' - l))."""
+    lo = ex["level_off"]
+    keys = ex["key"]
+    anc = {}
+    for l in range(D + 1):
+        lk = keys[lo[l]:lo[l + 1]]
+        for m in range(l, D + 1):
+            mk = keys[lo[m]:lo[m + 1]] >> np.uint64(3 * (m - l))
+            pos = np.searchsorted(lk, mk)
+            assert np.array_equal(lk[pos], mk)
+            anc[l, m] = lo[l] + pos
+    return anc
+
+
+def test_subtree_totals_are_conserved():
+    """Every node's totals (both sides) = the records landed anywhere in its
+    subtree, with the subtree taken from the keys (brute force).  Records in
+    free space stay at the deepest existing node above them, so inner nodes
+    hold records of their own too."""
+    w = inputs.tiny_box(3)
+    D = w.depth
+    s = oracle.SVO(w.scene, D)
+    rng = np.random.default_rng(3)
+    m = 20000
+    free = rng.uniform(0.2, 0.8, (m, 3)).astype(np.float32)
+    d = rng.normal(size=(m, 3))
+    d = (d / np.linalg.norm(d, axis=1, keepdims=True)).astype(np.float32)
+    pos = np.concatenate([w.rec_pos, free])
+    s.accumulate(pos, np.concatenate([w.rec_wout, d]), np.concatenate([w.rec_L, rng.uniform(0, 3, m).astype(np.float32)]))
+    e, ex = s.exitance(), s.export()
+    lo = ex["level_off"]
+    anc = _subtree_index(ex, D)
+    acc_s = e["acc_sum"].sum(axis=1, dtype=np.uint64)
+    acc_c = e["acc_cnt"].sum(axis=1, dtype=np.uint64)
+    want_s = np.zeros(s.n_nodes, np.uint64)
+    want_c = np.zeros(s.n_nodes, np.uint64)
+    for (l, m), a in anc.items():
+        np.add.at(want_s, a, acc_s[lo[m]:lo[m + 1]])
+        np.add.at(want_c, a, acc_c[lo[m]:lo[m + 1]])
+    np.testing.assert_array_equal(e["tot_sum"].sum(axis=1, dtype=np.uint64), want_s)
+    np.testing.assert_array_equal(e["tot_cnt"].sum(axis=1, dtype=np.uint64), want_c)
+    assert int(want_c[0]) == len(pos)
+    inner = np.arange(s.n_nodes) < lo[D]
+    assert int(acc_c[inner].sum()) > m // 2   # most free-space records sit on inner nodes
+
+
+def test_sides_follow_the_direction_records_leave_in():
+    """Two parallel quads facing away from each other (normals -y and +y) and
+    records leaving them in uniformly random directions: at every node, the
+    side whose direction is +y (the node's normal, or its negation for side 1)
+    holds exactly the records of its subtree that leave with w_y > 0, whatever
+    the normals of the levels in between."""
+    D = 5
+    h = 1.0 / (1 << D)
+    q = np.array([[1, 10.5 * h, 0.1, 0.9, 0.1, 0.9, -1, 0],
+                  [1, 21.5 * h, 0.1, 0.9, 0.1, 0.9, +1, 0]], np.float32)
+    sc = inputs.Scene(quads=q, spheres=np.zeros((0, 4), np.float32), albedo=np.ones(2, np.float32),
+                      emission=np.zeros(2, np.float32), lo=np.zeros(3, np.float32), size=1.0)
+    s = oracle.SVO(sc, D)
+    rng = np.random.default_rng(12)
+    n = 20000
+    which = rng.integers(0, 2, n)
+    pos = np.stack([rng.uniform(0.1, 0.9, n), q[which, 1], rng.uniform(0.1, 0.9, n)], 1).astype(np.float32)
+    wout = rng.normal(size=(n, 3))
+    wout = (wout / np.linalg.norm(wout, axis=1, keepdims=True)).astype(np.float32)
+    L = rng.uniform(0, 4, n).astype(np.float32)
+    s.accumulate(pos, wout, L)
+    e, ex = s.exitance(), s.export()
+    assert np.all(np.abs(ex["normal"][:, 1]) == 1.0)   # every normal is +y or -y
+    lo = ex["level_off"]
+    anc = _subtree_index(ex, D)
+    cells = np.floor(pos.astype(np.float64) * (1 << D)).astype(np.int64)
+    leaf_keys = ex["key"][lo[D]:lo[D + 1]]
+    rec_leaf = lo[D] + np.searchsorted(leaf_keys, np.array([oracle.morton(*c) for c in cells], np.uint64))
+    assert np.array_equal(ex["key"][rec_leaf], np.array([oracle.morton(*c) for c in cells], np.uint64))
+    up = wout[:, 1] > 0
+    qL = _q(L)
+    leaf_pos = rec_leaf - lo[D]
+    for l in range(D + 1):
+        a = anc[l, D][leaf_pos]
+        cnt_up = np.bincount(a[up], minlength=s.n_nodes)
+        cnt_dn = np.bincount(a[~up], minlength=s.n_nodes)
+        sum_up = np.zeros(s.n_nodes, np.uint64)
+        np.add.at(sum_up, a[up], qL[up])
+        nodes = np.arange(lo[l], lo[l + 1])
+        side_up = np.where(ex["normal"][nodes, 1] > 0, 0, 1)
+        np.testing.assert_array_equal(e["tot_cnt"][nodes, side_up], cnt_up[nodes], err_msg=f"level {l}")
+        np.testing.assert_array_equal(e["tot_cnt"][nodes, 1 - side_up], cnt_dn[nodes], err_msg=f"level {l}")
+        np.testing.assert_array_equal(e["tot_sum"][nodes, side_up], sum_up[nodes], err_msg=f"level {l}")
