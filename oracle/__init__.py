@@ -89,6 +89,7 @@ def _declare(L):
         "orc_pdf_cdf": (None, [P, I32, P, P, P]),
         "orc_trace": (None, [P, P, P, SZ, F, F, I32, P, P, P, P, P, P, P, P, P]),
         "orc_mlp_num_params": (SZ, []),
+        "orc_bf16_round": (None, [P, SZ, P]),
         "orc_product_block_sums": (None, [P, I32, SZ, P]),
         "orc_product_sample": (None, [P, P, I32, P, P, P, SZ, P, P, P]),
         "orc_product_eval": (None, [P, P, I32, P, P, P, SZ, P]),
@@ -339,6 +340,14 @@ MLP_IN, MLP_HID, MLP_OUT = 80, 64, 1024
 
 def mlp_num_params() -> int:
     return int(lib().orc_mlp_num_params())
+
+
+def bf16_round(x):
+    """The bfloat16 rounding (to nearest, ties to even) of the emulation."""
+    x = _c(x, np.float32).ravel()
+    out = np.zeros_like(x)
+    lib().orc_bf16_round(_p(x), len(x), _p(out))
+    return out
 
 
 def mlp_features(pos, nrm, lo, S):

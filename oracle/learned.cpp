@@ -110,6 +110,11 @@ extern "C" {
 
 size_t orc_mlp_num_params(void) { return kParams; }
 
+// the bfloat16 rounding used by the emulation, element by element
+void orc_bf16_round(const float* x, size_t n, float* out) {
+    for (size_t i = 0; i < n; ++i) out[i] = bf16_round(x[i]);
+}
+
 void orc_mlp_features(const float* pos, const float* nrm, size_t n, const float* lo, float S, double* out) {
     for (size_t i = 0; i < n; ++i) mlp_features(pos + 3 * i, nrm + 3 * i, lo, S, out + kIn * i);
 }

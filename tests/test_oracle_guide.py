@@ -157,6 +157,49 @@ def test_trace_axis_ray_hits_wall():
     assert (rr["side"] == 0).all()
 
 
+def test_cone_level_tie_goes_to_the_finer_level():
+    """Eq. 6 with A exactly halfway between two squared sides (all values
+    dyadic, so nothing rounds): the reading takes the finer level; a
+    footprint a little larger or smaller decides for the nearer side."""
+    D = 6
+    s = oracle.SVO(inputs.closed_box(1, D), D)
+    o = np.array([[47 / 64, 0.5, 0.5]], np.float32)
+    d = np.array([[1, 0, 0]], np.float32)
+    # entry at x = 63/64: t = 1/4, A = t^2 omega = omega / 16
+    r = s.trace(o, d, omega=2.5)        # A = 5/32: |1/4 - A| = |1/16 - A| = 3/32
+    assert float(r["t_entry"][0]) == 0.25
+    assert int(r["level"][0]) == 2
+    assert int(s.trace(o, d, omega=2.5 * (1 + 2 ** -20))["level"][0]) == 1
+    assert int(s.trace(o, d, omega=2.5 * (1 - 2 ** -20))["level"][0]) == 2
+    r = s.trace(o, d, omega=0.625)      # A = 5/128, halfway between 1/16 and 1/64
+    assert int(r["level"][0]) == 3
+
+
+def test_march_ties_step_x_before_y():
+    """A ray through a cell edge (equal boundary times on x and y) steps along
+    x first: it enters the x-neighbour, so a voxel there is hit, while the
+    y-neighbour's side of the edge would miss it."""
+    D = 6
+    h = 1.0 / (1 << D)
+    # a small quad (normal z) inside voxel (21, 20, 20) only
+    q = np.array([[2, 20.5 * h, 21.25 * h, 21.75 * h, 20.25 * h, 20.75 * h, 1, 0]], np.float32)
+    sc = inputs.Scene(quads=q, spheres=np.zeros((0, 4), np.float32), albedo=np.ones(1, np.float32),
+                      emission=np.zeros(1, np.float32), lo=np.zeros(3, np.float32), size=1.0)
+    s = oracle.SVO(sc, D)
+    assert s.n_nodes == D + 1
+    c = np.float32(1 / math.sqrt(2))
+    o = np.array([[20.5 * h, 20.5 * h, 20.5 * h]], np.float32)
+    r = s.trace(o, np.array([[c, c, 0]], np.float32), N=16, t_skip=0.0)
+    assert r["hit"][0] == 1 and int(r["leaf_key"][0]) == oracle.morton(21, 20, 20)
+    # mirrored about x = y the same edge leads into the y-neighbour first: no hit
+    q2 = q.copy()
+    q2[0, 2:6] = [20.25 * h, 20.75 * h, 21.25 * h, 21.75 * h]
+    s2 = oracle.SVO(inputs.Scene(quads=q2, spheres=sc.spheres, albedo=sc.albedo, emission=sc.emission,
+                                 lo=sc.lo, size=1.0), D)
+    r2 = s2.trace(o, np.array([[c, c, 0]], np.float32), N=16, t_skip=0.0)
+    assert r2["hit"][0] == 0
+
+
 def test_cone_level_is_closest_side():
     """Eq. 6: the chosen level's squared side is the closest to A = t^2 omega,
     and the level only gets coarser with distance."""
@@ -243,6 +286,38 @@ def test_single_emitter_peak_on_light():
     assert np.all(f[far & (t < 1.0)] < f.max())
 
 
+def test_jittered_field_draws_its_offsets_from_the_counter_generator():
+    """With jitter, cell c = j N + i of bin b in frame k is queried at the
+    octahedral image of ((i + x0) 2/N - 1, (j + x1) 2/N - 1), x0 and x1 the
+    24-bit uniforms of counters 2c and 2c + 1 of stream (k, b) under the
+    jitter purpose's seed (4 seed + 1); the field is eps plus the cone
+    query there.  Rebuilt here from the published generator (SplitMix64
+    finaliser, itself pinned to its reference outputs) and single cone
+    queries."""
+    w = inputs.tiny_box(2)
+    s = oracle.SVO(w.scene, w.depth)
+    s.accumulate(w.rec_pos, w.rec_wout, w.rec_L)
+    N, seed, frame, b, eps = 16, 7, 3, 5, np.float32(1e-2)
+    o = w.ray_pos[11:12]
+    g = s.guide_build(o, np.array([b]), N, eps=float(eps), jitter=True, blur=False, seed=seed, frame=frame)
+    stream = (frame << 32) | b
+    x = np.array([oracle.rng_u64(4 * seed + 1, stream, k) >> 40 for k in range(2 * N * N)], np.float64)
+    x = (x * 2.0 ** -24).astype(np.float32).reshape(N * N, 2)
+    c = np.arange(N * N)
+    tn = np.float32(2.0 / N)
+    uv = np.stack([((c % N).astype(np.float32) + x[:, 0]) * tn - np.float32(1),
+                   ((c // N).astype(np.float32) + x[:, 1]) * tn - np.float32(1)], axis=1).astype(np.float32)
+    d = oracle.octa_decode(uv)
+    val = s.trace(np.repeat(o, N * N, axis=0), d, N=N)["value"]
+    np.testing.assert_array_equal(g["field"][0], eps + val)
+    assert not np.array_equal(x[:, 0], x[:, 1])
+    # without jitter the same cells are queried at their centres
+    g0 = s.guide_build(o, np.array([b]), N, eps=float(eps), jitter=False, blur=False, seed=seed, frame=frame)
+    uv0 = np.stack([((c % N) + 0.5) * 2.0 / N - 1, ((c // N) + 0.5) * 2.0 / N - 1], axis=1).astype(np.float32)
+    val0 = s.trace(np.repeat(o, N * N, axis=0), oracle.octa_decode(uv0), N=N)["value"]
+    np.testing.assert_array_equal(g0["field"][0], eps + val0)
+
+
 def test_blur_mass_and_kernel():
     rng = np.random.default_rng(0)
     N = 16
@@ -265,7 +340,8 @@ def test_blur_wraps_with_octahedral_mirror():
     delta[0 * N + 2] = 16.0            # row 0, column 2
     got = oracle.blur(delta, N).reshape(N, N)
     # the row above row 0 is row 0 mirrored: column 2 sends weight to column N-1-2
-    assert got[0, N - 1 - 2] > 0 and got[0, N - 1 - 2] == got[0, N - 1 - 2]
+    # (column pass: 16 / 4 lands on row 0, column 5; row pass keeps half of it there)
+    assert got[0, N - 1 - 2] == 2.0 and got[0, N - 1 - 2 - 1] == 1.0 and got[0, N - 1 - 2 + 1] == 1.0
     assert got.sum() == 16.0
 
 
@@ -299,6 +375,24 @@ def _random_guide(N, seed, nb=1):
     out = [oracle.pdf_cdf(f, N) for f in fs]
     return (np.stack([o[0] for o in out]), np.stack([o[1] for o in out]),
             np.stack([o[2] for o in out]))
+
+
+def test_cdf_stays_monotone_where_the_tree_scan_does_not():
+    """Fields whose values span many orders of magnitude make the tree-shaped
+    warp scan round an entry below its predecessor; the CDFs still never
+    decrease (the running maximum), and equal the scan wherever it did not."""
+    rng = np.random.default_rng(0)
+    N = 32
+    hit = 0
+    for trial in range(40):
+        f = (rng.gamma(0.3, 1.0, N * N) * 10.0 ** rng.integers(-6, 3, N * N)).astype(np.float32)
+        rows = np.stack([oracle.warp_scan(f[j * N:(j + 1) * N]) for j in range(N)])
+        hit += int(np.any(np.diff(rows, axis=1) < 0))
+        pdf, cr, cm = oracle.pdf_cdf(f, N)
+        cr = cr.reshape(N, N)
+        assert np.all(np.diff(cr, axis=1) >= 0) and np.all(np.diff(cm) >= 0)
+        np.testing.assert_array_equal(cr, np.maximum.accumulate(rows, axis=1))
+    assert hit > 10
 
 
 def test_sampler_chi_square():
@@ -336,6 +430,45 @@ def test_sample_eval_consistency_and_bracket():
     t1 = u[:, 1] * crr[bins, r, N - 1]
     assert np.all(crr[bins, r, c] > t1)
     assert np.all(np.where(c > 0, crr[bins, r, np.maximum(c - 1, 0)] <= t1, True))
+
+
+def test_sampler_skips_empty_cells_even_at_u_zero():
+    """Rows and columns without mass are never chosen, also when a uniform is
+    exactly 0 (the first entry strictly greater than the target)."""
+    N = 16
+    rng = np.random.default_rng(3)
+    f = rng.gamma(0.5, 1.0, (N, N)).astype(np.float32)
+    f[:3] = 0.0          # empty first rows
+    f[:, :2] = 0.0       # empty first columns
+    f[7] = 0.0           # an empty row inside
+    pdf, cr, cm = oracle.pdf_cdf(f.ravel(), N)
+    u = inputs.uniforms24(8, (20000, 2))
+    u[:50] = 0.0
+    u[50:100, 0] = 0.0
+    u[100:150, 1] = 0.0
+    d, p, cell = oracle.guide_sample(pdf[None], cr[None], cm[None], N, np.zeros(len(u), np.uint32), u)
+    assert np.all(p > 0)
+    assert np.all(f.ravel()[cell] > 0)
+
+
+def test_sample_offsets_inside_the_cell_are_uniform_and_independent():
+    """Within its cell a sample's position on the octahedral square is uniform
+    (the density is constant over the cell) and its two offsets are
+    independent: Kolmogorov-Smirnov against U(0, 1) and their correlation."""
+    N = 16
+    pdf, cr, cm = _random_guide(N, 4)
+    n = 200_000
+    u = inputs.uniforms24(9, (n, 2))
+    d, p, cell = oracle.guide_sample(pdf, cr, cm, N, np.zeros(n, np.uint32), u)
+    uv = (oracle.octa_encode(d).astype(np.float64) + 1.0) * N / 2
+    a = uv[:, 0] - (cell % N)
+    b = uv[:, 1] - (cell // N)
+    ok = (a > -1e-4) & (a < 1 + 1e-4) & (b > -1e-4) & (b < 1 + 1e-4)
+    assert ok.mean() > 0.999
+    a, b = np.clip(a[ok], 0, 1), np.clip(b[ok], 0, 1)
+    assert stats.kstest(a, "uniform").pvalue > 1e-3
+    assert stats.kstest(b, "uniform").pvalue > 1e-3
+    assert abs(np.corrcoef(a, b)[0, 1]) < 0.02
 
 
 def test_guided_estimator_unbiased():

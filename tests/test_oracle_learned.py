@@ -77,7 +77,19 @@ def test_gradient_matches_central_differences():
             fd = (lp - lm) / (dp + dm)
             assert abs(fd - g[i]) <= 2e-4 * max(abs(fd), 1e-3) + 1e-7, (name, i, fd, g[i])
             checked += 1
-    assert checked == 48
+    # the first layer's position and normal columns, which random picks rarely reach
+    for row in (3, 40):
+        for col in (0, 1, 2, 75, 76, 77):
+            i = row * 80 + col
+            h = np.float32(1e-3 * max(1.0, abs(float(params[i]))))
+            pp, pm = params.copy(), params.copy()
+            pp[i], pm[i] = params[i] + h, params[i] - h
+            lp, _ = oracle.mlp_grad(pp, pos, nrm, LO, 1.0, q)
+            lm, _ = oracle.mlp_grad(pm, pos, nrm, LO, 1.0, q)
+            fd = (lp - lm) / ((float(pp[i]) - float(params[i])) + (float(params[i]) - float(pm[i])))
+            assert abs(fd - g[i]) <= 2e-4 * max(abs(fd), 1e-3) + 1e-7, ("W1", row, col, fd, g[i])
+            checked += 1
+    assert checked == 60
     assert P == 80064
     assert np.all(g[np.arange(64) * 80 + 78] == 0) and np.all(g[np.arange(64) * 80 + 79] == 0)
 
@@ -90,6 +102,24 @@ def test_bf16_emulation_close_to_fp64():
     # bfloat16 keeps 8 significant bits: the logits agree to a few 1e-2
     assert np.max(np.abs(z16 - z64)) < 0.05 * max(1.0, np.max(np.abs(z64)))
     assert np.max(np.abs(z16 - z64)) > 0
+
+
+def test_bf16_rounding_is_the_library_conversion():
+    """The emulation's bfloat16 rounding equals torch's float32 -> bfloat16
+    conversion (round to nearest, ties to even), on exact ties, on values one
+    step either side of a tie, and on random values of every magnitude."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(4)
+    base = rng.integers(0, 1 << 31, 4000, dtype=np.uint64).astype(np.uint32) & np.uint32(0xFFFF0000)
+    base = base[((base >> 23) & 0xFF) < 0xFE]                      # finite, not at the top binade
+    ties = base | np.uint32(0x8000)
+    near = np.concatenate([ties - np.uint32(1), ties + np.uint32(1)])
+    rand = rng.integers(0, 1 << 31, 20000, dtype=np.uint64).astype(np.uint32)
+    rand = rand[((rand >> 23) & 0xFF) < 0xFF]
+    x = np.concatenate([ties, near, rand]).view(np.float32)
+    x = np.concatenate([x, -x, np.array([0.0, -0.0, 1.0, 3.0e38], np.float32)])
+    want = torch.from_numpy(x.copy()).to(torch.bfloat16).to(torch.float32).numpy()
+    np.testing.assert_array_equal(oracle.bf16_round(x).view(np.uint32), want.view(np.uint32))
 
 
 def test_adam_first_step_is_lr_times_sign():

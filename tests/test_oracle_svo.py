@@ -189,6 +189,44 @@ def test_kmeans_matches_sklearn_lloyd():
         np.testing.assert_allclose(got, c0 / np.linalg.norm(c0), atol=2e-6)
 
 
+def test_kmeans_runs_four_rounds():
+    """Widely spread normals whose assignment still changes after the first
+    round: the result is the library's after four Lloyd rounds, not one.  Cases
+    where some round leaves a cluster empty are skipped (the library relocates
+    an empty cluster, the reading here keeps its centroid)."""
+    KMeans = pytest.importorskip("sklearn.cluster").KMeans
+    import warnings
+    rng = np.random.default_rng(11)
+    checked = 0
+    for trial in range(400):
+        m = int(rng.integers(6, 30))
+        a = rng.normal(size=3)
+        pts = a + 1.2 * np.linalg.norm(a) * rng.normal(size=(m, 3))
+        pts = (pts / np.linalg.norm(pts, axis=1, keepdims=True)).astype(np.float32)
+        w = rng.integers(1, 5, m).astype(np.float32)
+        init = np.stack([pts[0], -pts[0]]).astype(np.float64)
+        fits = {}
+        with warnings.catch_warnings():
+            warnings.simplefilter("ignore")
+            for it in (1, 2, 3, 4):
+                fits[it] = KMeans(n_clusters=2, init=init, n_init=1, max_iter=it, tol=0.0,
+                                  algorithm="lloyd").fit(pts.astype(np.float64), sample_weight=w)
+        d = ((pts[:, None, :].astype(np.float64) - init[None]) ** 2).sum(axis=2)
+        first = (d[:, 0] > d[:, 1]).astype(np.int64)  # the first round's assignment, from the initial centroids
+        if any(np.bincount(f.labels_, minlength=2).min() == 0 for f in fits.values()) or \
+                np.bincount(first, minlength=2).min() == 0:
+            continue
+        c1, c4 = (fits[k].cluster_centers_[0] for k in (1, 4))
+        c1, c4 = c1 / np.linalg.norm(c1), c4 / np.linalg.norm(c4)
+        if np.linalg.norm(c1 - c4) < 1e-3:
+            continue
+        np.testing.assert_allclose(oracle.kmeans2(pts, w), c4, atol=2e-6)
+        checked += 1
+        if checked == 6:
+            break
+    assert checked == 6
+
+
 # ---------------------------------------------------------------- UpdateExitance
 def _q(L):
     Lc = np.where(L > 0, np.minimum(L, np.float32(2 ** 24)), 0).astype(np.float32)
@@ -206,6 +244,24 @@ def test_accumulate_conserves_sums_and_counts():
     assert int(e["acc_cnt"].sum()) == len(q)
     assert int(e["tot_sum"][0].astype(object).sum()) == total  # root holds everything
     assert int(e["tot_cnt"][0].sum()) == len(q)
+
+
+def test_record_quantisation_clamps_and_rounds_to_even():
+    """L is clamped to [0, 2^24] (NaN -> 0) and quantised to the nearest
+    multiple of 2^-20, halfway cases to even; every record counts."""
+    D = 4
+    q = np.array([[1, 0.5, 0.0, 1.0, 0.0, 1.0, 1.0, 0.0]], np.float32)
+    sc = inputs.Scene(quads=q, spheres=np.zeros((0, 4), np.float32), albedo=np.ones(1, np.float32),
+                      emission=np.zeros(1, np.float32), lo=np.zeros(3, np.float32), size=1.0)
+    cases = [(1e9, 1 << 44), (2.0 ** 24, 1 << 44), (-5.0, 0), (float("nan"), 0), (0.5 * 2 ** -20, 0),
+             (1.5 * 2 ** -20, 2), (2.5 * 2 ** -20, 2), (3.0, 3 << 20)]
+    for L, want in cases:
+        s = oracle.SVO(sc, D)
+        s.accumulate(np.array([[0.3, 0.5, 0.7]], np.float32), np.array([[0, 1, 0]], np.float32),
+                     np.array([L], np.float32))
+        e = s.exitance()
+        assert int(e["acc_sum"].sum()) == want, L
+        assert int(e["acc_cnt"].sum()) == 1
 
 
 def test_accumulate_brute_force_counts_and_sides():
