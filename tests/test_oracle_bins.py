@@ -30,22 +30,38 @@ def _interior_rays(w, n):
 
 @pytest.mark.parametrize("l_min,c_ray", [(2, 0xFFFFFFFF), (1, 200), (2, 30), (3, 8), (0, 50)])
 def test_partition_s_brute_force(l_min, c_ray):
+    """Rays on the walls and rays in free space (whose deepest node is an inner
+    node, at level 1 in the middle of the box): brute force by coordinates."""
     w = inputs.tiny_box(7, n_rays=6000)
     D = w.depth
     pos, nrm = _interior_rays(w, 4000)
+    rng = np.random.default_rng(l_min + 7)
+    free = rng.uniform(0.27, 0.73, (300, 3)).astype(np.float32)
+    keep = (np.abs(free * (1 << D) - np.rint(free * (1 << D))) > 1e-4).all(axis=1)
+    pos = np.concatenate([pos, free[keep]])
+    nrm = np.concatenate([nrm, np.tile(np.array([[0, 1, 0]], np.float32), (int(keep.sum()), 1))])
     s = oracle.SVO(w.scene, D)
     r = s.bin_rays(pos, nrm, mode=0, l_min=l_min, c_ray=c_ray, seed=3, frame=1)
-    # brute force by coordinates: ray counts of every ancestor cell
+    # the tree's cells, level by level, from the node keys
+    ex = s.export()
+    lo = ex["level_off"]
+    exists = {(l, _decode(int(k), l)) for l in range(D + 1) for k in ex["key"][lo[l]:lo[l + 1]]}
     cells = np.minimum(np.floor(pos.astype(np.float64) * (1 << D)), (1 << D) - 1).astype(int)
+    anc = lambda c, l: (l, tuple(int(v) >> (D - l) for v in c))
+    deepest = [max(l for l in range(D + 1) if anc(c, l) in exists) for c in cells]
+    assert min(deepest) == 1 and max(deepest) == D
+    # ray counts of every existing ancestor cell down to l_min
     counts = {}
-    for c in cells:
-        for l in range(l_min, D + 1):
-            k = (l, tuple(int(v) >> (D - l) for v in c))
-            counts[k] = counts.get(k, 0) + 1
+    for c, L in zip(cells, deepest):
+        for l in range(l_min, L + 1):
+            counts[anc(c, l)] = counts.get(anc(c, l), 0) + 1
     groups = {}
-    for i, c in enumerate(cells):
-        for l in range(D, l_min - 1, -1):
-            k = (l, tuple(int(v) >> (D - l) for v in c))
+    for i, (c, L) in enumerate(zip(cells, deepest)):
+        if L < l_min:   # above l_min: the ray keeps its own node
+            groups.setdefault(anc(c, L), []).append(i)
+            continue
+        for l in range(L, l_min - 1, -1):
+            k = anc(c, l)
             if counts[k] >= c_ray or l == l_min:
                 groups.setdefault(k, []).append(i)
                 break
@@ -58,7 +74,7 @@ def test_partition_s_brute_force(l_min, c_ray):
         lo, hi = r["bin_offset"][b], r["bin_offset"][b + 1]
         assert r["ray_order"][lo:hi].tolist() == groups[k]   # stable partition
         assert r["origin_ray"][b] in groups[k]
-        if k[0] != l_min:
+        if k[0] > l_min:
             # marked for its subtree total; descendants that are marked keep
             # their own rays, so the bin itself may hold fewer
             assert counts[k] >= c_ray

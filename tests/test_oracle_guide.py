@@ -157,6 +157,26 @@ def test_trace_axis_ray_hits_wall():
     assert (rr["side"] == 0).all()
 
 
+def test_cos_weight_scales_by_the_absolute_cosine():
+    """The optional cos weight multiplies the looked-up value by |N . d| (the
+    value stays non-negative on either side)."""
+    D = 5
+    w = inputs.tiny_box(4)
+    s = oracle.SVO(w.scene, D)
+    s.accumulate(w.rec_pos, w.rec_wout, w.rec_L)
+    rng = np.random.default_rng(6)
+    v = rng.normal(size=(500, 3))
+    v = (v / np.linalg.norm(v, axis=1, keepdims=True)).astype(np.float32)
+    o = np.tile(np.array([[0.4, 0.55, 0.5]], np.float32), (len(v), 1))
+    a = s.trace(o, v, N=16)
+    b = s.trace(o, v, N=16, cos_weight=True)
+    assert a["hit"].all() and np.array_equal(a["node"], b["node"])
+    nrm = s.export()["normal"][a["node"]]
+    c = np.abs(np.einsum("ij,ij->i", nrm, v).astype(np.float32))
+    np.testing.assert_allclose(b["value"], a["value"] * c, rtol=1e-6)
+    assert np.all(b["value"] >= 0) and np.any(a["side"] == 0) and np.any(a["value"] > 0)
+
+
 def test_cone_level_tie_goes_to_the_finer_level():
     """Eq. 6 with A exactly halfway between two squared sides (all values
     dyadic, so nothing rounds): the reading takes the finer level; a
@@ -342,6 +362,13 @@ def test_blur_wraps_with_octahedral_mirror():
     # the row above row 0 is row 0 mirrored: column 2 sends weight to column N-1-2
     # (column pass: 16 / 4 lands on row 0, column 5; row pass keeps half of it there)
     assert got[0, N - 1 - 2] == 2.0 and got[0, N - 1 - 2 - 1] == 1.0 and got[0, N - 1 - 2 + 1] == 1.0
+    # the same at the bottom edge, and across the left and right edges (rows mirrored)
+    for (r, c), (rr, cc) in {((N - 1, 2), (N - 1, N - 3)), ((1, 0), (N - 2, 0)), ((1, N - 1), (N - 2, N - 1))}:
+        delta = np.zeros(N * N, np.float32)
+        delta[r * N + c] = 16.0
+        got = oracle.blur(delta, N).reshape(N, N)
+        assert got[rr, cc] == 2.0, (r, c)
+        assert got.sum() == 16.0
     assert got.sum() == 16.0
 
 

@@ -158,6 +158,30 @@ def test_sphere_normals_radial():
         assert float(ex["normal"][node] @ v) > 1 - 1e-6
 
 
+def test_inner_normals_are_leaf_count_weighted_means_of_one_cluster():
+    """Where all of a node's children have normals within 90 degrees of one
+    another, k-means keeps them in one cluster, so the node's normal is the
+    normalised mean of the children's normals weighted by their leaf counts."""
+    sc = inputs.cornell_spheres(3, n_spheres=20)
+    D = 6
+    s = oracle.SVO(sc, D)
+    ex = s.export()
+    lo = ex["level_off"]
+    n = ex["normal"].astype(np.float64)
+    checked = unequal = 0
+    for node in range(int(lo[D])):
+        ch = ex["first_child"][node] + np.arange(bin(int(ex["child_mask"][node])).count("1"))
+        cn = n[ch]
+        if len(ch) < 2 or np.any(cn @ cn.T <= 0.05):
+            continue
+        wts = ex["leaf_count"][ch].astype(np.float64)
+        m = (wts[:, None] * cn).sum(axis=0)
+        np.testing.assert_allclose(n[node], m / np.linalg.norm(m), atol=2e-6)
+        checked += 1
+        unequal += int(wts.min() != wts.max() and np.abs(cn - cn[0]).max() > 1e-3)
+    assert checked > 200 and unequal > 50
+
+
 def test_kmeans_opposite_normals_do_not_cancel():
     n = np.array([[0, 0, 1], [0, 0, -1]] * 3, np.float32)
     out = oracle.kmeans2(n, np.ones(6, np.float32))
