@@ -169,8 +169,8 @@ class ClockSampler:
 
 
 def measured_peaks(key="hbm_gbs"):
-    """The machine's measured peak (HBM copy GB/s, or cuBLAS bf16 TFLOP/s burst /
-    sustained), else the earlier GB300 measurement."""
+    """The measured GB300 peak from MEASURED_PEAKS.json (HBM copy GB/s, or
+    cuBLAS bf16 TFLOP/s burst / sustained), else an earlier GB300 measurement."""
     fallback = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
