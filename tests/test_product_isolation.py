@@ -72,3 +72,31 @@ def test_binding_raises_without_the_library(monkeypatch, tmp_path):
         W.lib()
     with pytest.raises(RuntimeError, match="not built"):
         W.kernel_launches()
+
+
+def test_host_tensors_are_refused_not_computed():
+    """Host (CPU) tensors are refused with a TypeError before anything runs;
+    no entry point computes on the host."""
+    import numpy as np
+    import torch
+
+    from paper_2405_06997_gb300 import inputs
+    from paper_2405_06997_gb300 import wfpg as W
+
+    w = inputs.tiny_box(1)
+    pdf, cr, cm = torch.zeros(4, 256), torch.zeros(4, 256), torch.zeros(4, 16)
+    bins = torch.zeros(10, dtype=torch.int32)
+    v3 = torch.zeros(10, 3)
+    calls = [
+        lambda: W.guide_sample(pdf, cr, cm, 16, bins, torch.zeros(10, 2)),
+        lambda: W.guide_eval_pdf(pdf, 16, bins, v3),
+        lambda: W.guide_sample_mix(pdf, cr, cm, 16, bins, v3, v3),
+        lambda: W.guide_product_sums(pdf, 16),
+        lambda: W.guide_product_sample(pdf, torch.zeros(4, 64), 16, bins, v3, v3),
+        lambda: W.guide_product_eval(pdf, torch.zeros(4, 64), 16, bins, v3, v3),
+        lambda: W.cast_rays(torch.from_numpy(w.scene.quads), torch.from_numpy(w.scene.spheres), v3, v3),
+    ]
+    for call in calls:
+        with pytest.raises(TypeError, match="CUDA tensor"):
+            call()
+    assert np.all(pdf.numpy() == 0)
