@@ -693,6 +693,8 @@ def run_gpu(args, world, rank, local):
                      "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                      "peak_kind": peak_kind, "algorithmic_bytes": alg["bytes"],
                      "algorithmic_model": alg["model"], "ncu": issue},
+        "issue_roofline": issue_roofline(issue, gms, clk.get("sm_mhz") if clk else None,
+                                         torch.cuda.get_device_properties(dev).multi_processor_count),
         "clocks": clk,
     }
     if not args.no_learned:
@@ -1027,6 +1029,27 @@ def trace_algorithmic_bytes(w, B, N, sample_bins=8):
                                      f"blocks + 24 B); blocks counted by the oracle on {len(sel)} bins"}
 
 
+def issue_roofline(counters, kernel_ms, sm_mhz, n_sm, schedulers=4):
+    """Instruction-issue roofline of the field kernel, beside its HBM one:
+    the warp instructions of one launch (the committed ncu capture of the same
+    source and workload) over the launch's mean CUDA-event duration in the
+    timed steps, against one warp instruction per scheduler per cycle (SMs x 4
+    schedulers x the SM clock sampled during the timed steps).  lane_frac
+    weighs each issued instruction by its active lanes out of 32.  None when
+    a figure is missing."""
+    if not counters or not kernel_ms or not sm_mhz or not n_sm:
+        return None
+    inst = counters.get("warp_instructions_per_launch")
+    lanes = counters.get("active_lanes_per_warp_instruction")
+    if inst is None or lanes is None:
+        return None
+    achieved = inst / (kernel_ms * 1e-3) / 1e9
+    peak = n_sm * schedulers * sm_mhz * 1e6 / 1e9
+    return {"bound": "issue", "achieved": achieved, "peak": peak, "unit": "G warp instructions/s",
+            "frac": achieved / peak, "lane_frac": achieved * lanes / (peak * 32.0),
+            "peak_model": f"{n_sm} SMs x {schedulers} schedulers x 1 warp instruction per cycle x {sm_mhz:.0f} MHz"}
+
+
 def read_profile_traffic():
     """DRAM bytes per launch of k_guide_build (and its issue counters) from the
     committed ncu summary -- only while the kernel source is the one captured."""
@@ -1041,6 +1064,7 @@ def read_profile_traffic():
             return None, None
     return d["dram_bytes_per_launch"], {"issue_active_pct": d["issue_active_pct"],
                                         "active_lanes_per_warp_instruction": d["active_lanes_per_warp_instruction"],
+                                        "warp_instructions_per_launch": d["warp_instructions_per_launch"],
                                         "limiter": "instruction issue and latency with divergence (DRAM well below peak)"}
 
 
