@@ -97,6 +97,7 @@ def _declare(L):
         "orc_mlp_features": (None, [P, P, SZ, P, F, P]),
         "orc_mlp_forward": (None, [P, P, P, SZ, P, F, I32, P, P]),
         "orc_mlp_grad": (C.c_double, [P, P, P, SZ, P, F, P, I32, P]),
+        "orc_mlp_grad_trace": (C.c_double, [P, P, P, SZ, P, F, P, I32, P] + [P] * 9),
         "orc_adam": (None, [P, P, P, P, SZ, I32, C.c_double, C.c_double, C.c_double, C.c_double]),
     }
     for name, (res, args) in sig.items():
@@ -375,6 +376,22 @@ def mlp_grad(params, pos, nrm, lo, S, target, bf16=False):
     loss = lib().orc_mlp_grad(_p(params), _p(pos), _p(nrm), len(pos), _p(lo), float(S), _p(target),
                               int(bf16), _p(g))
     return float(loss), g
+
+
+def mlp_grad_trace(params, pos, nrm, lo, S, target, bf16=False):
+    """mlp_grad plus its per-sample intermediates (dict of [n][width] float64
+    arrays: x, h1, h2, h3, z, g4, d3, d2, d1); the same arithmetic."""
+    params, pos, nrm, lo = (_c(params, np.float32), _c(pos, np.float32), _c(nrm, np.float32),
+                            _c(lo, np.float32))
+    target = _c(target, np.float32)
+    n = len(pos)
+    g = np.zeros(mlp_num_params(), np.float64)
+    widths = {"x": MLP_IN, "h1": MLP_HID, "h2": MLP_HID, "h3": MLP_HID, "z": MLP_OUT, "g4": MLP_OUT,
+              "d3": MLP_HID, "d2": MLP_HID, "d1": MLP_HID}
+    tr = {k: np.zeros((n, w), np.float64) for k, w in widths.items()}
+    loss = lib().orc_mlp_grad_trace(_p(params), _p(pos), _p(nrm), n, _p(lo), float(S), _p(target), int(bf16),
+                                    _p(g), *(_p(tr[k]) for k in widths))
+    return float(loss), g, tr
 
 
 def adam(params, m, v, grad, t, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):

@@ -133,11 +133,20 @@ void orc_mlp_forward(const float* params, const float* pos, const float* nrm, si
     }
 }
 
-// mean over the batch of KL(q_i || softmax(z_i)) and its gradient with respect
-// to every parameter (the padded input columns of W1 get gradient 0)
-double orc_mlp_grad(const float* params, const float* pos, const float* nrm, size_t n, const float* lo, float S,
-                    const float* target, int bf16, double* grad) {
-    const bool bf = bf16 != 0;
+}  // extern "C"
+
+namespace orc {
+
+// The per-sample intermediates of orc_mlp_grad, each [n][width] in binary64
+// (bf16-rounded where the kernels store bfloat16); any pointer may be NULL.
+struct Trace {
+    double *x, *h1, *h2, *h3, *z, *g4, *d3, *d2, *d1;
+};
+
+// mean over the batch of KL(q_i || softmax(z_i)), q_i the i-th target row
+// normalised to sum 1, and its gradient with respect to every parameter (the padded input columns of W1 get gradient 0)
+static double mlp_grad(const float* params, const float* pos, const float* nrm, size_t n, const float* lo, float S,
+                       const float* target, bool bf, double* grad, const Trace* tr) {
     std::vector<double> W[4], B[4];
     unpack(params, bf, W, B);
     const double* b[4] = {B[0].data(), B[1].data(), B[2].data(), B[3].data()};
@@ -148,10 +157,15 @@ double orc_mlp_grad(const float* params, const float* pos, const float* nrm, siz
     const double inv_n = 1.0 / (double)n;
     for (size_t s = 0; s < n; ++s) {
         forward_one(W, b, pos + 3 * s, nrm + 3 * s, lo, S, bf, f);
-        const float* q = target + (size_t)kOut * s;
+        // q: the target field normalised to sum 1 (any non-negative field is accepted)
+        const float* t = target + (size_t)kOut * s;
+        double tsum = 0.0;
+        for (int c = 0; c < kOut; ++c) tsum += (double)t[c];
+        const double inv_t = tsum > 0.0 ? 1.0 / tsum : 0.0;
         for (int c = 0; c < kOut; ++c) {
-            if (q[c] > 0) loss += (double)q[c] * (std::log((double)q[c]) - std::log(f.p[c]));
-            g4[c] = rnd((f.p[c] - (double)q[c]) * inv_n, bf);  // dKL/dz for the batch mean
+            const double q = (double)t[c] * inv_t;
+            if (q > 0) loss += q * (std::log(q) - std::log(f.p[c]));
+            g4[c] = rnd((f.p[c] - q) * inv_n, bf);  // dKL/dz for the batch mean
         }
         // output layer
         for (int o = 0; o < kOut; ++o) {
@@ -185,8 +199,42 @@ double orc_mlp_grad(const float* params, const float* pos, const float* nrm, siz
             for (int i = 0; i < kFeat; ++i) grad[kOffW1 + (size_t)o * kIn + i] += d1[o] * f.x[i];
             grad[kOffB1 + o] += d1[o];
         }
+        if (tr) {
+            auto put = [s](double* dst, const double* src, int w) {
+                if (dst) std::memcpy(dst + (size_t)w * s, src, (size_t)w * sizeof(double));
+            };
+            put(tr->x, f.x.data(), kIn);
+            put(tr->h1, f.h1.data(), kHid);
+            put(tr->h2, f.h2.data(), kHid);
+            put(tr->h3, f.h3.data(), kHid);
+            put(tr->z, f.z.data(), kOut);
+            put(tr->g4, g4.data(), kOut);
+            put(tr->d3, d3.data(), kHid);
+            put(tr->d2, d2.data(), kHid);
+            put(tr->d1, d1.data(), kHid);
+        }
     }
     return loss * inv_n;
+}
+
+}  // namespace orc
+
+extern "C" {
+
+double orc_mlp_grad(const float* params, const float* pos, const float* nrm, size_t n, const float* lo, float S,
+                    const float* target, int bf16, double* grad) {
+    return orc::mlp_grad(params, pos, nrm, n, lo, S, target, bf16 != 0, grad, nullptr);
+}
+
+// orc_mlp_grad that also hands back its per-sample intermediates: input
+// features x [n][80], hidden activations h1..h3 [n][64], logits z [n][1024],
+// logit gradients g4 [n][1024] and the masked hidden gradients d3, d2, d1
+// [n][64]; the arithmetic is orc_mlp_grad's, unchanged
+double orc_mlp_grad_trace(const float* params, const float* pos, const float* nrm, size_t n, const float* lo, float S,
+                          const float* target, int bf16, double* grad, double* x, double* h1, double* h2, double* h3,
+                          double* z, double* g4, double* d3, double* d2, double* d1) {
+    const orc::Trace tr{x, h1, h2, h3, z, g4, d3, d2, d1};
+    return orc::mlp_grad(params, pos, nrm, n, lo, S, target, bf16 != 0, grad, &tr);
 }
 
 // one Adam step (Kingma & Ba 2015) on float32 master weights; t counts from 1
