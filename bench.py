@@ -314,55 +314,54 @@ def oracle_fields_parallel(pool, cores, nb, per_worker, frame, offset=0):
     return wall * nb / total, total, sum(r for _, r in out)
 
 
-def oracle_step_time(w, mis, s, full_bins, frac, k, pool=None, cores=1):
-    """One bounded step of the CPU oracle: accumulate a rotating slice of the
-    frame's records, bin a rotating slice of its rays, build fields for a
-    rotating sample of the frame's bins (from one full binning done beforehand)
-    and sample/evaluate their rays (over the process pool when one is given);
-    each stage's time is scaled to the whole frame.  frac in (0, 1] sets the
-    slice sizes."""
-    import oracle
+def oracle_step(w, mis, s, full_bins, nsel, k, pool, cores):
+    """One measured step of the CPU oracle over a fraction f = nsel / bins of
+    the frame: accumulate f of its records and bin f of its rays on one core
+    (rotating slices), then build the fields of nsel of its bins (rotating,
+    spread over the frame, from one full binning done beforehand) and sample
+    and evaluate their rays over the process pool.  Returns the wall seconds
+    of the step, the guided samples it made (the sampled rays) and each
+    stage's time scaled to the whole frame."""
     nr, R, nb = len(w.rec_L), len(w.ray_pos), full_bins["n_bins"]
-    na = max(1000, int(frac * nr))
+    f = nsel / nb
+    na = max(1, int(round(f * nr)))
     o = (k * na) % nr
     sl = slice(o, min(nr, o + na))
-    t0 = time.perf_counter()
+    t_start = time.perf_counter()
     s.accumulate(w.rec_pos[sl], w.rec_wout[sl], w.rec_L[sl])
-    t_acc = (time.perf_counter() - t0) * nr / (sl.stop - sl.start)
-    nrb = max(1000, int(frac * R))
+    t_acc = time.perf_counter() - t_start
+    nrb = max(1, int(round(f * R)))
     o = (k * nrb) % R
     sr = slice(o, min(R, o + nrb))
     n_sub = sr.stop - sr.start
     t0 = time.perf_counter()
     s.bin_rays(w.ray_pos[sr], w.ray_nrm[sr], mode=1, sizes=np.array([n_sub], np.uint32), seed=w.seed, frame=k)
-    t_bin = (time.perf_counter() - t0) * R / n_sub
-    nsel = max(2, int(round(64 * frac)))
-    if pool is not None:
-        per = max(1, -(-nsel // cores))
-        t_fs, nsel, nrays = oracle_fields_parallel(pool, cores, nb, per, k, offset=k)
-        return t_acc + t_bin + t_fs, dict(records=sl.stop - sl.start, binned_rays=n_sub, bins=nsel,
-                                          sampled_rays=nrays)
-    sel = (np.arange(nsel, dtype=np.int64) * (nb // nsel) + k) % nb
+    t_bin = time.perf_counter() - t0
+    per = max(1, -(-nsel // cores))
     t0 = time.perf_counter()
-    g = s.guide_build(w.ray_pos[full_bins["origin_ray"][sel]], sel, w.grid_n, jitter=True, blur=True,
-                      seed=w.seed, frame=k)
-    t_guide = (time.perf_counter() - t0) * nb / nsel
-    rays = np.flatnonzero(np.isin(full_bins["bin_of_ray"], sel))
-    remap = np.zeros(nb, np.uint32)
-    remap[sel] = np.arange(nsel, dtype=np.uint32)
-    local = remap[full_bins["bin_of_ray"][rays]]
-    t0 = time.perf_counter()
-    oracle.guide_sample(g["pdf"], g["cdf_row"], g["cdf_marg"], w.grid_n, local, w.u[rays])
-    oracle.guide_eval_pdf(g["pdf"], w.grid_n, local, mis[rays])
-    t_samp = (time.perf_counter() - t0) * R / max(len(rays), 1)
-    return t_acc + t_bin + t_guide + t_samp, dict(records=sl.stop - sl.start, binned_rays=n_sub, bins=nsel,
-                                                   sampled_rays=int(len(rays)))
+    t_fs_scaled, nsel_done, nrays = oracle_fields_parallel(pool, cores, nb, per, k, offset=k)
+    t_fields = time.perf_counter() - t0
+    wall = time.perf_counter() - t_start
+    frame_s = t_acc * nr / (sl.stop - sl.start) + t_bin * R / n_sub + t_fs_scaled
+    return wall, nrays, frame_s, dict(records=sl.stop - sl.start, binned_rays=n_sub, bins=nsel_done,
+                                      sampled_rays=nrays, accumulate_s=t_acc, bin_s=t_bin, fields_s=t_fields)
+
+
+def arm_config(w, svo_nodes, world):
+    """The workload description both arms print."""
+    return {"workload": w.desc, "rays": len(w.ray_pos), "records": len(w.rec_L), "bins": len(w.bin_sizes),
+            "grid": w.grid_n, "svo_depth": w.depth, "svo_nodes": int(svo_nodes),
+            "l2": "flushed (256 MiB write) between steps", "parallelism": f"replicas x{world}",
+            "streams": "bin_rays on a second stream beside svo_accumulate; the field waits for both"}
 
 
 def run_reference(args, world, rank):
-    """The CPU oracle on the GPU arm's workload, metric and unit.  The steps are
-    bounded samples sized so that warm-up + timed steps take about two minutes
-    of oracle work whatever K and W are."""
+    """The CPU oracle on the GPU arm's workload, metric and unit.  Each step
+    does a fraction of the frame's work in every stage (records, rays, bins
+    alike), sized so that warm-up + timed steps take about two minutes; the
+    line's value and ms_per_step are the measured guided samples per second
+    and wall time of those steps, and the full-frame rate their stages
+    project is reported beside them."""
     if rank != 0:
         return
     import oracle
@@ -370,35 +369,41 @@ def run_reference(args, world, rank):
     R = len(w.ray_pos)
     svo = oracle.SVO(w.scene, w.depth)
     full_bins = svo.bin_rays(w.ray_pos, w.ray_nrm, mode=1, sizes=w.bin_sizes, seed=w.seed, frame=0)
+    nb = full_bins["n_bins"]
     cores = host_cores()
     pool = oracle_pool(args.seed, cores)
     try:
-        # probe one step at full size, then size the per-step sample to the budget
-        t_probe0 = time.perf_counter()
-        oracle_step_time(w, mis, svo, full_bins, 1.0, 0, pool, cores)
-        full_step_s = time.perf_counter() - t_probe0
-        budget = 120.0 / max(1, args.warmup + args.steps)
-        frac = float(min(1.0, max(0.02, budget / full_step_s)))
-        times, detail = [], None
+        # probe one small step, then size the per-step fraction to the budget
+        n0 = min(nb, 4 * cores)
+        wall0, *_ = oracle_step(w, mis, svo, full_bins, n0, 0, pool, cores)
+        budget = 100.0 / max(1, args.warmup + args.steps)
+        nsel = int(min(nb, max(n0, round(n0 * budget / max(wall0, 1e-3)))))
+        walls, units, frames, detail = [], [], [], None
         for k in range(args.warmup + args.steps):
-            t, detail = oracle_step_time(w, mis, svo, full_bins, frac, k + 1, pool, cores)
+            wall, nrays, frame_s, detail = oracle_step(w, mis, svo, full_bins, nsel, k + 1, pool, cores)
             if k >= args.warmup:
-                times.append(t)
+                walls.append(wall)
+                units.append(nrays)
+                frames.append(frame_s)
     finally:
         pool.close()
         pool.join()
-    t = statistics.mean(times)
-    value = R / t
-    sample = (f"per step: accumulate {detail['records']} of {len(w.rec_L)} records and bin {detail['binned_rays']} "
-              f"of {R} rays on one core, fields/CDFs for {detail['bins']} of {len(w.bin_sizes)} bins and "
-              f"sampling + PDF evaluation of their {detail['sampled_rays']} rays over {cores} processes; each "
-              f"stage scaled to the full frame")
+    ms = statistics.mean(walls) * 1e3
+    value = sum(units) / sum(walls)
+    frame_rate = R / statistics.mean(frames)
+    sample = (f"per step {nsel} of {nb} bins (fraction f = {nsel / nb:.3f} of the frame): accumulate f of the "
+              f"{len(w.rec_L)} records and bin f of the {R} rays on one core, fields/CDFs of the {nsel} bins and "
+              f"sampling + PDF evaluation of their rays over {cores} processes; value = guided samples made / "
+              f"wall time of the timed steps")
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": w.desc, "rays": R, "bins": len(w.bin_sizes), "grid": w.grid_n,
-                       "svo_depth": w.depth},
+            "config": arm_config(w, svo.n_nodes, world),
+            "guided_samples_per_step": statistics.mean(units),
+            "frame_rate_projected": {"value": frame_rate, "unit": UNIT,
+                                     "how": "each stage's measured time scaled by its fraction of the frame "
+                                            "(records, rays, bins), summed: one full frame's time"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": sample, "cpu": host_cpu()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -659,6 +664,7 @@ def run_gpu(args, world, rank, local):
         return
     # roofline of the dominant kernel (guide_build_pdf's field kernel)
     peak, peak_kind = measured_peaks()
+    l2_peak, l2_how = l2_read_peak(dev)
     gms = statistics.mean(guide_ms)
     alg = trace_algorithmic_bytes(w, B, N)
     achieved = alg["bytes"] / (gms / 1e3) / 1e9
@@ -667,10 +673,7 @@ def run_gpu(args, world, rank, local):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": w.desc, "rays": R, "records": n_rec, "bins": B, "grid": N,
-                   "svo_depth": w.depth, "svo_nodes": svo.n_nodes, "l2": "flushed (256 MiB write) between steps",
-                   "parallelism": f"replicas x{world}",
-                   "streams": "bin_rays on a second stream beside svo_accumulate; the field waits for both"},
+        "config": arm_config(w, svo.n_nodes, world),
         "sequential_step": {"value": seq_v, "unit": UNIT,
                             "ms_per_step": statistics.mean(seq_ms),
                             "calls": "the same five calls one after the other on one stream (the stage times)"},
@@ -692,9 +695,20 @@ def run_gpu(args, world, rank, local):
         "roofline": {"kernel": "k_guide_build", "bound": "hbm", "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                      "peak_kind": peak_kind, "algorithmic_bytes": alg["bytes"],
-                     "algorithmic_model": alg["model"], "ncu": issue},
+                     "algorithmic_model": alg["model"], "ncu": issue,
+                     "note": "algorithmic bytes over the measured HBM copy bandwidth, as the contract defines it; "
+                             "most of these bytes are L1/L2 hits (traffic = DRAM bytes per launch), so "
+                             "l2_roofline, dram_roofline and issue_roofline say what bounds the kernel"},
         "issue_roofline": issue_roofline(issue, gms, clk.get("sm_mhz") if clk else None,
                                          torch.cuda.get_device_properties(dev).multi_processor_count),
+        "l2_roofline": {"kernel": "k_guide_build", "bound": "l2", "achieved": achieved, "peak": l2_peak,
+                        "unit": "GB/s", "frac": achieved / l2_peak, "peak_kind": l2_how,
+                        "note": "the same algorithmic bytes against the L2 read bandwidth measured here: the "
+                                "walk's node records are served from L1/L2"},
+        "dram_roofline": ({"kernel": "k_guide_build", "bound": "hbm", "achieved": traffic / (gms / 1e3) / 1e9,
+                           "peak": peak, "unit": "GB/s", "frac": traffic / (gms / 1e3) / 1e9 / peak,
+                           "note": "DRAM bytes per launch (ncu, committed capture of this source) over the "
+                                   "live kernel time"} if traffic else None),
         "clocks": clk,
     }
     if not args.no_learned:
@@ -729,8 +743,9 @@ def run_gpu(args, world, rank, local):
 
 def learned_section(args, w, svo):
     """Learned proposal vs the SVO-traced field on the same frame: online
-    training (65,536 traced bins per step), held-out KL, and per-pixel variance
-    of guided two-bounce estimates at equal samples per pixel."""
+    training (65,536 traced bins per step), held-out KL, and the per-pixel
+    variance and guided samples/s of the batched frame (one guided bounce per
+    path from the 1080p camera, cache fixed) at equal samples per pixel."""
     import torch
     from paper_2405_06997_gb300 import learned as LG, wfpg as W
     # online training on the frame's own guided points (the primary hits), targets traced on the fly
@@ -758,7 +773,10 @@ def learned_section(args, w, svo):
     flop = 3 * 157440 * 65536  # forward + both backward GEMMs per layer
     peak, _ = measured_peaks("bf16_tflops_sustained")
     tau = 1.5 * floor
-    cmp = LG.compare_proposals(w, svo, tr.mlp, frames=args.learned_frames, alpha=0.5, seed=w.seed)
+    cam = dict(eye=(0.5, 0.5, -1.0), forward=(0.0, 0.0, 1.0), up=(0.0, 1.0, 0.0), vfov=40.0, width=1920,
+               height=1080, max_depth=1, rr_depth=2)
+    cmp = LG.compare_proposals(svo, w.scene, tr.mlp, cam, batches=8, frames=args.learned_frames, alpha=0.5,
+                               seed=w.seed)
     return {"train_steps": args.learned_steps, "train_batch_bins": 65536, "train_seconds": train_s,
             "train_points": "the frame's primary hits (4096 held out)",
             "train_step_mlp_ms": step_ms,
@@ -1066,6 +1084,29 @@ def read_profile_traffic():
                                         "active_lanes_per_warp_instruction": d["active_lanes_per_warp_instruction"],
                                         "warp_instructions_per_launch": d["warp_instructions_per_launch"],
                                         "limiter": "instruction issue and latency with divergence (DRAM well below peak)"}
+
+
+def l2_read_peak(dev, mib=32, reps=40, trials=5):
+    """L2 read bandwidth of this GPU, measured here: wfpg_stream_read over an
+    L2-resident buffer (reads through L2 only), best of `trials` launches,
+    bytes read / CUDA-event time."""
+    import torch
+    from paper_2405_06997_gb300 import wfpg as W
+    buf = torch.ones(mib << 18, dtype=torch.float32, device=dev)
+    sink = torch.zeros(1, dtype=torch.int32, device=dev)
+    blocks = 4 * torch.cuda.get_device_properties(dev).multi_processor_count
+    W.stream_read(buf, 2, sink, blocks)
+    best = None
+    for _ in range(trials):
+        a, b2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        W.stream_read(buf, reps, sink, blocks)
+        b2.record()
+        b2.synchronize()
+        ms = a.elapsed_time(b2)
+        best = ms if best is None else min(best, ms)
+    return (mib << 20) * reps / (best / 1e3) / 1e9, f"wfpg_stream_read: {mib} MiB buffer x {reps} passes through L2, " \
+        f"{blocks} blocks of 512 threads, best of {trials}"
 
 
 def main():

@@ -414,6 +414,29 @@ WFPG_API int guide_learned_build_pdf(wfpg_mlp* mlp, const float* pos, const floa
                                      float* cdf_row, float* cdf_marg, void* stream);
 
 /*
+ * guide_learned_logits -- the network's logits for n samples (n <= max_batch):
+ * logits[i][c] (device float [n][1024]) = the output layer's pre-softmax value
+ * of cell c for the sample at pos/nrm[i], computed as guide_learned_build_pdf
+ * computes it (bfloat16 operands, float32 accumulation).  For checking the
+ * network against a reference and for callers that post-process the
+ * distribution themselves.  Errors: null argument, n outside [1, max_batch]
+ * (WFPG_ERR_CAPACITY), size <= 0.
+ */
+WFPG_API int guide_learned_logits(wfpg_mlp* mlp, const float* pos, const float* nrm, uint32_t n,
+                                  const wfpg_learned_params* p, float* logits, void* stream);
+
+/*
+ * mlp_adam_step -- one Adam step (Kingma & Ba 2015) on the float32 master
+ * weights with a caller-supplied gradient: grad is a device array of
+ * WFPG_MLP_PARAMS floats in the parameter order above (e.g. the sum of several
+ * guide_learned_train_step gradients).  Moments and step count are the
+ * handle's, shared with guide_learned_train_step's own updates; the bfloat16
+ * weight copies are refreshed.  opt->update is not read (the step is taken).
+ * Errors: null argument; lr < 0, beta1 or beta2 outside [0, 1), eps < 0.
+ */
+WFPG_API int mlp_adam_step(wfpg_mlp* mlp, const float* grad, const wfpg_adam_params* opt, void* stream);
+
+/*
  * guide_learned_train_step -- one step on n samples (n <= max_batch): pos/nrm
  * (xyz) of the sample points and target[n][1024], any non-negative field per
  * sample (normalised here; e.g. the pdf of guide_build_pdf at N = 32).
@@ -591,6 +614,14 @@ WFPG_API int wfpg_cast_rays(const wfpg_scene* scene, const float* o, const float
 WFPG_API int wfpg_cast_rays_svo(const wfpg_svo* svo, const wfpg_scene* scene, const float* o, const float* d,
                                 uint32_t n, float tmin, float* t_out, uint32_t* prim_out, float* nrm_out,
                                 void* stream);
+
+/* Measurement helper (not part of the paper's method): reads `bytes` of the
+ * device buffer `buf` `reps` times through the L2 cache only (no L1
+ * allocation), with `blocks` blocks of 512 threads; a buffer that fits in L2
+ * gives the L2 read bandwidth the cone march is measured against.  *sink is
+ * written only in a case the data makes unlikely (it keeps the loads).  buf
+ * and bytes must be 16-byte aligned; reps, blocks >= 1. */
+WFPG_API int wfpg_stream_read(const void* buf, size_t bytes, int reps, uint32_t* sink, int blocks, void* stream);
 
 /* -------------------------------------------------------------------------
  * Inspection (used by tests; each synchronises `stream`).  Host buffers are

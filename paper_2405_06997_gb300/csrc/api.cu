@@ -56,15 +56,32 @@ void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 void note_launches(long long n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
 }  // namespace wfpg
 
+namespace wfpg {
+thread_local cudaError_t g_launch_error = cudaSuccess;
+int launch_status() {
+    const cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) return WFPG_OK;
+    g_launch_error = e;
+    return WFPG_ERR_CUDA;
+}
+cudaError_t take_launch_error() {
+    cudaError_t e = g_launch_error;
+    g_launch_error = cudaSuccess;
+    if (e == cudaSuccess) e = cudaGetLastError();
+    return e;
+}
+}  // namespace wfpg
+
 namespace {
 thread_local std::string g_last_error;
 
 int fail(int code, const std::string& msg) {
     g_last_error = msg;
+    wfpg::g_launch_error = cudaSuccess;  // a reported failure consumes any remembered launch error
     return code;
 }
 int cuda_fail(const char* where) {
-    cudaError_t e = cudaGetLastError();
+    const cudaError_t e = wfpg::take_launch_error();
     return fail(WFPG_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
 bool valid_n(int N) { return N == 8 || N == 16 || N == 32 || N == 64 || N == 128; }

@@ -264,7 +264,7 @@ int bin_rays_impl(const wfpg_svo* s, const float* pos, const float* nrm, uint32_
     if (bin_cap > 0)
         WFPG_LAUNCH(k_bin_origins, div_up(bin_cap, T), T, 0, st, bin_offset, ray_order, n, nd, n_bins_dev, bin_cap,
                     p->seed, p->frame, frame_dev, origin_ray);
-    return cudaGetLastError() == cudaSuccess ? WFPG_OK : WFPG_ERR_CUDA;
+    return launch_status();
 }
 
 }  // namespace wfpg

@@ -90,7 +90,7 @@ int bin_rays_static(const wfpg_svo* s, const float* pos, const float* nrm, uint3
                                        bin_cap, n_bins_dev, scratch, (size_t)WFPG_BIN_STATIC_SCRATCH_BYTES,
                                        static_cast<cudaStream_t>(stream));
     if (rc == WFPG_ERR_CUDA)
-        return static_fail(rc, std::string("bin_rays_static: ") + cudaGetErrorString(cudaGetLastError()));
+        return static_fail(rc, std::string("bin_rays_static: ") + cudaGetErrorString(wfpg::take_launch_error()));
     if (rc != WFPG_OK) return static_fail(rc, "bin_rays_static: failed");
     return WFPG_OK;
 }

@@ -230,6 +230,13 @@ __device__ __forceinline__ float3 cosine_dir(float nx, float ny, float nz, float
 // ---------------------------------------------------------------------------
 // host-side count of kernel launches issued by this library
 void note_launch();
+// Reads (and so clears) the last CUDA launch error: WFPG_OK, or WFPG_ERR_CUDA
+// with the error remembered for this thread's next error message.
+int launch_status();
+// The error launch_status() remembered on this thread (cleared), else a fresh
+// cudaGetLastError().
+cudaError_t take_launch_error();
+
 #define WFPG_LAUNCH(kernel, grid, block, smem, stream, ...)          \
     do {                                                              \
         kernel<<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__);   \

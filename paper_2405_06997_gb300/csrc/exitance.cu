@@ -121,7 +121,7 @@ int accumulate(wfpg_svo* s, const float* pos, const float* wout, const float* L,
         WFPG_LAUNCH(k_reduce_level, div_up(cnt, T), T, 0, st, s->level_off[l], cnt, l + 1 == D, s->node, s->route,
                     as, ac, ts, tc, s->value);
     }
-    return cudaGetLastError() == cudaSuccess ? WFPG_OK : WFPG_ERR_CUDA;
+    return launch_status();
 }
 
 }  // namespace wfpg

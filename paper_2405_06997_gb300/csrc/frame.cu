@@ -682,7 +682,7 @@ struct wfpg_frame {
             if (rc != WFPG_OK) return rc;
         }
         WFPG_LAUNCH(k_frame_end, 1, 1, 0, st, F);
-        return cudaGetLastError() == cudaSuccess ? WFPG_OK : WFPG_ERR_CUDA;
+        return launch_status();
     }
     // tables for the product proposal, allocated outside any capture (kept for the frame's lifetime)
     bool ensure_product_tables() {

@@ -890,7 +890,7 @@ static int launch_guide(const TraceArgs& T, const GuideArgs& G, const FusedArgs&
         WFPG_LAUNCH(k_zero_part_counters, div_up(bin_cap, 256), 256, 0, st, cdf_marg, G.N, n_bins_dev, bin_cap);
     WFPG_LAUNCH(kernel, grid, kThreads, smem, st, T, G, F, pos, origin_ray, n_bins_dev, bin_cap, pdf, cdf_row,
                 cdf_marg, status, bin_next, parts, (uint32_t)std::min<uint64_t>(slots, 0xFFFFFFFFull));
-    return cudaGetLastError() == cudaSuccess ? WFPG_OK : WFPG_ERR_CUDA;
+    return launch_status();
 }
 
 static void trace_setup(const wfpg_svo* s, const wfpg_guide_params* p, TraceArgs* T, GuideArgs* G,
@@ -1005,7 +1005,7 @@ int guide_fused_impl(const wfpg_svo* s, const float* pos, const float* nrm, cons
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     WFPG_LAUNCH(k_spill_sample, (uint32_t)sms * 8, kSpillChunk, 0, st, F, p->N);
-    return cudaGetLastError() == cudaSuccess ? WFPG_OK : WFPG_ERR_CUDA;
+    return launch_status();
 }
 
 int field_pdf_impl(const float* field, int N, const uint32_t* n_bins_dev, uint32_t bin_cap, float* pdf,
@@ -1016,7 +1016,7 @@ int field_pdf_impl(const float* field, int N, const uint32_t* n_bins_dev, uint32
         cudaFuncSetAttribute(k_field_pdf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return WFPG_ERR_CUDA;
     WFPG_LAUNCH(k_field_pdf, bin_cap, 256, smem, st, field, N, n_bins_dev, bin_cap, pdf, cdf_row, cdf_marg);
-    return cudaGetLastError() == cudaSuccess ? WFPG_OK : WFPG_ERR_CUDA;
+    return launch_status();
 }
 
 int guide_sample_impl(const float* pdf, const float* cdf_row, const float* cdf_marg, int N, uint32_t bin_cap,
@@ -1025,7 +1025,7 @@ int guide_sample_impl(const float* pdf, const float* cdf_row, const float* cdf_m
     if (n == 0) return WFPG_OK;
     WFPG_LAUNCH(k_guide_sample, div_up(n, 256), 256, 0, st, pdf, cdf_row, cdf_marg, N, bin_cap, bin_of_ray,
                                                    reinterpret_cast<const float2*>(u), n, dir, pdf_out, cell);
-    return cudaGetLastError() == cudaSuccess ? WFPG_OK : WFPG_ERR_CUDA;
+    return launch_status();
 }
 
 // mixture density alpha * table density + (1 - alpha) * cos+ / pi of given
@@ -1055,7 +1055,7 @@ int mix_eval_impl(const float* pdf, int N, uint32_t bin_cap, const uint32_t* n_b
     if (n == 0) return WFPG_OK;
     WFPG_LAUNCH(k_mix_eval, div_up(n, 256), 256, 0, st, pdf, N, bin_cap, n_bins_dev, bin_of_ray, nrm, dir, n, n_dev,
                 alpha, out);
-    return cudaGetLastError() == cudaSuccess ? WFPG_OK : WFPG_ERR_CUDA;
+    return launch_status();
 }
 
 int sample_mix_impl(const float* pdf, const float* cdf_row, const float* cdf_marg, int N, uint32_t bin_cap,
@@ -1064,14 +1064,14 @@ int sample_mix_impl(const float* pdf, const float* cdf_row, const float* cdf_mar
     if (n == 0) return WFPG_OK;
     WFPG_LAUNCH(k_sample_mix, div_up(n, 256), 256, 0, st, pdf, cdf_row, cdf_marg, N, bin_cap, n_bins_dev, bin_of_ray,
                 nrm, u, n, n_dev, alpha, dir, pdf_out);
-    return cudaGetLastError() == cudaSuccess ? WFPG_OK : WFPG_ERR_CUDA;
+    return launch_status();
 }
 
 int guide_eval_impl(const float* pdf, int N, uint32_t bin_cap, const uint32_t* bin, const float* dir, uint32_t n,
                     float* out, cudaStream_t st) {
     if (n == 0) return WFPG_OK;
     WFPG_LAUNCH(k_guide_eval, div_up(n, 256), 256, 0, st, pdf, N, bin_cap, bin, dir, n, out);
-    return cudaGetLastError() == cudaSuccess ? WFPG_OK : WFPG_ERR_CUDA;
+    return launch_status();
 }
 
 }  // namespace wfpg

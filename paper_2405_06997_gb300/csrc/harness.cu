@@ -60,6 +60,29 @@ SvoCast svo_cast_view(const wfpg_svo* s) {
 
 int set_last_error(int code, const std::string& msg);
 
+
+// Streaming read of an L2-resident buffer through the L2 only (ld.global.cg:
+// no L1 allocation), `reps` passes; the XOR of everything read goes to *sink
+// only when it equals a value no input makes likely, which keeps the loads.
+__global__ void __launch_bounds__(512) k_stream_read(const uint4* __restrict__ a, size_t n, int reps,
+                                                     uint32_t* __restrict__ sink) {
+    uint32_t acc = 0;
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (int r = 0; r < reps; ++r) {
+        size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+        for (; i + 3 * stride < n; i += 4 * stride) {
+            const uint4 v0 = __ldcg(a + i), v1 = __ldcg(a + i + stride), v2 = __ldcg(a + i + 2 * stride),
+                        v3 = __ldcg(a + i + 3 * stride);
+            acc ^= v0.x ^ v0.y ^ v0.z ^ v0.w ^ v1.x ^ v1.y ^ v1.z ^ v1.w ^ v2.x ^ v2.y ^ v2.z ^ v2.w ^ v3.x ^
+                   v3.y ^ v3.z ^ v3.w;
+        }
+        for (; i < n; i += stride) {
+            const uint4 v = __ldcg(a + i);
+            acc ^= v.x ^ v.y ^ v.z ^ v.w;
+        }
+    }
+    if (acc == 0x9e3779b9u) *sink = acc;
+}
 }  // namespace wfpg
 
 extern "C" int wfpg_cast_rays(const wfpg_scene* scene, const float* o, const float* d, uint32_t n, float tmin,
@@ -83,5 +106,18 @@ extern "C" int wfpg_cast_rays_svo(const wfpg_svo* svo, const wfpg_scene* scene, 
                 wfpg::svo_cast_view(svo), wfpg::prims_of(*scene), o, d, n, tmin, t_out, prim_out, nrm_out);
     if (cudaGetLastError() != cudaSuccess)
         return wfpg::set_last_error(WFPG_ERR_CUDA, "wfpg_cast_rays_svo: launch failed");
+    return WFPG_OK;
+}
+
+extern "C" int wfpg_stream_read(const void* buf, size_t bytes, int reps, uint32_t* sink, int blocks, void* stream) {
+    if (!buf || !sink) return wfpg::set_last_error(WFPG_ERR_INVALID_ARG, "wfpg_stream_read: null argument");
+    if ((reinterpret_cast<uintptr_t>(buf) & 15) != 0 || (bytes & 15) != 0)
+        return wfpg::set_last_error(WFPG_ERR_INVALID_ARG, "wfpg_stream_read: buffer and size must be 16-byte aligned");
+    if (reps < 1 || blocks < 1)
+        return wfpg::set_last_error(WFPG_ERR_INVALID_ARG, "wfpg_stream_read: reps and blocks must be >= 1");
+    if (bytes == 0) return WFPG_OK;
+    WFPG_LAUNCH(wfpg::k_stream_read, blocks, 512, 0, static_cast<cudaStream_t>(stream),
+                static_cast<const uint4*>(buf), bytes / 16, reps, sink);
+    if (cudaGetLastError() != cudaSuccess) return wfpg::set_last_error(WFPG_ERR_CUDA, "wfpg_stream_read: launch failed");
     return WFPG_OK;
 }

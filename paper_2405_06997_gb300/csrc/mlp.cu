@@ -594,8 +594,9 @@ void convert_weights(wfpg_mlp* s, cudaStream_t st) {
     WFPG_LAUNCH(k_convert, div_up(kOut * kHid, T), T, 0, st, s->params + kOffW4, kOut, kHid, s->w4, s->w4t);
 }
 
-// forward through the hidden layers and the logits for n rows (X already set)
-void forward(wfpg_mlp* s, int n, bool keep_transposes, cudaStream_t st) {
+// forward through the hidden layers and the logits for n rows (X already set);
+// the logits go to z_out ([n][1024]) when given, else to the handle's buffer
+void forward(wfpg_mlp* s, int n, bool keep_transposes, cudaStream_t st, float* z_out = nullptr) {
     const int mp = (int)s->mpad;
     GemmArgs g = gargs(s->x, kIn, s->w1, kIn, n, kHid, kIn, s->status);
     g.O = s->h1;
@@ -619,13 +620,23 @@ void forward(wfpg_mlp* s, int n, bool keep_transposes, cudaStream_t st) {
     g.bias = s->params + kOffB3;
     gemm<64, kEpiBf16Relu>(g, 1, st);
     g = gargs(s->h3, kHid, s->w4, kHid, n, kOut, kHid, s->status);
-    g.C = s->z;
+    g.C = z_out ? z_out : s->z;
     g.ldc = kOut;
     g.bias = s->params + kOffB4;
     gemm<256, kEpiF32>(g, 1, st);
 }
 
 int mlp_fail(int code, const std::string& msg) { return wfpg::set_last_error(code, msg); }
+
+// one Adam step on the float32 master weights with the gradient `grad` (device,
+// kParams floats), then fresh bfloat16 copies; the step count advances
+void adam_update(wfpg_mlp* s, const float* grad, const wfpg_adam_params& opt, cudaStream_t st) {
+    s->step += 1;
+    const float c1 = 1.0f - powf(opt.beta1, (float)s->step), c2 = 1.0f - powf(opt.beta2, (float)s->step);
+    WFPG_LAUNCH(k_adam, div_up(kParams, 256), 256, 0, st, s->params, s->m, s->v, grad, (uint32_t)kParams, opt.lr,
+                opt.beta1, opt.beta2, opt.eps, c1, c2);
+    convert_weights(s, st);
+}
 
 }  // namespace
 
@@ -746,6 +757,32 @@ int guide_learned_build_pdf(wfpg_mlp* s, const float* pos, const float* nrm, con
     return WFPG_OK;
 }
 
+int guide_learned_logits(wfpg_mlp* s, const float* pos, const float* nrm, uint32_t n, const wfpg_learned_params* p,
+                         float* logits, void* stream) {
+    if (!s || !p || !pos || !nrm || !logits)
+        return mlp_fail(WFPG_ERR_INVALID_ARG, "guide_learned_logits: null argument");
+    if (n == 0 || n > s->max_batch)
+        return mlp_fail(WFPG_ERR_CAPACITY, "guide_learned_logits: n must be in [1, max_batch]");
+    if (!(p->size > 0.0f)) return mlp_fail(WFPG_ERR_INVALID_ARG, "guide_learned_logits: size must be > 0");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    WFPG_LAUNCH(k_mlp_features, div_up(n, 128), 128, 0, st, pos, nrm, (const uint32_t*)nullptr,
+                (const uint32_t*)nullptr, n, p->lo[0], p->lo[1], p->lo[2], 1.0f / p->size, s->x, (bf16*)nullptr, 0);
+    forward(s, (int)n, false, st, logits);
+    if (cudaGetLastError() != cudaSuccess) return mlp_fail(WFPG_ERR_CUDA, "guide_learned_logits: launch failed");
+    return WFPG_OK;
+}
+
+int mlp_adam_step(wfpg_mlp* s, const float* grad, const wfpg_adam_params* opt, void* stream) {
+    if (!s || !grad || !opt) return mlp_fail(WFPG_ERR_INVALID_ARG, "mlp_adam_step: null argument");
+    if (!(opt->lr >= 0.0f) || !(opt->beta1 >= 0.0f && opt->beta1 < 1.0f) || !(opt->beta2 >= 0.0f && opt->beta2 < 1.0f) ||
+        !(opt->eps >= 0.0f))
+        return mlp_fail(WFPG_ERR_INVALID_ARG, "mlp_adam_step: need lr >= 0, beta1 and beta2 in [0, 1), eps >= 0");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    adam_update(s, grad, *opt, st);
+    if (cudaGetLastError() != cudaSuccess) return mlp_fail(WFPG_ERR_CUDA, "mlp_adam_step: launch failed");
+    return WFPG_OK;
+}
+
 int guide_learned_train_step(wfpg_mlp* s, const float* pos, const float* nrm, uint32_t n, const float* target,
                              const wfpg_learned_params* p, const wfpg_adam_params* opt, float* loss_out,
                              float* grad_out, void* stream) {
@@ -755,7 +792,6 @@ int guide_learned_train_step(wfpg_mlp* s, const float* pos, const float* nrm, ui
     if (!pos || !nrm || !target) return mlp_fail(WFPG_ERR_INVALID_ARG, "guide_learned_train_step: null array");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int mp = (int)s->mpad, N = (int)n;
-    const int T = 256;
     bool ok = cudaMemsetAsync(s->grad, 0, 4 * kParams, st) == cudaSuccess &&
               cudaMemsetAsync(s->loss, 0, 4, st) == cudaSuccess;
     WFPG_LAUNCH(k_mlp_features, div_up(n, 128), 128, 0, st, pos, nrm, (const uint32_t*)nullptr,
@@ -803,13 +839,7 @@ int guide_learned_train_step(wfpg_mlp* s, const float* pos, const float* nrm, ui
     }
     if (grad_out) ok = ok && cudaMemcpyAsync(grad_out, s->grad, 4 * kParams, cudaMemcpyDeviceToDevice, st) == cudaSuccess;
     if (loss_out) ok = ok && cudaMemcpyAsync(loss_out, s->loss, 4, cudaMemcpyDeviceToDevice, st) == cudaSuccess;
-    if (opt->update) {
-        s->step += 1;
-        const float c1 = 1.0f - powf(opt->beta1, (float)s->step), c2 = 1.0f - powf(opt->beta2, (float)s->step);
-        WFPG_LAUNCH(k_adam, div_up(kParams, T), T, 0, st, s->params, s->m, s->v, s->grad, (uint32_t)kParams, opt->lr,
-                    opt->beta1, opt->beta2, opt->eps, c1, c2);
-        convert_weights(s, st);
-    }
+    if (opt->update) adam_update(s, s->grad, *opt, st);
     if (!ok || cudaGetLastError() != cudaSuccess)
         return mlp_fail(WFPG_ERR_CUDA, "guide_learned_train_step: launch failed");
     return WFPG_OK;

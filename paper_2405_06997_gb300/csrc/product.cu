@@ -207,7 +207,7 @@ int product_sums_impl(const float* pdf, int N, uint32_t bin_cap, const uint32_t*
                       cudaStream_t st) {
     if (bin_cap == 0) return WFPG_OK;
     WFPG_LAUNCH(k_product_sums, bin_cap, 64, 0, st, pdf, N, n_bins_dev, bin_cap, S);
-    return cudaGetLastError() == cudaSuccess ? WFPG_OK : WFPG_ERR_CUDA;
+    return launch_status();
 }
 
 int product_sample_impl(const float* pdf, const float* S, int N, uint32_t bin_cap, const uint32_t* n_bins_dev,
@@ -217,7 +217,7 @@ int product_sample_impl(const float* pdf, const float* S, int N, uint32_t bin_ca
     if (n == 0) return WFPG_OK;
     WFPG_LAUNCH(k_product_sample, div_up(n, 256), 256, 0, st, pdf, S, N, bin_cap, n_bins_dev, bin_of_ray, nrm, u, n,
                 n_dev, alpha, dir, pdf_out, cell);
-    return cudaGetLastError() == cudaSuccess ? WFPG_OK : WFPG_ERR_CUDA;
+    return launch_status();
 }
 
 int product_eval_impl(const float* pdf, const float* S, int N, uint32_t bin_cap, const uint32_t* n_bins_dev,
@@ -226,7 +226,7 @@ int product_eval_impl(const float* pdf, const float* S, int N, uint32_t bin_cap,
     if (n == 0) return WFPG_OK;
     WFPG_LAUNCH(k_product_eval, div_up(n, 256), 256, 0, st, pdf, S, N, bin_cap, n_bins_dev, bin, nrm, dir, n, n_dev,
                 alpha, out);
-    return cudaGetLastError() == cudaSuccess ? WFPG_OK : WFPG_ERR_CUDA;
+    return launch_status();
 }
 
 }  // namespace wfpg

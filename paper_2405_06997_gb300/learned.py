@@ -4,14 +4,13 @@ the fallback rule, and an equal-samples variance comparison of guided path
 estimates.
 
 Everything on the hot path runs in libwfpg.so (guide_build_pdf,
-guide_learned_build_pdf, guide_learned_train_step, guide_sample,
-guide_eval_pdf, wfpg_cast_rays); this module only schedules the calls and
-accumulates the estimates.
+guide_learned_build_pdf, guide_learned_train_step, frame_run and its
+sampling, mixture density and shading kernels); this module only schedules
+the calls and reads back their results.
 """
 from __future__ import annotations
 
 import math
-import time
 
 import numpy as np
 import torch
@@ -126,130 +125,66 @@ def traced_frame_kl(trainer: "OnlineTrainer") -> float:
     return float((qa * (qa.log() - qb.log())).sum(dim=1).mean().item())
 
 
-def _cosine_dirs(nrm, u):
-    """Cosine-distributed directions about unit normals (u: [n, 2] uniforms)."""
-    n = nrm
-    helper = torch.where((n[:, 0].abs() > 0.9).unsqueeze(1),
-                         torch.tensor([0.0, 1.0, 0.0], device=n.device).expand_as(n),
-                         torch.tensor([1.0, 0.0, 0.0], device=n.device).expand_as(n))
-    t = torch.linalg.cross(helper, n)
-    t = t / t.norm(dim=1, keepdim=True)
-    b = torch.linalg.cross(n, t)
-    r = torch.sqrt(u[:, 0])
-    phi = 2 * math.pi * u[:, 1]
-    z = torch.sqrt(torch.clamp(1 - u[:, 0], min=0))
-    return t * (r * torch.cos(phi)).unsqueeze(1) + b * (r * torch.sin(phi)).unsqueeze(1) + n * z.unsqueeze(1)
+def run_batches(frame, batches, frames):
+    """Runs `batches` groups of `frames` frames on a batched frame (update off
+    for an unchanging cache) and returns, per group, the mean over pixels of
+    the per-pixel variance of one frame's estimate (frame_image), with the
+    guided samples and the GPU time of all groups (frame_stats, CUDA events)."""
+    var, ms, guided = [], 0.0, 0
+    for _ in range(batches):
+        frame.reset_image()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        frame.run(frames)
+        e1.record()
+        e1.synchronize()
+        ms += e0.elapsed_time(e1)
+        guided += frame.stats()["guided_samples"]
+        var.append(float(frame.image()[1].double().mean().item()))
+    return {"batch_variance": var, "variance": float(np.mean(var)), "ms_per_frame": ms / (batches * frames),
+            "guided_samples": guided, "guided_samples_per_s": guided / (ms / 1e3) if ms > 0 else None}
 
 
-def guided_estimates(w, svo, proposal, *, frames=16, alpha=0.5, mlp=None, seed=1, device="cuda", l_min=4,
-                     c_ray=512, bin_cap=16384):
-    """Per-pixel estimates of the light leaving each primary hit toward the
-    camera, one path per pixel per frame, two bounces deep: the first bounce
-    direction w1 is drawn from alpha * guided + (1 - alpha) * cosine and
-    weighted by that mixture density (so the estimator stays unbiased); the
-    second bounce is cosine-sampled.
-        L = (albedo1 / pi) cos1 / p(w1) * (Le(x2) + albedo2 * Le(x3))
-    proposal: 'svo' (traced field), 'svo_product' (traced field times the BSDF at
-    8 x 8 blocks, Sec. 3.6), 'learned' (MLP) or 'bsdf' (cosine only).
-    Rays are binned with Partition-S (l_min, c_ray; the paper's Table 1 uses
-    c_ray = 512 and its l_min 5, i.e. 4 here).  Returns the per-pixel mean and
-    variance over frames and the guiding time per frame (binning + field/PDF +
-    sampling + MIS density), in seconds.  A cheap proposal can afford finer
-    bins (smaller c_ray, more bins: bin_cap) than tracing."""
-    q = _dev(w.scene.quads, device)
-    sp = _dev(w.scene.spheres, device)
-    emission = _dev(w.scene.emission, device)
-    albedo_all = _dev(w.scene.albedo, device)
-    albedo = _dev(w.scene.albedo[w.extra["ray_prim"]], device)
-    pos = _dev(w.ray_pos, device)
-    nrm = _dev(w.ray_nrm, device)
-    R = pos.shape[0]
-    B = bin_cap  # Partition-S at c_ray = 512 gives a few thousand bins at 1080p
-    s1 = torch.zeros(R, dtype=torch.float64, device=device)
-    s2 = torch.zeros(R, dtype=torch.float64, device=device)
-    guide = None
-    times = []
-    a = alpha if proposal != "bsdf" else 0.0
-    for f in range(frames):
-        u = _dev(inputs.uniforms24(seed * 7919 + f, (R, 7)), device)
-        dc = _cosine_dirs(nrm, u[:, 2:4])
-        t_guide = 0.0
-        if a > 0:
-            e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-            e[0].record()
-            r = W.bin_rays(svo, pos, l_min=l_min, c_ray=c_ray, seed=seed, frame=f, bin_cap=B)
-            if proposal in ("svo", "svo_product"):
-                guide = W.guide_build_pdf(svo, pos, r["origin_ray"], r["n_bins"], B, N=32, jitter=True, blur=True,
-                                          seed=seed, frame=f, out=guide)
-            else:
-                guide = W.guide_learned_build_pdf(mlp, pos, nrm, r["origin_ray"], r["n_bins"], B, lo=w.scene.lo,
-                                                  size=w.scene.size, out=guide)
-            if proposal == "svo_product":
-                # Sec. 3.6: the field times the ray's BSDF at 8 x 8 blocks; the call
-                # returns the mixture (alpha product, 1 - alpha cosine) and its density
-                S = W.guide_product_sums(guide[0], 32, n_bins=r["n_bins"])
-                uu = torch.stack([u[:, 0], u[:, 1], u[:, 4]], dim=1).contiguous()
-                d, pmix, _ = W.guide_product_sample(guide[0], S, 32, r["bin_of_ray"], nrm, uu, alpha=a,
-                                                    n_bins=r["n_bins"])
-                e[1].record()
-                e[2].record()
-                e[3].record()
-                e[3].synchronize()
-                t_guide = e[0].elapsed_time(e[3]) / 1e3
-            else:
-                dg, _, _ = W.guide_sample(*guide, 32, r["bin_of_ray"], u[:, 0:2].contiguous())
-                e[1].record()
-                d = torch.where((u[:, 4] < a).unsqueeze(1), dg, dc).contiguous()
-                e[2].record()
-                pg = W.guide_eval_pdf(guide[0], 32, r["bin_of_ray"], d)
-                e[3].record()
-                e[3].synchronize()
-                t_guide = (e[0].elapsed_time(e[1]) + e[2].elapsed_time(e[3])) / 1e3
-        else:
-            d = dc.contiguous()
-        cos = torch.clamp((d * nrm).sum(dim=1), min=0.0)
-        if proposal == "svo_product":
-            p = pmix
-        else:
-            p = (1 - a) * cos / math.pi
-            if a > 0:
-                p = p + a * pg
-        t1, prim1, n2 = W.cast_rays(q, sp, (pos + 1e-4 * nrm).contiguous(), d)
-        hit1 = prim1 >= 0
-        pi1 = prim1.clamp(min=0).long()
-        le1 = torch.where(hit1, emission[pi1], torch.zeros_like(t1))
-        x2 = pos + t1.clamp(min=0).unsqueeze(1) * d
-        d2 = _cosine_dirs(n2, u[:, 5:7]).contiguous()
-        _, prim2, _ = W.cast_rays(q, sp, (x2 + 1e-4 * n2).contiguous(), d2, with_normal=False)
-        le2 = torch.where(prim2 >= 0, emission[prim2.clamp(min=0).long()], torch.zeros_like(t1))
-        li = le1 + torch.where(hit1 & (le1 == 0), albedo_all[pi1] * le2, torch.zeros_like(le2))
-        est = torch.where(p > 0, albedo / math.pi * li * cos / p, torch.zeros_like(p)).double()
-        s1 += est
-        s2 += est * est
-        times.append(t_guide)
-    mean = s1 / frames
-    var = (s2 - s1 * s1 / frames) / (frames - 1)
-    return mean, var, float(np.mean(times[1:] if len(times) > 1 else times))
+def variance_ratio(a, b):
+    """Mean and standard error over batches of the ratio a / b of two runs'
+    batch variances (batch i of both runs draws the same frame indices)."""
+    r = np.asarray(a["batch_variance"]) / np.asarray(b["batch_variance"])
+    return float(r.mean()), float(r.std(ddof=1) / np.sqrt(len(r))) if len(r) > 1 else float("inf")
 
 
-def compare_proposals(w, svo, mlp, *, frames=16, alpha=0.5, seed=1, fine_c_ray=32, fine_bin_cap=65536):
-    """Equal-samples comparison of the traced and learned proposals (and the
-    cosine-only baseline): mean per-pixel variance, mean estimate, proposal
-    time per frame and guided samples/s.  'learned_fine' evaluates the MLP on
-    Partition-S bins of fine_c_ray rays (the MLP's cost per bin is a few
-    hundred kFLOP, a traced field's is N^2 cone rays)."""
+def compare_proposals(svo, scene, mlp, camera, *, batches=8, frames=16, alpha=0.5, seed=1, traced_bins=None,
+                      learned_bins=None, with_product=True, with_bsdf=True):
+    """Equal-samples comparison of the guided proposals on the batched frame
+    (libwfpg.so's frame_run: binning, guided or learned tables, the one-sample
+    mixture with cosine sampling and its exact density, shading, per-pixel
+    variance; nothing here but scheduling).  camera: Frame keyword arguments
+    (eye, forward, up, vfov, width, height, max_depth, ...).  traced_bins /
+    learned_bins: Partition-S (l_min, c_ray) of each proposal; the MLP costs a
+    few hundred kFLOP per bin against N^2 cone rays for a traced field, so it
+    can afford finer bins.  Returns per-proposal variance, ms per frame and
+    guided samples/s, and the variance ratios over the traced field with their
+    standard errors."""
+    traced_bins = traced_bins or {"l_min": 4, "c_ray": 512}
+    learned_bins = learned_bins or {"l_min": 4, "c_ray": 32}
+    base = dict(camera, alpha=alpha, seed=seed, update=False)
+    runs = [("svo", dict(base, proposal=0, N=32, **traced_bins), False),
+            ("learned", dict(base, proposal=1, N=32, **learned_bins), True)]
+    if with_product:
+        runs.append(("svo_product", dict(base, proposal=2, N=32, **traced_bins), False))
+    if with_bsdf:
+        runs.append(("bsdf", dict(base, proposal=0, N=32, **dict(traced_bins, alpha=0.0)), False))
     out = {}
-    runs = (("bsdf", "bsdf", {}), ("svo", "svo", {}), ("svo_product", "svo_product", {}), ("learned", "learned", {}),
-            ("learned_fine", "learned", {"c_ray": fine_c_ray, "bin_cap": fine_bin_cap}))
-    for name, proposal, kw in runs:
-        m, v, t = guided_estimates(w, svo, proposal, frames=frames, alpha=alpha, mlp=mlp, seed=seed, **kw)
-        out[name] = {"mean": float(m.mean().item()), "variance": float(v.mean().item()),
-                     "guiding_seconds_per_frame": t, "guided_samples_per_s": len(w.ray_pos) / t if t > 0 else None}
-    out["learned_fine"]["c_ray"] = fine_c_ray
-    for name in ("svo_product", "learned", "learned_fine"):
-        out[f"variance_ratio_{name}_over_svo"] = out[name]["variance"] / out["svo"]["variance"]
-        # work-normalised: (variance x guiding time) of the traced over the learned proposal
-        out[f"efficiency_ratio_{name}_over_svo"] = (
-            (out["svo"]["variance"] * out["svo"]["guiding_seconds_per_frame"]) /
-            (out[name]["variance"] * out[name]["guiding_seconds_per_frame"]))
+    for name, kw, uses_mlp in runs:
+        f = W.Frame(svo, scene, **kw)
+        if uses_mlp:
+            f.set_mlp(mlp, scene.lo, scene.size)
+        f.run(2)  # warm-up (capture of the frame's graph)
+        out[name] = run_batches(f, batches, frames)
+        out[name]["bins"] = {k: kw[k] for k in ("l_min", "c_ray")}
+        del f
+    for name in list(out):
+        if name != "svo":
+            m, se = variance_ratio(out[name], out["svo"])
+            out[f"variance_ratio_{name}_over_svo"] = m
+            out[f"variance_ratio_{name}_over_svo_se"] = se
     return out

@@ -133,6 +133,8 @@ def lib():
             "guide_product_sample": [P, P, I32, U32, P, P, P, P, U32, P, F, P, P, P, P],
             "guide_product_eval": [P, P, I32, U32, P, P, P, P, U32, F, P, P],
             "wfpg_cast_rays_svo": [P, P, P, P, U32, F, P, P, P, P],
+            "bin_rays_static": [P, P, P, U32, P, P, P, P, P, P, U32, P, P],
+            "wfpg_stream_read": [P, SZ, I32, P, I32, P],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -428,8 +430,6 @@ def bin_rays_static(svo: SVO, pos, nrm=None, *, mode=BIN_PARTITION_S, l_min=2, c
     needs more scratch than that array holds.  Calls whose work overlaps on
     the GPU share the array and must be serialised."""
     fn = lib().bin_rays_static
-    fn.restype = I32
-    fn.argtypes = [P, P, P, U32, P, P, P, P, P, P, U32, P, P]
     n = pos.shape[0]
     dev = pos.device
     n_sizes = 0 if sizes is None else sizes.numel()
@@ -476,6 +476,8 @@ def _declare_mlp():
         "mlp_status": [P, P, I32, P],
         "guide_learned_build_pdf": [P, P, P, P, P, U32, P, P, P, P, P],
         "guide_learned_train_step": [P, P, P, U32, P, P, P, P, P, P],
+        "guide_learned_logits": [P, P, P, U32, P, P, P],
+        "mlp_adam_step": [P, P, P, P],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -573,6 +575,31 @@ def guide_learned_train_step(mlp: MLP, pos, nrm, target, *, lo=(0, 0, 0), size=1
         _ptr(loss, torch.float32, 1), _ptr(grad, torch.float32, MLP_PARAMS) if want_grad else None,
         _stream(stream)))
     return loss, (grad if want_grad else None)
+
+
+def guide_learned_logits(mlp: MLP, pos, nrm, *, lo=(0, 0, 0), size=1.0, out=None, stream=None):
+    """The network's logits [n][1024] for the samples at pos / nrm (float32)."""
+    n = pos.shape[0]
+    if out is None:
+        out = torch.empty((n, 1024), dtype=torch.float32, device=pos.device)
+    p = _learned(lo, size, 0.0)
+    _check(_declare_mlp().guide_learned_logits(mlp.handle, _ptr(pos, torch.float32, 3 * n, "pos"),
+                                               _ptr(nrm, torch.float32, 3 * n, "nrm"), n, C.byref(p),
+                                               _ptr(out, torch.float32, n * 1024, "out"), _stream(stream)))
+    return out
+
+
+def mlp_adam_step(mlp: MLP, grad, *, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    """One Adam step with a caller-supplied gradient (float32 CUDA tensor of MLP_PARAMS)."""
+    o = AdamParams(lr=lr, beta1=beta1, beta2=beta2, eps=eps, update=1)
+    _check(_declare_mlp().mlp_adam_step(mlp.handle, _ptr(grad, torch.float32, MLP_PARAMS, "grad"), C.byref(o),
+                                        _stream(stream)))
+
+
+def stream_read(buf, reps, sink, blocks, stream=None):
+    """Reads the CUDA tensor `buf` `reps` times through L2 only (wfpg_stream_read)."""
+    _check(lib().wfpg_stream_read(_ptr(buf), buf.numel() * buf.element_size(), int(reps), _ptr(sink, torch.int32, 1),
+                                  int(blocks), _stream(stream)))
 
 
 def cast_rays(quads, spheres, o, d, tmin=1e-5, with_normal=True, stream=None, tris=None):

@@ -42,6 +42,9 @@ def lib():
         "frame_create": [P, P, P, P, P, P, P, P],
         "frame_destroy": [P],
         "mlp_create": [P, U32, P, P],
+        "bin_rays_static": [P, P, P, U32, P, P, P, P, P, P, U32, P, P],
+        "guide_learned_logits": [P, P, P, U32, P, P, P],
+        "mlp_adam_step": [P, P, P, P],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -138,6 +141,48 @@ def test_bin_rays_checks_mode_sizes_and_capacity(lib):
     bp = W.BinParams()
     bp.mode = 9
     assert lib.bin_rays_workspace_size(b, 10, C.byref(bp), C.byref(nb)) == INVALID and "mode" in err(lib)
+
+
+def test_bin_rays_static_checks_mode_sizes_and_capacity(lib):
+    """The allocation-free binning call makes bin_rays's argument checks before
+    it looks at its static scratch or the device."""
+    b = C.addressof(host_buf())
+    sizes = (U32 * 4)(5, 5, 5, 5)
+
+    def call(mode, n, svo=b, nrm=b, sz=sizes, n_sizes=4, bin_cap=8, params=True):
+        bp = W.BinParams()
+        bp.mode, bp.n_sizes = mode, n_sizes
+        return lib.bin_rays_static(svo, b, nrm, n, C.byref(bp) if params else None, sz, b, b, b, b, bin_cap, b,
+                                   None)
+
+    assert call(W.BIN_PARTITION_S, 10, svo=None) == INVALID and "null svo" in err(lib)
+    assert call(W.BIN_PARTITION_S, 10, params=False) == INVALID and "null svo or params" in err(lib)
+    assert call(7, 10) == INVALID and "mode" in err(lib)
+    assert call(W.BIN_PARTITION_S, 0x80000000) == INVALID and "2^31" in err(lib)
+    assert call(W.BIN_RUNS, 10, nrm=None) == INVALID and "nrm" in err(lib)
+    assert call(W.BIN_RUNS, 10, sz=None) == INVALID and "sizes" in err(lib)
+    assert call(W.BIN_RUNS, 10, n_sizes=0) == INVALID and "sizes" in err(lib)
+    assert call(W.BIN_RUNS, 10, n_sizes=4, bin_cap=3) == CAPACITY and "bin_cap" in err(lib)
+    assert err(lib).startswith("bin_rays_static:")
+
+
+def test_learned_logits_and_adam_step_check_their_arguments(lib):
+    b = C.addressof(host_buf())
+    lp = W.LearnedParams()
+    lp.size = 1.0
+    opt = W.AdamParams(lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, update=1)
+    assert lib.guide_learned_logits(None, b, b, 4, C.byref(lp), b, None) == INVALID and "null" in err(lib)
+    assert lib.guide_learned_logits(b, None, b, 4, C.byref(lp), b, None) == INVALID
+    assert lib.guide_learned_logits(b, b, b, 4, None, b, None) == INVALID
+    assert lib.guide_learned_logits(b, b, b, 4, C.byref(lp), None, None) == INVALID
+    assert lib.mlp_adam_step(None, b, C.byref(opt), None) == INVALID and "null" in err(lib)
+    assert lib.mlp_adam_step(b, None, C.byref(opt), None) == INVALID
+    assert lib.mlp_adam_step(b, b, None, None) == INVALID
+    for bad in (dict(lr=-1.0), dict(beta1=1.0), dict(beta2=-0.5), dict(eps=-1e-8)):
+        o = W.AdamParams(lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, update=1)
+        for k, v in bad.items():
+            setattr(o, k, v)
+        assert lib.mlp_adam_step(b, b, C.byref(o), None) == INVALID and "beta1" in err(lib)
 
 
 def test_guide_build_checks_its_parameters(lib):

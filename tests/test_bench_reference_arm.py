@@ -25,3 +25,11 @@ def test_reference_arm_prints_one_contract_line():
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1 and cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    # value and ms_per_step are measured: the guided samples the step made over its wall time
+    rate = d["guided_samples_per_step"] / (d["ms_per_step"] / 1e3)
+    assert abs(d["value"] - rate) <= 1e-9 * rate
+    assert d["frame_rate_projected"]["value"] > 0 and d["frame_rate_projected"]["how"]
+    # the same config dict as the GPU arm prints
+    for k in ("workload", "rays", "records", "bins", "grid", "svo_depth", "svo_nodes", "l2", "parallelism", "streams"):
+        assert k in d["config"], k
+    assert d["config"]["records"] == 1_646_633 and d["config"]["svo_nodes"] > 0

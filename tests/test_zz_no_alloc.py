@@ -60,6 +60,31 @@ def test_static_scratch_matches_workspace_version_twice():
     assert svo.status() == 0
 
 
+def test_static_scratch_calls_allocate_nothing():
+    """With its outputs allocated up front and one warm-up call made (the
+    library's kernels loaded), further calls leave the device's free memory
+    and torch's allocated bytes unchanged."""
+    w = inputs.tiny_box(6, n_rays=6007)
+    svo = W.svo_from_scene(w.scene, w.depth)
+    pos = dev(w.ray_pos)
+    n = pos.shape[0]
+    bin_cap = max(1, min(n, svo.n_nodes))
+    out = dict(bin_of_ray=torch.empty(n, dtype=torch.int32, device="cuda"),
+               ray_order=torch.empty(n, dtype=torch.int32, device="cuda"),
+               bin_offset=torch.empty(bin_cap + 1, dtype=torch.int32, device="cuda"),
+               origin_ray=torch.empty(bin_cap, dtype=torch.int32, device="cuda"),
+               n_bins=torch.zeros(1, dtype=torch.int32, device="cuda"))
+    W.bin_rays_static(svo, pos, l_min=2, c_ray=32, seed=1, frame=0, bin_cap=bin_cap, out=out)
+    torch.cuda.synchronize()
+    free0, torch0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_allocated()
+    for k in range(3):
+        W.bin_rays_static(svo, pos, l_min=2, c_ray=32, seed=1, frame=k + 1, bin_cap=bin_cap, out=out)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert torch.cuda.memory_allocated() == torch0
+    assert svo.status() == 0
+
+
 def test_static_scratch_rejects_calls_that_do_not_fit():
     w = inputs.tiny_box(4, n_rays=10)
     svo = W.svo_from_scene(w.scene, w.depth)
