@@ -711,6 +711,7 @@ def run_gpu(args, world, rank, local):
                                    "live kernel time"} if traffic else None),
         "clocks": clk,
     }
+    line["large_fields"] = large_field_records(w, svo, inp, binout, B, peak, l2_peak, flush)
     if not args.no_learned:
         line["learned"] = learned_section(args, w, svo)
     if not args.no_batched:
@@ -1008,6 +1009,43 @@ def city_section(args):
     out["learned_training"] = {"steps": args.city_train_steps, "batch_bins": 65536, "seconds": train_s,
                                "heldout_kl": kl, "fallback_threshold": tau, "uses_learned": use}
     out["chosen"] = "learned" if use else "svo_traced (fallback)"
+    return out
+
+
+def large_field_records(w, svo, inp, binout, B, peak, l2_peak, flush, reps=10):
+    """guide_build_pdf on the 1080p workload's bins at N = 64 and 128 (the paper's
+    first-depth resolutions): mean CUDA-event time of `reps` launches (L2
+    flushed before each), cone rays/s, and the roofline of its algorithmic bytes
+    (the oracle's block counts at that N) against HBM and the measured L2."""
+    import torch
+    from paper_2405_06997_gb300 import wfpg as W
+    out = {}
+    dev = inp["ray_pos"].device
+    for N in (64, 128):
+        guide = (torch.empty((B, N * N), dtype=torch.float32, device=dev),
+                 torch.empty((B, N * N), dtype=torch.float32, device=dev),
+                 torch.empty((B, N), dtype=torch.float32, device=dev))
+        for k in range(3):
+            W.guide_build_pdf(svo, inp["ray_pos"], binout["origin_ray"], binout["n_bins"], B, N=N, jitter=True,
+                              blur=True, seed=w.seed, frame=9000 + k, out=guide)
+        ms = []
+        for k in range(reps):
+            flush.zero_()
+            a, b2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            W.guide_build_pdf(svo, inp["ray_pos"], binout["origin_ray"], binout["n_bins"], B, N=N, jitter=True,
+                              blur=True, seed=w.seed, frame=9100 + k, out=guide)
+            b2.record()
+            b2.synchronize()
+            ms.append(a.elapsed_time(b2))
+        m = statistics.mean(ms)
+        alg = trace_algorithmic_bytes(w, B, N)
+        ach = alg["bytes"] / (m / 1e3) / 1e9
+        out[f"N{N}"] = {"ms": m, "cone_rays_per_s": B * N * N / (m / 1e3),
+                        "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                                     "l2_peak": l2_peak, "l2_frac": ach / l2_peak, "algorithmic_bytes": alg["bytes"],
+                                     "algorithmic_model": alg["model"]},
+                        "kernels": "k_guide_march (cone march, (bin, 1024-cell) units) + k_field_pdf (blur, CDFs, PDF)"}
     return out
 
 

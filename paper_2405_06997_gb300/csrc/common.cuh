@@ -76,6 +76,10 @@ __device__ __forceinline__ int grid_index(float x, float lo, float scale, int D)
     return (int)g;
 }
 
+// deepest level of the SVO's top index (a dense grid per level 0 .. this)
+constexpr int kTopLevelMax = 6;
+constexpr uint32_t kTopNodeMask = (1u << 28) - 1u;
+
 // node record used by every tree walk: first child's global id and child mask
 struct Node {
     uint32_t first_child;

@@ -43,7 +43,18 @@ struct TraceArgs {
     float omega;
     int cos_weight;
     uint32_t smem_nodes;
+    const uint32_t* top;  // the SVO's top index (levels 0 .. G), NULL when it has none
+    int G;                // deepest indexed level, -1 without an index
 };
+
+// offset of level l's grid in the top index: 8^0 + ... + 8^(l-1) = (8^l - 1) / 7
+__device__ __forceinline__ uint32_t top_offset(int l) { return ((1u << (3 * l)) - 1u) / 7u; }
+// the top index's entry of leaf cell (cx, cy, cz) at level l: (level << 28) | node
+__device__ __forceinline__ uint32_t top_entry(const TraceArgs& T, int l, int cx, int cy, int cz) {
+    const int sh = T.D - l;
+    const uint32_t i = ((uint32_t)(cz >> sh) << (2 * l)) | ((uint32_t)(cy >> sh) << l) | (uint32_t)(cx >> sh);
+    return __ldg(T.top + top_offset(l) + i);
+}
 
 struct GuideArgs {
     int N;
@@ -298,6 +309,270 @@ __device__ __forceinline__ bool ray_start(const TraceArgs& T, bool has_origin, b
     return alive;
 }
 
+// separable [1 2 1] / 4 blur of an N x N field with the octahedral mirror at the
+// edges (rows first into tmp, then columns back into field); every thread of
+// the CTA calls it, with the barriers inside
+__device__ __forceinline__ void blur_field(float* field, float* tmp, int N, int tid, int nthreads) {
+    const int NN = N * N;
+    for (int c = tid; c < NN; c += nthreads) {
+        const int i = c % N, j = c / N;
+        const float up = (j > 0) ? field[(j - 1) * N + i] : field[N - 1 - i];
+        const float dn = (j < N - 1) ? field[(j + 1) * N + i] : field[(N - 1) * N + (N - 1 - i)];
+        const float m = field[c];
+        tmp[c] = __fmul_rn(__fadd_rn(__fadd_rn(up, dn), __fadd_rn(m, m)), 0.25f);
+    }
+    __syncthreads();
+    for (int c = tid; c < NN; c += nthreads) {
+        const int i = c % N, j = c / N;
+        const float lf = (i > 0) ? tmp[c - 1] : tmp[(N - 1 - j) * N];
+        const float rt = (i < N - 1) ? tmp[c + 1] : tmp[(N - 1 - j) * N + (N - 1)];
+        const float m = tmp[c];
+        field[c] = __fmul_rn(__fadd_rn(__fadd_rn(lf, rt), __fadd_rn(m, m)), 0.25f);
+    }
+    __syncthreads();
+}
+
+// The cone rays of cells c0 .. c0 + cn - 1 of one bin (Sec. 3.3, Eq. 6): each
+// lane marches one cell's ray through the SVO, a lane whose ray ends takes the
+// next cell; out[q] = eps + the cone query of cell c0 + q (shared or global
+// memory).  Called by every thread of the CTA; ends with a barrier.
+template <int kGuideThreads, bool kStage>
+__device__ __forceinline__ void march_chunk(const TraceArgs& T, const GuideArgs& G, const Node* s_nodes,
+                                            uint32_t* s_stack, float* s_ray, float* wbuf, int* s_next, int c0,
+                                            int cn, int chunk, bool has_origin, bool inside, float gx, float gy,
+                                            float gz, uint64_t jseed, uint64_t jstream, float tn, uint32_t* status,
+                                            float* out) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t lt = (1u << lane) - 1u;
+    const int D = T.D;
+    const int res = 1 << D;
+    const float fres = (float)res;
+    const float INF = __int_as_float(0x7f800000);
+    const int cap = 3 * res + 16;
+    uint32_t* stk = s_stack + tid;  // this thread's node path, one entry per level (stride = block size)
+    // ---- directions of this chunk's cells, computed by all threads together
+    for (int q = tid; kStage && q < cn; q += kGuideThreads) {
+        float3 d, iv;
+        cell_ray(T, G, c0 + q, jseed, jstream, tn, &d, &iv);
+        s_ray[0 * chunk + q] = d.x;
+        s_ray[1 * chunk + q] = d.y;
+        s_ray[2 * chunk + q] = d.z;
+        s_ray[3 * chunk + q] = iv.x;
+        s_ray[4 * chunk + q] = iv.y;
+        s_ray[5 * chunk + q] = iv.z;
+    }
+    if (tid == 0) *s_next = 0;
+    __syncthreads();
+    // ---- cone rays: each lane marches one cell's ray; finished lanes take the next cell
+    int q = -1;  // current cell of the chunk (-1: none, >= cn: no work left)
+    float dx = 0.f, dy = 0.f, dz = 0.f, ivx = 0.f, ivy = 0.f, ivz = 0.f, t = 0.f;
+    int cx = 0, cy = 0, cz = 0, level = 0, steps = 0;
+    uint32_t node = 0;
+    int wb_n = 0, wb_head = 0;  // unstaged: entries in this warp's ray buffer, next one to hand out
+    bool wb_dry = false;        // unstaged: no cells of the chunk left for this warp
+    float* wb = wbuf + warp * (kWbWords * 32);
+    for (;;) {
+        const bool idle = q < 0;
+        const uint32_t need = __ballot_sync(0xffffffffu, idle);
+        if (kStage) {
+            if (need) {
+                const int leader = __ffs(need) - 1;
+                int base = 0;
+                if (lane == leader) base = atomicAdd(s_next, __popc(need));
+                base = __shfl_sync(0xffffffffu, base, leader);
+                if (idle) {
+                    q = base + __popc(need & lt);
+                    if (q < cn) {
+                        dx = s_ray[0 * chunk + q];
+                        dy = s_ray[1 * chunk + q];
+                        dz = s_ray[2 * chunk + q];
+                        ivx = s_ray[3 * chunk + q];
+                        ivy = s_ray[4 * chunk + q];
+                        ivz = s_ray[5 * chunk + q];
+                        const bool alive = ray_start(T, has_origin, inside, gx, gy, gz, dx, dy, dz, ivx, ivy,
+                                                     ivz, res, fres, &t, &cx, &cy, &cz);
+                        if (!alive) {
+                            out[q] = __fadd_rn(G.eps, 0.0f);
+                            q = -1;
+                        } else {
+                            node = 0;
+                            level = T.G >= 0 ? -1 : 0;  // -1: enter through the top index
+                            steps = 0;
+                            stk[0] = 0;
+                        }
+                    }
+                }
+            }
+            // leave only when every lane has run out of cells (a lane whose new ray
+            // died at its start is idle again and fetches once more)
+            if (__all_sync(0xffffffffu, q >= cn)) break;
+            if (q < 0 || q >= cn) continue;  // idle, or out of cells: no ray to step
+        } else {
+            // the whole warp sets up the next 32 cells' rays at once (converged), so a
+            // lane that finishes a ray takes a ready one instead of stalling its warp
+            // on a setup of its own
+            if (need && wb_head == wb_n && !wb_dry) {
+                int base = 0;
+                if (lane == 0) base = atomicAdd(s_next, 32);
+                base = __shfl_sync(0xffffffffu, base, 0);
+                wb_n = max(0, min(32, cn - base));
+                wb_head = 0;
+                wb_dry = wb_n == 0;
+                if (lane < wb_n) {
+                    const int c = c0 + base + lane;
+                    float3 d, iv;
+                    cell_ray(T, G, c, jseed, jstream, tn, &d, &iv);
+                    float t0;
+                    int x0, y0, z0;
+                    const bool alive = ray_start(T, has_origin, inside, gx, gy, gz, d.x, d.y, d.z, iv.x,
+                                                 iv.y, iv.z, res, fres, &t0, &x0, &y0, &z0);
+                    if (!alive) out[base + lane] = __fadd_rn(G.eps, 0.0f);
+                    wb[0 * 32 + lane] = __int_as_float(alive ? base + lane : -1);
+                    wb[1 * 32 + lane] = d.x;
+                    wb[2 * 32 + lane] = d.y;
+                    wb[3 * 32 + lane] = d.z;
+                    wb[4 * 32 + lane] = iv.x;
+                    wb[5 * 32 + lane] = iv.y;
+                    wb[6 * 32 + lane] = iv.z;
+                    wb[7 * 32 + lane] = t0;
+                    wb[8 * 32 + lane] = __int_as_float(x0);
+                    wb[9 * 32 + lane] = __int_as_float(y0);
+                    wb[10 * 32 + lane] = __int_as_float(z0);
+                }
+                __syncwarp();
+            }
+            if (need && wb_head < wb_n) {
+                const int k = wb_head + __popc(need & lt);
+                if (idle && k < wb_n) {
+                    q = __float_as_int(wb[0 * 32 + k]);  // -1: the ray died at its start
+                    dx = wb[1 * 32 + k];
+                    dy = wb[2 * 32 + k];
+                    dz = wb[3 * 32 + k];
+                    ivx = wb[4 * 32 + k];
+                    ivy = wb[5 * 32 + k];
+                    ivz = wb[6 * 32 + k];
+                    t = wb[7 * 32 + k];
+                    cx = __float_as_int(wb[8 * 32 + k]);
+                    cy = __float_as_int(wb[9 * 32 + k]);
+                    cz = __float_as_int(wb[10 * 32 + k]);
+                    node = 0;
+                    level = T.G >= 0 ? -1 : 0;  // -1: enter through the top index
+                    steps = 0;
+                    stk[0] = 0;
+                }
+                wb_head = min(wb_n, wb_head + __popc(need));
+                __syncwarp();  // entries are read before a refill overwrites them
+            }
+            if (wb_dry && __all_sync(0xffffffffu, q < 0)) break;
+            if (q < 0) continue;  // idle: no ray to step
+        }
+        // ---- one step: deepest existing node holding the cell, then hit or skip its empty block.
+        // At most kDescentPerPass levels per pass of the loop: a lane with a deeper descent
+        // goes on in the next pass instead of holding its whole warp in this one
+        if (level < 0) {
+            // the deepest existing node at a level <= G holding the cell, from the top index
+            const uint32_t e = top_entry(T, T.G, cx, cy, cz);
+            level = (int)(e >> 28);
+            node = e & kTopNodeMask;
+            stk[level * kGuideThreads] = node;
+        }
+        bool settled = true;
+        for (int dl = 0; level < D; ++dl) {
+            if (dl == kDescentPerPass) {
+                settled = false;
+                break;
+            }
+            const Node nd = load_node(T, s_nodes, node);
+            const int sh = D - 1 - level;
+            const int k = ((cx >> sh) & 1) | (((cy >> sh) & 1) << 1) | (((cz >> sh) & 1) << 2);
+            if (!((nd.mask >> k) & 1u)) break;
+            node = child_id(nd, k);
+            ++level;
+            stk[level * kGuideThreads] = node;
+        }
+        if (!settled) continue;
+        float L = 0.0f;
+        bool done = false;
+        if (level == D && t >= T.t_skip) {
+            // Eq. 6: footprint A = t^2 omega; the level whose squared side is closest
+            const float A = __fmul_rn(__fmul_rn(t, t), T.omega);
+            float side = T.S, bd = INF;
+            int best = 0;
+            for (int l = 0; l <= D; ++l) {
+                const float diff = fabsf(__fsub_rn(__fmul_rn(side, side), A));
+                if (diff <= bd) {
+                    bd = diff;
+                    best = l;
+                }
+                side = __fmul_rn(side, 0.5f);
+            }
+            // the hit leaf's ancestor at that level: on this ray's node path below G, else in the top index
+            const uint32_t an =
+                best >= T.G ? stk[best * kGuideThreads] : (top_entry(T, best, cx, cy, cz) & kTopNodeMask);
+            const float4 Nn = T.normal[an];
+            const float2 V = T.value[an];
+            const float dd = __fadd_rn(__fadd_rn(__fmul_rn(Nn.x, dx), __fmul_rn(Nn.y, dy)), __fmul_rn(Nn.z, dz));
+            L = (dd <= 0.0f) ? V.x : V.y;  // the side facing back along the ray
+            if (T.cos_weight) L = __fmul_rn(L, fabsf(dd));
+            done = true;
+        } else {
+            // leave the empty block (or a leaf entered before t_skip) through its first exit crossing
+            const int sl = (level == D) ? 0 : D - level - 1;
+            const int size = 1 << sl;
+            const int bx = (cx >> sl) << sl, by = (cy >> sl) << sl, bz = (cz >> sl) << sl;
+            const int ex = ivx > 0.0f ? bx + size : bx - 1;
+            const int ey = ivy > 0.0f ? by + size : by - 1;
+            const int ez = ivz > 0.0f ? bz + size : bz - 1;
+            const float tex = ivx != 0.0f ? cross_time(ex, ivx > 0.0f, gx, ivx) : INF;
+            const float tey = ivy != 0.0f ? cross_time(ey, ivy > 0.0f, gy, ivy) : INF;
+            const float tez = ivz != 0.0f ? cross_time(ez, ivz > 0.0f, gz, ivz) : INF;
+            const int a = (tex <= tey && tex <= tez) ? 0 : (tey <= tez ? 1 : 2);
+            const float tx = a == 0 ? tex : (a == 1 ? tey : tez);
+            // the two other axes p < q, gathered by selects so that every lane runs
+            // the catch-up exactly twice (ties: an axis precedes the exit axis a
+            // when its index is smaller)
+            const int p = a == 0 ? 1 : 0, q = a == 2 ? 1 : 2;
+            const int cp = p == 0 ? cx : cy, cq = q == 1 ? cy : cz;
+            const int bp = p == 0 ? bx : by, bq = q == 1 ? by : bz;
+            const float gp = p == 0 ? gx : gy, gq = q == 1 ? gy : gz;
+            const float ip = p == 0 ? ivx : ivy, iq = q == 1 ? ivy : ivz;
+            const float dp = p == 0 ? dx : dy, dq = q == 1 ? dy : dz;
+            const int np = advance_axis(cp, bp, size, gp, ip, __fmul_rn(dp, T.scale), tx, p < a);
+            const int nq = advance_axis(cq, bq, size, gq, iq, __fmul_rn(dq, T.scale), tx, q < a);
+            const int na = a == 0 ? ex : (a == 1 ? ey : ez);
+            const int nx = a == 0 ? na : np;
+            const int ny = a == 1 ? na : (p == 1 ? np : nq);
+            const int nz = a == 2 ? na : nq;
+            if (tx == INF || na < 0 || na >= res) {
+                done = true;  // left the grid: miss
+            } else if (++steps > cap) {
+                atomicOr(status, (uint32_t)WFPG_STATUS_TRACE_CAP);
+                done = true;
+            } else {
+                // restart the descent from the deepest ancestor shared with the new cell, or
+                // through the top index when that ancestor lies above its deepest level
+                const uint32_t diff = (uint32_t)((cx ^ nx) | (cy ^ ny) | (cz ^ nz));
+                const int lc = D - 1 - (31 - __clz(diff));
+                if (lc >= T.G) {
+                    level = lc;
+                    node = stk[lc * kGuideThreads];
+                } else {
+                    level = -1;
+                }
+                cx = nx;
+                cy = ny;
+                cz = nz;
+                t = tx;
+            }
+        }
+        if (done) {
+            out[q] = __fadd_rn(G.eps, L);
+            q = -1;
+        }
+    }
+    __syncthreads();
+}
+
 // 1024 resident threads per SM (32 warps): up to 64 registers a thread.  The
 // walk is issue-bound, and 64 registers (fewer recomputed values) beat 48
 // registers with 40 warps on the GB300; the fused variant gets the same budget
@@ -326,9 +601,7 @@ __global__ void __launch_bounds__(kGuideThreads, 1024 / kGuideThreads) k_guide_b
     __shared__ int s_next;
     __shared__ uint32_t s_slot;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const uint32_t lt = (1u << lane) - 1u;
     constexpr int kWarps = kGuideThreads / 32;
-    uint32_t* stk = s_stack + tid;  // this thread's node path, one entry per level (stride = block size)
     for (uint32_t i = tid; i < T.smem_nodes; i += kGuideThreads) {
         const uint2 v = __ldg(reinterpret_cast<const uint2*>(T.node) + i);
         s_nodes[i].first_child = v.x;
@@ -340,7 +613,6 @@ __global__ void __launch_bounds__(kGuideThreads, 1024 / kGuideThreads) k_guide_b
     const int res = 1 << D;
     const float fres = (float)res;
     const float INF = __int_as_float(0x7f800000);
-    const int cap = 3 * res + 16;
     // Work units are (bin, part): the cells of a bin are split over `parts` CTAs
     // (1 for the fused call); the CTA that completes a bin's last part gathers its
     // field and finishes the bin.  Units are taken dynamically: the first by CTA
@@ -376,212 +648,9 @@ __global__ void __launch_bounds__(kGuideThreads, 1024 / kGuideThreads) k_guide_b
         const uint64_t jstream = bin_stream(G.frame_dev ? *G.frame_dev : G.frame, b);
         for (int c0 = cbeg; c0 < cend; c0 += chunk) {
             const int cn = min(chunk, cend - c0);  // cells in this chunk
-            // ---- directions of this chunk's cells, computed by all threads together
-            for (int q = tid; kStage && q < cn; q += kGuideThreads) {
-                float3 d, iv;
-                cell_ray(T, G, c0 + q, jseed, jstream, tn, &d, &iv);
-                s_ray[0 * chunk + q] = d.x;
-                s_ray[1 * chunk + q] = d.y;
-                s_ray[2 * chunk + q] = d.z;
-                s_ray[3 * chunk + q] = iv.x;
-                s_ray[4 * chunk + q] = iv.y;
-                s_ray[5 * chunk + q] = iv.z;
-            }
-            if (tid == 0) s_next = 0;
-            __syncthreads();
-            // ---- cone rays: each lane marches one cell's ray; finished lanes take the next cell
-            int q = -1;  // current cell of the chunk (-1: none, >= cn: no work left)
-            float dx = 0.f, dy = 0.f, dz = 0.f, ivx = 0.f, ivy = 0.f, ivz = 0.f, t = 0.f;
-            int cx = 0, cy = 0, cz = 0, level = 0, steps = 0;
-            uint32_t node = 0;
-            int wb_n = 0, wb_head = 0;  // unstaged: entries in this warp's ray buffer, next one to hand out
-            bool wb_dry = false;        // unstaged: no cells of the chunk left for this warp
-            float* wb = wbuf + warp * (kWbWords * 32);
-            for (;;) {
-                const bool idle = q < 0;
-                const uint32_t need = __ballot_sync(0xffffffffu, idle);
-                if (kStage) {
-                    if (need) {
-                        const int leader = __ffs(need) - 1;
-                        int base = 0;
-                        if (lane == leader) base = atomicAdd(&s_next, __popc(need));
-                        base = __shfl_sync(0xffffffffu, base, leader);
-                        if (idle) {
-                            q = base + __popc(need & lt);
-                            if (q < cn) {
-                                dx = s_ray[0 * chunk + q];
-                                dy = s_ray[1 * chunk + q];
-                                dz = s_ray[2 * chunk + q];
-                                ivx = s_ray[3 * chunk + q];
-                                ivy = s_ray[4 * chunk + q];
-                                ivz = s_ray[5 * chunk + q];
-                                const bool alive = ray_start(T, r != kNone, inside, gx, gy, gz, dx, dy, dz, ivx, ivy,
-                                                             ivz, res, fres, &t, &cx, &cy, &cz);
-                                if (!alive) {
-                                    field[c0 + q] = __fadd_rn(G.eps, 0.0f);
-                                    q = -1;
-                                } else {
-                                    node = 0;
-                                    level = 0;
-                                    steps = 0;
-                                    stk[0] = 0;
-                                }
-                            }
-                        }
-                    }
-                    // leave only when every lane has run out of cells (a lane whose new ray
-                    // died at its start is idle again and fetches once more)
-                    if (__all_sync(0xffffffffu, q >= cn)) break;
-                    if (q < 0 || q >= cn) continue;  // idle, or out of cells: no ray to step
-                } else {
-                    // the whole warp sets up the next 32 cells' rays at once (converged), so a
-                    // lane that finishes a ray takes a ready one instead of stalling its warp
-                    // on a setup of its own
-                    if (need && wb_head == wb_n && !wb_dry) {
-                        int base = 0;
-                        if (lane == 0) base = atomicAdd(&s_next, 32);
-                        base = __shfl_sync(0xffffffffu, base, 0);
-                        wb_n = max(0, min(32, cn - base));
-                        wb_head = 0;
-                        wb_dry = wb_n == 0;
-                        if (lane < wb_n) {
-                            const int c = c0 + base + lane;
-                            float3 d, iv;
-                            cell_ray(T, G, c, jseed, jstream, tn, &d, &iv);
-                            float t0;
-                            int x0, y0, z0;
-                            const bool alive = ray_start(T, r != kNone, inside, gx, gy, gz, d.x, d.y, d.z, iv.x,
-                                                         iv.y, iv.z, res, fres, &t0, &x0, &y0, &z0);
-                            if (!alive) field[c] = __fadd_rn(G.eps, 0.0f);
-                            wb[0 * 32 + lane] = __int_as_float(alive ? base + lane : -1);
-                            wb[1 * 32 + lane] = d.x;
-                            wb[2 * 32 + lane] = d.y;
-                            wb[3 * 32 + lane] = d.z;
-                            wb[4 * 32 + lane] = iv.x;
-                            wb[5 * 32 + lane] = iv.y;
-                            wb[6 * 32 + lane] = iv.z;
-                            wb[7 * 32 + lane] = t0;
-                            wb[8 * 32 + lane] = __int_as_float(x0);
-                            wb[9 * 32 + lane] = __int_as_float(y0);
-                            wb[10 * 32 + lane] = __int_as_float(z0);
-                        }
-                        __syncwarp();
-                    }
-                    if (need && wb_head < wb_n) {
-                        const int k = wb_head + __popc(need & lt);
-                        if (idle && k < wb_n) {
-                            q = __float_as_int(wb[0 * 32 + k]);  // -1: the ray died at its start
-                            dx = wb[1 * 32 + k];
-                            dy = wb[2 * 32 + k];
-                            dz = wb[3 * 32 + k];
-                            ivx = wb[4 * 32 + k];
-                            ivy = wb[5 * 32 + k];
-                            ivz = wb[6 * 32 + k];
-                            t = wb[7 * 32 + k];
-                            cx = __float_as_int(wb[8 * 32 + k]);
-                            cy = __float_as_int(wb[9 * 32 + k]);
-                            cz = __float_as_int(wb[10 * 32 + k]);
-                            node = 0;
-                            level = 0;
-                            steps = 0;
-                            stk[0] = 0;
-                        }
-                        wb_head = min(wb_n, wb_head + __popc(need));
-                        __syncwarp();  // entries are read before a refill overwrites them
-                    }
-                    if (wb_dry && __all_sync(0xffffffffu, q < 0)) break;
-                    if (q < 0) continue;  // idle: no ray to step
-                }
-                // ---- one step: deepest existing node holding the cell, then hit or skip its empty block.
-                // At most kDescentPerPass levels per pass of the loop: a lane with a deeper descent
-                // goes on in the next pass instead of holding its whole warp in this one
-                bool settled = true;
-                for (int dl = 0; level < D; ++dl) {
-                    if (dl == kDescentPerPass) {
-                        settled = false;
-                        break;
-                    }
-                    const Node nd = load_node(T, s_nodes, node);
-                    const int sh = D - 1 - level;
-                    const int k = ((cx >> sh) & 1) | (((cy >> sh) & 1) << 1) | (((cz >> sh) & 1) << 2);
-                    if (!((nd.mask >> k) & 1u)) break;
-                    node = child_id(nd, k);
-                    ++level;
-                    stk[level * kGuideThreads] = node;
-                }
-                if (!settled) continue;
-                float L = 0.0f;
-                bool done = false;
-                if (level == D && t >= T.t_skip) {
-                    // Eq. 6: footprint A = t^2 omega; the level whose squared side is closest
-                    const float A = __fmul_rn(__fmul_rn(t, t), T.omega);
-                    float side = T.S, bd = INF;
-                    int best = 0;
-                    for (int l = 0; l <= D; ++l) {
-                        const float diff = fabsf(__fsub_rn(__fmul_rn(side, side), A));
-                        if (diff <= bd) {
-                            bd = diff;
-                            best = l;
-                        }
-                        side = __fmul_rn(side, 0.5f);
-                    }
-                    const uint32_t an = stk[best * kGuideThreads];
-                    const float4 Nn = T.normal[an];
-                    const float2 V = T.value[an];
-                    const float dd = __fadd_rn(__fadd_rn(__fmul_rn(Nn.x, dx), __fmul_rn(Nn.y, dy)), __fmul_rn(Nn.z, dz));
-                    L = (dd <= 0.0f) ? V.x : V.y;  // the side facing back along the ray
-                    if (T.cos_weight) L = __fmul_rn(L, fabsf(dd));
-                    done = true;
-                } else {
-                    // leave the empty block (or a leaf entered before t_skip) through its first exit crossing
-                    const int sl = (level == D) ? 0 : D - level - 1;
-                    const int size = 1 << sl;
-                    const int bx = (cx >> sl) << sl, by = (cy >> sl) << sl, bz = (cz >> sl) << sl;
-                    const int ex = ivx > 0.0f ? bx + size : bx - 1;
-                    const int ey = ivy > 0.0f ? by + size : by - 1;
-                    const int ez = ivz > 0.0f ? bz + size : bz - 1;
-                    const float tex = ivx != 0.0f ? cross_time(ex, ivx > 0.0f, gx, ivx) : INF;
-                    const float tey = ivy != 0.0f ? cross_time(ey, ivy > 0.0f, gy, ivy) : INF;
-                    const float tez = ivz != 0.0f ? cross_time(ez, ivz > 0.0f, gz, ivz) : INF;
-                    const int a = (tex <= tey && tex <= tez) ? 0 : (tey <= tez ? 1 : 2);
-                    const float tx = a == 0 ? tex : (a == 1 ? tey : tez);
-                    // the two other axes p < q, gathered by selects so that every lane runs
-                    // the catch-up exactly twice (ties: an axis precedes the exit axis a
-                    // when its index is smaller)
-                    const int p = a == 0 ? 1 : 0, q = a == 2 ? 1 : 2;
-                    const int cp = p == 0 ? cx : cy, cq = q == 1 ? cy : cz;
-                    const int bp = p == 0 ? bx : by, bq = q == 1 ? by : bz;
-                    const float gp = p == 0 ? gx : gy, gq = q == 1 ? gy : gz;
-                    const float ip = p == 0 ? ivx : ivy, iq = q == 1 ? ivy : ivz;
-                    const float dp = p == 0 ? dx : dy, dq = q == 1 ? dy : dz;
-                    const int np = advance_axis(cp, bp, size, gp, ip, __fmul_rn(dp, T.scale), tx, p < a);
-                    const int nq = advance_axis(cq, bq, size, gq, iq, __fmul_rn(dq, T.scale), tx, q < a);
-                    const int na = a == 0 ? ex : (a == 1 ? ey : ez);
-                    const int nx = a == 0 ? na : np;
-                    const int ny = a == 1 ? na : (p == 1 ? np : nq);
-                    const int nz = a == 2 ? na : nq;
-                    if (tx == INF || na < 0 || na >= res) {
-                        done = true;  // left the grid: miss
-                    } else if (++steps > cap) {
-                        atomicOr(status, (uint32_t)WFPG_STATUS_TRACE_CAP);
-                        done = true;
-                    } else {
-                        // restart the descent from the deepest ancestor shared with the new cell
-                        const uint32_t diff = (uint32_t)((cx ^ nx) | (cy ^ ny) | (cz ^ nz));
-                        level = D - 1 - (31 - __clz(diff));
-                        node = stk[level * kGuideThreads];
-                        cx = nx;
-                        cy = ny;
-                        cz = nz;
-                        t = tx;
-                    }
-                }
-                if (done) {
-                    field[c0 + q] = __fadd_rn(G.eps, L);
-                    q = -1;
-                }
-            }
-            __syncthreads();
+            march_chunk<kGuideThreads, kStage>(T, G, s_nodes, s_stack, s_ray, wbuf, &s_next, c0, cn, chunk,
+                                               r != kNone, inside, gx, gy, gz, jseed, jstream, tn, status,
+                                               field + c0);
         }
         bool finish = true;
         if (parts > 1) {  // publish this part's cells; the CTA of the bin's last part gathers them all
@@ -599,24 +668,7 @@ __global__ void __launch_bounds__(kGuideThreads, 1024 / kGuideThreads) k_guide_b
                 __syncthreads();
             }
         }
-        if (finish && G.blur) {
-            for (int c = tid; c < NN; c += kGuideThreads) {
-                const int i = c % N, j = c / N;
-                const float up = (j > 0) ? field[(j - 1) * N + i] : field[N - 1 - i];
-                const float dn = (j < N - 1) ? field[(j + 1) * N + i] : field[(N - 1) * N + (N - 1 - i)];
-                const float m = field[c];
-                tmp[c] = __fmul_rn(__fadd_rn(__fadd_rn(up, dn), __fadd_rn(m, m)), 0.25f);
-            }
-            __syncthreads();
-            for (int c = tid; c < NN; c += kGuideThreads) {
-                const int i = c % N, j = c / N;
-                const float lf = (i > 0) ? tmp[c - 1] : tmp[(N - 1 - j) * N];
-                const float rt = (i < N - 1) ? tmp[c + 1] : tmp[(N - 1 - j) * N + (N - 1)];
-                const float m = tmp[c];
-                field[c] = __fmul_rn(__fadd_rn(__fadd_rn(lf, rt), __fadd_rn(m, m)), 0.25f);
-            }
-            __syncthreads();
-        }
+        if (finish && G.blur) blur_field(field, tmp, N, tid, kGuideThreads);
         // row CDFs (one warp per row) into tmp, row totals into rowtot
         for (int j = warp; finish && j < N; j += kWarps) {
             const float tot = warp_scan_row(field + j * N, tmp + j * N, N, lane);
@@ -674,11 +726,69 @@ __global__ void __launch_bounds__(kGuideThreads, 1024 / kGuideThreads) k_guide_b
     }
 }
 
-// PDF and CDFs of given fields (one CTA per bin): row CDFs and the marginal in
-// warp order with a running maximum, pdf = f N^2 / (T 4 pi), as in the traced path
-__global__ void __launch_bounds__(256) k_field_pdf(const float* __restrict__ field, int N,
-                                                   const uint32_t* __restrict__ n_bins_dev, uint32_t bin_cap,
-                                                   float* __restrict__ pdf, float* __restrict__ cdf_row,
+// Large fields (N >= 64): the cone march alone, persistent CTAs taking (bin,
+// part) units of kMarchPart cells from a counter; eps + L of each cell goes to
+// the bin's pdf row, which k_field_pdf then blurs and turns into the PDF and
+// CDFs in place.  Without the field in shared memory a CTA needs only the top
+// SVO levels, its node paths and its ray buffers, so as many CTAs stay
+// resident as at N = 32.
+constexpr int kMarchPart = 1024;
+
+template <int kGuideThreads>
+__global__ void __launch_bounds__(kGuideThreads, 1024 / kGuideThreads)
+    k_guide_march(TraceArgs T, GuideArgs G, const float* __restrict__ pos, const uint32_t* __restrict__ origin_ray,
+                  const uint32_t* __restrict__ n_bins_dev, uint32_t bin_cap, float* __restrict__ raw,
+                  uint32_t* status, uint32_t* __restrict__ unit_next) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int N = G.N, NN = N * N, D = T.D;
+    Node* s_nodes = reinterpret_cast<Node*>(smem);
+    uint32_t* s_stack = reinterpret_cast<uint32_t*>(smem + sizeof(Node) * T.smem_nodes);
+    float* wbuf = reinterpret_cast<float*>(s_stack + (D + 1) * kGuideThreads);
+    __shared__ int s_next;
+    __shared__ uint32_t s_unit;
+    const int tid = threadIdx.x;
+    for (uint32_t i = tid; i < T.smem_nodes; i += kGuideThreads) {
+        const uint2 v = __ldg(reinterpret_cast<const uint2*>(T.node) + i);
+        s_nodes[i].first_child = v.x;
+        s_nodes[i].mask = v.y;
+    }
+    __syncthreads();
+    const uint32_t nb = n_bins_dev ? min(*n_bins_dev, bin_cap) : bin_cap;
+    const int parts = NN / kMarchPart;
+    const uint32_t n_units = nb * (uint32_t)parts;
+    const float tn = __fdiv_rn(2.0f, (float)N);
+    const float fres = (float)(1 << D);
+    for (uint32_t u = blockIdx.x; u < n_units;) {
+        const uint32_t b = u / (uint32_t)parts;
+        const int c0 = (int)(u % (uint32_t)parts) * kMarchPart;
+        const uint32_t r = origin_ray ? origin_ray[b] : b;
+        float ox = 0.0f, oy = 0.0f, oz = 0.0f;
+        if (r != kNone) {
+            ox = pos[3 * (size_t)r + 0];
+            oy = pos[3 * (size_t)r + 1];
+            oz = pos[3 * (size_t)r + 2];
+        }
+        const float gx = __fmul_rn(__fsub_rn(ox, T.lo[0]), T.scale);
+        const float gy = __fmul_rn(__fsub_rn(oy, T.lo[1]), T.scale);
+        const float gz = __fmul_rn(__fsub_rn(oz, T.lo[2]), T.scale);
+        const bool inside = gx >= 0.0f && gx <= fres && gy >= 0.0f && gy <= fres && gz >= 0.0f && gz <= fres;
+        const uint64_t jseed = purpose(G.seed, kJitterPurpose);
+        const uint64_t jstream = bin_stream(G.frame_dev ? *G.frame_dev : G.frame, b);
+        march_chunk<kGuideThreads, false>(T, G, s_nodes, s_stack, nullptr, wbuf, &s_next, c0, kMarchPart, kMarchPart,
+                                          r != kNone, inside, gx, gy, gz, jseed, jstream, tn, status,
+                                          raw + (size_t)b * NN + c0);
+        if (tid == 0) s_unit = gridDim.x + atomicAdd(unit_next, 1u);
+        __syncthreads();
+        u = s_unit;
+    }
+}
+
+// PDF and CDFs of given fields (one CTA per bin): optionally the blur, then row
+// CDFs and the marginal in warp order with a running maximum, pdf = f N^2 /
+// (T 4 pi), as in the traced path.  The field may be the pdf rows themselves
+// (each CTA reads its whole row before writing it).
+__global__ void __launch_bounds__(256) k_field_pdf(const float* field, int N, const uint32_t* __restrict__ n_bins_dev,
+                                                   uint32_t bin_cap, int blur, float* pdf, float* __restrict__ cdf_row,
                                                    float* __restrict__ cdf_marg) {
     extern __shared__ __align__(16) float fsm[];
     const int NN = N * N;
@@ -692,6 +802,7 @@ __global__ void __launch_bounds__(256) k_field_pdf(const float* __restrict__ fie
     if (b >= nb) return;
     for (int c = tid; c < NN; c += 256) f[c] = field[(size_t)b * NN + c];
     __syncthreads();
+    if (blur) blur_field(f, rows, N, tid, 256);
     for (int j = warp; j < N; j += 8) {
         const float tot = warp_scan_row(f + j * N, rows + j * N, N, lane);
         if (lane == 0) rowtot[j] = tot;
@@ -907,6 +1018,8 @@ static void trace_setup(const wfpg_svo* s, const wfpg_guide_params* p, TraceArgs
     T->cos_weight = p->cos_weight;
     const int top = s->D < kSmemTopLevels ? s->D : kSmemTopLevels;
     T->smem_nodes = s->level_off[top + 1];
+    T->top = s->top;
+    T->G = s->top_levels - 1;
     G->N = p->N;
     G->eps = p->eps;
     G->jitter = p->jitter;
@@ -941,6 +1054,29 @@ static int dispatch_guide(const wfpg_svo* s, const wfpg_guide_params* p, const T
     return WFPG_ERR_INVALID_ARG;
 }
 
+int field_pdf_impl(const float* field, int N, const uint32_t* n_bins_dev, uint32_t bin_cap, float* pdf,
+                   float* cdf_row, float* cdf_marg, cudaStream_t st, int blur);
+
+template <int kThreads>
+static int launch_march(const wfpg_svo* s, const TraceArgs& T, const GuideArgs& G, const float* pos,
+                        const uint32_t* origin_ray, const uint32_t* n_bins_dev, uint32_t bin_cap, float* pdf,
+                        float* cdf_row, float* cdf_marg, cudaStream_t st) {
+    auto kernel = k_guide_march<kThreads>;
+    const size_t smem = sizeof(Node) * T.smem_nodes + sizeof(uint32_t) * (size_t)(s->D + 1) * kThreads +
+                        sizeof(float) * (size_t)(kThreads / 32) * kWbWords * 32;
+    int rc = WFPG_OK;
+    const uint64_t slots = guide_slots(kernel, kThreads, smem, &rc);
+    if (rc != WFPG_OK) return rc;
+    const uint64_t units = (uint64_t)bin_cap * (uint64_t)(G.N * G.N / kMarchPart);
+    const uint32_t grid = (uint32_t)std::min<uint64_t>(units, slots);
+    if (cudaMemsetAsync(s->bin_next, 0, sizeof(uint32_t), st) != cudaSuccess) return WFPG_ERR_CUDA;
+    WFPG_LAUNCH(kernel, grid, kThreads, smem, st, T, G, pos, origin_ray, n_bins_dev, bin_cap, pdf, s->status,
+                s->bin_next);
+    rc = launch_status();
+    if (rc != WFPG_OK) return rc;
+    return field_pdf_impl(pdf, G.N, n_bins_dev, bin_cap, pdf, cdf_row, cdf_marg, st, G.blur);
+}
+
 int guide_build_impl(const wfpg_svo* s, const float* pos, const uint32_t* origin_ray, const uint32_t* n_bins_dev,
                      uint32_t bin_cap, const wfpg_guide_params* p, float* pdf, float* cdf_row, float* cdf_marg,
                      cudaStream_t st, const uint32_t* frame_dev) {
@@ -948,6 +1084,13 @@ int guide_build_impl(const wfpg_svo* s, const float* pos, const uint32_t* origin
     TraceArgs T;
     GuideArgs G;
     trace_setup(s, p, &T, &G, frame_dev);
+    if (p->N >= 64 && p->parts == 0) {  // large fields: the march, then the per-bin finish
+        const int threads = p->block ? p->block : kGuideDefaultThreadsMid;
+        if (threads == 64) return launch_march<64>(s, T, G, pos, origin_ray, n_bins_dev, bin_cap, pdf, cdf_row, cdf_marg, st);
+        if (threads == 128) return launch_march<128>(s, T, G, pos, origin_ray, n_bins_dev, bin_cap, pdf, cdf_row, cdf_marg, st);
+        if (threads == 256) return launch_march<256>(s, T, G, pos, origin_ray, n_bins_dev, bin_cap, pdf, cdf_row, cdf_marg, st);
+        return WFPG_ERR_INVALID_ARG;
+    }
     FusedArgs F{};
     return dispatch_guide<false>(s, p, T, G, F, pos, origin_ray, n_bins_dev, bin_cap, pdf, cdf_row, cdf_marg, st);
 }
@@ -1009,13 +1152,13 @@ int guide_fused_impl(const wfpg_svo* s, const float* pos, const float* nrm, cons
 }
 
 int field_pdf_impl(const float* field, int N, const uint32_t* n_bins_dev, uint32_t bin_cap, float* pdf,
-                   float* cdf_row, float* cdf_marg, cudaStream_t st) {
+                   float* cdf_row, float* cdf_marg, cudaStream_t st, int blur) {
     if (bin_cap == 0) return WFPG_OK;
     const size_t smem = sizeof(float) * (2 * (size_t)N * N + 2 * (size_t)N);
     if (smem > 48 * 1024 &&
         cudaFuncSetAttribute(k_field_pdf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return WFPG_ERR_CUDA;
-    WFPG_LAUNCH(k_field_pdf, bin_cap, 256, smem, st, field, N, n_bins_dev, bin_cap, pdf, cdf_row, cdf_marg);
+    WFPG_LAUNCH(k_field_pdf, bin_cap, 256, smem, st, field, N, n_bins_dev, bin_cap, blur, pdf, cdf_row, cdf_marg);
     return launch_status();
 }
 

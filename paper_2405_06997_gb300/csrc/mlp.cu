@@ -28,7 +28,7 @@ typedef __nv_bfloat16 bf16;
 
 namespace wfpg {
 int field_pdf_impl(const float* field, int N, const uint32_t* n_bins_dev, uint32_t bin_cap, float* pdf,
-                   float* cdf_row, float* cdf_marg, cudaStream_t st);
+                   float* cdf_row, float* cdf_marg, cudaStream_t st, int blur = 0);
 int set_last_error(int code, const std::string& msg);
 }  // namespace wfpg
 
@@ -64,7 +64,7 @@ struct GemmArgs {
 
 constexpr int kGemmThreads = 128;
 constexpr int kSplitsW4 = 64;       // K splits of the output layer's weight gradient (8 row tiles each)
-constexpr int kSplitsHidden = 512;  // K splits of the hidden layers' weight gradients (one 128-row chunk each)
+constexpr int kSplitsHidden = 128;  // K splits of the hidden layers' weight gradients (4 chunks of 128 rows each at 65,536 rows)
 // K elements per pipeline step: 128 for narrow tiles (more bytes in flight per
 // CTA on the long-K weight-gradient GEMMs), 64 for the 256-wide logits tile
 template <int BN>
@@ -80,11 +80,11 @@ struct TmemCols {
 // copy rows [r0, r0 + rows) x k [k0, k0 + KC) of a K-contiguous bf16 matrix into
 // the no-swizzle K-major core-matrix layout: 16-byte chunk c of row r goes to
 // (r / 8) * (KC * 16) + c * 128 + (r % 8) * 16; rows or k past the end read zero
-template <int KC>
+template <int KC, int NT = kGemmThreads>
 __device__ __forceinline__ void load_tile(uint8_t* smem, const bf16* g, int ld, int r0, int rows, int nrows_total,
                                           int k0, int K) {
     constexpr int kCpr = KC / 8;  // 16-byte chunks per row
-    for (int idx = threadIdx.x; idx < rows * kCpr; idx += kGemmThreads) {
+    for (int idx = threadIdx.x; idx < rows * kCpr; idx += NT) {
         const int r = idx / kCpr, c = idx % kCpr;
         const int gr = r0 + r, gk = k0 + c * 8;
         uint4 v = make_uint4(0u, 0u, 0u, 0u);
@@ -93,13 +93,30 @@ __device__ __forceinline__ void load_tile(uint8_t* smem, const bf16* g, int ld, 
     }
 }
 
+// load_tile with asynchronous copies (the caller commits and waits)
+template <int KC, int NT = kGemmThreads>
+__device__ __forceinline__ void load_tile_async(uint8_t* smem, const bf16* g, int ld, int r0, int rows,
+                                                int nrows_total, int k0, int K) {
+    constexpr int kCpr = KC / 8;
+    for (int idx = threadIdx.x; idx < rows * kCpr; idx += NT) {
+        const int r = idx / kCpr, c = idx % kCpr;
+        const int gr = r0 + r, gk = k0 + c * 8;
+        const bool valid = gr < nrows_total && gk < K;
+        tc::cp_async16(smem + (r >> 3) * (KC * 16) + c * 128 + (r & 7) * 16, valid ? g + (size_t)gr * ld + gk : g,
+                       valid);
+    }
+}
+
 template <int BN, int EPI>
 __global__ void __launch_bounds__(kGemmThreads) k_gemm_tn(GemmArgs g) {
     constexpr int kKChunk = KChunk<BN>::value;
+    constexpr int kStageBytes = (128 + BN) * kKChunk * 2;
     extern __shared__ __align__(1024) uint8_t gemm_smem[];
-    uint8_t* sA = gemm_smem;                      // 128 x kKChunk bf16
-    uint8_t* sB = gemm_smem + 128 * kKChunk * 2;  // BN x kKChunk bf16
-    __shared__ __align__(8) uint64_t mbar;
+    // two stages of (A tile 128 x kKChunk, B tile BN x kKChunk): chunk i + 1 is
+    // loaded while the MMAs of chunk i run
+    auto sA = [&](int s) { return gemm_smem + s * kStageBytes; };
+    auto sB = [&](int s) { return gemm_smem + s * kStageBytes + 128 * kKChunk * 2; };
+    __shared__ __align__(8) uint64_t mbar[2];
     __shared__ uint32_t tmem_base;
     constexpr uint32_t kCols = TmemCols<BN>::value;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -107,40 +124,59 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm_tn(GemmArgs g) {
     const int total_chunks = (g.K + kKChunk - 1) / kKChunk;
     const int kc0 = blockIdx.z * g.chunks_per_split;
     const int kc1 = min(total_chunks, kc0 + g.chunks_per_split);
+    const int nch = kc1 - kc0;
     if (warp == 0) tc::tmem_alloc(&tmem_base, kCols);
     if (tid == 0) {
-        tc::mbar_init(&mbar, 1);
+        tc::mbar_init(&mbar[0], 1);
+        tc::mbar_init(&mbar[1], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (nch > 0) {
+        load_tile_async<kKChunk>(sA(0), g.A, g.lda, m0, 128, g.M, kc0 * kKChunk, g.K);
+        load_tile_async<kKChunk>(sB(0), g.B, g.ldb, n0, BN, g.N, kc0 * kKChunk, g.K);
+        tc::cp_async_commit();
     }
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = tmem_base;
     constexpr uint32_t idesc = tc::idesc_bf16_f32(128, BN);
-    uint32_t phase = 0;
+    uint32_t phase = 0u;  // bit s: parity of the next phase of mbar[s]
     bool ok = true;
-    for (int kc = kc0; kc < kc1 && ok; ++kc) {
-        load_tile<kKChunk>(sA, g.A, g.lda, m0, 128, g.M, kc * kKChunk, g.K);
-        load_tile<kKChunk>(sB, g.B, g.ldb, n0, BN, g.N, kc * kKChunk, g.K);
+    for (int i = 0; i < nch && ok; ++i) {
+        const int s = i & 1;
+        tc::cp_async_wait_all();  // this thread's copies into stage s have landed
         tc::fence_proxy_async();
-        __syncthreads();
+        __syncthreads();  // stage s is loaded and visible to the tensor cores
         if (tid == 0) {
             tc::fence_after_sync();
-            const uint32_t a0 = tc::smem_addr(sA), b0 = tc::smem_addr(sB);
+            const uint32_t a0 = tc::smem_addr(sA(s)), b0 = tc::smem_addr(sB(s));
 #pragma unroll
-            for (int s = 0; s < kKChunk / 16; ++s) {
+            for (int k = 0; k < kKChunk / 16; ++k) {
                 // K step of 16 = two core matrices along K (128 B apart); 8-row groups kKChunk * 16 B apart
-                const uint64_t ad = tc::smem_desc(a0 + s * 256, 128, kKChunk * 16);
-                const uint64_t bd = tc::smem_desc(b0 + s * 256, 128, kKChunk * 16);
-                tc::mma_bf16(tmem, ad, bd, idesc, (kc > kc0 || s > 0) ? 1u : 0u);
+                const uint64_t ad = tc::smem_desc(a0 + k * 256, 128, kKChunk * 16);
+                const uint64_t bd = tc::smem_desc(b0 + k * 256, 128, kKChunk * 16);
+                tc::mma_bf16(tmem, ad, bd, idesc, (i > 0 || k > 0) ? 1u : 0u);
             }
-            tc::mma_commit(&mbar);
+            tc::mma_commit(&mbar[s]);
         }
-        // the next chunk overwrites the tiles: wait until the MMAs have read them
-        // (bounded; the verdict is made uniform over the CTA)
-        ok = __syncthreads_and(tc::mbar_wait(&mbar, phase)) != 0;
-        phase ^= 1u;
+        if (i + 1 < nch) {
+            // stage s ^ 1 was read by the MMAs of chunk i - 1: wait for them (bounded; the
+            // verdict is made uniform over the CTA), then load chunk i + 1 into it
+            if (i >= 1) {
+                ok = __syncthreads_and(tc::mbar_wait(&mbar[s ^ 1], (phase >> (s ^ 1)) & 1u)) != 0;
+                phase ^= 1u << (s ^ 1);
+            }
+            if (ok) {  // in flight while the MMAs of chunk i run
+                load_tile_async<kKChunk>(sA(s ^ 1), g.A, g.lda, m0, 128, g.M, (kc0 + i + 1) * kKChunk, g.K);
+                load_tile_async<kKChunk>(sB(s ^ 1), g.B, g.ldb, n0, BN, g.N, (kc0 + i + 1) * kKChunk, g.K);
+                tc::cp_async_commit();
+            }
+        }
     }
+    tc::cp_async_wait_all();  // no copy left in flight (a timed-out CTA may still have some)
+    // the last chunk's commit tracks every MMA issued before it
+    if (ok && nch > 0) ok = __syncthreads_and(tc::mbar_wait(&mbar[(nch - 1) & 1], (phase >> ((nch - 1) & 1)) & 1u)) != 0;
     if (!ok && lane == 0) atomicOr(g.status, (uint32_t)WFPG_STATUS_MMA_TIMEOUT);
     tc::fence_after_sync();
     bool staged = false;
@@ -425,68 +461,296 @@ __global__ void __launch_bounds__(256) k_rowsum(const bf16* __restrict__ AT, int
     if (threadIdx.x == 0) atomicAdd(&out[blockIdx.y], red[0]);
 }
 
-// out[c][r] = in[r][c] and colsum[c] += sum over r of in[r][c], for a bf16
-// matrix with an even row stride: 64 x 64 tiles through shared memory, two
-// columns (rows of out) per 4-byte access; one block covers 64 columns x 256
-// rows and adds its column sums with one atomic per column
-__global__ void __launch_bounds__(256) k_transpose_colsum(const bf16* __restrict__ in, int rows, int cols, int ldi,
-                                                          bf16* __restrict__ out, int ldo,
-                                                          float* __restrict__ colsum) {
-    __shared__ bf16 t[64][66];
-    __shared__ float part[8][64];
-    const int c0 = blockIdx.x * 64, rb = blockIdx.y * 256;
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    float s0 = 0.0f, s1 = 0.0f;
-    const int rend = min(rows, rb + 256);
-    for (int r0 = rb; r0 < rend; r0 += 64) {
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const int r = r0 + ty + 8 * k, c = c0 + 2 * tx;
-            bf16 a = __float2bfloat16_rn(0.0f), b = a;
-            if (r < rows && c + 1 < cols) {
-                const __nv_bfloat162 v = *reinterpret_cast<const __nv_bfloat162*>(in + (size_t)r * ldi + c);
-                a = v.x;
-                b = v.y;
-            } else if (r < rows && c < cols) {
-                a = in[(size_t)r * ldi + c];
-            }
-            t[ty + 8 * k][2 * tx] = a;
-            t[ty + 8 * k][2 * tx + 1] = b;
-            s0 += __bfloat162float(a);
-            s1 += __bfloat162float(b);
-        }
-        __syncthreads();
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const int c = c0 + ty + 8 * k, r = r0 + 2 * tx;
-            if (c >= cols) continue;
-            if (r + 1 < rows && ((ldo & 1) == 0)) {
-                __nv_bfloat162 v;
-                v.x = t[2 * tx][ty + 8 * k];
-                v.y = t[2 * tx + 1][ty + 8 * k];
-                *reinterpret_cast<__nv_bfloat162*>(out + (size_t)c * ldo + r) = v;
-            } else {
-                if (r < rows) out[(size_t)c * ldo + r] = t[2 * tx][ty + 8 * k];
-                if (r + 1 < rows) out[(size_t)c * ldo + r + 1] = t[2 * tx + 1][ty + 8 * k];
-            }
-        }
-        __syncthreads();
-    }
-    part[ty][2 * tx] = s0;
-    part[ty][2 * tx + 1] = s1;
-    __syncthreads();
-    if (ty == 0) {
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int c = 2 * tx + h;
-            float sum = 0.0f;
-#pragma unroll
-            for (int y = 0; y < 8; ++y) sum += part[y][c];
-            if (c0 + c < cols) atomicAdd(&colsum[c0 + c], sum);
-        }
-    }
+// ---------------------------------------------------------------------------
+// The output layer of a training step, fused: for one 128-row tile, the logits
+// Z = H3 W4^T + b4 (1024 per row) are computed chunk by chunk on the tensor
+// cores into tensor memory and never stored.  Pass 1 keeps each row's running
+// maximum and exponential sum (and sums the target row); pass 2 recomputes
+// each chunk, forms the logit gradient G = bf16((softmax(Z) - q / sum q) / n)
+// and the KL term, writes G^T (for the weight gradient dW4 = G^T H3, a
+// separate split-K GEMM) and the column sums of G (db4), and accumulates
+// dA3 = G W4 in tensor memory with a second MMA per chunk.  The epilogue
+// writes d3 = bf16(dA3 o [H3 > 0]) and its transpose.
+// 256 threads: warp w reads TMEM lanes 32 (w % 4) .. + 31 (rows of the tile)
+// and handles columns 64 (w / 4) .. + 63 of each 128-logit chunk.
+constexpr int kOutThreads = 256;
+constexpr int kOutChunk = 128;                 // logits per chunk
+constexpr int kOutChunks = kOut / kOutChunk;   // 8
+constexpr uint32_t kOutTmemCols = 256;         // Z chunk at column 0 (128), dA3 at column 128 (64)
+constexpr int kOutSmemH = 0, kOutSmemW = 16384, kOutSmemWT = 32768, kOutSmemG = 49152, kOutSmemB = 81920,
+              kOutSmemStat = kOutSmemB + 4 * kOut;
+constexpr int kOutSmemBytes = kOutSmemStat + 3 * 2 * 128 * 4;
+
+struct OutTrainArgs {
+    const bf16* h3;      // [n][64]
+    const bf16* w4;      // [1024][64]
+    const bf16* w4t;     // [64][1024]
+    const float* b4;     // [1024]
+    const float* target; // [n][1024], any non-negative field per row (normalised here)
+    int n;
+    float inv_n;
+    bf16* g4t;           // [1024][ldg]: G^T
+    int ldg;
+    bf16* d3;            // [n][64]
+    bf16* d3t;           // [64][ldg]
+    float* db4;          // [1024], accumulated (zeroed before the launch)
+    float* loss;         // accumulated mean KL
+    uint32_t* status;
+};
+
+// byte offset of element (r, k) in a K-major no-swizzle core-matrix tile of KC columns
+template <int KC>
+__device__ __forceinline__ int cm_off(int r, int k) {
+    return (r >> 3) * (KC * 16) + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2;
 }
 
+__global__ void __launch_bounds__(kOutThreads) k_out_train(OutTrainArgs a) {
+    extern __shared__ __align__(1024) uint8_t out_smem[];
+    uint8_t* sH = out_smem + kOutSmemH;    // H3 tile: 128 x 64 (K = 64)
+    uint8_t* sW = out_smem + kOutSmemW;    // W4 rows of the chunk: 128 x 64 (K = 64)
+    uint8_t* sWT = out_smem + kOutSmemWT;  // W4^T columns of the chunk: 64 x 128 (K = 128)
+    uint8_t* sG = out_smem + kOutSmemG;    // G of the chunk: 128 x 128 (K = 128)
+    float* sb = reinterpret_cast<float*>(out_smem + kOutSmemB);
+    float* s_max = reinterpret_cast<float*>(out_smem + kOutSmemStat);  // [2][128] per column half
+    float* s_sum = s_max + 256;
+    float* s_tsum = s_sum + 256;
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tmem_base;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int quad = warp & 3, half = warp >> 2;
+    const int r = quad * 32 + lane;  // tile row of this thread
+    const int m0 = blockIdx.x * 128, row = m0 + r;
+    const bool live = row < a.n;
+    const int h0 = half * 64;        // first chunk column of this thread
+    if (warp == 0) tc::tmem_alloc(&tmem_base, kOutTmemCols);
+    if (tid == 0) {
+        tc::mbar_init(&mbar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    load_tile<64, kOutThreads>(sH, a.h3, kHid, m0, 128, a.n, 0, kHid);
+    for (int i = tid; i < kOut; i += kOutThreads) sb[i] = a.b4[i];
+    tc::fence_proxy_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = tmem_base;
+    const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16);
+    constexpr uint32_t idesc_z = tc::idesc_bf16_f32(128, kOutChunk);
+    constexpr uint32_t idesc_d = tc::idesc_bf16_f32(128, kHid);
+    const float* trow = a.target + (size_t)row * kOut;
+    uint32_t phase = 0;
+    bool ok = true;
+
+    // Z chunk -> TMEM columns [0, 128) from the staged W4 rows: 4 MMAs (K = 64)
+    auto issue_z = [&]() {
+        if (tid == 0) {
+            tc::fence_after_sync();
+            const uint32_t a0 = tc::smem_addr(sH), b0 = tc::smem_addr(sW);
+#pragma unroll
+            for (int s = 0; s < kHid / 16; ++s)
+                tc::mma_bf16(tmem, tc::smem_desc(a0 + s * 256, 128, 64 * 16), tc::smem_desc(b0 + s * 256, 128, 64 * 16),
+                             idesc_z, s > 0 ? 1u : 0u);
+            tc::mma_commit(&mbar);
+        }
+    };
+    auto wait_mma = [&]() {
+        ok = ok && __syncthreads_and(tc::mbar_wait(&mbar, phase)) != 0;
+        phase ^= 1u;
+        tc::fence_after_sync();
+    };
+
+    // ---- pass 1: running maximum and exponential sum over this thread's columns; target sum.
+    // The W4 rows of chunk c + 1 are copied in while chunk c's logits are processed.
+    float mrun = -3.4e38f, srun = 0.0f, tsum = 0.0f;
+    load_tile_async<64, kOutThreads>(sW, a.w4, kHid, 0, kOutChunk, kOut, 0, kHid);
+    tc::cp_async_commit();
+    for (int c = 0; c < kOutChunks && ok; ++c) {
+        tc::cp_async_wait_all();
+        tc::fence_proxy_async();
+        __syncthreads();
+        issue_z();
+        if (live) {
+            const float4* tq = reinterpret_cast<const float4*>(trow + c * kOutChunk + h0);
+#pragma unroll 8
+            for (int i = 0; i < 16; ++i) {
+                const float4 v = tq[i];
+                tsum += (v.x + v.y) + (v.z + v.w);
+            }
+        }
+        wait_mma();
+        if (!ok) break;
+        if (c + 1 < kOutChunks) {  // sW is free once the MMAs have read it
+            load_tile_async<64, kOutThreads>(sW, a.w4, kHid, (c + 1) * kOutChunk, kOutChunk, kOut, 0, kHid);
+            tc::cp_async_commit();
+        }
+#pragma unroll 1
+        for (int g = 0; g < 2; ++g) {
+            float v[32];
+            tc::tmem_ld32(lane_base + (uint32_t)(h0 + g * 32), v);
+            float gm = -3.4e38f;
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+                v[i] += sb[c * kOutChunk + h0 + g * 32 + i];
+                gm = fmaxf(gm, v[i]);
+            }
+            if (gm > mrun) {
+                srun *= __expf(mrun - gm);
+                mrun = gm;
+            }
+#pragma unroll
+            for (int i = 0; i < 32; ++i) srun += __expf(v[i] - mrun);
+        }
+        tc::fence_before_sync();
+        __syncthreads();  // every lane has read the chunk: TMEM and sW are free
+    }
+    // the row's statistics from its two column halves
+    s_max[half * 128 + r] = mrun;
+    s_sum[half * 128 + r] = srun;
+    s_tsum[half * 128 + r] = tsum;
+    __syncthreads();
+    {
+        const float m0v = s_max[r], m1v = s_max[128 + r];
+        mrun = fmaxf(m0v, m1v);
+        srun = s_sum[r] * __expf(m0v - mrun) + s_sum[128 + r] * __expf(m1v - mrun);
+        tsum = s_tsum[r] + s_tsum[128 + r];
+    }
+
+    // ---- pass 2 (chunks in reverse, so the target rows read last are read again first)
+    const float log_s = __logf(srun), inv_t = tsum > 0.0f ? 1.0f / tsum : 0.0f;
+    const float shift = mrun + log_s;
+    float kl = 0.0f;
+    tc::cp_async_wait_all();
+    __syncthreads();
+    if (ok) {
+        load_tile_async<64, kOutThreads>(sW, a.w4, kHid, (kOutChunks - 1) * kOutChunk, kOutChunk, kOut, 0, kHid);
+        load_tile_async<128, kOutThreads>(sWT, a.w4t, kOut, 0, kHid, kHid, (kOutChunks - 1) * kOutChunk, kOut);
+        tc::cp_async_commit();
+    }
+    for (int cc = 0; cc < kOutChunks && ok; ++cc) {
+        const int c = kOutChunks - 1 - cc;
+        tc::cp_async_wait_all();
+        tc::fence_proxy_async();
+        __syncthreads();
+        issue_z();
+        wait_mma();
+        if (!ok) break;
+        if (cc + 1 < kOutChunks) {  // the next chunk's W4 rows, while this one is processed
+            load_tile_async<64, kOutThreads>(sW, a.w4, kHid, (c - 1) * kOutChunk, kOutChunk, kOut, 0, kHid);
+            tc::cp_async_commit();
+        }
+#pragma unroll 1
+        for (int g = 0; g < 2; ++g) {
+            float v[32];
+            tc::tmem_ld32(lane_base + (uint32_t)(h0 + g * 32), v);
+            const int k0 = h0 + g * 32;  // chunk column of v[0]
+            float4 t4[8];
+            if (live) {
+                const float4* tq = reinterpret_cast<const float4*>(trow + c * kOutChunk + k0);
+#pragma unroll
+                for (int i = 0; i < 8; ++i) t4[i] = tq[i];
+            }
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {  // 8 columns = one 16-byte row of a core matrix
+                uint32_t w[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    bf16 x[2];
+#pragma unroll
+                    for (int k = 0; k < 2; ++k) {
+                        const int i = 8 * h + 2 * e + k;
+                        float gv = 0.0f;
+                        if (live) {
+                            const float4 tt = t4[i >> 2];
+                            const float q = ((i & 3) == 0 ? tt.x : (i & 3) == 1 ? tt.y : (i & 3) == 2 ? tt.z : tt.w) * inv_t;
+                            const float logp = v[i] + sb[c * kOutChunk + k0 + i] - shift;
+                            if (q > 0.0f) kl += q * (__logf(q) - logp);
+                            gv = (__expf(logp) - q) * a.inv_n;
+                        }
+                        x[k] = __float2bfloat16_rn(gv);
+                    }
+                    w[e] = (uint32_t)__bfloat16_as_ushort(x[0]) | ((uint32_t)__bfloat16_as_ushort(x[1]) << 16);
+                }
+                *reinterpret_cast<uint4*>(sG + cm_off<128>(r, k0 + 8 * h)) = make_uint4(w[0], w[1], w[2], w[3]);
+            }
+        }
+        tc::fence_proxy_async();
+        tc::fence_before_sync();
+        __syncthreads();  // G staged; the Z chunk has been read
+        if (tid == 0) {
+            tc::fence_after_sync();
+            const uint32_t a0 = tc::smem_addr(sG), b0 = tc::smem_addr(sWT);
+#pragma unroll
+            for (int s = 0; s < kOutChunk / 16; ++s)
+                tc::mma_bf16(tmem + (uint32_t)kOutChunk, tc::smem_desc(a0 + s * 256, 128, 128 * 16),
+                             tc::smem_desc(b0 + s * 256, 128, 128 * 16), idesc_d, (cc > 0 || s > 0) ? 1u : 0u);
+            tc::mma_commit(&mbar);
+        }
+        // G^T rows and db4 from the staged chunk: thread -> chunk column kc, 64 tile rows
+        {
+            const int kc = tid & 127, rh = (tid >> 7) * 64;
+            bf16* gt = a.g4t + (size_t)(c * kOutChunk + kc) * a.ldg + m0 + rh;
+            const bool full = m0 + rh + 64 <= a.n && (a.ldg & 7) == 0;
+            float cs = 0.0f;
+#pragma unroll 1
+            for (int r8 = 0; r8 < 64; r8 += 8) {
+                uint32_t w[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const bf16 x0 = *reinterpret_cast<const bf16*>(sG + cm_off<128>(rh + r8 + 2 * e, kc));
+                    const bf16 x1 = *reinterpret_cast<const bf16*>(sG + cm_off<128>(rh + r8 + 2 * e + 1, kc));
+                    cs += __bfloat162float(x0) + __bfloat162float(x1);
+                    w[e] = (uint32_t)__bfloat16_as_ushort(x0) | ((uint32_t)__bfloat16_as_ushort(x1) << 16);
+                }
+                if (full) {
+                    *reinterpret_cast<uint4*>(gt + r8) = make_uint4(w[0], w[1], w[2], w[3]);
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 8; ++e)
+                        if (m0 + rh + r8 + e < a.n)
+                            gt[r8 + e] = __ushort_as_bfloat16((unsigned short)(w[e >> 1] >> (16 * (e & 1))));
+                }
+            }
+            atomicAdd(&a.db4[c * kOutChunk + kc], cs);
+        }
+        wait_mma();  // dA3 has read sG and sWT
+        if (ok && cc + 1 < kOutChunks) {  // the next chunk's W4^T columns
+            load_tile_async<128, kOutThreads>(sWT, a.w4t, kOut, 0, kHid, kHid, (c - 1) * kOutChunk, kOut);
+            tc::cp_async_commit();
+        }
+    }
+    tc::cp_async_wait_all();
+    if (!ok && lane == 0) atomicOr(a.status, (uint32_t)WFPG_STATUS_MMA_TIMEOUT);
+
+    // ---- epilogue: d3 = bf16(dA3 o [H3 > 0]) (this thread's 32 of the 64 columns) and its transpose; the KL
+    if (ok) {
+        float v[32];
+        tc::tmem_ld32(lane_base + (uint32_t)(kOutChunk + half * 32), v);
+        if (live) {
+            uint32_t w[16];
+#pragma unroll
+            for (int h = 0; h < 16; ++h) {
+                bf16 x[2];
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    const int j = half * 32 + 2 * h + k;
+                    const float hv = __bfloat162float(*reinterpret_cast<const bf16*>(sH + cm_off<64>(r, j)));
+                    x[k] = __float2bfloat16_rn(hv > 0.0f ? v[2 * h + k] : 0.0f);
+                    a.d3t[(size_t)j * a.ldg + row] = x[k];
+                }
+                w[h] = (uint32_t)__bfloat16_as_ushort(x[0]) | ((uint32_t)__bfloat16_as_ushort(x[1]) << 16);
+            }
+            uint4* dp = reinterpret_cast<uint4*>(a.d3 + (size_t)row * kHid + half * 32);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) dp[q] = make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) kl += __shfl_xor_sync(0xffffffffu, kl, o);
+        if (lane == 0) atomicAdd(a.loss, kl * a.inv_n);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, kOutTmemCols);
+}
 
 // Adam (Kingma & Ba 2015) on the float32 master weights
 __global__ void k_adam(float* __restrict__ w, float* __restrict__ m, float* __restrict__ v,
@@ -523,7 +787,7 @@ struct wfpg_mlp {
     bf16 *w1 = nullptr, *w2 = nullptr, *w3 = nullptr, *w4 = nullptr, *w2t = nullptr, *w3t = nullptr,
          *w4t = nullptr;
     bf16 *x = nullptr, *xt = nullptr, *h1 = nullptr, *h1t = nullptr, *h2 = nullptr, *h2t = nullptr, *h3 = nullptr,
-         *h3t = nullptr, *g4 = nullptr, *g4t = nullptr, *d3 = nullptr, *d3t = nullptr, *d2 = nullptr,
+         *h3t = nullptr, *g4t = nullptr, *d3 = nullptr, *d3t = nullptr, *d2 = nullptr,
          *d2t = nullptr, *d1 = nullptr, *d1t = nullptr;
     float* z = nullptr;
     float* part = nullptr;  // split-K partial weight gradients
@@ -546,15 +810,18 @@ int gemm(const GemmArgs& a, int splits, cudaStream_t st) {
     splits = (chunks + g.chunks_per_split - 1) / g.chunks_per_split;
     const dim3 grid(div_up(g.M, 128), div_up(g.N, BN), splits);
     auto kernel = k_gemm_tn<BN, EPI>;
-    const int smem = (128 + BN) * kKChunk * 2;
-    // the tiles plus the kernel's static shared memory exceed the default 48 KB
-    // window for the wide instantiations: raise the dynamic limit once per device
+    // one tile stage when every CTA takes a single K chunk (nothing to overlap; the
+    // smaller footprint keeps more CTAs resident), two otherwise
+    const int stage_bytes = (128 + BN) * kKChunk * 2;
+    const int smem = (g.chunks_per_split > 1 ? 2 : 1) * stage_bytes;
+    // the two stages plus the kernel's static shared memory exceed the default 48 KB
+    // window: raise the dynamic limit (to the two-stage size) once per device
     static std::atomic<uint64_t> raised{0};
     int dev = 0;
     cudaGetDevice(&dev);
     const uint64_t bit = 1ull << (dev & 63);
-    if (smem > 32 * 1024 && !(raised.load(std::memory_order_relaxed) & bit)) {
-        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (!(raised.load(std::memory_order_relaxed) & bit)) {
+        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * stage_bytes);
         raised.fetch_or(bit, std::memory_order_relaxed);
     }
     WFPG_LAUNCH(kernel, grid, kGemmThreads, smem, st, g);
@@ -596,7 +863,8 @@ void convert_weights(wfpg_mlp* s, cudaStream_t st) {
 
 // forward through the hidden layers and the logits for n rows (X already set);
 // the logits go to z_out ([n][1024]) when given, else to the handle's buffer
-void forward(wfpg_mlp* s, int n, bool keep_transposes, cudaStream_t st, float* z_out = nullptr) {
+void forward(wfpg_mlp* s, int n, bool keep_transposes, cudaStream_t st, float* z_out = nullptr,
+             bool logits = true) {
     const int mp = (int)s->mpad;
     GemmArgs g = gargs(s->x, kIn, s->w1, kIn, n, kHid, kIn, s->status);
     g.O = s->h1;
@@ -619,6 +887,7 @@ void forward(wfpg_mlp* s, int n, bool keep_transposes, cudaStream_t st, float* z
     g.ldot = mp;
     g.bias = s->params + kOffB3;
     gemm<64, kEpiBf16Relu>(g, 1, st);
+    if (!logits) return;
     g = gargs(s->h3, kHid, s->w4, kHid, n, kOut, kHid, s->status);
     g.C = z_out ? z_out : s->z;
     g.ldc = kOut;
@@ -678,7 +947,6 @@ int mlp_create(const float* params, uint32_t max_batch, void* stream, wfpg_mlp**
     bf16** acts[] = {&s->h1, &s->h1t, &s->h2, &s->h2t, &s->h3, &s->h3t, &s->d3, &s->d3t, &s->d2, &s->d2t,
                      &s->d1, &s->d1t};
     for (bf16** a : acts) alloc(a, 2 * mp * kHid);
-    alloc(&s->g4, 2 * mp * kOut);
     alloc(&s->g4t, 2 * mp * kOut);
     alloc(&s->z, 4 * mp * kOut);
     alloc(&s->field, 4 * mp * kOut);
@@ -708,7 +976,7 @@ int mlp_create(const float* params, uint32_t max_batch, void* stream, wfpg_mlp**
 int mlp_destroy(wfpg_mlp* s) {
     if (!s) return WFPG_OK;
     void* ptrs[] = {s->params, s->m, s->v, s->grad, s->part, s->w1, s->w2, s->w3, s->w4, s->w2t, s->w3t, s->w4t,
-                    s->x, s->xt, s->h1, s->h1t, s->h2, s->h2t, s->h3, s->h3t, s->g4, s->g4t, s->d3,
+                    s->x, s->xt, s->h1, s->h1t, s->h2, s->h2t, s->h3, s->h3t, s->g4t, s->d3,
                     s->d3t, s->d2, s->d2t, s->d1, s->d1t, s->z, s->field, s->loss, s->status};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -796,23 +1064,37 @@ int guide_learned_train_step(wfpg_mlp* s, const float* pos, const float* nrm, ui
               cudaMemsetAsync(s->loss, 0, 4, st) == cudaSuccess;
     WFPG_LAUNCH(k_mlp_features, div_up(n, 128), 128, 0, st, pos, nrm, (const uint32_t*)nullptr,
                 (const uint32_t*)nullptr, n, p->lo[0], p->lo[1], p->lo[2], 1.0f / p->size, s->x, s->xt, mp);
-    forward(s, N, true, st);
-    WFPG_LAUNCH(k_softmax_rows, div_up((uint64_t)n * 32, 256), 256, 0, st, s->z, n, (const uint32_t*)nullptr, 0.0f,
-                (float*)nullptr, target, 1.0f / (float)n, s->g4, s->loss);
-    // output layer: dW4 = G4^T H3 (split-K over the batch), db4, dA3 = (G4 W4) o [H3 > 0]
-    // G4^T for the weight gradient, and db4 = column sums of G4, in one pass over G4
-    WFPG_LAUNCH(k_transpose_colsum, dim3(div_up(kOut, 64), div_up(n, 256)), dim3(32, 8), 0, st, s->g4, N, kOut, kOut,
-                s->g4t, mp, s->grad + kOffB4);
+    forward(s, N, true, st, nullptr, false);
+    // output layer, fused: logits, softmax, KL, G4^T, db4 and dA3 = (G4 W4) o [H3 > 0] per 128-row tile
+    {
+        static std::atomic<uint64_t> raised{0};
+        int dev = 0;
+        cudaGetDevice(&dev);
+        const uint64_t bit = 1ull << (dev & 63);
+        if (!(raised.load(std::memory_order_relaxed) & bit)) {
+            cudaFuncSetAttribute(k_out_train, cudaFuncAttributeMaxDynamicSharedMemorySize, kOutSmemBytes);
+            raised.fetch_or(bit, std::memory_order_relaxed);
+        }
+        OutTrainArgs oa;
+        oa.h3 = s->h3;
+        oa.w4 = s->w4;
+        oa.w4t = s->w4t;
+        oa.b4 = s->params + kOffB4;
+        oa.target = target;
+        oa.n = N;
+        oa.inv_n = 1.0f / (float)n;
+        oa.g4t = s->g4t;
+        oa.ldg = mp;
+        oa.d3 = s->d3;
+        oa.d3t = s->d3t;
+        oa.db4 = s->grad + kOffB4;
+        oa.loss = s->loss;
+        oa.status = s->status;
+        WFPG_LAUNCH(k_out_train, div_up(n, 128), kOutThreads, kOutSmemBytes, st, oa);
+    }
+    // dW4 = G4^T H3 (split-K over the batch)
     GemmArgs g = gargs(s->g4t, mp, s->h3t, mp, kOut, kHid, N, s->status);
     weight_grad<64>(s, g, kSplitsW4, s->grad + kOffW4, st);
-    g = gargs(s->g4, kOut, s->w4t, kOut, N, kHid, kOut, s->status);
-    g.O = s->d3;
-    g.ldo = kHid;
-    g.OT = s->d3t;
-    g.ldot = mp;
-    g.act = s->h3;
-    g.ldact = kHid;
-    gemm<64, kEpiReluGrad>(g, 1, st);
     // hidden layers
     struct Layer {
         bf16 *dA, *dAt, *Hprev_t, *Hprev, *Wt, *dAprev, *dAprev_t;

@@ -21,6 +21,12 @@ struct wfpg_svo {
     uint32_t* leaf_count = nullptr;
     float4* normal = nullptr;                 // (nx, ny, nz, 0)
     uint8_t* route = nullptr;                 // bit0/bit1: parent side taking this node's side 0/1
+    // top index: for each level l <= top_levels - 1, a dense grid over that level's cells
+    // (x fastest) holding (L << 28) | node, node = the deepest existing node at a level
+    // L <= l containing the cell (empty when top_levels == 0)
+    uint32_t* top = nullptr;
+    int top_levels = 0;
+    uint32_t top_off[8] = {0};
     uint32_t* frag_off = nullptr;             // leaves + 1
     uint32_t* frag_prim = nullptr;            // n_frags
     // radiant exitance, two sides per node

@@ -501,9 +501,29 @@ __global__ void k_route(uint32_t n, const uint32_t* __restrict__ parent, const f
     route[i] = (uint8_t)((dpos >= 0.0f ? 0u : 1u) | (dneg >= 0.0f ? 0u : 2u));
 }
 
+// One level of the top index: for each cell of level l (row-major, x fastest), the
+// deepest existing node at a level <= l containing it, as (level << 28) | node
+__global__ void k_top_level(const Node* __restrict__ node, int l, uint32_t* __restrict__ out) {
+    const uint32_t R = 1u << l;
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= R * R * R) return;
+    const uint32_t x = i & (R - 1), y = (i >> l) & (R - 1), z = i >> (2 * l);
+    uint32_t nd = 0;
+    int L = 0;
+    while (L < l) {
+        const Node n = node[nd];
+        const int sh = l - 1 - L;
+        const int k = (int)(((x >> sh) & 1u) | (((y >> sh) & 1u) << 1) | (((z >> sh) & 1u) << 2));
+        if (!((n.mask >> k) & 1u)) break;
+        nd = child_id(n, k);
+        ++L;
+    }
+    out[i] = ((uint32_t)L << 28) | nd;
+}
+
 void svo_free_arrays(wfpg_svo* s) {
     void* ptrs[] = {s->node, s->parent, s->key, s->leaf_count, s->normal, s->route, s->frag_off, s->frag_prim,
-                    s->acc_sum, s->acc_cnt, s->tot_sum, s->tot_cnt, s->value, s->status};
+                    s->acc_sum, s->acc_cnt, s->tot_sum, s->tot_cnt, s->value, s->status, s->top};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -653,7 +673,20 @@ int build_svo(const wfpg_scene* scene, int D, cudaStream_t st, wfpg_svo* s, std:
                                                            s->leaf_count);
     WFPG_ALLOC(s->route, (size_t)nn);
     WFPG_LAUNCH(k_route, div_up(nn, T), T, 0, st, nn, s->parent, s->normal, s->route);
-    // 8. exitance arrays, zeroed
+    // 8. the top index of levels 0 .. min(D, kTopLevelMax) (node ids must fit in 28 bits)
+    if (nn < (1u << 28)) {
+        const int G = D < kTopLevelMax ? D : kTopLevelMax;
+        size_t cells = 0;
+        for (int l = 0; l <= G; ++l) {
+            s->top_off[l] = (uint32_t)cells;
+            cells += (size_t)1 << (3 * l);
+        }
+        WFPG_ALLOC(s->top, sizeof(uint32_t) * cells);
+        for (int l = 0; l <= G; ++l)
+            WFPG_LAUNCH(k_top_level, div_up((size_t)1 << (3 * l), T), T, 0, st, s->node, l, s->top + s->top_off[l]);
+        s->top_levels = G + 1;
+    }
+    // 9. exitance arrays, zeroed
     WFPG_ALLOC(s->acc_sum, 16 * (size_t)nn);
     WFPG_ALLOC(s->tot_sum, 16 * (size_t)nn);
     WFPG_ALLOC(s->acc_cnt, 8 * (size_t)nn);
