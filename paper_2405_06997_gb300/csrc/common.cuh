@@ -79,6 +79,14 @@ __device__ __forceinline__ int grid_index(float x, float lo, float scale, int D)
 // deepest level of the SVO's top index (a dense grid per level 0 .. this)
 constexpr int kTopLevelMax = 6;
 constexpr uint32_t kTopNodeMask = (1u << 28) - 1u;
+// deepest SVO for which every level below the top index has an occupancy bitmap
+constexpr int kOccMaxDepth = 9;
+// word offset of level l's bitmap when levels g + 1 .. l - 1 precede it (8^j bits each, j > 6)
+__host__ __device__ __forceinline__ uint64_t occ_offset(int g, int l) {
+    uint64_t o = 0;
+    for (int j = g + 1; j < l; ++j) o += (1ull << (3 * j)) >> 5;
+    return o;
+}
 
 // node record used by every tree walk: first child's global id and child mask
 struct Node {

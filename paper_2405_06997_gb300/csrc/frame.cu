@@ -382,31 +382,32 @@ __global__ void __launch_bounds__(256) k_shade(FrameView F, Queue Q, const float
 
 // Eq. 5 for every vertex of every path, back to front: the suffix sum
 // S_k = sum_{n >= k} T_n Le_n gives L_k = S_k / T_k; S_1 is the path estimate.
+// The record array is compact in any order: per vertex depth, each warp
+// reserves one contiguous run for its lanes that have that vertex (one atomic
+// per warp and depth), so every store instruction writes one run.
 __global__ void __launch_bounds__(256) k_records(FrameView F, float* __restrict__ rec_pos,
                                                  float* __restrict__ rec_wout, float* __restrict__ rec_L,
                                                  uint32_t* __restrict__ rec_src) {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    const uint32_t lane = threadIdx.x & 31;
-    const uint32_t n = i < F.P ? F.nv[i] : 0u;
-    // one atomic per warp reserves the warp's records
-    uint32_t incl = n;
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= (uint32_t)o) incl += t;
-    }
-    uint32_t base = 0;
-    if (lane == 31) base = atomicAdd(&F.counters[WFPG_FRAME_MAX_DEPTH + 1], incl);
-    base = __shfl_sync(0xffffffffu, base, 31) + incl - n;
-    if (i >= F.P) return;
+    const uint32_t lane = threadIdx.x & 31, lt = (1u << lane) - 1u;
+    const int n = i < F.P ? (int)F.nv[i] : 0;
+    int nmax = n;
+    for (int o = 16; o > 0; o >>= 1) nmax = max(nmax, __shfl_xor_sync(0xffffffffu, nmax, o));
     // S: what the vertices after v contribute, as v sees them; Sv: v's own record (with NEE a
     // vertex's record holds its full emission, the vertex before it the MIS-weighted share)
     float S = 0.0f, Sv = 0.0f;
-    for (int v = (int)n - 1; v >= 0; --v) {
+    for (int v = nmax - 1; v >= 0; --v) {
+        const bool has = v < n;
+        const uint32_t m = __ballot_sync(0xffffffffu, has);
+        uint32_t base = 0;
+        if (lane == (uint32_t)(__ffs(m) - 1)) base = atomicAdd(&F.counters[WFPG_FRAME_MAX_DEPTH + 1], __popc(m));
+        base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
+        if (!has) continue;
         const size_t e = (size_t)v * F.P + i;
         const float T = F.vT[e];
         Sv = S + T * (F.nee ? F.vLe[e] + F.vNee[e] : F.vLe[e]);
         S = F.nee ? S + T * (F.vLw[e] + F.vNee[e]) : Sv;
-        const uint32_t r = base + (uint32_t)v;
+        const uint32_t r = base + __popc(m & lt);
         rec_pos[3 * (size_t)r] = F.vpos[3 * e];
         rec_pos[3 * (size_t)r + 1] = F.vpos[3 * e + 1];
         rec_pos[3 * (size_t)r + 2] = F.vpos[3 * e + 2];
@@ -416,6 +417,7 @@ __global__ void __launch_bounds__(256) k_records(FrameView F, float* __restrict_
         rec_L[r] = Sv / T;
         rec_src[r] = (uint32_t)e;
     }
+    if (i >= F.P) return;
     const double L = (double)Sv;
     F.img_sum[i] += L;
     F.img_sq[i] += L * L;

@@ -45,6 +45,10 @@ struct TraceArgs {
     uint32_t smem_nodes;
     const uint32_t* top;  // the SVO's top index (levels 0 .. G), NULL when it has none
     int G;                // deepest indexed level, -1 without an index
+    uint32_t top_offG;    // offset of level G's grid in the top index
+    const uint32_t* occ;  // occupancy bitmaps of levels G + 1 .. D (NULL: none)
+    uint32_t occ_off[kOccMaxDepth - kTopLevelMax];  // word offsets of levels G + 1, G + 2, ...
+    int flat;             // 1: the index and the bitmaps give every cell's deepest level directly
 };
 
 // offset of level l's grid in the top index: 8^0 + ... + 8^(l-1) = (8^l - 1) / 7
@@ -54,6 +58,44 @@ __device__ __forceinline__ uint32_t top_entry(const TraceArgs& T, int l, int cx,
     const int sh = T.D - l;
     const uint32_t i = ((uint32_t)(cz >> sh) << (2 * l)) | ((uint32_t)(cy >> sh) << l) | (uint32_t)(cx >> sh);
     return __ldg(T.top + top_offset(l) + i);
+}
+
+// bits 0 .. 9 of v moved to bits 0, 3, 6, ..., 27 (one coordinate of a Morton key)
+__device__ __forceinline__ uint32_t spread3_10(uint32_t v) {
+    v = (v | (v << 16)) & 0x030000FFu;
+    v = (v | (v << 8)) & 0x0300F00Fu;
+    v = (v | (v << 4)) & 0x030C30C3u;
+    v = (v | (v << 2)) & 0x09249249u;
+    return v;
+}
+
+// Deepest level holding an existing node that contains leaf cell (cx, cy, cz),
+// when the index and the bitmaps cover every level (T.flat): the index gives
+// it down to level G, one bit per deeper level the rest; the loads are
+// independent of one another.
+__device__ __forceinline__ int deepest_level(const TraceArgs& T, int cx, int cy, int cz) {
+    const int sh = T.D - T.G;
+    const uint32_t ti =
+        ((uint32_t)(cz >> sh) << (2 * T.G)) | ((uint32_t)(cy >> sh) << T.G) | (uint32_t)(cx >> sh);
+    const int L0 = (int)(__ldg(T.top + T.top_offG + ti) >> 28);
+    // the Morton key (x bits at 3i, y at 3i + 1, z at 3i + 2) of the leaf cell; D <= 9
+    const uint32_t key = spread3_10((uint32_t)cx) | (spread3_10((uint32_t)cy) << 1) | (spread3_10((uint32_t)cz) << 2);
+    uint32_t w[kOccMaxDepth - kTopLevelMax];
+#pragma unroll
+    for (int j = 0; j < kOccMaxDepth - kTopLevelMax; ++j) {
+        const int l = T.G + 1 + j;
+        w[j] = 0u;
+        if (l <= T.D) w[j] = __ldg(T.occ + T.occ_off[j] + ((key >> (3 * (T.D - l))) >> 5));
+    }
+    if (L0 < T.G) return L0;
+    int L = T.G;
+#pragma unroll
+    for (int j = 0; j < kOccMaxDepth - kTopLevelMax; ++j) {
+        const int l = T.G + 1 + j;
+        if (l > T.D || L != l - 1) break;
+        if ((w[j] >> ((key >> (3 * (T.D - l))) & 31u)) & 1u) L = l;
+    }
+    return L;
 }
 
 struct GuideArgs {
@@ -97,6 +139,20 @@ __device__ __forceinline__ Node load_node(const TraceArgs& T, const Node* s_node
     n.first_child = v.x;
     n.mask = v.y;
     return n;
+}
+
+// the node at level l (>= G) holding leaf cell (cx, cy, cz), which must exist:
+// from the index's node at level G, descending l - G levels
+__device__ __forceinline__ uint32_t node_at_level(const TraceArgs& T, const Node* s_nodes, int l, int cx, int cy,
+                                                  int cz) {
+    uint32_t node = top_entry(T, T.G, cx, cy, cz) & kTopNodeMask;
+    for (int lv = T.G; lv < l; ++lv) {
+        const Node nd = load_node(T, s_nodes, node);
+        const int sh = T.D - 1 - lv;
+        const int k = ((cx >> sh) & 1) | (((cy >> sh) & 1) << 1) | (((cz >> sh) & 1) << 2);
+        node = child_id(nd, k);
+    }
+    return node;
 }
 
 // first index with x[i] > t (N if none) in a non-decreasing shared-memory row
@@ -309,6 +365,53 @@ __device__ __forceinline__ bool ray_start(const TraceArgs& T, bool has_origin, b
     return alive;
 }
 
+// The cone query of a hit leaf (Eq. 6): the level whose squared side is closest
+// to the footprint t^2 omega (ties to the finer level), its node holding the
+// leaf, and that node's value on the side facing back along the ray.  an_path:
+// the ancestor at the chosen level when it lies on the caller's node path at or
+// below G (only used without the flat index).
+__device__ __forceinline__ float hit_value(const TraceArgs& T, const Node* s_nodes, float t, int cx, int cy, int cz,
+                                           float dx, float dy, float dz, const uint32_t* stk, int stride) {
+    const float A = __fmul_rn(__fmul_rn(t, t), T.omega);
+    float side = T.S, bd = __int_as_float(0x7f800000);
+    int best = 0;
+    for (int l = 0; l <= T.D; ++l) {
+        const float diff = fabsf(__fsub_rn(__fmul_rn(side, side), A));
+        if (diff <= bd) {
+            bd = diff;
+            best = l;
+        }
+        side = __fmul_rn(side, 0.5f);
+    }
+    // the hit leaf's ancestor at that level: the top index, else the node path (or a short descent)
+    const uint32_t an = best < T.G ? (top_entry(T, best, cx, cy, cz) & kTopNodeMask)
+                                   : (T.flat ? node_at_level(T, s_nodes, best, cx, cy, cz) : stk[best * stride]);
+    const float4 Nn = T.normal[an];
+    const float2 V = T.value[an];
+    const float dd = __fadd_rn(__fadd_rn(__fmul_rn(Nn.x, dx), __fmul_rn(Nn.y, dy)), __fmul_rn(Nn.z, dz));
+    float L = (dd <= 0.0f) ? V.x : V.y;  // the side facing back along the ray
+    if (T.cos_weight) L = __fmul_rn(L, fabsf(dd));
+    return L;
+}
+
+constexpr int kHitQueue = 32;  // per-warp queue of hits awaiting their cone query (flat index only)
+constexpr int kHitWords = 6;   // cell, t, leaf cell (10 bits per axis, D <= 9), direction (3)
+
+// the cone queries of queue entries [e0, e0 + n) (n <= 32), one per lane, into out[cell]
+__device__ __forceinline__ void flush_hits(const TraceArgs& T, const GuideArgs& G, const Node* s_nodes,
+                                           const uint32_t* hq, int e0, int n, int lane, float* out) {
+    if (lane < n) {
+        const int e = e0 + lane;
+        const int q = (int)hq[0 * kHitQueue + e];
+        const float t = __uint_as_float(hq[1 * kHitQueue + e]);
+        const uint32_t c = hq[2 * kHitQueue + e];
+        const int cx = (int)(c & 1023u), cy = (int)((c >> 10) & 1023u), cz = (int)(c >> 20);
+        const float dx = __uint_as_float(hq[3 * kHitQueue + e]), dy = __uint_as_float(hq[4 * kHitQueue + e]),
+                    dz = __uint_as_float(hq[5 * kHitQueue + e]);
+        out[q] = __fadd_rn(G.eps, hit_value(T, s_nodes, t, cx, cy, cz, dx, dy, dz, nullptr, 0));
+    }
+}
+
 // separable [1 2 1] / 4 blur of an N x N field with the octahedral mirror at the
 // edges (rows first into tmp, then columns back into field); every thread of
 // the CTA calls it, with the barriers inside
@@ -341,7 +444,7 @@ __device__ __forceinline__ void march_chunk(const TraceArgs& T, const GuideArgs&
                                             uint32_t* s_stack, float* s_ray, float* wbuf, int* s_next, int c0,
                                             int cn, int chunk, bool has_origin, bool inside, float gx, float gy,
                                             float gz, uint64_t jseed, uint64_t jstream, float tn, uint32_t* status,
-                                            float* out) {
+                                            float* out, uint32_t* hqueue) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t lt = (1u << lane) - 1u;
     const int D = T.D;
@@ -371,7 +474,35 @@ __device__ __forceinline__ void march_chunk(const TraceArgs& T, const GuideArgs&
     int wb_n = 0, wb_head = 0;  // unstaged: entries in this warp's ray buffer, next one to hand out
     bool wb_dry = false;        // unstaged: no cells of the chunk left for this warp
     float* wb = wbuf + warp * (kWbWords * 32);
+    uint32_t* hq = hqueue + warp * (kHitQueue * kHitWords);
+    int hq_n = 0;       // entries in this warp's hit queue
+    bool pend = false;  // this lane's ray hit a leaf in the last pass and waits for the queue
     for (;;) {
+        if (T.flat) {
+            // hits of the last pass join the warp's queue; when it would overflow, its entries
+            // get their cone queries together, nearly every lane busy
+            const uint32_t hm = __ballot_sync(0xffffffffu, pend);
+            if (hm) {
+                if (hq_n + __popc(hm) > kHitQueue) {
+                    flush_hits(T, G, s_nodes, hq, 0, hq_n, lane, out);
+                    hq_n = 0;
+                    __syncwarp();
+                }
+                if (pend) {
+                    const int e = hq_n + __popc(hm & lt);
+                    hq[0 * kHitQueue + e] = (uint32_t)q;
+                    hq[1 * kHitQueue + e] = __float_as_uint(t);
+                    hq[2 * kHitQueue + e] = (uint32_t)cx | ((uint32_t)cy << 10) | ((uint32_t)cz << 20);
+                    hq[3 * kHitQueue + e] = __float_as_uint(dx);
+                    hq[4 * kHitQueue + e] = __float_as_uint(dy);
+                    hq[5 * kHitQueue + e] = __float_as_uint(dz);
+                    q = -1;
+                    pend = false;
+                }
+                hq_n += __popc(hm);
+                __syncwarp();
+            }
+        }
         const bool idle = q < 0;
         const uint32_t need = __ballot_sync(0xffffffffu, idle);
         if (kStage) {
@@ -405,7 +536,10 @@ __device__ __forceinline__ void march_chunk(const TraceArgs& T, const GuideArgs&
             }
             // leave only when every lane has run out of cells (a lane whose new ray
             // died at its start is idle again and fetches once more)
-            if (__all_sync(0xffffffffu, q >= cn)) break;
+            if (__all_sync(0xffffffffu, q >= cn)) {
+                if (hq_n > 0) flush_hits(T, G, s_nodes, hq, 0, hq_n, lane, out);
+                break;
+            }
             if (q < 0 || q >= cn) continue;  // idle, or out of cells: no ray to step
         } else {
             // the whole warp sets up the next 32 cells' rays at once (converged), so a
@@ -463,21 +597,29 @@ __device__ __forceinline__ void march_chunk(const TraceArgs& T, const GuideArgs&
                 wb_head = min(wb_n, wb_head + __popc(need));
                 __syncwarp();  // entries are read before a refill overwrites them
             }
-            if (wb_dry && __all_sync(0xffffffffu, q < 0)) break;
+            if (wb_dry && __all_sync(0xffffffffu, q < 0)) {
+                if (hq_n > 0) flush_hits(T, G, s_nodes, hq, 0, hq_n, lane, out);
+                break;
+            }
             if (q < 0) continue;  // idle: no ray to step
         }
         // ---- one step: deepest existing node holding the cell, then hit or skip its empty block.
         // At most kDescentPerPass levels per pass of the loop: a lane with a deeper descent
         // goes on in the next pass instead of holding its whole warp in this one
         if (level < 0) {
-            // the deepest existing node at a level <= G holding the cell, from the top index
-            const uint32_t e = top_entry(T, T.G, cx, cy, cz);
-            level = (int)(e >> 28);
-            node = e & kTopNodeMask;
-            stk[level * kGuideThreads] = node;
+            if (T.flat) {
+                // one step per pass: the cell's deepest existing level, then its hit or skip
+                level = deepest_level(T, cx, cy, cz);
+            } else {
+                // the deepest existing node at a level <= G holding the cell, from the top index
+                const uint32_t e = top_entry(T, T.G, cx, cy, cz);
+                level = (int)(e >> 28);
+                node = e & kTopNodeMask;
+                stk[level * kGuideThreads] = node;
+            }
         }
         bool settled = true;
-        for (int dl = 0; level < D; ++dl) {
+        for (int dl = 0; !T.flat && level < D; ++dl) {
             if (dl == kDescentPerPass) {
                 settled = false;
                 break;
@@ -494,27 +636,12 @@ __device__ __forceinline__ void march_chunk(const TraceArgs& T, const GuideArgs&
         float L = 0.0f;
         bool done = false;
         if (level == D && t >= T.t_skip) {
-            // Eq. 6: footprint A = t^2 omega; the level whose squared side is closest
-            const float A = __fmul_rn(__fmul_rn(t, t), T.omega);
-            float side = T.S, bd = INF;
-            int best = 0;
-            for (int l = 0; l <= D; ++l) {
-                const float diff = fabsf(__fsub_rn(__fmul_rn(side, side), A));
-                if (diff <= bd) {
-                    bd = diff;
-                    best = l;
-                }
-                side = __fmul_rn(side, 0.5f);
+            if (T.flat) {
+                pend = true;  // its cone query waits for a full batch (queued at the next pass)
+            } else {
+                L = hit_value(T, s_nodes, t, cx, cy, cz, dx, dy, dz, stk, kGuideThreads);
+                done = true;
             }
-            // the hit leaf's ancestor at that level: on this ray's node path below G, else in the top index
-            const uint32_t an =
-                best >= T.G ? stk[best * kGuideThreads] : (top_entry(T, best, cx, cy, cz) & kTopNodeMask);
-            const float4 Nn = T.normal[an];
-            const float2 V = T.value[an];
-            const float dd = __fadd_rn(__fadd_rn(__fmul_rn(Nn.x, dx), __fmul_rn(Nn.y, dy)), __fmul_rn(Nn.z, dz));
-            L = (dd <= 0.0f) ? V.x : V.y;  // the side facing back along the ray
-            if (T.cos_weight) L = __fmul_rn(L, fabsf(dd));
-            done = true;
         } else {
             // leave the empty block (or a leaf entered before t_skip) through its first exit crossing
             const int sl = (level == D) ? 0 : D - level - 1;
@@ -553,7 +680,7 @@ __device__ __forceinline__ void march_chunk(const TraceArgs& T, const GuideArgs&
                 // through the top index when that ancestor lies above its deepest level
                 const uint32_t diff = (uint32_t)((cx ^ nx) | (cy ^ ny) | (cz ^ nz));
                 const int lc = D - 1 - (31 - __clz(diff));
-                if (lc >= T.G) {
+                if (!T.flat && lc >= T.G) {
                     level = lc;
                     node = stk[lc * kGuideThreads];
                 } else {
@@ -594,7 +721,8 @@ __global__ void __launch_bounds__(kGuideThreads, 1024 / kGuideThreads) k_guide_b
     uint32_t* s_stack = reinterpret_cast<uint32_t*>(smem + sizeof(Node) * T.smem_nodes);
     float* s_ray = reinterpret_cast<float*>(s_stack + (D + 1) * kGuideThreads);  // 6 x chunk: d, 1/(d 2^D/S)
     float* wbuf = s_ray;  // unstaged: per warp, kWbWords x 32 entries of ready rays
-    float* field = s_ray + (kStage ? 6 * chunk : (kGuideThreads / 32) * kWbWords * 32);
+    uint32_t* hqueue = reinterpret_cast<uint32_t*>(s_ray + (kStage ? 6 * chunk : (kGuideThreads / 32) * kWbWords * 32));
+    float* field = reinterpret_cast<float*>(hqueue + (kGuideThreads / 32) * kHitQueue * kHitWords);
     float* tmp = field + NN;
     float* rowtot = tmp + NN;
     float* marg = rowtot + N;
@@ -650,7 +778,7 @@ __global__ void __launch_bounds__(kGuideThreads, 1024 / kGuideThreads) k_guide_b
             const int cn = min(chunk, cend - c0);  // cells in this chunk
             march_chunk<kGuideThreads, kStage>(T, G, s_nodes, s_stack, s_ray, wbuf, &s_next, c0, cn, chunk,
                                                r != kNone, inside, gx, gy, gz, jseed, jstream, tn, status,
-                                               field + c0);
+                                               field + c0, hqueue);
         }
         bool finish = true;
         if (parts > 1) {  // publish this part's cells; the CTA of the bin's last part gathers them all
@@ -744,6 +872,7 @@ __global__ void __launch_bounds__(kGuideThreads, 1024 / kGuideThreads)
     Node* s_nodes = reinterpret_cast<Node*>(smem);
     uint32_t* s_stack = reinterpret_cast<uint32_t*>(smem + sizeof(Node) * T.smem_nodes);
     float* wbuf = reinterpret_cast<float*>(s_stack + (D + 1) * kGuideThreads);
+    uint32_t* hqueue = reinterpret_cast<uint32_t*>(wbuf + (kGuideThreads / 32) * kWbWords * 32);
     __shared__ int s_next;
     __shared__ uint32_t s_unit;
     const int tid = threadIdx.x;
@@ -776,7 +905,7 @@ __global__ void __launch_bounds__(kGuideThreads, 1024 / kGuideThreads)
         const uint64_t jstream = bin_stream(G.frame_dev ? *G.frame_dev : G.frame, b);
         march_chunk<kGuideThreads, false>(T, G, s_nodes, s_stack, nullptr, wbuf, &s_next, c0, kMarchPart, kMarchPart,
                                           r != kNone, inside, gx, gy, gz, jseed, jstream, tn, status,
-                                          raw + (size_t)b * NN + c0);
+                                          raw + (size_t)b * NN + c0, hqueue);
         if (tid == 0) s_unit = gridDim.x + atomicAdd(unit_next, 1u);
         __syncthreads();
         u = s_unit;
@@ -946,7 +1075,7 @@ static size_t guide_smem_bytes(uint32_t smem_nodes, int N, int D, int threads, b
     const size_t chunk = NN < (size_t)kGuideChunk ? NN : (size_t)kGuideChunk;
     const size_t rays = stage ? 6 * chunk : (size_t)(threads / 32) * kWbWords * 32;
     return sizeof(Node) * smem_nodes + sizeof(uint32_t) * (size_t)(D + 1) * threads +
-           sizeof(float) * (rays + 2 * NN + 2 * (size_t)N);
+           sizeof(float) * (rays + 2 * NN + 2 * (size_t)N) + sizeof(uint32_t) * (size_t)(threads / 32) * kHitQueue * kHitWords;
 }
 
 // zeroes the per-bin part counters (the first word of each bin's cdf_marg row)
@@ -1020,6 +1149,13 @@ static void trace_setup(const wfpg_svo* s, const wfpg_guide_params* p, TraceArgs
     T->smem_nodes = s->level_off[top + 1];
     T->top = s->top;
     T->G = s->top_levels - 1;
+    T->top_offG = T->G >= 0 ? s->top_off[T->G] : 0u;
+    T->occ = s->occ;
+    for (int j = 0; j < kOccMaxDepth - kTopLevelMax; ++j) {
+        const int l = T->G + 1 + j;
+        T->occ_off[j] = (s->occ && l <= s->D) ? (uint32_t)s->occ_off[l] : 0u;
+    }
+    T->flat = T->G >= 0 && (T->G == s->D || s->occ != nullptr);
     G->N = p->N;
     G->eps = p->eps;
     G->jitter = p->jitter;
@@ -1063,7 +1199,8 @@ static int launch_march(const wfpg_svo* s, const TraceArgs& T, const GuideArgs& 
                         float* cdf_row, float* cdf_marg, cudaStream_t st) {
     auto kernel = k_guide_march<kThreads>;
     const size_t smem = sizeof(Node) * T.smem_nodes + sizeof(uint32_t) * (size_t)(s->D + 1) * kThreads +
-                        sizeof(float) * (size_t)(kThreads / 32) * kWbWords * 32;
+                        sizeof(float) * (size_t)(kThreads / 32) * kWbWords * 32 +
+                        sizeof(uint32_t) * (size_t)(kThreads / 32) * kHitQueue * kHitWords;
     int rc = WFPG_OK;
     const uint64_t slots = guide_slots(kernel, kThreads, smem, &rc);
     if (rc != WFPG_OK) return rc;

@@ -462,24 +462,32 @@ __global__ void __launch_bounds__(256) k_rowsum(const bf16* __restrict__ AT, int
 }
 
 // ---------------------------------------------------------------------------
-// The output layer of a training step, fused: for one 128-row tile, the logits
-// Z = H3 W4^T + b4 (1024 per row) are computed chunk by chunk on the tensor
-// cores into tensor memory and never stored.  Pass 1 keeps each row's running
-// maximum and exponential sum (and sums the target row); pass 2 recomputes
-// each chunk, forms the logit gradient G = bf16((softmax(Z) - q / sum q) / n)
-// and the KL term, writes G^T (for the weight gradient dW4 = G^T H3, a
-// separate split-K GEMM) and the column sums of G (db4), and accumulates
-// dA3 = G W4 in tensor memory with a second MMA per chunk.  The epilogue
-// writes d3 = bf16(dA3 o [H3 > 0]) and its transpose.
-// 256 threads: warp w reads TMEM lanes 32 (w % 4) .. + 31 (rows of the tile)
-// and handles columns 64 (w / 4) .. + 63 of each 128-logit chunk.
-constexpr int kOutThreads = 256;
+// The output layer of a training step, fused: for each 128-row tile, the
+// logits Z = H3 W4^T + b4 (1024 per row) are computed chunk by chunk on the
+// tensor cores into tensor memory and never stored.  Pass 1 keeps each row's
+// running maximum and exponential sum and sums its target row; pass 2
+// recomputes each chunk, forms the logit gradient
+// G = bf16((softmax(Z) - q / sum q) / n) and the KL term, writes G^T (for the
+// weight gradient dW4 = G^T H3, a separate split-K GEMM) and the column sums
+// of G (db4), and accumulates dA3 = G W4 in tensor memory with a second MMA
+// per chunk.  The epilogue writes d3 = bf16(dA3 o [H3 > 0]) and its transpose.
+//
+// One CTA per SM, persistent over tiles, 512 threads: warp w reads TMEM lanes
+// 32 (w % 4) .. + 31 (the tile's rows) and handles columns 32 (w / 4) .. + 31
+// of each 128-logit chunk.  The logits of chunk c + 1 are computed into the
+// second of two TMEM buffers while chunk c is processed; W4 rows, W4^T
+// columns and the target chunk (staged with a padded row stride, so that each
+// thread reads its own row without bank conflicts) are copied in by cp.async
+// ahead of their use.
+constexpr int kOutThreads = 512;
 constexpr int kOutChunk = 128;                 // logits per chunk
 constexpr int kOutChunks = kOut / kOutChunk;   // 8
-constexpr uint32_t kOutTmemCols = 256;         // Z chunk at column 0 (128), dA3 at column 128 (64)
-constexpr int kOutSmemH = 0, kOutSmemW = 16384, kOutSmemWT = 32768, kOutSmemG = 49152, kOutSmemB = 81920,
+constexpr uint32_t kOutTmemCols = 512;         // Z buffers at columns 0 and 128, dA3 at 256
+constexpr int kOutTLd = kOutChunk + 4;         // staged target row stride (floats)
+constexpr int kOutSmemH = 0, kOutSmemW = 16384, kOutSmemWT = kOutSmemW + 2 * 16384, kOutSmemG = kOutSmemWT + 16384,
+              kOutSmemT = kOutSmemG + 32768, kOutSmemB = kOutSmemT + 128 * kOutTLd * 4,
               kOutSmemStat = kOutSmemB + 4 * kOut;
-constexpr int kOutSmemBytes = kOutSmemStat + 3 * 2 * 128 * 4;
+constexpr int kOutSmemBytes = kOutSmemStat + 3 * 4 * 128 * 4;
 
 struct OutTrainArgs {
     const bf16* h3;      // [n][64]
@@ -504,32 +512,40 @@ __device__ __forceinline__ int cm_off(int r, int k) {
     return (r >> 3) * (KC * 16) + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2;
 }
 
-__global__ void __launch_bounds__(kOutThreads) k_out_train(OutTrainArgs a) {
+// target rows [m0, m0 + 128) x columns [c0, c0 + 128) into the staging buffer
+// (row stride kOutTLd floats); rows past n are not read
+__device__ __forceinline__ void stage_target(float* sT, const float* target, int n, int m0, int c0) {
+    for (int idx = threadIdx.x; idx < 128 * (kOutChunk / 4); idx += kOutThreads) {
+        const int r = idx >> 5, c4 = idx & 31;
+        const bool valid = m0 + r < n;
+        tc::cp_async16(sT + r * kOutTLd + 4 * c4, valid ? target + (size_t)(m0 + r) * kOut + c0 + 4 * c4 : target,
+                       valid);
+    }
+}
+
+__global__ void __launch_bounds__(kOutThreads, 1) k_out_train(OutTrainArgs a) {
     extern __shared__ __align__(1024) uint8_t out_smem[];
     uint8_t* sH = out_smem + kOutSmemH;    // H3 tile: 128 x 64 (K = 64)
-    uint8_t* sW = out_smem + kOutSmemW;    // W4 rows of the chunk: 128 x 64 (K = 64)
-    uint8_t* sWT = out_smem + kOutSmemWT;  // W4^T columns of the chunk: 64 x 128 (K = 128)
+    uint8_t* sW0 = out_smem + kOutSmemW;   // W4 rows of a chunk: 128 x 64 (K = 64), two buffers
+    uint8_t* sWT = out_smem + kOutSmemWT;  // W4^T columns of a chunk: 64 x 128 (K = 128)
     uint8_t* sG = out_smem + kOutSmemG;    // G of the chunk: 128 x 128 (K = 128)
+    float* sT = reinterpret_cast<float*>(out_smem + kOutSmemT);
     float* sb = reinterpret_cast<float*>(out_smem + kOutSmemB);
-    float* s_max = reinterpret_cast<float*>(out_smem + kOutSmemStat);  // [2][128] per column half
-    float* s_sum = s_max + 256;
-    float* s_tsum = s_sum + 256;
-    __shared__ __align__(8) uint64_t mbar;
+    float* s_max = reinterpret_cast<float*>(out_smem + kOutSmemStat);  // [4 column groups][128 rows]
+    float* s_sum = s_max + 512;
+    float* s_tsum = s_sum + 512;
+    __shared__ __align__(8) uint64_t mbar[3];  // 0, 1: Z buffers; 2: dA3
     __shared__ uint32_t tmem_base;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int quad = warp & 3, half = warp >> 2;
+    const int quad = warp & 3, cg = warp >> 2;
     const int r = quad * 32 + lane;  // tile row of this thread
-    const int m0 = blockIdx.x * 128, row = m0 + r;
-    const bool live = row < a.n;
-    const int h0 = half * 64;        // first chunk column of this thread
+    const int k0 = cg * 32;          // first chunk column of this thread
     if (warp == 0) tc::tmem_alloc(&tmem_base, kOutTmemCols);
     if (tid == 0) {
-        tc::mbar_init(&mbar, 1);
+        for (int i = 0; i < 3; ++i) tc::mbar_init(&mbar[i], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    load_tile<64, kOutThreads>(sH, a.h3, kHid, m0, 128, a.n, 0, kHid);
     for (int i = tid; i < kOut; i += kOutThreads) sb[i] = a.b4[i];
-    tc::fence_proxy_async();
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
@@ -537,216 +553,234 @@ __global__ void __launch_bounds__(kOutThreads) k_out_train(OutTrainArgs a) {
     const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16);
     constexpr uint32_t idesc_z = tc::idesc_bf16_f32(128, kOutChunk);
     constexpr uint32_t idesc_d = tc::idesc_bf16_f32(128, kHid);
-    const float* trow = a.target + (size_t)row * kOut;
-    uint32_t phase = 0;
+    uint32_t phase = 0;  // bit i: parity of mbar[i]'s next phase
     bool ok = true;
-
-    // Z chunk -> TMEM columns [0, 128) from the staged W4 rows: 4 MMAs (K = 64)
-    auto issue_z = [&]() {
+    auto sW = [&](int buf) { return sW0 + buf * 16384; };
+    // Z of the chunk whose W4 rows are in buffer `buf` -> TMEM columns 128 buf, 4 MMAs (K = 64)
+    auto issue_z = [&](int buf) {
         if (tid == 0) {
             tc::fence_after_sync();
-            const uint32_t a0 = tc::smem_addr(sH), b0 = tc::smem_addr(sW);
+            const uint32_t a0 = tc::smem_addr(sH), b0 = tc::smem_addr(sW(buf));
 #pragma unroll
             for (int s = 0; s < kHid / 16; ++s)
-                tc::mma_bf16(tmem, tc::smem_desc(a0 + s * 256, 128, 64 * 16), tc::smem_desc(b0 + s * 256, 128, 64 * 16),
-                             idesc_z, s > 0 ? 1u : 0u);
-            tc::mma_commit(&mbar);
+                tc::mma_bf16(tmem + (uint32_t)(buf * kOutChunk), tc::smem_desc(a0 + s * 256, 128, 64 * 16),
+                             tc::smem_desc(b0 + s * 256, 128, 64 * 16), idesc_z, s > 0 ? 1u : 0u);
+            tc::mma_commit(&mbar[buf]);
         }
     };
-    auto wait_mma = [&]() {
-        ok = ok && __syncthreads_and(tc::mbar_wait(&mbar, phase)) != 0;
-        phase ^= 1u;
+    auto wait_bar = [&](int i) {
+        ok = ok && __syncthreads_and(tc::mbar_wait(&mbar[i], (phase >> i) & 1u)) != 0;
+        phase ^= 1u << i;
         tc::fence_after_sync();
     };
-
-    // ---- pass 1: running maximum and exponential sum over this thread's columns; target sum.
-    // The W4 rows of chunk c + 1 are copied in while chunk c's logits are processed.
-    float mrun = -3.4e38f, srun = 0.0f, tsum = 0.0f;
-    load_tile_async<64, kOutThreads>(sW, a.w4, kHid, 0, kOutChunk, kOut, 0, kHid);
-    tc::cp_async_commit();
-    for (int c = 0; c < kOutChunks && ok; ++c) {
+    float kl = 0.0f;
+    const int n_tiles = (a.n + 127) / 128;
+    for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+        const int m0 = tile * 128, row = m0 + r;
+        const bool live = row < a.n;
+        // ---- pass 1: running maximum and exponential sum of this thread's columns; target row sums
+        load_tile_async<64, kOutThreads>(sH, a.h3, kHid, m0, 128, a.n, 0, kHid);
+        load_tile_async<64, kOutThreads>(sW(0), a.w4, kHid, 0, kOutChunk, kOut, 0, kHid);
+        load_tile_async<64, kOutThreads>(sW(1), a.w4, kHid, kOutChunk, kOutChunk, kOut, 0, kHid);
+        stage_target(sT, a.target, a.n, m0, 0);
+        tc::cp_async_commit();
         tc::cp_async_wait_all();
         tc::fence_proxy_async();
         __syncthreads();
-        issue_z();
-        if (live) {
-            const float4* tq = reinterpret_cast<const float4*>(trow + c * kOutChunk + h0);
-#pragma unroll 8
-            for (int i = 0; i < 16; ++i) {
-                const float4 v = tq[i];
-                tsum += (v.x + v.y) + (v.z + v.w);
+        issue_z(0);
+        float mrun = -3.4e38f, srun = 0.0f, tsum = 0.0f;
+        for (int c = 0; c < kOutChunks && ok; ++c) {
+            if (c > 0) {  // target chunk c and the W4 rows of chunk c + 1 have landed
+                tc::cp_async_wait_all();
+                tc::fence_proxy_async();
+                __syncthreads();
             }
-        }
-        wait_mma();
-        if (!ok) break;
-        if (c + 1 < kOutChunks) {  // sW is free once the MMAs have read it
-            load_tile_async<64, kOutThreads>(sW, a.w4, kHid, (c + 1) * kOutChunk, kOutChunk, kOut, 0, kHid);
-            tc::cp_async_commit();
-        }
-#pragma unroll 1
-        for (int g = 0; g < 2; ++g) {
+            if (c + 1 < kOutChunks) issue_z((c + 1) & 1);  // overlaps this chunk's processing
+            wait_bar(c & 1);
+            if (!ok) break;
             float v[32];
-            tc::tmem_ld32(lane_base + (uint32_t)(h0 + g * 32), v);
+            tc::tmem_ld32(lane_base + (uint32_t)((c & 1) * kOutChunk + k0), v);
             float gm = -3.4e38f;
 #pragma unroll
             for (int i = 0; i < 32; ++i) {
-                v[i] += sb[c * kOutChunk + h0 + g * 32 + i];
+                v[i] += sb[c * kOutChunk + k0 + i];
                 gm = fmaxf(gm, v[i]);
             }
             if (gm > mrun) {
                 srun *= __expf(mrun - gm);
                 mrun = gm;
             }
+            const float* tr = sT + r * kOutTLd + k0;
 #pragma unroll
             for (int i = 0; i < 32; ++i) srun += __expf(v[i] - mrun);
+#pragma unroll
+            for (int i = 0; i < 32; i += 4) {
+                const float4 t4 = *reinterpret_cast<const float4*>(tr + i);
+                tsum += (t4.x + t4.y) + (t4.z + t4.w);
+            }
+            tc::fence_before_sync();
+            __syncthreads();  // the chunk's TMEM buffer, W4 rows and target stage are free
+            if (c + 1 < kOutChunks) {
+                stage_target(sT, a.target, a.n, m0, (c + 1) * kOutChunk);
+                if (c + 2 < kOutChunks)
+                    load_tile_async<64, kOutThreads>(sW(c & 1), a.w4, kHid, (c + 2) * kOutChunk, kOutChunk, kOut, 0, kHid);
+                tc::cp_async_commit();
+            }
         }
-        tc::fence_before_sync();
-        __syncthreads();  // every lane has read the chunk: TMEM and sW are free
-    }
-    // the row's statistics from its two column halves
-    s_max[half * 128 + r] = mrun;
-    s_sum[half * 128 + r] = srun;
-    s_tsum[half * 128 + r] = tsum;
-    __syncthreads();
-    {
-        const float m0v = s_max[r], m1v = s_max[128 + r];
-        mrun = fmaxf(m0v, m1v);
-        srun = s_sum[r] * __expf(m0v - mrun) + s_sum[128 + r] * __expf(m1v - mrun);
-        tsum = s_tsum[r] + s_tsum[128 + r];
-    }
+        // the row's statistics from its four column groups
+        s_max[cg * 128 + r] = mrun;
+        s_sum[cg * 128 + r] = srun;
+        s_tsum[cg * 128 + r] = tsum;
+        __syncthreads();
+        {
+            float mm = s_max[r];
+            for (int g = 1; g < 4; ++g) mm = fmaxf(mm, s_max[g * 128 + r]);
+            float ss = 0.0f, tt = 0.0f;
+            for (int g = 0; g < 4; ++g) {
+                ss += s_sum[g * 128 + r] * __expf(s_max[g * 128 + r] - mm);
+                tt += s_tsum[g * 128 + r];
+            }
+            mrun = mm;
+            srun = ss;
+            tsum = tt;
+        }
+        if (!ok) break;
 
-    // ---- pass 2 (chunks in reverse, so the target rows read last are read again first)
-    const float log_s = __logf(srun), inv_t = tsum > 0.0f ? 1.0f / tsum : 0.0f;
-    const float shift = mrun + log_s;
-    float kl = 0.0f;
-    tc::cp_async_wait_all();
-    __syncthreads();
-    if (ok) {
-        load_tile_async<64, kOutThreads>(sW, a.w4, kHid, (kOutChunks - 1) * kOutChunk, kOutChunk, kOut, 0, kHid);
+        // ---- pass 2, chunks in reverse (the target rows read last are read again first)
+        const float shift = mrun + __logf(srun), inv_t = tsum > 0.0f ? 1.0f / tsum : 0.0f;
+        __syncthreads();  // statistics read before the buffers are refilled
+        load_tile_async<64, kOutThreads>(sW(0), a.w4, kHid, (kOutChunks - 1) * kOutChunk, kOutChunk, kOut, 0, kHid);
+        load_tile_async<64, kOutThreads>(sW(1), a.w4, kHid, (kOutChunks - 2) * kOutChunk, kOutChunk, kOut, 0, kHid);
         load_tile_async<128, kOutThreads>(sWT, a.w4t, kOut, 0, kHid, kHid, (kOutChunks - 1) * kOutChunk, kOut);
+        stage_target(sT, a.target, a.n, m0, (kOutChunks - 1) * kOutChunk);
         tc::cp_async_commit();
-    }
-    for (int cc = 0; cc < kOutChunks && ok; ++cc) {
-        const int c = kOutChunks - 1 - cc;
         tc::cp_async_wait_all();
         tc::fence_proxy_async();
         __syncthreads();
-        issue_z();
-        wait_mma();
-        if (!ok) break;
-        if (cc + 1 < kOutChunks) {  // the next chunk's W4 rows, while this one is processed
-            load_tile_async<64, kOutThreads>(sW, a.w4, kHid, (c - 1) * kOutChunk, kOutChunk, kOut, 0, kHid);
-            tc::cp_async_commit();
-        }
-#pragma unroll 1
-        for (int g = 0; g < 2; ++g) {
-            float v[32];
-            tc::tmem_ld32(lane_base + (uint32_t)(h0 + g * 32), v);
-            const int k0 = h0 + g * 32;  // chunk column of v[0]
-            float4 t4[8];
-            if (live) {
-                const float4* tq = reinterpret_cast<const float4*>(trow + c * kOutChunk + k0);
-#pragma unroll
-                for (int i = 0; i < 8; ++i) t4[i] = tq[i];
+        issue_z(0);
+        for (int i = 0; i < kOutChunks && ok; ++i) {
+            const int c = kOutChunks - 1 - i, buf = i & 1;
+            if (i > 0) {  // target chunk c, W4^T chunk c and the next W4 rows have landed
+                tc::cp_async_wait_all();
+                tc::fence_proxy_async();
+                __syncthreads();
             }
+            if (i + 1 < kOutChunks) issue_z(buf ^ 1);
+            wait_bar(buf);
+            if (!ok) break;
+            {
+                float v[32];
+                tc::tmem_ld32(lane_base + (uint32_t)(buf * kOutChunk + k0), v);
+                const float* tr = sT + r * kOutTLd + k0;
 #pragma unroll
-            for (int h = 0; h < 4; ++h) {  // 8 columns = one 16-byte row of a core matrix
-                uint32_t w[4];
+                for (int h = 0; h < 4; ++h) {  // 8 columns = one 16-byte row of a core matrix
+                    const float4 ta = *reinterpret_cast<const float4*>(tr + 8 * h);
+                    const float4 tb = *reinterpret_cast<const float4*>(tr + 8 * h + 4);
+                    const float qv[8] = {ta.x, ta.y, ta.z, ta.w, tb.x, tb.y, tb.z, tb.w};
+                    uint32_t w[4];
 #pragma unroll
-                for (int e = 0; e < 4; ++e) {
+                    for (int e = 0; e < 4; ++e) {
+                        bf16 x[2];
+#pragma unroll
+                        for (int k = 0; k < 2; ++k) {
+                            const int j = 2 * e + k, col = k0 + 8 * h + j;
+                            float gv = 0.0f;
+                            if (live) {
+                                const float q = qv[j] * inv_t;
+                                const float logp = v[8 * h + j] + sb[c * kOutChunk + col] - shift;
+                                if (q > 0.0f) kl += q * (__logf(q) - logp);
+                                gv = (__expf(logp) - q) * a.inv_n;
+                            }
+                            x[k] = __float2bfloat16_rn(gv);
+                        }
+                        w[e] = (uint32_t)__bfloat16_as_ushort(x[0]) | ((uint32_t)__bfloat16_as_ushort(x[1]) << 16);
+                    }
+                    *reinterpret_cast<uint4*>(sG + cm_off<128>(r, k0 + 8 * h)) = make_uint4(w[0], w[1], w[2], w[3]);
+                }
+            }
+            tc::fence_proxy_async();
+            tc::fence_before_sync();
+            __syncthreads();  // G staged; the Z buffer and the target stage have been read
+            if (tid == 0) {
+                tc::fence_after_sync();
+                const uint32_t a0 = tc::smem_addr(sG), b0 = tc::smem_addr(sWT);
+#pragma unroll
+                for (int s = 0; s < kOutChunk / 16; ++s)
+                    tc::mma_bf16(tmem + 2u * kOutChunk, tc::smem_desc(a0 + s * 256, 128, 128 * 16),
+                                 tc::smem_desc(b0 + s * 256, 128, 128 * 16), idesc_d, (i > 0 || s > 0) ? 1u : 0u);
+                tc::mma_commit(&mbar[2]);
+            }
+            if (i + 1 < kOutChunks) {  // the next target chunk, and the W4 rows two chunks on
+                stage_target(sT, a.target, a.n, m0, (c - 1) * kOutChunk);
+                if (i + 2 < kOutChunks)
+                    load_tile_async<64, kOutThreads>(sW(buf), a.w4, kHid, (c - 2) * kOutChunk, kOutChunk, kOut, 0, kHid);
+                tc::cp_async_commit();
+            }
+            // G^T rows and db4 from the staged chunk: thread -> chunk column kc, 32 tile rows
+            {
+                const int kc = tid & 127, rq = (tid >> 7) * 32;
+                bf16* gt = a.g4t + (size_t)(c * kOutChunk + kc) * a.ldg + m0 + rq;
+                const bool full = m0 + rq + 32 <= a.n && (a.ldg & 7) == 0;
+                float cs = 0.0f;
+#pragma unroll 1
+                for (int r8 = 0; r8 < 32; r8 += 8) {
+                    uint32_t w[4];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const bf16 x0 = *reinterpret_cast<const bf16*>(sG + cm_off<128>(rq + r8 + 2 * e, kc));
+                        const bf16 x1 = *reinterpret_cast<const bf16*>(sG + cm_off<128>(rq + r8 + 2 * e + 1, kc));
+                        cs += __bfloat162float(x0) + __bfloat162float(x1);
+                        w[e] = (uint32_t)__bfloat16_as_ushort(x0) | ((uint32_t)__bfloat16_as_ushort(x1) << 16);
+                    }
+                    if (full) {
+                        *reinterpret_cast<uint4*>(gt + r8) = make_uint4(w[0], w[1], w[2], w[3]);
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < 8; ++e)
+                            if (m0 + rq + r8 + e < a.n)
+                                gt[r8 + e] = __ushort_as_bfloat16((unsigned short)(w[e >> 1] >> (16 * (e & 1))));
+                    }
+                }
+                atomicAdd(&a.db4[c * kOutChunk + kc], cs);
+            }
+            wait_bar(2);  // dA3 has read sG and W4^T
+            if (ok && i + 1 < kOutChunks) {
+                load_tile_async<128, kOutThreads>(sWT, a.w4t, kOut, 0, kHid, kHid, (c - 1) * kOutChunk, kOut);
+                tc::cp_async_commit();
+            }
+        }
+        if (!ok) break;
+        // ---- epilogue: d3 = bf16(dA3 o [H3 > 0]) (16 of the 64 columns per thread) and its transpose
+        {
+            float v[16];
+            tc::tmem_ld16(lane_base + (uint32_t)(2 * kOutChunk + cg * 16), v);
+            if (live) {
+                uint32_t w[8];
+#pragma unroll
+                for (int h = 0; h < 8; ++h) {
                     bf16 x[2];
 #pragma unroll
                     for (int k = 0; k < 2; ++k) {
-                        const int i = 8 * h + 2 * e + k;
-                        float gv = 0.0f;
-                        if (live) {
-                            const float4 tt = t4[i >> 2];
-                            const float q = ((i & 3) == 0 ? tt.x : (i & 3) == 1 ? tt.y : (i & 3) == 2 ? tt.z : tt.w) * inv_t;
-                            const float logp = v[i] + sb[c * kOutChunk + k0 + i] - shift;
-                            if (q > 0.0f) kl += q * (__logf(q) - logp);
-                            gv = (__expf(logp) - q) * a.inv_n;
-                        }
-                        x[k] = __float2bfloat16_rn(gv);
+                        const int j = cg * 16 + 2 * h + k;
+                        const float hv = __bfloat162float(*reinterpret_cast<const bf16*>(sH + cm_off<64>(r, j)));
+                        x[k] = __float2bfloat16_rn(hv > 0.0f ? v[2 * h + k] : 0.0f);
+                        a.d3t[(size_t)j * a.ldg + row] = x[k];
                     }
-                    w[e] = (uint32_t)__bfloat16_as_ushort(x[0]) | ((uint32_t)__bfloat16_as_ushort(x[1]) << 16);
+                    w[h] = (uint32_t)__bfloat16_as_ushort(x[0]) | ((uint32_t)__bfloat16_as_ushort(x[1]) << 16);
                 }
-                *reinterpret_cast<uint4*>(sG + cm_off<128>(r, k0 + 8 * h)) = make_uint4(w[0], w[1], w[2], w[3]);
+                uint4* dp = reinterpret_cast<uint4*>(a.d3 + (size_t)row * kHid + cg * 16);
+                dp[0] = make_uint4(w[0], w[1], w[2], w[3]);
+                dp[1] = make_uint4(w[4], w[5], w[6], w[7]);
             }
         }
-        tc::fence_proxy_async();
         tc::fence_before_sync();
-        __syncthreads();  // G staged; the Z chunk has been read
-        if (tid == 0) {
-            tc::fence_after_sync();
-            const uint32_t a0 = tc::smem_addr(sG), b0 = tc::smem_addr(sWT);
-#pragma unroll
-            for (int s = 0; s < kOutChunk / 16; ++s)
-                tc::mma_bf16(tmem + (uint32_t)kOutChunk, tc::smem_desc(a0 + s * 256, 128, 128 * 16),
-                             tc::smem_desc(b0 + s * 256, 128, 128 * 16), idesc_d, (cc > 0 || s > 0) ? 1u : 0u);
-            tc::mma_commit(&mbar);
-        }
-        // G^T rows and db4 from the staged chunk: thread -> chunk column kc, 64 tile rows
-        {
-            const int kc = tid & 127, rh = (tid >> 7) * 64;
-            bf16* gt = a.g4t + (size_t)(c * kOutChunk + kc) * a.ldg + m0 + rh;
-            const bool full = m0 + rh + 64 <= a.n && (a.ldg & 7) == 0;
-            float cs = 0.0f;
-#pragma unroll 1
-            for (int r8 = 0; r8 < 64; r8 += 8) {
-                uint32_t w[4];
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const bf16 x0 = *reinterpret_cast<const bf16*>(sG + cm_off<128>(rh + r8 + 2 * e, kc));
-                    const bf16 x1 = *reinterpret_cast<const bf16*>(sG + cm_off<128>(rh + r8 + 2 * e + 1, kc));
-                    cs += __bfloat162float(x0) + __bfloat162float(x1);
-                    w[e] = (uint32_t)__bfloat16_as_ushort(x0) | ((uint32_t)__bfloat16_as_ushort(x1) << 16);
-                }
-                if (full) {
-                    *reinterpret_cast<uint4*>(gt + r8) = make_uint4(w[0], w[1], w[2], w[3]);
-                } else {
-#pragma unroll
-                    for (int e = 0; e < 8; ++e)
-                        if (m0 + rh + r8 + e < a.n)
-                            gt[r8 + e] = __ushort_as_bfloat16((unsigned short)(w[e >> 1] >> (16 * (e & 1))));
-                }
-            }
-            atomicAdd(&a.db4[c * kOutChunk + kc], cs);
-        }
-        wait_mma();  // dA3 has read sG and sWT
-        if (ok && cc + 1 < kOutChunks) {  // the next chunk's W4^T columns
-            load_tile_async<128, kOutThreads>(sWT, a.w4t, kOut, 0, kHid, kHid, (c - 1) * kOutChunk, kOut);
-            tc::cp_async_commit();
-        }
+        __syncthreads();  // dA3 read before the next tile's MMAs
     }
     tc::cp_async_wait_all();
     if (!ok && lane == 0) atomicOr(a.status, (uint32_t)WFPG_STATUS_MMA_TIMEOUT);
-
-    // ---- epilogue: d3 = bf16(dA3 o [H3 > 0]) (this thread's 32 of the 64 columns) and its transpose; the KL
-    if (ok) {
-        float v[32];
-        tc::tmem_ld32(lane_base + (uint32_t)(kOutChunk + half * 32), v);
-        if (live) {
-            uint32_t w[16];
 #pragma unroll
-            for (int h = 0; h < 16; ++h) {
-                bf16 x[2];
-#pragma unroll
-                for (int k = 0; k < 2; ++k) {
-                    const int j = half * 32 + 2 * h + k;
-                    const float hv = __bfloat162float(*reinterpret_cast<const bf16*>(sH + cm_off<64>(r, j)));
-                    x[k] = __float2bfloat16_rn(hv > 0.0f ? v[2 * h + k] : 0.0f);
-                    a.d3t[(size_t)j * a.ldg + row] = x[k];
-                }
-                w[h] = (uint32_t)__bfloat16_as_ushort(x[0]) | ((uint32_t)__bfloat16_as_ushort(x[1]) << 16);
-            }
-            uint4* dp = reinterpret_cast<uint4*>(a.d3 + (size_t)row * kHid + half * 32);
-#pragma unroll
-            for (int q = 0; q < 4; ++q) dp[q] = make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) kl += __shfl_xor_sync(0xffffffffu, kl, o);
-        if (lane == 0) atomicAdd(a.loss, kl * a.inv_n);
-    }
+    for (int o = 16; o > 0; o >>= 1) kl += __shfl_xor_sync(0xffffffffu, kl, o);
+    if (lane == 0 && kl != 0.0f) atomicAdd(a.loss, kl * a.inv_n);
     tc::fence_before_sync();
     __syncthreads();
     if (warp == 0) tc::tmem_dealloc(tmem, kOutTmemCols);
@@ -1090,7 +1124,10 @@ int guide_learned_train_step(wfpg_mlp* s, const float* pos, const float* nrm, ui
         oa.db4 = s->grad + kOffB4;
         oa.loss = s->loss;
         oa.status = s->status;
-        WFPG_LAUNCH(k_out_train, div_up(n, 128), kOutThreads, kOutSmemBytes, st, oa);
+        int sms = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        WFPG_LAUNCH(k_out_train, std::min<uint32_t>(div_up(n, 128), (uint32_t)std::max(sms, 1)), kOutThreads,
+                    kOutSmemBytes, st, oa);
     }
     // dW4 = G4^T H3 (split-K over the batch)
     GemmArgs g = gargs(s->g4t, mp, s->h3t, mp, kOut, kHid, N, s->status);

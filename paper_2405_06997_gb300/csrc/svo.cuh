@@ -27,6 +27,11 @@ struct wfpg_svo {
     uint32_t* top = nullptr;
     int top_levels = 0;
     uint32_t top_off[8] = {0};
+    // occupancy bitmaps of the levels top_levels .. D (only when D <= kOccMaxDepth): level
+    // l's bit k is set iff the node of Morton key k exists at level l; words of level l
+    // start at occ_off[l]
+    uint32_t* occ = nullptr;
+    uint64_t occ_off[WFPG_MAX_DEPTH + 2] = {0};
     uint32_t* frag_off = nullptr;             // leaves + 1
     uint32_t* frag_prim = nullptr;            // n_frags
     // radiant exitance, two sides per node

@@ -521,9 +521,18 @@ __global__ void k_top_level(const Node* __restrict__ node, int l, uint32_t* __re
     out[i] = ((uint32_t)L << 28) | nd;
 }
 
+// Occupancy bitmap of one level: the bit of each existing node's Morton key
+__global__ void k_occ_level(const uint64_t* __restrict__ key, uint32_t first, uint32_t count,
+                            uint32_t* __restrict__ bits) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const uint64_t k = key[first + i];
+    atomicOr(&bits[k >> 5], 1u << (uint32_t)(k & 31u));
+}
+
 void svo_free_arrays(wfpg_svo* s) {
     void* ptrs[] = {s->node, s->parent, s->key, s->leaf_count, s->normal, s->route, s->frag_off, s->frag_prim,
-                    s->acc_sum, s->acc_cnt, s->tot_sum, s->tot_cnt, s->value, s->status, s->top};
+                    s->acc_sum, s->acc_cnt, s->tot_sum, s->tot_cnt, s->value, s->status, s->top, s->occ};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -685,6 +694,17 @@ int build_svo(const wfpg_scene* scene, int D, cudaStream_t st, wfpg_svo* s, std:
         for (int l = 0; l <= G; ++l)
             WFPG_LAUNCH(k_top_level, div_up((size_t)1 << (3 * l), T), T, 0, st, s->node, l, s->top + s->top_off[l]);
         s->top_levels = G + 1;
+        // occupancy bitmaps of the levels below the index (levels > 6 hold 8^l >= 2^21 bits)
+        if (D > G && D <= kOccMaxDepth) {
+            const uint64_t words = occ_offset(G, D + 1);
+            WFPG_ALLOC(s->occ, sizeof(uint32_t) * words);
+            WFPG_TRY(cudaMemsetAsync(s->occ, 0, sizeof(uint32_t) * words, st));
+            for (int l = G + 1; l <= D; ++l) {
+                s->occ_off[l] = occ_offset(G, l);
+                const uint32_t cnt = s->level_off[l + 1] - s->level_off[l];
+                WFPG_LAUNCH(k_occ_level, div_up(cnt, T), T, 0, st, s->key, s->level_off[l], cnt, s->occ + s->occ_off[l]);
+            }
+        }
     }
     // 9. exitance arrays, zeroed
     WFPG_ALLOC(s->acc_sum, 16 * (size_t)nn);
