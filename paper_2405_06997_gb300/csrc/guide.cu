@@ -912,6 +912,188 @@ __global__ void __launch_bounds__(kGuideThreads, 1024 / kGuideThreads)
     }
 }
 
+// Unfused fields over a flat SVO index: the cone rays of every bin as one
+// stream.  Each warp takes batches of 32 cells of one bin from a counter over
+// all bins, sets up their rays, and hands a ray to each lane as it frees; a
+// lane keeps its ray's own origin, so lanes of a warp may march rays of
+// different bins.  No barrier holds a warp back at the end of a bin.  eps + L
+// of each cell goes to the bin's pdf row (leaf hits through the warp's queue);
+// k_field_pdf then blurs the rows and builds the PDF and CDFs in place.
+template <int kGuideThreads>
+__global__ void __launch_bounds__(kGuideThreads, 1024 / kGuideThreads)
+    k_guide_stream(TraceArgs T, GuideArgs G, const float* __restrict__ pos, const uint32_t* __restrict__ origin_ray,
+                   const uint32_t* __restrict__ n_bins_dev, uint32_t bin_cap, float* __restrict__ raw,
+                   uint32_t* status, uint32_t* __restrict__ batch_next) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t lt = (1u << lane) - 1u;
+    float* wb = reinterpret_cast<float*>(smem) + warp * (kWbWords * 32);
+    uint32_t* hq = reinterpret_cast<uint32_t*>(reinterpret_cast<float*>(smem) + (kGuideThreads / 32) * kWbWords * 32) +
+                   warp * (kHitQueue * kHitWords);
+    const int N = G.N, NN = N * N, D = T.D;
+    const uint32_t nb = n_bins_dev ? min(*n_bins_dev, bin_cap) : bin_cap;
+    const uint32_t per_bin = (uint32_t)NN / 32u;
+    const uint32_t n_batches = nb * per_bin;
+    const float tn = __fdiv_rn(2.0f, (float)N);
+    const int res = 1 << D;
+    const float fres = (float)res;
+    const float INF = __int_as_float(0x7f800000);
+    const int cap = 3 * res + 16;
+    const uint64_t jseed = purpose(G.seed, kJitterPurpose);
+    const uint32_t frame = G.frame_dev ? *G.frame_dev : G.frame;
+    int q = -1;  // global cell index b N^2 + c of this lane's ray (-1: none)
+    float dx = 0.f, dy = 0.f, dz = 0.f, ivx = 0.f, ivy = 0.f, ivz = 0.f, t = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
+    int cx = 0, cy = 0, cz = 0, level = -1, steps = 0;
+    float bgx = 0.f, bgy = 0.f, bgz = 0.f;  // origin (grid units) of the warp's current batch
+    int wb_n = 0, wb_head = 0;
+    bool dry = false, pend = false;
+    int hq_n = 0;
+    for (;;) {
+        // hits of the last pass join the warp's queue (finished together when it would overflow)
+        const uint32_t hm = __ballot_sync(0xffffffffu, pend);
+        if (hm) {
+            if (hq_n + __popc(hm) > kHitQueue) {
+                flush_hits(T, G, nullptr, hq, 0, hq_n, lane, raw);
+                hq_n = 0;
+                __syncwarp();
+            }
+            if (pend) {
+                const int e = hq_n + __popc(hm & lt);
+                hq[0 * kHitQueue + e] = (uint32_t)q;
+                hq[1 * kHitQueue + e] = __float_as_uint(t);
+                hq[2 * kHitQueue + e] = (uint32_t)cx | ((uint32_t)cy << 10) | ((uint32_t)cz << 20);
+                hq[3 * kHitQueue + e] = __float_as_uint(dx);
+                hq[4 * kHitQueue + e] = __float_as_uint(dy);
+                hq[5 * kHitQueue + e] = __float_as_uint(dz);
+                q = -1;
+                pend = false;
+            }
+            hq_n += __popc(hm);
+            __syncwarp();
+        }
+        const bool idle = q < 0;
+        const uint32_t need = __ballot_sync(0xffffffffu, idle);
+        if (need && wb_head == wb_n && !dry) {
+            // the next batch of 32 cells of some bin: origin, then every lane sets up one ray
+            uint32_t batch = 0;
+            if (lane == 0) batch = atomicAdd(batch_next, 1u);
+            batch = __shfl_sync(0xffffffffu, batch, 0);
+            if (batch >= n_batches) {
+                dry = true;
+                wb_n = wb_head = 0;
+            } else {
+                const uint32_t b = batch / per_bin;
+                const int c = (int)(batch % per_bin) * 32 + lane;
+                const uint32_t r = origin_ray ? origin_ray[b] : b;
+                float ox = 0.0f, oy = 0.0f, oz = 0.0f;
+                if (r != kNone) {
+                    ox = pos[3 * (size_t)r + 0];
+                    oy = pos[3 * (size_t)r + 1];
+                    oz = pos[3 * (size_t)r + 2];
+                }
+                bgx = __fmul_rn(__fsub_rn(ox, T.lo[0]), T.scale);
+                bgy = __fmul_rn(__fsub_rn(oy, T.lo[1]), T.scale);
+                bgz = __fmul_rn(__fsub_rn(oz, T.lo[2]), T.scale);
+                const bool inside = bgx >= 0.0f && bgx <= fres && bgy >= 0.0f && bgy <= fres && bgz >= 0.0f &&
+                                    bgz <= fres;
+                float3 d, iv;
+                cell_ray(T, G, c, jseed, bin_stream(frame, b), tn, &d, &iv);
+                float t0;
+                int x0, y0, z0;
+                const bool alive = ray_start(T, r != kNone, inside, bgx, bgy, bgz, d.x, d.y, d.z, iv.x, iv.y, iv.z,
+                                             res, fres, &t0, &x0, &y0, &z0);
+                const int g = (int)b * NN + c;
+                if (!alive) raw[g] = __fadd_rn(G.eps, 0.0f);
+                wb[0 * 32 + lane] = __int_as_float(alive ? g : -1);
+                wb[1 * 32 + lane] = d.x;
+                wb[2 * 32 + lane] = d.y;
+                wb[3 * 32 + lane] = d.z;
+                wb[4 * 32 + lane] = iv.x;
+                wb[5 * 32 + lane] = iv.y;
+                wb[6 * 32 + lane] = iv.z;
+                wb[7 * 32 + lane] = t0;
+                wb[8 * 32 + lane] = __int_as_float(x0);
+                wb[9 * 32 + lane] = __int_as_float(y0);
+                wb[10 * 32 + lane] = __int_as_float(z0);
+                wb_n = 32;
+                wb_head = 0;
+            }
+            __syncwarp();
+        }
+        if (need && wb_head < wb_n) {
+            const int k = wb_head + __popc(need & lt);
+            if (idle && k < wb_n) {
+                q = __float_as_int(wb[0 * 32 + k]);  // -1: the ray died at its start
+                dx = wb[1 * 32 + k];
+                dy = wb[2 * 32 + k];
+                dz = wb[3 * 32 + k];
+                ivx = wb[4 * 32 + k];
+                ivy = wb[5 * 32 + k];
+                ivz = wb[6 * 32 + k];
+                t = wb[7 * 32 + k];
+                cx = __float_as_int(wb[8 * 32 + k]);
+                cy = __float_as_int(wb[9 * 32 + k]);
+                cz = __float_as_int(wb[10 * 32 + k]);
+                gx = bgx;
+                gy = bgy;
+                gz = bgz;
+                level = -1;
+                steps = 0;
+            }
+            wb_head = min(wb_n, wb_head + __popc(need));
+            __syncwarp();  // entries are read before a refill overwrites them
+        }
+        if (dry && __all_sync(0xffffffffu, q < 0)) {
+            if (hq_n > 0) flush_hits(T, G, nullptr, hq, 0, hq_n, lane, raw);
+            break;
+        }
+        if (q < 0) continue;
+        // ---- one step: the cell's deepest existing level, then its hit or the skip of its empty block
+        if (level < 0) level = deepest_level(T, cx, cy, cz);
+        bool done = false;
+        if (level == D && t >= T.t_skip) {
+            pend = true;  // its cone query waits in the warp's queue
+        } else {
+            const int sl = (level == D) ? 0 : D - level - 1;
+            const int size = 1 << sl;
+            const int bx = (cx >> sl) << sl, by = (cy >> sl) << sl, bz = (cz >> sl) << sl;
+            const int ex = ivx > 0.0f ? bx + size : bx - 1;
+            const int ey = ivy > 0.0f ? by + size : by - 1;
+            const int ez = ivz > 0.0f ? bz + size : bz - 1;
+            const float tex = ivx != 0.0f ? cross_time(ex, ivx > 0.0f, gx, ivx) : INF;
+            const float tey = ivy != 0.0f ? cross_time(ey, ivy > 0.0f, gy, ivy) : INF;
+            const float tez = ivz != 0.0f ? cross_time(ez, ivz > 0.0f, gz, ivz) : INF;
+            const int a = (tex <= tey && tex <= tez) ? 0 : (tey <= tez ? 1 : 2);
+            const float tx = a == 0 ? tex : (a == 1 ? tey : tez);
+            const int p = a == 0 ? 1 : 0, pq = a == 2 ? 1 : 2;
+            const int cp = p == 0 ? cx : cy, cq = pq == 1 ? cy : cz;
+            const int bp = p == 0 ? bx : by, bq = pq == 1 ? by : bz;
+            const float gp = p == 0 ? gx : gy, gq = pq == 1 ? gy : gz;
+            const float ip = p == 0 ? ivx : ivy, iq = pq == 1 ? ivy : ivz;
+            const float dp = p == 0 ? dx : dy, dq = pq == 1 ? dy : dz;
+            const int np = advance_axis(cp, bp, size, gp, ip, __fmul_rn(dp, T.scale), tx, p < a);
+            const int nq = advance_axis(cq, bq, size, gq, iq, __fmul_rn(dq, T.scale), tx, pq < a);
+            const int na = a == 0 ? ex : (a == 1 ? ey : ez);
+            if (tx == INF || na < 0 || na >= res) {
+                done = true;  // left the grid: miss
+            } else if (++steps > cap) {
+                atomicOr(status, (uint32_t)WFPG_STATUS_TRACE_CAP);
+                done = true;
+            } else {
+                cx = a == 0 ? na : np;
+                cy = a == 1 ? na : (p == 1 ? np : nq);
+                cz = a == 2 ? na : nq;
+                t = tx;
+                level = -1;
+            }
+        }
+        if (done) {
+            raw[q] = __fadd_rn(G.eps, 0.0f);
+            q = -1;
+        }
+    }
+}
+
 // PDF and CDFs of given fields (one CTA per bin): optionally the blur, then row
 // CDFs and the marginal in warp order with a running maximum, pdf = f N^2 /
 // (T 4 pi), as in the traced path.  The field may be the pdf rows themselves
@@ -1194,6 +1376,28 @@ int field_pdf_impl(const float* field, int N, const uint32_t* n_bins_dev, uint32
                    float* cdf_row, float* cdf_marg, cudaStream_t st, int blur);
 
 template <int kThreads>
+static int launch_stream(const wfpg_svo* s, const TraceArgs& T0, const GuideArgs& G, const float* pos,
+                         const uint32_t* origin_ray, const uint32_t* n_bins_dev, uint32_t bin_cap, float* pdf,
+                         float* cdf_row, float* cdf_marg, cudaStream_t st) {
+    TraceArgs T = T0;
+    T.smem_nodes = 0;  // no node cache: the flat walk reads nodes only below the index
+    auto kernel = k_guide_stream<kThreads>;
+    const size_t smem = sizeof(float) * (size_t)(kThreads / 32) * kWbWords * 32 +
+                        sizeof(uint32_t) * (size_t)(kThreads / 32) * kHitQueue * kHitWords;
+    int rc = WFPG_OK;
+    const uint64_t slots = guide_slots(kernel, kThreads, smem, &rc);
+    if (rc != WFPG_OK) return rc;
+    const uint64_t warps_needed = ((uint64_t)bin_cap * (uint64_t)(G.N * G.N) / 32 + kThreads / 32 - 1) / (kThreads / 32);
+    const uint32_t grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(warps_needed, slots));
+    if (cudaMemsetAsync(s->bin_next, 0, sizeof(uint32_t), st) != cudaSuccess) return WFPG_ERR_CUDA;
+    WFPG_LAUNCH(kernel, grid, kThreads, smem, st, T, G, pos, origin_ray, n_bins_dev, bin_cap, pdf, s->status,
+                s->bin_next);
+    rc = launch_status();
+    if (rc != WFPG_OK) return rc;
+    return field_pdf_impl(pdf, G.N, n_bins_dev, bin_cap, pdf, cdf_row, cdf_marg, st, G.blur);
+}
+
+template <int kThreads>
 static int launch_march(const wfpg_svo* s, const TraceArgs& T, const GuideArgs& G, const float* pos,
                         const uint32_t* origin_ray, const uint32_t* n_bins_dev, uint32_t bin_cap, float* pdf,
                         float* cdf_row, float* cdf_marg, cudaStream_t st) {
@@ -1221,6 +1425,13 @@ int guide_build_impl(const wfpg_svo* s, const float* pos, const uint32_t* origin
     TraceArgs T;
     GuideArgs G;
     trace_setup(s, p, &T, &G, frame_dev);
+    if (T.flat && p->parts == 0) {  // flat index: every bin's cone rays as one stream, then the per-bin finish
+        const int threads = p->block ? p->block : kGuideDefaultThreadsMid;
+        if (threads == 64) return launch_stream<64>(s, T, G, pos, origin_ray, n_bins_dev, bin_cap, pdf, cdf_row, cdf_marg, st);
+        if (threads == 128) return launch_stream<128>(s, T, G, pos, origin_ray, n_bins_dev, bin_cap, pdf, cdf_row, cdf_marg, st);
+        if (threads == 256) return launch_stream<256>(s, T, G, pos, origin_ray, n_bins_dev, bin_cap, pdf, cdf_row, cdf_marg, st);
+        return WFPG_ERR_INVALID_ARG;
+    }
     if (p->N >= 64 && p->parts == 0) {  // large fields: the march, then the per-bin finish
         const int threads = p->block ? p->block : kGuideDefaultThreadsMid;
         if (threads == 64) return launch_march<64>(s, T, G, pos, origin_ray, n_bins_dev, bin_cap, pdf, cdf_row, cdf_marg, st);
