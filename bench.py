@@ -692,7 +692,7 @@ def run_gpu(args, world, rank, local):
                        "calls": "the timed step's five calls captured once into a CUDA graph and replayed "
                                 "(same work; the captured frame index keys the random streams)"},
         "stages": stage_rooflines(stage_ms, alg["bytes"], R, n_rec, svo.n_nodes, peak),
-        "roofline": {"kernel": "k_guide_build", "bound": "hbm", "achieved": achieved, "peak": peak,
+        "roofline": {"kernel": "k_guide_stream + k_field_pdf (guide_build_pdf)", "bound": "hbm", "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                      "peak_kind": peak_kind, "algorithmic_bytes": alg["bytes"],
                      "algorithmic_model": alg["model"], "ncu": issue,
@@ -701,11 +701,11 @@ def run_gpu(args, world, rank, local):
                              "l2_roofline, dram_roofline and issue_roofline say what bounds the kernel"},
         "issue_roofline": issue_roofline(issue, gms, clk.get("sm_mhz") if clk else None,
                                          torch.cuda.get_device_properties(dev).multi_processor_count),
-        "l2_roofline": {"kernel": "k_guide_build", "bound": "l2", "achieved": achieved, "peak": l2_peak,
+        "l2_roofline": {"kernel": "k_guide_stream + k_field_pdf (guide_build_pdf)", "bound": "l2", "achieved": achieved, "peak": l2_peak,
                         "unit": "GB/s", "frac": achieved / l2_peak, "peak_kind": l2_how,
                         "note": "the same algorithmic bytes against the L2 read bandwidth measured here: the "
                                 "walk's node records are served from L1/L2"},
-        "dram_roofline": ({"kernel": "k_guide_build", "bound": "hbm", "achieved": traffic / (gms / 1e3) / 1e9,
+        "dram_roofline": ({"kernel": "k_guide_stream", "bound": "hbm", "achieved": traffic / (gms / 1e3) / 1e9,
                            "peak": peak, "unit": "GB/s", "frac": traffic / (gms / 1e3) / 1e9 / peak,
                            "note": "DRAM bytes per launch (ncu, committed capture of this source) over the "
                                    "live kernel time"} if traffic else None),
@@ -1045,7 +1045,7 @@ def large_field_records(w, svo, inp, binout, B, peak, l2_peak, flush, reps=10):
                         "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
                                      "l2_peak": l2_peak, "l2_frac": ach / l2_peak, "algorithmic_bytes": alg["bytes"],
                                      "algorithmic_model": alg["model"]},
-                        "kernels": "k_guide_march (cone march, (bin, 1024-cell) units) + k_field_pdf (blur, CDFs, PDF)"}
+                        "kernels": "k_guide_stream (cone rays of every bin as 32-cell batches) + k_field_pdf (blur, CDFs, PDF)"}
     return out
 
 
@@ -1107,10 +1107,11 @@ def issue_roofline(counters, kernel_ms, sm_mhz, n_sm, schedulers=4):
 
 
 def read_profile_traffic():
-    """DRAM bytes per launch of k_guide_build (and its issue counters) from the
-    committed ncu summary -- only while the kernel source is the one captured."""
+    """DRAM bytes per launch of the field kernel (k_guide_stream) and its issue
+    counters from the committed ncu summary -- only while the kernel source is
+    the one captured."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", "k_guide_build_frame1080p.json")
+    path = os.path.join(ROOT, "profiles", "k_guide_stream_frame1080p.json")
     if not os.path.exists(path):
         return None, None
     with open(path) as f:

@@ -15,7 +15,7 @@ import bench  # noqa: E402
 
 def test_profile_counters_belong_to_the_current_source():
     traffic, counters = bench.read_profile_traffic()
-    d = json.load(open(os.path.join(ROOT, "profiles", "k_guide_build_frame1080p.json")))
+    d = json.load(open(os.path.join(ROOT, "profiles", "k_guide_stream_frame1080p.json")))
     if traffic is None:
         pytest.skip("the field kernel changed since the capture: its counters are withheld")
     assert traffic == d["dram_bytes_per_launch"]
@@ -25,13 +25,13 @@ def test_profile_counters_belong_to_the_current_source():
 def test_profile_counters_are_withheld_for_another_source(tmp_path, monkeypatch):
     prof = tmp_path / "profiles"
     prof.mkdir()
-    d = json.load(open(os.path.join(ROOT, "profiles", "k_guide_build_frame1080p.json")))
+    d = json.load(open(os.path.join(ROOT, "profiles", "k_guide_stream_frame1080p.json")))
     src = tmp_path / d["source"]
     src.parent.mkdir(parents=True)
     shutil.copy(os.path.join(ROOT, d["source"]), src)
     with open(src, "a") as f:
         f.write("\n// edited\n")
-    (prof / "k_guide_build_frame1080p.json").write_text(json.dumps(d))
+    (prof / "k_guide_stream_frame1080p.json").write_text(json.dumps(d))
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     assert bench.read_profile_traffic() == (None, None)
 
