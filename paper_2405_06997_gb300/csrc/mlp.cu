@@ -37,6 +37,8 @@ using namespace wfpg;
 namespace {
 
 constexpr int kIn = 80, kHid = 64, kOut = 1024;
+constexpr int kFeatIn = 78;  // input features (the rest of the 80 columns is padding)
+constexpr int kTRows = 80;   // rows of the transposed activations: 64 (or 78 + 2) values, a row of ones, zeros
 constexpr size_t kOffW1 = 0, kOffB1 = kOffW1 + kHid * kIn, kOffW2 = kOffB1 + kHid, kOffB2 = kOffW2 + kHid * kHid,
                  kOffW3 = kOffB2 + kHid, kOffB3 = kOffW3 + kHid * kHid, kOffW4 = kOffB3 + kHid,
                  kOffB4 = kOffW4 + (size_t)kOut * kHid, kParams = kOffB4 + kOut;
@@ -353,7 +355,7 @@ __global__ void k_mlp_features(const float* __restrict__ pos, const float* __res
     }
     if (XT) {  // transposed copy: consecutive threads write consecutive rows of XT
 #pragma unroll
-        for (int k = 0; k < kIn; ++k) XT[(size_t)k * ldxt + i] = __float2bfloat16_rn(f[k]);
+        for (int k = 0; k < kIn; ++k) XT[(size_t)k * ldxt + i] = __float2bfloat16_rn(k == kFeatIn ? 1.0f : f[k]);
     }
 }
 
@@ -415,11 +417,13 @@ __global__ void k_softmax_rows(const float* __restrict__ Z, uint32_t rows, const
 }
 
 
-// out[i] = sum over the splits of part[z][i] (split-K weight gradients): a
-// block covers 32 outputs, its 8 warps take every 8th split, then the 8
-// partial sums are added in warp order (deterministic)
-__global__ void __launch_bounds__(256) k_sum_splits(const float* __restrict__ part, int splits, uint32_t mn,
-                                                    float* __restrict__ out) {
+// The sum over the K splits of a [M][ncols] weight-and-bias gradient (a block
+// covers 32 outputs, its 8 warps take every 8th split, the 8 partial sums are
+// added in warp order: deterministic): column c < wcols of row m goes to
+// out_w[m * ldw + c], column bias_col to out_b[m], the rest is dropped
+__global__ void __launch_bounds__(256) k_sum_splits_wb(const float* __restrict__ part, int splits, uint32_t mn,
+                                                       int ncols, float* __restrict__ out_w, int ldw, int wcols,
+                                                       float* __restrict__ out_b, int bias_col) {
     __shared__ float red[8][32];
     const uint32_t i = blockIdx.x * 32 + threadIdx.x;
     float acc = 0.0f;
@@ -431,63 +435,38 @@ __global__ void __launch_bounds__(256) k_sum_splits(const float* __restrict__ pa
         float sum = 0.0f;
 #pragma unroll
         for (int y = 0; y < 8; ++y) sum += red[y][threadIdx.x];
-        out[i] = sum;
+        const uint32_t m = i / (uint32_t)ncols, c = i % (uint32_t)ncols;
+        if ((int)c < wcols) out_w[(size_t)m * ldw + c] = sum;
+        else if ((int)c == bias_col) out_b[m] = sum;
     }
 }
 
-// out[r] += sum over k < n of AT[r][k] for a bf16 matrix stored transposed
-// (rows = features, k = batch): blockIdx.y = row, blockIdx.x = a stretch of
-// 8192 k, coalesced 4-byte reads, one atomic per block (out zeroed before)
-__global__ void __launch_bounds__(256) k_rowsum(const bf16* __restrict__ AT, int n, int ld, float* __restrict__ out) {
-    __shared__ float red[256];
-    const bf16* a = AT + (size_t)blockIdx.y * ld;
-    const int k0 = blockIdx.x * 8192, k1 = min(n, k0 + 8192);
-    float acc = 0.0f;
-    for (int k = k0 + 2 * (int)threadIdx.x; k < k1; k += 512) {
-        if (k + 1 < k1 && (ld & 1) == 0) {
-            const __nv_bfloat162 v = *reinterpret_cast<const __nv_bfloat162*>(a + k);
-            acc += __bfloat162float(v.x) + __bfloat162float(v.y);
-        } else {
-            acc += __bfloat162float(a[k]);
-            if (k + 1 < k1) acc += __bfloat162float(a[k + 1]);
-        }
-    }
-    red[threadIdx.x] = acc;
-    __syncthreads();
-    for (int o = 128; o > 0; o >>= 1) {
-        if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) atomicAdd(&out[blockIdx.y], red[0]);
+// out[i] = v for i < n (bfloat16)
+__global__ void k_fill_bf16(bf16* __restrict__ out, uint32_t n, float v) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = __float2bfloat16_rn(v);
 }
 
 // ---------------------------------------------------------------------------
-// The output layer of a training step, fused: for each 128-row tile, the
-// logits Z = H3 W4^T + b4 (1024 per row) are computed chunk by chunk on the
-// tensor cores into tensor memory and never stored.  Pass 1 keeps each row's
-// running maximum and exponential sum and sums its target row; pass 2
-// recomputes each chunk, forms the logit gradient
-// G = bf16((softmax(Z) - q / sum q) / n) and the KL term, writes G^T (for the
-// weight gradient dW4 = G^T H3, a separate split-K GEMM) and the column sums
-// of G (db4), and accumulates dA3 = G W4 in tensor memory with a second MMA
+// The output layer of a training step, fused: for one 128-row tile, the logits
+// Z = H3 W4^T + b4 (1024 per row) are computed 64 at a time on the tensor
+// cores into tensor memory and never stored.  Pass 1 keeps each row's running
+// maximum and exponential sum and sums its target row; pass 2 recomputes each
+// chunk, forms the logit gradient G = bf16((softmax(Z) - q / sum q) / n) and
+// the KL term, stores G^T (the weight-gradient GEMM dW4 = G^T [H3 | 1] gives
+// dW4 and db4) and accumulates dA3 = G W4 in tensor memory with a second MMA
 // per chunk.  The epilogue writes d3 = bf16(dA3 o [H3 > 0]) and its transpose.
-//
-// One CTA per SM, persistent over tiles, 512 threads: warp w reads TMEM lanes
-// 32 (w % 4) .. + 31 (the tile's rows) and handles columns 32 (w / 4) .. + 31
-// of each 128-logit chunk.  The logits of chunk c + 1 are computed into the
-// second of two TMEM buffers while chunk c is processed; W4 rows, W4^T
-// columns and the target chunk (staged with a padded row stride, so that each
-// thread reads its own row without bank conflicts) are copied in by cp.async
-// ahead of their use.
-constexpr int kOutThreads = 512;
-constexpr int kOutChunk = 128;                 // logits per chunk
-constexpr int kOutChunks = kOut / kOutChunk;   // 8
-constexpr uint32_t kOutTmemCols = 512;         // Z buffers at columns 0 and 128, dA3 at 256
-constexpr int kOutTLd = kOutChunk + 4;         // staged target row stride (floats)
-constexpr int kOutSmemH = 0, kOutSmemW = 16384, kOutSmemWT = kOutSmemW + 2 * 16384, kOutSmemG = kOutSmemWT + 16384,
-              kOutSmemT = kOutSmemG + 32768, kOutSmemB = kOutSmemT + 128 * kOutTLd * 4,
+// 256 threads, four CTAs per SM (128 TMEM columns each): warp w reads TMEM
+// lanes 32 (w % 4) .. + 31 (the tile's rows) and handles columns 32 (w / 4)
+// .. + 31 of each chunk.  W4 rows and W4^T columns of the next chunk are
+// copied in (cp.async) while the current one is processed.
+constexpr int kOutThreads = 256;
+constexpr int kOutChunk = 64;                  // logits per chunk
+constexpr int kOutChunks = kOut / kOutChunk;   // 16
+constexpr uint32_t kOutTmemCols = 128;         // Z chunk at column 0, dA3 at column 64
+constexpr int kOutSmemH = 0, kOutSmemW = 16384, kOutSmemWT = 24576, kOutSmemG = 32768, kOutSmemB = 49152,
               kOutSmemStat = kOutSmemB + 4 * kOut;
-constexpr int kOutSmemBytes = kOutSmemStat + 3 * 4 * 128 * 4;
+constexpr int kOutSmemBytes = kOutSmemStat + 3 * 2 * 128 * 4;
 
 struct OutTrainArgs {
     const bf16* h3;      // [n][64]
@@ -501,7 +480,6 @@ struct OutTrainArgs {
     int ldg;
     bf16* d3;            // [n][64]
     bf16* d3t;           // [64][ldg]
-    float* db4;          // [1024], accumulated (zeroed before the launch)
     float* loss;         // accumulated mean KL
     uint32_t* status;
 };
@@ -512,60 +490,54 @@ __device__ __forceinline__ int cm_off(int r, int k) {
     return (r >> 3) * (KC * 16) + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2;
 }
 
-// target rows [m0, m0 + 128) x columns [c0, c0 + 128) into the staging buffer
-// (row stride kOutTLd floats); rows past n are not read
-__device__ __forceinline__ void stage_target(float* sT, const float* target, int n, int m0, int c0) {
-    for (int idx = threadIdx.x; idx < 128 * (kOutChunk / 4); idx += kOutThreads) {
-        const int r = idx >> 5, c4 = idx & 31;
-        const bool valid = m0 + r < n;
-        tc::cp_async16(sT + r * kOutTLd + 4 * c4, valid ? target + (size_t)(m0 + r) * kOut + c0 + 4 * c4 : target,
-                       valid);
-    }
-}
-
-__global__ void __launch_bounds__(kOutThreads, 1) k_out_train(OutTrainArgs a) {
+__global__ void __launch_bounds__(kOutThreads, 4) k_out_train(OutTrainArgs a) {
     extern __shared__ __align__(1024) uint8_t out_smem[];
     uint8_t* sH = out_smem + kOutSmemH;    // H3 tile: 128 x 64 (K = 64)
-    uint8_t* sW0 = out_smem + kOutSmemW;   // W4 rows of a chunk: 128 x 64 (K = 64), two buffers
-    uint8_t* sWT = out_smem + kOutSmemWT;  // W4^T columns of a chunk: 64 x 128 (K = 128)
-    uint8_t* sG = out_smem + kOutSmemG;    // G of the chunk: 128 x 128 (K = 128)
-    float* sT = reinterpret_cast<float*>(out_smem + kOutSmemT);
+    uint8_t* sW = out_smem + kOutSmemW;    // W4 rows of the chunk: 64 x 64 (K = 64)
+    uint8_t* sWT = out_smem + kOutSmemWT;  // W4^T columns of the chunk: 64 x 64 (K = 64)
+    uint8_t* sG = out_smem + kOutSmemG;    // G of the chunk: 128 x 64 (K = 64)
     float* sb = reinterpret_cast<float*>(out_smem + kOutSmemB);
-    float* s_max = reinterpret_cast<float*>(out_smem + kOutSmemStat);  // [4 column groups][128 rows]
-    float* s_sum = s_max + 512;
-    float* s_tsum = s_sum + 512;
-    __shared__ __align__(8) uint64_t mbar[3];  // 0, 1: Z buffers; 2: dA3
+    float* s_max = reinterpret_cast<float*>(out_smem + kOutSmemStat);  // [2 column halves][128 rows]
+    float* s_sum = s_max + 256;
+    float* s_tsum = s_sum + 256;
+    __shared__ __align__(8) uint64_t mbar[2];  // 0: Z, 1: dA3
     __shared__ uint32_t tmem_base;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int quad = warp & 3, cg = warp >> 2;
+    const int quad = warp & 3, half = warp >> 2;
     const int r = quad * 32 + lane;  // tile row of this thread
-    const int k0 = cg * 32;          // first chunk column of this thread
+    const int m0 = blockIdx.x * 128, row = m0 + r;
+    const bool live = row < a.n;
+    const int k0 = half * 32;        // first chunk column of this thread
     if (warp == 0) tc::tmem_alloc(&tmem_base, kOutTmemCols);
     if (tid == 0) {
-        for (int i = 0; i < 3; ++i) tc::mbar_init(&mbar[i], 1);
+        tc::mbar_init(&mbar[0], 1);
+        tc::mbar_init(&mbar[1], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    load_tile_async<64, kOutThreads>(sH, a.h3, kHid, m0, 128, a.n, 0, kHid);
+    load_tile_async<64, kOutThreads>(sW, a.w4, kHid, 0, kOutChunk, kOut, 0, kHid);
+    tc::cp_async_commit();
     for (int i = tid; i < kOut; i += kOutThreads) sb[i] = a.b4[i];
+    tc::cp_async_wait_all();
+    tc::fence_proxy_async();
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = tmem_base;
     const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16);
-    constexpr uint32_t idesc_z = tc::idesc_bf16_f32(128, kOutChunk);
-    constexpr uint32_t idesc_d = tc::idesc_bf16_f32(128, kHid);
+    constexpr uint32_t idesc = tc::idesc_bf16_f32(128, 64);  // both MMAs: M = 128, N = 64
+    const float* trow = a.target + (size_t)row * kOut;
     uint32_t phase = 0;  // bit i: parity of mbar[i]'s next phase
     bool ok = true;
-    auto sW = [&](int buf) { return sW0 + buf * 16384; };
-    // Z of the chunk whose W4 rows are in buffer `buf` -> TMEM columns 128 buf, 4 MMAs (K = 64)
-    auto issue_z = [&](int buf) {
+    auto mma64 = [&](uint32_t d, const uint8_t* A, const uint8_t* B, int bar, bool acc) {
         if (tid == 0) {
             tc::fence_after_sync();
-            const uint32_t a0 = tc::smem_addr(sH), b0 = tc::smem_addr(sW(buf));
+            const uint32_t a0 = tc::smem_addr(A), b0 = tc::smem_addr(B);
 #pragma unroll
-            for (int s = 0; s < kHid / 16; ++s)
-                tc::mma_bf16(tmem + (uint32_t)(buf * kOutChunk), tc::smem_desc(a0 + s * 256, 128, 64 * 16),
-                             tc::smem_desc(b0 + s * 256, 128, 64 * 16), idesc_z, s > 0 ? 1u : 0u);
-            tc::mma_commit(&mbar[buf]);
+            for (int s = 0; s < 4; ++s)
+                tc::mma_bf16(d, tc::smem_desc(a0 + s * 256, 128, 64 * 16), tc::smem_desc(b0 + s * 256, 128, 64 * 16),
+                             idesc, (acc || s > 0) ? 1u : 0u);
+            tc::mma_commit(&mbar[bar]);
         }
     };
     auto wait_bar = [&](int i) {
@@ -573,214 +545,159 @@ __global__ void __launch_bounds__(kOutThreads, 1) k_out_train(OutTrainArgs a) {
         phase ^= 1u << i;
         tc::fence_after_sync();
     };
-    float kl = 0.0f;
-    const int n_tiles = (a.n + 127) / 128;
-    for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
-        const int m0 = tile * 128, row = m0 + r;
-        const bool live = row < a.n;
-        // ---- pass 1: running maximum and exponential sum of this thread's columns; target row sums
-        load_tile_async<64, kOutThreads>(sH, a.h3, kHid, m0, 128, a.n, 0, kHid);
-        load_tile_async<64, kOutThreads>(sW(0), a.w4, kHid, 0, kOutChunk, kOut, 0, kHid);
-        load_tile_async<64, kOutThreads>(sW(1), a.w4, kHid, kOutChunk, kOutChunk, kOut, 0, kHid);
-        stage_target(sT, a.target, a.n, m0, 0);
-        tc::cp_async_commit();
-        tc::cp_async_wait_all();
-        tc::fence_proxy_async();
-        __syncthreads();
-        issue_z(0);
-        float mrun = -3.4e38f, srun = 0.0f, tsum = 0.0f;
-        for (int c = 0; c < kOutChunks && ok; ++c) {
-            if (c > 0) {  // target chunk c and the W4 rows of chunk c + 1 have landed
-                tc::cp_async_wait_all();
-                tc::fence_proxy_async();
-                __syncthreads();
+
+    // ---- pass 1: running maximum and exponential sum of this thread's columns; target row sum
+    float mrun = -3.4e38f, srun = 0.0f, tsum = 0.0f;
+    for (int c = 0; c < kOutChunks && ok; ++c) {
+        mma64(tmem, sH, sW, 0, false);
+        if (live) {
+            const float4* tq = reinterpret_cast<const float4*>(trow + c * kOutChunk + k0);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const float4 v = tq[i];
+                tsum += (v.x + v.y) + (v.z + v.w);
             }
-            if (c + 1 < kOutChunks) issue_z((c + 1) & 1);  // overlaps this chunk's processing
-            wait_bar(c & 1);
-            if (!ok) break;
-            float v[32];
-            tc::tmem_ld32(lane_base + (uint32_t)((c & 1) * kOutChunk + k0), v);
+        }
+        wait_bar(0);
+        if (!ok) break;
+        if (c + 1 < kOutChunks) {  // the MMA has read sW: the next chunk's W4 rows
+            load_tile_async<64, kOutThreads>(sW, a.w4, kHid, (c + 1) * kOutChunk, kOutChunk, kOut, 0, kHid);
+            tc::cp_async_commit();
+        }
+#pragma unroll 1
+        for (int g = 0; g < 2; ++g) {
+            float v[16];
+            tc::tmem_ld16(lane_base + (uint32_t)(k0 + g * 16), v);
             float gm = -3.4e38f;
 #pragma unroll
-            for (int i = 0; i < 32; ++i) {
-                v[i] += sb[c * kOutChunk + k0 + i];
+            for (int i = 0; i < 16; ++i) {
+                v[i] += sb[c * kOutChunk + k0 + g * 16 + i];
                 gm = fmaxf(gm, v[i]);
             }
             if (gm > mrun) {
                 srun *= __expf(mrun - gm);
                 mrun = gm;
             }
-            const float* tr = sT + r * kOutTLd + k0;
 #pragma unroll
-            for (int i = 0; i < 32; ++i) srun += __expf(v[i] - mrun);
-#pragma unroll
-            for (int i = 0; i < 32; i += 4) {
-                const float4 t4 = *reinterpret_cast<const float4*>(tr + i);
-                tsum += (t4.x + t4.y) + (t4.z + t4.w);
-            }
-            tc::fence_before_sync();
-            __syncthreads();  // the chunk's TMEM buffer, W4 rows and target stage are free
-            if (c + 1 < kOutChunks) {
-                stage_target(sT, a.target, a.n, m0, (c + 1) * kOutChunk);
-                if (c + 2 < kOutChunks)
-                    load_tile_async<64, kOutThreads>(sW(c & 1), a.w4, kHid, (c + 2) * kOutChunk, kOutChunk, kOut, 0, kHid);
-                tc::cp_async_commit();
-            }
+            for (int i = 0; i < 16; ++i) srun += __expf(v[i] - mrun);
         }
-        // the row's statistics from its four column groups
-        s_max[cg * 128 + r] = mrun;
-        s_sum[cg * 128 + r] = srun;
-        s_tsum[cg * 128 + r] = tsum;
-        __syncthreads();
-        {
-            float mm = s_max[r];
-            for (int g = 1; g < 4; ++g) mm = fmaxf(mm, s_max[g * 128 + r]);
-            float ss = 0.0f, tt = 0.0f;
-            for (int g = 0; g < 4; ++g) {
-                ss += s_sum[g * 128 + r] * __expf(s_max[g * 128 + r] - mm);
-                tt += s_tsum[g * 128 + r];
-            }
-            mrun = mm;
-            srun = ss;
-            tsum = tt;
-        }
-        if (!ok) break;
+        tc::cp_async_wait_all();
+        tc::fence_proxy_async();
+        tc::fence_before_sync();
+        __syncthreads();  // TMEM read; the next W4 rows have landed
+    }
+    s_max[half * 128 + r] = mrun;
+    s_sum[half * 128 + r] = srun;
+    s_tsum[half * 128 + r] = tsum;
+    __syncthreads();
+    {
+        const float ma = s_max[r], mb = s_max[128 + r];
+        mrun = fmaxf(ma, mb);
+        srun = s_sum[r] * __expf(ma - mrun) + s_sum[128 + r] * __expf(mb - mrun);
+        tsum = s_tsum[r] + s_tsum[128 + r];
+    }
+    const float shift = mrun + __logf(srun), inv_t = tsum > 0.0f ? 1.0f / tsum : 0.0f;
+    float kl = 0.0f;
 
-        // ---- pass 2, chunks in reverse (the target rows read last are read again first)
-        const float shift = mrun + __logf(srun), inv_t = tsum > 0.0f ? 1.0f / tsum : 0.0f;
-        __syncthreads();  // statistics read before the buffers are refilled
-        load_tile_async<64, kOutThreads>(sW(0), a.w4, kHid, (kOutChunks - 1) * kOutChunk, kOutChunk, kOut, 0, kHid);
-        load_tile_async<64, kOutThreads>(sW(1), a.w4, kHid, (kOutChunks - 2) * kOutChunk, kOutChunk, kOut, 0, kHid);
-        load_tile_async<128, kOutThreads>(sWT, a.w4t, kOut, 0, kHid, kHid, (kOutChunks - 1) * kOutChunk, kOut);
-        stage_target(sT, a.target, a.n, m0, (kOutChunks - 1) * kOutChunk);
+    // ---- pass 2, chunks in reverse (the target rows read last are read again first)
+    if (ok) {
+        load_tile_async<64, kOutThreads>(sW, a.w4, kHid, (kOutChunks - 1) * kOutChunk, kOutChunk, kOut, 0, kHid);
+        load_tile_async<64, kOutThreads>(sWT, a.w4t, kOut, 0, kHid, kHid, (kOutChunks - 1) * kOutChunk, kOut);
         tc::cp_async_commit();
         tc::cp_async_wait_all();
         tc::fence_proxy_async();
         __syncthreads();
-        issue_z(0);
-        for (int i = 0; i < kOutChunks && ok; ++i) {
-            const int c = kOutChunks - 1 - i, buf = i & 1;
-            if (i > 0) {  // target chunk c, W4^T chunk c and the next W4 rows have landed
-                tc::cp_async_wait_all();
-                tc::fence_proxy_async();
-                __syncthreads();
-            }
-            if (i + 1 < kOutChunks) issue_z(buf ^ 1);
-            wait_bar(buf);
-            if (!ok) break;
-            {
-                float v[32];
-                tc::tmem_ld32(lane_base + (uint32_t)(buf * kOutChunk + k0), v);
-                const float* tr = sT + r * kOutTLd + k0;
+    }
+    for (int i = 0; i < kOutChunks && ok; ++i) {
+        const int c = kOutChunks - 1 - i;
+        mma64(tmem, sH, sW, 0, false);
+        float4 t4[8];
+        if (live) {
+            const float4* tq = reinterpret_cast<const float4*>(trow + c * kOutChunk + k0);
 #pragma unroll
-                for (int h = 0; h < 4; ++h) {  // 8 columns = one 16-byte row of a core matrix
-                    const float4 ta = *reinterpret_cast<const float4*>(tr + 8 * h);
-                    const float4 tb = *reinterpret_cast<const float4*>(tr + 8 * h + 4);
-                    const float qv[8] = {ta.x, ta.y, ta.z, ta.w, tb.x, tb.y, tb.z, tb.w};
-                    uint32_t w[4];
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        bf16 x[2];
-#pragma unroll
-                        for (int k = 0; k < 2; ++k) {
-                            const int j = 2 * e + k, col = k0 + 8 * h + j;
-                            float gv = 0.0f;
-                            if (live) {
-                                const float q = qv[j] * inv_t;
-                                const float logp = v[8 * h + j] + sb[c * kOutChunk + col] - shift;
-                                if (q > 0.0f) kl += q * (__logf(q) - logp);
-                                gv = (__expf(logp) - q) * a.inv_n;
-                            }
-                            x[k] = __float2bfloat16_rn(gv);
-                        }
-                        w[e] = (uint32_t)__bfloat16_as_ushort(x[0]) | ((uint32_t)__bfloat16_as_ushort(x[1]) << 16);
-                    }
-                    *reinterpret_cast<uint4*>(sG + cm_off<128>(r, k0 + 8 * h)) = make_uint4(w[0], w[1], w[2], w[3]);
-                }
-            }
-            tc::fence_proxy_async();
-            tc::fence_before_sync();
-            __syncthreads();  // G staged; the Z buffer and the target stage have been read
-            if (tid == 0) {
-                tc::fence_after_sync();
-                const uint32_t a0 = tc::smem_addr(sG), b0 = tc::smem_addr(sWT);
-#pragma unroll
-                for (int s = 0; s < kOutChunk / 16; ++s)
-                    tc::mma_bf16(tmem + 2u * kOutChunk, tc::smem_desc(a0 + s * 256, 128, 128 * 16),
-                                 tc::smem_desc(b0 + s * 256, 128, 128 * 16), idesc_d, (i > 0 || s > 0) ? 1u : 0u);
-                tc::mma_commit(&mbar[2]);
-            }
-            if (i + 1 < kOutChunks) {  // the next target chunk, and the W4 rows two chunks on
-                stage_target(sT, a.target, a.n, m0, (c - 1) * kOutChunk);
-                if (i + 2 < kOutChunks)
-                    load_tile_async<64, kOutThreads>(sW(buf), a.w4, kHid, (c - 2) * kOutChunk, kOutChunk, kOut, 0, kHid);
-                tc::cp_async_commit();
-            }
-            // G^T rows and db4 from the staged chunk: thread -> chunk column kc, 32 tile rows
-            {
-                const int kc = tid & 127, rq = (tid >> 7) * 32;
-                bf16* gt = a.g4t + (size_t)(c * kOutChunk + kc) * a.ldg + m0 + rq;
-                const bool full = m0 + rq + 32 <= a.n && (a.ldg & 7) == 0;
-                float cs = 0.0f;
-#pragma unroll 1
-                for (int r8 = 0; r8 < 32; r8 += 8) {
-                    uint32_t w[4];
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const bf16 x0 = *reinterpret_cast<const bf16*>(sG + cm_off<128>(rq + r8 + 2 * e, kc));
-                        const bf16 x1 = *reinterpret_cast<const bf16*>(sG + cm_off<128>(rq + r8 + 2 * e + 1, kc));
-                        cs += __bfloat162float(x0) + __bfloat162float(x1);
-                        w[e] = (uint32_t)__bfloat16_as_ushort(x0) | ((uint32_t)__bfloat16_as_ushort(x1) << 16);
-                    }
-                    if (full) {
-                        *reinterpret_cast<uint4*>(gt + r8) = make_uint4(w[0], w[1], w[2], w[3]);
-                    } else {
-#pragma unroll
-                        for (int e = 0; e < 8; ++e)
-                            if (m0 + rq + r8 + e < a.n)
-                                gt[r8 + e] = __ushort_as_bfloat16((unsigned short)(w[e >> 1] >> (16 * (e & 1))));
-                    }
-                }
-                atomicAdd(&a.db4[c * kOutChunk + kc], cs);
-            }
-            wait_bar(2);  // dA3 has read sG and W4^T
-            if (ok && i + 1 < kOutChunks) {
-                load_tile_async<128, kOutThreads>(sWT, a.w4t, kOut, 0, kHid, kHid, (c - 1) * kOutChunk, kOut);
-                tc::cp_async_commit();
-            }
+            for (int k = 0; k < 8; ++k) t4[k] = tq[k];
         }
+        wait_bar(0);
         if (!ok) break;
-        // ---- epilogue: d3 = bf16(dA3 o [H3 > 0]) (16 of the 64 columns per thread) and its transpose
-        {
-            float v[16];
-            tc::tmem_ld16(lane_base + (uint32_t)(2 * kOutChunk + cg * 16), v);
-            if (live) {
-                uint32_t w[8];
+        if (i + 1 < kOutChunks) {
+            load_tile_async<64, kOutThreads>(sW, a.w4, kHid, (c - 1) * kOutChunk, kOutChunk, kOut, 0, kHid);
+            tc::cp_async_commit();
+        }
 #pragma unroll
-                for (int h = 0; h < 8; ++h) {
+        for (int g = 0; g < 2; ++g) {
+            float v[16];
+            tc::tmem_ld16(lane_base + (uint32_t)(k0 + g * 16), v);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {  // 8 columns = one 16-byte row of a core matrix
+                uint32_t w[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
                     bf16 x[2];
 #pragma unroll
                     for (int k = 0; k < 2; ++k) {
-                        const int j = cg * 16 + 2 * h + k;
-                        const float hv = __bfloat162float(*reinterpret_cast<const bf16*>(sH + cm_off<64>(r, j)));
-                        x[k] = __float2bfloat16_rn(hv > 0.0f ? v[2 * h + k] : 0.0f);
-                        a.d3t[(size_t)j * a.ldg + row] = x[k];
+                        const int j = 8 * h + 2 * e + k;        // column within the 16
+                        const int col = k0 + g * 16 + j;        // column within the chunk
+                        float gv = 0.0f;
+                        if (live) {
+                            const float4 tt = t4[(g * 16 + j) >> 2];
+                            const int s4 = (g * 16 + j) & 3;
+                            const float q = (s4 == 0 ? tt.x : s4 == 1 ? tt.y : s4 == 2 ? tt.z : tt.w) * inv_t;
+                            const float logp = v[j] + sb[c * kOutChunk + col] - shift;
+                            if (q > 0.0f) kl += q * (__logf(q) - logp);
+                            gv = (__expf(logp) - q) * a.inv_n;
+                        }
+                        x[k] = __float2bfloat16_rn(gv);
+                        if (live) a.g4t[(size_t)(c * kOutChunk + col) * a.ldg + row] = x[k];
                     }
-                    w[h] = (uint32_t)__bfloat16_as_ushort(x[0]) | ((uint32_t)__bfloat16_as_ushort(x[1]) << 16);
+                    w[e] = (uint32_t)__bfloat16_as_ushort(x[0]) | ((uint32_t)__bfloat16_as_ushort(x[1]) << 16);
                 }
-                uint4* dp = reinterpret_cast<uint4*>(a.d3 + (size_t)row * kHid + cg * 16);
-                dp[0] = make_uint4(w[0], w[1], w[2], w[3]);
-                dp[1] = make_uint4(w[4], w[5], w[6], w[7]);
+                *reinterpret_cast<uint4*>(sG + cm_off<64>(r, k0 + g * 16 + 8 * h)) = make_uint4(w[0], w[1], w[2], w[3]);
             }
         }
+        tc::fence_proxy_async();
         tc::fence_before_sync();
-        __syncthreads();  // dA3 read before the next tile's MMAs
+        __syncthreads();  // G staged; the Z chunk has been read
+        mma64(tmem + (uint32_t)kOutChunk, sG, sWT, 1, i > 0);
+        wait_bar(1);      // dA3 has read sG and W4^T
+        if (i + 1 < kOutChunks) {
+            load_tile_async<64, kOutThreads>(sWT, a.w4t, kOut, 0, kHid, kHid, (c - 1) * kOutChunk, kOut);
+            tc::cp_async_commit();
+        }
+        tc::cp_async_wait_all();
+        tc::fence_proxy_async();
+        __syncthreads();  // the next chunk's W4 rows and W4^T columns have landed
     }
     tc::cp_async_wait_all();
     if (!ok && lane == 0) atomicOr(a.status, (uint32_t)WFPG_STATUS_MMA_TIMEOUT);
+
+    // ---- epilogue: d3 = bf16(dA3 o [H3 > 0]) (this thread's 32 of the 64 columns) and its transpose; the KL
+    if (ok) {
+#pragma unroll 1
+        for (int g = 0; g < 2; ++g) {
+            float v[16];
+            tc::tmem_ld16(lane_base + (uint32_t)(kOutChunk + half * 32 + g * 16), v);
+            if (!live) continue;
+            uint32_t w[8];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) kl += __shfl_xor_sync(0xffffffffu, kl, o);
-    if (lane == 0 && kl != 0.0f) atomicAdd(a.loss, kl * a.inv_n);
+            for (int h = 0; h < 8; ++h) {
+                bf16 x[2];
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    const int j = half * 32 + g * 16 + 2 * h + k;
+                    const float hv = __bfloat162float(*reinterpret_cast<const bf16*>(sH + cm_off<64>(r, j)));
+                    x[k] = __float2bfloat16_rn(hv > 0.0f ? v[2 * h + k] : 0.0f);
+                    a.d3t[(size_t)j * a.ldg + row] = x[k];
+                }
+                w[h] = (uint32_t)__bfloat16_as_ushort(x[0]) | ((uint32_t)__bfloat16_as_ushort(x[1]) << 16);
+            }
+            uint4* dp = reinterpret_cast<uint4*>(a.d3 + (size_t)row * kHid + half * 32 + g * 16);
+            dp[0] = make_uint4(w[0], w[1], w[2], w[3]);
+            dp[1] = make_uint4(w[4], w[5], w[6], w[7]);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) kl += __shfl_xor_sync(0xffffffffu, kl, o);
+        if (lane == 0) atomicAdd(a.loss, kl * a.inv_n);
+    }
     tc::fence_before_sync();
     __syncthreads();
     if (warp == 0) tc::tmem_dealloc(tmem, kOutTmemCols);
@@ -862,15 +779,17 @@ int gemm(const GemmArgs& a, int splits, cudaStream_t st) {
     return splits;
 }
 
-// split-K weight gradient: partial tiles into s->part, then their sum into out
-template <int BN>
-void weight_grad(wfpg_mlp* s, GemmArgs g, int splits, float* out, cudaStream_t st) {
+// split-K weight and bias gradient: partial tiles [splits][M][kTRows] into s->part,
+// then their sum: columns < wcols to out_w (row stride ldw), column bias_col to out_b
+void weight_grad_wb(wfpg_mlp* s, GemmArgs g, int splits, float* out_w, int ldw, int wcols, float* out_b,
+                    int bias_col, cudaStream_t st) {
     g.C = s->part;
     g.ldc = g.N;
     g.split_stride = (size_t)g.M * g.N;
-    const int used = gemm<BN, kEpiPartial>(g, splits, st);
+    const int used = gemm<kTRows, kEpiPartial>(g, splits, st);
     const uint32_t mn = (uint32_t)(g.M * g.N);
-    WFPG_LAUNCH(k_sum_splits, div_up(mn, 32), dim3(32, 8), 0, st, s->part, used, mn, out);
+    WFPG_LAUNCH(k_sum_splits_wb, div_up(mn, 32), dim3(32, 8), 0, st, s->part, used, mn, g.N, out_w, ldw, wcols,
+                out_b, bias_col);
 }
 
 GemmArgs gargs(const bf16* A, int lda, const bf16* B, int ldb, int M, int N, int K, uint32_t* status) {
@@ -968,7 +887,7 @@ int mlp_create(const float* params, uint32_t max_batch, void* stream, wfpg_mlp**
     alloc(&s->m, 4 * kParams);
     alloc(&s->v, 4 * kParams);
     alloc(&s->grad, 4 * kParams);
-    alloc(&s->part, 4 * (size_t)std::max(kSplitsW4 * kOut * kHid, kSplitsHidden * kHid * kIn));
+    alloc(&s->part, 4 * (size_t)std::max(kSplitsW4 * kOut * kTRows, kSplitsHidden * kHid * kTRows));
     alloc(&s->w1, 2 * kHid * kIn);
     alloc(&s->w2, 2 * kHid * kHid);
     alloc(&s->w3, 2 * kHid * kHid);
@@ -978,9 +897,12 @@ int mlp_create(const float* params, uint32_t max_batch, void* stream, wfpg_mlp**
     alloc(&s->w4t, 2 * (size_t)kOut * kHid);
     alloc(&s->x, 2 * mp * kIn);
     alloc(&s->xt, 2 * mp * kIn);
-    bf16** acts[] = {&s->h1, &s->h1t, &s->h2, &s->h2t, &s->h3, &s->h3t, &s->d3, &s->d3t, &s->d2, &s->d2t,
-                     &s->d1, &s->d1t};
+    bf16** acts[] = {&s->h1, &s->h2, &s->h3, &s->d3, &s->d3t, &s->d2, &s->d2t, &s->d1, &s->d1t};
     for (bf16** a : acts) alloc(a, 2 * mp * kHid);
+    // the hidden activations' transposes carry a row of ones (row 64) and zero rows up to 80:
+    // the weight-gradient GEMMs then give each bias gradient as one more column
+    bf16** tacts[] = {&s->h1t, &s->h2t, &s->h3t};
+    for (bf16** a : tacts) alloc(a, 2 * mp * kTRows);
     alloc(&s->g4t, 2 * mp * kOut);
     alloc(&s->z, 4 * mp * kOut);
     alloc(&s->field, 4 * mp * kOut);
@@ -994,6 +916,10 @@ int mlp_create(const float* params, uint32_t max_batch, void* stream, wfpg_mlp**
         ok = cudaMemcpyAsync(s->params, params, 4 * kParams, cudaMemcpyHostToDevice, st) == cudaSuccess;
     else
         ok = cudaMemsetAsync(s->params, 0, 4 * kParams, st) == cudaSuccess;
+    for (bf16* t : {s->h1t, s->h2t, s->h3t}) {
+        ok = ok && cudaMemsetAsync(t, 0, 2 * mp * kTRows, st) == cudaSuccess;
+        if (ok) WFPG_LAUNCH(k_fill_bf16, div_up(mp, 256), 256, 0, st, t + (size_t)kHid * mp, (uint32_t)mp, 1.0f);
+    }
     ok = ok && cudaMemsetAsync(s->m, 0, 4 * kParams, st) == cudaSuccess &&
          cudaMemsetAsync(s->v, 0, 4 * kParams, st) == cudaSuccess &&
          cudaMemsetAsync(s->status, 0, 16, st) == cudaSuccess;
@@ -1121,17 +1047,13 @@ int guide_learned_train_step(wfpg_mlp* s, const float* pos, const float* nrm, ui
         oa.ldg = mp;
         oa.d3 = s->d3;
         oa.d3t = s->d3t;
-        oa.db4 = s->grad + kOffB4;
         oa.loss = s->loss;
         oa.status = s->status;
-        int sms = 0;
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        WFPG_LAUNCH(k_out_train, std::min<uint32_t>(div_up(n, 128), (uint32_t)std::max(sms, 1)), kOutThreads,
-                    kOutSmemBytes, st, oa);
+        WFPG_LAUNCH(k_out_train, div_up(n, 128), kOutThreads, kOutSmemBytes, st, oa);
     }
-    // dW4 = G4^T H3 (split-K over the batch)
-    GemmArgs g = gargs(s->g4t, mp, s->h3t, mp, kOut, kHid, N, s->status);
-    weight_grad<64>(s, g, kSplitsW4, s->grad + kOffW4, st);
+    // [dW4 | db4] = G4^T [H3 | 1] (split-K over the batch; H3^T carries a row of ones)
+    GemmArgs g = gargs(s->g4t, mp, s->h3t, mp, kOut, kTRows, N, s->status);
+    weight_grad_wb(s, g, kSplitsW4, s->grad + kOffW4, kHid, kHid, s->grad + kOffB4, kHid, st);
     // hidden layers
     struct Layer {
         bf16 *dA, *dAt, *Hprev_t, *Hprev, *Wt, *dAprev, *dAprev_t;
@@ -1141,10 +1063,11 @@ int guide_learned_train_step(wfpg_mlp* s, const float* pos, const float* nrm, ui
               {s->d2, s->d2t, s->h1t, s->h1, s->w2t, s->d1, s->d1t, kOffW2, kOffB2, kHid},
               {s->d1, s->d1t, s->xt, s->x, nullptr, nullptr, nullptr, kOffW1, kOffB1, kIn}};
     for (int l = 0; l < 3; ++l) {
-        g = gargs(L[l].dAt, mp, L[l].Hprev_t, mp, kHid, L[l].nin, N, s->status);
-        if (L[l].nin == kIn) weight_grad<80>(s, g, kSplitsHidden, s->grad + L[l].offW, st);
-        else weight_grad<64>(s, g, kSplitsHidden, s->grad + L[l].offW, st);
-        WFPG_LAUNCH(k_rowsum, dim3(div_up(n, 8192), kHid), 256, 0, st, L[l].dAt, N, mp, s->grad + L[l].offB);
+        // [dW | db] = dA^T [H_prev | 1]: the bias gradient is the column of the ones row
+        // (row 64 of the hidden transposes, padding row 78 of X^T)
+        g = gargs(L[l].dAt, mp, L[l].Hprev_t, mp, kHid, kTRows, N, s->status);
+        const int wcols = L[l].nin == kIn ? kFeatIn : kHid, ones = L[l].nin == kIn ? kFeatIn : kHid;
+        weight_grad_wb(s, g, kSplitsHidden, s->grad + L[l].offW, L[l].nin, wcols, s->grad + L[l].offB, ones, st);
         if (L[l].Wt) {
             g = gargs(L[l].dA, kHid, L[l].Wt, kHid, N, kHid, kHid, s->status);
             g.O = L[l].dAprev;
