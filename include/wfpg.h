@@ -439,10 +439,13 @@ WFPG_API int mlp_adam_step(wfpg_mlp* mlp, const float* grad, const wfpg_adam_par
 /*
  * guide_learned_train_step -- one step on n samples (n <= max_batch): pos/nrm
  * (xyz) of the sample points and target[n][1024], any non-negative field per
- * sample (normalised here; e.g. the pdf of guide_build_pdf at N = 32).
+ * sample (normalised here; e.g. the pdf of guide_build_pdf at N = 32); target
+ * must be 32-byte aligned (its rows are read with 32-byte loads).
  * Writes the mean KL to *loss_out and the gradient (WFPG_MLP_PARAMS floats)
  * to grad_out when they are not NULL (device pointers); with opt->update the
  * weights take one Adam step.
+ * Errors: null argument or array, target not 32-byte aligned
+ * (WFPG_ERR_INVALID_ARG); n = 0 or n > max_batch (WFPG_ERR_CAPACITY).
  */
 WFPG_API int guide_learned_train_step(wfpg_mlp* mlp, const float* pos, const float* nrm, uint32_t n,
                                       const float* target, const wfpg_learned_params* p,

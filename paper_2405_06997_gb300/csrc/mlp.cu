@@ -109,6 +109,12 @@ __device__ __forceinline__ void load_tile_async(uint8_t* smem, const bf16* g, in
     }
 }
 
+// byte offset of element (r, k) in a K-major no-swizzle core-matrix tile of KC columns
+template <int KC>
+__device__ __forceinline__ int cm_off(int r, int k) {
+    return (r >> 3) * (KC * 16) + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2;
+}
+
 template <int BN, int EPI>
 __global__ void __launch_bounds__(kGemmThreads) k_gemm_tn(GemmArgs g) {
     constexpr int kKChunk = KChunk<BN>::value;
@@ -310,15 +316,11 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm_tn(GemmArgs g) {
     if (warp == 0) tc::tmem_dealloc(tmem, kCols);
 }
 
-// input features of sample i (origin ray r of bin i when origin_ray is given)
-__global__ void k_mlp_features(const float* __restrict__ pos, const float* __restrict__ nrm,
-                               const uint32_t* __restrict__ origin_ray, const uint32_t* __restrict__ n_dev,
-                               uint32_t n_cap, float lox, float loy, float loz, float inv_s, bf16* __restrict__ X,
-                               bf16* __restrict__ XT, int ldxt) {
-    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n_cap) return;
-    const uint32_t n = n_dev ? min(*n_dev, n_cap) : n_cap;
-    float f[kIn];
+// input features of sample i (origin ray r of bin i when origin_ray is given);
+// zero for i >= n or an empty bin
+__device__ __forceinline__ void mlp_features(const float* __restrict__ pos, const float* __restrict__ nrm,
+                                             const uint32_t* __restrict__ origin_ray, uint32_t i, uint32_t n,
+                                             float lox, float loy, float loz, float inv_s, float f[kIn]) {
 #pragma unroll
     for (int k = 0; k < kIn; ++k) f[k] = 0.0f;
     const uint32_t r = origin_ray ? (i < n ? origin_ray[i] : kNone) : i;
@@ -341,22 +343,136 @@ __global__ void k_mlp_features(const float* __restrict__ pos, const float* __res
         f[76] = nrm[3 * (size_t)r + 1];
         f[77] = nrm[3 * (size_t)r + 2];
     }
-    // the row: 80 bf16 = 10 x 16-byte stores (rows are 160 B apart, so 16-byte aligned)
-    uint4* xr = reinterpret_cast<uint4*>(X + (size_t)i * kIn);
+}
+
+// ---------------------------------------------------------------------------
+// The three hidden layers, fused per 128-row tile: each thread computes the
+// input features of its row into shared memory (bfloat16, the MMA's K-major
+// layout), then every layer is one MMA into tensor memory (K = 80, then 64)
+// whose epilogue (bias, ReLU, bfloat16) writes the activations back over the
+// same shared tile for the next layer and out to global memory: row-major H3
+// always, H1 and H2 and the transposes X^T, H1^T, H2^T, H3^T when given (a
+// training step's weight gradients and ReLU masks).  128 threads, thread =
+// row = TMEM lane; 64 TMEM columns; four CTAs per SM.
+constexpr int kHidThreads = 128;
+constexpr int kHidSmemX = 0, kHidSmemW1 = 20480, kHidSmemW2 = 30720, kHidSmemW3 = 38912, kHidSmemB = 47104;
+constexpr int kHidSmemBytes = kHidSmemB + 3 * kHid * 4;
+
+struct HiddenArgs {
+    const float* pos;
+    const float* nrm;
+    const uint32_t* origin_ray;  // bins' origin rays, or null (row i = sample i)
+    const uint32_t* n_dev;       // device row count (<= n_cap), or null (n_cap rows)
+    uint32_t n_cap;
+    float lo[3], inv_s;
+    const bf16 *w1, *w2, *w3;    // [64][80], [64][64], [64][64]
+    const float *b1, *b2, *b3;
+    bf16 *h1, *h2, *h3;          // [rows][64]; h1, h2 may be null
+    bf16 *xt, *h1t, *h2t, *h3t;  // [80][ldt] (rows 0..79 of X^T; row 78 = 1), [64 of 80][ldt]; null: not written
+    int ldt;
+    uint32_t* status;
+};
+
+__global__ void __launch_bounds__(kHidThreads, 4) k_mlp_hidden(HiddenArgs a) {
+    extern __shared__ __align__(1024) uint8_t hid_smem[];
+    uint8_t* sX = hid_smem + kHidSmemX;  // X tile 128 x 80 (K = 80), then H1, H2: 128 x 64 (K = 64)
+    float* sb = reinterpret_cast<float*>(hid_smem + kHidSmemB);
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tmem_base;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const uint32_t i = blockIdx.x * 128 + tid;  // row of this thread
+    const bool in = i < a.n_cap;
+    if (warp == 0) tc::tmem_alloc(&tmem_base, 64);
+    if (tid == 0) {
+        tc::mbar_init(&mbar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    load_tile_async<kIn, kHidThreads>(hid_smem + kHidSmemW1, a.w1, kIn, 0, kHid, kHid, 0, kIn);
+    load_tile_async<kHid, kHidThreads>(hid_smem + kHidSmemW2, a.w2, kHid, 0, kHid, kHid, 0, kHid);
+    load_tile_async<kHid, kHidThreads>(hid_smem + kHidSmemW3, a.w3, kHid, 0, kHid, kHid, 0, kHid);
+    tc::cp_async_commit();
+    for (int j = tid; j < 3 * kHid; j += kHidThreads) sb[j] = (j < kHid ? a.b1 : j < 2 * kHid ? a.b2 : a.b3)[j % kHid];
+    {
+        const uint32_t n = a.n_dev ? min(*a.n_dev, a.n_cap) : a.n_cap;
+        float f[kIn];
+        mlp_features(a.pos, a.nrm, a.origin_ray, i, n, a.lo[0], a.lo[1], a.lo[2], a.inv_s, f);
 #pragma unroll
-    for (int q = 0; q < kIn / 8; ++q) {
-        uint32_t w[4];
+        for (int q = 0; q < kIn / 8; ++q) {  // one 16-byte core-matrix row per 8 features
+            uint32_t w[4];
 #pragma unroll
-        for (int h = 0; h < 4; ++h) {
-            const bf16 lo = __float2bfloat16_rn(f[8 * q + 2 * h]), hi = __float2bfloat16_rn(f[8 * q + 2 * h + 1]);
-            w[h] = (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+            for (int h = 0; h < 4; ++h) {
+                const __nv_bfloat162 p = __floats2bfloat162_rn(f[8 * q + 2 * h], f[8 * q + 2 * h + 1]);
+                w[h] = *reinterpret_cast<const uint32_t*>(&p);
+            }
+            *reinterpret_cast<uint4*>(sX + cm_off<kIn>(tid, 8 * q)) = make_uint4(w[0], w[1], w[2], w[3]);
         }
-        xr[q] = make_uint4(w[0], w[1], w[2], w[3]);
-    }
-    if (XT) {  // transposed copy: consecutive threads write consecutive rows of XT
+        if (a.xt && in) {  // consecutive threads write consecutive entries of each row of X^T
 #pragma unroll
-        for (int k = 0; k < kIn; ++k) XT[(size_t)k * ldxt + i] = __float2bfloat16_rn(k == kFeatIn ? 1.0f : f[k]);
+            for (int k = 0; k < kIn; ++k) a.xt[(size_t)k * a.ldt + i] = __float2bfloat16_rn(k == kFeatIn ? 1.0f : f[k]);
+        }
     }
+    tc::cp_async_wait_all();
+    tc::fence_proxy_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = tmem_base, lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+    constexpr uint32_t idesc = tc::idesc_bf16_f32(128, kHid);
+    bool ok = true;
+    uint32_t phase = 0;
+#pragma unroll 1
+    for (int l = 0; l < 3 && ok; ++l) {
+        if (tid == 0) {
+            const int K = l == 0 ? kIn : kHid;
+            const uint32_t a0 = tc::smem_addr(sX),
+                           b0 = tc::smem_addr(hid_smem + (l == 0 ? kHidSmemW1 : l == 1 ? kHidSmemW2 : kHidSmemW3));
+            for (int k = 0; k < K / 16; ++k)
+                tc::mma_bf16(tmem, tc::smem_desc(a0 + k * 256, 128, K * 16), tc::smem_desc(b0 + k * 256, 128, K * 16),
+                             idesc, k > 0 ? 1u : 0u);
+            tc::mma_commit(&mbar);
+        }
+        ok = __syncthreads_and(tc::mbar_wait(&mbar, phase)) != 0;
+        phase ^= 1u;
+        tc::fence_after_sync();
+        if (!ok) break;
+        bf16* O = l == 0 ? a.h1 : l == 1 ? a.h2 : a.h3;
+        bf16* OT = l == 0 ? a.h1t : l == 1 ? a.h2t : a.h3t;
+#pragma unroll
+        for (int c0 = 0; c0 < kHid; c0 += 16) {
+            float v[16];
+            tc::tmem_ld16(lane_base + (uint32_t)c0, v);
+            uint32_t w[8];
+#pragma unroll
+            for (int h = 0; h < 8; ++h) {
+                const __nv_bfloat162 p = __floats2bfloat162_rn(fmaxf(v[2 * h] + sb[l * kHid + c0 + 2 * h], 0.0f),
+                                                               fmaxf(v[2 * h + 1] + sb[l * kHid + c0 + 2 * h + 1], 0.0f));
+                w[h] = *reinterpret_cast<const uint32_t*>(&p);
+            }
+            if (l < 2) {  // the next layer's A operand (the MMA of this layer has completed)
+                *reinterpret_cast<uint4*>(sX + cm_off<kHid>(tid, c0)) = make_uint4(w[0], w[1], w[2], w[3]);
+                *reinterpret_cast<uint4*>(sX + cm_off<kHid>(tid, c0 + 8)) = make_uint4(w[4], w[5], w[6], w[7]);
+            }
+            if (O && in) {
+                uint4* op = reinterpret_cast<uint4*>(O + (size_t)i * kHid + c0);
+                op[0] = make_uint4(w[0], w[1], w[2], w[3]);
+                op[1] = make_uint4(w[4], w[5], w[6], w[7]);
+            }
+            if (OT && in) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j)
+                    OT[(size_t)(c0 + j) * a.ldt + i] =
+                        __ushort_as_bfloat16((unsigned short)((w[j >> 1] >> (16 * (j & 1))) & 0xffffu));
+            }
+        }
+        tc::fence_proxy_async();
+        tc::fence_before_sync();
+        __syncthreads();  // the accumulator has been read; the next layer's A tile is staged
+        tc::fence_after_sync();
+    }
+    if (!ok && (tid & 31) == 0) atomicOr(a.status, (uint32_t)WFPG_STATUS_MMA_TIMEOUT);
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, 64);
 }
 
 // one warp per row of 1024 logits: softmax; inference writes the field
@@ -451,56 +567,72 @@ __global__ void k_fill_bf16(bf16* __restrict__ out, uint32_t n, float v) {
 // The output layer of a training step, fused: for one 128-row tile, the logits
 // Z = H3 W4^T + b4 (1024 per row) are computed 64 at a time on the tensor
 // cores into tensor memory and never stored.  Pass 1 keeps each row's running
-// maximum and exponential sum and sums its target row; pass 2 recomputes each
-// chunk, forms the logit gradient G = bf16((softmax(Z) - q / sum q) / n) and
-// the KL term, stores G^T (the weight-gradient GEMM dW4 = G^T [H3 | 1] gives
-// dW4 and db4) and accumulates dA3 = G W4 in tensor memory with a second MMA
-// per chunk.  The epilogue writes d3 = bf16(dA3 o [H3 > 0]) and its transpose.
-// 256 threads, four CTAs per SM (128 TMEM columns each): warp w reads TMEM
-// lanes 32 (w % 4) .. + 31 (the tile's rows) and handles columns 32 (w / 4)
-// .. + 31 of each chunk.  W4 rows and W4^T columns of the next chunk are
-// copied in (cp.async) while the current one is processed.
+// maximum and exponential sum (base 2: u = Z log2 e) and the sums T = sum t
+// and A = sum t log2 t of its target row t; pass 2 recomputes each chunk,
+// forms the logit gradient G = bf16((softmax(Z) - t / T) / n), stores G^T
+// (the weight-gradient GEMM dW4 = G^T [H3 | 1] gives dW4 and db4) and
+// accumulates dA3 = G W4 in tensor memory with a second MMA per chunk.  The
+// KL term of a row needs no per-element logarithm of q: with S the base-2 log
+// of the softmax denominator and B = sum t u,
+//   KL = sum q (ln q - ln p) = ln 2 (A / T - log2 T - B / T + S)   (T > 0).
+// The epilogue writes d3 = bf16(dA3 o [H3 > 0]) and its transpose.  256
+// threads, four CTAs per SM (128 TMEM columns each): warp w reads TMEM lanes
+// 32 (w % 4) .. + 31 (the tile's rows) and handles columns 32 (w / 4) .. + 31
+// of each chunk.  Pass 1 double-buffers the logits (TMEM columns 0 and 64)
+// and the W4 rows (the W4^T buffer is free then); in pass 2 the dA3 MMA of a
+// chunk and the logits MMA of the next one are issued together.  Rows past n
+// take zero weight and write zeros (the transposes are mpad >= 128 ceil(n /
+// 128) rows long).
 constexpr int kOutThreads = 256;
 constexpr int kOutChunk = 64;                  // logits per chunk
 constexpr int kOutChunks = kOut / kOutChunk;   // 16
-constexpr uint32_t kOutTmemCols = 128;         // Z chunk at column 0, dA3 at column 64
-constexpr int kOutSmemH = 0, kOutSmemW = 16384, kOutSmemWT = 24576, kOutSmemG = 32768, kOutSmemB = 49152,
-              kOutSmemStat = kOutSmemB + 4 * kOut;
-constexpr int kOutSmemBytes = kOutSmemStat + 3 * 2 * 128 * 4;
+constexpr uint32_t kOutTmemCols = 128;
+constexpr int kOutSmemH = 0, kOutSmemW = 16384, kOutSmemWT = 24576, kOutSmemG = 32768, kOutSmemB = 49152;
+constexpr int kOutSmemBytes = kOutSmemB + 4 * kOut;
+constexpr float kLog2e = 1.4426950408889634f, kLn2 = 0.6931471805599453f;
 
 struct OutTrainArgs {
     const bf16* h3;      // [n][64]
     const bf16* w4;      // [1024][64]
     const bf16* w4t;     // [64][1024]
     const float* b4;     // [1024]
-    const float* target; // [n][1024], any non-negative field per row (normalised here)
+    const float* target; // [n][1024], any non-negative field per row (normalised here); 32-byte aligned
     int n;
     float inv_n;
     bf16* g4t;           // [1024][ldg]: G^T
     int ldg;
-    bf16* d3;            // [n][64]
+    bf16* d3;            // [ldg][64]
     bf16* d3t;           // [64][ldg]
     float* loss;         // accumulated mean KL
     uint32_t* status;
 };
 
-// byte offset of element (r, k) in a K-major no-swizzle core-matrix tile of KC columns
-template <int KC>
-__device__ __forceinline__ int cm_off(int r, int k) {
-    return (r >> 3) * (KC * 16) + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2;
+// base-2 exponential and logarithm of the special function unit
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float lg2_approx(float x) {
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+// eight floats with one 32-byte load that bypasses L1 (p 32-byte aligned)
+__device__ __forceinline__ void ld8_stream(const float* p, float v[8]) {
+    asm("ld.global.nc.L1::no_allocate.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7])
+        : "l"(p));
 }
 
 __global__ void __launch_bounds__(kOutThreads, 4) k_out_train(OutTrainArgs a) {
     extern __shared__ __align__(1024) uint8_t out_smem[];
     uint8_t* sH = out_smem + kOutSmemH;    // H3 tile: 128 x 64 (K = 64)
     uint8_t* sW = out_smem + kOutSmemW;    // W4 rows of the chunk: 64 x 64 (K = 64)
-    uint8_t* sWT = out_smem + kOutSmemWT;  // W4^T columns of the chunk: 64 x 64 (K = 64)
-    uint8_t* sG = out_smem + kOutSmemG;    // G of the chunk: 128 x 64 (K = 64)
-    float* sb = reinterpret_cast<float*>(out_smem + kOutSmemB);
-    float* s_max = reinterpret_cast<float*>(out_smem + kOutSmemStat);  // [2 column halves][128 rows]
-    float* s_sum = s_max + 256;
-    float* s_tsum = s_sum + 256;
-    __shared__ __align__(8) uint64_t mbar[2];  // 0: Z, 1: dA3
+    uint8_t* sWT = out_smem + kOutSmemWT;  // W4^T columns of the chunk (pass 2) / second W4 buffer (pass 1)
+    uint8_t* sG = out_smem + kOutSmemG;    // G of the chunk: 128 x 64 (K = 64); row statistics after pass 1
+    float* sbl = reinterpret_cast<float*>(out_smem + kOutSmemB);  // b4 log2 e
+    __shared__ __align__(8) uint64_t mbar[2];
     __shared__ uint32_t tmem_base;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int quad = warp & 3, half = warp >> 2;
@@ -508,6 +640,8 @@ __global__ void __launch_bounds__(kOutThreads, 4) k_out_train(OutTrainArgs a) {
     const int m0 = blockIdx.x * 128, row = m0 + r;
     const bool live = row < a.n;
     const int k0 = half * 32;        // first chunk column of this thread
+    const int rot = blockIdx.x & (kOutChunks - 1);  // chunk order rotated by CTA: spreads the target reads
+    auto chunk = [rot](int c) { return (c + rot) & (kOutChunks - 1); };
     if (warp == 0) tc::tmem_alloc(&tmem_base, kOutTmemCols);
     if (tid == 0) {
         tc::mbar_init(&mbar[0], 1);
@@ -515,9 +649,10 @@ __global__ void __launch_bounds__(kOutThreads, 4) k_out_train(OutTrainArgs a) {
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     load_tile_async<64, kOutThreads>(sH, a.h3, kHid, m0, 128, a.n, 0, kHid);
-    load_tile_async<64, kOutThreads>(sW, a.w4, kHid, 0, kOutChunk, kOut, 0, kHid);
+    load_tile_async<64, kOutThreads>(sW, a.w4, kHid, chunk(0) * kOutChunk, kOutChunk, kOut, 0, kHid);
+    load_tile_async<64, kOutThreads>(sWT, a.w4, kHid, chunk(1) * kOutChunk, kOutChunk, kOut, 0, kHid);
     tc::cp_async_commit();
-    for (int i = tid; i < kOut; i += kOutThreads) sb[i] = a.b4[i];
+    for (int i = tid; i < kOut; i += kOutThreads) sbl[i] = a.b4[i] * kLog2e;
     tc::cp_async_wait_all();
     tc::fence_proxy_async();
     tc::fence_before_sync();
@@ -525,148 +660,186 @@ __global__ void __launch_bounds__(kOutThreads, 4) k_out_train(OutTrainArgs a) {
     tc::fence_after_sync();
     const uint32_t tmem = tmem_base;
     const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16);
-    constexpr uint32_t idesc = tc::idesc_bf16_f32(128, 64);  // both MMAs: M = 128, N = 64
-    const float* trow = a.target + (size_t)row * kOut;
+    constexpr uint32_t idesc = tc::idesc_bf16_f32(128, 64);  // every MMA: M = 128, N = 64, K = 64
+    const float* trow = a.target + (size_t)(live ? row : a.n - 1) * kOut;
     uint32_t phase = 0;  // bit i: parity of mbar[i]'s next phase
     bool ok = true;
-    auto mma64 = [&](uint32_t d, const uint8_t* A, const uint8_t* B, int bar, bool acc) {
-        if (tid == 0) {
-            tc::fence_after_sync();
-            const uint32_t a0 = tc::smem_addr(A), b0 = tc::smem_addr(B);
+    // D (+)= A B^T over K = 64 as four K = 16 MMAs (issued by thread 0 only)
+    auto mma64 = [&](uint32_t d, const uint8_t* A, const uint8_t* B, bool acc) {
+        const uint32_t a0 = tc::smem_addr(A), b0 = tc::smem_addr(B);
 #pragma unroll
-            for (int s = 0; s < 4; ++s)
-                tc::mma_bf16(d, tc::smem_desc(a0 + s * 256, 128, 64 * 16), tc::smem_desc(b0 + s * 256, 128, 64 * 16),
-                             idesc, (acc || s > 0) ? 1u : 0u);
-            tc::mma_commit(&mbar[bar]);
-        }
+        for (int s = 0; s < 4; ++s)
+            tc::mma_bf16(d, tc::smem_desc(a0 + s * 256, 128, 64 * 16), tc::smem_desc(b0 + s * 256, 128, 64 * 16),
+                         idesc, (acc || s > 0) ? 1u : 0u);
     };
     auto wait_bar = [&](int i) {
         ok = ok && __syncthreads_and(tc::mbar_wait(&mbar[i], (phase >> i) & 1u)) != 0;
         phase ^= 1u << i;
         tc::fence_after_sync();
     };
+    if (tid == 0) {
+        mma64(tmem, sH, sW, false);
+        tc::mma_commit(&mbar[0]);
+        mma64(tmem + 64, sH, sWT, false);
+        tc::mma_commit(&mbar[1]);
+    }
 
-    // ---- pass 1: running maximum and exponential sum of this thread's columns; target row sum
-    float mrun = -3.4e38f, srun = 0.0f, tsum = 0.0f;
+    // ---- pass 1: running maximum and base-2 exponential sum of this thread's columns; T and A of the target row
+    float mrun = -3.0e38f, srun = 0.0f;
+    float* s_st = reinterpret_cast<float*>(sG);  // [m, s][2 column halves][128 rows], then T[128], A[128]
     for (int c = 0; c < kOutChunks && ok; ++c) {
-        mma64(tmem, sH, sW, 0, false);
-        if (live) {
-            const float4* tq = reinterpret_cast<const float4*>(trow + c * kOutChunk + k0);
+        const int buf = c & 1;
+        // the target sums of one whole row per warp and chunk (tile row 16 warp + c), read contiguously
+        const int lr = warp * 16 + c;
+        const float* tr = a.target + (size_t)min(m0 + lr, a.n - 1) * kOut + lane * 8;
+        float t[32];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const float4 v = tq[i];
-                tsum += (v.x + v.y) + (v.z + v.w);
-            }
-        }
-        wait_bar(0);
+        for (int i = 0; i < 4; ++i) ld8_stream(tr + 256 * i, t + 8 * i);
+        wait_bar(buf);
         if (!ok) break;
-        if (c + 1 < kOutChunks) {  // the MMA has read sW: the next chunk's W4 rows
-            load_tile_async<64, kOutThreads>(sW, a.w4, kHid, (c + 1) * kOutChunk, kOutChunk, kOut, 0, kHid);
+        if (c + 2 < kOutChunks) {  // the MMA has read this buffer's W4 rows
+            load_tile_async<64, kOutThreads>(buf ? sWT : sW, a.w4, kHid, chunk(c + 2) * kOutChunk, kOutChunk, kOut,
+                                             0, kHid);
             tc::cp_async_commit();
         }
-#pragma unroll 1
+#pragma unroll
         for (int g = 0; g < 2; ++g) {
             float v[16];
-            tc::tmem_ld16(lane_base + (uint32_t)(k0 + g * 16), v);
-            float gm = -3.4e38f;
+            tc::tmem_ld16(lane_base + (uint32_t)(64 * buf + k0 + g * 16), v);
+            const float4* bq = reinterpret_cast<const float4*>(sbl + chunk(c) * kOutChunk + k0 + g * 16);
+            float gm = -3.0e38f;
 #pragma unroll
-            for (int i = 0; i < 16; ++i) {
-                v[i] += sb[c * kOutChunk + k0 + g * 16 + i];
-                gm = fmaxf(gm, v[i]);
+            for (int i = 0; i < 4; ++i) {
+                const float4 b = bq[i];
+                v[4 * i + 0] = fmaf(v[4 * i + 0], kLog2e, b.x);
+                v[4 * i + 1] = fmaf(v[4 * i + 1], kLog2e, b.y);
+                v[4 * i + 2] = fmaf(v[4 * i + 2], kLog2e, b.z);
+                v[4 * i + 3] = fmaf(v[4 * i + 3], kLog2e, b.w);
             }
+#pragma unroll
+            for (int i = 0; i < 16; ++i) gm = fmaxf(gm, v[i]);
             if (gm > mrun) {
-                srun *= __expf(mrun - gm);
+                srun *= ex2_approx(mrun - gm);
                 mrun = gm;
             }
 #pragma unroll
-            for (int i = 0; i < 16; ++i) srun += __expf(v[i] - mrun);
+            for (int i = 0; i < 16; ++i) srun += ex2_approx(v[i] - mrun);
+        }
+        float tsum = 0.0f, tlog = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+            tsum += t[i];
+            tlog = fmaf(t[i], lg2_approx(fmaxf(t[i], 1e-30f)), tlog);  // t = 0 adds 0
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            tsum += __shfl_xor_sync(0xffffffffu, tsum, o);
+            tlog += __shfl_xor_sync(0xffffffffu, tlog, o);
+        }
+        if (lane == 0) {
+            s_st[512 + lr] = tsum;
+            s_st[640 + lr] = tlog;
         }
         tc::cp_async_wait_all();
         tc::fence_proxy_async();
         tc::fence_before_sync();
-        __syncthreads();  // TMEM read; the next W4 rows have landed
+        __syncthreads();  // the logits have been read; the W4 rows of chunk c + 2 have landed
+        tc::fence_after_sync();
+        if (tid == 0 && c + 2 < kOutChunks) {
+            mma64(tmem + 64 * buf, sH, buf ? sWT : sW, false);
+            tc::mma_commit(&mbar[buf]);
+        }
     }
-    s_max[half * 128 + r] = mrun;
-    s_sum[half * 128 + r] = srun;
-    s_tsum[half * 128 + r] = tsum;
+    s_st[0 * 256 + half * 128 + r] = mrun;
+    s_st[1 * 256 + half * 128 + r] = srun;
+    if (ok) {  // pass 2 starts at the last chunk
+        load_tile_async<64, kOutThreads>(sW, a.w4, kHid, chunk(kOutChunks - 1) * kOutChunk, kOutChunk, kOut, 0,
+                                         kHid);
+        tc::cp_async_commit();
+    }
     __syncthreads();
+    float S, invT, A, tsum;
     {
-        const float ma = s_max[r], mb = s_max[128 + r];
-        mrun = fmaxf(ma, mb);
-        srun = s_sum[r] * __expf(ma - mrun) + s_sum[128 + r] * __expf(mb - mrun);
-        tsum = s_tsum[r] + s_tsum[128 + r];
+        const float ma = s_st[r], mb = s_st[128 + r];
+        const float m = fmaxf(ma, mb);
+        S = m + lg2_approx(s_st[256 + r] * ex2_approx(ma - m) + s_st[384 + r] * ex2_approx(mb - m));
+        tsum = s_st[512 + r];
+        A = s_st[640 + r];
+        invT = tsum > 0.0f ? 1.0f / tsum : 0.0f;
     }
-    const float shift = mrun + __logf(srun), inv_t = tsum > 0.0f ? 1.0f / tsum : 0.0f;
-    float kl = 0.0f;
+    // G = p / n - t / (T n); rows past n give zero
+    const float gp = live ? a.inv_n : 0.0f, gq = live ? -invT * a.inv_n : 0.0f;
+    float bsum = 0.0f;  // B = sum t u over this thread's columns
+    tc::cp_async_wait_all();
+    tc::fence_proxy_async();
+    tc::fence_before_sync();
+    __syncthreads();  // the statistics have been read (sG is G again); the last chunk's W4 rows have landed
+    tc::fence_after_sync();
+    if (tid == 0 && ok) {
+        mma64(tmem, sH, sW, false);
+        tc::mma_commit(&mbar[0]);
+    }
 
     // ---- pass 2, chunks in reverse (the target rows read last are read again first)
-    if (ok) {
-        load_tile_async<64, kOutThreads>(sW, a.w4, kHid, (kOutChunks - 1) * kOutChunk, kOutChunk, kOut, 0, kHid);
-        load_tile_async<64, kOutThreads>(sWT, a.w4t, kOut, 0, kHid, kHid, (kOutChunks - 1) * kOutChunk, kOut);
-        tc::cp_async_commit();
-        tc::cp_async_wait_all();
-        tc::fence_proxy_async();
-        __syncthreads();
-    }
     for (int i = 0; i < kOutChunks && ok; ++i) {
-        const int c = kOutChunks - 1 - i;
-        mma64(tmem, sH, sW, 0, false);
-        float4 t4[8];
-        if (live) {
-            const float4* tq = reinterpret_cast<const float4*>(trow + c * kOutChunk + k0);
+        const int c = chunk(kOutChunks - 1 - i);
+        float t[32];
 #pragma unroll
-            for (int k = 0; k < 8; ++k) t4[k] = tq[k];
-        }
-        wait_bar(0);
+        for (int k = 0; k < 4; ++k) ld8_stream(trow + c * kOutChunk + k0 + 8 * k, t + 8 * k);
+        wait_bar(0);  // the logits of chunk c are in TMEM; the previous dA3 MMA has read sG and W4^T
         if (!ok) break;
-        if (i + 1 < kOutChunks) {
-            load_tile_async<64, kOutThreads>(sW, a.w4, kHid, (c - 1) * kOutChunk, kOutChunk, kOut, 0, kHid);
-            tc::cp_async_commit();
-        }
+        load_tile_async<64, kOutThreads>(sWT, a.w4t, kOut, 0, kHid, kHid, c * kOutChunk, kOut);
+        if (i + 1 < kOutChunks)
+            load_tile_async<64, kOutThreads>(sW, a.w4, kHid, chunk(kOutChunks - 2 - i) * kOutChunk, kOutChunk,
+                                             kOut, 0, kHid);
+        tc::cp_async_commit();
+        bf16* gcol = a.g4t + (size_t)(c * kOutChunk + k0) * a.ldg + row;  // G^T of this thread's first column
 #pragma unroll
         for (int g = 0; g < 2; ++g) {
             float v[16];
             tc::tmem_ld16(lane_base + (uint32_t)(k0 + g * 16), v);
+            const float4* bq = reinterpret_cast<const float4*>(sbl + c * kOutChunk + k0 + g * 16);
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {  // 8 columns = one 16-byte row of a core matrix
+            for (int h = 0; h < 2; ++h) {  // 8 columns: one 16-byte row of a core matrix
                 uint32_t w[4];
 #pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    bf16 x[2];
+                for (int e = 0; e < 2; ++e) {
+                    const float4 b = bq[2 * h + e];
+                    const float bb[4] = {b.x, b.y, b.z, b.w};
+                    float gv[4];
 #pragma unroll
-                    for (int k = 0; k < 2; ++k) {
-                        const int j = 8 * h + 2 * e + k;        // column within the 16
-                        const int col = k0 + g * 16 + j;        // column within the chunk
-                        float gv = 0.0f;
-                        if (live) {
-                            const float4 tt = t4[(g * 16 + j) >> 2];
-                            const int s4 = (g * 16 + j) & 3;
-                            const float q = (s4 == 0 ? tt.x : s4 == 1 ? tt.y : s4 == 2 ? tt.z : tt.w) * inv_t;
-                            const float logp = v[j] + sb[c * kOutChunk + col] - shift;
-                            if (q > 0.0f) kl += q * (__logf(q) - logp);
-                            gv = (__expf(logp) - q) * a.inv_n;
-                        }
-                        x[k] = __float2bfloat16_rn(gv);
-                        if (live) a.g4t[(size_t)(c * kOutChunk + col) * a.ldg + row] = x[k];
+                    for (int k = 0; k < 4; ++k) {
+                        const int j = 8 * h + 4 * e + k;
+                        const float u = fmaf(v[j], kLog2e, bb[k]);
+                        const float tj = t[g * 16 + j];
+                        bsum = fmaf(tj, u, bsum);
+                        gv[k] = fmaf(ex2_approx(u - S), gp, tj * gq);
                     }
-                    w[e] = (uint32_t)__bfloat16_as_ushort(x[0]) | ((uint32_t)__bfloat16_as_ushort(x[1]) << 16);
+                    const __nv_bfloat162 lo = __floats2bfloat162_rn(gv[0], gv[1]);
+                    const __nv_bfloat162 hi = __floats2bfloat162_rn(gv[2], gv[3]);
+                    w[2 * e] = *reinterpret_cast<const uint32_t*>(&lo);
+                    w[2 * e + 1] = *reinterpret_cast<const uint32_t*>(&hi);
+                }
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const uint32_t x = (w[j >> 1] >> (16 * (j & 1))) & 0xffffu;
+                    gcol[(size_t)(g * 16 + 8 * h + j) * a.ldg] = __ushort_as_bfloat16((unsigned short)x);
                 }
                 *reinterpret_cast<uint4*>(sG + cm_off<64>(r, k0 + g * 16 + 8 * h)) = make_uint4(w[0], w[1], w[2], w[3]);
             }
         }
-        tc::fence_proxy_async();
-        tc::fence_before_sync();
-        __syncthreads();  // G staged; the Z chunk has been read
-        mma64(tmem + (uint32_t)kOutChunk, sG, sWT, 1, i > 0);
-        wait_bar(1);      // dA3 has read sG and W4^T
-        if (i + 1 < kOutChunks) {
-            load_tile_async<64, kOutThreads>(sWT, a.w4t, kOut, 0, kHid, kHid, (c - 1) * kOutChunk, kOut);
-            tc::cp_async_commit();
-        }
         tc::cp_async_wait_all();
         tc::fence_proxy_async();
-        __syncthreads();  // the next chunk's W4 rows and W4^T columns have landed
+        tc::fence_before_sync();
+        __syncthreads();  // G staged, the logits read, W4^T of chunk c and W4 of chunk c - 1 landed
+        tc::fence_after_sync();
+        if (tid == 0) {
+            mma64(tmem + (uint32_t)kOutChunk, sG, sWT, i > 0);
+            if (i + 1 < kOutChunks) mma64(tmem, sH, sW, false);
+            tc::mma_commit(&mbar[0]);
+        }
     }
+    if (ok) wait_bar(0);  // the last dA3 MMA
     tc::cp_async_wait_all();
     if (!ok && lane == 0) atomicOr(a.status, (uint32_t)WFPG_STATUS_MMA_TIMEOUT);
 
@@ -676,7 +849,6 @@ __global__ void __launch_bounds__(kOutThreads, 4) k_out_train(OutTrainArgs a) {
         for (int g = 0; g < 2; ++g) {
             float v[16];
             tc::tmem_ld16(lane_base + (uint32_t)(kOutChunk + half * 32 + g * 16), v);
-            if (!live) continue;
             uint32_t w[8];
 #pragma unroll
             for (int h = 0; h < 8; ++h) {
@@ -694,6 +866,9 @@ __global__ void __launch_bounds__(kOutThreads, 4) k_out_train(OutTrainArgs a) {
             dp[0] = make_uint4(w[0], w[1], w[2], w[3]);
             dp[1] = make_uint4(w[4], w[5], w[6], w[7]);
         }
+        float kl = 0.0f;
+        if (live && tsum > 0.0f)
+            kl = kLn2 * ((half == 0 ? A * invT - lg2_approx(tsum) + S : 0.0f) - bsum * invT);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) kl += __shfl_xor_sync(0xffffffffu, kl, o);
         if (lane == 0) atomicAdd(a.loss, kl * a.inv_n);
@@ -737,7 +912,7 @@ struct wfpg_mlp {
     float *params = nullptr, *m = nullptr, *v = nullptr, *grad = nullptr;
     bf16 *w1 = nullptr, *w2 = nullptr, *w3 = nullptr, *w4 = nullptr, *w2t = nullptr, *w3t = nullptr,
          *w4t = nullptr;
-    bf16 *x = nullptr, *xt = nullptr, *h1 = nullptr, *h1t = nullptr, *h2 = nullptr, *h2t = nullptr, *h3 = nullptr,
+    bf16 *xt = nullptr, *h1 = nullptr, *h1t = nullptr, *h2 = nullptr, *h2t = nullptr, *h3 = nullptr,
          *h3t = nullptr, *g4t = nullptr, *d3 = nullptr, *d3t = nullptr, *d2 = nullptr,
          *d2t = nullptr, *d1 = nullptr, *d1t = nullptr;
     float* z = nullptr;
@@ -814,34 +989,42 @@ void convert_weights(wfpg_mlp* s, cudaStream_t st) {
     WFPG_LAUNCH(k_convert, div_up(kOut * kHid, T), T, 0, st, s->params + kOffW4, kOut, kHid, s->w4, s->w4t);
 }
 
-// forward through the hidden layers and the logits for n rows (X already set);
-// the logits go to z_out ([n][1024]) when given, else to the handle's buffer
-void forward(wfpg_mlp* s, int n, bool keep_transposes, cudaStream_t st, float* z_out = nullptr,
-             bool logits = true) {
-    const int mp = (int)s->mpad;
-    GemmArgs g = gargs(s->x, kIn, s->w1, kIn, n, kHid, kIn, s->status);
-    g.O = s->h1;
-    g.ldo = kHid;
-    g.OT = keep_transposes ? s->h1t : nullptr;
-    g.ldot = mp;
-    g.bias = s->params + kOffB1;
-    gemm<64, kEpiBf16Relu>(g, 1, st);
-    g = gargs(s->h1, kHid, s->w2, kHid, n, kHid, kHid, s->status);
-    g.O = s->h2;
-    g.ldo = kHid;
-    g.OT = keep_transposes ? s->h2t : nullptr;
-    g.ldot = mp;
-    g.bias = s->params + kOffB2;
-    gemm<64, kEpiBf16Relu>(g, 1, st);
-    g = gargs(s->h2, kHid, s->w3, kHid, n, kHid, kHid, s->status);
-    g.O = s->h3;
-    g.ldo = kHid;
-    g.OT = keep_transposes ? s->h3t : nullptr;
-    g.ldot = mp;
-    g.bias = s->params + kOffB3;
-    gemm<64, kEpiBf16Relu>(g, 1, st);
-    if (!logits) return;
-    g = gargs(s->h3, kHid, s->w4, kHid, n, kOut, kHid, s->status);
+// the hidden layers for n_cap rows (the row count is on the device when n_dev is
+// given); a training step also keeps H1, H2 and the transposes
+void hidden(wfpg_mlp* s, const float* pos, const float* nrm, const uint32_t* origin_ray, const uint32_t* n_dev,
+            uint32_t n_cap, const wfpg_learned_params* p, bool training, cudaStream_t st) {
+    HiddenArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.pos = pos;
+    a.nrm = nrm;
+    a.origin_ray = origin_ray;
+    a.n_dev = n_dev;
+    a.n_cap = n_cap;
+    for (int k = 0; k < 3; ++k) a.lo[k] = p->lo[k];
+    a.inv_s = 1.0f / p->size;
+    a.w1 = s->w1;
+    a.w2 = s->w2;
+    a.w3 = s->w3;
+    a.b1 = s->params + kOffB1;
+    a.b2 = s->params + kOffB2;
+    a.b3 = s->params + kOffB3;
+    a.h3 = s->h3;
+    if (training) {
+        a.h1 = s->h1;
+        a.h2 = s->h2;
+        a.xt = s->xt;
+        a.h1t = s->h1t;
+        a.h2t = s->h2t;
+        a.h3t = s->h3t;
+    }
+    a.ldt = (int)s->mpad;
+    a.status = s->status;
+    WFPG_LAUNCH(k_mlp_hidden, div_up(n_cap, 128), kHidThreads, kHidSmemBytes, st, a);
+}
+
+// the logits Z = H3 W4^T + b4 of n rows into z_out ([n][1024]), else the handle's buffer
+void output_logits(wfpg_mlp* s, int n, cudaStream_t st, float* z_out = nullptr) {
+    GemmArgs g = gargs(s->h3, kHid, s->w4, kHid, n, kOut, kHid, s->status);
     g.C = z_out ? z_out : s->z;
     g.ldc = kOut;
     g.bias = s->params + kOffB4;
@@ -895,7 +1078,6 @@ int mlp_create(const float* params, uint32_t max_batch, void* stream, wfpg_mlp**
     alloc(&s->w2t, 2 * kHid * kHid);
     alloc(&s->w3t, 2 * kHid * kHid);
     alloc(&s->w4t, 2 * (size_t)kOut * kHid);
-    alloc(&s->x, 2 * mp * kIn);
     alloc(&s->xt, 2 * mp * kIn);
     bf16** acts[] = {&s->h1, &s->h2, &s->h3, &s->d3, &s->d3t, &s->d2, &s->d2t, &s->d1, &s->d1t};
     for (bf16** a : acts) alloc(a, 2 * mp * kHid);
@@ -936,7 +1118,7 @@ int mlp_create(const float* params, uint32_t max_batch, void* stream, wfpg_mlp**
 int mlp_destroy(wfpg_mlp* s) {
     if (!s) return WFPG_OK;
     void* ptrs[] = {s->params, s->m, s->v, s->grad, s->part, s->w1, s->w2, s->w3, s->w4, s->w2t, s->w3t, s->w4t,
-                    s->x, s->xt, s->h1, s->h1t, s->h2, s->h2t, s->h3, s->h3t, s->g4t, s->d3,
+                    s->xt, s->h1, s->h1t, s->h2, s->h2t, s->h3, s->h3t, s->g4t, s->d3,
                     s->d3t, s->d2, s->d2t, s->d1, s->d1t, s->z, s->field, s->loss, s->status};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -974,9 +1156,8 @@ int guide_learned_build_pdf(wfpg_mlp* s, const float* pos, const float* nrm, con
         return mlp_fail(WFPG_ERR_INVALID_ARG, "guide_learned_build_pdf: size must be > 0 and eps >= 0");
     if (bin_cap == 0) return WFPG_OK;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    WFPG_LAUNCH(k_mlp_features, div_up(bin_cap, 128), 128, 0, st, pos, nrm, origin_ray, n_bins_dev, bin_cap,
-                p->lo[0], p->lo[1], p->lo[2], 1.0f / p->size, s->x, (bf16*)nullptr, 0);
-    forward(s, (int)bin_cap, false, st);
+    hidden(s, pos, nrm, origin_ray, n_bins_dev, bin_cap, p, false, st);
+    output_logits(s, (int)bin_cap, st);
     WFPG_LAUNCH(k_softmax_rows, div_up((uint64_t)bin_cap * 32, 256), 256, 0, st, s->z, bin_cap, n_bins_dev, p->eps,
                 s->field, (const float*)nullptr, 0.0f, (bf16*)nullptr, (float*)nullptr);
     if (wfpg::field_pdf_impl(s->field, 32, n_bins_dev, bin_cap, pdf, cdf_row, cdf_marg, st) != WFPG_OK ||
@@ -993,9 +1174,8 @@ int guide_learned_logits(wfpg_mlp* s, const float* pos, const float* nrm, uint32
         return mlp_fail(WFPG_ERR_CAPACITY, "guide_learned_logits: n must be in [1, max_batch]");
     if (!(p->size > 0.0f)) return mlp_fail(WFPG_ERR_INVALID_ARG, "guide_learned_logits: size must be > 0");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    WFPG_LAUNCH(k_mlp_features, div_up(n, 128), 128, 0, st, pos, nrm, (const uint32_t*)nullptr,
-                (const uint32_t*)nullptr, n, p->lo[0], p->lo[1], p->lo[2], 1.0f / p->size, s->x, (bf16*)nullptr, 0);
-    forward(s, (int)n, false, st, logits);
+    hidden(s, pos, nrm, nullptr, nullptr, n, p, false, st);
+    output_logits(s, (int)n, st, logits);
     if (cudaGetLastError() != cudaSuccess) return mlp_fail(WFPG_ERR_CUDA, "guide_learned_logits: launch failed");
     return WFPG_OK;
 }
@@ -1015,16 +1195,16 @@ int guide_learned_train_step(wfpg_mlp* s, const float* pos, const float* nrm, ui
                              const wfpg_learned_params* p, const wfpg_adam_params* opt, float* loss_out,
                              float* grad_out, void* stream) {
     if (!s || !p || !opt) return mlp_fail(WFPG_ERR_INVALID_ARG, "guide_learned_train_step: null argument");
+    if (!pos || !nrm || !target) return mlp_fail(WFPG_ERR_INVALID_ARG, "guide_learned_train_step: null array");
+    if (reinterpret_cast<uintptr_t>(target) % 32 != 0)
+        return mlp_fail(WFPG_ERR_INVALID_ARG, "guide_learned_train_step: target must be 32-byte aligned");
     if (n == 0 || n > s->max_batch)
         return mlp_fail(WFPG_ERR_CAPACITY, "guide_learned_train_step: n must be in [1, max_batch]");
-    if (!pos || !nrm || !target) return mlp_fail(WFPG_ERR_INVALID_ARG, "guide_learned_train_step: null array");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int mp = (int)s->mpad, N = (int)n;
     bool ok = cudaMemsetAsync(s->grad, 0, 4 * kParams, st) == cudaSuccess &&
               cudaMemsetAsync(s->loss, 0, 4, st) == cudaSuccess;
-    WFPG_LAUNCH(k_mlp_features, div_up(n, 128), 128, 0, st, pos, nrm, (const uint32_t*)nullptr,
-                (const uint32_t*)nullptr, n, p->lo[0], p->lo[1], p->lo[2], 1.0f / p->size, s->x, s->xt, mp);
-    forward(s, N, true, st, nullptr, false);
+    hidden(s, pos, nrm, nullptr, nullptr, n, p, true, st);
     // output layer, fused: logits, softmax, KL, G4^T, db4 and dA3 = (G4 W4) o [H3 > 0] per 128-row tile
     {
         static std::atomic<uint64_t> raised{0};
@@ -1061,7 +1241,7 @@ int guide_learned_train_step(wfpg_mlp* s, const float* pos, const float* nrm, ui
         int nin;
     } L[3] = {{s->d3, s->d3t, s->h2t, s->h2, s->w3t, s->d2, s->d2t, kOffW3, kOffB3, kHid},
               {s->d2, s->d2t, s->h1t, s->h1, s->w2t, s->d1, s->d1t, kOffW2, kOffB2, kHid},
-              {s->d1, s->d1t, s->xt, s->x, nullptr, nullptr, nullptr, kOffW1, kOffB1, kIn}};
+              {s->d1, s->d1t, s->xt, nullptr, nullptr, nullptr, nullptr, kOffW1, kOffB1, kIn}};
     for (int l = 0; l < 3; ++l) {
         // [dW | db] = dA^T [H_prev | 1]: the bias gradient is the column of the ones row
         // (row 64 of the hidden transposes, padding row 78 of X^T)

@@ -44,6 +44,7 @@ def lib():
         "mlp_create": [P, U32, P, P],
         "bin_rays_static": [P, P, P, U32, P, P, P, P, P, P, U32, P, P],
         "guide_learned_logits": [P, P, P, U32, P, P, P],
+        "guide_learned_train_step": [P, P, P, U32, P, P, P, P, P, P],
         "mlp_adam_step": [P, P, P, P],
     }
     for name, args in sig.items():
@@ -183,6 +184,31 @@ def test_learned_logits_and_adam_step_check_their_arguments(lib):
         for k, v in bad.items():
             setattr(o, k, v)
         assert lib.mlp_adam_step(b, b, C.byref(o), None) == INVALID and "beta1" in err(lib)
+
+
+def test_learned_train_step_checks_its_arguments(lib):
+    """Null arguments, then the target's 32-byte alignment (the kernel reads
+    target rows with 32-byte loads), then the batch size against the handle's
+    capacity (a zeroed stand-in handle has max_batch 0)."""
+    keep = host_buf(8192)
+    b = C.addressof(keep)
+    a32 = (b + 31) // 32 * 32
+    lp = W.LearnedParams()
+    lp.size = 1.0
+    opt = W.AdamParams(lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, update=1)
+
+    def call(mlp=a32, pos=a32, nrm=a32, n=4, target=a32, p=C.byref(lp), o=C.byref(opt)):
+        return lib.guide_learned_train_step(mlp, pos, nrm, n, target, p, o, None, None, None)
+
+    assert call(mlp=None) == INVALID and "null argument" in err(lib)
+    assert call(p=None) == INVALID and "null argument" in err(lib)
+    assert call(o=None) == INVALID and "null argument" in err(lib)
+    assert call(target=None) == INVALID and "null array" in err(lib)
+    assert call(pos=None) == INVALID and "null array" in err(lib)
+    for off in (4, 16):
+        assert call(target=a32 + off) == INVALID and "32-byte aligned" in err(lib)
+    assert call() == CAPACITY and "max_batch" in err(lib)
+    assert err(lib).startswith("guide_learned_train_step:")
 
 
 def test_guide_build_checks_its_parameters(lib):
