@@ -13,6 +13,7 @@
 // forward epilogues and the weight-conversion kernel).  Weight gradients
 // reduce over the batch with split-K: per-split partial tiles, then one summing pass.  Adam updates
 // float32 master weights, then bfloat16 copies are refreshed.
+#include <cuda.h>  // CUtensorMap and its enums (the encoder is fetched from the driver at run time)
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -51,6 +52,7 @@ struct GemmArgs {
     int lda, ldb;
     int M, N, K;
     int chunks_per_split;  // K chunks (KChunk<BN>) per blockIdx.z
+    int stages;            // shared-memory tile stages, 1 .. kMaxStages
     float* C;              // f32 output [M][ldc] (kEpiF32); per split z: C + z * split_stride (kEpiPartial)
     int ldc;
     size_t split_stride;
@@ -65,8 +67,15 @@ struct GemmArgs {
 };
 
 constexpr int kGemmThreads = 128;
-constexpr int kSplitsW4 = 64;       // K splits of the output layer's weight gradient (8 row tiles each)
-constexpr int kSplitsHidden = 128;  // K splits of the hidden layers' weight gradients (4 chunks of 128 rows each at 65,536 rows)
+constexpr int kMaxStages = 4;  // K chunks in flight: stages - 1 loading while the MMAs of one run
+
+// streaming multiprocessors of the current device
+int sm_count() {
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 1;
+}
 // K elements per pipeline step: 128 for narrow tiles (more bytes in flight per
 // CTA on the long-K weight-gradient GEMMs), 64 for the 256-wide logits tile
 template <int BN>
@@ -80,32 +89,38 @@ struct TmemCols {
 };
 
 // copy rows [r0, r0 + rows) x k [k0, k0 + KC) of a K-contiguous bf16 matrix into
-// the no-swizzle K-major core-matrix layout: 16-byte chunk c of row r goes to
-// (r / 8) * (KC * 16) + c * 128 + (r % 8) * 16; rows or k past the end read zero
-template <int KC, int NT = kGemmThreads>
-__device__ __forceinline__ void load_tile(uint8_t* smem, const bf16* g, int ld, int r0, int rows, int nrows_total,
-                                          int k0, int K) {
-    constexpr int kCpr = KC / 8;  // 16-byte chunks per row
-    for (int idx = threadIdx.x; idx < rows * kCpr; idx += NT) {
-        const int r = idx / kCpr, c = idx % kCpr;
-        const int gr = r0 + r, gk = k0 + c * 8;
-        uint4 v = make_uint4(0u, 0u, 0u, 0u);
-        if (gr < nrows_total && gk < K) v = *reinterpret_cast<const uint4*>(g + (size_t)gr * ld + gk);
-        *reinterpret_cast<uint4*>(smem + (r >> 3) * (KC * 16) + c * 128 + (r & 7) * 16) = v;
-    }
-}
-
-// load_tile with asynchronous copies (the caller commits and waits)
+// the no-swizzle K-major core-matrix layout with asynchronous 16-byte copies (the
+// caller commits and waits): 16-byte piece c of row r goes to (r / 8) * (KC * 16)
+// + c * 128 + (r % 8) * 16; rows or k past the end read zero.  When NT threads
+// cover whole 8-row groups per pass, each thread keeps one piece column and steps
+// its source pointer and destination by whole passes (no index arithmetic per
+// copy); otherwise the copies are numbered and split.
 template <int KC, int NT = kGemmThreads>
 __device__ __forceinline__ void load_tile_async(uint8_t* smem, const bf16* g, int ld, int r0, int rows,
                                                 int nrows_total, int k0, int K) {
-    constexpr int kCpr = KC / 8;
-    for (int idx = threadIdx.x; idx < rows * kCpr; idx += NT) {
-        const int r = idx / kCpr, c = idx % kCpr;
-        const int gr = r0 + r, gk = k0 + c * 8;
-        const bool valid = gr < nrows_total && gk < K;
-        tc::cp_async16(smem + (r >> 3) * (KC * 16) + c * 128 + (r & 7) * 16, valid ? g + (size_t)gr * ld + gk : g,
-                       valid);
+    constexpr int kCpr = KC / 8;  // 16-byte pieces per row
+    if constexpr (NT % kCpr == 0 && (NT / kCpr) % 8 == 0) {
+        constexpr int kRstep = NT / kCpr;  // rows per pass
+        const int c = threadIdx.x % kCpr, rr = threadIdx.x / kCpr;
+        const bool kvalid = k0 + c * 8 < K;
+        const bf16* src = g + (size_t)(r0 + rr) * ld + k0 + c * 8;
+        uint8_t* dst = smem + (rr >> 3) * (KC * 16) + c * 128 + (rr & 7) * 16;
+        const size_t step = (size_t)kRstep * ld;
+#pragma unroll
+        for (int r = rr; r < rows; r += kRstep) {
+            const bool valid = kvalid && r0 + r < nrows_total;
+            tc::cp_async16(dst, valid ? src : g, valid);
+            src += step;
+            dst += (kRstep / 8) * (KC * 16);
+        }
+    } else {
+        for (int idx = threadIdx.x; idx < rows * kCpr; idx += NT) {
+            const int r = idx / kCpr, c = idx % kCpr;
+            const int gr = r0 + r, gk = k0 + c * 8;
+            const bool valid = gr < nrows_total && gk < K;
+            tc::cp_async16(smem + (r >> 3) * (KC * 16) + c * 128 + (r & 7) * 16, valid ? g + (size_t)gr * ld + gk : g,
+                           valid);
+        }
     }
 }
 
@@ -116,15 +131,25 @@ __device__ __forceinline__ int cm_off(int r, int k) {
 }
 
 template <int BN, int EPI>
-__global__ void __launch_bounds__(kGemmThreads) k_gemm_tn(GemmArgs g) {
+__global__ void __launch_bounds__(kGemmThreads) k_gemm_tn(const __grid_constant__ CUtensorMap tma_a,
+                                                          const __grid_constant__ CUtensorMap tma_b, GemmArgs g) {
     constexpr int kKChunk = KChunk<BN>::value;
-    constexpr int kStageBytes = (128 + BN) * kKChunk * 2;
-    extern __shared__ __align__(1024) uint8_t gemm_smem[];
-    // two stages of (A tile 128 x kKChunk, B tile BN x kKChunk): chunk i + 1 is
-    // loaded while the MMAs of chunk i run
+    constexpr int kAtoms = kKChunk / 64;                 // 128-byte swizzle atoms along K per tile
+    constexpr int kABytes = 128 * kKChunk * 2, kBBytes = BN * kKChunk * 2;
+    constexpr int kStageBytes = kABytes + kBBytes;
+    extern __shared__ __align__(1024) uint8_t gemm_smem_raw[];
+    // the swizzled tiles need 1024-byte alignment (the launch adds 1 KB of slack)
+    uint8_t* gemm_smem = gemm_smem_raw + ((1024u - (tc::smem_addr(gemm_smem_raw) & 1023u)) & 1023u);
+    // g.stages stages of (A tile 128 x kKChunk, B tile BN x kKChunk), each the TMA's
+    // 128-byte swizzled layout: atom a (K columns 64 a .. 64 a + 63) of the A tile at
+    // a * 16 KB, of the B tile at kABytes + a * BN * 128.  Chunk j sits in stage j % S.
+    // One thread runs the pipeline: it issues the TMA copies of chunks i + 1 .. i + S - 1
+    // while the MMAs of chunk i run, each stage guarded by a full barrier (the copies
+    // have landed) and an empty barrier (the MMAs reading it are done).
+    const int S = g.stages;
     auto sA = [&](int s) { return gemm_smem + s * kStageBytes; };
-    auto sB = [&](int s) { return gemm_smem + s * kStageBytes + 128 * kKChunk * 2; };
-    __shared__ __align__(8) uint64_t mbar[2];
+    auto sB = [&](int s) { return gemm_smem + s * kStageBytes + kABytes; };
+    __shared__ __align__(8) uint64_t full[kMaxStages], empty[kMaxStages];
     __shared__ uint32_t tmem_base;
     constexpr uint32_t kCols = TmemCols<BN>::value;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -135,56 +160,76 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm_tn(GemmArgs g) {
     const int nch = kc1 - kc0;
     if (warp == 0) tc::tmem_alloc(&tmem_base, kCols);
     if (tid == 0) {
-        tc::mbar_init(&mbar[0], 1);
-        tc::mbar_init(&mbar[1], 1);
+        for (int s = 0; s < S; ++s) {
+            tc::mbar_init(&full[s], 1);
+            tc::mbar_init(&empty[s], 1);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    if (nch > 0) {
-        load_tile_async<kKChunk>(sA(0), g.A, g.lda, m0, 128, g.M, kc0 * kKChunk, g.K);
-        load_tile_async<kKChunk>(sB(0), g.B, g.ldb, n0, BN, g.N, kc0 * kKChunk, g.K);
-        tc::cp_async_commit();
     }
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = tmem_base;
     constexpr uint32_t idesc = tc::idesc_bf16_f32(128, BN);
-    uint32_t phase = 0u;  // bit s: parity of the next phase of mbar[s]
+    // the k-th use of stage j % S (k = j / S) completes phase k of its barriers
+    auto par = [&](int j) { return (uint32_t)(j / S) & 1u; };
+    // the ReLU-mask activations of this thread's row, loaded while the pipeline runs
+    constexpr int kActQ = EPI == kEpiReluGrad ? BN / 8 : 1;
+    uint4 act_pre[kActQ];
+    const bool act_vec = EPI == kEpiReluGrad && n0 + BN <= g.N && (g.ldact & 7) == 0 &&
+                         ((uintptr_t)g.act & 15) == 0 && m0 + warp * 32 + lane < g.M;
+    if constexpr (EPI == kEpiReluGrad) {
+        if (act_vec) {
+            const uint4* ap = reinterpret_cast<const uint4*>(g.act + (size_t)(m0 + warp * 32 + lane) * g.ldact + n0);
+#pragma unroll
+            for (int q = 0; q < kActQ; ++q) act_pre[q] = ap[q];
+        }
+    }
     bool ok = true;
-    for (int i = 0; i < nch && ok; ++i) {
-        const int s = i & 1;
-        tc::cp_async_wait_all();  // this thread's copies into stage s have landed
-        tc::fence_proxy_async();
-        __syncthreads();  // stage s is loaded and visible to the tensor cores
-        if (tid == 0) {
+    if (tid == 0) {
+        auto issue = [&](int j) {  // the TMA copies of chunk j (x = K offsets: multiples of 64 elements)
+            const int s = j % S, k0 = (kc0 + j) * kKChunk;
+            tc::mbar_expect_tx(&full[s], (uint32_t)kStageBytes);
+#pragma unroll
+            for (int at = 0; at < kAtoms; ++at) {
+                tc::tma_load_2d(sA(s) + at * (128 * 128), &tma_a, k0 + 64 * at, m0, &full[s]);
+                tc::tma_load_2d(sB(s) + at * (BN * 128), &tma_b, k0 + 64 * at, n0, &full[s]);
+            }
+        };
+        const int P = S > 1 ? S - 1 : 1;  // chunks in flight ahead of the MMAs
+        int issued = 0, landed = 0;
+        for (; issued < P && issued < nch; ++issued) issue(issued);
+        for (int i = 0; i < nch; ++i) {
+            const int s = i % S;
+            if (!tc::mbar_wait(&full[s], par(i))) {
+                ok = false;
+                break;
+            }
+            landed = i + 1;
             tc::fence_after_sync();
             const uint32_t a0 = tc::smem_addr(sA(s)), b0 = tc::smem_addr(sB(s));
 #pragma unroll
             for (int k = 0; k < kKChunk / 16; ++k) {
-                // K step of 16 = two core matrices along K (128 B apart); 8-row groups kKChunk * 16 B apart
-                const uint64_t ad = tc::smem_desc(a0 + k * 256, 128, kKChunk * 16);
-                const uint64_t bd = tc::smem_desc(b0 + k * 256, 128, kKChunk * 16);
+                const uint32_t off = (uint32_t)(k & 3) * 32u;  // 16 K elements = 32 bytes inside the atom
+                const uint64_t ad = tc::smem_desc_sw128(a0 + (uint32_t)(k >> 2) * (128 * 128) + off);
+                const uint64_t bd = tc::smem_desc_sw128(b0 + (uint32_t)(k >> 2) * (BN * 128) + off);
                 tc::mma_bf16(tmem, ad, bd, idesc, (i > 0 || k > 0) ? 1u : 0u);
             }
-            tc::mma_commit(&mbar[s]);
-        }
-        if (i + 1 < nch) {
-            // stage s ^ 1 was read by the MMAs of chunk i - 1: wait for them (bounded; the
-            // verdict is made uniform over the CTA), then load chunk i + 1 into it
-            if (i >= 1) {
-                ok = __syncthreads_and(tc::mbar_wait(&mbar[s ^ 1], (phase >> (s ^ 1)) & 1u)) != 0;
-                phase ^= 1u << (s ^ 1);
-            }
-            if (ok) {  // in flight while the MMAs of chunk i run
-                load_tile_async<kKChunk>(sA(s ^ 1), g.A, g.lda, m0, 128, g.M, (kc0 + i + 1) * kKChunk, g.K);
-                load_tile_async<kKChunk>(sB(s ^ 1), g.B, g.ldb, n0, BN, g.N, (kc0 + i + 1) * kKChunk, g.K);
-                tc::cp_async_commit();
+            tc::mma_commit(&empty[s]);
+            if (issued < nch) {  // refill the stage last read by the MMAs of chunk issued - S
+                if (issued - S >= 0 && !tc::mbar_wait(&empty[issued % S], par(issued - S))) {
+                    ok = false;
+                    break;
+                }
+                issue(issued++);
             }
         }
+        // the last chunk's commit tracks every MMA issued before it
+        if (ok && nch > 0) ok = tc::mbar_wait(&empty[(nch - 1) % S], par(nch - 1));
+        // after a timeout, let the copies already issued land before the CTA exits
+        for (int j = landed; j < issued; ++j) tc::mbar_wait(&full[j % S], par(j));
     }
-    tc::cp_async_wait_all();  // no copy left in flight (a timed-out CTA may still have some)
-    // the last chunk's commit tracks every MMA issued before it
-    if (ok && nch > 0) ok = __syncthreads_and(tc::mbar_wait(&mbar[(nch - 1) & 1], (phase >> ((nch - 1) & 1)) & 1u)) != 0;
+    ok = __syncthreads_and(ok) != 0;
     if (!ok && lane == 0) atomicOr(g.status, (uint32_t)WFPG_STATUS_MMA_TIMEOUT);
     tc::fence_after_sync();
     bool staged = false;
@@ -228,6 +273,7 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm_tn(GemmArgs g) {
     }
     if (ok && kc1 > kc0 && !staged) {
         const int row = m0 + warp * 32 + lane;
+#pragma unroll
         for (int c0 = 0; c0 < BN; c0 += 16) {
             float v[16];
             tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
@@ -255,11 +301,11 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm_tn(GemmArgs g) {
                 if ((EPI == kEpiBf16Relu || EPI == kEpiReluGrad) && (g.ldo & 7) == 0 && ((uintptr_t)g.O & 15) == 0 &&
                     (EPI != kEpiReluGrad || ((g.ldact & 7) == 0 && ((uintptr_t)g.act & 15) == 0))) {
                     float ar[16];  // forward activations of the 16 columns (ReLU gradient mask)
-                    if (EPI == kEpiReluGrad) {
+                    if constexpr (EPI == kEpiReluGrad) {
                         const uint4* ap = reinterpret_cast<const uint4*>(g.act + (size_t)row * g.ldact + n0 + c0);
 #pragma unroll
                         for (int q = 0; q < 2; ++q) {
-                            const uint4 a4 = ap[q];
+                            const uint4 a4 = act_vec ? act_pre[c0 / 8 + q] : ap[q];
                             const uint32_t aw[4] = {a4.x, a4.y, a4.z, a4.w};
 #pragma unroll
                             for (int h = 0; h < 4; ++h) {
@@ -908,6 +954,7 @@ __global__ void k_convert(const float* __restrict__ W, int nout, int nin, bf16* 
 struct wfpg_mlp {
     int device = 0;
     uint32_t max_batch = 0, mpad = 0;
+    uint32_t ldt = 0;  // row stride of the transposed activations: mpad + 64, off the power-of-two strides
     int step = 0;
     float *params = nullptr, *m = nullptr, *v = nullptr, *grad = nullptr;
     bf16 *w1 = nullptr, *w2 = nullptr, *w3 = nullptr, *w4 = nullptr, *w2t = nullptr, *w3t = nullptr,
@@ -925,6 +972,48 @@ struct wfpg_mlp {
 namespace {
 
 // launches the GEMM; returns the number of K splits it used
+// cuTensorMapEncodeTiled of the driver, fetched once through the runtime (no link
+// dependency on the driver library)
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled() {
+    static const EncodeTiledFn fn = [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            f = nullptr;
+        return reinterpret_cast<EncodeTiledFn>(f);
+    }();
+    return fn;
+}
+
+// 2-D tensor map of a bf16 matrix [rows][ld] whose first K entries per row are used:
+// boxes of 64 (K) x box_rows, 128-byte swizzling, zero fill outside; false when the
+// driver refuses it
+bool tensor_map(CUtensorMap* m, const bf16* base, int K, int rows, int ld, int box_rows) {
+    const EncodeTiledFn fn = encode_tiled();
+    if (!fn || K < 1 || rows < 1) return false;
+    const cuuint64_t dim[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+    const cuuint64_t stride[1] = {(cuuint64_t)ld * 2};
+    const cuuint32_t box[2] = {64u, (cuuint32_t)box_rows};
+    const cuuint32_t estride[2] = {1u, 1u};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<bf16*>(base), dim, stride, box, estride,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// set when a GEMM could not be launched (its tensor maps were refused); read and
+// cleared by the entry points
+thread_local bool g_gemm_failed = false;
+bool gemm_failed() {
+    const bool f = g_gemm_failed;
+    g_gemm_failed = false;
+    return f;
+}
+
 template <int BN, int EPI>
 int gemm(const GemmArgs& a, int splits, cudaStream_t st) {
     constexpr int kKChunk = KChunk<BN>::value;
@@ -936,32 +1025,40 @@ int gemm(const GemmArgs& a, int splits, cudaStream_t st) {
     splits = (chunks + g.chunks_per_split - 1) / g.chunks_per_split;
     const dim3 grid(div_up(g.M, 128), div_up(g.N, BN), splits);
     auto kernel = k_gemm_tn<BN, EPI>;
-    // one tile stage when every CTA takes a single K chunk (nothing to overlap; the
-    // smaller footprint keeps more CTAs resident), two otherwise
+    // up to kMaxStages tile stages, never more than a CTA's chunks (a single chunk
+    // needs one: the smaller footprint keeps more CTAs resident), plus 1 KB so that
+    // the kernel can align the swizzled tiles to 1024 bytes
     const int stage_bytes = (128 + BN) * kKChunk * 2;
-    const int smem = (g.chunks_per_split > 1 ? 2 : 1) * stage_bytes;
-    // the two stages plus the kernel's static shared memory exceed the default 48 KB
-    // window: raise the dynamic limit (to the two-stage size) once per device
+    g.stages = std::max(1, std::min(kMaxStages, g.chunks_per_split));
+    const int smem = g.stages * stage_bytes + 1024;
     static std::atomic<uint64_t> raised{0};
     int dev = 0;
     cudaGetDevice(&dev);
     const uint64_t bit = 1ull << (dev & 63);
     if (!(raised.load(std::memory_order_relaxed) & bit)) {
-        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * stage_bytes);
+        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxStages * stage_bytes + 1024);
         raised.fetch_or(bit, std::memory_order_relaxed);
     }
-    WFPG_LAUNCH(kernel, grid, kGemmThreads, smem, st, g);
+    alignas(64) CUtensorMap ta, tb;
+    if (!tensor_map(&ta, g.A, g.K, g.M, g.lda, 128) || !tensor_map(&tb, g.B, g.K, g.N, g.ldb, BN)) {
+        g_gemm_failed = true;
+        return 0;
+    }
+    WFPG_LAUNCH(kernel, grid, kGemmThreads, smem, st, ta, tb, g);
     return splits;
 }
 
 // split-K weight and bias gradient: partial tiles [splits][M][kTRows] into s->part,
 // then their sum: columns < wcols to out_w (row stride ldw), column bias_col to out_b
-void weight_grad_wb(wfpg_mlp* s, GemmArgs g, int splits, float* out_w, int ldw, int wcols, float* out_b,
-                    int bias_col, cudaStream_t st) {
+void weight_grad_wb(wfpg_mlp* s, GemmArgs g, float* out_w, int ldw, int wcols, float* out_b, int bias_col,
+                    cudaStream_t st) {
+    // one wave: a CTA per SM (four 53 KB stages each), the K range split over the SMs left per row tile
+    const int splits = std::max(1, sm_count() / (int)div_up((uint64_t)g.M, 128));
     g.C = s->part;
     g.ldc = g.N;
     g.split_stride = (size_t)g.M * g.N;
     const int used = gemm<kTRows, kEpiPartial>(g, splits, st);
+    if (used < 1) return;  // not launched: the entry point reports it
     const uint32_t mn = (uint32_t)(g.M * g.N);
     WFPG_LAUNCH(k_sum_splits_wb, div_up(mn, 32), dim3(32, 8), 0, st, s->part, used, mn, g.N, out_w, ldw, wcols,
                 out_b, bias_col);
@@ -1017,7 +1114,7 @@ void hidden(wfpg_mlp* s, const float* pos, const float* nrm, const uint32_t* ori
         a.h2t = s->h2t;
         a.h3t = s->h3t;
     }
-    a.ldt = (int)s->mpad;
+    a.ldt = (int)s->ldt;
     a.status = s->status;
     WFPG_LAUNCH(k_mlp_hidden, div_up(n_cap, 128), kHidThreads, kHidSmemBytes, st, a);
 }
@@ -1061,7 +1158,8 @@ int mlp_create(const float* params, uint32_t max_batch, void* stream, wfpg_mlp**
     cudaGetDevice(&s->device);
     s->max_batch = max_batch;
     s->mpad = (max_batch + 127) / 128 * 128;
-    const size_t mp = s->mpad;
+    s->ldt = s->mpad + 64;
+    const size_t mp = s->mpad, lt = s->ldt;
     bool ok = true;
     auto alloc = [&](auto** p, size_t bytes) {
         if (ok && cudaMalloc(reinterpret_cast<void**>(p), bytes ? bytes : 16) != cudaSuccess) ok = false;
@@ -1070,7 +1168,7 @@ int mlp_create(const float* params, uint32_t max_batch, void* stream, wfpg_mlp**
     alloc(&s->m, 4 * kParams);
     alloc(&s->v, 4 * kParams);
     alloc(&s->grad, 4 * kParams);
-    alloc(&s->part, 4 * (size_t)std::max(kSplitsW4 * kOut * kTRows, kSplitsHidden * kHid * kTRows));
+    alloc(&s->part, 4 * (size_t)sm_count() * 128 * kTRows);  // splits x row tiles <= SMs, 128 rows each
     alloc(&s->w1, 2 * kHid * kIn);
     alloc(&s->w2, 2 * kHid * kHid);
     alloc(&s->w3, 2 * kHid * kHid);
@@ -1078,14 +1176,14 @@ int mlp_create(const float* params, uint32_t max_batch, void* stream, wfpg_mlp**
     alloc(&s->w2t, 2 * kHid * kHid);
     alloc(&s->w3t, 2 * kHid * kHid);
     alloc(&s->w4t, 2 * (size_t)kOut * kHid);
-    alloc(&s->xt, 2 * mp * kIn);
+    alloc(&s->xt, 2 * lt * kIn);
     bf16** acts[] = {&s->h1, &s->h2, &s->h3, &s->d3, &s->d3t, &s->d2, &s->d2t, &s->d1, &s->d1t};
-    for (bf16** a : acts) alloc(a, 2 * mp * kHid);
+    for (bf16** a : acts) alloc(a, 2 * lt * kHid);  // row-major [mp][64] or transposed [64][ldt]
     // the hidden activations' transposes carry a row of ones (row 64) and zero rows up to 80:
     // the weight-gradient GEMMs then give each bias gradient as one more column
     bf16** tacts[] = {&s->h1t, &s->h2t, &s->h3t};
-    for (bf16** a : tacts) alloc(a, 2 * mp * kTRows);
-    alloc(&s->g4t, 2 * mp * kOut);
+    for (bf16** a : tacts) alloc(a, 2 * lt * kTRows);
+    alloc(&s->g4t, 2 * lt * kOut);
     alloc(&s->z, 4 * mp * kOut);
     alloc(&s->field, 4 * mp * kOut);
     alloc(&s->loss, 16);
@@ -1099,8 +1197,8 @@ int mlp_create(const float* params, uint32_t max_batch, void* stream, wfpg_mlp**
     else
         ok = cudaMemsetAsync(s->params, 0, 4 * kParams, st) == cudaSuccess;
     for (bf16* t : {s->h1t, s->h2t, s->h3t}) {
-        ok = ok && cudaMemsetAsync(t, 0, 2 * mp * kTRows, st) == cudaSuccess;
-        if (ok) WFPG_LAUNCH(k_fill_bf16, div_up(mp, 256), 256, 0, st, t + (size_t)kHid * mp, (uint32_t)mp, 1.0f);
+        ok = ok && cudaMemsetAsync(t, 0, 2 * lt * kTRows, st) == cudaSuccess;
+        if (ok) WFPG_LAUNCH(k_fill_bf16, div_up(lt, 256), 256, 0, st, t + (size_t)kHid * lt, (uint32_t)lt, 1.0f);
     }
     ok = ok && cudaMemsetAsync(s->m, 0, 4 * kParams, st) == cudaSuccess &&
          cudaMemsetAsync(s->v, 0, 4 * kParams, st) == cudaSuccess &&
@@ -1161,7 +1259,7 @@ int guide_learned_build_pdf(wfpg_mlp* s, const float* pos, const float* nrm, con
     WFPG_LAUNCH(k_softmax_rows, div_up((uint64_t)bin_cap * 32, 256), 256, 0, st, s->z, bin_cap, n_bins_dev, p->eps,
                 s->field, (const float*)nullptr, 0.0f, (bf16*)nullptr, (float*)nullptr);
     if (wfpg::field_pdf_impl(s->field, 32, n_bins_dev, bin_cap, pdf, cdf_row, cdf_marg, st) != WFPG_OK ||
-        cudaGetLastError() != cudaSuccess)
+        cudaGetLastError() != cudaSuccess || gemm_failed())
         return mlp_fail(WFPG_ERR_CUDA, "guide_learned_build_pdf: launch failed");
     return WFPG_OK;
 }
@@ -1176,7 +1274,8 @@ int guide_learned_logits(wfpg_mlp* s, const float* pos, const float* nrm, uint32
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     hidden(s, pos, nrm, nullptr, nullptr, n, p, false, st);
     output_logits(s, (int)n, st, logits);
-    if (cudaGetLastError() != cudaSuccess) return mlp_fail(WFPG_ERR_CUDA, "guide_learned_logits: launch failed");
+    if (cudaGetLastError() != cudaSuccess || gemm_failed())
+        return mlp_fail(WFPG_ERR_CUDA, "guide_learned_logits: launch failed");
     return WFPG_OK;
 }
 
@@ -1201,7 +1300,7 @@ int guide_learned_train_step(wfpg_mlp* s, const float* pos, const float* nrm, ui
     if (n == 0 || n > s->max_batch)
         return mlp_fail(WFPG_ERR_CAPACITY, "guide_learned_train_step: n must be in [1, max_batch]");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const int mp = (int)s->mpad, N = (int)n;
+    const int lt = (int)s->ldt, N = (int)n;
     bool ok = cudaMemsetAsync(s->grad, 0, 4 * kParams, st) == cudaSuccess &&
               cudaMemsetAsync(s->loss, 0, 4, st) == cudaSuccess;
     hidden(s, pos, nrm, nullptr, nullptr, n, p, true, st);
@@ -1224,7 +1323,7 @@ int guide_learned_train_step(wfpg_mlp* s, const float* pos, const float* nrm, ui
         oa.n = N;
         oa.inv_n = 1.0f / (float)n;
         oa.g4t = s->g4t;
-        oa.ldg = mp;
+        oa.ldg = lt;
         oa.d3 = s->d3;
         oa.d3t = s->d3t;
         oa.loss = s->loss;
@@ -1232,8 +1331,8 @@ int guide_learned_train_step(wfpg_mlp* s, const float* pos, const float* nrm, ui
         WFPG_LAUNCH(k_out_train, div_up(n, 128), kOutThreads, kOutSmemBytes, st, oa);
     }
     // [dW4 | db4] = G4^T [H3 | 1] (split-K over the batch; H3^T carries a row of ones)
-    GemmArgs g = gargs(s->g4t, mp, s->h3t, mp, kOut, kTRows, N, s->status);
-    weight_grad_wb(s, g, kSplitsW4, s->grad + kOffW4, kHid, kHid, s->grad + kOffB4, kHid, st);
+    GemmArgs g = gargs(s->g4t, lt, s->h3t, lt, kOut, kTRows, N, s->status);
+    weight_grad_wb(s, g, s->grad + kOffW4, kHid, kHid, s->grad + kOffB4, kHid, st);
     // hidden layers
     struct Layer {
         bf16 *dA, *dAt, *Hprev_t, *Hprev, *Wt, *dAprev, *dAprev_t;
@@ -1245,15 +1344,15 @@ int guide_learned_train_step(wfpg_mlp* s, const float* pos, const float* nrm, ui
     for (int l = 0; l < 3; ++l) {
         // [dW | db] = dA^T [H_prev | 1]: the bias gradient is the column of the ones row
         // (row 64 of the hidden transposes, padding row 78 of X^T)
-        g = gargs(L[l].dAt, mp, L[l].Hprev_t, mp, kHid, kTRows, N, s->status);
+        g = gargs(L[l].dAt, lt, L[l].Hprev_t, lt, kHid, kTRows, N, s->status);
         const int wcols = L[l].nin == kIn ? kFeatIn : kHid, ones = L[l].nin == kIn ? kFeatIn : kHid;
-        weight_grad_wb(s, g, kSplitsHidden, s->grad + L[l].offW, L[l].nin, wcols, s->grad + L[l].offB, ones, st);
+        weight_grad_wb(s, g, s->grad + L[l].offW, L[l].nin, wcols, s->grad + L[l].offB, ones, st);
         if (L[l].Wt) {
             g = gargs(L[l].dA, kHid, L[l].Wt, kHid, N, kHid, kHid, s->status);
             g.O = L[l].dAprev;
             g.ldo = kHid;
             g.OT = L[l].dAprev_t;
-            g.ldot = mp;
+            g.ldot = lt;
             g.act = L[l].Hprev;
             g.ldact = kHid;
             gemm<64, kEpiReluGrad>(g, 1, st);
@@ -1262,7 +1361,7 @@ int guide_learned_train_step(wfpg_mlp* s, const float* pos, const float* nrm, ui
     if (grad_out) ok = ok && cudaMemcpyAsync(grad_out, s->grad, 4 * kParams, cudaMemcpyDeviceToDevice, st) == cudaSuccess;
     if (loss_out) ok = ok && cudaMemcpyAsync(loss_out, s->loss, 4, cudaMemcpyDeviceToDevice, st) == cudaSuccess;
     if (opt->update) adam_update(s, s->grad, *opt, st);
-    if (!ok || cudaGetLastError() != cudaSuccess)
+    if (!ok || cudaGetLastError() != cudaSuccess || gemm_failed())
         return mlp_fail(WFPG_ERR_CUDA, "guide_learned_train_step: launch failed");
     return WFPG_OK;
 }

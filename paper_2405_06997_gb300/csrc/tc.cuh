@@ -22,6 +22,21 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
     return d;                // base offset 0, swizzle none
 }
 
+// Shared-memory matrix descriptor of a K-major operand in the 128-byte swizzled
+// layout that a TMA copy with 128-byte swizzling writes: 8-row x 128-byte atoms
+// (64 bf16 of K per row), 8-row groups 1024 B apart, atoms 1024-byte aligned.
+// A K step of 16 elements inside an atom advances saddr by 32 bytes (the swizzle
+// is applied to the address bits by the hardware).
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3ffffu) >> 4);
+    d |= (uint64_t)1 << 16;                    // leading byte offset: unused for swizzled K-major
+    d |= (uint64_t)(1024 >> 4) << 32;          // stride byte offset: 8-row groups
+    d |= (uint64_t)1 << 46;                    // descriptor version of the tcgen05 family
+    d |= (uint64_t)2 << 61;                    // swizzle: 128 bytes
+    return d;
+}
+
 // Instruction descriptor of kind::f16: bf16 A and B (both K-major), f32 D.
 __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
     return (1u << 4)                       // D: f32
@@ -117,6 +132,23 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float v[32]) {
                    "+r"(r[29]), "+r"(r[30]), "+r"(r[31])::"memory");
 #pragma unroll
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// the mbarrier expects `bytes` more transaction bytes (one arrival of this thread)
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* mbar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(mbar)), "r"(bytes)
+                 : "memory");
+}
+
+// TMA: the box of a 2-D tensor map at element coordinates (x, y) (x innermost) into
+// shared memory; completion is signalled on mbar as transaction bytes.  x times the
+// element size must be a multiple of 16 bytes.
+__device__ __forceinline__ void tma_load_2d(void* smem_dst, const void* tmap, int x, int y, uint64_t* mbar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+            "r"(smem_addr(smem_dst)),
+        "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y), "r"(smem_addr(mbar))
+        : "memory");
 }
 
 // 16-byte asynchronous global -> shared copy (cp.async, L2 only); with valid
