@@ -671,14 +671,19 @@ __device__ __forceinline__ void ld8_stream(const float* p, float v[8]) {
         : "l"(p));
 }
 
-__global__ void __launch_bounds__(kOutThreads, 4) k_out_train(OutTrainArgs a) {
-    extern __shared__ __align__(1024) uint8_t out_smem[];
-    uint8_t* sH = out_smem + kOutSmemH;    // H3 tile: 128 x 64 (K = 64)
-    uint8_t* sW = out_smem + kOutSmemW;    // W4 rows of the chunk: 64 x 64 (K = 64)
+__global__ void __launch_bounds__(kOutThreads, 4)
+    k_out_train(const __grid_constant__ CUtensorMap tma_h3, const __grid_constant__ CUtensorMap tma_w4,
+                const __grid_constant__ CUtensorMap tma_w4t, OutTrainArgs a) {
+    extern __shared__ __align__(1024) uint8_t out_smem_raw[];
+    // the TMA tiles (128-byte swizzled) need 1024-byte alignment (the launch adds 1 KB of slack)
+    uint8_t* out_smem = out_smem_raw + ((1024u - (tc::smem_addr(out_smem_raw) & 1023u)) & 1023u);
+    uint8_t* sH = out_smem + kOutSmemH;    // H3 tile: 128 x 64 (K = 64), TMA, 128-byte swizzled
+    uint8_t* sW = out_smem + kOutSmemW;    // W4 rows of the chunk: 64 x 64, TMA, swizzled
     uint8_t* sWT = out_smem + kOutSmemWT;  // W4^T columns of the chunk (pass 2) / second W4 buffer (pass 1)
-    uint8_t* sG = out_smem + kOutSmemG;    // G of the chunk: 128 x 64 (K = 64); row statistics after pass 1
+    uint8_t* sG = out_smem + kOutSmemG;    // G of the chunk: 128 x 64, core matrices; row statistics after pass 1
     float* sbl = reinterpret_cast<float*>(out_smem + kOutSmemB);  // b4 log2 e
-    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ __align__(8) uint64_t mbar[2];  // MMA completion: logits buffer 0 / 1
+    __shared__ __align__(8) uint64_t tbar[3];  // TMA completion: sW, sWT, sH
     __shared__ uint32_t tmem_base;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int quad = warp & 3, half = warp >> 2;
@@ -688,19 +693,38 @@ __global__ void __launch_bounds__(kOutThreads, 4) k_out_train(OutTrainArgs a) {
     const int k0 = half * 32;        // first chunk column of this thread
     const int rot = blockIdx.x & (kOutChunks - 1);  // chunk order rotated by CTA: spreads the target reads
     auto chunk = [rot](int c) { return (c + rot) & (kOutChunks - 1); };
+    // thread 0 issues every TMA copy and MMA; tph holds the parity of each TMA barrier's
+    // next phase, tpend the barriers with a copy in flight, tok whether its waits succeeded
+    uint32_t tph = 0, tpend = 0;
+    bool tok = true;
+    auto tma_w = [&](uint8_t* dst, int bi, int c) {  // W4 rows of chunk c (x = 0)
+        tc::mbar_expect_tx(&tbar[bi], 64 * 64 * 2);
+        tc::tma_load_2d(dst, &tma_w4, 0, c * kOutChunk, &tbar[bi]);
+        tpend |= 1u << bi;
+    };
+    auto tma_wt = [&](int c) {  // W4^T columns of chunk c (x = 64 c: 128-byte aligned)
+        tc::mbar_expect_tx(&tbar[1], 64 * 64 * 2);
+        tc::tma_load_2d(sWT, &tma_w4t, c * kOutChunk, 0, &tbar[1]);
+        tpend |= 1u << 1;
+    };
+    auto tma_done = [&](int bi) {
+        tok = tc::mbar_wait(&tbar[bi], (tph >> bi) & 1u) && tok;
+        tph ^= 1u << bi;
+        tpend &= ~(1u << bi);
+    };
     if (warp == 0) tc::tmem_alloc(&tmem_base, kOutTmemCols);
     if (tid == 0) {
         tc::mbar_init(&mbar[0], 1);
         tc::mbar_init(&mbar[1], 1);
+        for (int i = 0; i < 3; ++i) tc::mbar_init(&tbar[i], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        tc::mbar_expect_tx(&tbar[2], 128 * 64 * 2);
+        tc::tma_load_2d(sH, &tma_h3, 0, m0, &tbar[2]);  // rows past n read zero
+        tpend |= 1u << 2;
+        tma_w(sW, 0, chunk(0));
+        tma_w(sWT, 1, chunk(1));
     }
-    load_tile_async<64, kOutThreads>(sH, a.h3, kHid, m0, 128, a.n, 0, kHid);
-    load_tile_async<64, kOutThreads>(sW, a.w4, kHid, chunk(0) * kOutChunk, kOutChunk, kOut, 0, kHid);
-    load_tile_async<64, kOutThreads>(sWT, a.w4, kHid, chunk(1) * kOutChunk, kOutChunk, kOut, 0, kHid);
-    tc::cp_async_commit();
     for (int i = tid; i < kOut; i += kOutThreads) sbl[i] = a.b4[i] * kLog2e;
-    tc::cp_async_wait_all();
-    tc::fence_proxy_async();
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
@@ -710,23 +734,27 @@ __global__ void __launch_bounds__(kOutThreads, 4) k_out_train(OutTrainArgs a) {
     const float* trow = a.target + (size_t)(live ? row : a.n - 1) * kOut;
     uint32_t phase = 0;  // bit i: parity of mbar[i]'s next phase
     bool ok = true;
-    // D (+)= A B^T over K = 64 as four K = 16 MMAs (issued by thread 0 only)
-    auto mma64 = [&](uint32_t d, const uint8_t* A, const uint8_t* B, bool acc) {
+    // D (+)= A B^T over K = 64 as four K = 16 MMAs (issued by thread 0 only); B is a
+    // swizzled TMA tile, A either the swizzled H3 tile (the logits) or the core-matrix G tile (dA3)
+    auto mma64 = [&](uint32_t d, const uint8_t* A, bool a_swizzled, const uint8_t* B, bool acc) {
         const uint32_t a0 = tc::smem_addr(A), b0 = tc::smem_addr(B);
 #pragma unroll
         for (int s = 0; s < 4; ++s)
-            tc::mma_bf16(d, tc::smem_desc(a0 + s * 256, 128, 64 * 16), tc::smem_desc(b0 + s * 256, 128, 64 * 16),
-                         idesc, (acc || s > 0) ? 1u : 0u);
+            tc::mma_bf16(d, a_swizzled ? tc::smem_desc_sw128(a0 + s * 32) : tc::smem_desc(a0 + s * 256, 128, 64 * 16),
+                         tc::smem_desc_sw128(b0 + s * 32), idesc, (acc || s > 0) ? 1u : 0u);
     };
     auto wait_bar = [&](int i) {
-        ok = ok && __syncthreads_and(tc::mbar_wait(&mbar[i], (phase >> i) & 1u)) != 0;
+        ok = ok && __syncthreads_and(tc::mbar_wait(&mbar[i], (phase >> i) & 1u) && tok) != 0;
         phase ^= 1u << i;
         tc::fence_after_sync();
     };
     if (tid == 0) {
-        mma64(tmem, sH, sW, false);
+        tma_done(2);
+        tma_done(0);
+        mma64(tmem, sH, true, sW, false);
         tc::mma_commit(&mbar[0]);
-        mma64(tmem + 64, sH, sWT, false);
+        tma_done(1);
+        mma64(tmem + 64, sH, true, sWT, false);
         tc::mma_commit(&mbar[1]);
     }
 
@@ -743,11 +771,7 @@ __global__ void __launch_bounds__(kOutThreads, 4) k_out_train(OutTrainArgs a) {
         for (int i = 0; i < 4; ++i) ld8_stream(tr + 256 * i, t + 8 * i);
         wait_bar(buf);
         if (!ok) break;
-        if (c + 2 < kOutChunks) {  // the MMA has read this buffer's W4 rows
-            load_tile_async<64, kOutThreads>(buf ? sWT : sW, a.w4, kHid, chunk(c + 2) * kOutChunk, kOutChunk, kOut,
-                                             0, kHid);
-            tc::cp_async_commit();
-        }
+        if (tid == 0 && c + 2 < kOutChunks) tma_w(buf ? sWT : sW, buf, chunk(c + 2));  // the MMA has read the buffer
 #pragma unroll
         for (int g = 0; g < 2; ++g) {
             float v[16];
@@ -786,22 +810,20 @@ __global__ void __launch_bounds__(kOutThreads, 4) k_out_train(OutTrainArgs a) {
             s_st[512 + lr] = tsum;
             s_st[640 + lr] = tlog;
         }
-        tc::cp_async_wait_all();
-        tc::fence_proxy_async();
         tc::fence_before_sync();
-        __syncthreads();  // the logits have been read; the W4 rows of chunk c + 2 have landed
+        __syncthreads();  // the logits have been read
         tc::fence_after_sync();
         if (tid == 0 && c + 2 < kOutChunks) {
-            mma64(tmem + 64 * buf, sH, buf ? sWT : sW, false);
+            tma_done(buf);  // the W4 rows of chunk c + 2
+            mma64(tmem + 64 * buf, sH, true, buf ? sWT : sW, false);
             tc::mma_commit(&mbar[buf]);
         }
     }
     s_st[0 * 256 + half * 128 + r] = mrun;
     s_st[1 * 256 + half * 128 + r] = srun;
-    if (ok) {  // pass 2 starts at the last chunk
-        load_tile_async<64, kOutThreads>(sW, a.w4, kHid, chunk(kOutChunks - 1) * kOutChunk, kOutChunk, kOut, 0,
-                                         kHid);
-        tc::cp_async_commit();
+    if (tid == 0 && ok) {  // pass 2 starts at the last chunk (both buffers' MMAs are done)
+        tma_w(sW, 0, chunk(kOutChunks - 1));
+        tma_wt(chunk(kOutChunks - 1));
     }
     __syncthreads();
     float S, invT, A, tsum;
@@ -816,13 +838,12 @@ __global__ void __launch_bounds__(kOutThreads, 4) k_out_train(OutTrainArgs a) {
     // G = p / n - t / (T n); rows past n give zero
     const float gp = live ? a.inv_n : 0.0f, gq = live ? -invT * a.inv_n : 0.0f;
     float bsum = 0.0f;  // B = sum t u over this thread's columns
-    tc::cp_async_wait_all();
-    tc::fence_proxy_async();
     tc::fence_before_sync();
-    __syncthreads();  // the statistics have been read (sG is G again); the last chunk's W4 rows have landed
+    __syncthreads();  // the statistics have been read (sG is G again)
     tc::fence_after_sync();
     if (tid == 0 && ok) {
-        mma64(tmem, sH, sW, false);
+        tma_done(0);
+        mma64(tmem, sH, true, sW, false);
         tc::mma_commit(&mbar[0]);
     }
 
@@ -834,11 +855,10 @@ __global__ void __launch_bounds__(kOutThreads, 4) k_out_train(OutTrainArgs a) {
         for (int k = 0; k < 4; ++k) ld8_stream(trow + c * kOutChunk + k0 + 8 * k, t + 8 * k);
         wait_bar(0);  // the logits of chunk c are in TMEM; the previous dA3 MMA has read sG and W4^T
         if (!ok) break;
-        load_tile_async<64, kOutThreads>(sWT, a.w4t, kOut, 0, kHid, kHid, c * kOutChunk, kOut);
-        if (i + 1 < kOutChunks)
-            load_tile_async<64, kOutThreads>(sW, a.w4, kHid, chunk(kOutChunks - 2 - i) * kOutChunk, kOutChunk,
-                                             kOut, 0, kHid);
-        tc::cp_async_commit();
+        if (tid == 0) {  // the logits MMA has read sW, the last dA3 MMA sWT
+            if (i > 0) tma_wt(c);
+            if (i + 1 < kOutChunks) tma_w(sW, 0, chunk(kOutChunks - 2 - i));
+        }
         bf16* gcol = a.g4t + (size_t)(c * kOutChunk + k0) * a.ldg + row;  // G^T of this thread's first column
 #pragma unroll
         for (int g = 0; g < 2; ++g) {
@@ -874,23 +894,31 @@ __global__ void __launch_bounds__(kOutThreads, 4) k_out_train(OutTrainArgs a) {
                 *reinterpret_cast<uint4*>(sG + cm_off<64>(r, k0 + g * 16 + 8 * h)) = make_uint4(w[0], w[1], w[2], w[3]);
             }
         }
-        tc::cp_async_wait_all();
-        tc::fence_proxy_async();
+        tc::fence_proxy_async();  // G, written by the threads, is read by the tensor cores
         tc::fence_before_sync();
-        __syncthreads();  // G staged, the logits read, W4^T of chunk c and W4 of chunk c - 1 landed
+        __syncthreads();  // G staged, the logits read
         tc::fence_after_sync();
         if (tid == 0) {
-            mma64(tmem + (uint32_t)kOutChunk, sG, sWT, i > 0);
-            if (i + 1 < kOutChunks) mma64(tmem, sH, sW, false);
+            tma_done(1);  // W4^T of chunk c
+            mma64(tmem + (uint32_t)kOutChunk, sG, false, sWT, i > 0);
+            if (i + 1 < kOutChunks) {
+                tma_done(0);  // W4 of the next chunk
+                mma64(tmem, sH, true, sW, false);
+            }
             tc::mma_commit(&mbar[0]);
         }
     }
     if (ok) wait_bar(0);  // the last dA3 MMA
-    tc::cp_async_wait_all();
+    if (tid == 0) {  // after a timeout, let the copies in flight land before the CTA exits
+        for (int bi = 0; bi < 3; ++bi)
+            if (tpend & (1u << bi)) tma_done(bi);
+    }
     if (!ok && lane == 0) atomicOr(a.status, (uint32_t)WFPG_STATUS_MMA_TIMEOUT);
+    // every thread reads the H3 tile below: observe its copy's completion (phase 0)
+    const bool h3_ok = tc::mbar_wait(&tbar[2], 0u);
 
     // ---- epilogue: d3 = bf16(dA3 o [H3 > 0]) (this thread's 32 of the 64 columns) and its transpose; the KL
-    if (ok) {
+    if (ok && h3_ok) {
 #pragma unroll 1
         for (int g = 0; g < 2; ++g) {
             float v[16];
@@ -902,7 +930,9 @@ __global__ void __launch_bounds__(kOutThreads, 4) k_out_train(OutTrainArgs a) {
 #pragma unroll
                 for (int k = 0; k < 2; ++k) {
                     const int j = half * 32 + g * 16 + 2 * h + k;
-                    const float hv = __bfloat162float(*reinterpret_cast<const bf16*>(sH + cm_off<64>(r, j)));
+                    // element (r, j) of the swizzled tile: 16-byte chunk j / 8 of row r at chunk (j / 8) ^ (r % 8)
+                    const float hv = __bfloat162float(*reinterpret_cast<const bf16*>(
+                        sH + (r >> 3) * 1024 + (r & 7) * 128 + ((((j >> 3) ^ r) & 7) << 4) + (j & 7) * 2));
                     x[k] = __float2bfloat16_rn(hv > 0.0f ? v[2 * h + k] : 0.0f);
                     a.d3t[(size_t)j * a.ldg + row] = x[k];
                 }
@@ -1311,7 +1341,7 @@ int guide_learned_train_step(wfpg_mlp* s, const float* pos, const float* nrm, ui
         cudaGetDevice(&dev);
         const uint64_t bit = 1ull << (dev & 63);
         if (!(raised.load(std::memory_order_relaxed) & bit)) {
-            cudaFuncSetAttribute(k_out_train, cudaFuncAttributeMaxDynamicSharedMemorySize, kOutSmemBytes);
+            cudaFuncSetAttribute(k_out_train, cudaFuncAttributeMaxDynamicSharedMemorySize, kOutSmemBytes + 1024);
             raised.fetch_or(bit, std::memory_order_relaxed);
         }
         OutTrainArgs oa;
@@ -1328,7 +1358,13 @@ int guide_learned_train_step(wfpg_mlp* s, const float* pos, const float* nrm, ui
         oa.d3t = s->d3t;
         oa.loss = s->loss;
         oa.status = s->status;
-        WFPG_LAUNCH(k_out_train, div_up(n, 128), kOutThreads, kOutSmemBytes, st, oa);
+        // TMA maps: H3 tiles of 128 rows, W4 row blocks and W4^T column blocks of 64 x 64
+        alignas(64) CUtensorMap mh, mw, mwt;
+        if (tensor_map(&mh, s->h3, kHid, N, kHid, 128) && tensor_map(&mw, s->w4, kHid, kOut, kHid, 64) &&
+            tensor_map(&mwt, s->w4t, kOut, kHid, kOut, 64))
+            WFPG_LAUNCH(k_out_train, div_up(n, 128), kOutThreads, kOutSmemBytes + 1024, st, mh, mw, mwt, oa);
+        else
+            g_gemm_failed = true;
     }
     // [dW4 | db4] = G4^T [H3 | 1] (split-K over the batch; H3^T carries a row of ones)
     GemmArgs g = gargs(s->g4t, lt, s->h3t, lt, kOut, kTRows, N, s->status);
