@@ -51,11 +51,24 @@ struct TraceArgs {
     int flat;             // 1: the index and the bitmaps give every cell's deepest level directly
 };
 
+// depth D and index depth G of the SVO: compile-time constants in a kernel
+// specialised on the depth (kD > 0; the index then covers levels 0 .. min(kD, 6)),
+// else read from T
+template <int kD>
+__device__ __forceinline__ int svo_depth(const TraceArgs& T) {
+    return kD > 0 ? kD : T.D;
+}
+template <int kD>
+__device__ __forceinline__ int index_depth(const TraceArgs& T) {
+    return kD > 0 ? (kD < kTopLevelMax ? kD : kTopLevelMax) : T.G;
+}
+
 // offset of level l's grid in the top index: 8^0 + ... + 8^(l-1) = (8^l - 1) / 7
 __device__ __forceinline__ uint32_t top_offset(int l) { return ((1u << (3 * l)) - 1u) / 7u; }
 // the top index's entry of leaf cell (cx, cy, cz) at level l: (level << 28) | node
+template <int kD = 0>
 __device__ __forceinline__ uint32_t top_entry(const TraceArgs& T, int l, int cx, int cy, int cz) {
-    const int sh = T.D - l;
+    const int sh = svo_depth<kD>(T) - l;
     const uint32_t i = ((uint32_t)(cz >> sh) << (2 * l)) | ((uint32_t)(cy >> sh) << l) | (uint32_t)(cx >> sh);
     return __ldg(T.top + top_offset(l) + i);
 }
@@ -73,27 +86,29 @@ __device__ __forceinline__ uint32_t spread3_10(uint32_t v) {
 // when the index and the bitmaps cover every level (T.flat): the index gives
 // it down to level G, one bit per deeper level the rest; the loads are
 // independent of one another.
+template <int kD = 0>
 __device__ __forceinline__ int deepest_level(const TraceArgs& T, int cx, int cy, int cz) {
-    const int sh = T.D - T.G;
+    const int D = svo_depth<kD>(T), G = index_depth<kD>(T);
+    const int sh = D - G;
     const uint32_t ti =
-        ((uint32_t)(cz >> sh) << (2 * T.G)) | ((uint32_t)(cy >> sh) << T.G) | (uint32_t)(cx >> sh);
+        ((uint32_t)(cz >> sh) << (2 * G)) | ((uint32_t)(cy >> sh) << G) | (uint32_t)(cx >> sh);
     const int L0 = (int)(__ldg(T.top + T.top_offG + ti) >> 28);
     // the Morton key (x bits at 3i, y at 3i + 1, z at 3i + 2) of the leaf cell; D <= 9
     const uint32_t key = spread3_10((uint32_t)cx) | (spread3_10((uint32_t)cy) << 1) | (spread3_10((uint32_t)cz) << 2);
     uint32_t w[kOccMaxDepth - kTopLevelMax];
 #pragma unroll
     for (int j = 0; j < kOccMaxDepth - kTopLevelMax; ++j) {
-        const int l = T.G + 1 + j;
+        const int l = G + 1 + j;
         w[j] = 0u;
-        if (l <= T.D) w[j] = __ldg(T.occ + T.occ_off[j] + ((key >> (3 * (T.D - l))) >> 5));
+        if (l <= D) w[j] = __ldg(T.occ + T.occ_off[j] + ((key >> (3 * (D - l))) >> 5));
     }
-    if (L0 < T.G) return L0;
-    int L = T.G;
+    if (L0 < G) return L0;
+    int L = G;
 #pragma unroll
     for (int j = 0; j < kOccMaxDepth - kTopLevelMax; ++j) {
-        const int l = T.G + 1 + j;
-        if (l > T.D || L != l - 1) break;
-        if ((w[j] >> ((key >> (3 * (T.D - l))) & 31u)) & 1u) L = l;
+        const int l = G + 1 + j;
+        if (l > D || L != l - 1) break;
+        if ((w[j] >> ((key >> (3 * (D - l))) & 31u)) & 1u) L = l;
     }
     return L;
 }
@@ -143,12 +158,14 @@ __device__ __forceinline__ Node load_node(const TraceArgs& T, const Node* s_node
 
 // the node at level l (>= G) holding leaf cell (cx, cy, cz), which must exist:
 // from the index's node at level G, descending l - G levels
+template <int kD = 0>
 __device__ __forceinline__ uint32_t node_at_level(const TraceArgs& T, const Node* s_nodes, int l, int cx, int cy,
                                                   int cz) {
-    uint32_t node = top_entry(T, T.G, cx, cy, cz) & kTopNodeMask;
-    for (int lv = T.G; lv < l; ++lv) {
+    const int D = svo_depth<kD>(T), G = index_depth<kD>(T);
+    uint32_t node = top_entry<kD>(T, G, cx, cy, cz) & kTopNodeMask;
+    for (int lv = G; lv < l; ++lv) {
         const Node nd = load_node(T, s_nodes, node);
-        const int sh = T.D - 1 - lv;
+        const int sh = D - 1 - lv;
         const int k = ((cx >> sh) & 1) | (((cy >> sh) & 1) << 1) | (((cz >> sh) & 1) << 2);
         node = child_id(nd, k);
     }
@@ -370,12 +387,14 @@ __device__ __forceinline__ bool ray_start(const TraceArgs& T, bool has_origin, b
 // leaf, and that node's value on the side facing back along the ray.  an_path:
 // the ancestor at the chosen level when it lies on the caller's node path at or
 // below G (only used without the flat index).
+template <int kD = 0>
 __device__ __forceinline__ float hit_value(const TraceArgs& T, const Node* s_nodes, float t, int cx, int cy, int cz,
                                            float dx, float dy, float dz, const uint32_t* stk, int stride) {
+    const int D = svo_depth<kD>(T), G = index_depth<kD>(T);
     const float A = __fmul_rn(__fmul_rn(t, t), T.omega);
     float side = T.S, bd = __int_as_float(0x7f800000);
     int best = 0;
-    for (int l = 0; l <= T.D; ++l) {
+    for (int l = 0; l <= D; ++l) {
         const float diff = fabsf(__fsub_rn(__fmul_rn(side, side), A));
         if (diff <= bd) {
             bd = diff;
@@ -384,8 +403,8 @@ __device__ __forceinline__ float hit_value(const TraceArgs& T, const Node* s_nod
         side = __fmul_rn(side, 0.5f);
     }
     // the hit leaf's ancestor at that level: the top index, else the node path (or a short descent)
-    const uint32_t an = best < T.G ? (top_entry(T, best, cx, cy, cz) & kTopNodeMask)
-                                   : (T.flat ? node_at_level(T, s_nodes, best, cx, cy, cz) : stk[best * stride]);
+    const uint32_t an = best < G ? (top_entry<kD>(T, best, cx, cy, cz) & kTopNodeMask)
+                                   : (T.flat ? node_at_level<kD>(T, s_nodes, best, cx, cy, cz) : stk[best * stride]);
     const float4 Nn = T.normal[an];
     const float2 V = T.value[an];
     const float dd = __fadd_rn(__fadd_rn(__fmul_rn(Nn.x, dx), __fmul_rn(Nn.y, dy)), __fmul_rn(Nn.z, dz));
@@ -398,6 +417,7 @@ constexpr int kHitQueue = 32;  // per-warp queue of hits awaiting their cone que
 constexpr int kHitWords = 6;   // cell, t, leaf cell (10 bits per axis, D <= 9), direction (3)
 
 // the cone queries of queue entries [e0, e0 + n) (n <= 32), one per lane, into out[cell]
+template <int kD = 0>
 __device__ __forceinline__ void flush_hits(const TraceArgs& T, const GuideArgs& G, const Node* s_nodes,
                                            const uint32_t* hq, int e0, int n, int lane, float* out) {
     if (lane < n) {
@@ -408,7 +428,7 @@ __device__ __forceinline__ void flush_hits(const TraceArgs& T, const GuideArgs& 
         const int cx = (int)(c & 1023u), cy = (int)((c >> 10) & 1023u), cz = (int)(c >> 20);
         const float dx = __uint_as_float(hq[3 * kHitQueue + e]), dy = __uint_as_float(hq[4 * kHitQueue + e]),
                     dz = __uint_as_float(hq[5 * kHitQueue + e]);
-        out[q] = __fadd_rn(G.eps, hit_value(T, s_nodes, t, cx, cy, cz, dx, dy, dz, nullptr, 0));
+        out[q] = __fadd_rn(G.eps, hit_value<kD>(T, s_nodes, t, cx, cy, cz, dx, dy, dz, nullptr, 0));
     }
 }
 
@@ -919,7 +939,7 @@ __global__ void __launch_bounds__(kGuideThreads, 1024 / kGuideThreads)
 // different bins.  No barrier holds a warp back at the end of a bin.  eps + L
 // of each cell goes to the bin's pdf row (leaf hits through the warp's queue);
 // k_field_pdf then blurs the rows and builds the PDF and CDFs in place.
-template <int kGuideThreads>
+template <int kGuideThreads, int kD>
 __global__ void __launch_bounds__(kGuideThreads, 1024 / kGuideThreads)
     k_guide_stream(TraceArgs T, GuideArgs G, const float* __restrict__ pos, const uint32_t* __restrict__ origin_ray,
                    const uint32_t* __restrict__ n_bins_dev, uint32_t bin_cap, float* __restrict__ raw,
@@ -930,7 +950,7 @@ __global__ void __launch_bounds__(kGuideThreads, 1024 / kGuideThreads)
     float* wb = reinterpret_cast<float*>(smem) + warp * (kWbWords * 32);
     uint32_t* hq = reinterpret_cast<uint32_t*>(reinterpret_cast<float*>(smem) + (kGuideThreads / 32) * kWbWords * 32) +
                    warp * (kHitQueue * kHitWords);
-    const int N = G.N, NN = N * N, D = T.D;
+    const int N = G.N, NN = N * N, D = svo_depth<kD>(T);
     const uint32_t nb = n_bins_dev ? min(*n_bins_dev, bin_cap) : bin_cap;
     const uint32_t per_bin = (uint32_t)NN / 32u;
     const uint32_t n_batches = nb * per_bin;
@@ -953,7 +973,7 @@ __global__ void __launch_bounds__(kGuideThreads, 1024 / kGuideThreads)
         const uint32_t hm = __ballot_sync(0xffffffffu, pend);
         if (hm) {
             if (hq_n + __popc(hm) > kHitQueue) {
-                flush_hits(T, G, nullptr, hq, 0, hq_n, lane, raw);
+                flush_hits<kD>(T, G, nullptr, hq, 0, hq_n, lane, raw);
                 hq_n = 0;
                 __syncwarp();
             }
@@ -1044,12 +1064,12 @@ __global__ void __launch_bounds__(kGuideThreads, 1024 / kGuideThreads)
             __syncwarp();  // entries are read before a refill overwrites them
         }
         if (dry && __all_sync(0xffffffffu, q < 0)) {
-            if (hq_n > 0) flush_hits(T, G, nullptr, hq, 0, hq_n, lane, raw);
+            if (hq_n > 0) flush_hits<kD>(T, G, nullptr, hq, 0, hq_n, lane, raw);
             break;
         }
         if (q < 0) continue;
         // ---- one step: the cell's deepest existing level, then its hit or the skip of its empty block
-        if (level < 0) level = deepest_level(T, cx, cy, cz);
+        if (level < 0) level = deepest_level<kD>(T, cx, cy, cz);
         bool done = false;
         if (level == D && t >= T.t_skip) {
             pend = true;  // its cone query waits in the warp's queue
@@ -1375,13 +1395,13 @@ static int dispatch_guide(const wfpg_svo* s, const wfpg_guide_params* p, const T
 int field_pdf_impl(const float* field, int N, const uint32_t* n_bins_dev, uint32_t bin_cap, float* pdf,
                    float* cdf_row, float* cdf_marg, cudaStream_t st, int blur);
 
-template <int kThreads>
+template <int kThreads, int kD>
 static int launch_stream(const wfpg_svo* s, const TraceArgs& T0, const GuideArgs& G, const float* pos,
                          const uint32_t* origin_ray, const uint32_t* n_bins_dev, uint32_t bin_cap, float* pdf,
                          float* cdf_row, float* cdf_marg, cudaStream_t st) {
     TraceArgs T = T0;
     T.smem_nodes = 0;  // no node cache: the flat walk reads nodes only below the index
-    auto kernel = k_guide_stream<kThreads>;
+    auto kernel = k_guide_stream<kThreads, kD>;
     const size_t smem = sizeof(float) * (size_t)(kThreads / 32) * kWbWords * 32 +
                         sizeof(uint32_t) * (size_t)(kThreads / 32) * kHitQueue * kHitWords;
     int rc = WFPG_OK;
@@ -1427,9 +1447,17 @@ int guide_build_impl(const wfpg_svo* s, const float* pos, const uint32_t* origin
     trace_setup(s, p, &T, &G, frame_dev);
     if (T.flat && p->parts == 0) {  // flat index: every bin's cone rays as one stream, then the per-bin finish
         const int threads = p->block ? p->block : kGuideDefaultThreadsMid;
-        if (threads == 64) return launch_stream<64>(s, T, G, pos, origin_ray, n_bins_dev, bin_cap, pdf, cdf_row, cdf_marg, st);
-        if (threads == 128) return launch_stream<128>(s, T, G, pos, origin_ray, n_bins_dev, bin_cap, pdf, cdf_row, cdf_marg, st);
-        if (threads == 256) return launch_stream<256>(s, T, G, pos, origin_ray, n_bins_dev, bin_cap, pdf, cdf_row, cdf_marg, st);
+        // the default block size has kernels specialised on the SVO depth 7 .. 9 (constant shifts and loop bounds)
+#define WFPG_STREAM(TH, KD) launch_stream<TH, KD>(s, T, G, pos, origin_ray, n_bins_dev, bin_cap, pdf, cdf_row, cdf_marg, st)
+        if (threads == 128) {
+            if (s->D == 9) return WFPG_STREAM(128, 9);
+            if (s->D == 8) return WFPG_STREAM(128, 8);
+            if (s->D == 7) return WFPG_STREAM(128, 7);
+            return WFPG_STREAM(128, 0);
+        }
+        if (threads == 64) return WFPG_STREAM(64, 0);
+        if (threads == 256) return WFPG_STREAM(256, 0);
+#undef WFPG_STREAM
         return WFPG_ERR_INVALID_ARG;
     }
     if (p->N >= 64 && p->parts == 0) {  // large fields: the march, then the per-bin finish
