@@ -63,6 +63,8 @@ def parse():
     ap.add_argument("--city-train-steps", type=int, default=200, help="online training steps on the city")
     ap.add_argument("--no-mesh", action="store_true", help="skip the triangle-mesh section")
     ap.add_argument("--mesh-only", action="store_true", help="run only the triangle-mesh section and print it")
+    ap.add_argument("--l2-peak-only", action="store_true",
+                    help="print the L2 read bandwidth measured by wfpg_stream_read over a sweep of buffer sizes")
     ap.add_argument("--batched-only", action="store_true",
                     help="run only the batched section with a fixed N = 32 tile (for profiling) and print it")
     return ap.parse_args()
@@ -1163,6 +1165,15 @@ def main():
         import torch
         torch.cuda.set_device(local)
         print(json.dumps(batched_section(args, autotune=False)))
+    elif args.l2_peak_only:
+        import torch
+        torch.cuda.set_device(local)
+        sweep = {}
+        for mib, reps in ((8, 160), (16, 80), (32, 40), (64, 20), (2048, 2)):
+            gbs, how = l2_read_peak(local, mib=mib, reps=reps)
+            sweep[f"{mib}MiB"] = {"GB_s": gbs, "how": how}
+        print(json.dumps({"l2_read_peak": sweep, "note": "buffers up to 64 MiB stay in the 126 MB L2; "
+                          "the 2 GiB buffer streams from HBM"}))
     elif args.impl == "reference":
         run_reference(args, world, rank)
     else:
