@@ -464,6 +464,15 @@ __global__ void k_mean_var(const double* __restrict__ sum, const double* __restr
     if (threadIdx.x == 0) *out = red[0] / (double)P;
 }
 
+// The traced proposal's bins of one depth, split between the two field paths: all of them
+// to the stream path (field tables, then the mixture sample) when they fit its tables, else
+// all of them to the fused GuideRays launch.  The path that gets none does no work.
+__global__ void k_split_bins(const uint32_t* __restrict__ n_bins, uint32_t cap, uint32_t* __restrict__ out) {
+    const uint32_t nb = *n_bins;
+    out[0] = nb <= cap ? nb : 0u;
+    out[1] = nb <= cap ? 0u : nb;
+}
+
 }  // namespace wfpg
 
 using namespace wfpg;
@@ -535,6 +544,12 @@ struct wfpg_frame {
     float* prod_cr = nullptr;
     float* prod_cm = nullptr;        // [product_cap][N]
     float* prod_S = nullptr;         // [product_cap][64]
+    uint32_t trace_cap = 0;          // bins per depth the traced proposal's tables hold (0: fused only)
+    int trace_n = 0;                 // grid side they are sized for
+    float* trace_pdf = nullptr;      // [trace_cap][N^2]
+    float* trace_cr = nullptr;
+    float* trace_cm = nullptr;       // [trace_cap][N]
+    uint32_t* bin_split = nullptr;   // [WFPG_FRAME_MAX_DEPTH + 1][2]: bins of the stream path, of the fused launch
     uint32_t learned_cap = 0;        // bins per depth the learned tables hold
     float* tab_pdf = nullptr;        // [learned_cap][32 * 32]
     float* tab_cr = nullptr;
@@ -554,6 +569,12 @@ struct wfpg_frame {
         allocs.push_back(ptr);
         *out = static_cast<T*>(ptr);
         return true;
+    }
+    void release(void* ptr) {  // free one allocation of this frame (no graph may still use it)
+        if (!ptr) return;
+        auto it = std::find(allocs.begin(), allocs.end(), ptr);
+        if (it != allocs.end()) allocs.erase(it);
+        cudaFree(ptr);
     }
     void drop_graph() {
         if (exec) cudaGraphExecDestroy(exec);
@@ -670,9 +691,26 @@ struct wfpg_frame {
                 wfpg_guide_params gp = p.guide;
                 gp.seed = p.seed;
                 if (p.decay) gp.N = std::max(8, p.guide.N >> k);
-                rc = guide_fused_impl(svo, Q.pos, Q.nrm, origin_ray, n_bins + k, bin_cap, ray_order, bin_offset,
-                                      Q.u, p.alpha, &gp, dir, pdf, P, guide_ws, guide_ws_bytes, st, fidx + k,
-                                      nee ? nee_dir : nullptr, nee ? nee_pm : nullptr);
+                const uint32_t* fused_bins = n_bins + k;
+                if (trace_cap > 0) {
+                    // the stream field kernel into tables, then the mixture sample (bit-identical
+                    // to the fused launch); the fused launch takes over when the bins overflow
+                    uint32_t* split = bin_split + 2 * k;
+                    WFPG_LAUNCH(k_split_bins, 1, 1, 0, st, n_bins + k, trace_cap, split);
+                    rc = guide_build_impl(svo, Q.pos, origin_ray, split, trace_cap, &gp, trace_pdf, trace_cr,
+                                          trace_cm, st, fidx + k);
+                    if (rc == WFPG_OK)
+                        rc = sample_mix_impl(trace_pdf, trace_cr, trace_cm, gp.N, trace_cap, split, bin_of_ray, Q.nrm,
+                                             Q.u, P, counters + k, p.alpha, dir, pdf, st);
+                    if (rc == WFPG_OK && nee)
+                        rc = mix_eval_impl(trace_pdf, gp.N, trace_cap, split, bin_of_ray, Q.nrm, nee_dir, P,
+                                           counters + k, p.alpha, nee_pm, st);
+                    fused_bins = split + 1;
+                }
+                if (rc == WFPG_OK)
+                    rc = guide_fused_impl(svo, Q.pos, Q.nrm, origin_ray, fused_bins, bin_cap, ray_order, bin_offset,
+                                          Q.u, p.alpha, &gp, dir, pdf, P, guide_ws, guide_ws_bytes, st, fidx + k,
+                                          nee ? nee_dir : nullptr, nee ? nee_pm : nullptr);
             }
             if (rc != WFPG_OK) return rc;
             WFPG_LAUNCH(k_shade, g, T, 0, st, F, Q, dir, pdf, stage, flags, k);
@@ -685,6 +723,29 @@ struct wfpg_frame {
         }
         WFPG_LAUNCH(k_frame_end, 1, 1, 0, st, F);
         return launch_status();
+    }
+    // tables for the traced proposal's stream path, allocated outside any capture (kept for the
+    // frame's lifetime): only with the SVO's flat index (top index and occupancy bitmaps), at most
+    // 64M floats per table (65,536 bins at N = 32, 16,384 at 64, 4,096 at 128)
+    bool ensure_trace_tables() {
+        const bool flat = svo->top_levels > 0 && (svo->top_levels - 1 == svo->D || svo->occ != nullptr);
+        if (p.proposal != 0 || !flat || p.guide.parts != 0) return true;
+        const size_t NN = (size_t)p.guide.N * p.guide.N;
+        const uint32_t cap = (uint32_t)std::min<size_t>({(size_t)bin_cap, 65536u, ((size_t)64 << 20) / NN});
+        if (cap <= trace_cap && p.guide.N <= trace_n) return true;
+        release(trace_pdf);
+        release(trace_cr);
+        release(trace_cm);
+        trace_pdf = trace_cr = trace_cm = nullptr;
+        trace_cap = 0;
+        trace_n = 0;
+        if (!alloc(&trace_pdf, cap * NN) || !alloc(&trace_cr, cap * NN) || !alloc(&trace_cm, (size_t)cap * p.guide.N)) {
+            cudaGetLastError();
+            return false;
+        }
+        trace_cap = cap;
+        trace_n = p.guide.N;
+        return true;
     }
     // tables for the product proposal, allocated outside any capture (kept for the frame's lifetime)
     bool ensure_product_tables() {
@@ -799,15 +860,15 @@ int frame_create(wfpg_svo* svo, const wfpg_scene* scene, const float* emission, 
          f->alloc(&f->img_wsum, P) && f->alloc(&f->wsum, 1) &&
          f->alloc(&f->counters, WFPG_FRAME_MAX_DEPTH + 2) && f->alloc(&f->fidx, WFPG_FRAME_MAX_DEPTH + 1) &&
          f->alloc(&f->frame_counter, 1) && f->alloc(&f->frames_run, 1) && f->alloc(&f->guided, 1) &&
-         f->alloc(&f->scalar, 1);
+         f->alloc(&f->scalar, 1) && f->alloc(&f->bin_split, 2 * (WFPG_FRAME_MAX_DEPTH + 1));
     if (!ok) {
         delete f;
         cudaGetLastError();
         return ffail(WFPG_ERR_OOM, "frame_create: device allocation failed");
     }
-    if (!f->ensure_product_tables()) {
+    if (!f->ensure_product_tables() || !f->ensure_trace_tables()) {
         delete f;
-        return ffail(WFPG_ERR_OOM, "frame_create: device allocation of the product tables failed");
+        return ffail(WFPG_ERR_OOM, "frame_create: device allocation of the guiding tables failed");
     }
     if (cam->probe_pos) {
         if (!f->alloc(&f->probe_pos, 3 * (size_t)cam->height) ||
@@ -935,9 +996,9 @@ int frame_set_params(wfpg_frame* f, const wfpg_frame_params* p) {
     f->drop_graph();
     const wfpg_frame_params old = f->p;
     f->p = *p;
-    if (!f->ensure_product_tables()) {
+    if (!f->ensure_product_tables() || !f->ensure_trace_tables()) {
         f->p = old;
-        return ffail(WFPG_ERR_OOM, "frame_set_params: device allocation of the product tables failed");
+        return ffail(WFPG_ERR_OOM, "frame_set_params: device allocation of the guiding tables failed");
     }
     return WFPG_OK;
 }
