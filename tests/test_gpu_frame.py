@@ -183,6 +183,26 @@ def test_frame_guiding_equals_standalone_calls():
     assert np.all(np.diff(qpath.astype(np.int64)) > 0)
 
 
+@pytest.mark.parametrize("N,width,height,c_ray,overflow", [(32, 160, 90, 64, False), (128, 640, 360, 8, True)])
+def test_both_field_paths_of_the_frame_equal_the_fused_call(N, width, height, c_ray, overflow):
+    """The frame's traced proposal runs the stream field kernel into tables and the mixture
+    sampler while a depth's bins fit those tables (4,096 bins at N = 128), the fused GuideRays
+    launch when they do not; both give the standalone fused call's directions and densities."""
+    w, g, _ = box_svo(3)
+    f = make_frame(g, w.scene, max_depth=1, update=False, N=N, c_ray=c_ray, width=width, height=height)
+    f.run(1, use_graph=False)
+    st = f.stats()
+    n, nb = st["paths"][0], st["bins"][0]
+    assert n > 0
+    assert (nb > 4096) == overflow, nb
+    qp, qn, qu = (f.export(k)[:n].contiguous() for k in ("q_pos", "q_nrm", "q_u"))
+    r = W.bin_rays(g, qp, qn, l_min=2, c_ray=c_ray, seed=3, frame=0, bin_cap=min(f.pixels, g.n_nodes))
+    d, pm = W.guide_build_sample(g, qp, qn, r, qu, alpha=0.5, N=N, jitter=True, blur=True, seed=3, frame=0)
+    assert torch.equal(f.export("q_dir")[:n], d)
+    assert torch.equal(f.export("q_pdf")[:n], pm)
+    assert st["status"] == 0
+
+
 def test_graph_replay_equals_eager():
     w, g1, _ = box_svo(5)
     _, g2, _ = box_svo(5)
