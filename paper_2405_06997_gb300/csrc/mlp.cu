@@ -521,64 +521,6 @@ __global__ void __launch_bounds__(kHidThreads, 4) k_mlp_hidden(HiddenArgs a) {
     if (warp == 0) tc::tmem_dealloc(tmem, 64);
 }
 
-// one warp per row of 1024 logits: softmax; inference writes the field
-// softmax + eps, training writes G = (softmax - q) / n (bf16) and the KL
-__global__ void k_softmax_rows(const float* __restrict__ Z, uint32_t rows, const uint32_t* __restrict__ n_dev,
-                               float eps, float* __restrict__ field, const float* __restrict__ target,
-                               float inv_n, bf16* __restrict__ G, float* __restrict__ loss) {
-    const uint32_t row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (row >= rows) return;
-    const uint32_t nvalid = n_dev ? min(*n_dev, rows) : rows;
-    const float* z = Z + (size_t)row * kOut;
-    float v[32];
-    float m = -3.4e38f;
-#pragma unroll
-    for (int k = 0; k < 32; ++k) {
-        v[k] = z[k * 32 + lane];
-        m = fmaxf(m, v[k]);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-    float s = 0.0f;
-#pragma unroll
-    for (int k = 0; k < 32; ++k) {
-        v[k] = v[k] - m;
-        s += expf(v[k]);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    const float inv_s = 1.0f / s, log_s = logf(s);
-    if (!target) {
-#pragma unroll
-        for (int k = 0; k < 32; ++k) field[(size_t)row * kOut + k * 32 + lane] = expf(v[k]) * inv_s + eps;
-        (void)nvalid;
-        return;
-    }
-    const float* t = target + (size_t)row * kOut;
-    float tv[32], ts = 0.0f;
-#pragma unroll
-    for (int k = 0; k < 32; ++k) {
-        tv[k] = t[k * 32 + lane];
-        ts += tv[k];
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) ts += __shfl_xor_sync(0xffffffffu, ts, o);
-    const float inv_t = ts > 0.0f ? 1.0f / ts : 0.0f;
-    float kl = 0.0f;
-#pragma unroll
-    for (int k = 0; k < 32; ++k) {
-        const float q = tv[k] * inv_t;
-        const float logp = v[k] - log_s;
-        if (q > 0.0f) kl += q * (logf(q) - logp);
-        G[(size_t)row * kOut + k * 32 + lane] = __float2bfloat16_rn((expf(logp) - q) * inv_n);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) kl += __shfl_xor_sync(0xffffffffu, kl, o);
-    if (lane == 0) atomicAdd(loss, kl * inv_n);
-}
-
-
 // The sum over the K splits of a [M][ncols] weight-and-bias gradient (a block
 // covers 32 outputs, its 8 warps take every 8th split, the 8 partial sums are
 // added in warp order: deterministic): column c < wcols of row m goes to
@@ -954,6 +896,161 @@ __global__ void __launch_bounds__(kOutThreads, 4)
     if (warp == 0) tc::tmem_dealloc(tmem, kOutTmemCols);
 }
 
+// ---------------------------------------------------------------------------
+// The output layer of an inference, fused: for one 128-row tile the logits
+// Z = H3 W4^T + b4 are computed 64 at a time on the tensor cores into tensor
+// memory and never stored.  Pass 1 keeps each row's running maximum and base-2
+// exponential sum (u = Z log2 e); pass 2 recomputes every chunk and writes the
+// field softmax(Z) + eps = 2^(u - S) + eps, S the base-2 log of the softmax
+// denominator.  The logits MMAs of both passes run as one pipeline of 32 chunks,
+// double-buffered in TMEM (columns 0 and 64) and in shared memory (two W4 row
+// blocks by TMA).  256 threads, four CTAs per SM: warp w reads TMEM lanes
+// 32 (w % 4) .. + 31 and handles columns 32 (w / 4) .. + 31 of each chunk.
+constexpr int kInferSmemH = 0, kInferSmemW0 = 16384, kInferSmemW1 = 24576, kInferSmemB = 32768,
+              kInferSmemStat = kInferSmemB + 4 * kOut;
+constexpr int kInferSmemBytes = kInferSmemStat + 2 * 2 * 128 * 4;
+
+struct InferArgs {
+    const float* b4;   // [1024]
+    int n;             // rows
+    float eps;
+    float* field;      // [n][1024]: softmax + eps
+    uint32_t* status;
+};
+
+__global__ void __launch_bounds__(kOutThreads, 4)
+    k_out_infer(const __grid_constant__ CUtensorMap tma_h3, const __grid_constant__ CUtensorMap tma_w4, InferArgs a) {
+    extern __shared__ __align__(1024) uint8_t inf_smem_raw[];
+    // the TMA tiles (128-byte swizzled) need 1024-byte alignment (the launch adds 1 KB of slack)
+    uint8_t* sm = inf_smem_raw + ((1024u - (tc::smem_addr(inf_smem_raw) & 1023u)) & 1023u);
+    uint8_t* sH = sm + kInferSmemH;                       // H3 tile: 128 x 64
+    auto sW = [sm](int b) { return sm + (b ? kInferSmemW1 : kInferSmemW0); };  // W4 rows for logits buffer b
+    float* sbl = reinterpret_cast<float*>(sm + kInferSmemB);    // b4 log2 e
+    float* s_st = reinterpret_cast<float*>(sm + kInferSmemStat);  // [m, s][2 column halves][128 rows]
+    __shared__ __align__(8) uint64_t mbar[2];  // MMA completion: logits buffer 0 / 1
+    __shared__ __align__(8) uint64_t tbar[3];  // TMA completion: W4 buffer 0 / 1, H3
+    __shared__ uint32_t tmem_base;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int quad = warp & 3, half = warp >> 2;
+    const int r = quad * 32 + lane;  // tile row of this thread
+    const int m0 = blockIdx.x * 128, row = m0 + r;
+    const int k0 = half * 32;
+    constexpr int kSteps = 2 * kOutChunks;  // pass 1 then pass 2, chunk it % 16
+    uint32_t tph = 0, tpend = 0;            // thread 0: parity of each TMA barrier's next phase, copies in flight
+    bool tok = true;
+    auto tma_w = [&](int bi, int c) {
+        tc::mbar_expect_tx(&tbar[bi], 64 * 64 * 2);
+        tc::tma_load_2d(sW(bi), &tma_w4, 0, c * kOutChunk, &tbar[bi]);
+        tpend |= 1u << bi;
+    };
+    auto tma_done = [&](int bi) {
+        tok = tc::mbar_wait(&tbar[bi], (tph >> bi) & 1u) && tok;
+        tph ^= 1u << bi;
+        tpend &= ~(1u << bi);
+    };
+    if (warp == 0) tc::tmem_alloc(&tmem_base, kOutTmemCols);
+    if (tid == 0) {
+        tc::mbar_init(&mbar[0], 1);
+        tc::mbar_init(&mbar[1], 1);
+        for (int i = 0; i < 3; ++i) tc::mbar_init(&tbar[i], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        tc::mbar_expect_tx(&tbar[2], 128 * 64 * 2);
+        tc::tma_load_2d(sH, &tma_h3, 0, m0, &tbar[2]);  // rows past n read zero
+        tpend |= 1u << 2;
+        tma_w(0, 0);
+        tma_w(1, 1);
+    }
+    for (int i = tid; i < kOut; i += kOutThreads) sbl[i] = a.b4[i] * kLog2e;
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = tmem_base;
+    const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16);
+    constexpr uint32_t idesc = tc::idesc_bf16_f32(128, 64);
+    auto mma_z = [&](int buf) {  // logits of the chunk in W4 buffer buf into TMEM columns 64 buf
+        const uint32_t a0 = tc::smem_addr(sH), b0 = tc::smem_addr(sW(buf));
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+            tc::mma_bf16(tmem + 64 * buf, tc::smem_desc_sw128(a0 + s * 32), tc::smem_desc_sw128(b0 + s * 32), idesc,
+                         s > 0 ? 1u : 0u);
+        tc::mma_commit(&mbar[buf]);
+    };
+    if (tid == 0) {
+        tma_done(2);
+        tma_done(0);
+        mma_z(0);
+        tma_done(1);
+        mma_z(1);
+    }
+    uint32_t phase = 0;  // bit i: parity of mbar[i]'s next phase
+    bool ok = true;
+    float mrun = -3.0e38f, srun = 0.0f, S = 0.0f;
+    const bool live = row < a.n;
+    for (int it = 0; it < kSteps && ok; ++it) {
+        const int buf = it & 1, c = it % kOutChunks;
+        ok = __syncthreads_and(tc::mbar_wait(&mbar[buf], (phase >> buf) & 1u) && tok) != 0;
+        phase ^= 1u << buf;
+        tc::fence_after_sync();
+        if (!ok) break;
+        if (tid == 0 && it + 2 < kSteps) tma_w(buf, (it + 2) % kOutChunks);  // the MMA has read the buffer
+        if (it == kOutChunks) {  // both halves' statistics were exchanged at the end of pass 1
+            const float ma = s_st[r], mb = s_st[128 + r];
+            const float m = fmaxf(ma, mb);
+            S = m + lg2_approx(s_st[256 + r] * ex2_approx(ma - m) + s_st[384 + r] * ex2_approx(mb - m));
+        }
+#pragma unroll
+        for (int g = 0; g < 2; ++g) {
+            float v[16];
+            tc::tmem_ld16(lane_base + (uint32_t)(64 * buf + k0 + g * 16), v);
+            const float4* bq = reinterpret_cast<const float4*>(sbl + c * kOutChunk + k0 + g * 16);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const float4 b = bq[i];
+                v[4 * i + 0] = fmaf(v[4 * i + 0], kLog2e, b.x);
+                v[4 * i + 1] = fmaf(v[4 * i + 1], kLog2e, b.y);
+                v[4 * i + 2] = fmaf(v[4 * i + 2], kLog2e, b.z);
+                v[4 * i + 3] = fmaf(v[4 * i + 3], kLog2e, b.w);
+            }
+            if (it < kOutChunks) {
+                float gm = -3.0e38f;
+#pragma unroll
+                for (int i = 0; i < 16; ++i) gm = fmaxf(gm, v[i]);
+                if (gm > mrun) {
+                    srun *= ex2_approx(mrun - gm);
+                    mrun = gm;
+                }
+#pragma unroll
+                for (int i = 0; i < 16; ++i) srun += ex2_approx(v[i] - mrun);
+            } else if (live) {
+                float4* fp = reinterpret_cast<float4*>(a.field + (size_t)row * kOut + c * kOutChunk + k0 + g * 16);
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    fp[i] = make_float4(ex2_approx(v[4 * i] - S) + a.eps, ex2_approx(v[4 * i + 1] - S) + a.eps,
+                                        ex2_approx(v[4 * i + 2] - S) + a.eps, ex2_approx(v[4 * i + 3] - S) + a.eps);
+            }
+        }
+        if (it == kOutChunks - 1) {
+            s_st[half * 128 + r] = mrun;
+            s_st[256 + half * 128 + r] = srun;
+        }
+        tc::fence_before_sync();
+        __syncthreads();  // the logits have been read (and the statistics exchanged)
+        tc::fence_after_sync();
+        if (tid == 0 && it + 2 < kSteps) {
+            tma_done(buf);  // the W4 rows of step it + 2
+            mma_z(buf);
+        }
+    }
+    if (tid == 0) {  // after a timeout, let the copies in flight land before the CTA exits
+        for (int bi = 0; bi < 3; ++bi)
+            if (tpend & (1u << bi)) tma_done(bi);
+    }
+    if (!ok && lane == 0) atomicOr(a.status, (uint32_t)WFPG_STATUS_MMA_TIMEOUT);
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, kOutTmemCols);
+}
+
 // Adam (Kingma & Ba 2015) on the float32 master weights
 __global__ void k_adam(float* __restrict__ w, float* __restrict__ m, float* __restrict__ v,
                        const float* __restrict__ grad, uint32_t n, float lr, float b1, float b2, float eps, float c1,
@@ -1285,9 +1382,14 @@ int guide_learned_build_pdf(wfpg_mlp* s, const float* pos, const float* nrm, con
     if (bin_cap == 0) return WFPG_OK;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     hidden(s, pos, nrm, origin_ray, n_bins_dev, bin_cap, p, false, st);
-    output_logits(s, (int)bin_cap, st);
-    WFPG_LAUNCH(k_softmax_rows, div_up((uint64_t)bin_cap * 32, 256), 256, 0, st, s->z, bin_cap, n_bins_dev, p->eps,
-                s->field, (const float*)nullptr, 0.0f, (bf16*)nullptr, (float*)nullptr);
+    // the output layer fused with the softmax: field = softmax(logits) + eps, no logits stored
+    alignas(64) CUtensorMap mh, mw;
+    if (tensor_map(&mh, s->h3, kHid, (int)bin_cap, kHid, 128) && tensor_map(&mw, s->w4, kHid, kOut, kHid, 64)) {
+        InferArgs ia{s->params + kOffB4, (int)bin_cap, p->eps, s->field, s->status};
+        WFPG_LAUNCH(k_out_infer, div_up(bin_cap, 128), kOutThreads, kInferSmemBytes + 1024, st, mh, mw, ia);
+    } else {
+        g_gemm_failed = true;
+    }
     if (wfpg::field_pdf_impl(s->field, 32, n_bins_dev, bin_cap, pdf, cdf_row, cdf_marg, st) != WFPG_OK ||
         cudaGetLastError() != cudaSuccess || gemm_failed())
         return mlp_fail(WFPG_ERR_CUDA, "guide_learned_build_pdf: launch failed");
