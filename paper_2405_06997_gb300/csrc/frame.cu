@@ -382,32 +382,48 @@ __global__ void __launch_bounds__(256) k_shade(FrameView F, Queue Q, const float
 
 // Eq. 5 for every vertex of every path, back to front: the suffix sum
 // S_k = sum_{n >= k} T_n Le_n gives L_k = S_k / T_k; S_1 is the path estimate.
-// The record array is compact in any order: per vertex depth, each warp
-// reserves one contiguous run for its lanes that have that vertex (one atomic
-// per warp and depth), so every store instruction writes one run.
+// The record array is compact in any order: each CTA reserves one run for all
+// its records (one atomic per CTA), its warps take consecutive parts of it, and
+// per vertex depth a warp's lanes that have that vertex write one contiguous
+// piece, so every store instruction writes one run.
 __global__ void __launch_bounds__(256) k_records(FrameView F, float* __restrict__ rec_pos,
                                                  float* __restrict__ rec_wout, float* __restrict__ rec_L,
                                                  uint32_t* __restrict__ rec_src) {
+    __shared__ uint32_t s_warp[8], s_base;
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    const uint32_t lane = threadIdx.x & 31, lt = (1u << lane) - 1u;
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, lt = (1u << lane) - 1u;
     const int n = i < F.P ? (int)F.nv[i] : 0;
-    int nmax = n;
-    for (int o = 16; o > 0; o >>= 1) nmax = max(nmax, __shfl_xor_sync(0xffffffffu, nmax, o));
+    int nmax = n, wtot = n;
+    for (int o = 16; o > 0; o >>= 1) {
+        nmax = max(nmax, __shfl_xor_sync(0xffffffffu, nmax, o));
+        wtot += __shfl_xor_sync(0xffffffffu, wtot, o);
+    }
+    if (lane == 0) s_warp[warp] = (uint32_t)wtot;
+    __syncthreads();
+    if (threadIdx.x == 0) {  // the CTA's run, then each warp's part of it
+        uint32_t tot = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            const uint32_t c = s_warp[w];
+            s_warp[w] = tot;
+            tot += c;
+        }
+        s_base = tot ? atomicAdd(&F.counters[WFPG_FRAME_MAX_DEPTH + 1], tot) : 0u;
+    }
+    __syncthreads();
+    uint32_t base = s_base + s_warp[warp];
     // S: what the vertices after v contribute, as v sees them; Sv: v's own record (with NEE a
     // vertex's record holds its full emission, the vertex before it the MIS-weighted share)
     float S = 0.0f, Sv = 0.0f;
     for (int v = nmax - 1; v >= 0; --v) {
         const bool has = v < n;
         const uint32_t m = __ballot_sync(0xffffffffu, has);
-        uint32_t base = 0;
-        if (lane == (uint32_t)(__ffs(m) - 1)) base = atomicAdd(&F.counters[WFPG_FRAME_MAX_DEPTH + 1], __popc(m));
-        base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
+        const uint32_t r = base + __popc(m & lt);
+        base += __popc(m);
         if (!has) continue;
         const size_t e = (size_t)v * F.P + i;
         const float T = F.vT[e];
         Sv = S + T * (F.nee ? F.vLe[e] + F.vNee[e] : F.vLe[e]);
         S = F.nee ? S + T * (F.vLw[e] + F.vNee[e]) : Sv;
-        const uint32_t r = base + __popc(m & lt);
         rec_pos[3 * (size_t)r] = F.vpos[3 * e];
         rec_pos[3 * (size_t)r + 1] = F.vpos[3 * e + 1];
         rec_pos[3 * (size_t)r + 2] = F.vpos[3 * e + 2];
