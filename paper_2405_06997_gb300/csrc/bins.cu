@@ -27,15 +27,21 @@ __global__ void __launch_bounds__(256) k_bin_descend(const Node* __restrict__ no
                                                      const uint32_t* __restrict__ n_dev, uint32_t* __restrict__ ray_node,
                                                      uint32_t* __restrict__ count) {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= ray_count(n, n_dev)) return;
-    int c[3];
-    c[0] = grid_index(pos[3 * (size_t)i + 0], lox, scale, D);
-    c[1] = grid_index(pos[3 * (size_t)i + 1], loy, scale, D);
-    c[2] = grid_index(pos[3 * (size_t)i + 2], loz, scale, D);
-    int lvl;
-    const uint32_t nd = descend(nodes, c, D, &lvl);
-    ray_node[i] = nd;
-    atomicAdd(&count[nd], 1u);
+    const bool valid = i < ray_count(n, n_dev);
+    uint32_t nd = 0xffffffffu;
+    if (valid) {
+        int c[3];
+        c[0] = grid_index(pos[3 * (size_t)i + 0], lox, scale, D);
+        c[1] = grid_index(pos[3 * (size_t)i + 1], loy, scale, D);
+        c[2] = grid_index(pos[3 * (size_t)i + 2], loz, scale, D);
+        int lvl;
+        nd = descend(nodes, c, D, &lvl);
+        ray_node[i] = nd;
+    }
+    // neighbouring rays mostly share a node: one atomic per distinct node of the warp
+    const uint32_t peers = __match_any_sync(0xffffffffu, nd);
+    const uint32_t lane = threadIdx.x & 31u;
+    if (valid && lane == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&count[nd], (uint32_t)__popc(peers));
 }
 
 // one level of the bottom-up ray totals; bit 31 marks the node
