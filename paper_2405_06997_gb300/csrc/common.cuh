@@ -79,8 +79,9 @@ __device__ __forceinline__ int grid_index(float x, float lo, float scale, int D)
 // deepest level of the SVO's top index (a dense grid per level 0 .. this)
 constexpr int kTopLevelMax = 6;
 constexpr uint32_t kTopNodeMask = (1u << 28) - 1u;
-// deepest SVO for which every level below the top index has an occupancy bitmap
-constexpr int kOccMaxDepth = 9;
+// deepest SVO for which every level below the top index has an occupancy bitmap (8^l bits per
+// level l: 1.2 GB in all at depth 11)
+constexpr int kOccMaxDepth = 11;
 // word offset of level l's bitmap when levels g + 1 .. l - 1 precede it (8^j bits each, j > 6)
 __host__ __device__ __forceinline__ uint64_t occ_offset(int g, int l) {
     uint64_t o = 0;

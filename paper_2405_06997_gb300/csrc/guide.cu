@@ -17,6 +17,8 @@
 // that crossing (crossings earlier in (time, axis) order).
 #include <algorithm>
 
+#include <type_traits>
+
 #include "common.cuh"
 #include "march.cuh"
 #include "sort.cuh"
@@ -82,6 +84,17 @@ __device__ __forceinline__ uint32_t spread3_10(uint32_t v) {
     return v;
 }
 
+// bits 0 .. 20 of v moved to bits 0, 3, 6, ..., 60 (the 64-bit Morton key of depths 10 and 11)
+__device__ __forceinline__ uint64_t spread3_21(uint32_t v) {
+    uint64_t x = v & 0x1fffffu;
+    x = (x | (x << 32)) & 0x001f00000000ffffull;
+    x = (x | (x << 16)) & 0x001f0000ff0000ffull;
+    x = (x | (x << 8)) & 0x100f00f00f00f00full;
+    x = (x | (x << 4)) & 0x10c30c30c30c30c3ull;
+    x = (x | (x << 2)) & 0x1249249249249249ull;
+    return x;
+}
+
 // Deepest level holding an existing node that contains leaf cell (cx, cy, cz),
 // when the index and the bitmaps cover every level (T.flat): the index gives
 // it down to level G, one bit per deeper level the rest; the loads are
@@ -93,14 +106,20 @@ __device__ __forceinline__ int deepest_level(const TraceArgs& T, int cx, int cy,
     const uint32_t ti =
         ((uint32_t)(cz >> sh) << (2 * G)) | ((uint32_t)(cy >> sh) << G) | (uint32_t)(cx >> sh);
     const int L0 = (int)(__ldg(T.top + T.top_offG + ti) >> 28);
-    // the Morton key (x bits at 3i, y at 3i + 1, z at 3i + 2) of the leaf cell; D <= 9
-    const uint32_t key = spread3_10((uint32_t)cx) | (spread3_10((uint32_t)cy) << 1) | (spread3_10((uint32_t)cz) << 2);
+    // the Morton key (x bits at 3i, y at 3i + 1, z at 3i + 2) of the leaf cell: 32 bits up to
+    // depth 10, 64 bits beyond (and when the depth is known only at run time)
+    using Key = typename std::conditional<(kD > 0 && kD <= 10), uint32_t, uint64_t>::type;
+    Key key;
+    if constexpr (kD > 0 && kD <= 10)
+        key = spread3_10((uint32_t)cx) | (spread3_10((uint32_t)cy) << 1) | (spread3_10((uint32_t)cz) << 2);
+    else
+        key = spread3_21((uint32_t)cx) | (spread3_21((uint32_t)cy) << 1) | (spread3_21((uint32_t)cz) << 2);
     uint32_t w[kOccMaxDepth - kTopLevelMax];
 #pragma unroll
     for (int j = 0; j < kOccMaxDepth - kTopLevelMax; ++j) {
         const int l = G + 1 + j;
         w[j] = 0u;
-        if (l <= D) w[j] = __ldg(T.occ + T.occ_off[j] + ((key >> (3 * (D - l))) >> 5));
+        if (l <= D) w[j] = __ldg(T.occ + T.occ_off[j] + (uint32_t)((key >> (3 * (D - l))) >> 5));
     }
     if (L0 < G) return L0;
     int L = G;
@@ -108,7 +127,7 @@ __device__ __forceinline__ int deepest_level(const TraceArgs& T, int cx, int cy,
     for (int j = 0; j < kOccMaxDepth - kTopLevelMax; ++j) {
         const int l = G + 1 + j;
         if (l > D || L != l - 1) break;
-        if ((w[j] >> ((key >> (3 * (D - l))) & 31u)) & 1u) L = l;
+        if ((w[j] >> (uint32_t)((key >> (3 * (D - l))) & 31u)) & 1u) L = l;
     }
     return L;
 }
@@ -414,7 +433,7 @@ __device__ __forceinline__ float hit_value(const TraceArgs& T, const Node* s_nod
 }
 
 constexpr int kHitQueue = 32;  // per-warp queue of hits awaiting their cone query (flat index only)
-constexpr int kHitWords = 6;   // cell, t, leaf cell (10 bits per axis, D <= 9), direction (3)
+constexpr int kHitWords = 7;   // cell, t, leaf cell (x | y << 16, then z; D <= 11), direction (3)
 
 // the cone queries of queue entries [e0, e0 + n) (n <= 32), one per lane, into out[cell]
 template <int kD = 0>
@@ -425,9 +444,9 @@ __device__ __forceinline__ void flush_hits(const TraceArgs& T, const GuideArgs& 
         const int q = (int)hq[0 * kHitQueue + e];
         const float t = __uint_as_float(hq[1 * kHitQueue + e]);
         const uint32_t c = hq[2 * kHitQueue + e];
-        const int cx = (int)(c & 1023u), cy = (int)((c >> 10) & 1023u), cz = (int)(c >> 20);
-        const float dx = __uint_as_float(hq[3 * kHitQueue + e]), dy = __uint_as_float(hq[4 * kHitQueue + e]),
-                    dz = __uint_as_float(hq[5 * kHitQueue + e]);
+        const int cx = (int)(c & 0xffffu), cy = (int)(c >> 16), cz = (int)hq[3 * kHitQueue + e];
+        const float dx = __uint_as_float(hq[4 * kHitQueue + e]), dy = __uint_as_float(hq[5 * kHitQueue + e]),
+                    dz = __uint_as_float(hq[6 * kHitQueue + e]);
         out[q] = __fadd_rn(G.eps, hit_value<kD>(T, s_nodes, t, cx, cy, cz, dx, dy, dz, nullptr, 0));
     }
 }
@@ -512,10 +531,11 @@ __device__ __forceinline__ void march_chunk(const TraceArgs& T, const GuideArgs&
                     const int e = hq_n + __popc(hm & lt);
                     hq[0 * kHitQueue + e] = (uint32_t)q;
                     hq[1 * kHitQueue + e] = __float_as_uint(t);
-                    hq[2 * kHitQueue + e] = (uint32_t)cx | ((uint32_t)cy << 10) | ((uint32_t)cz << 20);
-                    hq[3 * kHitQueue + e] = __float_as_uint(dx);
-                    hq[4 * kHitQueue + e] = __float_as_uint(dy);
-                    hq[5 * kHitQueue + e] = __float_as_uint(dz);
+                    hq[2 * kHitQueue + e] = (uint32_t)cx | ((uint32_t)cy << 16);
+                    hq[3 * kHitQueue + e] = (uint32_t)cz;
+                    hq[4 * kHitQueue + e] = __float_as_uint(dx);
+                    hq[5 * kHitQueue + e] = __float_as_uint(dy);
+                    hq[6 * kHitQueue + e] = __float_as_uint(dz);
                     q = -1;
                     pend = false;
                 }
@@ -981,10 +1001,11 @@ __global__ void __launch_bounds__(kGuideThreads, 1024 / kGuideThreads)
                 const int e = hq_n + __popc(hm & lt);
                 hq[0 * kHitQueue + e] = (uint32_t)q;
                 hq[1 * kHitQueue + e] = __float_as_uint(t);
-                hq[2 * kHitQueue + e] = (uint32_t)cx | ((uint32_t)cy << 10) | ((uint32_t)cz << 20);
-                hq[3 * kHitQueue + e] = __float_as_uint(dx);
-                hq[4 * kHitQueue + e] = __float_as_uint(dy);
-                hq[5 * kHitQueue + e] = __float_as_uint(dz);
+                hq[2 * kHitQueue + e] = (uint32_t)cx | ((uint32_t)cy << 16);
+                hq[3 * kHitQueue + e] = (uint32_t)cz;
+                hq[4 * kHitQueue + e] = __float_as_uint(dx);
+                hq[5 * kHitQueue + e] = __float_as_uint(dy);
+                hq[6 * kHitQueue + e] = __float_as_uint(dz);
                 q = -1;
                 pend = false;
             }
@@ -1447,13 +1468,18 @@ int guide_build_impl(const wfpg_svo* s, const float* pos, const uint32_t* origin
     trace_setup(s, p, &T, &G, frame_dev);
     if (T.flat && p->parts == 0) {  // flat index: every bin's cone rays as one stream, then the per-bin finish
         const int threads = p->block ? p->block : kGuideDefaultThreadsMid;
-        // the default block size has kernels specialised on the SVO depth 7 .. 9 (constant shifts and loop bounds)
+        // the default block size has kernels specialised on the SVO depth 6 .. 11 (constant shifts and loop bounds)
 #define WFPG_STREAM(TH, KD) launch_stream<TH, KD>(s, T, G, pos, origin_ray, n_bins_dev, bin_cap, pdf, cdf_row, cdf_marg, st)
         if (threads == 128) {
-            if (s->D == 9) return WFPG_STREAM(128, 9);
-            if (s->D == 8) return WFPG_STREAM(128, 8);
-            if (s->D == 7) return WFPG_STREAM(128, 7);
-            return WFPG_STREAM(128, 0);
+            switch (s->D) {
+                case 6: return WFPG_STREAM(128, 6);
+                case 7: return WFPG_STREAM(128, 7);
+                case 8: return WFPG_STREAM(128, 8);
+                case 9: return WFPG_STREAM(128, 9);
+                case 10: return WFPG_STREAM(128, 10);
+                case 11: return WFPG_STREAM(128, 11);
+                default: return WFPG_STREAM(128, 0);
+            }
         }
         if (threads == 64) return WFPG_STREAM(64, 0);
         if (threads == 256) return WFPG_STREAM(256, 0);
