@@ -84,17 +84,6 @@ __device__ __forceinline__ uint32_t spread3_10(uint32_t v) {
     return v;
 }
 
-// bits 0 .. 20 of v moved to bits 0, 3, 6, ..., 60 (the 64-bit Morton key of depths 10 and 11)
-__device__ __forceinline__ uint64_t spread3_21(uint32_t v) {
-    uint64_t x = v & 0x1fffffu;
-    x = (x | (x << 32)) & 0x001f00000000ffffull;
-    x = (x | (x << 16)) & 0x001f0000ff0000ffull;
-    x = (x | (x << 8)) & 0x100f00f00f00f00full;
-    x = (x | (x << 4)) & 0x10c30c30c30c30c3ull;
-    x = (x | (x << 2)) & 0x1249249249249249ull;
-    return x;
-}
-
 // Deepest level holding an existing node that contains leaf cell (cx, cy, cz),
 // when the index and the bitmaps cover every level (T.flat): the index gives
 // it down to level G, one bit per deeper level the rest; the loads are
@@ -113,7 +102,7 @@ __device__ __forceinline__ int deepest_level(const TraceArgs& T, int cx, int cy,
     if constexpr (kD > 0 && kD <= 10)
         key = spread3_10((uint32_t)cx) | (spread3_10((uint32_t)cy) << 1) | (spread3_10((uint32_t)cz) << 2);
     else
-        key = spread3_21((uint32_t)cx) | (spread3_21((uint32_t)cy) << 1) | (spread3_21((uint32_t)cz) << 2);
+        key = morton3((uint32_t)cx, (uint32_t)cy, (uint32_t)cz);
     uint32_t w[kOccMaxDepth - kTopLevelMax];
 #pragma unroll
     for (int j = 0; j < kOccMaxDepth - kTopLevelMax; ++j) {
