@@ -84,6 +84,26 @@ __device__ __forceinline__ uint32_t spread3_10(uint32_t v) {
     return v;
 }
 
+// the deepest existing level below the index from the bitmaps, with Morton keys of type Key
+template <typename Key>
+__device__ __forceinline__ int bitmap_level(const TraceArgs& T, int D, int G, Key key) {
+    uint32_t w[kOccMaxDepth - kTopLevelMax];
+#pragma unroll
+    for (int j = 0; j < kOccMaxDepth - kTopLevelMax; ++j) {
+        const int l = G + 1 + j;
+        w[j] = 0u;
+        if (l <= D) w[j] = __ldg(T.occ + T.occ_off[j] + (uint32_t)((key >> (3 * (D - l))) >> 5));
+    }
+    int L = G;
+#pragma unroll
+    for (int j = 0; j < kOccMaxDepth - kTopLevelMax; ++j) {
+        const int l = G + 1 + j;
+        if (l > D || L != l - 1) break;
+        if ((w[j] >> (uint32_t)((key >> (3 * (D - l))) & 31u)) & 1u) L = l;
+    }
+    return L;
+}
+
 // Deepest level holding an existing node that contains leaf cell (cx, cy, cz),
 // when the index and the bitmaps cover every level (T.flat): the index gives
 // it down to level G, one bit per deeper level the rest; the loads are
@@ -96,29 +116,16 @@ __device__ __forceinline__ int deepest_level(const TraceArgs& T, int cx, int cy,
         ((uint32_t)(cz >> sh) << (2 * G)) | ((uint32_t)(cy >> sh) << G) | (uint32_t)(cx >> sh);
     const int L0 = (int)(__ldg(T.top + T.top_offG + ti) >> 28);
     // the Morton key (x bits at 3i, y at 3i + 1, z at 3i + 2) of the leaf cell: 32 bits up to
-    // depth 10, 64 bits beyond (and when the depth is known only at run time)
-    using Key = typename std::conditional<(kD > 0 && kD <= 10), uint32_t, uint64_t>::type;
-    Key key;
-    if constexpr (kD > 0 && kD <= 10)
-        key = spread3_10((uint32_t)cx) | (spread3_10((uint32_t)cy) << 1) | (spread3_10((uint32_t)cz) << 2);
-    else
-        key = morton3((uint32_t)cx, (uint32_t)cy, (uint32_t)cz);
-    uint32_t w[kOccMaxDepth - kTopLevelMax];
-#pragma unroll
-    for (int j = 0; j < kOccMaxDepth - kTopLevelMax; ++j) {
-        const int l = G + 1 + j;
-        w[j] = 0u;
-        if (l <= D) w[j] = __ldg(T.occ + T.occ_off[j] + (uint32_t)((key >> (3 * (D - l))) >> 5));
+    // depth 10 (the flat walk of a kernel not specialised on the depth stops there), 64 bits at 11
+    if constexpr (kD > 10) {
+        const uint64_t key = morton3((uint32_t)cx, (uint32_t)cy, (uint32_t)cz);
+        const int L = bitmap_level<uint64_t>(T, D, G, key);
+        return L0 < G ? L0 : L;
     }
-    if (L0 < G) return L0;
-    int L = G;
-#pragma unroll
-    for (int j = 0; j < kOccMaxDepth - kTopLevelMax; ++j) {
-        const int l = G + 1 + j;
-        if (l > D || L != l - 1) break;
-        if ((w[j] >> (uint32_t)((key >> (3 * (D - l))) & 31u)) & 1u) L = l;
-    }
-    return L;
+    const uint32_t key =
+        spread3_10((uint32_t)cx) | (spread3_10((uint32_t)cy) << 1) | (spread3_10((uint32_t)cz) << 2);
+    const int L = bitmap_level<uint32_t>(T, D, G, key);
+    return L0 < G ? L0 : L;
 }
 
 struct GuideArgs {
@@ -1367,7 +1374,9 @@ static void trace_setup(const wfpg_svo* s, const wfpg_guide_params* p, TraceArgs
         const int l = T->G + 1 + j;
         T->occ_off[j] = (s->occ && l <= s->D) ? (uint32_t)s->occ_off[l] : 0u;
     }
-    T->flat = T->G >= 0 && (T->G == s->D || s->occ != nullptr);
+    // the flat walk of the generic kernels uses 32-bit Morton keys: up to depth 10 (the stream
+    // kernel specialised on depth 11 turns it on for itself)
+    T->flat = T->G >= 0 && (T->G == s->D || s->occ != nullptr) && s->D <= 10;
     G->N = p->N;
     G->eps = p->eps;
     G->jitter = p->jitter;
@@ -1411,6 +1420,7 @@ static int launch_stream(const wfpg_svo* s, const TraceArgs& T0, const GuideArgs
                          float* cdf_row, float* cdf_marg, cudaStream_t st) {
     TraceArgs T = T0;
     T.smem_nodes = 0;  // no node cache: the flat walk reads nodes only below the index
+    T.flat = 1;
     auto kernel = k_guide_stream<kThreads, kD>;
     const size_t smem = sizeof(float) * (size_t)(kThreads / 32) * kWbWords * 32 +
                         sizeof(uint32_t) * (size_t)(kThreads / 32) * kHitQueue * kHitWords;
@@ -1455,8 +1465,10 @@ int guide_build_impl(const wfpg_svo* s, const float* pos, const uint32_t* origin
     TraceArgs T;
     GuideArgs G;
     trace_setup(s, p, &T, &G, frame_dev);
-    if (T.flat && p->parts == 0) {  // flat index: every bin's cone rays as one stream, then the per-bin finish
-        const int threads = p->block ? p->block : kGuideDefaultThreadsMid;
+    const int sthreads = p->block ? p->block : kGuideDefaultThreadsMid;
+    const bool wide_flat = s->D == 11 && s->occ != nullptr && s->top_levels > 0 && sthreads == 128;
+    if ((T.flat || wide_flat) && p->parts == 0) {  // flat index: every bin's cone rays as one stream, then the per-bin finish
+        const int threads = sthreads;
         // the default block size has kernels specialised on the SVO depth 6 .. 11 (constant shifts and loop bounds)
 #define WFPG_STREAM(TH, KD) launch_stream<TH, KD>(s, T, G, pos, origin_ray, n_bins_dev, bin_cap, pdf, cdf_row, cdf_marg, st)
         if (threads == 128) {
