@@ -339,6 +339,31 @@ def test_guide_build_tile_variants(block, stage):
     assert g.status() == 0
 
 
+@pytest.mark.parametrize("D", [7, 8, 10])
+def test_field_kernel_depth_specialisations(D):
+    """The stream field kernel is compiled for each SVO depth 6 .. 11 (depths 6, 9 and 11 run in
+    the tests above): at depths 7, 8 and 10 its fields equal the oracle's bit for bit."""
+    sc = inputs.small_deep(1)
+    g, o = build_both(sc, D)
+    rng = np.random.default_rng(7)
+    pos, nrm, prim = inputs.surface_points(sc, rng, 20000)
+    wout = inputs.cosine_dirs(nrm, rng).astype(np.float32)
+    L = np.where(prim == 3, 10.0, sc.albedo[prim] * 10.0 * rng.uniform(0, 1, len(prim))).astype(np.float32)
+    W.svo_accumulate(g, dev(pos), dev(wout), dev(L))
+    o.accumulate(pos, wout, L)
+    rp, rn, _ = inputs.surface_points(sc, np.random.default_rng(8), 3001)
+    r = W.bin_rays(g, dev(rp), dev(rn), l_min=3, c_ray=64, seed=5, frame=2)
+    ro = o.bin_rays(rp, rn, l_min=3, c_ray=64, seed=5, frame=2)
+    nb = ro["n_bins"]
+    np.testing.assert_array_equal(u32(r["origin_ray"])[:nb], ro["origin_ray"][:nb])
+    pdf, cr, cm = W.guide_build_pdf(g, dev(rp), r["origin_ray"], r["n_bins"], r["bin_cap"], N=16, jitter=True,
+                                    blur=True, seed=5, frame=2)
+    sel = np.arange(0, nb, max(1, nb // 16))
+    og = o.guide_build(rp[ro["origin_ray"][sel]], sel, 16, jitter=True, blur=True, seed=5, frame=2)
+    assert np.array_equal(pdf.cpu().numpy()[sel], og["pdf"])
+    assert g.status() == 0
+
+
 # ------------------------------------------------------------------ maximum depth
 def test_depth_11_end_to_end_exact():
     """Depth 11 (2048^3, 33-bit Morton keys): SVO layout, exitance sums, bins,
