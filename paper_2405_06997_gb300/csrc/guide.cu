@@ -955,6 +955,9 @@ __global__ void __launch_bounds__(kGuideThreads, 1024 / kGuideThreads)
 // different bins.  No barrier holds a warp back at the end of a bin.  eps + L
 // of each cell goes to the bin's pdf row (leaf hits through the warp's queue);
 // k_field_pdf then blurs the rows and builds the PDF and CDFs in place.
+// walk steps a lane may take per pass of the stream kernel's loop before the warp meets again
+// (3 measured best: 2 shares less of the pass overhead, 4 and more let the lanes drift apart)
+constexpr int kStreamSteps = 3;
 template <int kGuideThreads, int kD>
 __global__ void __launch_bounds__(kGuideThreads, 1024 / kGuideThreads)
     k_guide_stream(TraceArgs T, GuideArgs G, const float* __restrict__ pos, const uint32_t* __restrict__ origin_ray,
@@ -1085,43 +1088,47 @@ __global__ void __launch_bounds__(kGuideThreads, 1024 / kGuideThreads)
             break;
         }
         if (q < 0) continue;
-        // ---- one step: the cell's deepest existing level, then its hit or the skip of its empty block
-        if (level < 0) level = deepest_level<kD>(T, cx, cy, cz);
+        // ---- up to kStreamSteps steps: the cell's deepest existing level, then its hit or the skip
+        // of its empty block (the pass overhead of the queue and the hand-out is shared by them)
         bool done = false;
-        if (level == D && t >= T.t_skip) {
-            pend = true;  // its cone query waits in the warp's queue
-        } else {
-            const int sl = (level == D) ? 0 : D - level - 1;
-            const int size = 1 << sl;
-            const int bx = (cx >> sl) << sl, by = (cy >> sl) << sl, bz = (cz >> sl) << sl;
-            const int ex = ivx > 0.0f ? bx + size : bx - 1;
-            const int ey = ivy > 0.0f ? by + size : by - 1;
-            const int ez = ivz > 0.0f ? bz + size : bz - 1;
-            const float tex = ivx != 0.0f ? cross_time(ex, ivx > 0.0f, gx, ivx) : INF;
-            const float tey = ivy != 0.0f ? cross_time(ey, ivy > 0.0f, gy, ivy) : INF;
-            const float tez = ivz != 0.0f ? cross_time(ez, ivz > 0.0f, gz, ivz) : INF;
-            const int a = (tex <= tey && tex <= tez) ? 0 : (tey <= tez ? 1 : 2);
-            const float tx = a == 0 ? tex : (a == 1 ? tey : tez);
-            const int p = a == 0 ? 1 : 0, pq = a == 2 ? 1 : 2;
-            const int cp = p == 0 ? cx : cy, cq = pq == 1 ? cy : cz;
-            const int bp = p == 0 ? bx : by, bq = pq == 1 ? by : bz;
-            const float gp = p == 0 ? gx : gy, gq = pq == 1 ? gy : gz;
-            const float ip = p == 0 ? ivx : ivy, iq = pq == 1 ? ivy : ivz;
-            const float dp = p == 0 ? dx : dy, dq = pq == 1 ? dy : dz;
-            const int np = advance_axis(cp, bp, size, gp, ip, __fmul_rn(dp, T.scale), tx, p < a);
-            const int nq = advance_axis(cq, bq, size, gq, iq, __fmul_rn(dq, T.scale), tx, pq < a);
-            const int na = a == 0 ? ex : (a == 1 ? ey : ez);
-            if (tx == INF || na < 0 || na >= res) {
-                done = true;  // left the grid: miss
-            } else if (++steps > cap) {
-                atomicOr(status, (uint32_t)WFPG_STATUS_TRACE_CAP);
-                done = true;
+#pragma unroll 1
+        for (int ks = 0; ks < kStreamSteps && !done && !pend; ++ks) {
+            if (level < 0) level = deepest_level<kD>(T, cx, cy, cz);
+            if (level == D && t >= T.t_skip) {
+                pend = true;  // its cone query waits in the warp's queue
             } else {
-                cx = a == 0 ? na : np;
-                cy = a == 1 ? na : (p == 1 ? np : nq);
-                cz = a == 2 ? na : nq;
-                t = tx;
-                level = -1;
+                const int sl = (level == D) ? 0 : D - level - 1;
+                const int size = 1 << sl;
+                const int bx = (cx >> sl) << sl, by = (cy >> sl) << sl, bz = (cz >> sl) << sl;
+                const int ex = ivx > 0.0f ? bx + size : bx - 1;
+                const int ey = ivy > 0.0f ? by + size : by - 1;
+                const int ez = ivz > 0.0f ? bz + size : bz - 1;
+                const float tex = ivx != 0.0f ? cross_time(ex, ivx > 0.0f, gx, ivx) : INF;
+                const float tey = ivy != 0.0f ? cross_time(ey, ivy > 0.0f, gy, ivy) : INF;
+                const float tez = ivz != 0.0f ? cross_time(ez, ivz > 0.0f, gz, ivz) : INF;
+                const int a = (tex <= tey && tex <= tez) ? 0 : (tey <= tez ? 1 : 2);
+                const float tx = a == 0 ? tex : (a == 1 ? tey : tez);
+                const int p = a == 0 ? 1 : 0, pq = a == 2 ? 1 : 2;
+                const int cp = p == 0 ? cx : cy, cq = pq == 1 ? cy : cz;
+                const int bp = p == 0 ? bx : by, bq = pq == 1 ? by : bz;
+                const float gp = p == 0 ? gx : gy, gq = pq == 1 ? gy : gz;
+                const float ip = p == 0 ? ivx : ivy, iq = pq == 1 ? ivy : ivz;
+                const float dp = p == 0 ? dx : dy, dq = pq == 1 ? dy : dz;
+                const int np = advance_axis(cp, bp, size, gp, ip, __fmul_rn(dp, T.scale), tx, p < a);
+                const int nq = advance_axis(cq, bq, size, gq, iq, __fmul_rn(dq, T.scale), tx, pq < a);
+                const int na = a == 0 ? ex : (a == 1 ? ey : ez);
+                if (tx == INF || na < 0 || na >= res) {
+                    done = true;  // left the grid: miss
+                } else if (++steps > cap) {
+                    atomicOr(status, (uint32_t)WFPG_STATUS_TRACE_CAP);
+                    done = true;
+                } else {
+                    cx = a == 0 ? na : np;
+                    cy = a == 1 ? na : (p == 1 ? np : nq);
+                    cz = a == 2 ? na : nq;
+                    t = tx;
+                    level = -1;
+                }
             }
         }
         if (done) {
