@@ -98,8 +98,9 @@ __device__ __forceinline__ int bitmap_level(const TraceArgs& T, int D, int G, Ke
 #pragma unroll
     for (int j = 0; j < kOccMaxDepth - kTopLevelMax; ++j) {
         const int l = G + 1 + j;
-        if (l > D || L != l - 1) break;
-        if ((w[j] >> (uint32_t)((key >> (3 * (D - l))) & 31u)) & 1u) L = l;
+        if (l > D) break;
+        // a select rather than an early exit: every lane runs the same few iterations
+        if (L == l - 1 && ((w[j] >> (uint32_t)((key >> (3 * (D - l))) & 31u)) & 1u)) L = l;
     }
     return L;
 }
@@ -950,14 +951,18 @@ __global__ void __launch_bounds__(kGuideThreads, 1024 / kGuideThreads)
 
 // Unfused fields over a flat SVO index: the cone rays of every bin as one
 // stream.  Each warp takes batches of 32 cells of one bin from a counter over
-// all bins, sets up their rays, and hands a ray to each lane as it frees; a
-// lane keeps its ray's own origin, so lanes of a warp may march rays of
-// different bins.  No barrier holds a warp back at the end of a bin.  eps + L
-// of each cell goes to the bin's pdf row (leaf hits through the warp's queue);
-// k_field_pdf then blurs the rows and builds the PDF and CDFs in place.
+// all bins, sets up their rays (keeping only those alive at their start) and
+// hands a ray to each lane as it frees; a lane keeps its ray's own origin, so
+// lanes of a warp may march rays of different bins.  No barrier holds a warp
+// back at the end of a bin.  eps + L of each cell goes to the bin's pdf row
+// (leaf hits through the warp's queue); k_field_pdf then blurs the rows and
+// builds the PDF and CDFs in place.
 // walk steps a lane may take per pass of the stream kernel's loop before the warp meets again
 // (3 measured best: 2 shares less of the pass overhead, 4 and more let the lanes drift apart)
 constexpr int kStreamSteps = 3;
+// the same once the warp's batches have run out: no lane can take new work, so a longer pass
+// only saves the pass overhead of the few rays left (16 measured best of 8, 16 and 64)
+constexpr int kStreamDrySteps = 16;
 template <int kGuideThreads, int kD>
 __global__ void __launch_bounds__(kGuideThreads, 1024 / kGuideThreads)
     k_guide_stream(TraceArgs T, GuideArgs G, const float* __restrict__ pos, const uint32_t* __restrict__ origin_ray,
@@ -1011,17 +1016,23 @@ __global__ void __launch_bounds__(kGuideThreads, 1024 / kGuideThreads)
             hq_n += __popc(hm);
             __syncwarp();
         }
-        const bool idle = q < 0;
-        const uint32_t need = __ballot_sync(0xffffffffu, idle);
-        if (need && wb_head == wb_n && !dry) {
-            // the next batch of 32 cells of some bin: origin, then every lane sets up one ray
-            uint32_t batch = 0;
-            if (lane == 0) batch = atomicAdd(batch_next, 1u);
-            batch = __shfl_sync(0xffffffffu, batch, 0);
-            if (batch >= n_batches) {
-                dry = true;
-                wb_n = wb_head = 0;
-            } else {
+        // hand out buffered rays to idle lanes; an empty buffer takes the next batch of 32 cells of
+        // some bin (origin, then every lane sets up one ray; only rays alive at their start are kept)
+#pragma unroll 1
+        for (int round = 0; round < 4; ++round) {
+            const bool idle = q < 0;
+            const uint32_t need = __ballot_sync(0xffffffffu, idle);
+            if (!need) break;
+            if (wb_head == wb_n) {
+                if (dry) break;
+                uint32_t batch = 0;
+                if (lane == 0) batch = atomicAdd(batch_next, 1u);
+                batch = __shfl_sync(0xffffffffu, batch, 0);
+                if (batch >= n_batches) {
+                    dry = true;
+                    wb_n = wb_head = 0;
+                    break;
+                }
                 const uint32_t b = batch / per_bin;
                 const int c = (int)(batch % per_bin) * 32 + lane;
                 const uint32_t r = origin_ray ? origin_ray[b] : b;
@@ -1043,27 +1054,30 @@ __global__ void __launch_bounds__(kGuideThreads, 1024 / kGuideThreads)
                 const bool alive = ray_start(T, r != kNone, inside, bgx, bgy, bgz, d.x, d.y, d.z, iv.x, iv.y, iv.z,
                                              res, fres, &t0, &x0, &y0, &z0);
                 const int g = (int)b * NN + c;
-                if (!alive) raw[g] = __fadd_rn(G.eps, 0.0f);
-                wb[0 * 32 + lane] = __int_as_float(alive ? g : -1);
-                wb[1 * 32 + lane] = d.x;
-                wb[2 * 32 + lane] = d.y;
-                wb[3 * 32 + lane] = d.z;
-                wb[4 * 32 + lane] = iv.x;
-                wb[5 * 32 + lane] = iv.y;
-                wb[6 * 32 + lane] = iv.z;
-                wb[7 * 32 + lane] = t0;
-                wb[8 * 32 + lane] = __int_as_float(x0);
-                wb[9 * 32 + lane] = __int_as_float(y0);
-                wb[10 * 32 + lane] = __int_as_float(z0);
-                wb_n = 32;
+                const uint32_t am = __ballot_sync(0xffffffffu, alive);
+                if (!alive) {
+                    raw[g] = __fadd_rn(G.eps, 0.0f);
+                } else {
+                    const int k = __popc(am & lt);
+                    wb[0 * 32 + k] = __int_as_float(g);
+                    wb[1 * 32 + k] = d.x;
+                    wb[2 * 32 + k] = d.y;
+                    wb[3 * 32 + k] = d.z;
+                    wb[4 * 32 + k] = iv.x;
+                    wb[5 * 32 + k] = iv.y;
+                    wb[6 * 32 + k] = iv.z;
+                    wb[7 * 32 + k] = t0;
+                    wb[8 * 32 + k] = __int_as_float(x0);
+                    wb[9 * 32 + k] = __int_as_float(y0);
+                    wb[10 * 32 + k] = __int_as_float(z0);
+                }
+                wb_n = __popc(am);
                 wb_head = 0;
+                __syncwarp();
             }
-            __syncwarp();
-        }
-        if (need && wb_head < wb_n) {
             const int k = wb_head + __popc(need & lt);
             if (idle && k < wb_n) {
-                q = __float_as_int(wb[0 * 32 + k]);  // -1: the ray died at its start
+                q = __float_as_int(wb[0 * 32 + k]);
                 dx = wb[1 * 32 + k];
                 dy = wb[2 * 32 + k];
                 dz = wb[3 * 32 + k];
@@ -1088,11 +1102,13 @@ __global__ void __launch_bounds__(kGuideThreads, 1024 / kGuideThreads)
             break;
         }
         if (q < 0) continue;
-        // ---- up to kStreamSteps steps: the cell's deepest existing level, then its hit or the skip
-        // of its empty block (the pass overhead of the queue and the hand-out is shared by them)
+        // ---- up to kStreamSteps steps (kStreamDrySteps once no batch is left): the cell's deepest
+        // existing level, then its hit or the skip of its empty block (the pass overhead of the
+        // queue and the hand-out is shared by them)
         bool done = false;
+        const int nsteps = dry ? kStreamDrySteps : kStreamSteps;
 #pragma unroll 1
-        for (int ks = 0; ks < kStreamSteps && !done && !pend; ++ks) {
+        for (int ks = 0; ks < nsteps && !done && !pend; ++ks) {
             if (level < 0) level = deepest_level<kD>(T, cx, cy, cz);
             if (level == D && t >= T.t_skip) {
                 pend = true;  // its cone query waits in the warp's queue
