@@ -224,6 +224,33 @@ def test_guide_build_matches_oracle(N, jitter, blur):
     assert g.status() == 0
 
 
+def test_field_from_origins_outside_the_box():
+    """Cone rays from origins outside the SVO's box (Sec. 3.3): most of each
+    32-cell batch misses the box and ends at its start, so the stream kernel's
+    batches keep few or no live rays and its lanes refill over several rounds;
+    some origins inside the box mix both kinds of batch.  Fields equal the
+    oracle's bit for bit."""
+    w = inputs.tiny_box(6, n_rays=64)
+    g, o = build_both(w.scene, w.depth)
+    W.svo_accumulate(g, dev(w.rec_pos), dev(w.rec_wout), dev(w.rec_L))
+    o.accumulate(w.rec_pos, w.rec_wout, w.rec_L)
+    rng = np.random.default_rng(5)
+    v = rng.normal(size=(48, 3))
+    outside = 0.5 + 1.2 * v / np.linalg.norm(v, axis=1, keepdims=True)  # farther than the corners (0.87)
+    inside = rng.uniform(0.1, 0.9, size=(16, 3))
+    org = np.concatenate([outside, inside]).astype(np.float32)
+    n = len(org)
+    pdf, cr, cm = W.guide_build_pdf(g, dev(org), None, None, n, N=16, jitter=True, blur=True, seed=7, frame=3)
+    og = o.guide_build(org, np.arange(n), 16, jitter=True, blur=True, seed=7, frame=3)
+    assert np.array_equal(pdf.cpu().numpy(), og["pdf"])
+    np.testing.assert_allclose(cr.cpu().numpy(), og["cdf_row"], rtol=RTOL, atol=0)
+    np.testing.assert_allclose(cm.cpu().numpy(), og["cdf_marg"], rtol=RTOL, atol=0)
+    # the outside origins see the box in a minority of their cells; the rest hold eps only
+    field_min = og["pdf"][:48].min(axis=1, keepdims=True)
+    assert np.mean(og["pdf"][:48] == field_min) > 0.5
+    assert g.status() == 0
+
+
 @pytest.mark.parametrize("N", [16, 32])
 def test_sample_and_eval_match_oracle(N):
     w = inputs.tiny_box(7, n_rays=4099)
