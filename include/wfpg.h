@@ -57,7 +57,9 @@ enum {
     WFPG_STATUS_TRACE_CAP = 1u << 0,    /* a cone ray hit the walk's step cap (treated as a miss) */
     WFPG_STATUS_BIN_CAPACITY = 1u << 1, /* bin_rays found more bins than bin_cap */
     WFPG_STATUS_RUN_SIZES = 1u << 2,    /* run sizes do not add up to the ray count */
-    WFPG_STATUS_MMA_TIMEOUT = 1u << 3   /* a tensor-core wait hit its limit (results invalid) */
+    WFPG_STATUS_MMA_TIMEOUT = 1u << 3,  /* a tensor-core wait hit its limit (results invalid) */
+    WFPG_STATUS_WAIT_TIMEOUT = 1u << 4  /* a block's wait for an earlier block of the same launch
+                                           hit its limit (the sort behind bin_rays; results invalid) */
 };
 
 #define WFPG_MAX_DEPTH 11
@@ -182,7 +184,10 @@ WFPG_API int bin_rays_workspace_size(const wfpg_svo* svo, uint32_t n, const wfpg
  * WFPG_STATUS_BIN_CAPACITY is set.  `workspace` holds at least
  * bin_rays_workspace_size() bytes (256-byte aligned); its contents on entry
  * do not matter.  nrm (xyz) is only read in RUNS mode (may be NULL
- * otherwise), sizes only in RUNS mode.
+ * otherwise), sizes only in RUNS mode.  The rays are ordered by a stable
+ * radix sort whose blocks wait for earlier blocks' digit counts; each wait is
+ * bounded, and WFPG_STATUS_WAIT_TIMEOUT is set (the bins are then invalid) if
+ * one runs out.
  */
 WFPG_API int bin_rays(const wfpg_svo* svo, const float* pos, const float* nrm, uint32_t n,
              const wfpg_bin_params* p, const uint32_t* sizes, uint32_t* bin_of_ray,

@@ -246,7 +246,7 @@ int bin_rays_impl(const wfpg_svo* s, const float* pos, const float* nrm, uint32_
         if (n > 0)
             WFPG_LAUNCH(k_bin_ids, div_up(n, T), T, 0, st, ray_node, n, nd, used, bin_of_ray, keys, vals);
         const uint64_t max_bins = n < s->n_nodes ? n : s->n_nodes;
-        radix_sort_pairs_u32(keys, keys_alt, vals, vals_alt, n, bits_for(max_bins), ws, st, &skeys, &svals);
+        radix_sort_pairs_u32(keys, keys_alt, vals, vals_alt, n, bits_for(max_bins), ws, st, &skeys, &svals, s->status);
         if (n > 0 && svals != ray_order)
             cudaMemcpyAsync(ray_order, svals, 4 * (size_t)n, cudaMemcpyDeviceToDevice, st);
         WFPG_LAUNCH(k_bin_offsets, div_up(n + 1, T), T, 0, st, skeys, n, nd, bin_offset, bin_cap, n_bins_dev, s->status);
@@ -258,7 +258,7 @@ int bin_rays_impl(const wfpg_svo* s, const float* pos, const float* nrm, uint32_
         if (n > 0)
             WFPG_LAUNCH(k_runs_keys, div_up(n, T), T, 0, st, pos, nrm, n, nd, s->lo[0], s->lo[1], s->lo[2], s->scale, D,
                         keys, vals);
-        radix_sort_pairs_u32(keys, keys_alt, vals, vals_alt, n, 3 * q + 3, ws, st, &skeys, &svals);
+        radix_sort_pairs_u32(keys, keys_alt, vals, vals_alt, n, 3 * q + 3, ws, st, &skeys, &svals, s->status);
         if (n > 0 && svals != ray_order)
             cudaMemcpyAsync(ray_order, svals, 4 * (size_t)n, cudaMemcpyDeviceToDevice, st);
         scan_exclusive(sizes, bin_offset, p->n_sizes, tot, ws, st);

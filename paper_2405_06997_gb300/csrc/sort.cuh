@@ -44,8 +44,10 @@ size_t radix_sort_workspace_bytes(uint32_t n);
 // ends in whichever buffer the returned pointers name.
 void radix_sort_u64(uint64_t* keys, uint64_t* keys_alt, uint32_t n, int bits, Arena& ws,
                     cudaStream_t s, uint64_t** sorted);
+// status (may be null): WFPG_STATUS_WAIT_TIMEOUT is or-ed into it when a wait of the one-sweep
+// passes runs out (the result is then invalid)
 void radix_sort_pairs_u32(uint32_t* keys, uint32_t* keys_alt, uint32_t* vals, uint32_t* vals_alt,
                           uint32_t n, int bits, Arena& ws, cudaStream_t s, uint32_t** keys_out,
-                          uint32_t** vals_out);
+                          uint32_t** vals_out, uint32_t* status);
 
 }  // namespace wfpg

@@ -30,6 +30,7 @@ ERRORS = {-1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "TIMEOUT", -5: "CAPACITY
 STATUS_TRACE_CAP = 1
 STATUS_BIN_CAPACITY = 2
 STATUS_RUN_SIZES = 4
+STATUS_WAIT_TIMEOUT = 16  # a wait inside the binning's sort ran out (results invalid)
 BIN_PARTITION_S = 0
 BIN_RUNS = 1
 MAX_DEPTH = 11
