@@ -208,7 +208,7 @@ WFPG_API int bin_rays(const wfpg_svo* svo, const float* pos, const float* nrm, u
  * reserved on every GPU that loads the library and held until the process
  * exits.  It calls no cudaMalloc, cudaFree or allocating routine.
  * Limit: the scratch bin_rays_workspace_size() reports for the same call must
- * fit in WFPG_BIN_STATIC_SCRATCH_BYTES (about 2M rays in RUNS mode; in
+ * fit in WFPG_BIN_STATIC_SCRATCH_BYTES (about 2.7M rays in RUNS mode; in
  * PARTITION_S mode 4 more bytes per ray and 12 per SVO node count too), otherwise the call
  * returns WFPG_ERR_CAPACITY and does nothing.
  * The first call on each device looks up the array's device address with the

@@ -192,9 +192,17 @@ static int bits_for(uint64_t max_value) {
     return b;
 }
 
+// The sort alternates between its two value buffers, one 8-bit pass each, so
+// the ray order ends in the caller's ray_order without a copy when the pass
+// count picks which buffer the ray indices start in.
+static uint32_t* sort_values_start(int bits, uint32_t* ray_order, uint32_t* vals) {
+    const int b = bits < 32 ? bits : 32;
+    return ((b + 7) / 8) % 2 == 0 ? ray_order : vals;
+}
+
 size_t bin_workspace_bytes(const wfpg_svo* s, uint32_t n, int mode, uint32_t n_sizes) {
     size_t b = 0;
-    b += 4 * arena_bytes<uint32_t>(n);                     // keys, keys_alt, vals, vals_alt
+    b += 3 * arena_bytes<uint32_t>(n);                     // keys, keys_alt, vals (ray_order is the 4th)
     b += radix_sort_workspace_bytes(n);
     if (mode == WFPG_BIN_PARTITION_S) {
         b += arena_bytes<uint32_t>(n);                     // ray_node
@@ -217,7 +225,6 @@ int bin_rays_impl(const wfpg_svo* s, const float* pos, const float* nrm, uint32_
     uint32_t* keys = ws.take<uint32_t>(n);
     uint32_t* keys_alt = ws.take<uint32_t>(n);
     uint32_t* vals = ws.take<uint32_t>(n);
-    uint32_t* vals_alt = ws.take<uint32_t>(n);
     if (ws.overflow) return WFPG_ERR_INVALID_ARG;
     uint32_t* skeys = nullptr;
     uint32_t* svals = nullptr;
@@ -243,10 +250,13 @@ int bin_rays_impl(const wfpg_svo* s, const float* pos, const float* nrm, uint32_
         if (n > 0)
             WFPG_LAUNCH(k_bin_ascend, div_up(n, T), T, 0, st, ray_node, n, nd, L, D, l_min, s->parent, total, used);
         scan_exclusive(used, used, s->n_nodes, n_bins_dev, ws, st);
-        if (n > 0)
-            WFPG_LAUNCH(k_bin_ids, div_up(n, T), T, 0, st, ray_node, n, nd, used, bin_of_ray, keys, vals);
         const uint64_t max_bins = n < s->n_nodes ? n : s->n_nodes;
-        radix_sort_pairs_u32(keys, keys_alt, vals, vals_alt, n, bits_for(max_bins), ws, st, &skeys, &svals, s->status);
+        const int bits = bits_for(max_bins);
+        uint32_t* v0 = sort_values_start(bits, ray_order, vals);
+        uint32_t* v1 = v0 == ray_order ? vals : ray_order;
+        if (n > 0)
+            WFPG_LAUNCH(k_bin_ids, div_up(n, T), T, 0, st, ray_node, n, nd, used, bin_of_ray, keys, v0);
+        radix_sort_pairs_u32(keys, keys_alt, v0, v1, n, bits, ws, st, &skeys, &svals, s->status);
         if (n > 0 && svals != ray_order)
             cudaMemcpyAsync(ray_order, svals, 4 * (size_t)n, cudaMemcpyDeviceToDevice, st);
         WFPG_LAUNCH(k_bin_offsets, div_up(n + 1, T), T, 0, st, skeys, n, nd, bin_offset, bin_cap, n_bins_dev, s->status);
@@ -255,10 +265,13 @@ int bin_rays_impl(const wfpg_svo* s, const float* pos, const float* nrm, uint32_
         const int q = D < 6 ? D : 6;
         uint32_t* tot = ws.take<uint32_t>(1);
         if (ws.overflow) return WFPG_ERR_INVALID_ARG;
+        const int bits = 3 * q + 3;
+        uint32_t* v0 = sort_values_start(bits, ray_order, vals);
+        uint32_t* v1 = v0 == ray_order ? vals : ray_order;
         if (n > 0)
             WFPG_LAUNCH(k_runs_keys, div_up(n, T), T, 0, st, pos, nrm, n, nd, s->lo[0], s->lo[1], s->lo[2], s->scale, D,
-                        keys, vals);
-        radix_sort_pairs_u32(keys, keys_alt, vals, vals_alt, n, 3 * q + 3, ws, st, &skeys, &svals, s->status);
+                        keys, v0);
+        radix_sort_pairs_u32(keys, keys_alt, v0, v1, n, bits, ws, st, &skeys, &svals, s->status);
         if (n > 0 && svals != ray_order)
             cudaMemcpyAsync(ray_order, svals, 4 * (size_t)n, cudaMemcpyDeviceToDevice, st);
         scan_exclusive(sizes, bin_offset, p->n_sizes, tot, ws, st);

@@ -88,7 +88,7 @@ def test_static_scratch_calls_allocate_nothing():
 def test_static_scratch_rejects_calls_that_do_not_fit():
     w = inputs.tiny_box(4, n_rays=10)
     svo = W.svo_from_scene(w.scene, w.depth)
-    n = 3_000_000   # RUNS mode needs ~16 B per ray: more than the 32 MiB scratch
+    n = 3_000_000   # RUNS mode needs ~12.3 B per ray: more than the 32 MiB scratch
     pos = torch.zeros((n, 3), dtype=torch.float32, device="cuda")
     sizes = torch.tensor([n], dtype=torch.int32, device="cuda")
     with pytest.raises(W.WfpgError) as e:
