@@ -257,6 +257,7 @@ int bin_rays_impl(const wfpg_svo* s, const float* pos, const float* nrm, uint32_
         if (n > 0)
             WFPG_LAUNCH(k_bin_ids, div_up(n, T), T, 0, st, ray_node, n, nd, used, bin_of_ray, keys, v0);
         radix_sort_pairs_u32(keys, keys_alt, v0, v1, n, bits, ws, st, &skeys, &svals, s->status);
+        if (ws.overflow) return WFPG_ERR_INVALID_ARG;  // the sort's look-back words did not fit
         if (n > 0 && svals != ray_order)
             cudaMemcpyAsync(ray_order, svals, 4 * (size_t)n, cudaMemcpyDeviceToDevice, st);
         WFPG_LAUNCH(k_bin_offsets, div_up(n + 1, T), T, 0, st, skeys, n, nd, bin_offset, bin_cap, n_bins_dev, s->status);
@@ -272,6 +273,7 @@ int bin_rays_impl(const wfpg_svo* s, const float* pos, const float* nrm, uint32_
             WFPG_LAUNCH(k_runs_keys, div_up(n, T), T, 0, st, pos, nrm, n, nd, s->lo[0], s->lo[1], s->lo[2], s->scale, D,
                         keys, v0);
         radix_sort_pairs_u32(keys, keys_alt, v0, v1, n, bits, ws, st, &skeys, &svals, s->status);
+        if (ws.overflow) return WFPG_ERR_INVALID_ARG;  // the sort's look-back words did not fit
         if (n > 0 && svals != ray_order)
             cudaMemcpyAsync(ray_order, svals, 4 * (size_t)n, cudaMemcpyDeviceToDevice, st);
         scan_exclusive(sizes, bin_offset, p->n_sizes, tot, ws, st);
