@@ -5,8 +5,9 @@
 // every (digit, tile) output base, (3) a stable scatter: each tile ranks its
 // keys round by round (256 keys per round, lane order inside a warp from
 // __match_any_sync, warp order from a per-round prefix over per-warp digit
-// counts).  32-bit keys with values (the binning): the same ranking, but one
-// launch per pass, the tile bases found by decoupled look-back (below).
+// counts).  32-bit keys with values (the binning): one launch per pass, each
+// warp ranking its own run of the tile's keys, the tile bases found by
+// decoupled look-back (below).
 #include <algorithm>
 #include <utility>
 
@@ -181,7 +182,9 @@ __global__ void __launch_bounds__(kSortBlock) k_radix_scatter(const K* __restric
 // ---------------------------------------------------------------------------
 // One-sweep LSD radix sort of 32-bit keys with values (8-bit digits).  One
 // kernel counts the digits of every pass over the whole input; then one kernel
-// per pass ranks each tile's keys (stable, as above), publishes the tile's
+// per pass ranks each tile's keys (stable: each warp ranks 512 consecutive
+// keys against its own digit counters, with warp barriers only, then one block
+// barrier turns the warps' counts into their bases), publishes the tile's
 // digit counts, adds up the counts of all earlier tiles by looking back over
 // what they published (decoupled look-back), and scatters.  A block takes its
 // tile from a ticket counter, so it only ever waits on tiles held by blocks
@@ -235,9 +238,8 @@ __global__ void __launch_bounds__(kSortBlock) k_sweep_pass(const uint32_t* __res
                                                            const uint32_t* __restrict__ ghist, uint32_t* look,
                                                            uint32_t* ticket, uint32_t* status) {
     constexpr int W = kSortBlock / 32;
-    __shared__ uint32_t whist[W][257];
-    __shared__ uint32_t wbase[W][257];
-    __shared__ uint32_t run[256];
+    constexpr int kWarpKeys = 32 * kSortItems;  // each warp ranks 512 consecutive keys of the tile
+    __shared__ uint32_t whist[W][256];          // per warp: its keys of each digit so far, then its base
     __shared__ uint32_t start[256];
     __shared__ uint32_t wt[kScanBlock / 32];
     __shared__ uint32_t s_tile;
@@ -246,44 +248,47 @@ __global__ void __launch_bounds__(kSortBlock) k_sweep_pass(const uint32_t* __res
     const int shift = 8 * pass;
     const uint32_t tag = (uint32_t)(pass + 1) << kLbTagShift;
     if (tid == 0) s_tile = atomicAdd(ticket + pass, 1u);
-    for (int i = tid; i < W * 257; i += kSortBlock) (&whist[0][0])[i] = 0u;
-    run[tid] = 0u;
+    for (int i = tid; i < W * 256; i += kSortBlock) (&whist[0][0])[i] = 0u;
     // where each digit's keys start in the output (exclusive scan of the pass's counts)
     uint32_t total;
     const uint32_t g0 = block_exclusive(ghist[pass * 256 + tid], wt, &total);
     __syncthreads();
     const uint32_t tile = s_tile;
-    const uint32_t base = tile * kSortTile;
-    uint32_t kr[kSortItems], vr[kSortItems], loc[kSortItems];  // loc: digit << 16 | offset among the tile's keys of it
+    const uint32_t base = tile * kSortTile + (uint32_t)w * kWarpKeys;
+    uint32_t* wh = whist[w];
+    // ranks inside the warp's keys (key order: round by round, lanes in order); only this warp
+    // touches its row, so warp barriers suffice
+    uint32_t kr[kSortItems], vr[kSortItems], loc[kSortItems];  // loc: digit << 16 | offset among the warp's keys of it
 #pragma unroll
     for (int r = 0; r < kSortItems; ++r) {
-        const uint32_t e = base + r * kSortBlock + tid;
+        const uint32_t e = base + r * 32 + lane;
         const bool valid = e < n;
         const uint32_t k = valid ? kin[e] : 0u;
         kr[r] = k;
         vr[r] = (kVals && valid) ? vin[e] : 0u;
         const int d = valid ? (int)((k >> shift) & 255u) : 256;
         const uint32_t peers = __match_any_sync(0xffffffffu, d);
-        const uint32_t rank = __popc(peers & lt);
-        if (rank == 0) whist[w][d] = __popc(peers);
-        __syncthreads();
-        {
-            uint32_t acc = run[tid];
-#pragma unroll
-            for (int ww = 0; ww < W; ++ww) {
-                const uint32_t t = whist[ww][tid];
-                wbase[ww][tid] = acc;
-                acc += t;
-                whist[ww][tid] = 0u;
-            }
-            run[tid] = acc;
-            if (tid < W) whist[tid][256] = 0u;
+        const int leader = __ffs(peers) - 1;
+        uint32_t before = 0u;
+        if (valid && lane == leader) {
+            before = wh[d];
+            wh[d] = before + __popc(peers);
         }
-        __syncthreads();
-        loc[r] = valid ? (((uint32_t)d << 16) | (wbase[w][d] + rank)) : 0xFFFFFFFFu;
+        before = __shfl_sync(0xffffffffu, before, leader);
+        __syncwarp();
+        loc[r] = valid ? (((uint32_t)d << 16) | (before + __popc(peers & lt))) : 0xFFFFFFFFu;
+    }
+    __syncthreads();
+    // thread t: digit t.  Each warp's base among the tile's keys of it, and the tile's count.
+    uint32_t run = 0u;
+#pragma unroll
+    for (int ww = 0; ww < W; ++ww) {
+        const uint32_t t = whist[ww][tid];
+        whist[ww][tid] = run;
+        run += t;
     }
     // thread t: digit t.  Publish this tile's count, add up the earlier tiles' counts, publish the sum.
-    const uint32_t cnt = run[tid];
+    const uint32_t cnt = run;
     uint32_t* mine = look + (size_t)tile * 256 + tid;
     uint32_t excl = 0u;
     bool ok = true;
@@ -315,7 +320,8 @@ __global__ void __launch_bounds__(kSortBlock) k_sweep_pass(const uint32_t* __res
 #pragma unroll
     for (int r = 0; r < kSortItems; ++r) {
         if (loc[r] != 0xFFFFFFFFu) {
-            const uint32_t pos = start[loc[r] >> 16] + (loc[r] & 0xFFFFu);
+            const uint32_t dg = loc[r] >> 16;
+            const uint32_t pos = start[dg] + whist[w][dg] + (loc[r] & 0xFFFFu);
             if (pos < n) {  // always, unless a wait ran out above
                 kout[pos] = kr[r];
                 if (kVals) vout[pos] = vr[r];
